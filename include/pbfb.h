@@ -1,0 +1,221 @@
+/*
+ * pbfb -- nonlinear Poisson-Boltzmann FEM-BEM Newton solver for one GPU.
+ *
+ * C ABI of libpbfb.so.  The method is the self-adjusting FEM-BEM coupling of
+ * Guerrero-Montero, Bosy and Cooper (arXiv 2511.21713): the three-region
+ * model of Eq. pbe_vp, the Newton-Raphson iteration of Eqs. NR_main /
+ * Ec_NL_NR / Norma_Newton-Raphson with the cubic Taylor nonlinearity in the
+ * first iteration (Sec. 3.2, scheme T3-HS), the optimal relaxation factor of
+ * Eq. fd=0 found by Newton's method (Appendix A), the L_e skip rule and the
+ * adjustable GMRES tolerance (Appendix B), and the solvation energy of
+ * Eqs. Esolv / Potential_in_Omega_m.
+ *
+ * Discretisation solved (the three-region FEM-BEM system, reduced potential
+ * u = e phi / kB T, lengths in Angstrom):
+ *
+ *   [ A + J(u)           eps_m R_m' M_m    -eps_s R_s' M_s ] [u    ]   [ 0            ]
+ *   [ (M_m/2 + K_L) R_m  -V_L               0              ] [lam_m] = [ <u_coul,psi> ]
+ *   [ (M_s/2 - K_Y) R_s   0                 V_Y            ] [lam_s]   [ 0            ]
+ *
+ * P1 elements everywhere; the volume unknown u lives on every vertex of the
+ * tetrahedral shell Omega_i (including the vertices of Gamma_m and Gamma_s),
+ * lam_m on the vertices of Gamma_m and lam_s on the vertices of Gamma_s, each
+ * surface vertex list sorted by ascending shell vertex id.
+ *
+ * Conventions for every call:
+ *   - return value: PBFB_OK (0) or an error code below; pbfb_last_error()
+ *     then returns a message (thread-local, owned by the library, valid until
+ *     the next call on the same thread).
+ *   - input arrays are copied; the caller keeps ownership.
+ *   - "host" pointers are ordinary CPU memory, "device" pointers are CUDA
+ *     global memory on the device that was current when the mesh was made.
+ *   - all GPU work of a mesh is ordered on the stream given at creation
+ *     (0 = the legacy default stream); calls return after that work is done
+ *     unless stated otherwise.
+ *   - there is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns PBFB_ERR_CUDA.
+ *   - a mesh handle may be used by one thread at a time.
+ */
+#ifndef PBFB_H
+#define PBFB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PBFB_OK = 0,
+  PBFB_ERR_INVALID = 1,        /* bad argument or mesh */
+  PBFB_ERR_CUDA = 2,           /* CUDA runtime error or no device */
+  PBFB_ERR_GMRES_NOCONV = 3,   /* GMRES hit max_gmres above its tolerance */
+  PBFB_ERR_NEWTON_NOCONV = 4,  /* Newton hit max_newton */
+  PBFB_ERR_OMEGA = 5,          /* no relaxation factor reduced ||d|| */
+  PBFB_ERR_NONFINITE = 6,      /* NaN / Inf in a residual, update or energy */
+  PBFB_ERR_OOM = 7,            /* device allocation failed */
+  PBFB_ERR_STATE = 8           /* call out of order (e.g. solve before charges) */
+};
+
+enum { PBFB_FP64 = 0, PBFB_MIXED = 1 };
+enum { PBFB_LINEAR = 0, PBFB_T3 = 1, PBFB_HS = 2 };
+enum { PBFB_GAMMA_M = 0, PBFB_GAMMA_S = 1 };
+
+typedef struct pbfb_mesh pbfb_mesh;
+
+/* Newton options; the defaults (pbfb_default_opts) are the paper's best
+ * Newton configuration (Appendix B: L_e = 0.35, Tol_omega = 0.1,
+ * Tol_GR0 = 1e-3, Tol_GR = 1e-6, Tol_NL = 1e-3; omega_0 = 2 for the T3
+ * iteration and 1 afterwards, Sec. 3.3). */
+typedef struct pbfb_newton_opts {
+  int precision;        /* PBFB_FP64, or PBFB_MIXED: BEM far field in float32 */
+  double tol_nl;        /* stop when e_k = omega ||Delta||_2 < tol_nl */
+  double tol_gmres;     /* final relative GMRES tolerance Tol_GR */
+  double tol_gmres0;    /* initial tolerance Tol_GR0 (linear part, early steps) */
+  double tol_omega;     /* |f_d(omega)| < tol_omega ends the omega search */
+  double L_e;           /* reuse the previous omega once e_k < L_e (0 = never) */
+  double omega0_first;  /* start of the omega search in the first iteration */
+  double omega0_rest;   /* start afterwards */
+  double omega_max;     /* admissible omega in (0, omega_max] */
+  int max_newton;
+  int max_gmres;        /* GMRES iterations per linear solve */
+  int restart;          /* GMRES restart length (<= 400) */
+  int max_omega_iters;
+  int first_scheme;     /* PBFB_T3 (paper) or PBFB_HS */
+  int omega_search;     /* 1: automatic omega; 0: constant omega0_first / omega0_rest */
+} pbfb_newton_opts;
+
+#define PBFB_MAX_TRACE 64
+
+/* Result of one solve; energies in kcal/mol (Eq. Esolv). */
+typedef struct pbfb_result {
+  double dG_total, dG_LC, dG_NC, dG_Omega_i;
+  int status;
+  int newton_iters;
+  int linear_gmres_iters;
+  int omega_fallbacks;                 /* omega searches that needed the scan */
+  int gmres_iters[PBFB_MAX_TRACE];
+  double omega[PBFB_MAX_TRACE];
+  double e[PBFB_MAX_TRACE];            /* e_{k+1} = omega ||Delta||_2 */
+  int omega_evals[PBFB_MAX_TRACE];     /* batched residual evaluations per step */
+  double ms_linear, ms_newton, ms_energy;
+} pbfb_result;
+
+/* Fills *opts with the defaults above. */
+void pbfb_default_opts(pbfb_newton_opts* opts);
+
+/* Creates a mesh on the current CUDA device.
+ *   xyz      host, n_v x 3 float64 vertex coordinates of the shell Omega_i.
+ *   tets     host, n_t x 4 int32 vertex ids (any orientation, nonzero volume).
+ *   gm_tris  host, n_gm x 3 int32 ids of the Gamma_m faces, oriented with the
+ *            normal pointing into Omega_i (out of the solute).
+ *   gs_tris  host, n_gs x 3 int32 ids of the Gamma_s faces, oriented with the
+ *            normal pointing out of Omega_i (into the far field).
+ *   stream   cudaStream_t as an integer (0 = default stream).
+ * The two surfaces must be closed and disjoint, and together be exactly the
+ * boundary faces of the tets (PBFB_ERR_INVALID otherwise).  Builds the CSR
+ * pattern and element-to-slot maps of the FEM rows, the surface quadrature
+ * data, and the Laplace near-field correction of Gamma_m (Sauter-Schwab
+ * quadrature for touching triangle pairs, subdivided quadrature for close
+ * ones).  *out is owned by the caller until pbfb_mesh_destroy. */
+int pbfb_mesh_create(const double* xyz, int32_t n_v, const int32_t* tets, int64_t n_t,
+                     const int32_t* gm_tris, int32_t n_gm, const int32_t* gs_tris, int32_t n_gs,
+                     uintptr_t stream, pbfb_mesh** out);
+
+/* sizes[0..7] = n_v, n_t, n_m, n_s, n = n_v + n_m + n_s, nnz of the FEM rows,
+ * nnz of the Gamma_m and Gamma_s BEM-row sparse parts.  sizes: host. */
+int pbfb_mesh_sizes(const pbfb_mesh* mesh, int64_t* sizes);
+
+/* Shell vertex ids of the vertices of surface `which` (PBFB_GAMMA_M/S), in
+ * the order of the lam_m / lam_s unknowns.  out: host, n_m or n_s int32. */
+int pbfb_surface_vertices(const pbfb_mesh* mesh, int which, int32_t* out);
+
+/* Sets the point charges (host, n_q x 3 positions in Angstrom, n_q charges in
+ * units of e) and computes <sum_k z_k / |x - x_k|, psi_i> on Gamma_m
+ * (the Coulomb data of Sec. 2.3.1).  Charges must be finite; n_q >= 1. */
+int pbfb_charges_set(pbfb_mesh* mesh, const double* xyz, const double* z, int32_t n_q);
+
+/* Full solve (Sec. 2.4): linear part, Newton with the omega search, energy.
+ * eps_in = eps_m, eps_out = eps_s (> 0), kappa >= 0 in 1/Angstrom, T > 0 K.
+ * opts: NULL for the defaults.  u_out (n_v), lam_m_out (n_m), lam_s_out (n_s):
+ * host buffers for Phi_T = Phi_L + Phi_NL, or NULL to skip.  res: host, may
+ * be NULL.  Returns the solve status (also in res->status). */
+int pbfb_solve(pbfb_mesh* mesh, double eps_in, double eps_out, double kappa, double T,
+               const pbfb_newton_opts* opts, double* u_out, double* lam_m_out,
+               double* lam_s_out, pbfb_result* res);
+
+/* As pbfb_solve, with x_out a device buffer of n float64 receiving
+ * [u; lam_m; lam_s] (or NULL). */
+int pbfb_solve_device(pbfb_mesh* mesh, double eps_in, double eps_out, double kappa, double T,
+                      const pbfb_newton_opts* opts, double* x_out_dev, pbfb_result* res);
+
+/* Releases every resource of the mesh (NULL is accepted). */
+int pbfb_mesh_destroy(pbfb_mesh* mesh);
+
+/* Message of the last error on this thread ("" if none). */
+const char* pbfb_last_error(void);
+
+/* ---- Step-level entry points (device pointers), for verification and timing. */
+
+/* Sets eps_in, eps_out, kappa, T and the precision used by the calls below;
+ * builds the Yukawa near-field correction of Gamma_s for this kappa (cached
+ * until kappa changes).  The Jacobian block is reset to J = 0. */
+int pbfb_set_params(pbfb_mesh* mesh, double eps_in, double eps_out, double kappa, double T,
+                    int precision);
+
+/* Step a1 (Eqs. Vector_c, NR_main): for u (device, n_v) and scheme
+ * PBFB_LINEAR / PBFB_T3 / PBFB_HS, stores J(u) = eps_s kappa^2 int F'(u_h) v_i v_j
+ * in the operator's FEM block and, if N_out is not NULL, writes
+ * N(u)_i = eps_s kappa^2 int F(u_h) v_i (device, n_v). */
+int pbfb_assemble(pbfb_mesh* mesh, int scheme, const double* u_dev, double* N_out_dev);
+
+/* Resets the Jacobian block to J = 0 (the operator Acal of Eq. general_nonlinear). */
+int pbfb_clear_jacobian(pbfb_mesh* mesh);
+
+/* Steps a2-a4: y = Acal(J) x for the current J (device, n each). */
+int pbfb_apply(pbfb_mesh* mesh, const double* x_dev, double* y_dev);
+
+/* One boundary operator alone on surface `which`: op 0 = V (single layer),
+ * op 1 = K (double layer), Laplace on Gamma_m and Yukawa on Gamma_s, applied
+ * to the P1 coefficients x (device, n_m or n_s); y (device) same length. */
+int pbfb_bem_apply(pbfb_mesh* mesh, int which, int op, const double* x_dev, double* y_dev);
+
+/* FEM rows in CSR over the full unknown vector: rowptr (n_v + 1), col and val
+ * (nnz) copied to host buffers (val = A + J and the coupling masses). */
+int pbfb_fem_rows(const pbfb_mesh* mesh, int32_t* rowptr, int32_t* col, double* val);
+
+/* Step a5: GMRES (restarted, x0 = 0, right Jacobi preconditioner, CGS2) on
+ * Acal(J) x = b; stops when ||b - Acal x|| <= tol ||b||.  b, x: device (n).
+ * iters and relres: host outputs (may be NULL). */
+int pbfb_gmres(pbfb_mesh* mesh, const double* b_dev, double* x_dev, double tol, int restart,
+               int maxit, int* iters, double* relres);
+
+/* Step a7, batched over n_omega relaxation factors (host array omegas):
+ * with w = u + omega du (device, n_v each), c = b - Acal(0) Phi and
+ * p = -Acal(0) Delta (device, n each), writes for every omega 8 scalars to
+ * dots (host, n_omega x 8):
+ *   (p+r').r, (p+r').p, (p+r').r', r.r'', p.r'', r.r, p.r, p.p
+ * where r = c - [N(w);0;0], r' = -[J(w) du;0;0], r'' = -[N''(w)[du,du];0;0]
+ * (Eq. ab_pic and Appendix A).  These give f_d, f_d' and ||d(omega)||^2. */
+int pbfb_omega_eval(pbfb_mesh* mesh, int scheme, const double* u_dev, const double* du_dev,
+                    const double* c_dev, const double* p_dev, const double* omegas,
+                    int n_omega, double* dots);
+
+/* Step a9: energies (kcal/mol) of x_L and x_NL (device, n each) into
+ * out[0..3] = Total, LC, NC, dG_Omega_i (host) (Eq. Esolv). */
+int pbfb_energy(pbfb_mesh* mesh, const double* xL_dev, const double* xNL_dev, double* out);
+
+/* Per-kernel-class timing (CUDA events around each launch of the class) and
+ * launch counters.  enable != 0 turns event timing on (it adds a little host
+ * overhead per launch).  stats (host, 16 doubles):
+ *   [0] launches of all kernels since the last reset,
+ *   [1] BEM far-field (N-body) launches, [2] their total ms, [3] their pair
+ *       interactions, [4] FEM SpMV launches, [5] their ms,
+ *   [6] element (assembly + omega) launches, [7] their ms.
+ * reset != 0 zeroes the counters after reading. */
+int pbfb_profile(pbfb_mesh* mesh, int enable, int reset, double* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBFB_H */

@@ -1,0 +1,704 @@
+// Boundary-element kernels: Galerkin P1 single- and double-layer operators of the
+// Laplace kernel on Gamma_m (Eq. KV) and of the Yukawa kernel on Gamma_s (Sec. 2.2):
+//   V_ij = int int psi_i(x) g(x,y) psi_j(y),  K_ij = int int psi_i(x) dg/dn_y(x,y) psi_j(y)
+//   g = exp(-kappa r) / (4 pi r),  dg/dn_y = n_y.(x-y) (1 + kappa r) exp(-kappa r) / (4 pi r^3)
+// (Laplace is kappa = 0).
+//
+// Matrix-free far field: every matvec evaluates all pairs of 6-point quadrature
+// points of the surface (an N-body sum, coincident points excluded) and reduces the
+// target potentials against the test functions.  Touching and close triangle pairs
+// are corrected by a precomputed sparse matrix holding, per P1 pair (i, j), the
+// difference between the accurate rule of the pair's class and the 6 x 6 rule:
+//   identical / common edge / common vertex: Sauter-Schwab (Sauter & Schwab,
+//     Boundary Element Methods, 2011, Sec. 5.2), 5 Gauss-Legendre points per variable;
+//   near (no shared vertex, centroid distance < 2 max(h_tau, h_sigma)): 6 points on
+//     the test triangle x 6 points on each of the 16 sub-triangles of the trial one.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "pbfb_internal.cuh"
+#include "quad_tables.cuh"
+
+namespace pbfb {
+
+namespace {
+
+constexpr int NGL = 5;       // Gauss-Legendre points per Sauter-Schwab variable
+constexpr int NSUB = 96;     // 16 sub-triangles x 6 points
+constexpr double INV4PI = 0.079577471545947667884;
+
+__constant__ double c_gl_x[NGL];
+__constant__ double c_gl_w[NGL];
+__constant__ double c_sub_b[NSUB][3];
+__constant__ double c_sub_w[NSUB];
+
+// Gauss-Legendre nodes on [-1, 1] by Newton's method on the three-term recurrence of
+// P_n, mapped to [0, 1].
+void gauss_legendre01(int n, double* x01, double* w01) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double pp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      pp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / pp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      pp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    x01[i] = 0.5 * (1.0 - z);
+    w01[i] = 1.0 / ((1.0 - z * z) * pp * pp);  // (2 / ((1 - z^2) P'^2)) / 2
+  }
+}
+
+// ---------------------------------------------------------------- geometry
+
+__global__ void k_surface_geometry(const double* __restrict__ xyz, int nvtot, const int* __restrict__ tri,
+                                   const int* __restrict__ vmap, int nt, double cx, double cy, double cz,
+                                   double* __restrict__ qx, double* __restrict__ qw, double* __restrict__ nrm,
+                                   double* __restrict__ area, float4* __restrict__ qpf) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double P[3][3];
+  for (int a = 0; a < 3; ++a) {
+    int v = vmap[tri[3 * t + a]];
+    for (int d = 0; d < 3; ++d) P[a][d] = xyz[d * nvtot + v];
+  }
+  double e1[3], e2[3];
+  for (int d = 0; d < 3; ++d) {
+    e1[d] = P[1][d] - P[0][d];
+    e2[d] = P[2][d] - P[0][d];
+  }
+  double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  double nn = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+  double A = 0.5 * nn;
+  area[t] = A;
+  for (int d = 0; d < 3; ++d) nrm[d * nt + t] = c[d] / nn;
+  int nq = QS * nt;
+  for (int q = 0; q < QS; ++q) {
+    int j = QS * t + q;
+    double y[3];
+    for (int d = 0; d < 3; ++d) {
+      y[d] = c_tri_b[q][0] * P[0][d] + c_tri_b[q][1] * P[1][d] + c_tri_b[q][2] * P[2][d];
+      qx[d * nq + j] = y[d];
+    }
+    qw[j] = c_tri_w[q] * A;
+    qpf[j] = make_float4((float)(y[0] - cx), (float)(y[1] - cy), (float)(y[2] - cz), 0.f);
+  }
+}
+
+// ---------------------------------------------------------------- near-field corrections
+
+struct PairKer {
+  double kappa;
+  __device__ __forceinline__ void eval(const double* x, const double* y, const double* n, double& g,
+                                       double& dl) const {
+    double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+    double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    double r = sqrt(r2);
+    double e = exp(-kappa * r);
+    g = e * INV4PI / r;
+    dl = (n[0] * d0 + n[1] * d1 + n[2] * d2) * (1.0 + kappa * r) * e * INV4PI / (r2 * r);
+  }
+};
+
+// Sauter-Schwab reference points of region `reg` for class `cls` at (xi, e1, e2, e3):
+// returns the two points (s1, s2) in {0 <= s2 <= s1 <= 1} and the Jacobian of the map.
+__device__ __forceinline__ double ss_point(int cls, int reg, double xi, double e1, double e2, double e3,
+                                           double& x1, double& x2, double& y1, double& y2) {
+  if (cls == PAIR_IDENTICAL) {
+    double a1, a2, b1, b2;
+    int base = reg >> 1;
+    if (base == 0) {
+      a1 = xi; a2 = xi * (1.0 - e1 + e1 * e2);
+      b1 = xi * (1.0 - e1 * e2 * e3); b2 = xi * (1.0 - e1);
+    } else if (base == 1) {
+      a1 = xi; a2 = xi * e1 * (1.0 - e2 + e2 * e3);
+      b1 = xi * (1.0 - e1 * e2); b2 = xi * e1 * (1.0 - e2);
+    } else {
+      a1 = xi * (1.0 - e1 * e2 * e3); a2 = xi * e1 * (1.0 - e2 * e3);
+      b1 = xi; b2 = xi * e1 * (1.0 - e2);
+    }
+    if (reg & 1) { x1 = b1; x2 = b2; y1 = a1; y2 = a2; }
+    else { x1 = a1; x2 = a2; y1 = b1; y2 = b2; }
+    return xi * xi * xi * e1 * e1 * e2;
+  }
+  if (cls == PAIR_EDGE) {
+    double j = xi * xi * xi * e1 * e1;
+    switch (reg) {
+      case 0:
+        x1 = xi; x2 = xi * e1 * e3; y1 = xi * (1.0 - e1 * e2); y2 = xi * e1 * (1.0 - e2);
+        return j;
+      case 1:
+        x1 = xi; x2 = xi * e1; y1 = xi * (1.0 - e1 * e2 * e3); y2 = xi * e1 * e2 * (1.0 - e3);
+        return j * e2;
+      case 2:
+        x1 = xi * (1.0 - e1 * e2); x2 = xi * e1 * (1.0 - e2); y1 = xi; y2 = xi * e1 * e2 * e3;
+        return j * e2;
+      case 3:
+        x1 = xi * (1.0 - e1 * e2 * e3); x2 = xi * e1 * e2 * (1.0 - e3); y1 = xi; y2 = xi * e1;
+        return j * e2;
+      default:
+        x1 = xi * (1.0 - e1 * e2 * e3); x2 = xi * e1 * (1.0 - e2 * e3); y1 = xi; y2 = xi * e1 * e2;
+        return j * e2;
+    }
+  }
+  // common vertex
+  if (reg == 0) { x1 = xi; x2 = xi * e1; y1 = xi * e2; y2 = xi * e2 * e3; }
+  else { x1 = xi * e2; x2 = xi * e2 * e3; y1 = xi; y2 = xi * e1; }
+  return xi * xi * xi * e2;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One warp per special pair.  Outputs, per pair, 9 entries in stored local vertex
+// order (a of the test triangle, b of the trial one):
+//   corrV/corrK = accurate rule - 6x6 rule (coincident points excluded),
+//   fullV = accurate single-layer value (for the operator diagonal),
+//   mass = P1 mass entries (identical pairs only).
+__global__ void k_pair_corrections(int npair, const int* __restrict__ pt_, const int* __restrict__ ps_,
+                                   const int* __restrict__ cls_, const int* __restrict__ perm_,
+                                   const int* __restrict__ tri, const int* __restrict__ vmap,
+                                   const double* __restrict__ xyz, int nvtot, const double* __restrict__ nrm,
+                                   const double* __restrict__ area, const double* __restrict__ qx,
+                                   const double* __restrict__ qw, int nt, double kappa,
+                                   double* __restrict__ corrV, double* __restrict__ corrK,
+                                   double* __restrict__ fullV, double* __restrict__ mass) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= npair) return;
+  const int t = pt_[warp], s = ps_[warp], cls = cls_[warp];
+  int pt[3], ps[3];
+  for (int a = 0; a < 3; ++a) {
+    pt[a] = perm_[6 * warp + a];
+    ps[a] = perm_[6 * warp + 3 + a];
+  }
+  double Pt[3][3], Ps[3][3];  // corners in rule order
+  for (int a = 0; a < 3; ++a) {
+    int vt = vmap[tri[3 * t + pt[a]]], vs = vmap[tri[3 * s + ps[a]]];
+    for (int d = 0; d < 3; ++d) {
+      Pt[a][d] = xyz[d * nvtot + vt];
+      Ps[a][d] = xyz[d * nvtot + vs];
+    }
+  }
+  double ns[3] = {nrm[s], nrm[nt + s], nrm[2 * nt + s]};
+  double At = area[t], As = area[s];
+  PairKer K{kappa};
+  double SL[9], DL[9];
+  for (int k = 0; k < 9; ++k) SL[k] = DL[k] = 0.0;
+  if (cls != PAIR_NEAR) {
+    int nreg = cls == PAIR_IDENTICAL ? 6 : (cls == PAIR_EDGE ? 5 : 2);
+    int npts = nreg * NGL * NGL * NGL * NGL;
+    for (int k = lane; k < npts; k += 32) {
+      int reg = k / (NGL * NGL * NGL * NGL);
+      int i = k - reg * (NGL * NGL * NGL * NGL);
+      int i0 = i / (NGL * NGL * NGL), i1 = (i / (NGL * NGL)) % NGL, i2 = (i / NGL) % NGL, i3 = i % NGL;
+      double x1, x2, y1, y2;
+      double jac = ss_point(cls, reg, c_gl_x[i0], c_gl_x[i1], c_gl_x[i2], c_gl_x[i3], x1, x2, y1, y2);
+      double W = jac * c_gl_w[i0] * c_gl_w[i1] * c_gl_w[i2] * c_gl_w[i3];
+      double bx[3] = {1.0 - x1, x1 - x2, x2}, by[3] = {1.0 - y1, y1 - y2, y2};
+      double X[3], Y[3];
+      for (int d = 0; d < 3; ++d) {
+        X[d] = bx[0] * Pt[0][d] + bx[1] * Pt[1][d] + bx[2] * Pt[2][d];
+        Y[d] = by[0] * Ps[0][d] + by[1] * Ps[1][d] + by[2] * Ps[2][d];
+      }
+      double g, dl;
+      K.eval(X, Y, ns, g, dl);
+      g *= W;
+      dl *= W;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          SL[3 * a + b] += g * bx[a] * by[b];
+          DL[3 * a + b] += dl * bx[a] * by[b];
+        }
+    }
+    double jac = 4.0 * At * As;
+    for (int k = 0; k < 9; ++k) {
+      SL[k] *= jac;
+      DL[k] *= jac;
+    }
+  } else {
+    for (int k = lane; k < QS * NSUB; k += 32) {
+      int q = k / NSUB, p = k - q * NSUB;
+      double X[3], Y[3];
+      for (int d = 0; d < 3; ++d) {
+        X[d] = c_tri_b[q][0] * Pt[0][d] + c_tri_b[q][1] * Pt[1][d] + c_tri_b[q][2] * Pt[2][d];
+        Y[d] = c_sub_b[p][0] * Ps[0][d] + c_sub_b[p][1] * Ps[1][d] + c_sub_b[p][2] * Ps[2][d];
+      }
+      double g, dl;
+      K.eval(X, Y, ns, g, dl);
+      double W = c_tri_w[q] * c_sub_w[p] * At * As;
+      g *= W;
+      dl *= W;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          SL[3 * a + b] += g * c_tri_b[q][a] * c_sub_b[p][b];
+          DL[3 * a + b] += dl * c_tri_b[q][a] * c_sub_b[p][b];
+        }
+    }
+  }
+  // 6 x 6 rule in stored order (what the far-field sum adds), coincident points excluded
+  double RS[9], RD[9];
+  for (int k = 0; k < 9; ++k) RS[k] = RD[k] = 0.0;
+  int nqt = QS * nt;
+  for (int k = lane; k < QS * QS; k += 32) {
+    int q = k / QS, p = k - q * QS;
+    if (t == s && q == p) continue;
+    double X[3], Y[3];
+    for (int d = 0; d < 3; ++d) {
+      X[d] = qx[d * nqt + QS * t + q];
+      Y[d] = qx[d * nqt + QS * s + p];
+    }
+    double g, dl;
+    K.eval(X, Y, ns, g, dl);
+    double W = qw[QS * t + q] * qw[QS * s + p];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        RS[3 * a + b] += W * g * c_tri_b[q][a] * c_tri_b[p][b];
+        RD[3 * a + b] += W * dl * c_tri_b[q][a] * c_tri_b[p][b];
+      }
+  }
+  for (int k = 0; k < 9; ++k) {
+    SL[k] = warp_sum(SL[k]);
+    DL[k] = warp_sum(DL[k]);
+    RS[k] = warp_sum(RS[k]);
+    RD[k] = warp_sum(RD[k]);
+  }
+  if (lane == 0) {
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        int o = 9 * warp + 3 * pt[a] + ps[b];  // rule order -> stored order
+        int r = 3 * a + b;
+        fullV[o] = SL[r];
+        corrV[o] = SL[r] - RS[3 * pt[a] + ps[b]];
+        corrK[o] = DL[r] - RD[3 * pt[a] + ps[b]];
+      }
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        mass[9 * warp + 3 * a + b] = (cls == PAIR_IDENTICAL) ? At * (a == b ? 2.0 : 1.0) / 12.0 : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- far field
+
+// Source data at every quadrature point j = 6 tau + q:
+//   s_j = cs w_j lam_h(y_j)   (single layer),   m_j = cd w_j u_h(y_j) n_tau   (double layer)
+__global__ void k_sources(int nt, const int* __restrict__ tri, const int* __restrict__ vmap,
+                          const double* __restrict__ lam, const double* __restrict__ u, int u_local,
+                          const double* __restrict__ qw, const double* __restrict__ nrm,
+                          const float4* __restrict__ qpf, const double* __restrict__ qx, double cs, double cd,
+                          int want64, float4* __restrict__ spos, float4* __restrict__ sdl,
+                          double* __restrict__ s64) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int nq = QS * nt;
+  if (j >= nq) return;
+  int t = j / QS, q = j - t * QS;
+  double lh = 0.0, uh = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    int v = tri[3 * t + a];
+    double b = c_tri_b[q][a];
+    if (lam) lh += b * lam[v];
+    if (u) uh += b * u[u_local ? v : vmap[v]];
+  }
+  double w = qw[j];
+  double sv = cs * w * lh, mu = cd * w * uh;
+  double n0 = nrm[t], n1 = nrm[nt + t], n2 = nrm[2 * nt + t];
+  if (want64) {
+    s64[j] = qx[j];
+    s64[nq + j] = qx[nq + j];
+    s64[2 * nq + j] = qx[2 * nq + j];
+    s64[3 * nq + j] = sv;
+    s64[4 * nq + j] = mu * n0;
+    s64[5 * nq + j] = mu * n1;
+    s64[6 * nq + j] = mu * n2;
+  } else {
+    float4 p = qpf[j];
+    p.w = (float)sv;
+    spos[j] = p;
+    sdl[j] = make_float4((float)(mu * n0), (float)(mu * n1), (float)(mu * n2), 0.f);
+  }
+}
+
+// float32 N-body: targets = sources = the nq quadrature points.  Block = NT threads, each
+// owning TPT targets (interleaved by NT); sources streamed through shared memory in tiles
+// of NT; blockIdx.y selects a contiguous source range (split).  Each tile's float partial
+// sum is added to a double accumulator.  Coincident points (target index == source
+// index) are skipped; only tiles containing one of the thread's targets test for it.
+template <int NT, int TPT, bool YUK>
+__global__ void __launch_bounds__(NT) k_nbody_f32(int nq, const float4* __restrict__ tgt,
+                                                  const float4* __restrict__ spos,
+                                                  const float4* __restrict__ sdl, float kappa, int per_split,
+                                                  double* __restrict__ out) {
+  __shared__ float4 shp[NT];
+  __shared__ float4 shd[NT];
+  const int t0 = blockIdx.x * NT * TPT;
+  int ti[TPT];
+  float tx[TPT], ty[TPT], tz[TPT];
+  double acc64[TPT];
+#pragma unroll
+  for (int k = 0; k < TPT; ++k) {
+    ti[k] = t0 + k * NT + threadIdx.x;
+    float4 p = tgt[ti[k] < nq ? ti[k] : 0];
+    tx[k] = p.x;
+    ty[k] = p.y;
+    tz[k] = p.z;
+    acc64[k] = 0.0;
+  }
+  const int sb = blockIdx.y * per_split;
+  const int se = min(nq, sb + per_split);
+  const float nk = -kappa * 1.4426950408889634f;  // -kappa log2(e)
+  for (int s0 = sb; s0 < se; s0 += NT) {
+    int j = s0 + threadIdx.x;
+    if (j < se) {
+      shp[threadIdx.x] = spos[j];
+      shd[threadIdx.x] = sdl[j];
+    } else {
+      shp[threadIdx.x] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+      shd[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const bool diag = (s0 < t0 + NT * TPT) && (s0 + NT > t0);
+    float acc[TPT];
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) acc[k] = 0.f;
+    if (!diag) {
+#pragma unroll 4
+      for (int jj = 0; jj < NT; ++jj) {
+        const float4 p = shp[jj];
+        const float4 d = shd[jj];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+          float dx = tx[k] - p.x, dy = ty[k] - p.y, dz = tz[k] - p.z;
+          float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          float ri = rsqrtf(r2);
+          float nd = fmaf(d.x, dx, fmaf(d.y, dy, d.z * dz));
+          float ri2 = ri * ri;
+          if (YUK) {
+            float r = r2 * ri;
+            float e = exp2f(nk * r);
+            float kr1 = fmaf(kappa, r, 1.f);
+            float tt = fmaf(nd * kr1, ri2, p.w);
+            acc[k] = fmaf(tt, e * ri, acc[k]);
+          } else {
+            float tt = fmaf(nd, ri2, p.w);
+            acc[k] = fmaf(tt, ri, acc[k]);
+          }
+        }
+      }
+    } else {
+      for (int jj = 0; jj < NT; ++jj) {
+        const float4 p = shp[jj];
+        const float4 d = shd[jj];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+          if (s0 + jj == ti[k]) continue;
+          float dx = tx[k] - p.x, dy = ty[k] - p.y, dz = tz[k] - p.z;
+          float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          float ri = rsqrtf(r2);
+          float nd = fmaf(d.x, dx, fmaf(d.y, dy, d.z * dz));
+          float ri2 = ri * ri;
+          if (YUK) {
+            float r = r2 * ri;
+            float e = exp2f(nk * r);
+            float kr1 = fmaf(kappa, r, 1.f);
+            float tt = fmaf(nd * kr1, ri2, p.w);
+            acc[k] = fmaf(tt, e * ri, acc[k]);
+          } else {
+            float tt = fmaf(nd, ri2, p.w);
+            acc[k] = fmaf(tt, ri, acc[k]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) acc64[k] += (double)acc[k];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < TPT; ++k)
+    if (ti[k] < nq) out[(int64_t)blockIdx.y * nq + ti[k]] = acc64[k];
+}
+
+// float64 N-body, same organisation (one target per thread).
+template <int NT, bool YUK>
+__global__ void __launch_bounds__(NT) k_nbody_f64(int nq, const double* __restrict__ s64, double kappa,
+                                                  int per_split, double* __restrict__ out) {
+  __shared__ double sh[7][NT];
+  const int i = blockIdx.x * NT + threadIdx.x;
+  const int ii = i < nq ? i : 0;
+  const double x = s64[ii], y = s64[nq + ii], z = s64[2 * nq + ii];
+  const int sb = blockIdx.y * per_split;
+  const int se = min(nq, sb + per_split);
+  double acc = 0.0;
+  for (int s0 = sb; s0 < se; s0 += NT) {
+    int j = s0 + threadIdx.x;
+    if (j < se) {
+      for (int c = 0; c < 7; ++c) sh[c][threadIdx.x] = s64[c * nq + j];
+    } else {
+      sh[0][threadIdx.x] = sh[1][threadIdx.x] = sh[2][threadIdx.x] = 1e150;
+      for (int c = 3; c < 7; ++c) sh[c][threadIdx.x] = 0.0;
+    }
+    __syncthreads();
+    const int cnt = min(NT, se - s0);
+    for (int jj = 0; jj < cnt; ++jj) {
+      if (s0 + jj == i) continue;
+      double dx = x - sh[0][jj], dy = y - sh[1][jj], dz = z - sh[2][jj];
+      double r2 = dx * dx + dy * dy + dz * dz;
+      double ri = rsqrt(r2);
+      double nd = sh[4][jj] * dx + sh[5][jj] * dy + sh[6][jj] * dz;
+      double ri2 = ri * ri;
+      if (YUK) {
+        double r = r2 * ri;
+        double e = exp(-kappa * r);
+        acc += (sh[3][jj] + nd * (1.0 + kappa * r) * ri2) * e * ri;
+      } else {
+        acc += (sh[3][jj] + nd * ri2) * ri;
+      }
+    }
+    __syncthreads();
+  }
+  if (i < nq) out[(int64_t)blockIdx.y * nq + i] = acc;
+}
+
+// y[row0 + i] (+)= sum over incident (tau, a) of sum_q psi_a(x_q) w_q sum_split val[split][6 tau + q]
+__global__ void k_test_reduce(int nv, const int* __restrict__ ptr, const int* __restrict__ idx,
+                              const double* __restrict__ val, int nsplit, int nq, const double* __restrict__ qw,
+                              double scale, int accumulate, double* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv) return;
+  double acc = 0.0;
+  for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+    int e = idx[k];
+    int t = e / 3, a = e - 3 * t;
+    for (int q = 0; q < QS; ++q) {
+      int j = QS * t + q;
+      double v = 0.0;
+      for (int sp = 0; sp < nsplit; ++sp) v += val[(int64_t)sp * nq + j];
+      acc += c_tri_b[q][a] * qw[j] * v;
+    }
+  }
+  acc *= scale;
+  y[i] = accumulate ? y[i] + acc : acc;
+}
+
+// Coulomb sum at Gamma_m quadrature points: sum_k z_k / |x_j - x_k|.
+__global__ void k_coulomb_qp(int nq, const double* __restrict__ qx, int ncharge, const double* __restrict__ cxyz,
+                             const double* __restrict__ cz, double* __restrict__ out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nq) return;
+  double x = qx[j], y = qx[nq + j], z = qx[2 * nq + j];
+  double acc = 0.0;
+  for (int k = 0; k < ncharge; ++k) {
+    double dx = x - cxyz[k], dy = y - cxyz[ncharge + k], dz = z - cxyz[2 * ncharge + k];
+    acc += cz[k] / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  out[j] = acc;
+}
+
+// Reaction potential at the charges: (V_L lam)(x_k) - (K_L u)(x_k), 6-point rule (one block per charge).
+__global__ void k_reaction_potential(int nt, const int* __restrict__ tri, const int* __restrict__ vmap,
+                                     const double* __restrict__ qx, const double* __restrict__ qw,
+                                     const double* __restrict__ nrm, const double* __restrict__ lam,
+                                     const double* __restrict__ u, const double* __restrict__ cxyz, int ncharge,
+                                     double* __restrict__ out) {
+  int k = blockIdx.x;
+  int nq = QS * nt;
+  double px = cxyz[k], py = cxyz[ncharge + k], pz = cxyz[2 * ncharge + k];
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+    int t = j / QS, q = j - t * QS;
+    double lh = 0.0, uh = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      int v = tri[3 * t + a];
+      lh += c_tri_b[q][a] * lam[v];
+      uh += c_tri_b[q][a] * u[vmap[v]];
+    }
+    double dx = px - qx[j], dy = py - qx[nq + j], dz = pz - qx[2 * nq + j];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    double r = sqrt(r2);
+    double nd = nrm[t] * dx + nrm[nt + t] * dy + nrm[2 * nt + t] * dz;
+    acc += qw[j] * (lh / r - uh * nd / (r2 * r));
+  }
+  __shared__ double sh[32];
+  double v = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    out[k] = s * INV4PI;
+  }
+}
+
+inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+int init_quadrature() {
+  static bool done = false;
+  if (done) return PBFB_OK;
+  double x[NGL], w[NGL];
+  gauss_legendre01(NGL, x, w);
+  PB_CUDA(cudaMemcpyToSymbol(c_gl_x, x, sizeof(x)));
+  PB_CUDA(cudaMemcpyToSymbol(c_gl_w, w, sizeof(w)));
+  // 6-point rule on the 16 congruent sub-triangles of the 4-fold uniform refinement
+  double sb[NSUB][3], sw[NSUB];
+  int k = 0;
+  const int m = 4;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m - i; ++j) {
+      int cnt = (i + j < m - 1) ? 2 : 1;
+      for (int up = 0; up < cnt; ++up) {
+        int li[3][2];
+        if (up == 0) {
+          li[0][0] = i; li[0][1] = j; li[1][0] = i + 1; li[1][1] = j; li[2][0] = i; li[2][1] = j + 1;
+        } else {
+          li[0][0] = i + 1; li[0][1] = j; li[1][0] = i + 1; li[1][1] = j + 1; li[2][0] = i; li[2][1] = j + 1;
+        }
+        double cb[3][3];
+        for (int c = 0; c < 3; ++c) {
+          cb[c][0] = 1.0 - (li[c][0] + li[c][1]) / (double)m;
+          cb[c][1] = li[c][0] / (double)m;
+          cb[c][2] = li[c][1] / (double)m;
+        }
+        for (int q = 0; q < QS; ++q) {
+          for (int d = 0; d < 3; ++d)
+            sb[k][d] = h_tri_b[q][0] * cb[0][d] + h_tri_b[q][1] * cb[1][d] + h_tri_b[q][2] * cb[2][d];
+          sw[k] = h_tri_w[q] / (m * m);
+          ++k;
+        }
+      }
+    }
+  PB_CUDA(cudaMemcpyToSymbol(c_sub_b, sb, sizeof(sb)));
+  PB_CUDA(cudaMemcpyToSymbol(c_sub_w, sw, sizeof(sw)));
+  done = true;
+  return PBFB_OK;
+}
+
+int launch_surface_geometry(Mesh* m, Surface* s) {
+  k_surface_geometry<<<blocks_for(s->nt, 128), 128, 0, m->stream>>>(
+      m->xyz.p, m->nv, s->tri.p, s->vmap.p, s->nt, s->ctr[0], s->ctr[1], s->ctr[2], s->qx.p, s->qw.p, s->nrm.p,
+      s->area.p, s->qpf.p);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+int launch_pair_corrections(Mesh* m, Surface* s, double kappa) {
+  if (s->npair == 0) return PBFB_OK;
+  int threads = 128;
+  int blocks = blocks_for((int64_t)s->npair * 32, threads);
+  k_pair_corrections<<<blocks, threads, 0, m->stream>>>(
+      s->npair, s->pair_t.p, s->pair_s.p, s->pair_cls.p, s->pair_perm.p, s->tri.p, s->vmap.p, m->xyz.p, m->nv,
+      s->nrm.p, s->area.p, s->qx.p, s->qw.p, s->nt, kappa, s->pairV.p, s->pairK.p, s->pairVfull.p,
+      m->red2.p);
+  PB_LAUNCHED(m);
+  // per-slot sums (fixed order): corrections, mass, V diagonal
+  PB_TRY(launch_gather(m, s->cnnz, s->cg_ptr.p, s->cg_idx.p, s->pairV.p, nullptr, 1.0, s->corrV.p));
+  PB_TRY(launch_gather(m, s->cnnz, s->cg_ptr.p, s->cg_idx.p, s->pairK.p, nullptr, 1.0, s->corrK.p));
+  PB_TRY(launch_gather(m, s->cnnz, s->cg_ptr.p, s->cg_idx.p, m->red2.p, nullptr, 1.0, s->mass.p));
+  PB_TRY(launch_gather(m, s->nv, s->dg_ptr.p, s->dg_idx.p, s->pairVfull.p, nullptr, 1.0, s->diagV.p));
+  return PBFB_OK;
+}
+
+// y (+)= far-field part of the surface rows: for every test function psi_i,
+//   sum_{x_q, y_p, q != p} psi_i(x_q) w_q [ g(x_q,y_p) s_p + dg/dn_y(x_q,y_p) m_p ]
+// with s_p = cs w_p lam_h(y_p), m_p = cd w_p u_h(y_p) (kernel factors 1/(4 pi) included).
+// lam indexed by local surface vertex; x (the shell part of the full vector, or a local
+// surface vector when lam == x is a surface vector) indexed through vmap.
+int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, double cs, double cd, double kappa,
+                   int precision, double* y, bool accumulate) {
+  const int nq = s->nq;
+  const bool yuk = kappa != 0.0;
+  const int u_local = (x != nullptr && x == lam) ? 1 : 0;
+  const double* uvec = (cd != 0.0) ? x : nullptr;
+  const double* lvec = (cs != 0.0) ? lam : nullptr;
+  const bool f64 = precision == PBFB_FP64;
+  k_sources<<<blocks_for(nq, 256), 256, 0, m->stream>>>(s->nt, s->tri.p, s->vmap.p, lvec, uvec, u_local, s->qw.p,
+                                                        s->nrm.p, s->qpf.p, s->qx.p, cs * INV4PI, cd * INV4PI,
+                                                        f64 ? 1 : 0, s->spos.p, s->sdl.p, s->s64.p);
+  PB_LAUNCHED(m);
+  cudaEvent_t ev;
+  timer_begin(m, m->t_nbody, &ev);
+  int nsplit;
+  if (f64) {
+    constexpr int NT = 128;
+    int ntb = blocks_for(nq, NT);
+    nsplit = std::max(1, std::min(blocks_for(4 * 152, ntb), blocks_for(nq, 4 * NT)));
+    int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
+    nsplit = blocks_for(nq, per);
+    dim3 grid(ntb, nsplit);
+    if ((size_t)nsplit * nq > s->val.n) {
+      set_error("far-field split buffer too small");
+      return PBFB_ERR_STATE;
+    }
+    if (yuk)
+      k_nbody_f64<NT, true><<<grid, NT, 0, m->stream>>>(nq, s->s64.p, kappa, per, s->val.p);
+    else
+      k_nbody_f64<NT, false><<<grid, NT, 0, m->stream>>>(nq, s->s64.p, kappa, per, s->val.p);
+  } else {
+    constexpr int NT = 128;
+    const bool big = nq >= 16384;
+    const int tpt = big ? 4 : 1;
+    int ntb = blocks_for(nq, NT * tpt);
+    nsplit = std::max(1, std::min(blocks_for(4 * 152, ntb), blocks_for(nq, 4 * NT)));
+    int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
+    nsplit = blocks_for(nq, per);
+    dim3 grid(ntb, nsplit);
+    if ((size_t)nsplit * nq > s->val.n) {
+      set_error("far-field split buffer too small");
+      return PBFB_ERR_STATE;
+    }
+    float kf = (float)kappa;
+    if (big) {
+      if (yuk) k_nbody_f32<NT, 4, true><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, s->spos.p, s->sdl.p, kf, per, s->val.p);
+      else k_nbody_f32<NT, 4, false><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, s->spos.p, s->sdl.p, kf, per, s->val.p);
+    } else {
+      if (yuk) k_nbody_f32<NT, 1, true><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, s->spos.p, s->sdl.p, kf, per, s->val.p);
+      else k_nbody_f32<NT, 1, false><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, s->spos.p, s->sdl.p, kf, per, s->val.p);
+    }
+  }
+  PB_LAUNCHED(m);
+  timer_end(m, m->t_nbody, ev, (double)nq * (double)nq);
+  k_test_reduce<<<blocks_for(s->nv, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, s->val.p, nsplit,
+                                                               nq, s->qw.p, 1.0, accumulate ? 1 : 0, y);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+int launch_coulomb(Mesh* m) {
+  Surface* s = &m->sm;
+  k_coulomb_qp<<<blocks_for(s->nq, 128), 128, 0, m->stream>>>(s->nq, s->qx.p, m->nq, m->qxyz.p, m->qz.p, s->val.p);
+  PB_LAUNCHED(m);
+  k_test_reduce<<<blocks_for(s->nv, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, s->val.p, 1,
+                                                               s->nq, s->qw.p, 1.0, 0, m->coul.p);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev) {
+  Surface* s = &m->sm;
+  k_reaction_potential<<<m->nq, 256, 0, m->stream>>>(s->nt, s->tri.p, s->vmap.p, s->qx.p, s->qw.p, s->nrm.p,
+                                                     x + s->col0, x, m->qxyz.p, m->nq, ur_dev);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+}  // namespace pbfb

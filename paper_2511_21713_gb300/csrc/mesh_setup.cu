@@ -1,0 +1,571 @@
+// Mesh creation: validation, topology (host) and device data.
+//
+// The host builds integer structure only (CSR pattern of the coupled operator's sparse
+// part, element-to-slot gather lists, triangle-pair classes); every floating-point
+// quantity of the discretisation is computed on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <unordered_map>
+#include <vector>
+
+#include "pbfb_internal.cuh"
+#include "quad_tables.cuh"
+
+namespace pbfb {
+
+namespace {
+
+thread_local std::string g_err;
+
+// counting sort of (key, value) pairs by key in [0, nkeys): returns ptr (nkeys+1) and values
+void bucket(const std::vector<int>& keys, const std::vector<int>& vals, int nkeys, std::vector<int>& ptr,
+            std::vector<int>& out) {
+  ptr.assign(nkeys + 1, 0);
+  for (int k : keys) ptr[k + 1]++;
+  for (int i = 0; i < nkeys; ++i) ptr[i + 1] += ptr[i];
+  out.resize(keys.size());
+  std::vector<int> pos(ptr.begin(), ptr.end() - 1);
+  for (size_t e = 0; e < keys.size(); ++e) out[pos[keys[e]]++] = vals[e];
+}
+
+struct HostSurface {
+  std::vector<int> tri;    // local ids
+  std::vector<int> verts;  // shell ids
+  std::vector<double> P;   // nt*9 corner coordinates
+};
+
+// Triangle-pair classification (ordered pairs: test t, trial s).
+void classify_pairs(const HostSurface& hs, std::vector<int>& pt, std::vector<int>& ps, std::vector<int>& cls,
+                    std::vector<int>& perm) {
+  const int nt = (int)hs.tri.size() / 3;
+  const int nv = (int)hs.verts.size();
+  std::vector<std::vector<int>> inc(nv);
+  for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < 3; ++a) inc[hs.tri[3 * t + a]].push_back(t);
+  std::vector<double> cen(3 * nt), h(nt);
+  double hmax = 0.0;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int t = 0; t < nt; ++t) {
+    const double* P = &hs.P[9 * t];
+    double hh = 0.0;
+    for (int d = 0; d < 3; ++d) cen[3 * t + d] = (P[d] + P[3 + d] + P[6 + d]) / 3.0;
+    for (int k = 0; k < 3; ++k) {
+      const double* A = P + 3 * k;
+      const double* B = P + 3 * ((k + 1) % 3);
+      double dx = B[0] - A[0], dy = B[1] - A[1], dz = B[2] - A[2];
+      hh = std::max(hh, std::sqrt(dx * dx + dy * dy + dz * dz));
+    }
+    h[t] = hh;
+    hmax = std::max(hmax, hh);
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], cen[3 * t + d]);
+      hi[d] = std::max(hi[d], cen[3 * t + d]);
+    }
+  }
+  // uniform grid of cell 2 hmax over the centroids
+  const double cell = 2.0 * hmax;
+  int dims[3];
+  for (int d = 0; d < 3; ++d) dims[d] = std::max(1, (int)std::floor((hi[d] - lo[d]) / cell) + 1);
+  auto cid = [&](const double* c, int* ijk) {
+    for (int d = 0; d < 3; ++d) ijk[d] = std::min(dims[d] - 1, (int)std::floor((c[d] - lo[d]) / cell));
+  };
+  std::unordered_map<int64_t, std::vector<int>> grid;
+  for (int t = 0; t < nt; ++t) {
+    int ijk[3];
+    cid(&cen[3 * t], ijk);
+    grid[((int64_t)ijk[0] * dims[1] + ijk[1]) * dims[2] + ijk[2]].push_back(t);
+  }
+  std::vector<int> cnt(nt, 0), touched;
+  for (int t = 0; t < nt; ++t) {
+    touched.clear();
+    for (int a = 0; a < 3; ++a)
+      for (int u : inc[hs.tri[3 * t + a]]) {
+        if (cnt[u] == 0) touched.push_back(u);
+        cnt[u]++;
+      }
+    std::vector<std::array<int, 2>> row;  // (s, class)
+    for (int u : touched) {
+      int c = cnt[u];
+      row.push_back({u, c == 3 ? PAIR_IDENTICAL : (c == 2 ? PAIR_EDGE : PAIR_VERTEX)});
+    }
+    int ijk[3];
+    cid(&cen[3 * t], ijk);
+    for (int di = -1; di <= 1; ++di)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int dk = -1; dk <= 1; ++dk) {
+          int a = ijk[0] + di, b = ijk[1] + dj, c = ijk[2] + dk;
+          if (a < 0 || b < 0 || c < 0 || a >= dims[0] || b >= dims[1] || c >= dims[2]) continue;
+          auto it = grid.find(((int64_t)a * dims[1] + b) * dims[2] + c);
+          if (it == grid.end()) continue;
+          for (int u : it->second) {
+            if (cnt[u] > 0) continue;  // touching pairs are handled above
+            double dx = cen[3 * t] - cen[3 * u], dy = cen[3 * t + 1] - cen[3 * u + 1],
+                   dz = cen[3 * t + 2] - cen[3 * u + 2];
+            double lim = 2.0 * std::max(h[t], h[u]);
+            if (dx * dx + dy * dy + dz * dz < lim * lim) row.push_back({u, PAIR_NEAR});
+          }
+        }
+    std::sort(row.begin(), row.end());
+    for (auto& e : row) {
+      int u = e[0], c = e[1];
+      int p[6] = {0, 1, 2, 0, 1, 2};
+      const int* T = &hs.tri[3 * t];
+      const int* S = &hs.tri[3 * u];
+      if (c == PAIR_EDGE) {
+        // shared vertices in the test triangle's order go to reference vertices 0 and 1
+        int sh[2], ns = 0;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            if (T[a] == S[b]) sh[ns++] = a;
+        int sb[2];
+        for (int k = 0; k < 2; ++k)
+          for (int b = 0; b < 3; ++b)
+            if (S[b] == T[sh[k]]) sb[k] = b;
+        p[0] = sh[0]; p[1] = sh[1]; p[2] = 3 - sh[0] - sh[1];
+        p[3] = sb[0]; p[4] = sb[1]; p[5] = 3 - sb[0] - sb[1];
+      } else if (c == PAIR_VERTEX) {
+        int ia = 0, ib = 0;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            if (T[a] == S[b]) { ia = a; ib = b; }
+        for (int k = 0; k < 3; ++k) {
+          p[k] = (ia + k) % 3;
+          p[3 + k] = (ib + k) % 3;
+        }
+      }
+      pt.push_back(t);
+      ps.push_back(u);
+      cls.push_back(c);
+      for (int k = 0; k < 6; ++k) perm.push_back(p[k]);
+    }
+    for (int u : touched) cnt[u] = 0;
+  }
+}
+
+int build_surface(Mesh* m, Surface* s, const std::vector<int>& gtri, const std::vector<double>& xyz_h) {
+  const int nt = (int)gtri.size() / 3;
+  std::vector<int> verts(gtri.begin(), gtri.end());
+  std::sort(verts.begin(), verts.end());
+  verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
+  std::unordered_map<int, int> loc;
+  for (int i = 0; i < (int)verts.size(); ++i) loc[verts[i]] = i;
+  HostSurface hs;
+  hs.verts = verts;
+  hs.tri.resize(gtri.size());
+  hs.P.resize(9 * (size_t)nt);
+  double c[3] = {0, 0, 0};
+  for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < 3; ++a) {
+      int g = gtri[3 * t + a];
+      hs.tri[3 * t + a] = loc[g];
+      for (int d = 0; d < 3; ++d) hs.P[9 * t + 3 * a + d] = xyz_h[3 * (size_t)g + d];
+    }
+  for (int v : verts)
+    for (int d = 0; d < 3; ++d) c[d] += xyz_h[3 * (size_t)v + d];
+  for (int d = 0; d < 3; ++d) s->ctr[d] = c[d] / verts.size();
+  s->nt = nt;
+  s->nv = (int)verts.size();
+  s->nq = QS * nt;
+  s->tri_h = hs.tri;
+  s->vmap_h = verts;
+  PB_TRY(s->tri.upload(hs.tri.data(), hs.tri.size(), m->stream));
+  PB_TRY(s->vmap.upload(verts.data(), verts.size(), m->stream));
+  // test-reduction incidence: per vertex (t*3 + a)
+  {
+    std::vector<int> keys, vals;
+    for (int t = 0; t < nt; ++t)
+      for (int a = 0; a < 3; ++a) {
+        keys.push_back(hs.tri[3 * t + a]);
+        vals.push_back(3 * t + a);
+      }
+    std::vector<int> ptr, out;
+    bucket(keys, vals, s->nv, ptr, out);
+    PB_TRY(s->inc_ptr.upload(ptr.data(), ptr.size(), m->stream));
+    PB_TRY(s->inc_idx.upload(out.data(), out.size(), m->stream));
+  }
+  // special pairs and the correction pattern
+  std::vector<int> pt, ps, cls, perm;
+  classify_pairs(hs, pt, ps, cls, perm);
+  s->npair = (int)pt.size();
+  PB_TRY(s->pair_t.upload(pt.data(), pt.size(), m->stream));
+  PB_TRY(s->pair_s.upload(ps.data(), ps.size(), m->stream));
+  PB_TRY(s->pair_cls.upload(cls.data(), cls.size(), m->stream));
+  PB_TRY(s->pair_perm.upload(perm.data(), perm.size(), m->stream));
+  {
+    std::vector<int64_t> keys;
+    keys.reserve(9 * (size_t)s->npair);
+    for (int p = 0; p < s->npair; ++p)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+          keys.push_back((int64_t)hs.tri[3 * pt[p] + a] * s->nv + hs.tri[3 * ps[p] + b]);
+    std::vector<int64_t> uk(keys);
+    std::sort(uk.begin(), uk.end());
+    uk.erase(std::unique(uk.begin(), uk.end()), uk.end());
+    s->cnnz = (int)uk.size();
+    s->c_ptr_h.assign(s->nv + 1, 0);
+    s->c_col_h.resize(uk.size());
+    for (size_t k = 0; k < uk.size(); ++k) {
+      int i = (int)(uk[k] / s->nv);
+      s->c_col_h[k] = (int)(uk[k] % s->nv);
+      s->c_ptr_h[i + 1]++;
+    }
+    for (int i = 0; i < s->nv; ++i) s->c_ptr_h[i + 1] += s->c_ptr_h[i];
+    std::vector<int> slot_of(keys.size()), vals(keys.size()), dk, dv;
+    for (size_t e = 0; e < keys.size(); ++e) {
+      slot_of[e] = (int)(std::lower_bound(uk.begin(), uk.end(), keys[e]) - uk.begin());
+      vals[e] = (int)e;
+      int p = (int)(e / 9), a = (int)(e / 3) % 3, b = (int)e % 3;
+      int vi = hs.tri[3 * pt[p] + a], vj = hs.tri[3 * ps[p] + b];
+      if (vi == vj) {
+        dk.push_back(vi);
+        dv.push_back((int)e);
+      }
+    }
+    std::vector<int> ptr, out;
+    bucket(slot_of, vals, s->cnnz, ptr, out);
+    PB_TRY(s->cg_ptr.upload(ptr.data(), ptr.size(), m->stream));
+    PB_TRY(s->cg_idx.upload(out.data(), out.size(), m->stream));
+    bucket(dk, dv, s->nv, ptr, out);
+    PB_TRY(s->dg_ptr.upload(ptr.data(), ptr.size(), m->stream));
+    PB_TRY(s->dg_idx.upload(out.data(), out.size(), m->stream));
+    PB_TRY(s->c_ptr.upload(s->c_ptr_h.data(), s->c_ptr_h.size(), m->stream));
+    PB_TRY(s->c_col.upload(s->c_col_h.data(), s->c_col_h.size(), m->stream));
+  }
+  PB_TRY(s->qx.alloc(3 * (size_t)s->nq));
+  PB_TRY(s->qw.alloc(s->nq));
+  PB_TRY(s->nrm.alloc(3 * (size_t)nt));
+  PB_TRY(s->area.alloc(nt));
+  PB_TRY(s->qpf.alloc(s->nq));
+  PB_TRY(s->pairV.alloc(9 * (size_t)s->npair));
+  PB_TRY(s->pairK.alloc(9 * (size_t)s->npair));
+  PB_TRY(s->pairVfull.alloc(9 * (size_t)s->npair));
+  PB_TRY(s->corrV.alloc(s->cnnz));
+  PB_TRY(s->corrK.alloc(s->cnnz));
+  PB_TRY(s->mass.alloc(s->cnnz));
+  PB_TRY(s->diagV.alloc(s->nv));
+  PB_TRY(s->spos.alloc(s->nq));
+  PB_TRY(s->sdl.alloc(s->nq));
+  PB_TRY(s->s64.alloc(7 * (size_t)s->nq));
+  // far-field partial-sum buffer: enough splits for either precision's launch shape
+  // (at most ceil(nq / 512) source splits; see launch_bem_far)
+  size_t maxsplit = (size_t)(s->nq / 512 + 2);
+  PB_TRY(s->val.alloc(maxsplit * s->nq));
+  return PBFB_OK;
+}
+
+int64_t key2(int r, int c) { return ((int64_t)r << 32) | (uint32_t)c; }
+
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+const char* last_error() { return g_err.c_str(); }
+
+// Validation of the shell mesh and its two boundary surfaces (host).
+static int validate(const double* xyz, int nv, const int* tets, int64_t nt, const int* gm, int ngm, const int* gs,
+                    int ngs) {
+  if (!xyz || !tets || !gm || !gs || nv < 4 || nt < 1 || ngm < 4 || ngs < 4) {
+    set_error("mesh_create: empty or missing arrays");
+    return PBFB_ERR_INVALID;
+  }
+  for (int64_t i = 0; i < 3 * (int64_t)nv; ++i)
+    if (!std::isfinite(xyz[i])) {
+      set_error("mesh_create: non-finite coordinate");
+      return PBFB_ERR_INVALID;
+    }
+  for (int64_t i = 0; i < 4 * nt; ++i)
+    if (tets[i] < 0 || tets[i] >= nv) {
+      set_error("mesh_create: tet vertex id out of range");
+      return PBFB_ERR_INVALID;
+    }
+  for (int i = 0; i < 3 * ngm; ++i)
+    if (gm[i] < 0 || gm[i] >= nv) {
+      set_error("mesh_create: Gamma_m vertex id out of range");
+      return PBFB_ERR_INVALID;
+    }
+  for (int i = 0; i < 3 * ngs; ++i)
+    if (gs[i] < 0 || gs[i] >= nv) {
+      set_error("mesh_create: Gamma_s vertex id out of range");
+      return PBFB_ERR_INVALID;
+    }
+  // boundary faces of the tets: faces used once; with the opposite vertex for orientation
+  std::map<std::array<int, 3>, std::array<int, 2>> faces;  // sorted face -> (count, opposite vertex)
+  for (int64_t t = 0; t < nt; ++t) {
+    const int* T = tets + 4 * t;
+    double e[3][3];
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) e[k][d] = xyz[3 * T[k + 1] + d] - xyz[3 * T[0] + d];
+    double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                 e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+    double L2 = 0.0;
+    for (int k = 0; k < 3; ++k) L2 = std::max(L2, e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2]);
+    if (!(std::fabs(det) > 1e-12 * L2 * std::sqrt(L2))) {
+      set_error("mesh_create: degenerate tetrahedron %lld", (long long)t);
+      return PBFB_ERR_INVALID;
+    }
+    for (int k = 0; k < 4; ++k) {
+      std::array<int, 3> f;
+      int q = 0;
+      for (int a = 0; a < 4; ++a)
+        if (a != k) f[q++] = T[a];
+      std::sort(f.begin(), f.end());
+      auto& slot = faces[f];
+      slot[0]++;
+      slot[1] = T[k];
+    }
+  }
+  size_t nb = 0;
+  for (auto& kv : faces) {
+    if (kv.second[0] > 2) {
+      set_error("mesh_create: a face is shared by more than two tets");
+      return PBFB_ERR_INVALID;
+    }
+    if (kv.second[0] == 1) nb++;
+  }
+  if (nb != (size_t)ngm + (size_t)ngs) {
+    set_error("mesh_create: %zu boundary faces but %d + %d surface triangles", nb, ngm, ngs);
+    return PBFB_ERR_INVALID;
+  }
+  std::vector<char> onm(nv, 0), ons(nv, 0);
+  for (int surf = 0; surf < 2; ++surf) {
+    const int* tri = surf == 0 ? gm : gs;
+    int ntri = surf == 0 ? ngm : ngs;
+    std::map<std::pair<int, int>, int> dedges;
+    for (int t = 0; t < ntri; ++t) {
+      const int* F = tri + 3 * t;
+      if (F[0] == F[1] || F[1] == F[2] || F[0] == F[2]) {
+        set_error("mesh_create: repeated vertex in a surface triangle");
+        return PBFB_ERR_INVALID;
+      }
+      std::array<int, 3> f = {F[0], F[1], F[2]};
+      std::sort(f.begin(), f.end());
+      auto it = faces.find(f);
+      if (it == faces.end() || it->second[0] != 1) {
+        set_error("mesh_create: surface triangle %d of %s is not a boundary face of the tets", t,
+                  surf == 0 ? "Gamma_m" : "Gamma_s");
+        return PBFB_ERR_INVALID;
+      }
+      it->second[0] = 3;  // claimed
+      // orientation: the opposite tet vertex lies on the positive side for Gamma_m
+      int o = it->second[1];
+      double a[3], b[3], c[3];
+      for (int d = 0; d < 3; ++d) {
+        a[d] = xyz[3 * F[1] + d] - xyz[3 * F[0] + d];
+        b[d] = xyz[3 * F[2] + d] - xyz[3 * F[0] + d];
+        c[d] = xyz[3 * o + d] - xyz[3 * F[0] + d];
+      }
+      double n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+      double side = n[0] * c[0] + n[1] * c[1] + n[2] * c[2];
+      if ((surf == 0 && !(side > 0)) || (surf == 1 && !(side < 0))) {
+        set_error("mesh_create: %s triangle %d has the wrong orientation", surf == 0 ? "Gamma_m" : "Gamma_s", t);
+        return PBFB_ERR_INVALID;
+      }
+      for (int k = 0; k < 3; ++k) {
+        auto key = std::make_pair(F[k], F[(k + 1) % 3]);
+        if (++dedges[key] > 1) {
+          set_error("mesh_create: surface is not consistently oriented / manifold");
+          return PBFB_ERR_INVALID;
+        }
+        (surf == 0 ? onm : ons)[F[k]] = 1;
+      }
+    }
+    for (auto& kv : dedges)
+      if (!dedges.count(std::make_pair(kv.first.second, kv.first.first))) {
+        set_error("mesh_create: %s is not closed", surf == 0 ? "Gamma_m" : "Gamma_s");
+        return PBFB_ERR_INVALID;
+      }
+  }
+  for (int v = 0; v < nv; ++v)
+    if (onm[v] && ons[v]) {
+      set_error("mesh_create: Gamma_m and Gamma_s share vertex %d", v);
+      return PBFB_ERR_INVALID;
+    }
+  return PBFB_OK;
+}
+
+int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const int* gm, int ngm, const int* gs,
+                int ngs, cudaStream_t stream, Mesh** out) {
+  PB_TRY(validate(xyz, nv, tets, nt, gm, ngm, gs, ngs));
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    set_error("no CUDA device");
+    return PBFB_ERR_CUDA;
+  }
+  PB_TRY(init_quadrature());
+  Mesh* m = new Mesh();
+  int st = PBFB_OK;
+  auto fail = [&](int s) {
+    delete m;
+    return s;
+  };
+  cudaGetDevice(&m->dev);
+  m->stream = stream;
+  m->nv = nv;
+  m->nt = nt;
+  std::vector<double> xyz_h(xyz, xyz + 3 * (size_t)nv);
+  {
+    std::vector<double> soa(3 * (size_t)nv);
+    for (int v = 0; v < nv; ++v)
+      for (int d = 0; d < 3; ++d) soa[(size_t)d * nv + v] = xyz[3 * (size_t)v + d];
+    if ((st = m->xyz.upload(soa.data(), soa.size(), stream))) return fail(st);
+    std::vector<int> tsoa(4 * (size_t)nt);
+    for (int64_t t = 0; t < nt; ++t)
+      for (int a = 0; a < 4; ++a) tsoa[(size_t)a * nt + t] = tets[4 * t + a];
+    if ((st = m->tets.upload(tsoa.data(), tsoa.size(), stream))) return fail(st);
+  }
+  std::vector<int> gmv(gm, gm + 3 * (size_t)ngm), gsv(gs, gs + 3 * (size_t)ngs);
+  if ((st = build_surface(m, &m->sm, gmv, xyz_h))) return fail(st);
+  if ((st = build_surface(m, &m->ss, gsv, xyz_h))) return fail(st);
+  Surface& sm = m->sm;
+  Surface& ss = m->ss;
+  sm.col0 = nv;
+  ss.col0 = nv + sm.nv;
+  m->n = nv + sm.nv + ss.nv;
+  // ---- sparse-part pattern of the coupled operator
+  std::vector<int64_t> keys;
+  keys.reserve(16 * (size_t)nt + 4 * (size_t)(sm.cnnz + ss.cnnz));
+  for (int64_t t = 0; t < nt; ++t)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) keys.push_back(key2(tets[4 * t + a], tets[4 * t + b]));
+  // mass pattern (vertices sharing a triangle) for the FEM coupling entries
+  auto mass_pairs = [](const Surface& s, std::vector<std::pair<int, int>>& mp) {
+    for (int t = 0; t < s.nt; ++t)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) mp.push_back({s.tri_h[3 * t + a], s.tri_h[3 * t + b]});
+    std::sort(mp.begin(), mp.end());
+    mp.erase(std::unique(mp.begin(), mp.end()), mp.end());
+  };
+  std::vector<std::pair<int, int>> mpm, mps;
+  mass_pairs(sm, mpm);
+  mass_pairs(ss, mps);
+  for (auto& e : mpm) keys.push_back(key2(sm.vmap_h[e.first], sm.col0 + e.second));
+  for (auto& e : mps) keys.push_back(key2(ss.vmap_h[e.first], ss.col0 + e.second));
+  for (const Surface* s : {&sm, &ss})
+    for (int i = 0; i < s->nv; ++i)
+      for (int k = s->c_ptr_h[i]; k < s->c_ptr_h[i + 1]; ++k) {
+        int j = s->c_col_h[k];
+        keys.push_back(key2(s->col0 + i, s->vmap_h[j]));
+        keys.push_back(key2(s->col0 + i, s->col0 + j));
+      }
+  std::vector<int64_t> uk(keys.begin(), keys.end());
+  std::sort(uk.begin(), uk.end());
+  uk.erase(std::unique(uk.begin(), uk.end()), uk.end());
+  m->snnz = (int)uk.size();
+  m->s_ptr_h.assign(m->n + 1, 0);
+  m->s_col_h.resize(uk.size());
+  for (size_t k = 0; k < uk.size(); ++k) {
+    m->s_col_h[k] = (int)(uk[k] & 0xffffffff);
+    m->s_ptr_h[(uk[k] >> 32) + 1]++;
+  }
+  for (int r = 0; r < m->n; ++r) m->s_ptr_h[r + 1] += m->s_ptr_h[r];
+  m->fem_nnz = m->s_ptr_h[nv];
+  auto slot = [&](int r, int c) -> int {
+    auto b = m->s_col_h.begin() + m->s_ptr_h[r], e = m->s_col_h.begin() + m->s_ptr_h[r + 1];
+    return (int)(std::lower_bound(b, e, c) - m->s_col_h.begin());
+  };
+  std::vector<int> kind(m->snnz, -1), ref(m->snnz, 0);
+  {
+    std::vector<int> jk, jv;
+    jk.reserve(16 * (size_t)nt);
+    jv.reserve(16 * (size_t)nt);
+    for (int64_t t = 0; t < nt; ++t)
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          int sl = slot(tets[4 * t + a], tets[4 * t + b]);
+          kind[sl] = 0;
+          jk.push_back(sl);
+          jv.push_back((int)(sym10(a, b) * nt + t));
+        }
+    std::vector<int> ptr, outv;
+    bucket(jk, jv, m->snnz, ptr, outv);
+    if ((st = m->jg_ptr.upload(ptr.data(), ptr.size(), stream))) return fail(st);
+    if ((st = m->jg_idx.upload(outv.data(), outv.size(), stream))) return fail(st);
+    std::vector<int> nk, nvv;
+    for (int64_t t = 0; t < nt; ++t)
+      for (int a = 0; a < 4; ++a) {
+        nk.push_back(tets[4 * t + a]);
+        nvv.push_back((int)(a * nt + t));
+      }
+    bucket(nk, nvv, nv, ptr, outv);
+    if ((st = m->ng_ptr.upload(ptr.data(), ptr.size(), stream))) return fail(st);
+    if ((st = m->ng_idx.upload(outv.data(), outv.size(), stream))) return fail(st);
+  }
+  auto cslot = [](const Surface& s, int i, int j) -> int {
+    auto b = s.c_col_h.begin() + s.c_ptr_h[i], e = s.c_col_h.begin() + s.c_ptr_h[i + 1];
+    return (int)(std::lower_bound(b, e, j) - s.c_col_h.begin());
+  };
+  for (auto& e : mpm) {
+    int sl = slot(sm.vmap_h[e.first], sm.col0 + e.second);
+    kind[sl] = 1;
+    ref[sl] = cslot(sm, e.first, e.second);
+  }
+  for (auto& e : mps) {
+    int sl = slot(ss.vmap_h[e.first], ss.col0 + e.second);
+    kind[sl] = 2;
+    ref[sl] = cslot(ss, e.first, e.second);
+  }
+  for (int si = 0; si < 2; ++si) {
+    const Surface& s = si == 0 ? sm : ss;
+    for (int i = 0; i < s.nv; ++i)
+      for (int k = s.c_ptr_h[i]; k < s.c_ptr_h[i + 1]; ++k) {
+        int j = s.c_col_h[k];
+        int a = slot(s.col0 + i, s.vmap_h[j]);
+        int b = slot(s.col0 + i, s.col0 + j);
+        kind[a] = si == 0 ? 3 : 5;
+        ref[a] = k;
+        kind[b] = si == 0 ? 4 : 6;
+        ref[b] = k;
+      }
+  }
+  for (int k = 0; k < m->snnz; ++k)
+    if (kind[k] < 0) {
+      set_error("internal: unassigned operator slot");
+      return fail(PBFB_ERR_STATE);
+    }
+  if ((st = m->s_ptr.upload(m->s_ptr_h.data(), m->s_ptr_h.size(), stream))) return fail(st);
+  if ((st = m->s_col.upload(m->s_col_h.data(), m->s_col_h.size(), stream))) return fail(st);
+  if ((st = m->s_kind.upload(kind.data(), kind.size(), stream))) return fail(st);
+  if ((st = m->s_ref.upload(ref.data(), ref.size(), stream))) return fail(st);
+  if ((st = m->s_val.alloc(m->snnz))) return fail(st);
+  if ((st = m->s_base.alloc(m->snnz))) return fail(st);
+  if ((st = m->a1.alloc(m->snnz))) return fail(st);
+  if ((st = m->vol.alloc(nt))) return fail(st);
+  if ((st = m->tloc.alloc(14 * (size_t)nt))) return fail(st);
+  if ((st = m->red.alloc((size_t)152 * 7 * 64 + 1024))) return fail(st);
+  if ((st = m->scal.alloc(8192))) return fail(st);
+  if ((st = m->red2.alloc(9 * (size_t)std::max(sm.npair, ss.npair)))) return fail(st);
+  if (cudaMallocHost((void**)&m->pinned, 4096 * sizeof(double)) != cudaSuccess) {
+    set_error("cudaMallocHost failed");
+    return fail(PBFB_ERR_OOM);
+  }
+  // ---- device geometry and constant operator parts
+  if ((st = launch_tet_volumes(m))) return fail(st);
+  if ((st = launch_stiffness_local(m, m->tloc.p))) return fail(st);
+  if ((st = launch_gather(m, m->snnz, m->jg_ptr.p, m->jg_idx.p, m->tloc.p, nullptr, 1.0, m->a1.p))) return fail(st);
+  if ((st = launch_surface_geometry(m, &sm))) return fail(st);
+  if ((st = launch_surface_geometry(m, &ss))) return fail(st);
+  if ((st = launch_pair_corrections(m, &sm, 0.0))) return fail(st);
+  sm.kappa = 0.0;
+  sm.built = true;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) {
+    set_error("mesh_create: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(PBFB_ERR_CUDA);
+  }
+  *out = m;
+  return PBFB_OK;
+}
+
+}  // namespace pbfb

@@ -1,0 +1,210 @@
+// Internal declarations of libpbfb: device data of a mesh and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pbfb.h"
+
+namespace pbfb {
+
+void set_error(const char* fmt, ...);
+
+#define PB_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      pbfb::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? PBFB_ERR_OOM : PBFB_ERR_CUDA;            \
+    }                                                                                    \
+  } while (0)
+
+#define PB_TRY(call)                 \
+  do {                               \
+    int s_ = (call);                 \
+    if (s_ != PBFB_OK) return s_;    \
+  } while (0)
+
+#define PB_LAUNCHED(mesh)                                                                  \
+  do {                                                                                     \
+    (mesh)->launches++;                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                                   \
+    if (e_ != cudaSuccess) {                                                               \
+      pbfb::set_error("%s:%d kernel launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+      return PBFB_ERR_CUDA;                                                                \
+    }                                                                                      \
+  } while (0)
+
+// Quadrature points per surface triangle and per tetrahedron.
+constexpr int QS = 6;
+constexpr int QT = 14;
+
+// Owned device allocation.
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  int alloc(size_t count) {
+    release();
+    if (count == 0) return PBFB_OK;
+    PB_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+    n = count;
+    return PBFB_OK;
+  }
+  int upload(const T* h, size_t count, cudaStream_t s) {
+    PB_TRY(alloc(count));
+    if (count) PB_CUDA(cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    return PBFB_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DBuf() { release(); }
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+};
+
+// Special (near-field) triangle pair classes.
+enum PairClass { PAIR_IDENTICAL = 0, PAIR_EDGE = 1, PAIR_VERTEX = 2, PAIR_NEAR = 3 };
+
+// A closed surface (Gamma_m or Gamma_s) over shell vertices.
+struct Surface {
+  int nt = 0;   // triangles
+  int nv = 0;   // vertices (unknowns lam)
+  int nq = 0;   // quadrature points = QS * nt
+  int col0 = 0; // offset of this surface's lam unknowns in the full vector
+  std::vector<int> tri_h;   // nt*3 local vertex ids
+  std::vector<int> vmap_h;  // nv shell ids (ascending)
+  DBuf<int> tri;            // nt*3 local ids
+  DBuf<int> vmap;           // nv shell ids
+  DBuf<double> qx;          // 3*nq SoA quadrature points (x block, y block, z block)
+  DBuf<double> qw;          // nq: w_q |tau|
+  DBuf<double> nrm;         // 3*nt SoA unit normals (stored orientation)
+  DBuf<double> area;        // nt
+  DBuf<float4> qpf;         // nq float (x, y, z, 0) relative to ctr
+  double ctr[3] = {0, 0, 0};
+  // test reduction: per vertex list of (tri*3 + a)
+  DBuf<int> inc_ptr, inc_idx;
+  // special pairs
+  int npair = 0;
+  DBuf<int> pair_t, pair_s, pair_cls, pair_perm;  // perm: 6 ints per pair (pt[3], ps[3])
+  // correction CSR over surface vertices (pattern of all special pairs)
+  int cnnz = 0;
+  std::vector<int> c_ptr_h, c_col_h;
+  DBuf<int> c_ptr, c_col;
+  DBuf<int> cg_ptr, cg_idx;     // per slot: pair-local entries p*9 + a*3 + b
+  DBuf<int> dg_ptr, dg_idx;     // per vertex: pair-local entries feeding the V diagonal
+  DBuf<double> pairV, pairK, pairVfull;  // 9 per pair
+  DBuf<double> corrV, corrK;    // per slot: exact-minus-regular corrections
+  DBuf<double> mass;            // per slot: P1 mass matrix entries (0 off the mass pattern)
+  DBuf<double> diagV;           // per vertex: full single-layer diagonal
+  double kappa = -1.0;          // kernel inverse length the corrections were built for
+  bool built = false;
+  // far-field work buffers
+  DBuf<float4> spos, sdl;       // float32 sources
+  DBuf<double> s64;             // float64 sources: 7 * nq (x, y, z, s, mx, my, mz)
+  DBuf<double> val;             // nsplit * nq target potentials
+  int nsplit = 1;
+};
+
+struct KernelClassTimer {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  double ms = 0.0;
+  double count = 0.0;
+  double work = 0.0;
+};
+
+struct Mesh {
+  int dev = 0;
+  cudaStream_t stream = 0;
+  int nv = 0;
+  int64_t nt = 0;
+  int n = 0;              // nv + nm + ns
+  // geometry
+  DBuf<double> xyz;       // 3*nv SoA
+  DBuf<int> tets;         // 4*nt SoA (vertex a of tet t at a*nt + t)
+  DBuf<double> vol;       // nt
+  // sparse part of the coupled operator, CSR over all n rows and n columns
+  int snnz = 0;
+  std::vector<int> s_ptr_h, s_col_h;
+  DBuf<int> s_ptr, s_col;
+  DBuf<double> s_val;     // current values (A + J, couplings, BEM near parts)
+  DBuf<double> s_base;    // values with J = 0
+  DBuf<double> a1;        // per slot: int grad v_i . grad v_j (0 off the stiffness pattern)
+  DBuf<int> s_kind, s_ref;  // per slot fill descriptor (see fill kernel)
+  DBuf<int> jg_ptr, jg_idx; // per slot: tet-local Jacobian entries (k * nt + t, k in 0..9)
+  DBuf<int> ng_ptr, ng_idx; // per vertex: tet-local load entries (a * nt + t)
+  int fem_nnz = 0;          // slots in the first nv rows
+  // surfaces
+  Surface sm, ss;
+  // charges
+  int nq = 0;
+  DBuf<double> qxyz, qz;    // 3*nq SoA, nq
+  DBuf<double> coul;        // nm: <sum z/|x-x_k|, psi_i> (no l_B/eps_m)
+  bool charges = false;
+  // parameters
+  double eps_m = 0, eps_s = 0, kappa = 0, T = 0, lB = 0, kT = 0, coef = 0;
+  int precision = PBFB_FP64;
+  bool params = false;
+  // element work buffers
+  DBuf<double> tloc;        // 10 * nt Jacobian + 4 * nt load, tet-local
+  DBuf<double> wloc;        // omega batch: nomega * 12 * nt
+  DBuf<double> red;         // block partial sums
+  DBuf<double> scal;        // device scalars: [0,64) omegas, [64, 64+7*64+3) omega dots,
+                            // [1000] ion integral, [4000] dot result
+  DBuf<double> red2;        // pair-local mass entries during correction builds
+  double* pinned = nullptr; // host pinned scratch (4096 doubles)
+  // GMRES workspace
+  int gm_restart = 0;
+  DBuf<double> gV, gw, gz, gr, gdiag, gh, gpart, gtmp;
+  // Newton workspace
+  DBuf<double> xL, xNL, phi, cvec, dvec, du, pvec, tmp, Nvec, bvec, xout, urb;
+  std::vector<double> qz_h;  // charges (host copy)
+  // statistics
+  double launches = 0;
+  bool timing = false;
+  KernelClassTimer t_nbody, t_spmv, t_elem;
+};
+
+// ---- quadrature constants (device) and their host initialisation
+int init_quadrature();
+
+// ---- fem_kernels.cu
+int launch_tet_volumes(Mesh* m);
+int launch_stiffness_local(Mesh* m, double* loc10);
+int launch_gather(Mesh* m, int nslots, const int* ptr, const int* idx, const double* local,
+                  const double* base, double scale, double* out);
+int launch_element_nl(Mesh* m, int scheme, const double* u, double coef, double* loc);
+int launch_spmv(Mesh* m, const double* x, double* y);
+int launch_omega_elements(Mesh* m, int scheme, const double* u, const double* du,
+                          const double* omegas_dev, int nomega, double coef, double* loc);
+int launch_omega_dots(Mesh* m, int nomega, const double* loc, const double* c, const double* p,
+                      double* dots_dev);
+int launch_ion_energy(Mesh* m, const double* u, double* out_dev);
+int launch_fill_operator(Mesh* m);
+int launch_csr_spmv(Mesh* m, int nrows, const int* ptr, const int* col, const double* val, const double* x,
+                    double* y, bool accumulate);
+
+// ---- bem_kernels.cu
+int launch_surface_geometry(Mesh* m, Surface* s);
+int launch_pair_corrections(Mesh* m, Surface* s, double kappa);
+int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, double cs, double cd,
+                   double kappa, int precision, double* y, bool accumulate);
+int launch_coulomb(Mesh* m);
+int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev);
+
+// ---- blas (solver.cu)
+int dot(Mesh* m, const double* a, const double* b, int n, double* out_host);
+int launch_axpby(Mesh* m, int n, double a, const double* x, double b, const double* y, double* z);
+int ensure(DBuf<double>& b, size_t n);
+
+// timing helpers
+void timer_begin(Mesh* m, KernelClassTimer& t, cudaEvent_t* ev);
+void timer_end(Mesh* m, KernelClassTimer& t, cudaEvent_t ev0, double work);
+
+}  // namespace pbfb

@@ -1,0 +1,1035 @@
+// Coupled operator, GMRES, Newton-Raphson with the optimal relaxation factor, energy,
+// and the C ABI (include/pbfb.h).
+//
+// Newton (Sec. 2.4.2, Eqs. NR_main, Ec_NL_NR, Norma_Newton-Raphson): with Phi = x_L + x_NL,
+//   d = b - Acal(0) Phi - [N(u);0;0],  Acal(J(u)) Delta = d,  x_NL += omega Delta,
+//   e = omega ||Delta||_2, stop when e < Tol_NL; T3 nonlinearity in the first iteration.
+// Relaxation factor (Sec. 2.5, Eq. fd=0, Appendix A): Newton's method on
+//   f_d(omega) = -((p + r').r) / ((p + r').p) - omega, p = -Acal(0) Delta,
+// accepted when 0 < omega <= omega_max and ||d(omega)|| < ||d(0)|| (the global convergence
+// condition of Sec. 2.5.2); otherwise a batched scan of g_d = d . d' over omega_max j / 16
+// followed by bisection of its first sign change.  L_e skip rule and the adjustable GMRES
+// tolerance follow Appendix B.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pbfb_internal.cuh"
+
+namespace pbfb {
+
+int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const int* gm, int ngm, const int* gs,
+                int ngs, cudaStream_t stream, Mesh** out);
+const char* last_error();
+
+namespace {
+
+// e^2/(4 pi eps0) in kcal mol^-1 Angstrom and the Boltzmann constant in kcal mol^-1 K^-1.
+constexpr double kCoulomb = 332.0637;
+constexpr double kBoltzmann = 0.0019872043;
+constexpr int DOT_B = 152;
+constexpr int DOT_T = 256;
+
+inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+__global__ void k_dot_partial(int n, const double* __restrict__ a, const double* __restrict__ b,
+                              double* __restrict__ part) {
+  double acc = 0.0;
+  for (int i = blockIdx.x * DOT_T + threadIdx.x; i < n; i += gridDim.x * DOT_T) acc += a[i] * b[i];
+  __shared__ double sh[DOT_T / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < DOT_T / 32; ++w) s += sh[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sum_to(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    *out = s;
+  }
+}
+
+__global__ void k_axpby(int n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* __restrict__ z) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+
+__global__ void k_mul(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ z) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = a[i] * b[i];
+}
+
+__global__ void k_scale_by(int n, const double* __restrict__ x, const double* __restrict__ s, double* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x[i] / sqrt(*s);
+}
+
+// h[j] partials: for basis vectors j0..j0+7 (< k), sum over a row range of V[j] . w
+constexpr int MD_T = 256;
+__global__ void __launch_bounds__(MD_T) k_multidot(int n, int k, const double* __restrict__ V,
+                                                   const double* __restrict__ w, double* __restrict__ part) {
+  int j0 = blockIdx.y * 8;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = blockIdx.x * MD_T + threadIdx.x; i < n; i += gridDim.x * MD_T) {
+    double wi = w[i];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj)
+      if (j0 + jj < k) acc[jj] += V[(int64_t)(j0 + jj) * n + i] * wi;
+  }
+  __shared__ double sh[MD_T / 32][8];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    double x = acc[jj];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[wid][jj] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8 && j0 + (int)threadIdx.x < k) {
+    double x = 0.0;
+    for (int q = 0; q < MD_T / 32; ++q) x += sh[q][threadIdx.x];
+    part[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = x;
+  }
+}
+
+__global__ void k_multidot_sum(const double* __restrict__ part, int nb, int k, double* __restrict__ h) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(int64_t)j * nb + b];
+  h[j] = s;
+}
+
+// w -= sum_j V[j] h[j]; optional partial sums of ||w||^2 after the update
+__global__ void __launch_bounds__(MD_T) k_multiaxpy(int n, int k, const double* __restrict__ V,
+                                                    const double* __restrict__ h, double* __restrict__ w,
+                                                    double* __restrict__ npart) {
+  double nrm = 0.0;
+  for (int i = blockIdx.x * MD_T + threadIdx.x; i < n; i += gridDim.x * MD_T) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += V[(int64_t)j * n + i] * h[j];
+    double v = w[i] - s;
+    w[i] = v;
+    nrm += v * v;
+  }
+  if (!npart) return;
+  __shared__ double sh[MD_T / 32];
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < MD_T / 32; ++q) s += sh[q];
+    npart[blockIdx.x] = s;
+  }
+}
+
+// x += dinv .* (sum_j V[j] y[j])
+__global__ void k_update_solution(int n, int k, const double* __restrict__ V, const double* __restrict__ y,
+                                  const double* __restrict__ dinv, double* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int j = 0; j < k; ++j) s += V[(int64_t)j * n + i] * y[j];
+  x[i] += dinv[i] * s;
+}
+
+// Jacobi preconditioner: 1 / diag(Acal(J)).  FEM rows from the sparse part; surface rows
+// from the full single-layer diagonals (-V_L on Gamma_m, +V_Y on Gamma_s).
+__global__ void k_jacobi(int nv, int nm, int ns, const int* __restrict__ ptr, const int* __restrict__ col,
+                         const double* __restrict__ val, const double* __restrict__ dVm,
+                         const double* __restrict__ dVs, double* __restrict__ dinv) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nv + nm + ns) return;
+  double d;
+  if (r < nv) {
+    d = 0.0;
+    for (int k = ptr[r]; k < ptr[r + 1]; ++k)
+      if (col[k] == r) d = val[k];
+  } else if (r < nv + nm) {
+    d = -dVm[r - nv];
+  } else {
+    d = dVs[r - nv - nm];
+  }
+  dinv[r] = 1.0 / d;
+}
+
+__global__ void k_set_rhs(int nm, int col0, double scale, const double* __restrict__ coul, double* __restrict__ b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nm) b[col0 + i] = scale * coul[i];
+}
+
+__global__ void k_sub_load(int nv, const double* __restrict__ N, double* __restrict__ d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nv) d[i] -= N[i];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ small BLAS
+
+void timer_begin(Mesh* m, KernelClassTimer& t, cudaEvent_t* ev) {
+  *ev = nullptr;
+  if (!m->timing) return;
+  cudaEventCreate(ev);
+  cudaEventRecord(*ev, m->stream);
+}
+
+void timer_end(Mesh* m, KernelClassTimer& t, cudaEvent_t ev0, double work) {
+  t.count += 1;
+  t.work += work;
+  if (!m->timing || !ev0) return;
+  cudaEvent_t ev1;
+  cudaEventCreate(&ev1);
+  cudaEventRecord(ev1, m->stream);
+  t.pending.push_back({ev0, ev1});
+}
+
+static void timer_flush(KernelClassTimer& t) {
+  for (auto& p : t.pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(p.second);
+    cudaEventElapsedTime(&ms, p.first, p.second);
+    t.ms += ms;
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  t.pending.clear();
+}
+
+int launch_axpby(Mesh* m, int n, double a, const double* x, double b, const double* y, double* z) {
+  k_axpby<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, a, x, b, y, z);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+// device dot product into device scalar out_dev
+static int dot_dev(Mesh* m, const double* a, const double* b, int n, double* out_dev) {
+  int nb = std::min(DOT_B, std::max(1, blocks_for(n, DOT_T)));
+  k_dot_partial<<<nb, DOT_T, 0, m->stream>>>(n, a, b, m->red.p);
+  PB_LAUNCHED(m);
+  k_sum_to<<<1, 32, 0, m->stream>>>(m->red.p, nb, out_dev);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+int dot(Mesh* m, const double* a, const double* b, int n, double* out_host) {
+  PB_TRY(dot_dev(m, a, b, n, m->scal.p + 4000));
+  PB_CUDA(cudaMemcpyAsync(m->pinned, m->scal.p + 4000, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  PB_CUDA(cudaStreamSynchronize(m->stream));
+  *out_host = m->pinned[0];
+  return PBFB_OK;
+}
+
+// ------------------------------------------------------------------ parameters and operator
+
+static int set_params(Mesh* m, double eps_in, double eps_out, double kappa, double T, int precision) {
+  if (!(eps_in > 0) || !(eps_out > 0) || !(kappa >= 0) || !(T > 0) || !std::isfinite(kappa) ||
+      !std::isfinite(eps_in) || !std::isfinite(eps_out) || !std::isfinite(T)) {
+    set_error("invalid parameters: eps_in %g eps_out %g kappa %g T %g", eps_in, eps_out, kappa, T);
+    return PBFB_ERR_INVALID;
+  }
+  if (precision != PBFB_FP64 && precision != PBFB_MIXED) {
+    set_error("invalid precision %d", precision);
+    return PBFB_ERR_INVALID;
+  }
+  PB_CUDA(cudaSetDevice(m->dev));
+  m->eps_m = eps_in;
+  m->eps_s = eps_out;
+  m->kappa = kappa;
+  m->T = T;
+  m->kT = kBoltzmann * T;
+  m->lB = kCoulomb / m->kT;
+  m->coef = eps_out * kappa * kappa;
+  m->precision = precision;
+  if (!m->ss.built || m->ss.kappa != kappa) {
+    PB_TRY(launch_pair_corrections(m, &m->ss, kappa));
+    m->ss.kappa = kappa;
+    m->ss.built = true;
+  }
+  PB_TRY(launch_fill_operator(m));
+  PB_CUDA(cudaMemcpyAsync(m->s_val.p, m->s_base.p, m->snnz * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  m->params = true;
+  return PBFB_OK;
+}
+
+// J(u) into the operator values; N(u) into N_out (may be null)
+static int assemble(Mesh* m, int scheme, const double* u, double* N_out) {
+  PB_TRY(launch_element_nl(m, scheme, u, m->coef, m->tloc.p));
+  PB_TRY(launch_gather(m, m->snnz, m->jg_ptr.p, m->jg_idx.p, m->tloc.p, m->s_base.p, 1.0, m->s_val.p));
+  if (N_out)
+    PB_TRY(launch_gather(m, m->nv, m->ng_ptr.p, m->ng_idx.p, m->tloc.p + 10 * m->nt, nullptr, 1.0, N_out));
+  return PBFB_OK;
+}
+
+static int clear_jacobian(Mesh* m) {
+  PB_CUDA(cudaMemcpyAsync(m->s_val.p, m->s_base.p, m->snnz * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  return PBFB_OK;
+}
+
+// y = Acal(J) x: sparse part, then the far field of both surfaces into their rows
+static int apply(Mesh* m, const double* x, double* y) {
+  PB_TRY(launch_spmv(m, x, y));
+  Surface* sm = &m->sm;
+  Surface* ss = &m->ss;
+  // Gamma_m rows: (M/2 + K_L) u - V_L lam_m; Gamma_s rows: (M/2 - K_Y) u + V_Y lam_s
+  PB_TRY(launch_bem_far(m, sm, x, x + sm->col0, -1.0, 1.0, 0.0, m->precision, y + sm->col0, true));
+  PB_TRY(launch_bem_far(m, ss, x, x + ss->col0, 1.0, -1.0, m->kappa, m->precision, y + ss->col0, true));
+  return PBFB_OK;
+}
+
+int ensure(DBuf<double>& b, size_t n) {
+  if (b.n >= n) return PBFB_OK;
+  return b.alloc(n);
+}
+
+static int jacobi(Mesh* m, double* dinv) {
+  k_jacobi<<<blocks_for(m->n, 256), 256, 0, m->stream>>>(m->nv, m->sm.nv, m->ss.nv, m->s_ptr.p, m->s_col.p,
+                                                          m->s_val.p, m->sm.diagV.p, m->ss.diagV.p, dinv);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+// ------------------------------------------------------------------ GMRES
+
+static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, int maxit, int* iters_out,
+                 double* rel_out) {
+  const int n = m->n;
+  if (restart < 1 || restart > 400) {
+    set_error("restart must be in [1, 400]");
+    return PBFB_ERR_INVALID;
+  }
+  PB_TRY(ensure(m->gV, (size_t)(restart + 1) * n));
+  PB_TRY(ensure(m->gw, n));
+  PB_TRY(ensure(m->gz, n));
+  PB_TRY(ensure(m->gr, n));
+  PB_TRY(ensure(m->gdiag, n));
+  PB_TRY(ensure(m->gh, 4 * (size_t)(restart + 2)));
+  const int nbr = std::min(152, std::max(1, blocks_for(n, MD_T)));
+  PB_TRY(ensure(m->gpart, (size_t)(restart + 2) * nbr + 8));
+  PB_TRY(jacobi(m, m->gdiag.p));
+  double* V = m->gV.p;
+  double* w = m->gw.p;
+  double* z = m->gz.p;
+  double* r = m->gr.p;
+  double* h1 = m->gh.p;                 // restart + 1
+  double* h2 = m->gh.p + (restart + 2);  // restart + 1
+  double* nrm = m->gh.p + 2 * (restart + 2);
+  double* ydev = m->gh.p + 3 * (restart + 2);
+  double bn2;
+  PB_TRY(dot(m, b, b, n, &bn2));
+  double bn = std::sqrt(bn2);
+  PB_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), m->stream));
+  if (iters_out) *iters_out = 0;
+  if (rel_out) *rel_out = 0.0;
+  if (!(bn > 0)) {
+    if (!std::isfinite(bn)) {
+      set_error("GMRES: non-finite right-hand side");
+      return PBFB_ERR_NONFINITE;
+    }
+    return PBFB_OK;
+  }
+  PB_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), y(restart);
+  int its = 0;
+  double rel = 1.0;
+  double beta = bn;
+  while (true) {
+    // V[0] = r / ||r||
+    PB_TRY(dot_dev(m, r, r, n, nrm));
+    k_scale_by<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, r, nrm, V);
+    PB_LAUNCHED(m);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (k = 0; k < restart; ++k) {
+      double* vk = V + (size_t)k * n;
+      k_mul<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, vk, m->gdiag.p, z);
+      PB_LAUNCHED(m);
+      PB_TRY(apply(m, z, w));
+      // classical Gram-Schmidt, twice
+      int kk = k + 1;
+      dim3 gd(nbr, (kk + 7) / 8);
+      for (int pass = 0; pass < 2; ++pass) {
+        double* hh = pass == 0 ? h1 : h2;
+        k_multidot<<<gd, MD_T, 0, m->stream>>>(n, kk, V, w, m->gpart.p);
+        PB_LAUNCHED(m);
+        k_multidot_sum<<<blocks_for(kk, 64), 64, 0, m->stream>>>(m->gpart.p, nbr, kk, hh);
+        PB_LAUNCHED(m);
+        k_multiaxpy<<<nbr, MD_T, 0, m->stream>>>(n, kk, V, hh, w, pass == 1 ? m->gpart.p : nullptr);
+        PB_LAUNCHED(m);
+      }
+      k_sum_to<<<1, 32, 0, m->stream>>>(m->gpart.p, nbr, nrm);
+      PB_LAUNCHED(m);
+      k_scale_by<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, w, nrm, V + (size_t)(k + 1) * n);
+      PB_LAUNCHED(m);
+      // h1 | h2 | nrm are contiguous chunks of gh: one copy
+      PB_CUDA(cudaMemcpyAsync(m->pinned, m->gh.p, (2 * (restart + 2) + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                              m->stream));
+      PB_CUDA(cudaStreamSynchronize(m->stream));
+      const double* H1 = m->pinned;
+      const double* H2 = m->pinned + (restart + 2);
+      double hn = std::sqrt(m->pinned[2 * (restart + 2)]);
+      double* col = &H[(size_t)k * (restart + 1)];
+      for (int i = 0; i <= k; ++i) col[i] = H1[i] + H2[i];
+      col[k + 1] = hn;
+      for (int i = 0; i < k; ++i) {
+        double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      double den = std::hypot(col[k], col[k + 1]);
+      if (!std::isfinite(den)) {
+        set_error("GMRES: non-finite Arnoldi coefficient");
+        return PBFB_ERR_NONFINITE;
+      }
+      cs[k] = col[k] / den;
+      sn[k] = col[k + 1] / den;
+      col[k] = den;
+      col[k + 1] = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      ++its;
+      rel = std::fabs(g[k + 1]) / bn;
+      if (rel <= tol || its >= maxit || hn == 0.0) {
+        break;
+      }
+    }
+    int mk = std::min(k + 1, restart);
+    for (int i = mk - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int j = i + 1; j < mk; ++j) s -= H[(size_t)j * (restart + 1) + i] * y[j];
+      y[i] = s / H[(size_t)i * (restart + 1) + i];
+    }
+    std::memcpy(m->pinned, y.data(), mk * sizeof(double));
+    PB_CUDA(cudaMemcpyAsync(ydev, m->pinned, mk * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    k_update_solution<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, mk, V, ydev, m->gdiag.p, x);
+    PB_LAUNCHED(m);
+    // true residual
+    PB_TRY(apply(m, x, w));
+    PB_TRY(launch_axpby(m, n, 1.0, b, -1.0, w, r));
+    double rn2;
+    PB_TRY(dot(m, r, r, n, &rn2));
+    beta = std::sqrt(rn2);
+    rel = beta / bn;
+    if (!std::isfinite(rel)) {
+      set_error("GMRES: non-finite residual");
+      return PBFB_ERR_NONFINITE;
+    }
+    if (rel <= tol || its >= maxit) break;
+  }
+  if (iters_out) *iters_out = its;
+  if (rel_out) *rel_out = rel;
+  if (rel > tol) {
+    set_error("GMRES did not converge: relative residual %.3e > %.1e after %d iterations", rel, tol, its);
+    return PBFB_ERR_GMRES_NOCONV;
+  }
+  return PBFB_OK;
+}
+
+// ------------------------------------------------------------------ omega evaluation
+
+// Batched a7: dots (host, nomega x 8) = (p+r').r, (p+r').p, (p+r').r', r.r'', p.r'', r.r, p.r, p.p
+static int omega_eval(Mesh* m, int scheme, const double* u, const double* du, const double* c, const double* p,
+                      const double* omegas, int nomega, double* dots) {
+  if (nomega < 1 || nomega > 64) {
+    set_error("n_omega must be in [1, 64]");
+    return PBFB_ERR_INVALID;
+  }
+  PB_TRY(ensure(m->wloc, (size_t)nomega * 12 * m->nt));
+  // constant (omega-independent) parts over the surface rows, and p.p
+  const int nv = m->nv, n = m->n, nb = n - nv;
+  double* dv = m->scal.p;  // [0, 64) omegas, [64, ...) results
+  std::memcpy(m->pinned, omegas, nomega * sizeof(double));
+  PB_CUDA(cudaMemcpyAsync(dv, m->pinned, nomega * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+  PB_TRY(launch_omega_elements(m, scheme, u, du, dv, nomega, m->coef, m->wloc.p));
+  PB_TRY(launch_omega_dots(m, nomega, m->wloc.p, c, p, dv + 64));
+  PB_TRY(dot_dev(m, p + nv, c + nv, nb, dv + 64 + 7 * 64));
+  PB_TRY(dot_dev(m, c + nv, c + nv, nb, dv + 64 + 7 * 64 + 1));
+  PB_TRY(dot_dev(m, p, p, n, dv + 64 + 7 * 64 + 2));
+  PB_CUDA(cudaMemcpyAsync(m->pinned, dv + 64, (7 * 64 + 3) * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  PB_CUDA(cudaStreamSynchronize(m->stream));
+  const double pcb = m->pinned[7 * 64], ccb = m->pinned[7 * 64 + 1], pp = m->pinned[7 * 64 + 2];
+  for (int o = 0; o < nomega; ++o) {
+    const double* f = m->pinned + 7 * o;  // p.r, r'.r, r'.p, r'.r', r.r'', p.r'', r.r (FEM rows)
+    double pr = f[0] + pcb;
+    dots[8 * o + 0] = pr + f[1];          // (p+r').r
+    dots[8 * o + 1] = pp + f[2];          // (p+r').p
+    dots[8 * o + 2] = f[2] + f[3];        // (p+r').r'
+    dots[8 * o + 3] = f[4];               // r.r''
+    dots[8 * o + 4] = f[5];               // p.r''
+    dots[8 * o + 5] = f[6] + ccb;         // r.r
+    dots[8 * o + 6] = pr;                 // p.r
+    dots[8 * o + 7] = pp;                 // p.p
+  }
+  return PBFB_OK;
+}
+
+static inline double dnorm2(const double* D, double om) { return om * om * D[7] + 2.0 * om * D[6] + D[5]; }
+
+static int omega_search(Mesh* m, int scheme, const double* u, const double* du, const double* c, const double* p,
+                        double d0n2, double omega0, const pbfb_newton_opts& o, double* omega_out, int* evals,
+                        int* fallback) {
+  double D[8 * 16];
+  double om = omega0;
+  bool ok = false;
+  *evals = 0;
+  for (int it = 0; it < o.max_omega_iters; ++it) {
+    PB_TRY(omega_eval(m, scheme, u, du, c, p, &om, 1, D));
+    ++*evals;
+    double PP = D[1];
+    if (!std::isfinite(PP) || std::fabs(PP) < 1e-300) break;
+    double f = -D[0] / PP - om;
+    double fp = -(D[2] + D[3]) / PP + D[0] * D[4] / (PP * PP) - 1.0;
+    if (!std::isfinite(f)) break;
+    if (std::fabs(f) < o.tol_omega) {
+      double dn = dnorm2(D, om);
+      ok = om > 0.0 && om <= o.omega_max && std::isfinite(dn) && dn < d0n2;
+      break;
+    }
+    if (!std::isfinite(fp) || fp == 0.0) break;
+    om = om - f / fp;
+    if (!std::isfinite(om)) break;
+  }
+  if (!ok) {
+    // scan g_d(omega) = omega (p+r').p + (p+r').r at omega_max j / 16, j = 1..16 (one batch)
+    double oms[16];
+    for (int j = 0; j < 16; ++j) oms[j] = o.omega_max * (j + 1) / 16.0;
+    PB_TRY(omega_eval(m, scheme, u, du, c, p, oms, 16, D));
+    ++*evals;
+    double lo = 0.0, hi = -1.0;
+    for (int j = 0; j < 16; ++j) {
+      double gdv = oms[j] * D[8 * j + 1] + D[8 * j + 0];
+      if (!std::isfinite(gdv) || gdv >= 0.0) {
+        hi = oms[j];
+        break;
+      }
+      lo = oms[j];
+    }
+    if (hi < 0.0) {
+      om = o.omega_max;
+    } else {
+      for (int it = 0; it < 20; ++it) {
+        double mid = 0.5 * (lo + hi);
+        PB_TRY(omega_eval(m, scheme, u, du, c, p, &mid, 1, D));
+        ++*evals;
+        double gdv = mid * D[1] + D[0];
+        if (std::isfinite(gdv) && gdv < 0.0)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      om = 0.5 * (lo + hi);
+    }
+    PB_TRY(omega_eval(m, scheme, u, du, c, p, &om, 1, D));
+    ++*evals;
+    double dn = dnorm2(D, om);
+    if (!(std::isfinite(dn) && dn < d0n2)) {
+      set_error("omega search: no relaxation factor in (0, %g] reduces ||d||", o.omega_max);
+      return PBFB_ERR_OMEGA;
+    }
+    ++*fallback;
+  }
+  *omega_out = om;
+  return PBFB_OK;
+}
+
+// ------------------------------------------------------------------ energy
+
+static int energy(Mesh* m, const double* xL, const double* xNL, double* out4) {
+  PB_TRY(ensure(m->tmp, m->n));
+  PB_TRY(ensure(m->urb, 2 * (size_t)m->nq));
+  PB_TRY(launch_reaction_potential(m, xL, m->urb.p));
+  PB_TRY(launch_reaction_potential(m, xNL, m->urb.p + m->nq));
+  std::vector<double> urh(2 * (size_t)m->nq);
+  PB_CUDA(cudaMemcpyAsync(urh.data(), m->urb.p, urh.size() * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  // ion term on u = (x_L + x_NL) restricted to the shell
+  PB_TRY(launch_axpby(m, m->nv, 1.0, xL, 1.0, xNL, m->tmp.p));
+  PB_TRY(launch_ion_energy(m, m->tmp.p, m->scal.p + 1000));
+  PB_CUDA(cudaMemcpyAsync(m->pinned, m->scal.p + 1000, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  PB_CUDA(cudaStreamSynchronize(m->stream));
+  double LC = 0.0, NC = 0.0;
+  for (int k = 0; k < m->nq; ++k) {
+    LC += m->qz_h[k] * urh[k];
+    NC += m->qz_h[k] * urh[m->nq + k];
+  }
+  LC *= 0.5 * m->kT;
+  NC *= 0.5 * m->kT;
+  const double c0 = m->coef / (8.0 * M_PI * m->lB);
+  const double dG = m->kT * c0 * m->pinned[0];
+  out4[0] = LC + NC + dG;
+  out4[1] = LC;
+  out4[2] = NC;
+  out4[3] = dG;
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(out4[k])) {
+      set_error("energy is not finite");
+      return PBFB_ERR_NONFINITE;
+    }
+  return PBFB_OK;
+}
+
+// ------------------------------------------------------------------ full solve
+
+static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T, const pbfb_newton_opts* opts_in,
+                 double* x_out_dev, pbfb_result* res) {
+  using clk = std::chrono::steady_clock;
+  pbfb_newton_opts o;
+  pbfb_default_opts(&o);
+  if (opts_in) o = *opts_in;
+  pbfb_result R;
+  std::memset(&R, 0, sizeof(R));
+  if (!m->charges) {
+    set_error("solve: charges not set");
+    return PBFB_ERR_STATE;
+  }
+  if (!(o.tol_nl > 0) || !(o.tol_gmres > 0) || !(o.tol_gmres0 > 0) || !(o.tol_omega > 0) || o.max_newton < 1 ||
+      o.max_gmres < 1 || !(o.omega_max > 0) || o.max_omega_iters < 1 ||
+      (o.first_scheme != PBFB_T3 && o.first_scheme != PBFB_HS && o.first_scheme != PBFB_LINEAR)) {
+    set_error("solve: invalid options");
+    return PBFB_ERR_INVALID;
+  }
+  PB_TRY(set_params(m, eps_in, eps_out, kappa, T, o.precision));
+  const int n = m->n, nv = m->nv;
+  for (auto* b : {&m->xL, &m->xNL, &m->phi, &m->cvec, &m->dvec, &m->du, &m->pvec, &m->Nvec, &m->tmp, &m->bvec})
+    PB_TRY(ensure(*b, n));
+  // right-hand side [0; (l_B/eps_m) <u_coul, psi>; 0]
+  double* bvec = m->bvec.p;
+  PB_CUDA(cudaMemsetAsync(bvec, 0, n * sizeof(double), m->stream));
+  k_set_rhs<<<blocks_for(m->sm.nv, 256), 256, 0, m->stream>>>(m->sm.nv, m->sm.col0, m->lB / m->eps_m, m->coul.p,
+                                                               bvec);
+  PB_LAUNCHED(m);
+  auto t0 = clk::now();
+  double tol = o.tol_gmres0;
+  // linear part: J = eps_s kappa^2 M (F' = 1)
+  PB_CUDA(cudaMemsetAsync(m->phi.p, 0, n * sizeof(double), m->stream));
+  PB_TRY(assemble(m, PBFB_LINEAR, m->phi.p, nullptr));
+  int its = 0;
+  double rel = 0;
+  int st = gmres(m, bvec, m->xL.p, tol, o.restart, o.max_gmres, &its, &rel);
+  R.linear_gmres_iters = its;
+  if (st) {
+    R.status = st;
+    if (res) *res = R;
+    return st;
+  }
+  auto t1 = clk::now();
+  PB_CUDA(cudaMemsetAsync(m->xNL.p, 0, n * sizeof(double), m->stream));
+  double om_last = -1.0, e_prev = -1.0;
+  bool converged = false;
+  int k = 0;
+  for (k = 0; k < o.max_newton; ++k) {
+    const int scheme = k == 0 ? o.first_scheme : PBFB_HS;
+    PB_TRY(launch_axpby(m, n, 1.0, m->xL.p, 1.0, m->xNL.p, m->phi.p));
+    // c = b - Acal(0) Phi
+    PB_TRY(clear_jacobian(m));
+    PB_TRY(apply(m, m->phi.p, m->cvec.p));
+    PB_TRY(launch_axpby(m, n, 1.0, bvec, -1.0, m->cvec.p, m->cvec.p));
+    // J(u), N(u); d = c - [N; 0; 0]
+    PB_TRY(assemble(m, scheme, m->phi.p, m->Nvec.p));
+    PB_CUDA(cudaMemcpyAsync(m->dvec.p, m->cvec.p, n * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+    k_sub_load<<<blocks_for(nv, 256), 256, 0, m->stream>>>(nv, m->Nvec.p, m->dvec.p);
+    PB_LAUNCHED(m);
+    double d2;
+    PB_TRY(dot(m, m->dvec.p, m->dvec.p, n, &d2));
+    if (!std::isfinite(d2)) {
+      set_error("Newton: non-finite residual at iteration %d", k);
+      R.status = PBFB_ERR_NONFINITE;
+      if (res) *res = R;
+      return R.status;
+    }
+    st = gmres(m, m->dvec.p, m->du.p, tol, o.restart, o.max_gmres, &its, &rel);
+    if (k < PBFB_MAX_TRACE) R.gmres_iters[k] = its;
+    if (st) {
+      R.status = st;
+      R.newton_iters = k + 1;
+      if (res) *res = R;
+      return st;
+    }
+    double om;
+    int evals = 0;
+    if (!o.omega_search) {
+      om = k == 0 ? o.omega0_first : o.omega0_rest;
+    } else if (k > 0 && e_prev >= 0.0 && e_prev < o.L_e && om_last > 0.0) {
+      om = om_last;
+    } else {
+      // p = -Acal(0) Delta
+      PB_TRY(clear_jacobian(m));
+      PB_TRY(apply(m, m->du.p, m->pvec.p));
+      PB_TRY(launch_axpby(m, n, -1.0, m->pvec.p, 0.0, nullptr, m->pvec.p));
+      st = omega_search(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, d2,
+                        k == 0 ? o.omega0_first : o.omega0_rest, o, &om, &evals, &R.omega_fallbacks);
+      if (st) {
+        R.status = st;
+        R.newton_iters = k + 1;
+        if (res) *res = R;
+        return st;
+      }
+    }
+    om_last = om;
+    PB_TRY(launch_axpby(m, n, om, m->du.p, 1.0, m->xNL.p, m->xNL.p));
+    double du2;
+    PB_TRY(dot(m, m->du.p, m->du.p, n, &du2));
+    double e = om * std::sqrt(du2);
+    if (k < PBFB_MAX_TRACE) {
+      R.omega[k] = om;
+      R.e[k] = e;
+      R.omega_evals[k] = evals;
+    }
+    if (!std::isfinite(e)) {
+      set_error("Newton: non-finite update at iteration %d", k);
+      R.status = PBFB_ERR_NONFINITE;
+      if (res) *res = R;
+      return R.status;
+    }
+    e_prev = e;
+    if (e < 1250.0 * tol) tol = std::max(0.1 * tol, o.tol_gmres);
+    if (e < o.tol_nl) {
+      converged = true;
+      break;
+    }
+  }
+  R.newton_iters = std::min(k + 1, o.max_newton);
+  auto t2 = clk::now();
+  if (!converged) {
+    set_error("Newton did not converge in %d iterations", o.max_newton);
+    R.status = PBFB_ERR_NEWTON_NOCONV;
+    if (res) *res = R;
+    return R.status;
+  }
+  double E[4];
+  PB_TRY(energy(m, m->xL.p, m->xNL.p, E));
+  auto t3 = clk::now();
+  R.dG_total = E[0];
+  R.dG_LC = E[1];
+  R.dG_NC = E[2];
+  R.dG_Omega_i = E[3];
+  R.ms_linear = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  R.ms_newton = std::chrono::duration<double, std::milli>(t2 - t1).count();
+  R.ms_energy = std::chrono::duration<double, std::milli>(t3 - t2).count();
+  if (x_out_dev) PB_TRY(launch_axpby(m, n, 1.0, m->xL.p, 1.0, m->xNL.p, x_out_dev));
+  PB_CUDA(cudaStreamSynchronize(m->stream));
+  R.status = PBFB_OK;
+  if (res) *res = R;
+  return PBFB_OK;
+}
+
+}  // namespace pbfb
+
+// ==================================================================== C ABI
+
+using pbfb::Mesh;
+
+struct pbfb_mesh {
+  Mesh* m;
+};
+
+#define PB_HANDLE(h)                                  \
+  if (!(h) || !(h)->m) {                              \
+    pbfb::set_error("null mesh handle");              \
+    return PBFB_ERR_INVALID;                          \
+  }                                                   \
+  Mesh* m = (h)->m;                                   \
+  if (cudaSetDevice(m->dev) != cudaSuccess) {         \
+    pbfb::set_error("cudaSetDevice failed");          \
+    return PBFB_ERR_CUDA;                             \
+  }
+
+extern "C" {
+
+void pbfb_default_opts(pbfb_newton_opts* o) {
+  if (!o) return;
+  o->precision = PBFB_FP64;
+  o->tol_nl = 1e-3;
+  o->tol_gmres = 1e-6;
+  o->tol_gmres0 = 1e-3;
+  o->tol_omega = 0.1;
+  o->L_e = 0.35;
+  o->omega0_first = 2.0;
+  o->omega0_rest = 1.0;
+  o->omega_max = 4.0;
+  o->max_newton = 50;
+  o->max_gmres = 1000;
+  o->restart = 200;
+  o->max_omega_iters = 30;
+  o->first_scheme = PBFB_T3;
+  o->omega_search = 1;
+}
+
+const char* pbfb_last_error(void) { return pbfb::last_error(); }
+
+int pbfb_mesh_create(const double* xyz, int32_t n_v, const int32_t* tets, int64_t n_t, const int32_t* gm_tris,
+                     int32_t n_gm, const int32_t* gs_tris, int32_t n_gs, uintptr_t stream, pbfb_mesh** out) {
+  pbfb::set_error("");
+  if (!out) {
+    pbfb::set_error("mesh_create: out is NULL");
+    return PBFB_ERR_INVALID;
+  }
+  *out = nullptr;
+  Mesh* m = nullptr;
+  int st = pbfb::mesh_create(xyz, n_v, tets, n_t, gm_tris, n_gm, gs_tris, n_gs, (cudaStream_t)stream, &m);
+  if (st) return st;
+  *out = new pbfb_mesh{m};
+  return PBFB_OK;
+}
+
+int pbfb_mesh_sizes(const pbfb_mesh* h, int64_t* s) {
+  if (!h || !h->m || !s) {
+    pbfb::set_error("mesh_sizes: null argument");
+    return PBFB_ERR_INVALID;
+  }
+  const Mesh* m = h->m;
+  s[0] = m->nv;
+  s[1] = m->nt;
+  s[2] = m->sm.nv;
+  s[3] = m->ss.nv;
+  s[4] = m->n;
+  s[5] = m->fem_nnz;
+  s[6] = m->s_ptr_h[m->ss.col0] - m->s_ptr_h[m->sm.col0];
+  s[7] = m->s_ptr_h[m->n] - m->s_ptr_h[m->ss.col0];
+  return PBFB_OK;
+}
+
+int pbfb_surface_vertices(const pbfb_mesh* h, int which, int32_t* out) {
+  if (!h || !h->m || !out || (which != PBFB_GAMMA_M && which != PBFB_GAMMA_S)) {
+    pbfb::set_error("surface_vertices: bad argument");
+    return PBFB_ERR_INVALID;
+  }
+  const pbfb::Surface& s = which == PBFB_GAMMA_M ? h->m->sm : h->m->ss;
+  std::memcpy(out, s.vmap_h.data(), s.vmap_h.size() * sizeof(int32_t));
+  return PBFB_OK;
+}
+
+int pbfb_charges_set(pbfb_mesh* h, const double* xyz, const double* z, int32_t n_q) {
+  PB_HANDLE(h);
+  if (!xyz || !z || n_q < 1) {
+    pbfb::set_error("charges_set: need at least one charge");
+    return PBFB_ERR_INVALID;
+  }
+  std::vector<double> soa(3 * (size_t)n_q);
+  for (int k = 0; k < n_q; ++k) {
+    for (int d = 0; d < 3; ++d) {
+      if (!std::isfinite(xyz[3 * k + d])) {
+        pbfb::set_error("charges_set: non-finite position");
+        return PBFB_ERR_INVALID;
+      }
+      soa[(size_t)d * n_q + k] = xyz[3 * k + d];
+    }
+    if (!std::isfinite(z[k])) {
+      pbfb::set_error("charges_set: non-finite charge");
+      return PBFB_ERR_INVALID;
+    }
+  }
+  int st;
+  if ((st = m->qxyz.upload(soa.data(), soa.size(), m->stream))) return st;
+  if ((st = m->qz.upload(z, n_q, m->stream))) return st;
+  m->qz_h.assign(z, z + n_q);
+  m->nq = n_q;
+  if ((st = m->coul.alloc(m->sm.nv))) return st;
+  if ((st = pbfb::launch_coulomb(m))) return st;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
+    pbfb::set_error("charges_set: %s", cudaGetErrorString(cudaGetLastError()));
+    return PBFB_ERR_CUDA;
+  }
+  m->charges = true;
+  return PBFB_OK;
+}
+
+int pbfb_solve_device(pbfb_mesh* h, double eps_in, double eps_out, double kappa, double T,
+                      const pbfb_newton_opts* opts, double* x_out_dev, pbfb_result* res) {
+  PB_HANDLE(h);
+  return pbfb::solve(m, eps_in, eps_out, kappa, T, opts, x_out_dev, res);
+}
+
+int pbfb_solve(pbfb_mesh* h, double eps_in, double eps_out, double kappa, double T, const pbfb_newton_opts* opts,
+               double* u_out, double* lam_m_out, double* lam_s_out, pbfb_result* res) {
+  PB_HANDLE(h);
+  int st = pbfb::ensure(m->xout, m->n);
+  if (st) return st;
+  pbfb::DBuf<double>& x = m->xout;
+  st = pbfb::solve(m, eps_in, eps_out, kappa, T, opts, x.p, res);
+  if (st) return st;
+  if (u_out && cudaMemcpy(u_out, x.p, m->nv * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) st = PBFB_ERR_CUDA;
+  if (lam_m_out && cudaMemcpy(lam_m_out, x.p + m->sm.col0, m->sm.nv * sizeof(double), cudaMemcpyDeviceToHost))
+    st = PBFB_ERR_CUDA;
+  if (lam_s_out && cudaMemcpy(lam_s_out, x.p + m->ss.col0, m->ss.nv * sizeof(double), cudaMemcpyDeviceToHost))
+    st = PBFB_ERR_CUDA;
+  if (st) pbfb::set_error("solve: copy of the solution failed");
+  return st;
+}
+
+int pbfb_mesh_destroy(pbfb_mesh* h) {
+  if (!h) return PBFB_OK;
+  if (h->m) {
+    cudaSetDevice(h->m->dev);
+    cudaStreamSynchronize(h->m->stream);
+    pbfb::timer_flush(h->m->t_nbody);
+    pbfb::timer_flush(h->m->t_spmv);
+    pbfb::timer_flush(h->m->t_elem);
+    if (h->m->pinned) cudaFreeHost(h->m->pinned);
+    delete h->m;
+  }
+  delete h;
+  return PBFB_OK;
+}
+
+int pbfb_set_params(pbfb_mesh* h, double eps_in, double eps_out, double kappa, double T, int precision) {
+  PB_HANDLE(h);
+  int st = pbfb::set_params(m, eps_in, eps_out, kappa, T, precision);
+  if (st) return st;
+  return cudaStreamSynchronize(m->stream) == cudaSuccess ? PBFB_OK : PBFB_ERR_CUDA;
+}
+
+#define PB_NEED_PARAMS                              \
+  if (!m->params) {                                 \
+    pbfb::set_error("call pbfb_set_params first");  \
+    return PBFB_ERR_STATE;                          \
+  }
+
+int pbfb_assemble(pbfb_mesh* h, int scheme, const double* u_dev, double* N_out_dev) {
+  PB_HANDLE(h);
+  PB_NEED_PARAMS;
+  if (!u_dev || (scheme != PBFB_LINEAR && scheme != PBFB_T3 && scheme != PBFB_HS)) {
+    pbfb::set_error("assemble: bad argument");
+    return PBFB_ERR_INVALID;
+  }
+  int st = pbfb::assemble(m, scheme, u_dev, N_out_dev);
+  if (st) return st;
+  return cudaStreamSynchronize(m->stream) == cudaSuccess ? PBFB_OK : PBFB_ERR_CUDA;
+}
+
+int pbfb_clear_jacobian(pbfb_mesh* h) {
+  PB_HANDLE(h);
+  PB_NEED_PARAMS;
+  int st = pbfb::clear_jacobian(m);
+  if (st) return st;
+  return cudaStreamSynchronize(m->stream) == cudaSuccess ? PBFB_OK : PBFB_ERR_CUDA;
+}
+
+int pbfb_apply(pbfb_mesh* h, const double* x_dev, double* y_dev) {
+  PB_HANDLE(h);
+  PB_NEED_PARAMS;
+  if (!x_dev || !y_dev || x_dev == y_dev) {
+    pbfb::set_error("apply: bad pointers");
+    return PBFB_ERR_INVALID;
+  }
+  int st = pbfb::apply(m, x_dev, y_dev);
+  if (st) return st;
+  return cudaStreamSynchronize(m->stream) == cudaSuccess ? PBFB_OK : PBFB_ERR_CUDA;
+}
+
+int pbfb_bem_apply(pbfb_mesh* h, int which, int op, const double* x_dev, double* y_dev) {
+  PB_HANDLE(h);
+  PB_NEED_PARAMS;
+  if (!x_dev || !y_dev || (which != PBFB_GAMMA_M && which != PBFB_GAMMA_S) || (op != 0 && op != 1)) {
+    pbfb::set_error("bem_apply: bad argument");
+    return PBFB_ERR_INVALID;
+  }
+  pbfb::Surface* s = which == PBFB_GAMMA_M ? &m->sm : &m->ss;
+  double kap = which == PBFB_GAMMA_M ? 0.0 : m->kappa;
+  int st = pbfb::launch_bem_far(m, s, x_dev, x_dev, op == 0 ? 1.0 : 0.0, op == 1 ? 1.0 : 0.0, kap, m->precision,
+                                y_dev, false);
+  if (st) return st;
+  // near-field correction: y += C x (CSR on the surface pattern)
+  st = pbfb::launch_csr_spmv(m, s->nv, s->c_ptr.p, s->c_col.p, op == 0 ? s->corrV.p : s->corrK.p, x_dev, y_dev,
+                             true);
+  if (st) return st;
+  return cudaStreamSynchronize(m->stream) == cudaSuccess ? PBFB_OK : PBFB_ERR_CUDA;
+}
+
+int pbfb_fem_rows(const pbfb_mesh* h, int32_t* rowptr, int32_t* col, double* val) {
+  if (!h || !h->m || !rowptr || !col || !val) {
+    pbfb::set_error("fem_rows: null argument");
+    return PBFB_ERR_INVALID;
+  }
+  const Mesh* m = h->m;
+  cudaSetDevice(m->dev);
+  cudaStreamSynchronize(m->stream);
+  std::memcpy(rowptr, m->s_ptr_h.data(), (m->nv + 1) * sizeof(int32_t));
+  std::memcpy(col, m->s_col_h.data(), m->fem_nnz * sizeof(int32_t));
+  if (cudaMemcpy(val, m->s_val.p, m->fem_nnz * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    pbfb::set_error("fem_rows: copy failed");
+    return PBFB_ERR_CUDA;
+  }
+  return PBFB_OK;
+}
+
+int pbfb_gmres(pbfb_mesh* h, const double* b_dev, double* x_dev, double tol, int restart, int maxit, int* iters,
+               double* relres) {
+  PB_HANDLE(h);
+  PB_NEED_PARAMS;
+  if (!b_dev || !x_dev || !(tol > 0) || maxit < 1) {
+    pbfb::set_error("gmres: bad argument");
+    return PBFB_ERR_INVALID;
+  }
+  int it = 0;
+  double rel = 0;
+  int st = pbfb::gmres(m, b_dev, x_dev, tol, restart, maxit, &it, &rel);
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  return st;
+}
+
+int pbfb_omega_eval(pbfb_mesh* h, int scheme, const double* u_dev, const double* du_dev, const double* c_dev,
+                    const double* p_dev, const double* omegas, int n_omega, double* dots) {
+  PB_HANDLE(h);
+  PB_NEED_PARAMS;
+  if (!u_dev || !du_dev || !c_dev || !p_dev || !omegas || !dots ||
+      (scheme != PBFB_LINEAR && scheme != PBFB_T3 && scheme != PBFB_HS)) {
+    pbfb::set_error("omega_eval: bad argument");
+    return PBFB_ERR_INVALID;
+  }
+  return pbfb::omega_eval(m, scheme, u_dev, du_dev, c_dev, p_dev, omegas, n_omega, dots);
+}
+
+int pbfb_energy(pbfb_mesh* h, const double* xL_dev, const double* xNL_dev, double* out) {
+  PB_HANDLE(h);
+  PB_NEED_PARAMS;
+  if (!m->charges || !xL_dev || !xNL_dev || !out) {
+    pbfb::set_error("energy: need charges and vectors");
+    return PBFB_ERR_STATE;
+  }
+  return pbfb::energy(m, xL_dev, xNL_dev, out);
+}
+
+int pbfb_profile(pbfb_mesh* h, int enable, int reset, double* stats) {
+  PB_HANDLE(h);
+  cudaStreamSynchronize(m->stream);
+  pbfb::timer_flush(m->t_nbody);
+  pbfb::timer_flush(m->t_spmv);
+  pbfb::timer_flush(m->t_elem);
+  if (stats) {
+    stats[0] = m->launches;
+    stats[1] = m->t_nbody.count;
+    stats[2] = m->t_nbody.ms;
+    stats[3] = m->t_nbody.work;
+    stats[4] = m->t_spmv.count;
+    stats[5] = m->t_spmv.ms;
+    stats[6] = m->t_elem.count;
+    stats[7] = m->t_elem.ms;
+    for (int k = 8; k < 16; ++k) stats[k] = 0.0;
+  }
+  if (reset) {
+    m->launches = 0;
+    for (auto* t : {&m->t_nbody, &m->t_spmv, &m->t_elem}) {
+      t->ms = 0;
+      t->count = 0;
+      t->work = 0;
+    }
+  }
+  m->timing = enable != 0;
+  return PBFB_OK;
+}
+
+}  // extern "C"

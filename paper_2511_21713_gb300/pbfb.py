@@ -1,0 +1,251 @@
+"""Python binding of libpbfb (include/pbfb.h): argument marshalling only.
+
+Every function here calls the C ABI of the same name; all computation happens in
+the CUDA library.  Device buffers are torch CUDA tensors (float64, contiguous);
+host buffers are numpy arrays.  Loading fails loudly when libpbfb.so has not
+been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpbfb.so")
+
+PBFB_OK = 0
+ERRORS = {1: "INVALID", 2: "CUDA", 3: "GMRES_NOCONV", 4: "NEWTON_NOCONV", 5: "OMEGA",
+          6: "NONFINITE", 7: "OOM", 8: "STATE"}
+FP64, MIXED = 0, 1
+LINEAR, T3, HS = 0, 1, 2
+GAMMA_M, GAMMA_S = 0, 1
+MAX_TRACE = 64
+
+# every symbol include/pbfb.h declares
+EXPORTS = [
+    "pbfb_default_opts", "pbfb_mesh_create", "pbfb_mesh_sizes", "pbfb_surface_vertices",
+    "pbfb_charges_set", "pbfb_solve", "pbfb_solve_device", "pbfb_mesh_destroy",
+    "pbfb_last_error", "pbfb_set_params", "pbfb_assemble", "pbfb_clear_jacobian",
+    "pbfb_apply", "pbfb_bem_apply", "pbfb_fem_rows", "pbfb_gmres", "pbfb_omega_eval",
+    "pbfb_energy", "pbfb_profile",
+]
+
+
+class PbfbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pbfb error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class NewtonOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol_nl", ctypes.c_double),
+                ("tol_gmres", ctypes.c_double), ("tol_gmres0", ctypes.c_double),
+                ("tol_omega", ctypes.c_double), ("L_e", ctypes.c_double),
+                ("omega0_first", ctypes.c_double), ("omega0_rest", ctypes.c_double),
+                ("omega_max", ctypes.c_double), ("max_newton", ctypes.c_int),
+                ("max_gmres", ctypes.c_int), ("restart", ctypes.c_int),
+                ("max_omega_iters", ctypes.c_int), ("first_scheme", ctypes.c_int),
+                ("omega_search", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("dG_total", ctypes.c_double), ("dG_LC", ctypes.c_double),
+                ("dG_NC", ctypes.c_double), ("dG_Omega_i", ctypes.c_double),
+                ("status", ctypes.c_int), ("newton_iters", ctypes.c_int),
+                ("linear_gmres_iters", ctypes.c_int), ("omega_fallbacks", ctypes.c_int),
+                ("gmres_iters", ctypes.c_int * MAX_TRACE), ("omega", ctypes.c_double * MAX_TRACE),
+                ("e", ctypes.c_double * MAX_TRACE), ("omega_evals", ctypes.c_int * MAX_TRACE),
+                ("ms_linear", ctypes.c_double), ("ms_newton", ctypes.c_double),
+                ("ms_energy", ctypes.c_double)]
+
+    def as_dict(self):
+        k = self.newton_iters
+        return dict(total=self.dG_total, LC=self.dG_LC, NC=self.dG_NC, dG_ion=self.dG_Omega_i,
+                    status=self.status, newton_iters=k, linear_gmres=self.linear_gmres_iters,
+                    gmres=list(self.gmres_iters[:k]), omega=list(self.omega[:k]), e=list(self.e[:k]),
+                    omega_evals=list(self.omega_evals[:k]), omega_fallbacks=self.omega_fallbacks,
+                    ms_linear=self.ms_linear, ms_newton=self.ms_newton, ms_energy=self.ms_energy)
+
+
+_lib = None
+
+
+def load():
+    """Load libpbfb.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, D, I, I64, U = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "pbfb_default_opts": (None, [ctypes.POINTER(NewtonOpts)]),
+        "pbfb_mesh_create": (I, [P, I, P, I64, P, I, P, I, U, ctypes.POINTER(P)]),
+        "pbfb_mesh_sizes": (I, [P, P]),
+        "pbfb_surface_vertices": (I, [P, I, P]),
+        "pbfb_charges_set": (I, [P, P, P, I]),
+        "pbfb_solve": (I, [P, D, D, D, D, P, P, P, P, P]),
+        "pbfb_solve_device": (I, [P, D, D, D, D, P, P, P]),
+        "pbfb_mesh_destroy": (I, [P]),
+        "pbfb_last_error": (ctypes.c_char_p, []),
+        "pbfb_set_params": (I, [P, D, D, D, D, I]),
+        "pbfb_assemble": (I, [P, I, P, P]),
+        "pbfb_clear_jacobian": (I, [P]),
+        "pbfb_apply": (I, [P, P, P]),
+        "pbfb_bem_apply": (I, [P, I, I, P, P]),
+        "pbfb_fem_rows": (I, [P, P, P, P]),
+        "pbfb_gmres": (I, [P, P, P, D, I, I, P, P]),
+        "pbfb_omega_eval": (I, [P, I, P, P, P, P, P, I, P]),
+        "pbfb_energy": (I, [P, P, P, P]),
+        "pbfb_profile": (I, [P, I, I, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != PBFB_OK:
+        raise PbfbError(code, load().pbfb_last_error().decode())
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def default_opts(**kw) -> NewtonOpts:
+    o = NewtonOpts()
+    load().pbfb_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def current_stream() -> int:
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Mesh:
+    """Owner of a pbfb_mesh handle."""
+
+    def __init__(self, xyz, tets, gm_tris, gs_tris, stream=None):
+        L = load()
+        self._keep = [np.ascontiguousarray(xyz, np.float64), np.ascontiguousarray(tets, np.int32),
+                      np.ascontiguousarray(gm_tris, np.int32), np.ascontiguousarray(gs_tris, np.int32)]
+        x, t, gm, gs = self._keep
+        h = ctypes.c_void_p()
+        s = current_stream() if stream is None else stream
+        _check(L.pbfb_mesh_create(_ptr(x), x.shape[0], _ptr(t), t.shape[0], _ptr(gm), gm.shape[0],
+                                  _ptr(gs), gs.shape[0], s, ctypes.byref(h)))
+        self.h = h
+        sz = np.zeros(8, np.int64)
+        _check(L.pbfb_mesh_sizes(self.h, _ptr(sz)))
+        self.n_v, self.n_t, self.n_m, self.n_s, self.n, self.fem_nnz, self.nnz_m, self.nnz_s = map(int, sz)
+
+    @classmethod
+    def from_case(cls, case, stream=None):
+        return cls(case.xyz, case.tets, case.gm_tris, case.gs_tris, stream)
+
+    def surface_vertices(self, which):
+        out = np.zeros(self.n_m if which == GAMMA_M else self.n_s, np.int32)
+        _check(load().pbfb_surface_vertices(self.h, which, _ptr(out)))
+        return out
+
+    def charges_set(self, xyz, z):
+        xyz = np.ascontiguousarray(xyz, np.float64)
+        z = np.ascontiguousarray(z, np.float64)
+        _check(load().pbfb_charges_set(self.h, _ptr(xyz), _ptr(z), int(z.shape[0])))
+
+    def solve(self, eps_in, eps_out, kappa, T, opts=None, outputs=True):
+        """Host-buffer solve; returns (x = [u; lam_m; lam_s] numpy or None, result dict)."""
+        res = Result()
+        if outputs:
+            u, lm, ls = np.zeros(self.n_v), np.zeros(self.n_m), np.zeros(self.n_s)
+            args = (_ptr(u), _ptr(lm), _ptr(ls))
+        else:
+            args = (None, None, None)
+        code = load().pbfb_solve(self.h, eps_in, eps_out, kappa, T,
+                                 ctypes.byref(opts) if opts is not None else None, *args,
+                                 ctypes.byref(res))
+        _check(code)
+        x = np.concatenate([u, lm, ls]) if outputs else None
+        return x, res.as_dict()
+
+    def solve_device(self, eps_in, eps_out, kappa, T, x_out=None, opts=None):
+        res = Result()
+        _check(load().pbfb_solve_device(self.h, eps_in, eps_out, kappa, T,
+                                        ctypes.byref(opts) if opts is not None else None,
+                                        _ptr(x_out), ctypes.byref(res)))
+        return res.as_dict()
+
+    def set_params(self, eps_in, eps_out, kappa, T, precision=FP64):
+        _check(load().pbfb_set_params(self.h, eps_in, eps_out, kappa, T, precision))
+
+    def assemble(self, scheme, u_dev, N_out_dev=None):
+        _check(load().pbfb_assemble(self.h, scheme, _ptr(u_dev), _ptr(N_out_dev)))
+
+    def clear_jacobian(self):
+        _check(load().pbfb_clear_jacobian(self.h))
+
+    def apply(self, x_dev, y_dev):
+        _check(load().pbfb_apply(self.h, _ptr(x_dev), _ptr(y_dev)))
+
+    def bem_apply(self, which, op, x_dev, y_dev):
+        _check(load().pbfb_bem_apply(self.h, which, op, _ptr(x_dev), _ptr(y_dev)))
+
+    def fem_rows(self):
+        rp = np.zeros(self.n_v + 1, np.int32)
+        col = np.zeros(self.fem_nnz, np.int32)
+        val = np.zeros(self.fem_nnz)
+        _check(load().pbfb_fem_rows(self.h, _ptr(rp), _ptr(col), _ptr(val)))
+        return rp, col, val
+
+    def gmres(self, b_dev, x_dev, tol, restart=200, maxit=1000):
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        _check(load().pbfb_gmres(self.h, _ptr(b_dev), _ptr(x_dev), tol, restart, maxit,
+                                 ctypes.byref(it), ctypes.byref(rel)))
+        return it.value, rel.value
+
+    def omega_eval(self, scheme, u_dev, du_dev, c_dev, p_dev, omegas):
+        om = np.ascontiguousarray(omegas, np.float64).reshape(-1)
+        out = np.zeros((om.size, 8))
+        _check(load().pbfb_omega_eval(self.h, scheme, _ptr(u_dev), _ptr(du_dev), _ptr(c_dev),
+                                      _ptr(p_dev), _ptr(om), om.size, _ptr(out)))
+        return out
+
+    def energy(self, xL_dev, xNL_dev):
+        out = np.zeros(4)
+        _check(load().pbfb_energy(self.h, _ptr(xL_dev), _ptr(xNL_dev), _ptr(out)))
+        return out
+
+    def profile(self, enable=True, reset=False):
+        st = np.zeros(16)
+        _check(load().pbfb_profile(self.h, int(enable), int(reset), _ptr(st)))
+        return dict(launches=st[0], nbody_launches=st[1], nbody_ms=st[2], nbody_pairs=st[3],
+                    spmv_launches=st[4], spmv_ms=st[5], elem_launches=st[6], elem_ms=st[7])
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().pbfb_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,98 @@
+"""The C ABI library builds, loads and exports every declared symbol; host-side
+validation works without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_21713_gb300 import build, pbfb
+    build.build()
+    return pbfb.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "pbfb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pbfb_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2511_21713_gb300 import pbfb
+    names = declared_symbols()
+    assert len(names) >= 19
+    assert sorted(pbfb.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_default_options_are_the_papers(lib):
+    from paper_2511_21713_gb300 import pbfb
+    o = pbfb.default_opts()
+    assert (o.tol_nl, o.tol_gmres, o.tol_gmres0, o.tol_omega, o.L_e) == (1e-3, 1e-6, 1e-3, 0.1, 0.35)
+    assert (o.omega0_first, o.omega0_rest, o.omega_max) == (2.0, 1.0, 4.0)
+    assert o.first_scheme == pbfb.T3 and o.omega_search == 1 and o.precision == pbfb.FP64
+
+
+def _create(lib, xyz, tets, gm, gs):
+    h = ctypes.c_void_p()
+    xyz = np.ascontiguousarray(xyz, np.float64)
+    tets = np.ascontiguousarray(tets, np.int32)
+    gm = np.ascontiguousarray(gm, np.int32)
+    gs = np.ascontiguousarray(gs, np.int32)
+    code = lib.pbfb_mesh_create(xyz.ctypes.data, xyz.shape[0], tets.ctypes.data, tets.shape[0],
+                                gm.ctypes.data, gm.shape[0], gs.ctypes.data, gs.shape[0], 0, ctypes.byref(h))
+    return code, h
+
+
+def test_mesh_validation_on_host(lib, tiny_case):
+    from paper_2511_21713_gb300 import pbfb
+    c = tiny_case
+    # out-of-range vertex id
+    bad = c.tets.copy()
+    bad[0, 0] = c.n_v
+    code, _ = _create(lib, c.xyz, bad, c.gm_tris, c.gs_tris)
+    assert code == 1 and b"out of range" in lib.pbfb_last_error()
+    # a missing surface triangle: the boundary is not covered
+    code, _ = _create(lib, c.xyz, c.tets, c.gm_tris[1:], c.gs_tris)
+    assert code == 1
+    # wrong orientation of Gamma_m
+    code, _ = _create(lib, c.xyz, c.tets, c.gm_tris[:, [0, 2, 1]], c.gs_tris)
+    assert code == 1 and b"orientation" in lib.pbfb_last_error()
+    # surfaces swapped: both orientations wrong
+    code, _ = _create(lib, c.xyz, c.tets, c.gs_tris, c.gm_tris)
+    assert code == 1
+    # degenerate tetrahedron
+    xyz = c.xyz.copy()
+    t0 = c.tets[0]
+    xyz[t0[3]] = xyz[t0[0]] + 0.5 * (xyz[t0[1]] - xyz[t0[0]]) + 0.5 * (xyz[t0[2]] - xyz[t0[0]])
+    code, _ = _create(lib, xyz, c.tets, c.gm_tris, c.gs_tris)
+    assert code == 1
+    # NaN coordinate
+    xyz = c.xyz.copy()
+    xyz[5, 1] = np.nan
+    code, _ = _create(lib, xyz, c.tets, c.gm_tris, c.gs_tris)
+    assert code == 1 and b"non-finite" in lib.pbfb_last_error()
+    assert pbfb.ERRORS[1] == "INVALID"
+
+
+def test_valid_mesh_without_gpu_reports_cuda_error(lib, tiny_case):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    c = tiny_case
+    code, h = _create(lib, c.xyz, c.tets, c.gm_tris, c.gs_tris)
+    assert code == 2 and not h.value          # PBFB_ERR_CUDA, no handle, no CPU fallback
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    z = np.zeros(8)
+    assert lib.pbfb_apply(None, z.ctypes.data, z.ctypes.data) == 1
+    assert lib.pbfb_solve(None, 1.0, 1.0, 0.1, 300.0, None, None, None, None, None) == 1
+    assert lib.pbfb_mesh_destroy(None) == 0

@@ -1,0 +1,243 @@
+"""Parity of every step of the CUDA path against the CPU oracle, through the C ABI.
+
+Inputs are the seeded spheres of paper_2511_21713_gb300.inputs: the small
+single-charge sphere (nu = 5, 13 layers: 3528 vertices, 19,500 tets, 500 + 500
+triangles, several GPU tiles and ragged tails everywhere) and a tiny one
+(nu = 3, 5 layers).  Tolerances: float64 path 1e-11 relative per step,
+1e-8 relative L2 on the converged potentials and 1e-9 on the solvation energy;
+the mixed path (float32 far field) 1e-5 on the energy.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(tol_gmres0=1e-12, tol_gmres=1e-12, tol_nl=1e-11)
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, np.float64), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module", params=["tiny", "small"])
+def pair(request, tiny_case, small_case, bem_cache):
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case = tiny_case if request.param == "tiny" else small_case
+    m = pbfb.Mesh.from_case(case)
+    m.charges_set(case.q_xyz, case.q_z)
+    P = pb.Problem(case, bem_cache=bem_cache)
+    yield case, m, P
+    m.close()
+
+
+def _u_field(P, seed=0):
+    rng = np.random.default_rng(seed)
+    r = np.linalg.norm(P.xyz, axis=1)
+    return 4.0 * np.exp(-0.3 * (r - r.min())) + 0.2 * rng.standard_normal(P.nv)
+
+
+def test_surface_vertex_order(pair):
+    from paper_2511_21713_gb300 import pbfb
+    _, m, P = pair
+    assert np.array_equal(m.surface_vertices(pbfb.GAMMA_M), P.sm.verts)
+    assert np.array_equal(m.surface_vertices(pbfb.GAMMA_S), P.ss.verts)
+    assert (m.n_v, m.n_m, m.n_s, m.n) == (P.nv, P.nm, P.ns, P.n)
+
+
+@pytest.mark.parametrize("scheme", ["linear", "T3", "HS"])
+def test_fem_rows_and_load(pair, scheme):
+    from paper_2511_21713_gb300 import pbfb
+    case, m, P = pair
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T)
+    u = _u_field(P, 1)
+    N_dev = dev(np.zeros(P.nv))
+    m.assemble({"linear": pbfb.LINEAR, "T3": pbfb.T3, "HS": pbfb.HS}[scheme], dev(u), N_dev)
+    rp, col, val = m.fem_rows()
+    G = sp.csr_matrix((val, col, rp), shape=(P.nv, P.n))
+    O = sp.hstack([P.A + P.J(u, scheme), P.B_um, P.B_us]).tocsr()
+    D = (G - O).toarray()
+    assert np.abs(D).max() <= 1e-12 * np.abs(O).max()
+    N_ref = P.N(u, scheme)
+    assert rel(host(N_dev), N_ref) < 1e-13
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_boundary_operators(pair, precision):
+    from paper_2511_21713_gb300 import pbfb
+    case, m, P = pair
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, precision)
+    tol = 1e-11 if precision == pbfb.FP64 else 3e-6
+    rng = np.random.default_rng(2)
+    for which, Vo, Ko, n in ((pbfb.GAMMA_M, P.VL, P.KL, P.nm), (pbfb.GAMMA_S, P.VY, P.KY, P.ns)):
+        for op, Mo in ((0, Vo), (1, Ko)):
+            x = rng.standard_normal(n) + 1.0
+            y = dev(np.zeros(n))
+            m.bem_apply(which, op, dev(x), y)
+            assert rel(host(y), Mo @ x) < tol, (which, op)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coupled_apply(pair, precision):
+    from paper_2511_21713_gb300 import pbfb
+    case, m, P = pair
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, precision)
+    u = _u_field(P, 3)
+    m.assemble(pbfb.HS, dev(u))
+    x = np.random.default_rng(4).standard_normal(P.n)
+    y = dev(np.zeros(P.n))
+    m.apply(dev(x), y)
+    ref = P.apply(x, P.J(u, "HS"))
+    tol = 1e-11 if precision == pbfb.FP64 else 3e-6
+    for a, b in zip(P.split(host(y)), P.split(ref)):
+        assert rel(a, b) < tol
+    m.clear_jacobian()
+    m.apply(dev(x), y)
+    assert rel(host(y), P.apply(x)) < tol
+
+
+def test_gmres_against_direct_solve(pair):
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T)
+    u = _u_field(P, 5)
+    m.assemble(pbfb.T3, dev(u))
+    b = np.random.default_rng(6).standard_normal(P.n)
+    x = dev(np.zeros(P.n))
+    its, r = m.gmres(dev(b), x, 1e-12)
+    xd = pb.linear_solve(P, P.J(u, "T3"), b, 0, pb.Opts(linear_solver="direct"))[0]
+    assert r <= 1e-12 and rel(host(x), xd) < 1e-9
+    # same Krylov method, same preconditioner: iteration counts agree closely
+    _, its_o, _ = pb.gmres(lambda v: P.apply(v, P.J(u, "T3")), b, 1e-12, 200, 2000, P.jacobi(P.J(u, "T3")))
+    assert abs(its - its_o) <= max(2, its_o // 50)
+
+
+def test_omega_batch(pair):
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T)
+    rng = np.random.default_rng(7)
+    u = _u_field(P, 8)
+    du = 0.3 * rng.standard_normal(P.nv)
+    c = rng.standard_normal(P.n)
+    p = rng.standard_normal(P.n)
+    oms = np.array([0.0, 0.5, 1.0, 1.7, 2.0, 3.9])
+    for scheme, sname in ((pbfb.T3, "T3"), (pbfb.HS, "HS")):
+        got = m.omega_eval(scheme, dev(u), dev(du), dev(c), dev(p), oms)
+        for o, om in enumerate(oms):
+            D = pb.omega_dots(P, u, du, c, p, om, sname)
+            ref = [D["PR"], D["PP"], D["PRp"], D["RRpp"], D["PRpp"], D["RR"], D["pr"], D["pp"]]
+            scale = max(abs(v) for v in ref)
+            assert np.abs(got[o] - ref).max() < 1e-11 * scale, (sname, om)
+
+
+def test_energy_of_oracle_solution(pair):
+    from oracle import pb
+    case, m, P = pair
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T)
+    R = pb.solve(P, pb.Opts(**TIGHT))
+    got = m.energy(dev(R.xL), dev(R.xNL))
+    ref = [R.total, R.LC, R.NC, R.dG_ion]
+    for g, r in zip(got, ref):
+        assert abs(g - r) < 1e-11 * abs(R.total)
+
+
+def test_full_solve_fp64_tight(pair):
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    x, res = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.default_opts(**TIGHT))
+    R = pb.solve(P, pb.Opts(**TIGHT))
+    for a, b in zip(P.split(x), P.split(R.x)):
+        assert rel(a, b) < 1e-8
+    assert abs(res["total"] - R.total) < 1e-9 * abs(R.total)
+    assert abs(res["LC"] - R.LC) < 1e-9 * abs(R.total)
+    assert abs(res["dG_ion"] - R.dG_ion) < 1e-9 * abs(R.total)
+    assert res["newton_iters"] == R.newton_iters
+
+
+def test_full_solve_mixed(pair):
+    """Float32 far field: its rounding noise floors the reachable relative residual near
+    1e-8, so the tolerances sit above it; the energy must still be within 1e-5."""
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    x, res = m.solve(case.eps_in, case.eps_out, case.kappa, case.T,
+                     pbfb.default_opts(precision=pbfb.MIXED, tol_gmres0=1e-7, tol_gmres=1e-7, tol_nl=1e-6))
+    R = pb.solve(P, pb.Opts(**TIGHT))
+    assert abs(res["total"] - R.total) < 1e-5 * abs(R.total)
+    assert rel(x, R.x) < 1e-4
+
+
+def test_paper_default_trace(pair):
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    _, res = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.default_opts())
+    R = pb.solve(P, pb.Opts())
+    assert res["newton_iters"] == R.newton_iters
+    assert np.allclose(res["omega"], R.trace["omega"], rtol=1e-3, atol=1e-3)
+    for g, o in zip(res["gmres"], R.trace["gmres"]):
+        assert abs(g - o) <= 2
+    assert abs(res["total"] - R.total) < 1e-4 * abs(R.total)
+
+
+def test_deterministic(pair):
+    from paper_2511_21713_gb300 import pbfb
+    case, m, _ = pair
+    o = pbfb.default_opts(**TIGHT)
+    x1, r1 = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, o)
+    x2, r2 = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, o)
+    assert np.array_equal(x1, x2) and r1["total"] == r2["total"]
+
+
+def test_kappa_zero_born_limit(tiny_case, bem_cache):
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    c = tiny_case
+    m = pbfb.Mesh.from_case(c)
+    m.charges_set(c.q_xyz, c.q_z)
+    x, res = m.solve(c.eps_in, c.eps_out, 0.0, c.T, pbfb.default_opts(**TIGHT))
+    P = pb.Problem(c, kappa=0.0, bem_cache=bem_cache)
+    R = pb.solve(P, pb.Opts(**TIGHT))
+    assert abs(res["total"] - R.total) < 1e-9 * abs(R.total)
+    assert res["dG_ion"] == 0.0
+    m.close()
+
+
+def test_error_statuses(tiny_case):
+    from paper_2511_21713_gb300 import pbfb
+    c = tiny_case
+    m = pbfb.Mesh.from_case(c)
+    with pytest.raises(pbfb.PbfbError) as e:
+        m.solve(c.eps_in, c.eps_out, c.kappa, c.T)
+    assert e.value.code == 8                       # STATE: no charges yet
+    with pytest.raises(pbfb.PbfbError) as e:
+        m.charges_set(np.array([[0.0, np.nan, 0.0]]), np.array([1.0]))
+    assert e.value.code == 1
+    m.charges_set(c.q_xyz, c.q_z)
+    with pytest.raises(pbfb.PbfbError) as e:
+        m.solve(-1.0, c.eps_out, c.kappa, c.T)
+    assert e.value.code == 1
+    with pytest.raises(pbfb.PbfbError) as e:
+        m.solve(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.default_opts(max_newton=1, tol_nl=1e-12))
+    assert e.value.code == 4                       # NEWTON_NOCONV
+    with pytest.raises(pbfb.PbfbError) as e:
+        m.solve(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.default_opts(max_gmres=3, tol_gmres0=1e-12))
+    assert e.value.code == 3                       # GMRES_NOCONV
+    # the handle stays usable after errors
+    _, res = m.solve(c.eps_in, c.eps_out, c.kappa, c.T)
+    assert res["status"] == 0
+    m.close()
