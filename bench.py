@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Throughput of the nonlinear Poisson-Boltzmann FEM-BEM Newton solve on GB300.
+
+One step = one complete solve of the multi-charge sphere workload through the
+C ABI: linear part (GMRES), Newton-Raphson with the cubic first iteration and
+the automatic relaxation factor (batched residual evaluations), and the
+solvation energy -- every row of the hot path.  The mesh is created and the
+charges set before timing (inputs resident in HBM).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--impl pbfb|reference]
+
+--impl reference times the CPU oracle (the plain float64 restatement of the
+method under oracle/) on a bounded sample of the same workload, scaled to
+solves/s.  Under torchrun (N > 1) every rank runs independent replicas of the
+solve (no collective on the data path); rank 0 prints.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nonlinear PB solves/s and p99 ms, mixed vs FP64 GPU at ≤1e-5 rel energy err"
+SM_COUNT = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+# float32 operations per far-field pair (FMA counted as 2): Laplace 18, Yukawa 24
+FLOP_PAIR = {"laplace": 18.0, "yukawa": 24.0}
+GOLDEN = os.path.join(ROOT, "tests", "golden", "multi_charge_sphere.json")
+
+
+def workload_config(case, precision):
+    return {
+        "workload": "multi_charge_sphere",
+        "geometry": "solute sphere r=12 A, FEM shell to 24 A (17 geometric layers), "
+                    "icosphere nu=20 on both surfaces",
+        "n_vertices": int(case.n_v), "n_tets": int(case.n_t),
+        "gamma_m_triangles": int(case.gm_tris.shape[0]), "gamma_s_triangles": int(case.gs_tris.shape[0]),
+        "charges": "200 x (+-1 e) uniform in r<10 A, net -20 e (seed 2000)",
+        "eps_in": case.eps_in, "eps_out": case.eps_out, "ionic_M": 0.1, "kappa_per_A": round(case.kappa, 6),
+        "T_K": case.T, "precision": precision,
+        "newton": "T3 first iteration, automatic omega (Newton on f_d), L_e 0.35, Tol_omega 0.1, "
+                  "Tol_GR0 1e-3 -> Tol_GR 1e-6, Tol_NL 1e-3",
+        "l2": "flushed between timed steps (256 MiB write)",
+    }
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_pbfb(args):
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+    from paper_2511_21713_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2511_21713_gb300 import inputs, pbfb
+
+    ws, rank, local = dist()
+    if ws > 1:
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = inputs.multi_charge_sphere()
+    prec = pbfb.MIXED if args.precision == "mixed" else pbfb.FP64
+    opts = pbfb.default_opts(precision=prec)
+    mesh = pbfb.Mesh.from_case(case)
+    mesh.charges_set(case.q_xyz, case.q_z)
+    x_out = torch.empty(mesh.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    res = None
+    for _ in range(args.warmup):
+        res = mesh.solve_device(case.eps_in, case.eps_out, case.kappa, case.T, x_out, opts)
+    torch.cuda.synchronize()
+    if ws > 1:
+        tdist.barrier()
+    clocks = Clocks(local)
+    mesh.profile(enable=True, reset=True)
+    clocks.start()
+    step_ms = []
+    results = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = mesh.solve_device(case.eps_in, case.eps_out, case.kappa, case.T, x_out, opts)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        results.append(res)
+    torch.cuda.synchronize()
+    if ws > 1:
+        tdist.barrier()
+    clk = clocks.stop()
+    prof = mesh.profile(enable=False, reset=True)
+    total_ms = sum(step_ms)
+    tot = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        tdist.all_reduce(tot, op=tdist.ReduceOp.MAX)
+    total_ms_max = float(tot.item())
+
+    # end to end through the public C ABI with host buffers: charges in, solution out
+    e2e_ms = []
+    h2d = case.q_xyz.nbytes + case.q_z.nbytes
+    d2h = 8 * mesh.n + 8 * 4
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mesh.charges_set(case.q_xyz, case.q_z)
+        xh, r2 = mesh.solve(case.eps_in, case.eps_out, case.kappa, case.T, opts)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_val = ws * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+
+    # roofline of the dominant kernel (the far-field N-body) from its live CUDA-event timing
+    nq_m = 6 * case.gm_tris.shape[0]
+    nq_s = 6 * case.gs_tris.shape[0]
+    launches = prof["nbody_launches"]
+    flops_per_launch_pair = 0.5 * (FLOP_PAIR["laplace"] + FLOP_PAIR["yukawa"])
+    pairs_per_launch = prof["nbody_pairs"] / max(launches, 1)
+    if prec == pbfb.MIXED:
+        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak_note = "fp32 non-tensor: 152 SM x 128 lanes x 2 flop x 2070 MHz"
+    else:
+        peak = 1.25
+        peak_note = "fp64 nominal 1.25 TFLOP/s"
+    avg_ms = prof["nbody_ms"] / max(launches, 1)
+    achieved = pairs_per_launch * flops_per_launch_pair / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else None
+
+    out = {
+        "metric": METRIC, "value": ws * args.steps / (total_ms_max / 1e3), "unit": "solves/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == pbfb.MIXED else "f64",
+        "data": "synthetic (seeded sphere mesh and charges)",
+        "config": workload_config(case, args.precision) | {"parallelism": f"replicas x{ws}"},
+        "p50_ms": statistics.median(step_ms),
+        "p99_ms": float(np.percentile(step_ms, 99)),
+        "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(prof["launches"]),
+        "roofline": {"bound": "alu", "kernel": "far-field N-body (k_nbody_f32/k_nbody_f64)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_basis": peak_note, "avg_launch_ms": avg_ms,
+                     "pairs_per_launch": pairs_per_launch, "launches": launches,
+                     "nbody_share_of_step": prof["nbody_ms"] / total_ms if total_ms else None},
+        "clocks": clk,
+        "solve": {"newton_iters": res["newton_iters"], "linear_gmres": res["linear_gmres"],
+                  "gmres": res["gmres"], "omega": [round(w, 4) for w in res["omega"]],
+                  "total_kcal_mol": res["total"], "LC": res["LC"], "NC": res["NC"], "dG_ion": res["dG_ion"]},
+    }
+    if os.path.exists(GOLDEN):
+        g = json.load(open(GOLDEN))
+        ref = g["tight"]["total"]
+        out["energy_rel_err_vs_oracle"] = abs(res["total"] - ref) / abs(ref)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(case, res, args.cpu_sample)
+    if ws > 1:
+        tdist.destroy_process_group()
+    mesh.close()
+    return out if rank == 0 else None
+
+
+def oracle_sample(case, gpu_res, frac_rows, newton=None):
+    """Time the oracle on a bounded sample of the workload and scale to one solve.
+
+    Sample: dense Galerkin assembly of 1/frac_rows of the test triangles of each
+    surface (both operators, all quadrature classes), one nonlinear load + Jacobian
+    assembly over all tets, one omega evaluation, and one coupled dense apply.  A
+    full oracle solve is modelled as frac_rows x the assembly sample + (Newton steps)
+    x (assembly + omega evaluations) + (matvecs) x apply, with the Newton, omega and
+    GMRES counts of the GPU solve.
+    """
+    import numpy as np
+    from oracle import bem, pb
+    t = {}
+    t0 = time.perf_counter()
+    P = object.__new__(pb.Problem)
+    # build the problem pieces without the full dense assembly
+    P.case = case
+    P.eps_m, P.eps_s, P.kappa, P.T = case.eps_in, case.eps_out, case.kappa, case.T
+    P.kT = pb.KB * P.T
+    P.lB = pb.COULOMB / P.kT
+    P.coef = P.eps_s * P.kappa ** 2
+    P.xyz, P.tets, P.nv = case.xyz, case.tets, case.xyz.shape[0]
+    P.sm, P.ss = bem.Surface(case.xyz, case.gm_tris), bem.Surface(case.xyz, case.gs_tris)
+    P.nm, P.ns = P.sm.n, P.ss.n
+    P.n = P.nv + P.nm + P.ns
+    from oracle import fem
+    import scipy.sparse as sp
+    P.A = fem.stiffness(case.xyz, case.tets, P.eps_s)
+    P.Mm, P.Ms = bem.mass_matrix(P.sm), bem.mass_matrix(P.ss)
+    P.Rm = sp.csr_matrix((np.ones(P.nm), (np.arange(P.nm), P.sm.verts)), shape=(P.nm, P.nv))
+    P.Rs = sp.csr_matrix((np.ones(P.ns), (np.arange(P.ns), P.ss.verts)), shape=(P.ns, P.nv))
+    P.B_um = P.eps_m * (P.Rm.T @ P.Mm)
+    P.B_us = -P.eps_s * (P.Rs.T @ P.Ms)
+    t["setup_fem_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sub_m = np.arange(0, P.sm.nt, frac_rows)
+    sub_s = np.arange(0, P.ss.nt, frac_rows)
+    P.VL, P.KL = bem.assemble(P.sm, 0.0, test_tris=sub_m)
+    P.VY, P.KY = bem.assemble(P.ss, P.kappa, test_tris=sub_s)
+    t["bem_sample_s"] = time.perf_counter() - t0
+    u = np.zeros(P.nv) + 0.5
+    t0 = time.perf_counter()
+    N = P.N(u, "HS")
+    Jm = P.J(u, "HS")
+    t["assembly_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x = np.ones(P.n)
+    P.apply(x, Jm)
+    t["apply_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pb.omega_dots(P, u, u, np.ones(P.n), np.ones(P.n), 1.0, "HS")
+    t["omega_eval_s"] = time.perf_counter() - t0
+    k = gpu_res["newton_iters"]
+    matvecs = gpu_res["linear_gmres"] + sum(gpu_res["gmres"]) + 3 * (k + 1)
+    evals = sum(gpu_res["omega_evals"])
+    sample_s = sum(t.values())
+    model_s = (t["setup_fem_s"] + frac_rows * t["bem_sample_s"] + (k + 1) * t["assembly_s"]
+               + evals * t["omega_eval_s"] + matvecs * t["apply_s"])
+    del N
+    return {"value": 1.0 / model_s, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"oracle (numpy float64) on this workload: BEM assembly of 1/{frac_rows} of the test "
+                       f"triangles per surface, one load+Jacobian assembly, one omega evaluation, one dense "
+                       f"coupled apply ({sample_s:.1f} s measured); one solve modelled as {frac_rows} x assembly "
+                       f"sample + {k + 1} assemblies + {evals} omega evaluations + {matvecs} applies "
+                       f"(GPU run's counts) = {model_s:.1f} s"),
+            "parts_s": {kk: round(v, 3) for kk, v in t.items()}, "model_s_per_solve": model_s}
+
+
+def run_reference(args):
+    """The CPU oracle arm: each step is the bounded oracle sample, scaled to solves/s."""
+    from paper_2511_21713_gb300 import inputs
+    ws, rank, _ = dist()
+    if rank != 0:
+        return None
+    case = inputs.multi_charge_sphere()
+    # iteration counts of a representative mixed GPU solve (from the golden oracle trace)
+    if os.path.exists(GOLDEN):
+        g = json.load(open(GOLDEN))["default"]
+        res = {"newton_iters": g["newton_iters"], "linear_gmres": g["linear_gmres"], "gmres": g["gmres"],
+               "omega_evals": [3] * g["newton_iters"]}
+    else:
+        res = {"newton_iters": 5, "linear_gmres": 150, "gmres": [150] * 5, "omega_evals": [3] * 5}
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; the sample itself is the step
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(case, res, args.cpu_sample)
+        vals.append(last["model_s_per_solve"])
+    v = len(vals) / sum(vals)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(vals) / len(vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded sphere mesh and charges)",
+            "config": workload_config(case, "fp64 (CPU oracle)") | {"parallelism": "1 host process"},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pbfb", choices=["pbfb", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-sample", type=int, default=64, help="1/k of the BEM rows in the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_pbfb(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -162,10 +162,21 @@ def _order_vertex(tt, ts):
     return [it, (it + 1) % 3, (it + 2) % 3], [is_, (is_ + 1) % 3, (is_ + 2) % 3]
 
 
-def assemble(s: Surface, kappa: float, n_ss: int = 5, chunk: int = 64, classes=None):
-    """Dense Galerkin (V, K) on surface s for the kernel with inverse length kappa."""
+def assemble(s: Surface, kappa: float, n_ss: int = 5, chunk: int = 64, classes=None, test_tris=None):
+    """Dense Galerkin (V, K) on surface s for the kernel with inverse length kappa.
+
+    test_tris: optional sorted subset of test triangles; only their contributions are
+    added (the rows of the other vertices are then incomplete).  Used to time or check
+    a sample of rows of a large surface.
+    """
     if classes is None:
         classes = classify_pairs(s)
+    if test_tris is not None:
+        test_tris = np.asarray(test_tris, dtype=np.int64)
+        keep = np.zeros(s.nt, dtype=bool)
+        keep[test_tris] = True
+        classes = {'identical': classes['identical'][keep[classes['identical']]],
+                   **{k: classes[k][keep[classes[k][:, 0]]] for k in ('edge', 'vertex', 'near')}}
     n, nt = s.n, s.nt
     V = np.zeros((n, n))
     K = np.zeros((n, n))
@@ -178,17 +189,19 @@ def assemble(s: Surface, kappa: float, n_ss: int = 5, chunk: int = 64, classes=N
     Y = s.qp.reshape(-1, 3)
     NY = np.repeat(s.normal, 6, axis=0)
     WY = s.qw.reshape(-1)
-    for t0 in range(0, nt, chunk):
-        t1 = min(nt, t0 + chunk)
-        X = s.qp[t0:t1].reshape(-1, 3)
-        WX = s.qw[t0:t1].reshape(-1)
-        mask = np.asarray(special[t0:t1].todense()) == 0                     # (c, nt) regular pairs
+    rows = np.arange(nt) if test_tris is None else test_tris
+    for c0 in range(0, rows.size, chunk):
+        tc = rows[c0:c0 + chunk]
+        q6 = (6 * tc[:, None] + np.arange(6)[None, :]).reshape(-1)
+        X = s.qp[tc].reshape(-1, 3)
+        WX = s.qw[tc].reshape(-1)
+        mask = np.asarray(special[tc].todense()) == 0                        # (c, nt) regular pairs
         m6 = np.repeat(np.repeat(mask, 6, axis=0), 6, axis=1)
         with np.errstate(divide='ignore', invalid='ignore'):
             g, dl = kernels(X[:, None, :], Y[None, :, :], NY[None, :, :], kappa)
         g = np.where(m6, g, 0.0) * WX[:, None] * WY[None, :]
         dl = np.where(m6, dl, 0.0) * WX[:, None] * WY[None, :]
-        Qc = s.Q[6 * t0:6 * t1]
+        Qc = s.Q[q6]
         V += (Qc.T @ (s.Q.T @ g.T).T)
         K += (Qc.T @ (s.Q.T @ dl.T).T)
     # --- special pairs
