@@ -60,13 +60,19 @@ enum {
 enum { PBFB_FP64 = 0, PBFB_MIXED = 1 };
 enum { PBFB_LINEAR = 0, PBFB_T3 = 1, PBFB_HS = 2 };
 enum { PBFB_GAMMA_M = 0, PBFB_GAMMA_S = 1 };
+enum { PBFB_PRECOND_JACOBI = 0, PBFB_PRECOND_BLOCK = 1 };
 
 typedef struct pbfb_mesh pbfb_mesh;
 
 /* Newton options; the defaults (pbfb_default_opts) are the paper's best
  * Newton configuration (Appendix B: L_e = 0.35, Tol_omega = 0.1,
  * Tol_GR0 = 1e-3, Tol_GR = 1e-6, Tol_NL = 1e-3; omega_0 = 2 for the T3
- * iteration and 1 afterwards, Sec. 3.3). */
+ * iteration and 1 afterwards, Sec. 3.3), with the block preconditioner
+ * (30 inner iterations; the paper does not state its preconditioner).
+ * In the PBFB_MIXED precision the GMRES operator (and the omega-search
+ * direction p = -Acal(0) Delta, whose f_d root is needed only to Tol_omega)
+ * evaluates the far field in float32, while the Newton residual
+ * d = b - Acal(0) Phi - N(Phi) uses the float64 far field. */
 typedef struct pbfb_newton_opts {
   int precision;        /* PBFB_FP64, or PBFB_MIXED: BEM far field in float32 */
   double tol_nl;        /* stop when e_k = omega ||Delta||_2 < tol_nl */
@@ -83,6 +89,11 @@ typedef struct pbfb_newton_opts {
   int max_omega_iters;
   int first_scheme;     /* PBFB_T3 (paper) or PBFB_HS */
   int omega_search;     /* 1: automatic omega; 0: constant omega0_first / omega0_rest */
+  int precond;          /* PBFB_PRECOND_JACOBI: diagonal of the coupled operator;
+                           PBFB_PRECOND_BLOCK: flexible GMRES whose preconditioner runs
+                           inner_iters Jacobi-PCG iterations on the FEM block A + J and
+                           the diagonal on the surface rows */
+  int inner_iters;      /* PCG iterations per block-preconditioner application (1..500) */
 } pbfb_newton_opts;
 
 #define PBFB_MAX_TRACE 64
@@ -184,11 +195,13 @@ int pbfb_bem_apply(pbfb_mesh* mesh, int which, int op, const double* x_dev, doub
  * (nnz) copied to host buffers (val = A + J and the coupling masses). */
 int pbfb_fem_rows(const pbfb_mesh* mesh, int32_t* rowptr, int32_t* col, double* val);
 
-/* Step a5: GMRES (restarted, x0 = 0, right Jacobi preconditioner, CGS2) on
+/* Step a5: GMRES (restarted, x0 = 0, right preconditioned, CGS2) on
  * Acal(J) x = b; stops when ||b - Acal x|| <= tol ||b||.  b, x: device (n).
- * iters and relres: host outputs (may be NULL). */
+ * precond: PBFB_PRECOND_JACOBI or PBFB_PRECOND_BLOCK (flexible GMRES with
+ * inner_iters PCG iterations on the FEM block).  iters and relres: host
+ * outputs (may be NULL). */
 int pbfb_gmres(pbfb_mesh* mesh, const double* b_dev, double* x_dev, double tol, int restart,
-               int maxit, int* iters, double* relres);
+               int maxit, int precond, int inner_iters, int* iters, double* relres);
 
 /* Step a7, batched over n_omega relaxation factors (host array omegas):
  * with w = u + omega du (device, n_v each), c = b - Acal(0) Phi and
@@ -209,9 +222,11 @@ int pbfb_energy(pbfb_mesh* mesh, const double* xL_dev, const double* xNL_dev, do
  * launch counters.  enable != 0 turns event timing on (it adds a little host
  * overhead per launch).  stats (host, 16 doubles):
  *   [0] launches of all kernels since the last reset,
- *   [1] BEM far-field (N-body) launches, [2] their total ms, [3] their pair
- *       interactions, [4] FEM SpMV launches, [5] their ms,
- *   [6] element (assembly + omega) launches, [7] their ms.
+ *   [1] float32 BEM far-field (N-body) launches, [2] their total ms, [3] their
+ *       pair interactions, [4] FEM SpMV launches, [5] their ms,
+ *   [6] element (assembly + omega) launches, [7] their ms,
+ *   [8] float32 far-field flops (18 per Laplace pair, 24 per Yukawa pair),
+ *   [9] float64 far-field launches, [10] their ms, [11] their pairs.
  * reset != 0 zeroes the counters after reading. */
 int pbfb_profile(pbfb_mesh* mesh, int enable, int reset, double* stats);
 

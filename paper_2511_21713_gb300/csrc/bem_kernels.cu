@@ -636,7 +636,8 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
                                                         f64 ? 1 : 0, s->spos.p, s->sdl.p, s->s64.p);
   PB_LAUNCHED(m);
   cudaEvent_t ev;
-  timer_begin(m, m->t_nbody, &ev);
+  KernelClassTimer& tm = f64 ? m->t_nbody64 : m->t_nbody;
+  timer_begin(m, tm, &ev);
   int nsplit;
   if (f64) {
     constexpr int NT = 128;
@@ -676,7 +677,8 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
     }
   }
   PB_LAUNCHED(m);
-  timer_end(m, m->t_nbody, ev, (double)nq * (double)nq);
+  timer_end(m, tm, ev, (double)nq * (double)nq);
+  if (!f64) m->nbody_flops += (yuk ? 24.0 : 18.0) * (double)nq * (double)nq;
   k_test_reduce<<<blocks_for(s->nv, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, s->val.p, nsplit,
                                                                nq, s->qw.p, 1.0, accumulate ? 1 : 0, y);
   PB_LAUNCHED(m);

@@ -517,6 +517,29 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
     kind[sl] = 2;
     ref[sl] = cslot(ss, e.first, e.second);
   }
+  {
+    // Robin term of the block preconditioner: u-u slots of Gamma_s vertex pairs sharing a triangle
+    std::vector<int> rs, rr;
+    for (auto& e : mps) {
+      rs.push_back(slot(ss.vmap_h[e.first], ss.vmap_h[e.second]));
+      rr.push_back(cslot(ss, e.first, e.second));
+    }
+    m->nrobin = (int)rs.size();
+    if ((st = m->robin_slot.upload(rs.data(), rs.size(), stream))) return fail(st);
+    if ((st = m->robin_ref.upload(rr.data(), rr.size(), stream))) return fail(st);
+    double area = 0.0;
+    for (int t = 0; t < ss.nt; ++t) {
+      const int* T = &ss.tri_h[3 * t];
+      double a[3], b[3];
+      for (int d = 0; d < 3; ++d) {
+        a[d] = xyz_h[3 * (size_t)ss.vmap_h[T[1]] + d] - xyz_h[3 * (size_t)ss.vmap_h[T[0]] + d];
+        b[d] = xyz_h[3 * (size_t)ss.vmap_h[T[2]] + d] - xyz_h[3 * (size_t)ss.vmap_h[T[0]] + d];
+      }
+      double c0 = a[1] * b[2] - a[2] * b[1], c1 = a[2] * b[0] - a[0] * b[2], c2 = a[0] * b[1] - a[1] * b[0];
+      area += 0.5 * std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+    }
+    m->gs_radius = std::sqrt(area / (4.0 * M_PI));
+  }
   for (int si = 0; si < 2; ++si) {
     const Surface& s = si == 0 ? sm : ss;
     for (int i = 0; i < s.nv; ++i)

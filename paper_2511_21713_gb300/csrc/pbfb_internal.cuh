@@ -156,19 +156,28 @@ struct Mesh {
   DBuf<double> wloc;        // omega batch: nomega * 12 * nt
   DBuf<double> red;         // block partial sums
   DBuf<double> scal;        // device scalars: [0,64) omegas, [64, 64+7*64+3) omega dots,
-                            // [1000] ion integral, [4000] dot result
+                            // [1000] ion integral, [4000] dot result, [5000, 5502) PCG scalars
   DBuf<double> red2;        // pair-local mass entries during correction builds
   double* pinned = nullptr; // host pinned scratch (4096 doubles)
   // GMRES workspace
   int gm_restart = 0;
   DBuf<double> gV, gw, gz, gr, gdiag, gh, gpart, gtmp;
+  DBuf<double> gZ;          // flexible GMRES: preconditioned basis (restart x n)
+  DBuf<double> gpcg;        // inner PCG vectors (5 x n)
+  DBuf<double> gones;       // n ones
+  // block preconditioner: FEM block + Robin term on Gamma_s, and its Jacobi diagonal
+  int nrobin = 0;
+  DBuf<int> robin_slot, robin_ref;  // FEM-row slot (u-u, both on Gamma_s) <- Gamma_s mass slot
+  DBuf<double> pval, pdinv;
+  double gs_radius = 1.0;           // sqrt(|Gamma_s| / 4 pi)
   // Newton workspace
   DBuf<double> xL, xNL, phi, cvec, dvec, du, pvec, tmp, Nvec, bvec, xout, urb;
   std::vector<double> qz_h;  // charges (host copy)
   // statistics
   double launches = 0;
   bool timing = false;
-  KernelClassTimer t_nbody, t_spmv, t_elem;
+  KernelClassTimer t_nbody, t_nbody64, t_spmv, t_elem;
+  double nbody_flops = 0.0;  // float32 far-field flops issued (18 per Laplace pair, 24 per Yukawa pair)
 };
 
 // ---- quadrature constants (device) and their host initialisation

@@ -165,6 +165,111 @@ __global__ void k_jacobi(int nv, int nm, int ns, const int* __restrict__ ptr, co
   dinv[r] = 1.0 / d;
 }
 
+// ---- Jacobi-PCG on the FEM block (rows < nv of the sparse part; the search direction
+// is kept zero on the surface unknowns so the coupling columns contribute nothing).
+constexpr int PCG_T = 256;
+
+__device__ __forceinline__ void block_sum_store(double v, double* out) {
+  __shared__ double sh[PCG_T / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < PCG_T / 32; ++w) s += sh[w];
+    *out = s;
+  }
+}
+
+// x = 0, r = b, z = dinv r, p = z, partial r.z
+__global__ void __launch_bounds__(PCG_T) k_pcg_init(int nv, const double* __restrict__ b,
+                                                     const double* __restrict__ dinv, double* __restrict__ x,
+                                                     double* __restrict__ r, double* __restrict__ z,
+                                                     double* __restrict__ p, double* __restrict__ part) {
+  double acc = 0.0;
+  for (int i = blockIdx.x * PCG_T + threadIdx.x; i < nv; i += gridDim.x * PCG_T) {
+    double bi = b[i], zi = dinv[i] * bi;
+    x[i] = 0.0;
+    r[i] = bi;
+    z[i] = zi;
+    p[i] = zi;
+    acc += bi * zi;
+  }
+  block_sum_store(acc, part + blockIdx.x);
+}
+
+// q = (A + J) p on the FEM rows (8 lanes per row), partial p.q
+__global__ void __launch_bounds__(PCG_T) k_pcg_spmv(int nv, const int* __restrict__ ptr,
+                                                     const int* __restrict__ col, const double* __restrict__ val,
+                                                     const double* __restrict__ p, double* __restrict__ q,
+                                                     double* __restrict__ part) {
+  const int lane = threadIdx.x & 7;
+  double acc = 0.0;
+  for (int row = (blockIdx.x * PCG_T + threadIdx.x) >> 3; row < nv; row += (gridDim.x * PCG_T) >> 3) {
+    double s = 0.0;
+    for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) s += val[k] * p[col[k]];
+    s += __shfl_down_sync(0xffffffffu, s, 4, 8);
+    s += __shfl_down_sync(0xffffffffu, s, 2, 8);
+    s += __shfl_down_sync(0xffffffffu, s, 1, 8);
+    if (lane == 0) {
+      q[row] = s;
+      acc += p[row] * s;
+    }
+  }
+  block_sum_store(acc, part + blockIdx.x);
+}
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; z = dinv r; partial r.z
+__global__ void __launch_bounds__(PCG_T) k_pcg_update(int nv, const double* __restrict__ rz,
+                                                       const double* __restrict__ pq, double* __restrict__ x,
+                                                       double* __restrict__ r, const double* __restrict__ p,
+                                                       const double* __restrict__ q, const double* __restrict__ dinv,
+                                                       double* __restrict__ z, double* __restrict__ part) {
+  const double alpha = (*pq != 0.0) ? (*rz / *pq) : 0.0;
+  double acc = 0.0;
+  for (int i = blockIdx.x * PCG_T + threadIdx.x; i < nv; i += gridDim.x * PCG_T) {
+    x[i] += alpha * p[i];
+    double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    double zi = dinv[i] * ri;
+    z[i] = zi;
+    acc += ri * zi;
+  }
+  block_sum_store(acc, part + blockIdx.x);
+}
+
+// beta = rz_new / rz_old; p = z + beta p
+__global__ void k_pcg_direction(int nv, const double* __restrict__ rz_old, const double* __restrict__ rz_new,
+                                const double* __restrict__ z, double* __restrict__ p) {
+  const double beta = (*rz_old != 0.0) ? (*rz_new / *rz_old) : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) p[i] = z[i] + beta * p[i];
+}
+
+// preconditioner FEM block: pval += c M_s on the Gamma_s u-u slots
+__global__ void k_add_robin(int nr, const int* __restrict__ slot, const int* __restrict__ ref,
+                            const double* __restrict__ mass, double c, double* __restrict__ pval) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nr) pval[slot[k]] += c * mass[ref[k]];
+}
+
+// Jacobi diagonal of the preconditioner's FEM block
+__global__ void k_diag_inv(int nv, const int* __restrict__ ptr, const int* __restrict__ col,
+                           const double* __restrict__ val, double* __restrict__ dinv) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nv) return;
+  double d = 0.0;
+  for (int k = ptr[r]; k < ptr[r + 1]; ++k)
+    if (col[k] == r) d = val[k];
+  dinv[r] = 1.0 / d;
+}
+
+// surface rows of the block preconditioner: z = dinv v
+__global__ void k_scale_rows(int r0, int r1, const double* __restrict__ v, const double* __restrict__ dinv,
+                             double* __restrict__ z) {
+  int i = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < r1) z[i] = dinv[i] * v[i];
+}
+
 __global__ void k_set_rhs(int nm, int col0, double scale, const double* __restrict__ coul, double* __restrict__ b) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nm) b[col0 + i] = scale * coul[i];
@@ -278,16 +383,19 @@ static int clear_jacobian(Mesh* m) {
   return PBFB_OK;
 }
 
-// y = Acal(J) x: sparse part, then the far field of both surfaces into their rows
-static int apply(Mesh* m, const double* x, double* y) {
+// y = Acal(J) x: sparse part, then the far field of both surfaces into their rows, with the
+// far field in the given precision
+static int apply_prec(Mesh* m, const double* x, double* y, int precision) {
   PB_TRY(launch_spmv(m, x, y));
   Surface* sm = &m->sm;
   Surface* ss = &m->ss;
   // Gamma_m rows: (M/2 + K_L) u - V_L lam_m; Gamma_s rows: (M/2 - K_Y) u + V_Y lam_s
-  PB_TRY(launch_bem_far(m, sm, x, x + sm->col0, -1.0, 1.0, 0.0, m->precision, y + sm->col0, true));
-  PB_TRY(launch_bem_far(m, ss, x, x + ss->col0, 1.0, -1.0, m->kappa, m->precision, y + ss->col0, true));
+  PB_TRY(launch_bem_far(m, sm, x, x + sm->col0, -1.0, 1.0, 0.0, precision, y + sm->col0, true));
+  PB_TRY(launch_bem_far(m, ss, x, x + ss->col0, 1.0, -1.0, m->kappa, precision, y + ss->col0, true));
   return PBFB_OK;
 }
+
+static int apply(Mesh* m, const double* x, double* y) { return apply_prec(m, x, y, m->precision); }
 
 int ensure(DBuf<double>& b, size_t n) {
   if (b.n >= n) return PBFB_OK;
@@ -303,12 +411,76 @@ static int jacobi(Mesh* m, double* dinv) {
 
 // ------------------------------------------------------------------ GMRES
 
-static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, int maxit, int* iters_out,
-                 double* rel_out) {
+// Block preconditioner z = P(v): inner_iters Jacobi-PCG iterations on (A + J) z_u = v_u from
+// z_u = 0, and z = diag^-1 v on the surface rows.  Deterministic (fixed reductions, fixed count).
+// FEM block of the preconditioner: A + J plus the Robin term eps_s (kappa + 1/R) M_s on Gamma_s
+// (the constant mode of the exterior Dirichlet-to-Neumann map of a sphere of Gamma_s's area),
+// which keeps it positive definite when J = 0.
+static int prepare_block_precond(Mesh* m) {
+  PB_TRY(ensure(m->pval, m->fem_nnz));
+  PB_TRY(ensure(m->pdinv, m->nv));
+  PB_CUDA(cudaMemcpyAsync(m->pval.p, m->s_val.p, m->fem_nnz * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  const double c = m->eps_s * (m->kappa + 1.0 / m->gs_radius);
+  if (m->nrobin) {
+    k_add_robin<<<blocks_for(m->nrobin, 256), 256, 0, m->stream>>>(m->nrobin, m->robin_slot.p, m->robin_ref.p,
+                                                                    m->ss.mass.p, c, m->pval.p);
+    PB_LAUNCHED(m);
+  }
+  k_diag_inv<<<blocks_for(m->nv, 256), 256, 0, m->stream>>>(m->nv, m->s_ptr.p, m->s_col.p, m->pval.p, m->pdinv.p);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
+  const int nv = m->nv, n = m->n;
+  const int nb = std::min(152, std::max(1, blocks_for(nv, PCG_T)));
+  double* pb = m->gpcg.p;            // pcg vectors (each n long; surface part of p stays 0)
+  double* pr = pb + (size_t)n;
+  double* pz = pb + 2 * (size_t)n;
+  double* pp = pb + 3 * (size_t)n;
+  double* pq = pb + 4 * (size_t)n;
+  double* part = m->gpart.p;
+  double* sc = m->scal.p + 5000;     // [0] pq, [1 + k] rz_k
+  const double* dinv = m->pdinv.p;
+  k_pcg_init<<<nb, PCG_T, 0, m->stream>>>(nv, v, dinv, z, pr, pz, pp, part);
+  PB_LAUNCHED(m);
+  k_sum_to<<<1, 32, 0, m->stream>>>(part, nb, sc + 1);
+  PB_LAUNCHED(m);
+  for (int k = 0; k < inner_iters; ++k) {
+    k_pcg_spmv<<<nb, PCG_T, 0, m->stream>>>(nv, m->s_ptr.p, m->s_col.p, m->pval.p, pp, pq, part);
+    PB_LAUNCHED(m);
+    k_sum_to<<<1, 32, 0, m->stream>>>(part, nb, sc);
+    PB_LAUNCHED(m);
+    k_pcg_update<<<nb, PCG_T, 0, m->stream>>>(nv, sc + 1 + k, sc, z, pr, pp, pq, dinv, pz, part);
+    PB_LAUNCHED(m);
+    k_sum_to<<<1, 32, 0, m->stream>>>(part, nb, sc + 2 + k);
+    PB_LAUNCHED(m);
+    k_pcg_direction<<<nb, PCG_T, 0, m->stream>>>(nv, sc + 1 + k, sc + 2 + k, pz, pp);
+    PB_LAUNCHED(m);
+  }
+  k_scale_rows<<<blocks_for(n - nv, 256), 256, 0, m->stream>>>(nv, n, v, m->gdiag.p, z);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, int maxit, int precond,
+                 int inner_iters, int* iters_out, double* rel_out) {
   const int n = m->n;
   if (restart < 1 || restart > 400) {
     set_error("restart must be in [1, 400]");
     return PBFB_ERR_INVALID;
+  }
+  if ((precond != PBFB_PRECOND_JACOBI && precond != PBFB_PRECOND_BLOCK) || inner_iters < 1 || inner_iters > 500) {
+    set_error("invalid preconditioner settings");
+    return PBFB_ERR_INVALID;
+  }
+  const bool flexible = precond == PBFB_PRECOND_BLOCK;
+  if (flexible) {
+    PB_TRY(ensure(m->gZ, (size_t)restart * n));
+    if (m->gpcg.n < 5 * (size_t)n) {
+      PB_TRY(m->gpcg.alloc(5 * (size_t)n));
+      PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 5 * (size_t)n * sizeof(double), m->stream));
+    }
   }
   PB_TRY(ensure(m->gV, (size_t)(restart + 1) * n));
   PB_TRY(ensure(m->gw, n));
@@ -319,6 +491,13 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
   const int nbr = std::min(152, std::max(1, blocks_for(n, MD_T)));
   PB_TRY(ensure(m->gpart, (size_t)(restart + 2) * nbr + 8));
   PB_TRY(jacobi(m, m->gdiag.p));
+  if (flexible) PB_TRY(prepare_block_precond(m));
+  if (flexible && m->gones.n < (size_t)n) {
+    PB_TRY(m->gones.alloc(n));
+    std::vector<double> ones(n, 1.0);
+    PB_CUDA(cudaMemcpyAsync(m->gones.p, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    PB_CUDA(cudaStreamSynchronize(m->stream));
+  }
   double* V = m->gV.p;
   double* w = m->gw.p;
   double* z = m->gz.p;
@@ -355,9 +534,15 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
     int k = 0;
     for (k = 0; k < restart; ++k) {
       double* vk = V + (size_t)k * n;
-      k_mul<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, vk, m->gdiag.p, z);
-      PB_LAUNCHED(m);
-      PB_TRY(apply(m, z, w));
+      if (flexible) {
+        double* zk = m->gZ.p + (size_t)k * n;
+        PB_TRY(block_precond(m, vk, zk, inner_iters));
+        PB_TRY(apply(m, zk, w));
+      } else {
+        k_mul<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, vk, m->gdiag.p, z);
+        PB_LAUNCHED(m);
+        PB_TRY(apply(m, z, w));
+      }
       // classical Gram-Schmidt, twice
       int kk = k + 1;
       dim3 gd(nbr, (kk + 7) / 8);
@@ -414,7 +599,11 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
     }
     std::memcpy(m->pinned, y.data(), mk * sizeof(double));
     PB_CUDA(cudaMemcpyAsync(ydev, m->pinned, mk * sizeof(double), cudaMemcpyHostToDevice, m->stream));
-    k_update_solution<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, mk, V, ydev, m->gdiag.p, x);
+    if (flexible) {
+      k_update_solution<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, mk, m->gZ.p, ydev, m->gones.p, x);
+    } else {
+      k_update_solution<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, mk, V, ydev, m->gdiag.p, x);
+    }
     PB_LAUNCHED(m);
     // true residual
     PB_TRY(apply(m, x, w));
@@ -617,7 +806,7 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   PB_TRY(assemble(m, PBFB_LINEAR, m->phi.p, nullptr));
   int its = 0;
   double rel = 0;
-  int st = gmres(m, bvec, m->xL.p, tol, o.restart, o.max_gmres, &its, &rel);
+  int st = gmres(m, bvec, m->xL.p, tol, o.restart, o.max_gmres, o.precond, o.inner_iters, &its, &rel);
   R.linear_gmres_iters = its;
   if (st) {
     R.status = st;
@@ -632,9 +821,9 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   for (k = 0; k < o.max_newton; ++k) {
     const int scheme = k == 0 ? o.first_scheme : PBFB_HS;
     PB_TRY(launch_axpby(m, n, 1.0, m->xL.p, 1.0, m->xNL.p, m->phi.p));
-    // c = b - Acal(0) Phi
+    // c = b - Acal(0) Phi (far field in float64 in both precisions: the nonlinear residual)
     PB_TRY(clear_jacobian(m));
-    PB_TRY(apply(m, m->phi.p, m->cvec.p));
+    PB_TRY(apply_prec(m, m->phi.p, m->cvec.p, PBFB_FP64));
     PB_TRY(launch_axpby(m, n, 1.0, bvec, -1.0, m->cvec.p, m->cvec.p));
     // J(u), N(u); d = c - [N; 0; 0]
     PB_TRY(assemble(m, scheme, m->phi.p, m->Nvec.p));
@@ -649,7 +838,7 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
       if (res) *res = R;
       return R.status;
     }
-    st = gmres(m, m->dvec.p, m->du.p, tol, o.restart, o.max_gmres, &its, &rel);
+    st = gmres(m, m->dvec.p, m->du.p, tol, o.restart, o.max_gmres, o.precond, o.inner_iters, &its, &rel);
     if (k < PBFB_MAX_TRACE) R.gmres_iters[k] = its;
     if (st) {
       R.status = st;
@@ -664,7 +853,7 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
     } else if (k > 0 && e_prev >= 0.0 && e_prev < o.L_e && om_last > 0.0) {
       om = om_last;
     } else {
-      // p = -Acal(0) Delta
+      // p = -Acal(0) Delta with the GMRES operator (the root of f_d is needed only to Tol_omega)
       PB_TRY(clear_jacobian(m));
       PB_TRY(apply(m, m->du.p, m->pvec.p));
       PB_TRY(launch_axpby(m, n, -1.0, m->pvec.p, 0.0, nullptr, m->pvec.p));
@@ -765,6 +954,8 @@ void pbfb_default_opts(pbfb_newton_opts* o) {
   o->max_omega_iters = 30;
   o->first_scheme = PBFB_T3;
   o->omega_search = 1;
+  o->precond = PBFB_PRECOND_BLOCK;
+  o->inner_iters = 30;
 }
 
 const char* pbfb_last_error(void) { return pbfb::last_error(); }
@@ -875,6 +1066,7 @@ int pbfb_mesh_destroy(pbfb_mesh* h) {
     cudaSetDevice(h->m->dev);
     cudaStreamSynchronize(h->m->stream);
     pbfb::timer_flush(h->m->t_nbody);
+    pbfb::timer_flush(h->m->t_nbody64);
     pbfb::timer_flush(h->m->t_spmv);
     pbfb::timer_flush(h->m->t_elem);
     if (h->m->pinned) cudaFreeHost(h->m->pinned);
@@ -965,8 +1157,8 @@ int pbfb_fem_rows(const pbfb_mesh* h, int32_t* rowptr, int32_t* col, double* val
   return PBFB_OK;
 }
 
-int pbfb_gmres(pbfb_mesh* h, const double* b_dev, double* x_dev, double tol, int restart, int maxit, int* iters,
-               double* relres) {
+int pbfb_gmres(pbfb_mesh* h, const double* b_dev, double* x_dev, double tol, int restart, int maxit, int precond,
+               int inner_iters, int* iters, double* relres) {
   PB_HANDLE(h);
   PB_NEED_PARAMS;
   if (!b_dev || !x_dev || !(tol > 0) || maxit < 1) {
@@ -975,7 +1167,7 @@ int pbfb_gmres(pbfb_mesh* h, const double* b_dev, double* x_dev, double tol, int
   }
   int it = 0;
   double rel = 0;
-  int st = pbfb::gmres(m, b_dev, x_dev, tol, restart, maxit, &it, &rel);
+  int st = pbfb::gmres(m, b_dev, x_dev, tol, restart, maxit, precond, inner_iters, &it, &rel);
   if (iters) *iters = it;
   if (relres) *relres = rel;
   return st;
@@ -1007,6 +1199,7 @@ int pbfb_profile(pbfb_mesh* h, int enable, int reset, double* stats) {
   PB_HANDLE(h);
   cudaStreamSynchronize(m->stream);
   pbfb::timer_flush(m->t_nbody);
+  pbfb::timer_flush(m->t_nbody64);
   pbfb::timer_flush(m->t_spmv);
   pbfb::timer_flush(m->t_elem);
   if (stats) {
@@ -1018,11 +1211,16 @@ int pbfb_profile(pbfb_mesh* h, int enable, int reset, double* stats) {
     stats[5] = m->t_spmv.ms;
     stats[6] = m->t_elem.count;
     stats[7] = m->t_elem.ms;
-    for (int k = 8; k < 16; ++k) stats[k] = 0.0;
+    stats[8] = m->nbody_flops;
+    stats[9] = m->t_nbody64.count;
+    stats[10] = m->t_nbody64.ms;
+    stats[11] = m->t_nbody64.work;
+    for (int k = 12; k < 16; ++k) stats[k] = 0.0;
   }
   if (reset) {
     m->launches = 0;
-    for (auto* t : {&m->t_nbody, &m->t_spmv, &m->t_elem}) {
+    m->nbody_flops = 0.0;
+    for (auto* t : {&m->t_nbody, &m->t_nbody64, &m->t_spmv, &m->t_elem}) {
       t->ms = 0;
       t->count = 0;
       t->work = 0;

@@ -21,6 +21,7 @@ ERRORS = {1: "INVALID", 2: "CUDA", 3: "GMRES_NOCONV", 4: "NEWTON_NOCONV", 5: "OM
 FP64, MIXED = 0, 1
 LINEAR, T3, HS = 0, 1, 2
 GAMMA_M, GAMMA_S = 0, 1
+JACOBI, BLOCK = 0, 1
 MAX_TRACE = 64
 
 # every symbol include/pbfb.h declares
@@ -47,7 +48,8 @@ class NewtonOpts(ctypes.Structure):
                 ("omega_max", ctypes.c_double), ("max_newton", ctypes.c_int),
                 ("max_gmres", ctypes.c_int), ("restart", ctypes.c_int),
                 ("max_omega_iters", ctypes.c_int), ("first_scheme", ctypes.c_int),
-                ("omega_search", ctypes.c_int)]
+                ("omega_search", ctypes.c_int), ("precond", ctypes.c_int),
+                ("inner_iters", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -97,7 +99,7 @@ def load():
         "pbfb_apply": (I, [P, P, P]),
         "pbfb_bem_apply": (I, [P, I, I, P, P]),
         "pbfb_fem_rows": (I, [P, P, P, P]),
-        "pbfb_gmres": (I, [P, P, P, D, I, I, P, P]),
+        "pbfb_gmres": (I, [P, P, P, D, I, I, I, I, P, P]),
         "pbfb_omega_eval": (I, [P, I, P, P, P, P, P, I, P]),
         "pbfb_energy": (I, [P, P, P, P]),
         "pbfb_profile": (I, [P, I, I, P]),
@@ -214,11 +216,11 @@ class Mesh:
         _check(load().pbfb_fem_rows(self.h, _ptr(rp), _ptr(col), _ptr(val)))
         return rp, col, val
 
-    def gmres(self, b_dev, x_dev, tol, restart=200, maxit=1000):
+    def gmres(self, b_dev, x_dev, tol, restart=200, maxit=1000, precond=JACOBI, inner_iters=30):
         it = ctypes.c_int()
         rel = ctypes.c_double()
-        _check(load().pbfb_gmres(self.h, _ptr(b_dev), _ptr(x_dev), tol, restart, maxit,
-                                 ctypes.byref(it), ctypes.byref(rel)))
+        _check(load().pbfb_gmres(self.h, _ptr(b_dev), _ptr(x_dev), tol, restart, maxit, precond,
+                                 inner_iters, ctypes.byref(it), ctypes.byref(rel)))
         return it.value, rel.value
 
     def omega_eval(self, scheme, u_dev, du_dev, c_dev, p_dev, omegas):
@@ -237,7 +239,8 @@ class Mesh:
         st = np.zeros(16)
         _check(load().pbfb_profile(self.h, int(enable), int(reset), _ptr(st)))
         return dict(launches=st[0], nbody_launches=st[1], nbody_ms=st[2], nbody_pairs=st[3],
-                    spmv_launches=st[4], spmv_ms=st[5], elem_launches=st[6], elem_ms=st[7])
+                    spmv_launches=st[4], spmv_ms=st[5], elem_launches=st[6], elem_ms=st[7],
+                    nbody_flops=st[8], nbody64_launches=st[9], nbody64_ms=st[10], nbody64_pairs=st[11])
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
