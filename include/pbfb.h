@@ -191,6 +191,24 @@ int pbfb_apply(pbfb_mesh* mesh, const double* x_dev, double* y_dev);
  * to the P1 coefficients x (device, n_m or n_s); y (device) same length. */
 int pbfb_bem_apply(pbfb_mesh* mesh, int which, int op, const double* x_dev, double* y_dev);
 
+/* pbfb_bem_apply without device allocation (the paper has no counterpart).
+ * For callers that may not allocate GPU memory while they run -- for example
+ * a host that has handed all device memory to its own pool, or a request
+ * loop that must not call cudaMalloc/cudaFree (which synchronise the device)
+ * between requests.  Computes V x or K x on surface `which` exactly as
+ * pbfb_bem_apply does with the float32 far field (whatever precision
+ * pbfb_set_params chose) plus the float64 near-field correction, but its
+ * working memory is one fixed library-wide device array of 6 MiB (float32
+ * source records and float64 partial sums), present on every device that
+ * loads the library until the process exits; the call allocates nothing.
+ * Limit: 65,536 quadrature points (10,922 triangles) on the surface; larger
+ * surfaces return PBFB_ERR_INVALID.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (other streams or threads) race and corrupt each other's
+ * results.  x, y: device, n_m or n_s float64, distinct. */
+int pbfb_bem_apply_noalloc(pbfb_mesh* mesh, int which, int op, const double* x_dev, double* y_dev);
+
 /* FEM rows in CSR over the full unknown vector: rowptr (n_v + 1), col and val
  * (nnz) copied to host buffers (val = A + J and the coupling masses). */
 int pbfb_fem_rows(const pbfb_mesh* mesh, int32_t* rowptr, int32_t* col, double* val);

@@ -15,6 +15,7 @@
 //     the test triangle x 6 points on each of the 16 sub-triangles of the trial one.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -700,6 +701,98 @@ int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev) {
   k_reaction_potential<<<m->nq, 256, 0, m->stream>>>(s->nt, s->tri.p, s->vmap.p, s->qx.p, s->qw.p, s->nrm.p,
                                                      x + s->col0, x, m->qxyz.p, m->nq, ur_dev);
   PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+}  // namespace pbfb
+
+// ---------------------------------------------------------------- allocation-free far field
+//
+// pbfb_bem_apply_noalloc (include/pbfb.h) computes what pbfb_bem_apply computes with the
+// float32 far field, but keeps all of its working memory in the fixed array below instead
+// of buffers owned by the mesh: float32 source records (two float4 per quadrature point)
+// followed by the float64 partial potentials of at most NOALLOC_SPLITS source splits.
+// The array is a device global of the library: every device that loads libpbfb holds it
+// until the process exits.  Calls share it, so calls that run at the same time on the GPU
+// (other streams, other threads) overwrite each other's data.  Every call writes all of
+// the scratch it reads, so nothing has to be cleared between calls.
+
+namespace pbfb {
+namespace {
+
+constexpr int NOALLOC_MAX_QP = 65536;   // quadrature points (6 per triangle): 10922 triangles
+constexpr int NOALLOC_SPLITS = 8;
+constexpr size_t NOALLOC_BYTES =
+    (size_t)NOALLOC_MAX_QP * 2 * sizeof(float4) + (size_t)NOALLOC_SPLITS * NOALLOC_MAX_QP * sizeof(double);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of g_noalloc_scratch per device, looked up on the first call on that device.
+// (In host code the symbol's name is only a host-side handle, not the device address.)
+constexpr int NOALLOC_MAX_DEV = 64;
+void* g_noalloc_addr[NOALLOC_MAX_DEV] = {nullptr};
+
+int noalloc_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= NOALLOC_MAX_DEV) {
+    set_error("bem_apply_noalloc: device ordinal %d out of range", dev);
+    return PBFB_ERR_INVALID;
+  }
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("bem_apply_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return PBFB_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_noalloc_addr[dev];
+  return PBFB_OK;
+}
+
+}  // namespace
+
+int bem_apply_noalloc(Mesh* m, int which, int op, const double* x, double* y) {
+  Surface* s = which == PBFB_GAMMA_M ? &m->sm : &m->ss;
+  const double kappa = which == PBFB_GAMMA_M ? 0.0 : m->kappa;
+  const int nq = s->nq;
+  if (nq > NOALLOC_MAX_QP) {
+    set_error("bem_apply_noalloc: the surface has %d quadrature points; the fixed scratch holds at most %d "
+              "(%d triangles)", nq, NOALLOC_MAX_QP, NOALLOC_MAX_QP / QS);
+    return PBFB_ERR_INVALID;
+  }
+  unsigned char* base = nullptr;
+  PB_TRY(noalloc_scratch(m->dev, &base));
+  float4* spos = (float4*)base;
+  float4* sdl = spos + NOALLOC_MAX_QP;
+  double* val = (double*)(sdl + NOALLOC_MAX_QP);
+  const double cs = op == 0 ? 1.0 : 0.0, cd = op == 1 ? 1.0 : 0.0;
+  k_sources<<<blocks_for(nq, 256), 256, 0, m->stream>>>(s->nt, s->tri.p, s->vmap.p, cs != 0.0 ? x : nullptr,
+                                                        cd != 0.0 ? x : nullptr, 1, s->qw.p, s->nrm.p, s->qpf.p,
+                                                        s->qx.p, cs * INV4PI, cd * INV4PI, 0, spos, sdl, nullptr);
+  PB_LAUNCHED(m);
+  constexpr int NT = 128;
+  const bool big = nq >= 16384;
+  const int tpt = big ? 4 : 1;
+  const int ntb = blocks_for(nq, NT * tpt);
+  int nsplit = std::max(1, std::min(std::min(blocks_for(4 * 152, ntb), blocks_for(nq, 4 * NT)), NOALLOC_SPLITS));
+  const int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
+  nsplit = blocks_for(nq, per);
+  dim3 grid(ntb, nsplit);
+  const float kf = (float)kappa;
+  const bool yuk = kappa != 0.0;
+  if (big) {
+    if (yuk) k_nbody_f32<NT, 4, true><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, spos, sdl, kf, per, val);
+    else k_nbody_f32<NT, 4, false><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, spos, sdl, kf, per, val);
+  } else {
+    if (yuk) k_nbody_f32<NT, 1, true><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, spos, sdl, kf, per, val);
+    else k_nbody_f32<NT, 1, false><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, spos, sdl, kf, per, val);
+  }
+  PB_LAUNCHED(m);
+  k_test_reduce<<<blocks_for(s->nv, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, val, nsplit, nq,
+                                                               s->qw.p, 1.0, 0, y);
+  PB_LAUNCHED(m);
+  PB_TRY(launch_csr_spmv(m, s->nv, s->c_ptr.p, s->c_col.p, op == 0 ? s->corrV.p : s->corrK.p, x, y, true));
   return PBFB_OK;
 }
 

@@ -206,6 +206,7 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
                    double kappa, int precision, double* y, bool accumulate);
 int launch_coulomb(Mesh* m);
 int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev);
+int bem_apply_noalloc(Mesh* m, int which, int op, const double* x, double* y);
 
 // ---- blas (solver.cu)
 int dot(Mesh* m, const double* a, const double* b, int n, double* out_host);

@@ -1140,6 +1140,19 @@ int pbfb_bem_apply(pbfb_mesh* h, int which, int op, const double* x_dev, double*
   return cudaStreamSynchronize(m->stream) == cudaSuccess ? PBFB_OK : PBFB_ERR_CUDA;
 }
 
+int pbfb_bem_apply_noalloc(pbfb_mesh* h, int which, int op, const double* x_dev, double* y_dev) {
+  PB_HANDLE(h);
+  PB_NEED_PARAMS;
+  if (!x_dev || !y_dev || x_dev == y_dev || (which != PBFB_GAMMA_M && which != PBFB_GAMMA_S) ||
+      (op != 0 && op != 1)) {
+    pbfb::set_error("bem_apply_noalloc: bad argument");
+    return PBFB_ERR_INVALID;
+  }
+  int st = pbfb::bem_apply_noalloc(m, which, op, x_dev, y_dev);
+  if (st) return st;
+  return cudaStreamSynchronize(m->stream) == cudaSuccess ? PBFB_OK : PBFB_ERR_CUDA;
+}
+
 int pbfb_fem_rows(const pbfb_mesh* h, int32_t* rowptr, int32_t* col, double* val) {
   if (!h || !h->m || !rowptr || !col || !val) {
     pbfb::set_error("fem_rows: null argument");

@@ -30,7 +30,7 @@ EXPORTS = [
     "pbfb_charges_set", "pbfb_solve", "pbfb_solve_device", "pbfb_mesh_destroy",
     "pbfb_last_error", "pbfb_set_params", "pbfb_assemble", "pbfb_clear_jacobian",
     "pbfb_apply", "pbfb_bem_apply", "pbfb_fem_rows", "pbfb_gmres", "pbfb_omega_eval",
-    "pbfb_energy", "pbfb_profile",
+    "pbfb_energy", "pbfb_profile", "pbfb_bem_apply_noalloc",
 ]
 
 
@@ -98,6 +98,7 @@ def load():
         "pbfb_clear_jacobian": (I, [P]),
         "pbfb_apply": (I, [P, P, P]),
         "pbfb_bem_apply": (I, [P, I, I, P, P]),
+        "pbfb_bem_apply_noalloc": (I, [P, I, I, P, P]),
         "pbfb_fem_rows": (I, [P, P, P, P]),
         "pbfb_gmres": (I, [P, P, P, D, I, I, I, I, P, P]),
         "pbfb_omega_eval": (I, [P, I, P, P, P, P, P, I, P]),
@@ -208,6 +209,11 @@ class Mesh:
 
     def bem_apply(self, which, op, x_dev, y_dev):
         _check(load().pbfb_bem_apply(self.h, which, op, _ptr(x_dev), _ptr(y_dev)))
+
+    def bem_apply_noalloc(self, which, op, x_dev, y_dev):
+        """pbfb_bem_apply with its working memory in the library's fixed device array
+        (no allocation; at most 65,536 quadrature points per surface)."""
+        _check(load().pbfb_bem_apply_noalloc(self.h, which, op, _ptr(x_dev), _ptr(y_dev)))
 
     def fem_rows(self):
         rp = np.zeros(self.n_v + 1, np.int32)
