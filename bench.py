@@ -206,7 +206,9 @@ def run_pbfb(args):
                      "peak_basis": peak_note, "avg_launch_ms": avg_ms,
                      "pairs_per_launch": pairs_per_launch, "launches": launches,
                      "share_of_step": kms / total_ms if total_ms else None,
-                     "fp64_residual_farfield_share": prof["nbody64_ms"] / total_ms if total_ms else None},
+                     "residual_farfield_share": (prof["nbody64_ms"] + prof["nbodyff_ms"]) / total_ms if total_ms else None,
+                     "residual_farfield_ms_per_launch": ((prof["nbodyff_ms"] / prof["nbodyff_launches"])
+                                                         if prof["nbodyff_launches"] else None)},
         "clocks": clk,
         "solve": {"newton_iters": res["newton_iters"], "linear_gmres": res["linear_gmres"],
                   "gmres": res["gmres"], "omega": [round(w, 4) for w in res["omega"]],

@@ -57,7 +57,12 @@ enum {
   PBFB_ERR_STATE = 8           /* call out of order (e.g. solve before charges) */
 };
 
-enum { PBFB_FP64 = 0, PBFB_MIXED = 1 };
+/* Precisions.  PBFB_FP64: everything float64.  PBFB_MIXED: GMRES operator far
+ * field in float32, Newton-residual far field in float-float (pairs of float32
+ * values, about 48 significant bits, on the float32 pipes), all other steps
+ * float64.  PBFB_FLOAT2 (pbfb_set_params / step calls only): far field in
+ * float-float. */
+enum { PBFB_FP64 = 0, PBFB_MIXED = 1, PBFB_FLOAT2 = 2 };
 enum { PBFB_LINEAR = 0, PBFB_T3 = 1, PBFB_HS = 2 };
 enum { PBFB_GAMMA_M = 0, PBFB_GAMMA_S = 1 };
 enum { PBFB_PRECOND_JACOBI = 0, PBFB_PRECOND_BLOCK = 1 };
@@ -72,7 +77,9 @@ typedef struct pbfb_mesh pbfb_mesh;
  * In the PBFB_MIXED precision the GMRES operator (and the omega-search
  * direction p = -Acal(0) Delta, whose f_d root is needed only to Tol_omega)
  * evaluates the far field in float32, while the Newton residual
- * d = b - Acal(0) Phi - N(Phi) uses the float64 far field. */
+ * d = b - Acal(0) Phi - N(Phi) uses the float-float far field (float64-level
+ * accuracy at a fraction of GB300's float64 cost); PBFB_FP64 uses float64
+ * everywhere. */
 typedef struct pbfb_newton_opts {
   int precision;        /* PBFB_FP64, or PBFB_MIXED: BEM far field in float32 */
   double tol_nl;        /* stop when e_k = omega ||Delta||_2 < tol_nl */
@@ -244,7 +251,8 @@ int pbfb_energy(pbfb_mesh* mesh, const double* xL_dev, const double* xNL_dev, do
  *       pair interactions, [4] FEM SpMV launches, [5] their ms,
  *   [6] element (assembly + omega) launches, [7] their ms,
  *   [8] float32 far-field flops (18 per Laplace pair, 24 per Yukawa pair),
- *   [9] float64 far-field launches, [10] their ms, [11] their pairs.
+ *   [9] float64 far-field launches, [10] their ms, [11] their pairs,
+ *   [12] float-float far-field launches, [13] their ms, [14] their pairs.
  * reset != 0 zeroes the counters after reading. */
 int pbfb_profile(pbfb_mesh* mesh, int enable, int reset, double* stats);
 

@@ -479,6 +479,198 @@ __global__ void __launch_bounds__(NT) k_nbody_f64(int nq, const double* __restri
   if (i < nq) out[(int64_t)blockIdx.y * nq + i] = acc;
 }
 
+// ---------------------------------------------------------------- float-float far field
+//
+// The Newton residual needs a far field accurate to float64 level, but the float64 rate of
+// GB300 is 1/64 of its float32 rate.  These kernels evaluate the same pair sums in
+// float-float arithmetic: every quantity is an unevaluated pair hi + lo of float32 values
+// (about 48 significant bits), built from error-free transformations -- Knuth's TwoSum,
+// Dekker's FastTwoSum (|a| >= |b|) and the FMA TwoProduct -- as in Ogita, Rump & Oishi,
+// "Accurate sum and dot product" (SIAM J. Sci. Comput. 2005).  1/sqrt uses one Newton step
+// from the hardware estimate; exp(-x) for the Yukawa kernel uses two float-float tables of
+// exp(-k delta) (delta = 1/256) and a 5-term Taylor series for the remainder f < delta.
+// The _rn intrinsics keep the compiler from contracting the transformations into FMAs.
+
+constexpr int FF_TABLE_HI = 640;      // exp(-16 delta k1), k1 < 640: x up to 40
+constexpr float FF_XMAX = 39.99f;      // exp(-40) ~ 4e-18: larger arguments give 0
+
+__constant__ float2 c_ff_exp_lo[16];   // exp(-delta k0), k0 < 16
+
+struct ff { float h, l; };
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.h, b.h);
+  float lo = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+  return fast_two_sum(s.h, lo);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_sq(ff a) {
+  float p = __fmul_rn(a.h, a.h);
+  float e = __fmaf_rn(a.h, a.h, -p);
+  e = __fmaf_rn(__fadd_rn(a.h, a.h), a.l, e);
+  return fast_two_sum(p, e);
+}
+// difference of two float-float coordinates
+__device__ __forceinline__ ff ff_diff(float xh, float xl, float yh, float yl) {
+  ff s = two_sum(xh, -yh);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fsub_rn(xl, yl)));
+}
+// a.x + b.y + c.z for float-float vectors
+__device__ __forceinline__ ff ff_dot3(ff a0, ff a1, ff a2, ff b0, ff b1, ff b2) {
+  float p0 = __fmul_rn(a0.h, b0.h), p1 = __fmul_rn(a1.h, b1.h), p2 = __fmul_rn(a2.h, b2.h);
+  float e0 = __fmaf_rn(a0.l, b0.h, __fmaf_rn(a0.h, b0.l, __fmaf_rn(a0.h, b0.h, -p0)));
+  float e1 = __fmaf_rn(a1.l, b1.h, __fmaf_rn(a1.h, b1.l, __fmaf_rn(a1.h, b1.h, -p1)));
+  float e2 = __fmaf_rn(a2.l, b2.h, __fmaf_rn(a2.h, b2.l, __fmaf_rn(a2.h, b2.h, -p2)));
+  ff s1 = two_sum(p0, p1);
+  ff s2 = two_sum(s1.h, p2);
+  float lo = __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(e0, e1), e2));
+  return fast_two_sum(s2.h, lo);
+}
+// 1/sqrt(r) for r = rh + rl > 0: one Newton step y0 (1 - (r y0^2 - 1)/2) from the hardware estimate
+__device__ __forceinline__ ff ff_rsqrt(ff r) {
+  float y0 = rsqrtf(r.h);
+  float t = __fmul_rn(y0, y0);
+  float te = __fmaf_rn(y0, y0, -t);
+  float a = __fmul_rn(r.h, t);
+  float ae = __fmaf_rn(r.h, t, -a);
+  float z = __fadd_rn(__fsub_rn(a, 1.0f), __fmaf_rn(r.l, t, __fmaf_rn(r.h, te, ae)));
+  return fast_two_sum(y0, __fmul_rn(__fmul_rn(-0.5f, y0), z));
+}
+// exp(-x), 0 <= x (float-float); tab_hi in shared memory: exp(-16 k1 / 256)
+__device__ __forceinline__ ff ff_expm(ff x, const float2* __restrict__ tab_hi) {
+  if (x.h >= FF_XMAX) return {0.f, 0.f};
+  int k = __float2int_rd(__fmul_rn(x.h, 256.0f));
+  k = k < 0 ? 0 : k;
+  ff f = fast_two_sum(__fsub_rn(x.h, __fmul_rn((float)k, 0.00390625f)), x.l);   // 0 <= f < 1/256 (+rounding)
+  // exp(-f) = (1 - f) + f^2/2 + f^2 (-f/6 + f^2/24 - f^3/120)
+  ff f2 = ff_sq(f);
+  float p2 = __fmul_rn(f.h, __fmaf_rn(f.h, __fmaf_rn(f.h, -1.0f / 120.0f, 1.0f / 24.0f), -1.0f / 6.0f));
+  ff one_minus = two_sum(1.0f, -f.h);
+  one_minus = fast_two_sum(one_minus.h, __fsub_rn(one_minus.l, f.l));
+  ff tail = fast_two_sum(__fmul_rn(0.5f, f2.h), __fmaf_rn(f2.h, p2, __fmul_rn(0.5f, f2.l)));
+  ff ef = ff_add(one_minus, tail);
+  float2 a = tab_hi[k >> 4];
+  float2 b = c_ff_exp_lo[k & 15];
+  return ff_mul(ff_mul(ef, ff{a.x, a.y}), ff{b.x, b.y});
+}
+
+// Float-float sources: 4 float4 per point: (y hi, s hi), (y lo, s lo), (m hi, 0), (m lo, 0),
+// with y relative to the surface centre, s = cs w lam_h, m = cd w u_h n.
+__global__ void k_sources_ff(int nt, const int* __restrict__ tri, const int* __restrict__ vmap,
+                             const double* __restrict__ lam, const double* __restrict__ u, int u_local,
+                             const double* __restrict__ qw, const double* __restrict__ nrm,
+                             const double* __restrict__ qx, double cx, double cy, double cz, double cs, double cd,
+                             float4* __restrict__ src, float4* __restrict__ tgt) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int nq = QS * nt;
+  if (j >= nq) return;
+  int t = j / QS, q = j - t * QS;
+  double lh = 0.0, uh = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    int v = tri[3 * t + a];
+    double b = c_tri_b[q][a];
+    if (lam) lh += b * lam[v];
+    if (u) uh += b * u[u_local ? v : vmap[v]];
+  }
+  double w = qw[j];
+  double sv = cs * w * lh, mu = cd * w * uh;
+  double y[3] = {qx[j] - cx, qx[nq + j] - cy, qx[2 * nq + j] - cz};
+  double mm[3] = {mu * nrm[t], mu * nrm[nt + t], mu * nrm[2 * nt + t]};
+  float yh[3], yl[3], mh[3], ml[3];
+  for (int d = 0; d < 3; ++d) {
+    yh[d] = (float)y[d];
+    yl[d] = (float)(y[d] - (double)yh[d]);
+    mh[d] = (float)mm[d];
+    ml[d] = (float)(mm[d] - (double)mh[d]);
+  }
+  float sh = (float)sv, sl = (float)(sv - (double)sh);
+  src[4 * j + 0] = make_float4(yh[0], yh[1], yh[2], sh);
+  src[4 * j + 1] = make_float4(yl[0], yl[1], yl[2], sl);
+  src[4 * j + 2] = make_float4(mh[0], mh[1], mh[2], 0.f);
+  src[4 * j + 3] = make_float4(ml[0], ml[1], ml[2], 0.f);
+  tgt[2 * j + 0] = make_float4(yh[0], yh[1], yh[2], 0.f);
+  tgt[2 * j + 1] = make_float4(yl[0], yl[1], yl[2], 0.f);
+}
+
+// One pair in float-float: (s + nd (1 + kappa r) / r^2) exp(-kappa r) / r  (kappa = 0: Laplace)
+template <bool YUK>
+__device__ __forceinline__ ff ff_pair(const float4& ph, const float4& pl, const float4& mh, const float4& ml,
+                                      const float (&th)[3], const float (&tl)[3], ff kap,
+                                      const float2* __restrict__ tab) {
+  ff d0 = ff_diff(th[0], tl[0], ph.x, pl.x);
+  ff d1 = ff_diff(th[1], tl[1], ph.y, pl.y);
+  ff d2 = ff_diff(th[2], tl[2], ph.z, pl.z);
+  ff r2 = ff_dot3(d0, d1, d2, d0, d1, d2);
+  ff ri = ff_rsqrt(r2);
+  ff nd = ff_dot3(ff{mh.x, ml.x}, ff{mh.y, ml.y}, ff{mh.z, ml.z}, d0, d1, d2);
+  ff ri2 = ff_sq(ri);
+  if (YUK) {
+    ff r = ff_mul(r2, ri);
+    ff x = ff_mul(kap, r);
+    ff e = ff_expm(x, tab);
+    ff one_x = two_sum(1.0f, x.h);
+    one_x = fast_two_sum(one_x.h, __fadd_rn(one_x.l, x.l));
+    ff t = ff_add(ff{ph.w, pl.w}, ff_mul(ff_mul(nd, one_x), ri2));
+    return ff_mul(t, ff_mul(e, ri));
+  }
+  ff t = ff_add(ff{ph.w, pl.w}, ff_mul(nd, ri2));
+  return ff_mul(t, ri);
+}
+
+// Float-float N-body: same tiling as the float32 kernel (one target per thread); each tile's
+// float-float partial sum is added to a float64 accumulator.
+template <int NT, bool YUK>
+__global__ void __launch_bounds__(NT) k_nbody_ff(int nq, const float4* __restrict__ tgt,
+                                                 const float4* __restrict__ src, float kh, float kl,
+                                                 const float2* __restrict__ tab_hi, int per_split,
+                                                 double* __restrict__ out) {
+  __shared__ float4 sh[4][NT];
+  __shared__ float2 tab[YUK ? FF_TABLE_HI : 1];
+  if (YUK)
+    for (int k = threadIdx.x; k < FF_TABLE_HI; k += NT) tab[k] = tab_hi[k];
+  const int i = blockIdx.x * NT + threadIdx.x;
+  const int ii = i < nq ? i : 0;
+  const float4 a = tgt[2 * ii], b = tgt[2 * ii + 1];
+  const float th[3] = {a.x, a.y, a.z}, tl[3] = {b.x, b.y, b.z};
+  const ff kap{kh, kl};
+  const int sb = blockIdx.y * per_split;
+  const int se = min(nq, sb + per_split);
+  double acc64 = 0.0;
+  for (int s0 = sb; s0 < se; s0 += NT) {
+    int j = s0 + threadIdx.x;
+    if (j < se) {
+      for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] = src[4 * j + c];
+    }
+    __syncthreads();
+    const int cnt = min(NT, se - s0);
+    ff acc{0.f, 0.f};
+    for (int jj = 0; jj < cnt; ++jj) {
+      if (s0 + jj == i) continue;
+      ff v = ff_pair<YUK>(sh[0][jj], sh[1][jj], sh[2][jj], sh[3][jj], th, tl, kap, tab);
+      acc = ff_add(acc, v);
+    }
+    acc64 += (double)acc.h + (double)acc.l;
+    __syncthreads();
+  }
+  if (i < nq) out[(int64_t)blockIdx.y * nq + i] = acc64;
+}
+
 // y[row0 + i] (+)= sum over incident (tau, a) of sum_q psi_a(x_q) w_q sum_split val[split][6 tau + q]
 __global__ void k_test_reduce(int nv, const int* __restrict__ ptr, const int* __restrict__ idx,
                               const double* __restrict__ val, int nsplit, int nq, const double* __restrict__ qw,
@@ -590,7 +782,28 @@ int init_quadrature() {
     }
   PB_CUDA(cudaMemcpyToSymbol(c_sub_b, sb, sizeof(sb)));
   PB_CUDA(cudaMemcpyToSymbol(c_sub_w, sw, sizeof(sw)));
+  // float-float exp tables: exp(-k0 / 256), k0 < 16 (constant memory)
+  float2 lo[16];
+  for (int k = 0; k < 16; ++k) {
+    double v = std::exp(-k / 256.0);
+    float h = (float)v;
+    lo[k] = make_float2(h, (float)(v - (double)h));
+  }
+  PB_CUDA(cudaMemcpyToSymbol(c_ff_exp_lo, lo, sizeof(lo)));
   done = true;
+  return PBFB_OK;
+}
+
+// exp(-16 k1 / 256), k1 < FF_TABLE_HI, as float-float pairs (host-computed in float64)
+int ff_exp_table(Mesh* m) {
+  if (m->ff_tab.n) return PBFB_OK;
+  std::vector<float2> t(FF_TABLE_HI);
+  for (int k = 0; k < FF_TABLE_HI; ++k) {
+    double v = std::exp(-16.0 * k / 256.0);
+    float h = (float)v;
+    t[k] = make_float2(h, (float)(v - (double)h));
+  }
+  PB_TRY(m->ff_tab.upload(t.data(), t.size(), m->stream));
   return PBFB_OK;
 }
 
@@ -632,6 +845,7 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
   const double* uvec = (cd != 0.0) ? x : nullptr;
   const double* lvec = (cs != 0.0) ? lam : nullptr;
   const bool f64 = precision == PBFB_FP64;
+  if (precision == PBFB_FLOAT2) return launch_bem_far_ff(m, s, x, lam, cs, cd, kappa, y, accumulate);
   k_sources<<<blocks_for(nq, 256), 256, 0, m->stream>>>(s->nt, s->tri.p, s->vmap.p, lvec, uvec, u_local, s->qw.p,
                                                         s->nrm.p, s->qpf.p, s->qx.p, cs * INV4PI, cd * INV4PI,
                                                         f64 ? 1 : 0, s->spos.p, s->sdl.p, s->s64.p);
@@ -680,6 +894,43 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
   PB_LAUNCHED(m);
   timer_end(m, tm, ev, (double)nq * (double)nq);
   if (!f64) m->nbody_flops += (yuk ? 24.0 : 18.0) * (double)nq * (double)nq;
+  k_test_reduce<<<blocks_for(s->nv, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, s->val.p, nsplit,
+                                                               nq, s->qw.p, 1.0, accumulate ? 1 : 0, y);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
+int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, double cs, double cd,
+                      double kappa, double* y, bool accumulate) {
+  const int nq = s->nq;
+  const bool yuk = kappa != 0.0;
+  const int u_local = (x != nullptr && x == lam) ? 1 : 0;
+  PB_TRY(ff_exp_table(m));
+  if (s->ffsrc.n < 4 * (size_t)nq) PB_TRY(s->ffsrc.alloc(4 * (size_t)nq));
+  if (s->fftgt.n < 2 * (size_t)nq) PB_TRY(s->fftgt.alloc(2 * (size_t)nq));
+  k_sources_ff<<<blocks_for(nq, 256), 256, 0, m->stream>>>(
+      s->nt, s->tri.p, s->vmap.p, cs != 0.0 ? lam : nullptr, cd != 0.0 ? x : nullptr, u_local, s->qw.p, s->nrm.p,
+      s->qx.p, s->ctr[0], s->ctr[1], s->ctr[2], cs * INV4PI, cd * INV4PI, s->ffsrc.p, s->fftgt.p);
+  PB_LAUNCHED(m);
+  cudaEvent_t ev;
+  timer_begin(m, m->t_nbodyff, &ev);
+  constexpr int NT = 128;
+  const int ntb = blocks_for(nq, NT);
+  int nsplit = std::max(1, std::min(blocks_for(4 * 152, ntb), blocks_for(nq, 4 * NT)));
+  const int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
+  nsplit = blocks_for(nq, per);
+  if ((size_t)nsplit * nq > s->val.n) {
+    set_error("far-field split buffer too small");
+    return PBFB_ERR_STATE;
+  }
+  const float kh = (float)kappa, kl = (float)(kappa - (double)kh);
+  dim3 grid(ntb, nsplit);
+  if (yuk)
+    k_nbody_ff<NT, true><<<grid, NT, 0, m->stream>>>(nq, s->fftgt.p, s->ffsrc.p, kh, kl, m->ff_tab.p, per, s->val.p);
+  else
+    k_nbody_ff<NT, false><<<grid, NT, 0, m->stream>>>(nq, s->fftgt.p, s->ffsrc.p, kh, kl, m->ff_tab.p, per, s->val.p);
+  PB_LAUNCHED(m);
+  timer_end(m, m->t_nbodyff, ev, (double)nq * (double)nq);
   k_test_reduce<<<blocks_for(s->nv, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, s->val.p, nsplit,
                                                                nq, s->qw.p, 1.0, accumulate ? 1 : 0, y);
   PB_LAUNCHED(m);

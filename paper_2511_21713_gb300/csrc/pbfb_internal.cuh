@@ -109,6 +109,7 @@ struct Surface {
   DBuf<float4> spos, sdl;       // float32 sources
   DBuf<double> s64;             // float64 sources: 7 * nq (x, y, z, s, mx, my, mz)
   DBuf<double> val;             // nsplit * nq target potentials
+  DBuf<float4> ffsrc, fftgt;    // float-float sources (4 float4) and targets (2 float4) per point
   int nsplit = 1;
 };
 
@@ -176,7 +177,8 @@ struct Mesh {
   // statistics
   double launches = 0;
   bool timing = false;
-  KernelClassTimer t_nbody, t_nbody64, t_spmv, t_elem;
+  KernelClassTimer t_nbody, t_nbody64, t_nbodyff, t_spmv, t_elem;
+  DBuf<float2> ff_tab;      // float-float exp table of the Yukawa kernel
   double nbody_flops = 0.0;  // float32 far-field flops issued (18 per Laplace pair, 24 per Yukawa pair)
 };
 
@@ -204,6 +206,8 @@ int launch_surface_geometry(Mesh* m, Surface* s);
 int launch_pair_corrections(Mesh* m, Surface* s, double kappa);
 int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, double cs, double cd,
                    double kappa, int precision, double* y, bool accumulate);
+int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, double cs, double cd,
+                      double kappa, double* y, bool accumulate);
 int launch_coulomb(Mesh* m);
 int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev);
 int bem_apply_noalloc(Mesh* m, int which, int op, const double* x, double* y);

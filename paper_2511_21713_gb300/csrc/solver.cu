@@ -345,7 +345,7 @@ static int set_params(Mesh* m, double eps_in, double eps_out, double kappa, doub
     set_error("invalid parameters: eps_in %g eps_out %g kappa %g T %g", eps_in, eps_out, kappa, T);
     return PBFB_ERR_INVALID;
   }
-  if (precision != PBFB_FP64 && precision != PBFB_MIXED) {
+  if (precision != PBFB_FP64 && precision != PBFB_MIXED && precision != PBFB_FLOAT2) {
     set_error("invalid precision %d", precision);
     return PBFB_ERR_INVALID;
   }
@@ -785,7 +785,8 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   }
   if (!(o.tol_nl > 0) || !(o.tol_gmres > 0) || !(o.tol_gmres0 > 0) || !(o.tol_omega > 0) || o.max_newton < 1 ||
       o.max_gmres < 1 || !(o.omega_max > 0) || o.max_omega_iters < 1 ||
-      (o.first_scheme != PBFB_T3 && o.first_scheme != PBFB_HS && o.first_scheme != PBFB_LINEAR)) {
+      (o.first_scheme != PBFB_T3 && o.first_scheme != PBFB_HS && o.first_scheme != PBFB_LINEAR) ||
+      (o.precision != PBFB_FP64 && o.precision != PBFB_MIXED)) {
     set_error("solve: invalid options");
     return PBFB_ERR_INVALID;
   }
@@ -821,9 +822,9 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   for (k = 0; k < o.max_newton; ++k) {
     const int scheme = k == 0 ? o.first_scheme : PBFB_HS;
     PB_TRY(launch_axpby(m, n, 1.0, m->xL.p, 1.0, m->xNL.p, m->phi.p));
-    // c = b - Acal(0) Phi (far field in float64 in both precisions: the nonlinear residual)
+    // c = b - Acal(0) Phi: the nonlinear residual's far field in float64 (FP64) or float-float (MIXED)
     PB_TRY(clear_jacobian(m));
-    PB_TRY(apply_prec(m, m->phi.p, m->cvec.p, PBFB_FP64));
+    PB_TRY(apply_prec(m, m->phi.p, m->cvec.p, m->precision == PBFB_MIXED ? PBFB_FLOAT2 : PBFB_FP64));
     PB_TRY(launch_axpby(m, n, 1.0, bvec, -1.0, m->cvec.p, m->cvec.p));
     // J(u), N(u); d = c - [N; 0; 0]
     PB_TRY(assemble(m, scheme, m->phi.p, m->Nvec.p));
@@ -1067,6 +1068,7 @@ int pbfb_mesh_destroy(pbfb_mesh* h) {
     cudaStreamSynchronize(h->m->stream);
     pbfb::timer_flush(h->m->t_nbody);
     pbfb::timer_flush(h->m->t_nbody64);
+    pbfb::timer_flush(h->m->t_nbodyff);
     pbfb::timer_flush(h->m->t_spmv);
     pbfb::timer_flush(h->m->t_elem);
     if (h->m->pinned) cudaFreeHost(h->m->pinned);
@@ -1213,6 +1215,7 @@ int pbfb_profile(pbfb_mesh* h, int enable, int reset, double* stats) {
   cudaStreamSynchronize(m->stream);
   pbfb::timer_flush(m->t_nbody);
   pbfb::timer_flush(m->t_nbody64);
+  pbfb::timer_flush(m->t_nbodyff);
   pbfb::timer_flush(m->t_spmv);
   pbfb::timer_flush(m->t_elem);
   if (stats) {
@@ -1228,12 +1231,15 @@ int pbfb_profile(pbfb_mesh* h, int enable, int reset, double* stats) {
     stats[9] = m->t_nbody64.count;
     stats[10] = m->t_nbody64.ms;
     stats[11] = m->t_nbody64.work;
-    for (int k = 12; k < 16; ++k) stats[k] = 0.0;
+    stats[12] = m->t_nbodyff.count;
+    stats[13] = m->t_nbodyff.ms;
+    stats[14] = m->t_nbodyff.work;
+    stats[15] = 0.0;
   }
   if (reset) {
     m->launches = 0;
     m->nbody_flops = 0.0;
-    for (auto* t : {&m->t_nbody, &m->t_nbody64, &m->t_spmv, &m->t_elem}) {
+    for (auto* t : {&m->t_nbody, &m->t_nbody64, &m->t_nbodyff, &m->t_spmv, &m->t_elem}) {
       t->ms = 0;
       t->count = 0;
       t->work = 0;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libpbfb.so")
 PBFB_OK = 0
 ERRORS = {1: "INVALID", 2: "CUDA", 3: "GMRES_NOCONV", 4: "NEWTON_NOCONV", 5: "OMEGA",
           6: "NONFINITE", 7: "OOM", 8: "STATE"}
-FP64, MIXED = 0, 1
+FP64, MIXED, FLOAT2 = 0, 1, 2
 LINEAR, T3, HS = 0, 1, 2
 GAMMA_M, GAMMA_S = 0, 1
 JACOBI, BLOCK = 0, 1
@@ -246,7 +246,8 @@ class Mesh:
         _check(load().pbfb_profile(self.h, int(enable), int(reset), _ptr(st)))
         return dict(launches=st[0], nbody_launches=st[1], nbody_ms=st[2], nbody_pairs=st[3],
                     spmv_launches=st[4], spmv_ms=st[5], elem_launches=st[6], elem_ms=st[7],
-                    nbody_flops=st[8], nbody64_launches=st[9], nbody64_ms=st[10], nbody64_pairs=st[11])
+                    nbody_flops=st[8], nbody64_launches=st[9], nbody64_ms=st[10], nbody64_pairs=st[11],
+                    nbodyff_launches=st[12], nbodyff_ms=st[13], nbodyff_pairs=st[14])
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -32,7 +32,7 @@ def main():
     sample = np.sort(rng.choice(P.n, 64, replace=False))
     out['sample_index'] = sample.tolist()
     for name, opts in (('default', pb.Opts()),
-                       ('tight', pb.Opts(tol_gmres0=1e-11, tol_gmres=1e-11, tol_nl=1e-10))):
+                       ('tight', pb.Opts(tol_gmres0=1e-10, tol_gmres=1e-10, tol_nl=1e-7))):
         t = time.time()
         R = pb.solve(P, opts)
         out[name] = dict(total=R.total, LC=R.LC, NC=R.NC, dG_ion=R.dG_ion, newton_iters=R.newton_iters,
