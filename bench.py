@@ -37,6 +37,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "multi_charge_sphere.json")
 
 
 def workload_config(case, precision):
+    if case.n_v != 72036:
+        return {"workload": "single_charge_sphere (profiling case)", "n_vertices": int(case.n_v),
+                "n_tets": int(case.n_t), "precision": precision}
     return {
         "workload": "multi_charge_sphere",
         "geometry": "solute sphere r=12 A, FEM shell to 24 A (17 geometric layers), "
@@ -117,7 +120,7 @@ def run_pbfb(args):
         tdist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    case = inputs.multi_charge_sphere()
+    case = inputs.multi_charge_sphere() if args.workload == "multi_charge_sphere" else inputs.single_charge_sphere()
     prec = pbfb.MIXED if args.precision == "mixed" else pbfb.FP64
     opts = pbfb.default_opts(precision=prec)
     mesh = pbfb.Mesh.from_case(case)
@@ -214,11 +217,11 @@ def run_pbfb(args):
                   "gmres": res["gmres"], "omega": [round(w, 4) for w in res["omega"]],
                   "total_kcal_mol": res["total"], "LC": res["LC"], "NC": res["NC"], "dG_ion": res["dG_ion"]},
     }
-    if os.path.exists(GOLDEN):
+    if os.path.exists(GOLDEN) and args.workload == "multi_charge_sphere":
         g = json.load(open(GOLDEN))
         ref = g["tight"]["total"]
         out["energy_rel_err_vs_oracle"] = abs(res["total"] - ref) / abs(ref)
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "multi_charge_sphere":
         out["cpu_baseline"] = oracle_sample(case, res, args.cpu_sample)
     if ws > 1:
         tdist.destroy_process_group()
@@ -336,6 +339,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=64, help="1/k of the BEM rows in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3, help="host-buffer solves timed for the e2e figure")
+    ap.add_argument("--workload", default="multi_charge_sphere", choices=["multi_charge_sphere", "small"],
+                    help="small = the single-charge sphere, for profiler launch lists")
     args = ap.parse_args()
     out = run_reference(args) if args.impl == "reference" else run_pbfb(args)
     if out is not None:

@@ -243,6 +243,12 @@ int pbfb_omega_eval(pbfb_mesh* mesh, int scheme, const double* u_dev, const doub
  * out[0..3] = Total, LC, NC, dG_Omega_i (host) (Eq. Esolv). */
 int pbfb_energy(pbfb_mesh* mesh, const double* xL_dev, const double* xNL_dev, double* out);
 
+/* Launch-shape knobs of the float32 far field (an autotuner sets them):
+ * targets per thread (1, 2, 4 or 8) and target blocks per SM used to choose
+ * the number of source splits (1..64).  0 restores the built-in heuristic.
+ * Results change only in float64 rounding (the float32 tile sums are the same). */
+int pbfb_set_tuning(pbfb_mesh* mesh, int nbody_targets_per_thread, int nbody_blocks_per_sm);
+
 /* Per-kernel-class timing (CUDA events around each launch of the class) and
  * launch counters.  enable != 0 turns event timing on (it adds a little host
  * overhead per launch).  stats (host, 16 doubles):

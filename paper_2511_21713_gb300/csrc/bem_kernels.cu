@@ -338,6 +338,18 @@ __global__ void k_sources(int nt, const int* __restrict__ tri, const int* __rest
   }
 }
 
+// Hardware approximations (MUFU) without denormal fix-ups: inputs here are normal numbers.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // float32 N-body: targets = sources = the nq quadrature points.  Block = NT threads, each
 // owning TPT targets (interleaved by NT); sources streamed through shared memory in tiles
 // of NT; blockIdx.y selects a contiguous source range (split).  Each tile's float partial
@@ -389,12 +401,12 @@ __global__ void __launch_bounds__(NT) k_nbody_f32(int nq, const float4* __restri
         for (int k = 0; k < TPT; ++k) {
           float dx = tx[k] - p.x, dy = ty[k] - p.y, dz = tz[k] - p.z;
           float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          float ri = rsqrtf(r2);
+          float ri = rsqrt_approx(r2);
           float nd = fmaf(d.x, dx, fmaf(d.y, dy, d.z * dz));
           float ri2 = ri * ri;
           if (YUK) {
             float r = r2 * ri;
-            float e = exp2f(nk * r);
+            float e = ex2_approx(nk * r);
             float kr1 = fmaf(kappa, r, 1.f);
             float tt = fmaf(nd * kr1, ri2, p.w);
             acc[k] = fmaf(tt, e * ri, acc[k]);
@@ -413,12 +425,12 @@ __global__ void __launch_bounds__(NT) k_nbody_f32(int nq, const float4* __restri
           if (s0 + jj == ti[k]) continue;
           float dx = tx[k] - p.x, dy = ty[k] - p.y, dz = tz[k] - p.z;
           float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          float ri = rsqrtf(r2);
+          float ri = rsqrt_approx(r2);
           float nd = fmaf(d.x, dx, fmaf(d.y, dy, d.z * dz));
           float ri2 = ri * ri;
           if (YUK) {
             float r = r2 * ri;
-            float e = exp2f(nk * r);
+            float e = ex2_approx(nk * r);
             float kr1 = fmaf(kappa, r, 1.f);
             float tt = fmaf(nd * kr1, ri2, p.w);
             acc[k] = fmaf(tt, e * ri, acc[k]);
@@ -671,25 +683,38 @@ __global__ void __launch_bounds__(NT) k_nbody_ff(int nq, const float4* __restric
   if (i < nq) out[(int64_t)blockIdx.y * nq + i] = acc64;
 }
 
-// y[row0 + i] (+)= sum over incident (tau, a) of sum_q psi_a(x_q) w_q sum_split val[split][6 tau + q]
+// val[0][j] = sum over the source splits of val[split][j] (fixed order)
+__global__ void k_split_sum(int nq, int nsplit, double* __restrict__ val) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nq || nsplit <= 1) return;
+  double v = val[j];
+  for (int sp = 1; sp < nsplit; ++sp) v += val[(int64_t)sp * nq + j];
+  val[j] = v;
+}
+
+// y[i] (+)= scale * sum over incident (tau, a) of sum_q psi_a(x_q) w_q val[0][6 tau + q]; 4 lanes per vertex
 __global__ void k_test_reduce(int nv, const int* __restrict__ ptr, const int* __restrict__ idx,
                               const double* __restrict__ val, int nsplit, int nq, const double* __restrict__ qw,
                               double scale, int accumulate, double* __restrict__ y) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 3;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 2;
   if (i >= nv) return;
+  (void)nsplit;
+  (void)nq;
   double acc = 0.0;
-  for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
-    int e = idx[k];
-    int t = e / 3, a = e - 3 * t;
-    for (int q = 0; q < QS; ++q) {
-      int j = QS * t + q;
-      double v = 0.0;
-      for (int sp = 0; sp < nsplit; ++sp) v += val[(int64_t)sp * nq + j];
-      acc += c_tri_b[q][a] * qw[j] * v;
-    }
+  const int b = ptr[i], e = ptr[i + 1];
+  for (int k = b * QS + lane; k < e * QS; k += 4) {
+    int ent = idx[k / QS], q = k % QS;
+    int t = ent / 3, a = ent - 3 * t;
+    int j = QS * t + q;
+    acc += c_tri_b[q][a] * qw[j] * val[j];
   }
-  acc *= scale;
-  y[i] = accumulate ? y[i] + acc : acc;
+  acc += __shfl_down_sync(0xffffffffu, acc, 2, 4);
+  acc += __shfl_down_sync(0xffffffffu, acc, 1, 4);
+  if (lane == 0) {
+    acc *= scale;
+    y[i] = accumulate ? y[i] + acc : acc;
+  }
 }
 
 // Coulomb sum at Gamma_m quadrature points: sum_k z_k / |x_j - x_k|.
@@ -807,6 +832,18 @@ int ff_exp_table(Mesh* m) {
   return PBFB_OK;
 }
 
+int test_reduce(Mesh* m, Surface* s, double* val, int nsplit, double* y, bool accumulate) {
+  if (nsplit > 1) {
+    k_split_sum<<<blocks_for(s->nq, 256), 256, 0, m->stream>>>(s->nq, nsplit, val);
+    PB_LAUNCHED(m);
+  }
+  k_test_reduce<<<blocks_for((int64_t)s->nv * 4, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, val,
+                                                                            nsplit, s->nq, s->qw.p, 1.0,
+                                                                            accumulate ? 1 : 0, y);
+  PB_LAUNCHED(m);
+  return PBFB_OK;
+}
+
 int launch_surface_geometry(Mesh* m, Surface* s) {
   k_surface_geometry<<<blocks_for(s->nt, 128), 128, 0, m->stream>>>(
       m->xyz.p, m->nv, s->tri.p, s->vmap.p, s->nt, s->ctr[0], s->ctr[1], s->ctr[2], s->qx.p, s->qw.p, s->nrm.p,
@@ -871,10 +908,11 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
       k_nbody_f64<NT, false><<<grid, NT, 0, m->stream>>>(nq, s->s64.p, kappa, per, s->val.p);
   } else {
     constexpr int NT = 128;
-    const bool big = nq >= 16384;
-    const int tpt = big ? 4 : 1;
+    // launch shape: targets per thread and source splits (tuning knobs; 0 = heuristic)
+    int tpt = m->tune_tpt > 0 ? m->tune_tpt : (nq >= 16384 ? 4 : 1);
+    const int bps = m->tune_bps > 0 ? m->tune_bps : 16;
     int ntb = blocks_for(nq, NT * tpt);
-    nsplit = std::max(1, std::min(blocks_for(4 * 152, ntb), blocks_for(nq, 4 * NT)));
+    nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * NT)));
     int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
     nsplit = blocks_for(nq, per);
     dim3 grid(ntb, nsplit);
@@ -883,21 +921,22 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
       return PBFB_ERR_STATE;
     }
     float kf = (float)kappa;
-    if (big) {
-      if (yuk) k_nbody_f32<NT, 4, true><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, s->spos.p, s->sdl.p, kf, per, s->val.p);
-      else k_nbody_f32<NT, 4, false><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, s->spos.p, s->sdl.p, kf, per, s->val.p);
-    } else {
-      if (yuk) k_nbody_f32<NT, 1, true><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, s->spos.p, s->sdl.p, kf, per, s->val.p);
-      else k_nbody_f32<NT, 1, false><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, s->spos.p, s->sdl.p, kf, per, s->val.p);
+    const float4* q4 = s->qpf.p;
+#define PB_NB(T)                                                                                                \
+  if (yuk) k_nbody_f32<NT, T, true><<<grid, NT, 0, m->stream>>>(nq, q4, s->spos.p, s->sdl.p, kf, per, s->val.p); \
+  else k_nbody_f32<NT, T, false><<<grid, NT, 0, m->stream>>>(nq, q4, s->spos.p, s->sdl.p, kf, per, s->val.p);
+    switch (tpt) {
+      case 1: PB_NB(1) break;
+      case 2: PB_NB(2) break;
+      case 8: PB_NB(8) break;
+      default: PB_NB(4) break;
     }
+#undef PB_NB
   }
   PB_LAUNCHED(m);
   timer_end(m, tm, ev, (double)nq * (double)nq);
   if (!f64) m->nbody_flops += (yuk ? 24.0 : 18.0) * (double)nq * (double)nq;
-  k_test_reduce<<<blocks_for(s->nv, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, s->val.p, nsplit,
-                                                               nq, s->qw.p, 1.0, accumulate ? 1 : 0, y);
-  PB_LAUNCHED(m);
-  return PBFB_OK;
+  return test_reduce(m, s, s->val.p, nsplit, y, accumulate);
 }
 
 int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, double cs, double cd,
@@ -931,20 +970,14 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
     k_nbody_ff<NT, false><<<grid, NT, 0, m->stream>>>(nq, s->fftgt.p, s->ffsrc.p, kh, kl, m->ff_tab.p, per, s->val.p);
   PB_LAUNCHED(m);
   timer_end(m, m->t_nbodyff, ev, (double)nq * (double)nq);
-  k_test_reduce<<<blocks_for(s->nv, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, s->val.p, nsplit,
-                                                               nq, s->qw.p, 1.0, accumulate ? 1 : 0, y);
-  PB_LAUNCHED(m);
-  return PBFB_OK;
+  return test_reduce(m, s, s->val.p, nsplit, y, accumulate);
 }
 
 int launch_coulomb(Mesh* m) {
   Surface* s = &m->sm;
   k_coulomb_qp<<<blocks_for(s->nq, 128), 128, 0, m->stream>>>(s->nq, s->qx.p, m->nq, m->qxyz.p, m->qz.p, s->val.p);
   PB_LAUNCHED(m);
-  k_test_reduce<<<blocks_for(s->nv, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, s->val.p, 1,
-                                                               s->nq, s->qw.p, 1.0, 0, m->coul.p);
-  PB_LAUNCHED(m);
-  return PBFB_OK;
+  return test_reduce(m, s, s->val.p, 1, m->coul.p, false);
 }
 
 int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev) {
@@ -1040,9 +1073,7 @@ int bem_apply_noalloc(Mesh* m, int which, int op, const double* x, double* y) {
     else k_nbody_f32<NT, 1, false><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, spos, sdl, kf, per, val);
   }
   PB_LAUNCHED(m);
-  k_test_reduce<<<blocks_for(s->nv, 128), 128, 0, m->stream>>>(s->nv, s->inc_ptr.p, s->inc_idx.p, val, nsplit, nq,
-                                                               s->qw.p, 1.0, 0, y);
-  PB_LAUNCHED(m);
+  PB_TRY(test_reduce(m, s, val, nsplit, y, false));
   PB_TRY(launch_csr_spmv(m, s->nv, s->c_ptr.p, s->c_col.p, op == 0 ? s->corrV.p : s->corrK.p, x, y, true));
   return PBFB_OK;
 }

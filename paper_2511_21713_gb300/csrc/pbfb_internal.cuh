@@ -164,13 +164,16 @@ struct Mesh {
   int gm_restart = 0;
   DBuf<double> gV, gw, gz, gr, gdiag, gh, gpart, gtmp;
   DBuf<double> gZ;          // flexible GMRES: preconditioned basis (restart x n)
-  DBuf<double> gpcg;        // inner PCG vectors (5 x n)
+  DBuf<double> gpcg;        // inner PCG vectors (6 x n)
   DBuf<double> gones;       // n ones
   // block preconditioner: FEM block + Robin term on Gamma_s, and its Jacobi diagonal
   int nrobin = 0;
   DBuf<int> robin_slot, robin_ref;  // FEM-row slot (u-u, both on Gamma_s) <- Gamma_s mass slot
   DBuf<double> pval, pdinv;
   double gs_radius = 1.0;           // sqrt(|Gamma_s| / 4 pi)
+  int coop_blocks = 0;              // grid of the cooperative inner PCG (-1: not available)
+  int tune_tpt = 0;                 // float32 far field: targets per thread (0 = heuristic)
+  int tune_bps = 0;                 // float32 far field: target blocks per SM for the source split
   // Newton workspace
   DBuf<double> xL, xNL, phi, cvec, dvec, du, pvec, tmp, Nvec, bvec, xout, urb;
   std::vector<double> qz_h;  // charges (host copy)
@@ -203,6 +206,8 @@ int launch_csr_spmv(Mesh* m, int nrows, const int* ptr, const int* col, const do
 
 // ---- bem_kernels.cu
 int launch_surface_geometry(Mesh* m, Surface* s);
+// test reduction of far-field partials (sums the source splits in place, then reduces per vertex)
+int test_reduce(Mesh* m, Surface* s, double* val, int nsplit, double* y, bool accumulate);
 int launch_pair_corrections(Mesh* m, Surface* s, double kappa);
 int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, double cs, double cd,
                    double kappa, int precision, double* y, bool accumulate);

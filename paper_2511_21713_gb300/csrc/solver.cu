@@ -10,6 +10,7 @@
 // condition of Sec. 2.5.2); otherwise a batched scan of g_d = d . d' over omega_max j / 16
 // followed by bisection of its first sign change.  L_e skip rule and the adjustable GMRES
 // tolerance follow Appendix B.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -179,6 +180,7 @@ __device__ __forceinline__ void block_sum_store(double v, double* out) {
     for (int w = 0; w < PCG_T / 32; ++w) s += sh[w];
     *out = s;
   }
+  __syncthreads();  // sh is reused by the next call
 }
 
 // x = 0, r = b, z = dinv r, p = z, partial r.z
@@ -261,6 +263,98 @@ __global__ void k_diag_inv(int nv, const int* __restrict__ ptr, const int* __res
   for (int k = ptr[r]; k < ptr[r + 1]; ++k)
     if (col[k] == r) d = val[k];
   dinv[r] = 1.0 / d;
+}
+
+// The whole inner PCG in one cooperative launch (all blocks resident; grid-wide barriers between
+// the dependent phases).  Every block sums the per-block partials itself in the same fixed order,
+// so all blocks see identical scalars and the result is deterministic.  part: 2 * gridDim.x.
+__device__ __forceinline__ double coop_sum(const double* part, int nb) {
+  __shared__ double tot;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    tot = s;
+  }
+  __syncthreads();
+  double v = tot;
+  __syncthreads();
+  return v;
+}
+
+// Chronopoulos-Gear form of preconditioned CG (one fused reduction per step): with w = A z,
+// gamma = r.z, delta = z.w: beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old),
+// p = z + beta p, q = w + beta q (= A p), x += alpha p, r -= alpha q, z = M r.  Same iterates as
+// standard PCG in exact arithmetic, two grid-wide barriers per step instead of three.
+__global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int* __restrict__ ptr,
+                                                     const int* __restrict__ col, const double* __restrict__ val,
+                                                     const double* __restrict__ b, const double* __restrict__ dinv,
+                                                     double* __restrict__ x, double* __restrict__ r,
+                                                     double* __restrict__ z, double* __restrict__ p,
+                                                     double* __restrict__ q, double* __restrict__ w,
+                                                     double* __restrict__ part) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int nb = gridDim.x;
+  double* part_g = part;
+  double* part_d = part + nb;
+  const int tid = blockIdx.x * PCG_T + threadIdx.x, stride = nb * PCG_T;
+  const int lane = threadIdx.x & 7;
+  for (int i = tid; i < nv; i += stride) {
+    double bi = b[i];
+    x[i] = 0.0;
+    r[i] = bi;
+    z[i] = dinv[i] * bi;
+    p[i] = 0.0;
+    q[i] = 0.0;
+  }
+  grid.sync();
+  double gamma_old = 1.0, alpha_old = 1.0;
+  for (int it = 0; it < iters; ++it) {
+    // w = A z; partial r.z and z.w
+    double ag = 0.0, ad = 0.0;
+    for (int row = tid >> 3; row < nv; row += stride >> 3) {
+      double sacc = 0.0;
+      for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) sacc += val[k] * z[col[k]];
+      sacc += __shfl_down_sync(0xffffffffu, sacc, 4, 8);
+      sacc += __shfl_down_sync(0xffffffffu, sacc, 2, 8);
+      sacc += __shfl_down_sync(0xffffffffu, sacc, 1, 8);
+      if (lane == 0) {
+        w[row] = sacc;
+        double zr = z[row];
+        ag += r[row] * zr;
+        ad += zr * sacc;
+      }
+    }
+    block_sum_store(ag, part_g + blockIdx.x);
+    block_sum_store(ad, part_d + blockIdx.x);
+    grid.sync();
+    const double gamma = coop_sum(part_g, nb);
+    const double delta = coop_sum(part_d, nb);
+    // zero residual (e.g. a right-hand side that vanishes on the FEM rows): nothing left to do
+    double beta = 0.0, alpha = 0.0;
+    if (gamma != 0.0) {
+      if (it == 0 || gamma_old == 0.0 || alpha_old == 0.0) {
+        alpha = delta != 0.0 ? gamma / delta : 0.0;
+      } else {
+        beta = gamma / gamma_old;
+        const double den = delta - beta * gamma / alpha_old;
+        alpha = den != 0.0 ? gamma / den : 0.0;
+      }
+    }
+    gamma_old = gamma;
+    alpha_old = alpha;
+    for (int i = tid; i < nv; i += stride) {
+      double pi = z[i] + beta * p[i];
+      double qi = w[i] + beta * q[i];
+      p[i] = pi;
+      q[i] = qi;
+      x[i] += alpha * pi;
+      double ri = r[i] - alpha * qi;
+      r[i] = ri;
+      z[i] = dinv[i] * ri;
+    }
+    grid.sync();
+  }
 }
 
 // surface rows of the block preconditioner: z = dinv v
@@ -417,8 +511,20 @@ static int jacobi(Mesh* m, double* dinv) {
 // (the constant mode of the exterior Dirichlet-to-Neumann map of a sphere of Gamma_s's area),
 // which keeps it positive definite when J = 0.
 static int prepare_block_precond(Mesh* m) {
+  if (m->coop_blocks == 0) {
+    int coop = 0, nsm = 0, per = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, m->dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->dev);
+    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_coop, PCG_T, 0));
+    // all resident blocks (memory-level parallelism for the SpMV phases), but no more than
+    // one pass of 8 lanes per row needs
+    int want = per * nsm;
+    want = std::min(want, std::max(1, blocks_for((int64_t)m->nv * 8, PCG_T)));
+    m->coop_blocks = (coop && per > 0) ? want : -1;
+  }
   PB_TRY(ensure(m->pval, m->fem_nnz));
   PB_TRY(ensure(m->pdinv, m->nv));
+  PB_TRY(ensure(m->gpart, 2 * (size_t)std::max(m->coop_blocks, 152) + 8));
   PB_CUDA(cudaMemcpyAsync(m->pval.p, m->s_val.p, m->fem_nnz * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
   const double c = m->eps_s * (m->kappa + 1.0 / m->gs_radius);
   if (m->nrobin) {
@@ -442,6 +548,19 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
   double* part = m->gpart.p;
   double* sc = m->scal.p + 5000;     // [0] pq, [1 + k] rz_k
   const double* dinv = m->pdinv.p;
+  if (m->coop_blocks > 0) {
+    int nbc = m->coop_blocks, iters = inner_iters, nvv = nv;
+    const int* sp = m->s_ptr.p;
+    const int* sc2 = m->s_col.p;
+    const double* pv = m->pval.p;
+    double* pw = pb + 5 * (size_t)n;
+    void* args[] = {&nvv, &iters, &sp, &sc2, &pv, (void*)&v, (void*)&dinv, &z, &pr, &pz, &pp, &pq, &pw, &part};
+    PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_coop, dim3(nbc), dim3(PCG_T), args, 0, m->stream));
+    PB_LAUNCHED(m);
+    k_scale_rows<<<blocks_for(n - nv, 256), 256, 0, m->stream>>>(nv, n, v, m->gdiag.p, z);
+    PB_LAUNCHED(m);
+    return PBFB_OK;
+  }
   k_pcg_init<<<nb, PCG_T, 0, m->stream>>>(nv, v, dinv, z, pr, pz, pp, part);
   PB_LAUNCHED(m);
   k_sum_to<<<1, 32, 0, m->stream>>>(part, nb, sc + 1);
@@ -477,9 +596,9 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
   const bool flexible = precond == PBFB_PRECOND_BLOCK;
   if (flexible) {
     PB_TRY(ensure(m->gZ, (size_t)restart * n));
-    if (m->gpcg.n < 5 * (size_t)n) {
-      PB_TRY(m->gpcg.alloc(5 * (size_t)n));
-      PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 5 * (size_t)n * sizeof(double), m->stream));
+    if (m->gpcg.n < 6 * (size_t)n) {
+      PB_TRY(m->gpcg.alloc(6 * (size_t)n));
+      PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 6 * (size_t)n * sizeof(double), m->stream));
     }
   }
   PB_TRY(ensure(m->gV, (size_t)(restart + 1) * n));
@@ -1208,6 +1327,22 @@ int pbfb_energy(pbfb_mesh* h, const double* xL_dev, const double* xNL_dev, doubl
     return PBFB_ERR_STATE;
   }
   return pbfb::energy(m, xL_dev, xNL_dev, out);
+}
+
+int pbfb_set_tuning(pbfb_mesh* h, int nbody_targets_per_thread, int nbody_blocks_per_sm) {
+  PB_HANDLE(h);
+  if (nbody_targets_per_thread != 0 && nbody_targets_per_thread != 1 && nbody_targets_per_thread != 2 &&
+      nbody_targets_per_thread != 4 && nbody_targets_per_thread != 8) {
+    pbfb::set_error("set_tuning: targets per thread must be 0, 1, 2, 4 or 8");
+    return PBFB_ERR_INVALID;
+  }
+  if (nbody_blocks_per_sm < 0 || nbody_blocks_per_sm > 64) {
+    pbfb::set_error("set_tuning: blocks per SM must be in [0, 64]");
+    return PBFB_ERR_INVALID;
+  }
+  m->tune_tpt = nbody_targets_per_thread;
+  m->tune_bps = nbody_blocks_per_sm;
+  return PBFB_OK;
 }
 
 int pbfb_profile(pbfb_mesh* h, int enable, int reset, double* stats) {

@@ -30,7 +30,7 @@ EXPORTS = [
     "pbfb_charges_set", "pbfb_solve", "pbfb_solve_device", "pbfb_mesh_destroy",
     "pbfb_last_error", "pbfb_set_params", "pbfb_assemble", "pbfb_clear_jacobian",
     "pbfb_apply", "pbfb_bem_apply", "pbfb_fem_rows", "pbfb_gmres", "pbfb_omega_eval",
-    "pbfb_energy", "pbfb_profile", "pbfb_bem_apply_noalloc",
+    "pbfb_energy", "pbfb_profile", "pbfb_bem_apply_noalloc", "pbfb_set_tuning",
 ]
 
 
@@ -104,6 +104,7 @@ def load():
         "pbfb_omega_eval": (I, [P, I, P, P, P, P, P, I, P]),
         "pbfb_energy": (I, [P, P, P, P]),
         "pbfb_profile": (I, [P, I, I, P]),
+        "pbfb_set_tuning": (I, [P, I, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -240,6 +241,9 @@ class Mesh:
         out = np.zeros(4)
         _check(load().pbfb_energy(self.h, _ptr(xL_dev), _ptr(xNL_dev), _ptr(out)))
         return out
+
+    def set_tuning(self, targets_per_thread=0, blocks_per_sm=0):
+        _check(load().pbfb_set_tuning(self.h, targets_per_thread, blocks_per_sm))
 
     def profile(self, enable=True, reset=False):
         st = np.zeros(16)
