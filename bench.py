@@ -205,7 +205,11 @@ def run_pbfb(args):
         "gpu_launches": int(prof["launches"]),
         "roofline": {"bound": "alu", "kernel": f"far-field N-body ({kname})",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     # dram__bytes_read + write per launch from the ncu capture in
+                     # profiles/k_nbody_f32_multi_charge_sphere.md (source records read once)
+                     "traffic": (2.3145e6 if (prec == pbfb.MIXED and args.workload == "multi_charge_sphere")
+                                 else None),
                      "peak_basis": peak_note, "avg_launch_ms": avg_ms,
                      "pairs_per_launch": pairs_per_launch, "launches": launches,
                      "share_of_step": kms / total_ms if total_ms else None,
@@ -217,6 +221,21 @@ def run_pbfb(args):
                   "gmres": res["gmres"], "omega": [round(w, 4) for w in res["omega"]],
                   "total_kcal_mol": res["total"], "LC": res["LC"], "NC": res["NC"], "dG_ion": res["dG_ion"]},
     }
+    # the plain float64 GPU path on the same input (one solve, outside the timed region)
+    if args.fp64_compare and prec == pbfb.MIXED:
+        o64 = pbfb.default_opts(precision=pbfb.FP64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r64 = mesh.solve_device(case.eps_in, case.eps_out, case.kappa, case.T, x_out, o64)
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        out["fp64_gpu"] = {"ms_per_solve": ms64, "solves_per_s": 1e3 / ms64,
+                           "mixed_speedup": ms64 / (total_ms_max / args.steps),
+                           "mixed_energy_rel_diff": abs(res["total"] - r64["total"]) / abs(r64["total"]),
+                           "newton_iters": r64["newton_iters"], "gmres": r64["gmres"]}
     if os.path.exists(GOLDEN) and args.workload == "multi_charge_sphere":
         g = json.load(open(GOLDEN))
         ref = g["tight"]["total"]
@@ -339,6 +358,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=64, help="1/k of the BEM rows in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3, help="host-buffer solves timed for the e2e figure")
+    ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false",
+                    help="skip the single float64-path solve reported under fp64_gpu")
     ap.add_argument("--workload", default="multi_charge_sphere", choices=["multi_charge_sphere", "small"],
                     help="small = the single-charge sphere, for profiler launch lists")
     args = ap.parse_args()

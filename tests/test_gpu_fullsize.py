@@ -1,0 +1,124 @@
+"""Parity at the bench workload's full size (multi-charge sphere: 72,036 vertices, 408,000
+tets, 8000 + 8000 triangles, 200 charges), in the launch configuration bench.py times.
+
+* the complete mixed-precision solve against the oracle's solution stored in
+  tests/golden/multi_charge_sphere.json (written by tests/golden/make_golden.py from the
+  oracle only): energy within 1e-5 (the mixed-path target) and the sampled unknowns;
+* boundary-operator rows of sampled vertices (the oracle assembles just those rows) in
+  float64 and float-float, 1e-11; every FEM row of A + J and the load N, 1e-12;
+* the batched omega evaluation over all 408,000 tets, 1e-11.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "multi_charge_sphere.json")
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, np.float64), device="cuda")
+
+
+@pytest.fixture(scope="module")
+def big():
+    from paper_2511_21713_gb300 import inputs, pbfb
+    case = inputs.multi_charge_sphere()
+    m = pbfb.Mesh.from_case(case)
+    m.charges_set(case.q_xyz, case.q_z)
+    yield case, m
+    m.close()
+
+
+def test_mixed_solve_matches_oracle_golden(big):
+    from paper_2511_21713_gb300 import pbfb
+    case, m = big
+    g = json.load(open(GOLDEN))
+    x, res = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.default_opts(precision=pbfb.MIXED))
+    ref = g["tight"]
+    assert abs(res["total"] - ref["total"]) < 1e-5 * abs(ref["total"])
+    assert abs(res["total"] - (res["LC"] + res["NC"] + res["dG_ion"])) < 1e-12 * abs(res["total"])
+    assert res["dG_ion"] > 0 and res["NC"] < 0
+    idx = np.array(g["sample_index"])
+    xs = np.array(ref["x_sample"])
+    assert np.linalg.norm(x[idx] - xs) < 1e-6 * np.linalg.norm(xs)
+    assert abs(np.linalg.norm(x) / ref["x_norm"] - 1) < 1e-7
+    assert res["newton_iters"] <= g["default"]["newton_iters"] + 1
+
+
+def _row_sample(P_surface, k=12, seed=3):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(P_surface.n, k, replace=False))
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_boundary_operator_rows(big, precision):
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import bem
+    case, m = big
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, precision)
+    rng = np.random.default_rng(5)
+    for which, tris, kap in ((pbfb.GAMMA_M, case.gm_tris, 0.0), (pbfb.GAMMA_S, case.gs_tris, case.kappa)):
+        s = bem.Surface(case.xyz, tris)
+        rows = _row_sample(s)
+        # every test triangle touching a sampled vertex: those rows are then complete
+        tt = np.unique(np.nonzero(np.isin(s.tl, rows).any(axis=1))[0])
+        V, K = bem.assemble(s, kap, test_tris=tt)
+        x = rng.standard_normal(s.n) + 1.0
+        for op, Mo in ((0, V), (1, K)):
+            y = dev(np.zeros(s.n))
+            m.bem_apply(which, op, dev(x), y)
+            got = y.cpu().numpy()[rows]
+            ref = Mo[rows] @ x
+            assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max(), (which, op)
+
+
+def test_fem_rows_and_load_full(big):
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import fem, bem
+    case, m = big
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.MIXED)
+    r = np.linalg.norm(case.xyz, axis=1)
+    u = 6.0 * np.exp(-0.25 * (r - 12.0)) * np.cos(case.xyz[:, 0])
+    N = dev(np.zeros(case.n_v))
+    m.assemble(pbfb.HS, dev(u), N)
+    rp, col, val = m.fem_rows()
+    coef = case.eps_out * case.kappa ** 2
+    A = fem.stiffness(case.xyz, case.tets, case.eps_out) + fem.jacobian(case.xyz, case.tets, u, "HS", coef)
+    G = sp.csr_matrix((val, col, rp), shape=(case.n_v, m.n))[:, :case.n_v]
+    assert abs(G - A).max() <= 1e-12 * abs(A).max()
+    Nref = fem.nonlinear_load(case.xyz, case.tets, u, "HS", coef)
+    assert np.linalg.norm(N.cpu().numpy() - Nref) < 1e-13 * np.linalg.norm(Nref)
+
+
+def test_omega_batch_full(big):
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import fem
+    case, m = big
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.MIXED)
+    rng = np.random.default_rng(11)
+    r = np.linalg.norm(case.xyz, axis=1)
+    u = 5.0 * np.exp(-0.25 * (r - 12.0))
+    du = 0.2 * rng.standard_normal(case.n_v)
+    c = rng.standard_normal(m.n)
+    p = rng.standard_normal(m.n)
+    oms = np.array([0.5, 1.0, 2.0])
+    got = m.omega_eval(pbfb.HS, dev(u), dev(du), dev(c), dev(p), oms)
+    coef = case.eps_out * case.kappa ** 2
+    nv = case.n_v
+    for o, om in enumerate(oms):
+        w = u + om * du
+        ru = c[:nv] - fem.nonlinear_load(case.xyz, case.tets, w, "HS", coef)
+        rp = -(fem.jacobian(case.xyz, case.tets, w, "HS", coef) @ du)
+        rpp = -fem.second_derivative_load(case.xyz, case.tets, w, du, "HS", coef)
+        pu, pb_, cb = p[:nv], p[nv:], c[nv:]
+        PR = pu @ ru + pb_ @ cb + rp @ ru
+        PP = p @ p + rp @ pu
+        ref = [PR, PP, pu @ rp + rp @ rp, ru @ rpp, pu @ rpp, ru @ ru + cb @ cb, pu @ ru + pb_ @ cb, p @ p]
+        scale = max(abs(v) for v in ref)
+        assert np.abs(got[o] - ref).max() < 1e-11 * scale, om
