@@ -244,10 +244,14 @@ int pbfb_omega_eval(pbfb_mesh* mesh, int scheme, const double* u_dev, const doub
 int pbfb_energy(pbfb_mesh* mesh, const double* xL_dev, const double* xNL_dev, double* out);
 
 /* Launch-shape knobs of the float32 far field (an autotuner sets them):
- * targets per thread (1, 2, 4 or 8) and target blocks per SM used to choose
- * the number of source splits (1..64).  0 restores the built-in heuristic.
- * Results change only in float64 rounding (the float32 tile sums are the same). */
-int pbfb_set_tuning(pbfb_mesh* mesh, int nbody_targets_per_thread, int nbody_blocks_per_sm);
+ * targets per thread (1, 2, 4 or 8), target blocks per SM used to choose the
+ * number of source splits (1..64), and packed = 1 for the variant that
+ * evaluates two targets per f32x2 instruction (needs 2 or more targets per
+ * thread).  0 restores the built-in heuristic.  The unpacked shapes change
+ * results only in float64 rounding; the packed variant rounds the same float32
+ * operations (no fused reassociation differences beyond FMA contraction). */
+int pbfb_set_tuning(pbfb_mesh* mesh, int nbody_targets_per_thread, int nbody_blocks_per_sm,
+                    int nbody_packed);
 
 /* Per-kernel-class timing (CUDA events around each launch of the class) and
  * launch counters.  enable != 0 turns event timing on (it adds a little host

@@ -450,6 +450,158 @@ __global__ void __launch_bounds__(NT) k_nbody_f32(int nq, const float4* __restri
     if (ti[k] < nq) out[(int64_t)blockIdx.y * nq + ti[k]] = acc64[k];
 }
 
+// Packed variant of k_nbody_f32: two targets per 64-bit register pair, evaluated with the
+// Blackwell f32x2 instructions (add/sub/mul/fma on pairs of float32 values), which halve the
+// instruction-issue slots of the pair arithmetic; the FP32 lanes do the same work.  Sources are
+// staged pre-duplicated ((x,x),(y,y),...) so shared-memory loads give packed operands.  Tiles
+// that contain one of the thread's own targets use the scalar path for the coincident-point test.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+template <int NT, int NP, bool YUK>
+__global__ void __launch_bounds__(NT) k_nbody_f32x2(int nq, const float4* __restrict__ tgt,
+                                                    const float4* __restrict__ spos,
+                                                    const float4* __restrict__ sdl, float kappa, int per_split,
+                                                    double* __restrict__ out) {
+  // per source: (x,x),(y,y) | (z,z),(s,s) | (mx,mx),(my,my) | (mz,mz),0
+  __shared__ ulonglong2 sh[4][NT];
+  __shared__ float4 shp[NT], shd[NT];  // scalar copies for the diagonal tiles
+  constexpr int TPT = 2 * NP;
+  const int t0 = blockIdx.x * NT * TPT;
+  int ti[TPT];
+  float txs[TPT], tys[TPT], tzs[TPT];
+  f32x2 tx[NP], ty[NP], tz[NP], acc[NP];
+  double acc64[TPT];
+#pragma unroll
+  for (int k = 0; k < TPT; ++k) {
+    ti[k] = t0 + k * NT + threadIdx.x;
+    float4 p = tgt[ti[k] < nq ? ti[k] : 0];
+    txs[k] = p.x;
+    tys[k] = p.y;
+    tzs[k] = p.z;
+    acc64[k] = 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    tx[k] = pk2(txs[2 * k], txs[2 * k + 1]);
+    ty[k] = pk2(tys[2 * k], tys[2 * k + 1]);
+    tz[k] = pk2(tzs[2 * k], tzs[2 * k + 1]);
+  }
+  const int sb = blockIdx.y * per_split;
+  const int se = min(nq, sb + per_split);
+  const float nk = -kappa * 1.4426950408889634f;
+  const f32x2 nk2 = pk2(nk, nk), kap2 = pk2(kappa, kappa), one2 = pk2(1.f, 1.f);
+  for (int s0 = sb; s0 < se; s0 += NT) {
+    int j = s0 + threadIdx.x;
+    float4 p, d;
+    if (j < se) {
+      p = spos[j];
+      d = sdl[j];
+    } else {
+      p = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+      d = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    sh[0][threadIdx.x] = make_ulonglong2(pk2(p.x, p.x), pk2(p.y, p.y));
+    sh[1][threadIdx.x] = make_ulonglong2(pk2(p.z, p.z), pk2(p.w, p.w));
+    sh[2][threadIdx.x] = make_ulonglong2(pk2(d.x, d.x), pk2(d.y, d.y));
+    sh[3][threadIdx.x] = make_ulonglong2(pk2(d.z, d.z), 0ull);
+    shp[threadIdx.x] = p;
+    shd[threadIdx.x] = d;
+    __syncthreads();
+    const bool diag = (s0 < t0 + NT * TPT) && (s0 + NT > t0);
+    if (!diag) {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) acc[k] = 0ull;
+#pragma unroll 2
+      for (int jj = 0; jj < NT; ++jj) {
+        const ulonglong2 a0 = sh[0][jj], a1 = sh[1][jj], a2 = sh[2][jj], a3 = sh[3][jj];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          f32x2 dx = sub2(tx[k], a0.x), dy = sub2(ty[k], a0.y), dz = sub2(tz[k], a1.x);
+          f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+          float ra, rb;
+          upk2(r2, ra, rb);
+          f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
+          f32x2 nd = fma2(a3.x, dz, fma2(a2.y, dy, mul2(a2.x, dx)));
+          f32x2 ri2 = mul2(ri, ri);
+          if (YUK) {
+            f32x2 r = mul2(r2, ri);
+            float xa, xb;
+            upk2(mul2(nk2, r), xa, xb);
+            f32x2 e = pk2(ex2_approx(xa), ex2_approx(xb));
+            f32x2 tt = fma2(mul2(nd, fma2(kap2, r, one2)), ri2, a1.y);
+            acc[k] = fma2(tt, mul2(e, ri), acc[k]);
+          } else {
+            acc[k] = fma2(fma2(nd, ri2, a1.y), ri, acc[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        float a, b;
+        upk2(acc[k], a, b);
+        acc64[2 * k] += (double)a;
+        acc64[2 * k + 1] += (double)b;
+      }
+    } else {
+      float accs[TPT];
+#pragma unroll
+      for (int k = 0; k < TPT; ++k) accs[k] = 0.f;
+      for (int jj = 0; jj < NT; ++jj) {
+        const float4 p = shp[jj];
+        const float4 d = shd[jj];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+          if (s0 + jj == ti[k]) continue;
+          float dx = txs[k] - p.x, dy = tys[k] - p.y, dz = tzs[k] - p.z;
+          float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          float ri = rsqrt_approx(r2);
+          float nd = fmaf(d.x, dx, fmaf(d.y, dy, d.z * dz));
+          float ri2 = ri * ri;
+          if (YUK) {
+            float r = r2 * ri;
+            float e = ex2_approx(nk * r);
+            float kr1 = fmaf(kappa, r, 1.f);
+            float tt = fmaf(nd * kr1, ri2, p.w);
+            accs[k] = fmaf(tt, e * ri, accs[k]);
+          } else {
+            float tt = fmaf(nd, ri2, p.w);
+            accs[k] = fmaf(tt, ri, accs[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < TPT; ++k) acc64[k] += (double)accs[k];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < TPT; ++k)
+    if (ti[k] < nq) out[(int64_t)blockIdx.y * nq + ti[k]] = acc64[k];
+}
+
 // float64 N-body, same organisation (one target per thread).
 template <int NT, bool YUK>
 __global__ void __launch_bounds__(NT) k_nbody_f64(int nq, const double* __restrict__ s64, double kappa,
@@ -869,6 +1021,52 @@ int launch_pair_corrections(Mesh* m, Surface* s, double kappa) {
   return PBFB_OK;
 }
 
+constexpr int F32_NT = 128;
+
+// Launch shape of the float32 far field: tuning knobs if set, else 2 targets per thread with
+// the packed kernel and 32 blocks per SM of source splits for large surfaces (GB300 sweep on
+// the multi-charge sphere), one target per thread unpacked for small ones.
+void f32_shape(const Mesh* m, int nq, int* tpt, int* packed, int* bps) {
+  const bool big = nq >= 16384;
+  *tpt = m->tune_tpt > 0 ? m->tune_tpt : (big ? 2 : 1);
+  *packed = m->tune_tpt > 0 ? m->tune_packed : (big ? 1 : 0);
+  if (*tpt < 2) *packed = 0;
+  *bps = m->tune_bps > 0 ? m->tune_bps : (big ? 32 : 16);
+}
+
+void launch_nbody_f32(Mesh* m, Surface* s, double kappa, int tpt, int packed, int nsplit, int per,
+                      const float4* spos, const float4* sdl, double* val) {
+  constexpr int NT = F32_NT;
+  const int nq = s->nq;
+  const int ntb = blocks_for(nq, NT * tpt);
+  dim3 grid(ntb, nsplit);
+  const float kf = (float)kappa;
+  const bool yuk = kappa != 0.0;
+  const float4* q4 = s->qpf.p;
+#define PB_NB(T)                                                                                    \
+  if (yuk) k_nbody_f32<NT, T, true><<<grid, NT, 0, m->stream>>>(nq, q4, spos, sdl, kf, per, val);  \
+  else k_nbody_f32<NT, T, false><<<grid, NT, 0, m->stream>>>(nq, q4, spos, sdl, kf, per, val);
+#define PB_NB2(P)                                                                                   \
+  if (yuk) k_nbody_f32x2<NT, P, true><<<grid, NT, 0, m->stream>>>(nq, q4, spos, sdl, kf, per, val); \
+  else k_nbody_f32x2<NT, P, false><<<grid, NT, 0, m->stream>>>(nq, q4, spos, sdl, kf, per, val);
+  if (packed) {
+    switch (tpt) {
+      case 2: PB_NB2(1) break;
+      case 8: PB_NB2(4) break;
+      default: PB_NB2(2) break;
+    }
+  } else {
+    switch (tpt) {
+      case 1: PB_NB(1) break;
+      case 2: PB_NB(2) break;
+      case 8: PB_NB(8) break;
+      default: PB_NB(4) break;
+    }
+  }
+#undef PB_NB
+#undef PB_NB2
+}
+
 // y (+)= far-field part of the surface rows: for every test function psi_i,
 //   sum_{x_q, y_p, q != p} psi_i(x_q) w_q [ g(x_q,y_p) s_p + dg/dn_y(x_q,y_p) m_p ]
 // with s_p = cs w_p lam_h(y_p), m_p = cd w_p u_h(y_p) (kernel factors 1/(4 pi) included).
@@ -907,31 +1105,17 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
     else
       k_nbody_f64<NT, false><<<grid, NT, 0, m->stream>>>(nq, s->s64.p, kappa, per, s->val.p);
   } else {
-    constexpr int NT = 128;
-    // launch shape: targets per thread and source splits (tuning knobs; 0 = heuristic)
-    int tpt = m->tune_tpt > 0 ? m->tune_tpt : (nq >= 16384 ? 4 : 1);
-    const int bps = m->tune_bps > 0 ? m->tune_bps : 16;
-    int ntb = blocks_for(nq, NT * tpt);
-    nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * NT)));
-    int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
+    int tpt, packed, bps;
+    f32_shape(m, nq, &tpt, &packed, &bps);
+    const int ntb = blocks_for(nq, F32_NT * tpt);
+    nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * F32_NT)));
+    const int per = blocks_for(blocks_for(nq, nsplit), F32_NT) * F32_NT;
     nsplit = blocks_for(nq, per);
-    dim3 grid(ntb, nsplit);
     if ((size_t)nsplit * nq > s->val.n) {
       set_error("far-field split buffer too small");
       return PBFB_ERR_STATE;
     }
-    float kf = (float)kappa;
-    const float4* q4 = s->qpf.p;
-#define PB_NB(T)                                                                                                \
-  if (yuk) k_nbody_f32<NT, T, true><<<grid, NT, 0, m->stream>>>(nq, q4, s->spos.p, s->sdl.p, kf, per, s->val.p); \
-  else k_nbody_f32<NT, T, false><<<grid, NT, 0, m->stream>>>(nq, q4, s->spos.p, s->sdl.p, kf, per, s->val.p);
-    switch (tpt) {
-      case 1: PB_NB(1) break;
-      case 2: PB_NB(2) break;
-      case 8: PB_NB(8) break;
-      default: PB_NB(4) break;
-    }
-#undef PB_NB
+    launch_nbody_f32(m, s, kappa, tpt, packed, nsplit, per, s->spos.p, s->sdl.p, s->val.p);
   }
   PB_LAUNCHED(m);
   timer_end(m, tm, ev, (double)nq * (double)nq);
@@ -1055,23 +1239,14 @@ int bem_apply_noalloc(Mesh* m, int which, int op, const double* x, double* y) {
                                                         cd != 0.0 ? x : nullptr, 1, s->qw.p, s->nrm.p, s->qpf.p,
                                                         s->qx.p, cs * INV4PI, cd * INV4PI, 0, spos, sdl, nullptr);
   PB_LAUNCHED(m);
-  constexpr int NT = 128;
-  const bool big = nq >= 16384;
-  const int tpt = big ? 4 : 1;
-  const int ntb = blocks_for(nq, NT * tpt);
-  int nsplit = std::max(1, std::min(std::min(blocks_for(4 * 152, ntb), blocks_for(nq, 4 * NT)), NOALLOC_SPLITS));
-  const int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
+  // same kernel and targets per thread as pbfb_bem_apply; at most NOALLOC_SPLITS source splits
+  int tpt, packed, bps;
+  f32_shape(m, nq, &tpt, &packed, &bps);
+  const int ntb = blocks_for(nq, F32_NT * tpt);
+  int nsplit = std::max(1, std::min(std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * F32_NT)), NOALLOC_SPLITS));
+  const int per = blocks_for(blocks_for(nq, nsplit), F32_NT) * F32_NT;
   nsplit = blocks_for(nq, per);
-  dim3 grid(ntb, nsplit);
-  const float kf = (float)kappa;
-  const bool yuk = kappa != 0.0;
-  if (big) {
-    if (yuk) k_nbody_f32<NT, 4, true><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, spos, sdl, kf, per, val);
-    else k_nbody_f32<NT, 4, false><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, spos, sdl, kf, per, val);
-  } else {
-    if (yuk) k_nbody_f32<NT, 1, true><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, spos, sdl, kf, per, val);
-    else k_nbody_f32<NT, 1, false><<<grid, NT, 0, m->stream>>>(nq, s->qpf.p, spos, sdl, kf, per, val);
-  }
+  launch_nbody_f32(m, s, kappa, tpt, packed, nsplit, per, spos, sdl, val);
   PB_LAUNCHED(m);
   PB_TRY(test_reduce(m, s, val, nsplit, y, false));
   PB_TRY(launch_csr_spmv(m, s->nv, s->c_ptr.p, s->c_col.p, op == 0 ? s->corrV.p : s->corrK.p, x, y, true));

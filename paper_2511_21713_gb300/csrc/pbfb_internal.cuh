@@ -174,6 +174,7 @@ struct Mesh {
   int coop_blocks = 0;              // grid of the cooperative inner PCG (-1: not available)
   int tune_tpt = 0;                 // float32 far field: targets per thread (0 = heuristic)
   int tune_bps = 0;                 // float32 far field: target blocks per SM for the source split
+  int tune_packed = 0;              // float32 far field: 1 = packed f32x2 kernel
   // Newton workspace
   DBuf<double> xL, xNL, phi, cvec, dvec, du, pvec, tmp, Nvec, bvec, xout, urb;
   std::vector<double> qz_h;  // charges (host copy)

@@ -104,7 +104,7 @@ def load():
         "pbfb_omega_eval": (I, [P, I, P, P, P, P, P, I, P]),
         "pbfb_energy": (I, [P, P, P, P]),
         "pbfb_profile": (I, [P, I, I, P]),
-        "pbfb_set_tuning": (I, [P, I, I]),
+        "pbfb_set_tuning": (I, [P, I, I, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -242,8 +242,8 @@ class Mesh:
         _check(load().pbfb_energy(self.h, _ptr(xL_dev), _ptr(xNL_dev), _ptr(out)))
         return out
 
-    def set_tuning(self, targets_per_thread=0, blocks_per_sm=0):
-        _check(load().pbfb_set_tuning(self.h, targets_per_thread, blocks_per_sm))
+    def set_tuning(self, targets_per_thread=0, blocks_per_sm=0, packed=0):
+        _check(load().pbfb_set_tuning(self.h, targets_per_thread, blocks_per_sm, packed))
 
     def profile(self, enable=True, reset=False):
         st = np.zeros(16)
