@@ -63,7 +63,10 @@ enum {
  * float64.  PBFB_FLOAT2 (pbfb_set_params / step calls only): far field in
  * float-float. */
 enum { PBFB_FP64 = 0, PBFB_MIXED = 1, PBFB_FLOAT2 = 2 };
-enum { PBFB_LINEAR = 0, PBFB_T3 = 1, PBFB_HS = 2 };
+/* Nonlinearity F of the load N(u) = eps_s kappa^2 int F(u_h) v: u, the Taylor
+ * polynomials of sinh of degree 3, 5, 7, or sinh (Sec. 3.2 schemes). */
+enum { PBFB_LINEAR = 0, PBFB_T3 = 1, PBFB_HS = 2, PBFB_T5 = 3, PBFB_T7 = 4 };
+enum { PBFB_NEWTON = 0, PBFB_PICARD = 1 };
 enum { PBFB_GAMMA_M = 0, PBFB_GAMMA_S = 1 };
 enum { PBFB_PRECOND_JACOBI = 0, PBFB_PRECOND_BLOCK = 1 };
 
@@ -94,7 +97,13 @@ typedef struct pbfb_newton_opts {
   int max_gmres;        /* GMRES iterations per linear solve */
   int restart;          /* GMRES restart length (<= 400) */
   int max_omega_iters;
-  int first_scheme;     /* PBFB_T3 (paper) or PBFB_HS */
+  int n_taylor;         /* iterations 0..n_taylor-1 use taylor[k], later ones sinh (0..4);
+                           default 1 with taylor[0] = PBFB_T3 (the paper's T3-HS) */
+  int taylor[4];        /* PBFB_T3 / PBFB_T5 / PBFB_T7 (e.g. T3-T5-T7-T7-HS) */
+  int method;           /* PBFB_NEWTON (Sec. 2.4.2) or PBFB_PICARD (Sec. 2.4.1: the same
+                           increment with J = 0 in the linear operator; omega by the direct
+                           secant of Appendix A, Eq. SEC_FD, and the R_e reuse rule) */
+  double R_e;           /* Picard: recompute omega only when e_{k-1}/e_k < R_e (0: always) */
   int omega_search;     /* 1: automatic omega; 0: constant omega0_first / omega0_rest */
   int precond;          /* PBFB_PRECOND_JACOBI: diagonal of the coupled operator;
                            PBFB_PRECOND_BLOCK: flexible GMRES whose preconditioner runs

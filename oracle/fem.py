@@ -10,8 +10,9 @@ Eqs. general_nonlinear / Vector_c:
   J(u)_ij    = eps_s kappa^2 int F'(u_h) v_i v_j             (Jacobian of N, Eq. NR_main)
   N2(u)[D,D]_i = eps_s kappa^2 int F''(u_h) D_h^2 v_i        (Appendix A, [Delta]^2 d^2 N)
 
-with F = u (linear), u + u^3/6 (T3, the cubic Taylor scheme of the first
-Newton iteration) or sinh u (HS), Sec. 3.2 "Gradually incorporating sinh".
+with F = u (linear), the Taylor polynomials of sinh of degree 3, 5, 7 (T3, T5,
+T7: the schemes of the first iterations) or sinh u (HS), Sec. 3.2 "Gradually
+incorporating sinh".
 Volume integrals of F use the 14-point rule; stiffness is exact for P1.
 """
 from __future__ import annotations
@@ -28,6 +29,13 @@ def F_scheme(scheme: str, u: np.ndarray):
         return u, np.ones_like(u), np.zeros_like(u)
     if scheme == 'T3':
         return u + u ** 3 / 6.0, 1.0 + 0.5 * u * u, u
+    if scheme == 'T5':
+        return (u + u ** 3 / 6.0 + u ** 5 / 120.0, 1.0 + 0.5 * u * u + u ** 4 / 24.0,
+                u + u ** 3 / 6.0)
+    if scheme == 'T7':
+        return (u + u ** 3 / 6.0 + u ** 5 / 120.0 + u ** 7 / 5040.0,
+                1.0 + 0.5 * u * u + u ** 4 / 24.0 + u ** 6 / 720.0,
+                u + u ** 3 / 6.0 + u ** 5 / 120.0)
     if scheme == 'HS':
         s = np.sinh(u)
         return s, np.cosh(u), s

@@ -52,9 +52,11 @@ class Opts:
     max_gmres: int = 1000
     restart: int = 200
     max_omega_iters: int = 30
-    first_scheme: str = 'T3'
+    taylor: tuple = ('T3',)       # schemes of the first iterations, then sinh (Sec. 3.2: T3-HS)
     linear_solver: str = 'gmres'  # 'gmres' (the paper's) or 'direct' (sparse LU)
     omega_search: bool = True     # False: constant omega = omega0_* every iteration
+    method: str = 'newton'        # 'newton' (Sec. 2.4.2) or 'picard' (Sec. 2.4.1)
+    R_e: float = 1.4              # Picard: recompute omega only when e_{k-1} / e_k < R_e (0 = always)
 
 
 class Problem:
@@ -274,36 +276,77 @@ def omega_search(P: Problem, u, du, c, p, d0n2, scheme, omega0, opts: Opts, trac
         if not np.isfinite(om):
             break
     if not ok:
-        def gd(o):
-            D = omega_dots(P, u, du, c, p, o, scheme)
-            return o * D['PP'] + D['PR'], D
-        lo, hi = 0.0, None
-        for j in range(1, 17):
-            o = opts.omega_max * j / 16.0
-            g, _ = gd(o)
-            evals += 1
-            if not np.isfinite(g) or g >= 0.0:
-                hi = o
-                break
-            lo = o
-        if hi is None:
-            om = opts.omega_max
-        else:
-            for _ in range(20):
-                mid = 0.5 * (lo + hi)
-                g, _ = gd(mid)
-                evals += 1
-                if np.isfinite(g) and g < 0.0:
-                    lo = mid
-                else:
-                    hi = mid
-            om = 0.5 * (lo + hi)
-        D = omega_dots(P, u, du, c, p, om, scheme)
-        evals += 1
-        if not (np.isfinite(dnorm2(D, om)) and dnorm2(D, om) < d0n2):
-            raise RuntimeError('omega search failed')
+        om = _fallback(P, u, du, c, p, d0n2, scheme, opts)
+        evals += 38
         trace['fallback'] = trace.get('fallback', 0) + 1
     trace['omega_evals'].append(evals)
+    return om
+
+
+def picard_omega(P: Problem, u, du, c, p, d0n2, scheme, omega0, opts: Opts, trace):
+    """Relaxation factor of a Picard step: the direct secant of Appendix A (Eq. SEC_FD) through
+    (0, f_d(0) = 1) and (omega0, f_d(omega0)), continued by secant steps (Eq. Met_Secante) until
+    |f_d| < Tol_omega; accepted under the same decrease test as the Newton search, else the same
+    scan-and-bisect fallback."""
+    o_prev, f_prev = 0.0, 1.0
+    o_cur = omega0
+    D = omega_dots(P, u, du, c, p, o_cur, scheme)
+    f_cur = fd_and_derivative(D, o_cur)[0]
+    evals = 1
+    ok = False
+    for _ in range(opts.max_omega_iters):
+        if not np.isfinite(f_cur):
+            break
+        if abs(f_cur) < opts.tol_omega:
+            dn = dnorm2(D, o_cur)
+            ok = 0.0 < o_cur <= opts.omega_max and np.isfinite(dn) and dn < d0n2
+            break
+        den = f_prev - f_cur
+        if den == 0.0 or not np.isfinite(den):
+            break
+        o_next = o_prev - (o_prev - o_cur) * f_prev / den
+        if not np.isfinite(o_next):
+            break
+        o_prev, f_prev, o_cur = o_cur, f_cur, o_next
+        D = omega_dots(P, u, du, c, p, o_cur, scheme)
+        f_cur = fd_and_derivative(D, o_cur)[0]
+        evals += 1
+    if ok:
+        trace['omega_evals'].append(evals)
+        return o_cur
+    om = _fallback(P, u, du, c, p, d0n2, scheme, opts)
+    trace['fallback'] = trace.get('fallback', 0) + 1
+    trace['omega_evals'].append(evals + 38)
+    return om
+
+
+def _fallback(P, u, du, c, p, d0n2, scheme, opts):
+    """Scan g_d at omega_max j / 16 and bisect the first sign change (reading R10)."""
+    def gd(o):
+        D = omega_dots(P, u, du, c, p, o, scheme)
+        return o * D['PP'] + D['PR']
+    lo, hi = 0.0, None
+    for j in range(1, 17):
+        o = opts.omega_max * j / 16.0
+        g = gd(o)
+        if not np.isfinite(g) or g >= 0.0:
+            hi = o
+            break
+        lo = o
+    if hi is None:
+        om = opts.omega_max
+    else:
+        for _ in range(20):
+            mid = 0.5 * (lo + hi)
+            g = gd(mid)
+            if np.isfinite(g) and g < 0.0:
+                lo = mid
+            else:
+                hi = mid
+        om = 0.5 * (lo + hi)
+    D = omega_dots(P, u, du, c, p, om, scheme)
+    if not (np.isfinite(dnorm2(D, om)) and dnorm2(D, om) < d0n2):
+        raise RuntimeError('omega search failed')
     return om
 
 
@@ -358,38 +401,51 @@ def solve(P: Problem, opts: Opts = None, linear_only=False):
     om_last = None
     e_prev = None
     k = 0
+    picard = opts.method == 'picard'
+    e_prev2 = None
     for k in range(opts.max_newton):
-        scheme = opts.first_scheme if k == 0 else 'HS'
+        scheme = opts.taylor[k] if k < len(opts.taylor) else 'HS'
         Phi = xL + xNL
         u = Phi[:P.nv]
         Nu = P.N(u, scheme)
         c = P.b - P.apply(Phi)                                  # b - Acal(0) Phi
         d = c - P.pad(Nu)
-        Jm = P.J(u, scheme)
+        # Newton: Acal(J) Delta = d (Eq. NR_main); Picard: Acal(0) Delta = d, Delta = Phi~ - Phi_NL
+        # (Eq. Ec_NL_Previo2 written for the increment)
+        Jm = None if picard else P.J(u, scheme)
         du, its = linear_solve(P, Jm, d, tol, opts)
         trace['gmres'].append(its)
         trace['scheme'].append(scheme)
         trace['dnorm'].append(float(np.linalg.norm(d)))
         if not opts.omega_search:
             om = opts.omega0_first if k == 0 else opts.omega0_rest
-        elif k > 0 and e_prev is not None and e_prev < opts.L_e and om_last is not None:
+        elif (not picard) and k > 0 and e_prev is not None and e_prev < opts.L_e and om_last is not None:
+            om = om_last
+            trace['omega_evals'].append(0)
+        elif picard and om_last is not None and e_prev2 is not None and opts.R_e > 0 \
+                and not (e_prev2 / e_prev < opts.R_e):
+            # R_e rule (Appendix B): keep omega while the error still falls by R_e per step
             om = om_last
             trace['omega_evals'].append(0)
         else:
             p = -P.apply(du)
-            om = omega_search(P, u, du[:P.nv], c, p, float(d @ d), scheme,
-                              opts.omega0_first if k == 0 else opts.omega0_rest, opts, trace)
+            om0 = opts.omega0_first if k == 0 else opts.omega0_rest
+            if picard:
+                om = picard_omega(P, u, du[:P.nv], c, p, float(d @ d), scheme, om0, opts, trace)
+            else:
+                om = omega_search(P, u, du[:P.nv], c, p, float(d @ d), scheme, om0, opts, trace)
         om_last = om
         xNL = xNL + om * du
         e = om * float(np.linalg.norm(du))
         trace['omega'].append(om)
         trace['e'].append(e)
+        e_prev2 = e_prev
         e_prev = e
         if e < 1250.0 * tol:
             tol = max(0.1 * tol, opts.tol_gmres)
         if e < opts.tol_nl:
             break
     else:
-        raise RuntimeError('Newton did not converge')
+        raise RuntimeError('nonlinear iteration did not converge')
     t, LC, NC, dG = energy(P, xL, xNL)
     return Result(xL + xNL, xL, xNL, t, LC, NC, dG, k + 1, trace)

@@ -25,10 +25,21 @@ __device__ __forceinline__ void scheme_F(int scheme, double u, double& F, double
     F = u;
     Fp = 1.0;
     Fpp = 0.0;
-  } else if (scheme == PBFB_T3) {
-    F = u + u * u * u * (1.0 / 6.0);
-    Fp = 1.0 + 0.5 * u * u;
-    Fpp = u;
+  } else if (scheme == PBFB_T3 || scheme == PBFB_T5 || scheme == PBFB_T7) {
+    // Taylor polynomials of sinh: F = sum u^(2j+1)/(2j+1)!, F' = sum u^(2j)/(2j)!, F'' = F of one degree less
+    const double u2 = u * u;
+    const int deg = scheme == PBFB_T3 ? 3 : (scheme == PBFB_T5 ? 5 : 7);
+    double term_odd = u, term_even = 1.0;  // u^(2j+1)/(2j+1)!, u^(2j)/(2j)!
+    F = u;
+    Fp = 1.0;
+    Fpp = 0.0;
+    for (int k = 3; k <= deg; k += 2) {
+      Fpp += term_odd;                            // F'' gets the odd terms up to degree deg-2
+      term_even *= u2 / ((k - 2) * (k - 1));      // u^(k-1)/(k-1)!
+      term_odd *= u2 / ((k - 1) * k);             // u^k/k!
+      F += term_odd;
+      Fp += term_even;
+    }
   } else {
     double e = exp(u);
     double ei = 1.0 / e;

@@ -786,6 +786,91 @@ static int omega_eval(Mesh* m, int scheme, const double* u, const double* du, co
 
 static inline double dnorm2(const double* D, double om) { return om * om * D[7] + 2.0 * om * D[6] + D[5]; }
 
+// Fallback of both searches (reading R10): scan g_d(omega) = omega (p+r').p + (p+r').r at
+// omega_max j / 16, j = 1..16 (one batched evaluation), bisect its first sign change 20 times,
+// accept only if ||d(omega)|| < ||d(0)||.
+static int omega_fallback(Mesh* m, int scheme, const double* u, const double* du, const double* c, const double* p,
+                          double d0n2, const pbfb_newton_opts& o, double* omega_out, int* evals) {
+  double D[8 * 16];
+  double om;
+  double oms[16];
+  for (int j = 0; j < 16; ++j) oms[j] = o.omega_max * (j + 1) / 16.0;
+  PB_TRY(omega_eval(m, scheme, u, du, c, p, oms, 16, D));
+  ++*evals;
+  double lo = 0.0, hi = -1.0;
+  for (int j = 0; j < 16; ++j) {
+    double gdv = oms[j] * D[8 * j + 1] + D[8 * j + 0];
+    if (!std::isfinite(gdv) || gdv >= 0.0) {
+      hi = oms[j];
+      break;
+    }
+    lo = oms[j];
+  }
+  if (hi < 0.0) {
+    om = o.omega_max;
+  } else {
+    for (int it = 0; it < 20; ++it) {
+      double mid = 0.5 * (lo + hi);
+      PB_TRY(omega_eval(m, scheme, u, du, c, p, &mid, 1, D));
+      ++*evals;
+      double gdv = mid * D[1] + D[0];
+      if (std::isfinite(gdv) && gdv < 0.0)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    om = 0.5 * (lo + hi);
+  }
+  PB_TRY(omega_eval(m, scheme, u, du, c, p, &om, 1, D));
+  ++*evals;
+  double dn = dnorm2(D, om);
+  if (!(std::isfinite(dn) && dn < d0n2)) {
+    set_error("omega search: no relaxation factor in (0, %g] reduces ||d||", o.omega_max);
+    return PBFB_ERR_OMEGA;
+  }
+  *omega_out = om;
+  return PBFB_OK;
+}
+
+// Picard relaxation factor: the direct secant of Appendix A (Eq. SEC_FD) through (0, f_d(0) = 1)
+// and (omega0, f_d(omega0)), continued by secant steps (Eq. Met_Secante) until |f_d| < Tol_omega;
+// accepted under the decrease test, else the shared fallback.
+static int picard_omega(Mesh* m, int scheme, const double* u, const double* du, const double* c, const double* p,
+                        double d0n2, double omega0, const pbfb_newton_opts& o, double* omega_out, int* evals,
+                        int* fallback) {
+  double D[8];
+  double o_prev = 0.0, f_prev = 1.0, o_cur = omega0;
+  PB_TRY(omega_eval(m, scheme, u, du, c, p, &o_cur, 1, D));
+  *evals = 1;
+  double f_cur = -D[0] / D[1] - o_cur;
+  bool ok = false;
+  for (int it = 0; it < o.max_omega_iters; ++it) {
+    if (!std::isfinite(f_cur)) break;
+    if (std::fabs(f_cur) < o.tol_omega) {
+      double dn = dnorm2(D, o_cur);
+      ok = o_cur > 0.0 && o_cur <= o.omega_max && std::isfinite(dn) && dn < d0n2;
+      break;
+    }
+    double den = f_prev - f_cur;
+    if (den == 0.0 || !std::isfinite(den)) break;
+    double o_next = o_prev - (o_prev - o_cur) * f_prev / den;
+    if (!std::isfinite(o_next)) break;
+    o_prev = o_cur;
+    f_prev = f_cur;
+    o_cur = o_next;
+    PB_TRY(omega_eval(m, scheme, u, du, c, p, &o_cur, 1, D));
+    ++*evals;
+    f_cur = -D[0] / D[1] - o_cur;
+  }
+  if (ok) {
+    *omega_out = o_cur;
+    return PBFB_OK;
+  }
+  PB_TRY(omega_fallback(m, scheme, u, du, c, p, d0n2, o, omega_out, evals));
+  ++*fallback;
+  return PBFB_OK;
+}
+
 static int omega_search(Mesh* m, int scheme, const double* u, const double* du, const double* c, const double* p,
                         double d0n2, double omega0, const pbfb_newton_opts& o, double* omega_out, int* evals,
                         int* fallback) {
@@ -811,42 +896,7 @@ static int omega_search(Mesh* m, int scheme, const double* u, const double* du, 
     if (!std::isfinite(om)) break;
   }
   if (!ok) {
-    // scan g_d(omega) = omega (p+r').p + (p+r').r at omega_max j / 16, j = 1..16 (one batch)
-    double oms[16];
-    for (int j = 0; j < 16; ++j) oms[j] = o.omega_max * (j + 1) / 16.0;
-    PB_TRY(omega_eval(m, scheme, u, du, c, p, oms, 16, D));
-    ++*evals;
-    double lo = 0.0, hi = -1.0;
-    for (int j = 0; j < 16; ++j) {
-      double gdv = oms[j] * D[8 * j + 1] + D[8 * j + 0];
-      if (!std::isfinite(gdv) || gdv >= 0.0) {
-        hi = oms[j];
-        break;
-      }
-      lo = oms[j];
-    }
-    if (hi < 0.0) {
-      om = o.omega_max;
-    } else {
-      for (int it = 0; it < 20; ++it) {
-        double mid = 0.5 * (lo + hi);
-        PB_TRY(omega_eval(m, scheme, u, du, c, p, &mid, 1, D));
-        ++*evals;
-        double gdv = mid * D[1] + D[0];
-        if (std::isfinite(gdv) && gdv < 0.0)
-          lo = mid;
-        else
-          hi = mid;
-      }
-      om = 0.5 * (lo + hi);
-    }
-    PB_TRY(omega_eval(m, scheme, u, du, c, p, &om, 1, D));
-    ++*evals;
-    double dn = dnorm2(D, om);
-    if (!(std::isfinite(dn) && dn < d0n2)) {
-      set_error("omega search: no relaxation factor in (0, %g] reduces ||d||", o.omega_max);
-      return PBFB_ERR_OMEGA;
-    }
+    PB_TRY(omega_fallback(m, scheme, u, du, c, p, d0n2, o, &om, evals));
     ++*fallback;
   }
   *omega_out = om;
@@ -904,11 +954,17 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   }
   if (!(o.tol_nl > 0) || !(o.tol_gmres > 0) || !(o.tol_gmres0 > 0) || !(o.tol_omega > 0) || o.max_newton < 1 ||
       o.max_gmres < 1 || !(o.omega_max > 0) || o.max_omega_iters < 1 ||
-      (o.first_scheme != PBFB_T3 && o.first_scheme != PBFB_HS && o.first_scheme != PBFB_LINEAR) ||
+      o.n_taylor < 0 || o.n_taylor > 4 || (o.method != PBFB_NEWTON && o.method != PBFB_PICARD) || !(o.R_e >= 0) ||
       (o.precision != PBFB_FP64 && o.precision != PBFB_MIXED)) {
     set_error("solve: invalid options");
     return PBFB_ERR_INVALID;
   }
+  for (int k = 0; k < o.n_taylor; ++k)
+    if (o.taylor[k] != PBFB_T3 && o.taylor[k] != PBFB_T5 && o.taylor[k] != PBFB_T7 && o.taylor[k] != PBFB_HS &&
+        o.taylor[k] != PBFB_LINEAR) {
+      set_error("solve: invalid Taylor schedule entry %d", o.taylor[k]);
+      return PBFB_ERR_INVALID;
+    }
   PB_TRY(set_params(m, eps_in, eps_out, kappa, T, o.precision));
   const int n = m->n, nv = m->nv;
   for (auto* b : {&m->xL, &m->xNL, &m->phi, &m->cvec, &m->dvec, &m->du, &m->pvec, &m->Nvec, &m->tmp, &m->bvec})
@@ -935,11 +991,12 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   }
   auto t1 = clk::now();
   PB_CUDA(cudaMemsetAsync(m->xNL.p, 0, n * sizeof(double), m->stream));
-  double om_last = -1.0, e_prev = -1.0;
+  double om_last = -1.0, e_prev = -1.0, e_prev2 = -1.0;
+  const bool picard = o.method == PBFB_PICARD;
   bool converged = false;
   int k = 0;
   for (k = 0; k < o.max_newton; ++k) {
-    const int scheme = k == 0 ? o.first_scheme : PBFB_HS;
+    const int scheme = k < o.n_taylor ? o.taylor[k] : PBFB_HS;
     PB_TRY(launch_axpby(m, n, 1.0, m->xL.p, 1.0, m->xNL.p, m->phi.p));
     // c = b - Acal(0) Phi: the nonlinear residual's far field in float64 (FP64) or float-float (MIXED)
     PB_TRY(clear_jacobian(m));
@@ -958,6 +1015,9 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
       if (res) *res = R;
       return R.status;
     }
+    // Newton: Acal(J) Delta = d (Eq. NR_main).  Picard: Acal(0) Delta = d, the increment form of
+    // Eq. Ec_NL_Previo2 (Delta = Phi~_NL - Phi_NL)
+    if (picard) PB_TRY(clear_jacobian(m));
     st = gmres(m, m->dvec.p, m->du.p, tol, o.restart, o.max_gmres, o.precond, o.inner_iters, &its, &rel);
     if (k < PBFB_MAX_TRACE) R.gmres_iters[k] = its;
     if (st) {
@@ -970,15 +1030,22 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
     int evals = 0;
     if (!o.omega_search) {
       om = k == 0 ? o.omega0_first : o.omega0_rest;
-    } else if (k > 0 && e_prev >= 0.0 && e_prev < o.L_e && om_last > 0.0) {
+    } else if (!picard && k > 0 && e_prev >= 0.0 && e_prev < o.L_e && om_last > 0.0) {
+      om = om_last;
+    } else if (picard && om_last > 0.0 && e_prev2 > 0.0 && e_prev > 0.0 && o.R_e > 0.0 &&
+               !(e_prev2 / e_prev < o.R_e)) {
+      // R_e rule (Appendix B): keep omega while the error still falls by R_e per step
       om = om_last;
     } else {
       // p = -Acal(0) Delta with the GMRES operator (the root of f_d is needed only to Tol_omega)
       PB_TRY(clear_jacobian(m));
       PB_TRY(apply(m, m->du.p, m->pvec.p));
       PB_TRY(launch_axpby(m, n, -1.0, m->pvec.p, 0.0, nullptr, m->pvec.p));
-      st = omega_search(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, d2,
-                        k == 0 ? o.omega0_first : o.omega0_rest, o, &om, &evals, &R.omega_fallbacks);
+      const double om0 = k == 0 ? o.omega0_first : o.omega0_rest;
+      st = picard ? picard_omega(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, d2, om0, o, &om, &evals,
+                                 &R.omega_fallbacks)
+                  : omega_search(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, d2, om0, o, &om, &evals,
+                                 &R.omega_fallbacks);
       if (st) {
         R.status = st;
         R.newton_iters = k + 1;
@@ -1002,6 +1069,7 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
       if (res) *res = R;
       return R.status;
     }
+    e_prev2 = e_prev;
     e_prev = e;
     if (e < 1250.0 * tol) tol = std::max(0.1 * tol, o.tol_gmres);
     if (e < o.tol_nl) {
@@ -1012,7 +1080,7 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   R.newton_iters = std::min(k + 1, o.max_newton);
   auto t2 = clk::now();
   if (!converged) {
-    set_error("Newton did not converge in %d iterations", o.max_newton);
+    set_error("%s did not converge in %d iterations", picard ? "Picard" : "Newton", o.max_newton);
     R.status = PBFB_ERR_NEWTON_NOCONV;
     if (res) *res = R;
     return R.status;
@@ -1072,7 +1140,11 @@ void pbfb_default_opts(pbfb_newton_opts* o) {
   o->max_gmres = 1000;
   o->restart = 200;
   o->max_omega_iters = 30;
-  o->first_scheme = PBFB_T3;
+  o->n_taylor = 1;
+  o->taylor[0] = PBFB_T3;
+  o->taylor[1] = o->taylor[2] = o->taylor[3] = PBFB_HS;
+  o->method = PBFB_NEWTON;
+  o->R_e = 1.4;
   o->omega_search = 1;
   o->precond = PBFB_PRECOND_BLOCK;
   o->inner_iters = 30;
@@ -1213,7 +1285,7 @@ int pbfb_set_params(pbfb_mesh* h, double eps_in, double eps_out, double kappa, d
 int pbfb_assemble(pbfb_mesh* h, int scheme, const double* u_dev, double* N_out_dev) {
   PB_HANDLE(h);
   PB_NEED_PARAMS;
-  if (!u_dev || (scheme != PBFB_LINEAR && scheme != PBFB_T3 && scheme != PBFB_HS)) {
+  if (!u_dev || scheme < PBFB_LINEAR || scheme > PBFB_T7) {
     pbfb::set_error("assemble: bad argument");
     return PBFB_ERR_INVALID;
   }
@@ -1311,8 +1383,7 @@ int pbfb_omega_eval(pbfb_mesh* h, int scheme, const double* u_dev, const double*
                     const double* p_dev, const double* omegas, int n_omega, double* dots) {
   PB_HANDLE(h);
   PB_NEED_PARAMS;
-  if (!u_dev || !du_dev || !c_dev || !p_dev || !omegas || !dots ||
-      (scheme != PBFB_LINEAR && scheme != PBFB_T3 && scheme != PBFB_HS)) {
+  if (!u_dev || !du_dev || !c_dev || !p_dev || !omegas || !dots || scheme < PBFB_LINEAR || scheme > PBFB_T7) {
     pbfb::set_error("omega_eval: bad argument");
     return PBFB_ERR_INVALID;
   }

@@ -19,7 +19,8 @@ PBFB_OK = 0
 ERRORS = {1: "INVALID", 2: "CUDA", 3: "GMRES_NOCONV", 4: "NEWTON_NOCONV", 5: "OMEGA",
           6: "NONFINITE", 7: "OOM", 8: "STATE"}
 FP64, MIXED, FLOAT2 = 0, 1, 2
-LINEAR, T3, HS = 0, 1, 2
+LINEAR, T3, HS, T5, T7 = 0, 1, 2, 3, 4
+NEWTON, PICARD = 0, 1
 GAMMA_M, GAMMA_S = 0, 1
 JACOBI, BLOCK = 0, 1
 MAX_TRACE = 64
@@ -47,7 +48,8 @@ class NewtonOpts(ctypes.Structure):
                 ("omega0_first", ctypes.c_double), ("omega0_rest", ctypes.c_double),
                 ("omega_max", ctypes.c_double), ("max_newton", ctypes.c_int),
                 ("max_gmres", ctypes.c_int), ("restart", ctypes.c_int),
-                ("max_omega_iters", ctypes.c_int), ("first_scheme", ctypes.c_int),
+                ("max_omega_iters", ctypes.c_int), ("n_taylor", ctypes.c_int),
+                ("taylor", ctypes.c_int * 4), ("method", ctypes.c_int), ("R_e", ctypes.c_double),
                 ("omega_search", ctypes.c_int), ("precond", ctypes.c_int),
                 ("inner_iters", ctypes.c_int)]
 
@@ -134,6 +136,10 @@ def default_opts(**kw) -> NewtonOpts:
     for k, v in kw.items():
         if not hasattr(o, k):
             raise KeyError(k)
+        if k == "taylor":
+            v = list(v)
+            o.n_taylor = len(v)
+            v = (ctypes.c_int * 4)(*(v + [0] * (4 - len(v))))
         setattr(o, k, v)
     return o
 

@@ -55,14 +55,16 @@ def test_surface_vertex_order(pair):
     assert (m.n_v, m.n_m, m.n_s, m.n) == (P.nv, P.nm, P.ns, P.n)
 
 
-@pytest.mark.parametrize("scheme", ["linear", "T3", "HS"])
+SCHEMES = {"linear": 0, "T3": 1, "HS": 2, "T5": 3, "T7": 4}
+
+
+@pytest.mark.parametrize("scheme", ["linear", "T3", "T5", "T7", "HS"])
 def test_fem_rows_and_load(pair, scheme):
-    from paper_2511_21713_gb300 import pbfb
     case, m, P = pair
     m.set_params(case.eps_in, case.eps_out, case.kappa, case.T)
     u = _u_field(P, 1)
     N_dev = dev(np.zeros(P.nv))
-    m.assemble({"linear": pbfb.LINEAR, "T3": pbfb.T3, "HS": pbfb.HS}[scheme], dev(u), N_dev)
+    m.assemble(SCHEMES[scheme], dev(u), N_dev)
     rp, col, val = m.fem_rows()
     G = sp.csr_matrix((val, col, rp), shape=(P.nv, P.n))
     O = sp.hstack([P.A + P.J(u, scheme), P.B_um, P.B_us]).tocsr()
@@ -153,8 +155,8 @@ def test_omega_batch(pair):
     c = rng.standard_normal(P.n)
     p = rng.standard_normal(P.n)
     oms = np.array([0.0, 0.5, 1.0, 1.7, 2.0, 3.9])
-    for scheme, sname in ((pbfb.T3, "T3"), (pbfb.HS, "HS")):
-        got = m.omega_eval(scheme, dev(u), dev(du), dev(c), dev(p), oms)
+    for sname in ("T3", "T5", "T7", "HS"):
+        got = m.omega_eval(SCHEMES[sname], dev(u), dev(du), dev(c), dev(p), oms)
         for o, om in enumerate(oms):
             D = pb.omega_dots(P, u, du, c, p, om, sname)
             ref = [D["PR"], D["PP"], D["PRp"], D["RRpp"], D["PRpp"], D["RR"], D["pr"], D["pp"]]
@@ -213,6 +215,27 @@ def test_paper_default_trace(pair):
     for g, o in zip(res["gmres"], R.trace["gmres"]):
         assert abs(g - o) <= 2
     assert abs(res["total"] - R.total) < 1e-4 * abs(R.total)
+
+
+def test_picard_and_taylor_schedules(pair):
+    """Picard (Sec. 2.4.1, direct-secant omega, R_e rule) and the T3-T5-T7-T7-HS schedule reach
+    the oracle's discrete solution; at the paper's tolerances Picard follows the oracle's path."""
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    ref = pb.solve(P, pb.Opts(**TIGHT))
+    for gkw, okw in ((dict(method=pbfb.PICARD, omega0_first=0.5, omega0_rest=0.5),
+                      dict(method="picard", omega0_first=0.5, omega0_rest=0.5)),
+                     (dict(taylor=[pbfb.T3, pbfb.T5, pbfb.T7, pbfb.T7]), dict(taylor=("T3", "T5", "T7", "T7")))):
+        tight = dict(tol_gmres0=1e-12, tol_gmres=1e-12, tol_nl=1e-10)
+        x, res = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.default_opts(**gkw, **tight))
+        assert abs(res["total"] - ref.total) < 1e-9 * abs(ref.total)
+        assert rel(x, ref.x) < 1e-8
+        _, rp = m.solve(case.eps_in, case.eps_out, case.kappa, case.T,
+                        pbfb.default_opts(precond=pbfb.JACOBI, **gkw))
+        Ro = pb.solve(P, pb.Opts(**okw))
+        assert rp["newton_iters"] == Ro.newton_iters
+        assert np.allclose(rp["omega"], Ro.trace["omega"], rtol=1e-3, atol=1e-3)
 
 
 def test_deterministic(pair):

@@ -67,7 +67,7 @@ def test_scheme_functions():
     assert np.abs(fem.F_scheme('T3', small)[0] - np.sinh(small)).max() < 1e-7
 
 
-@pytest.mark.parametrize("scheme", ["T3", "HS"])
+@pytest.mark.parametrize("scheme", ["T3", "T5", "T7", "HS"])
 def test_jacobian_and_second_derivative_by_finite_differences(tiny_case, scheme):
     c = tiny_case
     rng = np.random.default_rng(1)

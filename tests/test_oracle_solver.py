@@ -191,3 +191,40 @@ def test_paper_default_options_trace(small_problem):
     assert all(0 < w <= 4 for w in R.trace['omega'])
     assert R.trace['scheme'][0] == 'T3' and set(R.trace['scheme'][1:]) == {'HS'}
     assert abs(R.total - Rt.total) / abs(Rt.total) < 1e-4
+
+
+def test_taylor_schedules_and_picard_reach_the_newton_solution(tiny_problem):
+    """T3-T5-HS, T3-T5-T7-T7-HS (Sec. 3.2) and Picard (Sec. 2.4.1) iterate to the same discrete
+    fixed point as T3-HS Newton: the nonlinear system does not depend on the path."""
+    P = tiny_problem
+    ref = pb.solve(P, TIGHT)
+    tight = dict(tol_gmres0=1e-12, tol_gmres=1e-12, tol_nl=1e-10)
+    for o in (pb.Opts(taylor=('T3', 'T5'), **tight), pb.Opts(taylor=('T3', 'T5', 'T7', 'T7'), **tight),
+              pb.Opts(taylor=(), **tight),
+              pb.Opts(method='picard', omega0_first=0.5, omega0_rest=0.5, **tight)):
+        R = pb.solve(P, o)
+        assert abs(R.total - ref.total) < 1e-10 * abs(ref.total), (o.method, o.taylor)
+        assert np.linalg.norm(R.x - ref.x) < 1e-8 * np.linalg.norm(ref.x)
+
+
+def test_picard_defaults_converge_slower_than_newton(tiny_problem):
+    P = tiny_problem
+    Rn = pb.solve(P, pb.Opts())
+    Rp = pb.solve(P, pb.Opts(method='picard', omega0_first=0.5, omega0_rest=0.5))
+    assert Rp.newton_iters > Rn.newton_iters
+    assert all(0 < w < 1.0 for w in Rp.trace['omega'])
+    assert abs(Rp.total - Rn.total) < 1e-5 * abs(Rn.total)
+
+
+def test_taylor_schemes_are_sinh_series():
+    from oracle import fem
+    import math
+    u = np.linspace(-2, 2, 9)
+    for name, deg in (('T3', 3), ('T5', 5), ('T7', 7)):
+        F, Fp, Fpp = fem.F_scheme(name, u)
+        assert np.allclose(F, sum(u ** k / math.factorial(k) for k in range(1, deg + 1, 2)), rtol=0, atol=1e-14)
+        assert np.allclose(Fp, sum(u ** k / math.factorial(k) for k in range(0, deg, 2)), rtol=0, atol=1e-14)
+        assert np.allclose(Fpp, sum(u ** k / math.factorial(k) for k in range(1, deg - 1, 2)), rtol=0, atol=1e-14)
+    # higher degree is closer to sinh
+    errs = [np.abs(fem.F_scheme(n, u)[0] - np.sinh(u)).max() for n in ('T3', 'T5', 'T7')]
+    assert errs[0] > errs[1] > errs[2]
