@@ -76,7 +76,7 @@ typedef struct pbfb_mesh pbfb_mesh;
  * Newton configuration (Appendix B: L_e = 0.35, Tol_omega = 0.1,
  * Tol_GR0 = 1e-3, Tol_GR = 1e-6, Tol_NL = 1e-3; omega_0 = 2 for the T3
  * iteration and 1 afterwards, Sec. 3.3), with the block preconditioner
- * (30 inner iterations; the paper does not state its preconditioner).
+ * (20 inner iterations; the paper does not state its preconditioner).
  * In the PBFB_MIXED precision the GMRES operator (and the omega-search
  * direction p = -Acal(0) Delta, whose f_d root is needed only to Tol_omega)
  * evaluates the far field in float32, while the Newton residual
@@ -104,6 +104,9 @@ typedef struct pbfb_newton_opts {
                            increment with J = 0 in the linear operator; omega by the direct
                            secant of Appendix A, Eq. SEC_FD, and the R_e reuse rule) */
   double R_e;           /* Picard: recompute omega only when e_{k-1}/e_k < R_e (0: always) */
+  int omega_warm_start; /* Newton, first iteration: start the omega search from three
+                           bisection steps of f_d on [2, 3] followed by secant steps until
+                           |d omega| < 0.05 (Sec. 3.5); 0 = start from omega0_first */
   int omega_search;     /* 1: automatic omega; 0: constant omega0_first / omega0_rest */
   int precond;          /* PBFB_PRECOND_JACOBI: diagonal of the coupled operator;
                            PBFB_PRECOND_BLOCK: flexible GMRES whose preconditioner runs

@@ -56,6 +56,7 @@ class Opts:
     linear_solver: str = 'gmres'  # 'gmres' (the paper's) or 'direct' (sparse LU)
     omega_search: bool = True     # False: constant omega = omega0_* every iteration
     method: str = 'newton'        # 'newton' (Sec. 2.4.2) or 'picard' (Sec. 2.4.1)
+    omega_warm_start: bool = False  # Newton, first iteration: bisection + secant start (Sec. 3.5)
     R_e: float = 1.4              # Picard: recompute omega only when e_{k-1} / e_k < R_e (0 = always)
 
 
@@ -283,6 +284,49 @@ def omega_search(P: Problem, u, du, c, p, d0n2, scheme, omega0, opts: Opts, trac
     return om
 
 
+def warm_start_omega(P: Problem, u, du, c, p, scheme, opts: Opts, trace):
+    """Initial guess of the first Newton iteration's omega (Sec. 3.5, the 1HC8 optimisation):
+    three bisection steps of f_d on [2, 3] (f_d decreases through its root, so f_d > 0 moves
+    right), then secant steps (Eq. Met_Secante, standard form) until two iterates differ by less
+    than 0.05.  Returns omega0_first when a step is not finite."""
+    def fd(o):
+        return fd_and_derivative(omega_dots(P, u, du, c, p, o, scheme), o)[0]
+    lo, hi = 2.0, 3.0
+    pts = []
+    for _ in range(3):
+        mid = 0.5 * (lo + hi)
+        f = fd(mid)
+        pts.append((mid, f))
+        if not np.isfinite(f):
+            trace['omega_evals_warm'] = len(pts)
+            return opts.omega0_first
+        if f > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    (o_prev, f_prev), (o_cur, f_cur) = pts[-2], pts[-1]
+    evals = 3
+    o_next = o_cur
+    for _ in range(opts.max_omega_iters):
+        den = f_prev - f_cur
+        if den == 0.0 or not np.isfinite(den):
+            break
+        o_next = o_prev - (o_prev - o_cur) * f_prev / den
+        if not np.isfinite(o_next):
+            o_next = opts.omega0_first
+            break
+        if abs(o_next - o_cur) < 0.05:
+            break
+        o_prev, f_prev, o_cur = o_cur, f_cur, o_next
+        f_cur = fd(o_cur)
+        evals += 1
+        if not np.isfinite(f_cur):
+            o_next = opts.omega0_first
+            break
+    trace['omega_evals_warm'] = evals
+    return o_next
+
+
 def picard_omega(P: Problem, u, du, c, p, d0n2, scheme, omega0, opts: Opts, trace):
     """Relaxation factor of a Picard step: the direct secant of Appendix A (Eq. SEC_FD) through
     (0, f_d(0) = 1) and (omega0, f_d(omega0)), continued by secant steps (Eq. Met_Secante) until
@@ -430,6 +474,8 @@ def solve(P: Problem, opts: Opts = None, linear_only=False):
         else:
             p = -P.apply(du)
             om0 = opts.omega0_first if k == 0 else opts.omega0_rest
+            if k == 0 and opts.omega_warm_start and not picard:
+                om0 = warm_start_omega(P, u, du[:P.nv], c, p, scheme, opts, trace)
             if picard:
                 om = picard_omega(P, u, du[:P.nv], c, p, float(d @ d), scheme, om0, opts, trace)
             else:

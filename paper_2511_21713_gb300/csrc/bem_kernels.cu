@@ -1139,7 +1139,8 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
   timer_begin(m, m->t_nbodyff, &ev);
   constexpr int NT = 128;
   const int ntb = blocks_for(nq, NT);
-  int nsplit = std::max(1, std::min(blocks_for(4 * 152, ntb), blocks_for(nq, 4 * NT)));
+  const int bps = m->tune_bps > 0 ? m->tune_bps : 8;  // GB300 sweep: 8 blocks per SM of source splits
+  int nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * NT)));
   const int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
   nsplit = blocks_for(nq, per);
   if ((size_t)nsplit * nq > s->val.n) {

@@ -832,6 +832,56 @@ static int omega_fallback(Mesh* m, int scheme, const double* u, const double* du
   return PBFB_OK;
 }
 
+// Initial guess of the first Newton iteration's omega (Sec. 3.5): three bisection steps of f_d on
+// [2, 3] (f_d > 0 moves right), then standard secant steps until |omega_{j+1} - omega_j| < 0.05;
+// omega0_first when a value is not finite.
+static int warm_start_omega(Mesh* m, int scheme, const double* u, const double* du, const double* c,
+                            const double* p, const pbfb_newton_opts& o, double* omega_out, int* evals) {
+  double D[8];
+  auto fd = [&](double om, double* f) -> int {
+    PB_TRY(omega_eval(m, scheme, u, du, c, p, &om, 1, D));
+    ++*evals;
+    *f = -D[0] / D[1] - om;
+    return PBFB_OK;
+  };
+  double lo = 2.0, hi = 3.0, po[3], pf[3];
+  for (int i = 0; i < 3; ++i) {
+    double mid = 0.5 * (lo + hi), f;
+    PB_TRY(fd(mid, &f));
+    po[i] = mid;
+    pf[i] = f;
+    if (!std::isfinite(f)) {
+      *omega_out = o.omega0_first;
+      return PBFB_OK;
+    }
+    if (f > 0.0)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  double o_prev = po[1], f_prev = pf[1], o_cur = po[2], f_cur = pf[2], o_next = o_cur;
+  for (int it = 0; it < o.max_omega_iters; ++it) {
+    double den = f_prev - f_cur;
+    if (den == 0.0 || !std::isfinite(den)) break;
+    o_next = o_prev - (o_prev - o_cur) * f_prev / den;
+    if (!std::isfinite(o_next)) {
+      o_next = o.omega0_first;
+      break;
+    }
+    if (std::fabs(o_next - o_cur) < 0.05) break;
+    o_prev = o_cur;
+    f_prev = f_cur;
+    o_cur = o_next;
+    PB_TRY(fd(o_cur, &f_cur));
+    if (!std::isfinite(f_cur)) {
+      o_next = o.omega0_first;
+      break;
+    }
+  }
+  *omega_out = o_next;
+  return PBFB_OK;
+}
+
 // Picard relaxation factor: the direct secant of Appendix A (Eq. SEC_FD) through (0, f_d(0) = 1)
 // and (omega0, f_d(omega0)), continued by secant steps (Eq. Met_Secante) until |f_d| < Tol_omega;
 // accepted under the decrease test, else the shared fallback.
@@ -1041,11 +1091,15 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
       PB_TRY(clear_jacobian(m));
       PB_TRY(apply(m, m->du.p, m->pvec.p));
       PB_TRY(launch_axpby(m, n, -1.0, m->pvec.p, 0.0, nullptr, m->pvec.p));
-      const double om0 = k == 0 ? o.omega0_first : o.omega0_rest;
+      double om0 = k == 0 ? o.omega0_first : o.omega0_rest;
+      int warm_evals = 0;
+      if (k == 0 && o.omega_warm_start && !picard)
+        PB_TRY(warm_start_omega(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, o, &om0, &warm_evals));
       st = picard ? picard_omega(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, d2, om0, o, &om, &evals,
                                  &R.omega_fallbacks)
                   : omega_search(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, d2, om0, o, &om, &evals,
                                  &R.omega_fallbacks);
+      evals += warm_evals;
       if (st) {
         R.status = st;
         R.newton_iters = k + 1;
@@ -1145,9 +1199,10 @@ void pbfb_default_opts(pbfb_newton_opts* o) {
   o->taylor[1] = o->taylor[2] = o->taylor[3] = PBFB_HS;
   o->method = PBFB_NEWTON;
   o->R_e = 1.4;
+  o->omega_warm_start = 0;
   o->omega_search = 1;
   o->precond = PBFB_PRECOND_BLOCK;
-  o->inner_iters = 30;
+  o->inner_iters = 20;
 }
 
 const char* pbfb_last_error(void) { return pbfb::last_error(); }

@@ -50,6 +50,7 @@ class NewtonOpts(ctypes.Structure):
                 ("max_gmres", ctypes.c_int), ("restart", ctypes.c_int),
                 ("max_omega_iters", ctypes.c_int), ("n_taylor", ctypes.c_int),
                 ("taylor", ctypes.c_int * 4), ("method", ctypes.c_int), ("R_e", ctypes.c_double),
+                ("omega_warm_start", ctypes.c_int),
                 ("omega_search", ctypes.c_int), ("precond", ctypes.c_int),
                 ("inner_iters", ctypes.c_int)]
 

@@ -226,7 +226,8 @@ def test_picard_and_taylor_schedules(pair):
     ref = pb.solve(P, pb.Opts(**TIGHT))
     for gkw, okw in ((dict(method=pbfb.PICARD, omega0_first=0.5, omega0_rest=0.5),
                       dict(method="picard", omega0_first=0.5, omega0_rest=0.5)),
-                     (dict(taylor=[pbfb.T3, pbfb.T5, pbfb.T7, pbfb.T7]), dict(taylor=("T3", "T5", "T7", "T7")))):
+                     (dict(taylor=[pbfb.T3, pbfb.T5, pbfb.T7, pbfb.T7]), dict(taylor=("T3", "T5", "T7", "T7"))),
+                     (dict(omega_warm_start=1), dict(omega_warm_start=True))):
         tight = dict(tol_gmres0=1e-12, tol_gmres=1e-12, tol_nl=1e-10)
         x, res = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.default_opts(**gkw, **tight))
         assert abs(res["total"] - ref.total) < 1e-9 * abs(ref.total)

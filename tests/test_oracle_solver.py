@@ -200,11 +200,32 @@ def test_taylor_schedules_and_picard_reach_the_newton_solution(tiny_problem):
     ref = pb.solve(P, TIGHT)
     tight = dict(tol_gmres0=1e-12, tol_gmres=1e-12, tol_nl=1e-10)
     for o in (pb.Opts(taylor=('T3', 'T5'), **tight), pb.Opts(taylor=('T3', 'T5', 'T7', 'T7'), **tight),
-              pb.Opts(taylor=(), **tight),
+              pb.Opts(taylor=(), **tight), pb.Opts(omega_warm_start=True, **tight),
               pb.Opts(method='picard', omega0_first=0.5, omega0_rest=0.5, **tight)):
         R = pb.solve(P, o)
         assert abs(R.total - ref.total) < 1e-10 * abs(ref.total), (o.method, o.taylor)
         assert np.linalg.norm(R.x - ref.x) < 1e-8 * np.linalg.norm(ref.x)
+
+
+def test_omega_warm_start_steps(tiny_problem):
+    """Sec. 3.5 warm start: three bisection midpoints of [2, 3] (2.5 first), then secant steps;
+    the returned guess is a secant iterate of f_d."""
+    P = tiny_problem
+    xL = pb.solve(P, TIGHT, linear_only=True).x
+    u = xL[:P.nv]
+    c = P.b - P.apply(xL)
+    d = c - P.pad(P.N(u, 'T3'))
+    du = pb.linear_solve(P, P.J(u, 'T3'), d, 1e-12, TIGHT)[0]
+    p = -P.apply(du)
+    tr = {}
+    om0 = pb.warm_start_omega(P, u, du[:P.nv], c, p, 'T3', pb.Opts(), tr)
+    assert tr['omega_evals_warm'] >= 3 and np.isfinite(om0)
+    f = lambda o: pb.fd_and_derivative(pb.omega_dots(P, u, du[:P.nv], c, p, o, 'T3'), o)[0]
+    # the first bisection point is the midpoint and the search moves towards the root of f_d
+    f25 = f(2.5)
+    assert (om0 < 2.5) == (f25 < 0)
+    # near the returned guess f_d is small compared with its value at the start of the bracket
+    assert abs(f(om0)) < abs(f25)
 
 
 def test_picard_defaults_converge_slower_than_newton(tiny_problem):
