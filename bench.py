@@ -34,6 +34,9 @@ SM_MAX_MHZ = 2070.0
 # float32 operations per far-field pair (FMA counted as 2): Laplace 18, Yukawa 24
 FLOP_PAIR = {"laplace": 18.0, "yukawa": 24.0}
 GOLDEN = os.path.join(ROOT, "tests", "golden", "multi_charge_sphere.json")
+# DRAM bytes per launch of the packed far-field kernel on this workload, from its ncu capture
+# (None until the capture of the current kernel is recorded)
+NBODY_TRAFFIC = None
 
 
 def workload_config(case, precision):
@@ -105,6 +108,75 @@ class Clocks:
                 continue
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def serving_cases(n, seed=5000):
+    """Seeded serving requests: spheres of 2000-8000 triangles per surface (log-uniform in the
+    count), radius 12, shell to 24, 1-200 unit charges in r < 9.6, ionic strength U(0.01, 1) M,
+    eps_in in {2, 4}.  Meshes of the same frequency are reused."""
+    import numpy as np
+    from paper_2511_21713_gb300 import inputs
+    rng = inputs.SplitMix64(seed)
+    meshes, cases = {}, []
+    for i in range(n):
+        tri = 2000.0 * 4.0 ** rng.uniform()
+        nu = max(10, min(20, int(round((tri / 20.0) ** 0.5))))
+        nq = 1 + rng.below(200)
+        q, z = inputs.ball_charges(nq, 9.6, rng.below(nq + 1), seed + 17 * i)
+        ionic = 0.01 + 0.99 * rng.uniform()
+        eps_in = (2.0, 4.0)[rng.below(2)]
+        if nu not in meshes:
+            meshes[nu] = inputs.spherical_shell(nu, 12.0, 24.0, max(8, int(0.85 * nu)))
+        xyz, tets, gm, gs = meshes[nu]
+        kappa = inputs.kappa_from_ionic_strength(ionic, 80.0, 300.0)
+        cases.append(inputs.Case(f"serve{i}", xyz, tets, gm, gs, q, z, eps_in, 80.0, kappa, 300.0))
+    return cases
+
+
+def run_serving(pbfb, cases, max_inflight, budget):
+    """Saturation run (all requests at t = 0) for capacity, then Poisson arrivals at 0.8x
+    capacity; latency = arrival -> result (the request's own set-up included)."""
+    import numpy as np
+    from paper_2511_21713_gb300 import inputs
+
+    def drain(sv, n, until=None):
+        got = []
+        while len(got) < n:
+            got += sv.poll(64, 100000)
+        return got
+
+    opts = pbfb.default_opts(precision=pbfb.MIXED)
+    sv = pbfb.Server(budget, max_inflight)
+    t0 = time.perf_counter()
+    for i, c in enumerate(cases):
+        sv.submit(c, i, opts=opts)
+    res = drain(sv, len(cases))
+    makespan = time.perf_counter() - t0
+    st = sv.stats()
+    sv.close()
+    cap = len(cases) / makespan
+    rate = 0.8 * cap
+    rng = inputs.SplitMix64(77)
+    arrivals = np.cumsum([-np.log(1.0 - rng.uniform()) / rate for _ in cases])
+    sv = pbfb.Server(budget, max_inflight)
+    t0 = time.perf_counter()
+    got = []
+    for i, c in enumerate(cases):
+        while time.perf_counter() - t0 < arrivals[i]:
+            got += sv.poll(64, 1000)
+        sv.submit(c, i, opts=opts)
+    got += drain(sv, len(cases) - len(got))
+    span = time.perf_counter() - t0
+    sv.close()
+    lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in got])
+    ok = all(r["status"] == 0 for r in res + got)
+    return {"requests": len(cases), "max_inflight": max_inflight, "budget_bytes": budget,
+            "saturation_solves_per_s": cap, "peak_bytes": st["peak"],
+            "open_loop_rate_per_s": rate, "open_loop_solves_per_s": len(cases) / span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "all_ok": ok,
+            "workload": "spheres of 2000-8000 triangles per surface (log-uniform), 1-200 charges, "
+                        "0.01-1 M, eps_in 2 or 4; mixed precision, paper tolerances"}
 
 
 def run_pbfb(args):
@@ -180,7 +252,7 @@ def run_pbfb(args):
         flops = prof["nbody_flops"]
         peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         peak_note = "fp32 non-tensor: 152 SM x 128 lanes x 2 flop x 2070 MHz (18 flop/Laplace pair, 24/Yukawa)"
-        kname = "k_nbody_f32"
+        kname = "k_nbody_f32x2 (packed, 2 targets per thread)"
     else:
         launches, kms, pairs = prof["nbody64_launches"], prof["nbody64_ms"], prof["nbody64_pairs"]
         flops = pairs * 0.5 * (FLOP_PAIR["laplace"] + FLOP_PAIR["yukawa"])
@@ -207,8 +279,8 @@ def run_pbfb(args):
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
                      # dram__bytes_read + write per launch from the ncu capture in
-                     # profiles/k_nbody_f32_multi_charge_sphere.md (source records read once)
-                     "traffic": (2.3145e6 if (prec == pbfb.MIXED and args.workload == "multi_charge_sphere")
+                     # profiles/k_nbody_f32x2_multi_charge_sphere.md (source records read once)
+                     "traffic": (NBODY_TRAFFIC if (prec == pbfb.MIXED and args.workload == "multi_charge_sphere")
                                  else None),
                      "peak_basis": peak_note, "avg_launch_ms": avg_ms,
                      "pairs_per_launch": pairs_per_launch, "launches": launches,
@@ -236,6 +308,9 @@ def run_pbfb(args):
                            "mixed_speedup": ms64 / (total_ms_max / args.steps),
                            "mixed_energy_rel_diff": abs(res["total"] - r64["total"]) / abs(r64["total"]),
                            "newton_iters": r64["newton_iters"], "gmres": r64["gmres"]}
+    if args.serving > 0 and args.workload == "multi_charge_sphere":
+        cases = serving_cases(args.serving)
+        out["serving"] = run_serving(pbfb, cases, 4, 64 << 30)
     if os.path.exists(GOLDEN) and args.workload == "multi_charge_sphere":
         g = json.load(open(GOLDEN))
         ref = g["tight"]["total"]
@@ -358,6 +433,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=64, help="1/k of the BEM rows in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3, help="host-buffer solves timed for the e2e figure")
+    ap.add_argument("--serving", type=int, default=24, help="requests in the serving run (0 = skip)")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false",
                     help="skip the single float64-path solve reported under fp64_gpu")
     ap.add_argument("--workload", default="multi_charge_sphere", choices=["multi_charge_sphere", "small"],

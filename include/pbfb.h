@@ -278,6 +278,76 @@ int pbfb_set_tuning(pbfb_mesh* mesh, int nbody_targets_per_thread, int nbody_blo
  * reset != 0 zeroes the counters after reading. */
 int pbfb_profile(pbfb_mesh* mesh, int enable, int reset, double* stats);
 
+/* ---- Serving and batching (the paper has no counterpart; the solves are the same). */
+
+typedef struct pbfb_server pbfb_server;
+
+/* One solve request.  All arrays are host memory with the layouts of
+ * pbfb_mesh_create / pbfb_charges_set; they are copied by pbfb_server_submit.
+ * opts: NULL for the defaults. */
+typedef struct pbfb_request {
+  int64_t id;
+  const double* xyz;
+  int32_t n_v;
+  const int32_t* tets;
+  int64_t n_t;
+  const int32_t* gm_tris;
+  int32_t n_gm;
+  const int32_t* gs_tris;
+  int32_t n_gs;
+  const double* q_xyz;
+  const double* q_z;
+  int32_t n_q;
+  double eps_in, eps_out, kappa, T;
+  const pbfb_newton_opts* opts;
+} pbfb_request;
+
+/* Completed request: status and result of the solve; times in ms on the host's
+ * steady clock (submit, start of the solve's set-up, completion). */
+typedef struct pbfb_response {
+  int64_t id;
+  int status;
+  pbfb_result result;
+  double t_submit_ms, t_start_ms, t_done_ms;
+  char error[256];
+} pbfb_response;
+
+/* Starts a request server on `device`: max_inflight worker threads (1..64),
+ * each with its own CUDA stream, admit queued requests in arrival order while
+ * the sum of their estimated device memory stays within hbm_budget_bytes (a
+ * request alone is always admitted), and run mesh creation, charges and the
+ * full solve; requests that arrive while others run start as memory frees and
+ * their work overlaps on the GPU.  Each request is solved on its own buffers
+ * with deterministic kernels: its result is identical to solving it alone. */
+int pbfb_server_create(int device, uint64_t hbm_budget_bytes, int max_inflight, pbfb_server** out);
+
+/* Queues a request (copies its arrays; returns at once).  PBFB_ERR_OOM if its
+ * estimated memory exceeds the whole budget. */
+int pbfb_server_submit(pbfb_server* server, const pbfb_request* request);
+
+/* Moves up to `max` completed responses to out (host), waiting up to
+ * timeout_us microseconds for the first one; *n_out = how many. */
+int pbfb_server_poll(pbfb_server* server, pbfb_response* out, int max, int timeout_us, int* n_out);
+
+/* stats (host, 6 doubles): submitted, completed, queued, bytes in use, peak
+ * bytes in use, budget. */
+int pbfb_server_stats(pbfb_server* server, double* stats);
+
+/* Finishes the requests already admitted, drops the queued ones, frees all. */
+int pbfb_server_destroy(pbfb_server* server);
+
+/* Parameters of one instance of pbfb_solve_batch (opts: NULL = defaults). */
+typedef struct pbfb_batch_params {
+  double eps_in, eps_out, kappa, T;
+  const pbfb_newton_opts* opts;
+} pbfb_batch_params;
+
+/* Solves n meshes (charges already set) with up to max_concurrent host threads;
+ * meshes created on different streams run concurrently on the GPU.  results:
+ * host, n entries.  Returns the first failing instance's status. */
+int pbfb_solve_batch(pbfb_mesh* const* meshes, const pbfb_batch_params* params, int n, int max_concurrent,
+                     pbfb_result* results);
+
 #ifdef __cplusplus
 }
 #endif

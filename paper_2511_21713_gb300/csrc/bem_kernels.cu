@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "pbfb_internal.cuh"
@@ -850,11 +851,11 @@ __global__ void k_test_reduce(int nv, const int* __restrict__ ptr, const int* __
                               double scale, int accumulate, double* __restrict__ y) {
   const int lane = threadIdx.x & 3;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 2;
-  if (i >= nv) return;
+  const bool valid = i < nv;  // all lanes reach the shuffles
   (void)nsplit;
   (void)nq;
   double acc = 0.0;
-  const int b = ptr[i], e = ptr[i + 1];
+  const int b = valid ? ptr[i] : 0, e = valid ? ptr[i + 1] : 0;
   for (int k = b * QS + lane; k < e * QS; k += 4) {
     int ent = idx[k / QS], q = k % QS;
     int t = ent / 3, a = ent - 3 * t;
@@ -863,7 +864,7 @@ __global__ void k_test_reduce(int nv, const int* __restrict__ ptr, const int* __
   }
   acc += __shfl_down_sync(0xffffffffu, acc, 2, 4);
   acc += __shfl_down_sync(0xffffffffu, acc, 1, 4);
-  if (lane == 0) {
+  if (lane == 0 && valid) {
     acc *= scale;
     y[i] = accumulate ? y[i] + acc : acc;
   }
@@ -923,7 +924,9 @@ inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 }  // namespace
 
 int init_quadrature() {
+  static std::mutex mu;
   static bool done = false;
+  std::lock_guard<std::mutex> lk(mu);
   if (done) return PBFB_OK;
   double x[NGL], w[NGL];
   gauss_legendre01(NGL, x, w);

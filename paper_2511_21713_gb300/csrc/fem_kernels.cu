@@ -142,13 +142,14 @@ __global__ void k_spmv(int nrows, const int* __restrict__ ptr, const int* __rest
                        const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
   int lane = threadIdx.x & 7;
   int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-  if (row >= nrows) return;
+  const bool valid = row < nrows;  // all lanes reach the shuffles
   double acc = 0.0;
-  for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) acc += val[k] * __ldg(&x[col[k]]);
+  if (valid)
+    for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) acc += val[k] * __ldg(&x[col[k]]);
   acc += __shfl_down_sync(0xffffffffu, acc, 4, 8);
   acc += __shfl_down_sync(0xffffffffu, acc, 2, 8);
   acc += __shfl_down_sync(0xffffffffu, acc, 1, 8);
-  if (lane == 0) y[row] = acc;
+  if (lane == 0 && valid) y[row] = acc;
 }
 
 // Generic CSR y (+)= A x, 8 lanes per row.
@@ -157,13 +158,14 @@ __global__ void k_csr_acc(int nrows, const int* __restrict__ ptr, const int* __r
                           int accumulate) {
   int lane = threadIdx.x & 7;
   int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-  if (row >= nrows) return;
+  const bool valid = row < nrows;  // all lanes reach the shuffles
   double acc = 0.0;
-  for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) acc += val[k] * x[col[k]];
+  if (valid)
+    for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) acc += val[k] * x[col[k]];
   acc += __shfl_down_sync(0xffffffffu, acc, 4, 8);
   acc += __shfl_down_sync(0xffffffffu, acc, 2, 8);
   acc += __shfl_down_sync(0xffffffffu, acc, 1, 8);
-  if (lane == 0) y[row] = accumulate ? y[row] + acc : acc;
+  if (lane == 0 && valid) y[row] = accumulate ? y[row] + acc : acc;
 }
 
 // Omega batch: per tet and omega, local load of F(w), of F'(w) du and of F''(w) du^2 at

@@ -11,6 +11,7 @@
 namespace pbfb {
 
 void set_error(const char* fmt, ...);
+const char* last_error();
 
 #define PB_CUDA(call)                                                                    \
   do {                                                                                   \
@@ -172,6 +173,7 @@ struct Mesh {
   DBuf<double> pval, pdinv;
   double gs_radius = 1.0;           // sqrt(|Gamma_s| / 4 pi)
   int coop_blocks = 0;              // grid of the cooperative inner PCG (-1: not available)
+  bool no_coop = false;             // never use the grid-barrier PCG (meshes solved concurrently)
   int tune_tpt = 0;                 // float32 far field: targets per thread (0 = heuristic)
   int tune_bps = 0;                 // float32 far field: target blocks per SM for the source split
   int tune_packed = 0;              // float32 far field: 1 = packed f32x2 kernel
@@ -185,6 +187,18 @@ struct Mesh {
   DBuf<float2> ff_tab;      // float-float exp table of the Yukawa kernel
   double nbody_flops = 0.0;  // float32 far-field flops issued (18 per Laplace pair, 24 per Yukawa pair)
 };
+
+// ---- whole-solve entry points shared by the C ABI, the batch call and the server
+int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const int* gm, int ngm, const int* gs,
+                int ngs, cudaStream_t stream, Mesh** out);
+void mesh_destroy(Mesh* m);
+int charges_set(Mesh* m, const double* xyz, const double* z, int nq);
+int solve_mesh(Mesh* m, double eps_in, double eps_out, double kappa, double T, const pbfb_newton_opts* opts,
+               double* x_out_dev, pbfb_result* res);
+size_t estimate_bytes(int64_t nv, int64_t nt, int64_t ngm, int64_t ngs, int restart);
+}  // namespace pbfb
+pbfb::Mesh* pbfb_mesh_internal(pbfb_mesh* h);
+namespace pbfb {
 
 // ---- quadrature constants (device) and their host initialisation
 int init_quadrature();
@@ -226,5 +240,6 @@ int ensure(DBuf<double>& b, size_t n);
 // timing helpers
 void timer_begin(Mesh* m, KernelClassTimer& t, cudaEvent_t* ev);
 void timer_end(Mesh* m, KernelClassTimer& t, cudaEvent_t ev0, double work);
+void timer_flush(KernelClassTimer& t);
 
 }  // namespace pbfb

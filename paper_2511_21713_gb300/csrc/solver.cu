@@ -23,8 +23,6 @@
 
 namespace pbfb {
 
-int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const int* gm, int ngm, const int* gs,
-                int ngs, cudaStream_t stream, Mesh** out);
 const char* last_error();
 
 namespace {
@@ -205,15 +203,20 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_spmv(int nv, const int* __restric
                                                      const int* __restrict__ col, const double* __restrict__ val,
                                                      const double* __restrict__ p, double* __restrict__ q,
                                                      double* __restrict__ part) {
+  // warp-uniform trip count: every lane of a warp executes every shuffle (4 rows per warp pass)
   const int lane = threadIdx.x & 7;
+  const int warp = (blockIdx.x * PCG_T + threadIdx.x) >> 5, nwarp = (gridDim.x * PCG_T) >> 5;
   double acc = 0.0;
-  for (int row = (blockIdx.x * PCG_T + threadIdx.x) >> 3; row < nv; row += (gridDim.x * PCG_T) >> 3) {
+  for (int base = 4 * warp; base < nv; base += 4 * nwarp) {
+    const int row = base + ((threadIdx.x & 31) >> 3);
+    const bool valid = row < nv;
     double s = 0.0;
-    for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) s += val[k] * p[col[k]];
+    if (valid)
+      for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) s += val[k] * p[col[k]];
     s += __shfl_down_sync(0xffffffffu, s, 4, 8);
     s += __shfl_down_sync(0xffffffffu, s, 2, 8);
     s += __shfl_down_sync(0xffffffffu, s, 1, 8);
-    if (lane == 0) {
+    if (lane == 0 && valid) {
       q[row] = s;
       acc += p[row] * s;
     }
@@ -312,13 +315,17 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int
   for (int it = 0; it < iters; ++it) {
     // w = A z; partial r.z and z.w
     double ag = 0.0, ad = 0.0;
-    for (int row = tid >> 3; row < nv; row += stride >> 3) {
+    // warp-uniform trip count: every lane of a warp executes every shuffle (4 rows per warp pass)
+    for (int base = 4 * (tid >> 5); base < nv; base += 4 * (stride >> 5)) {
+      const int row = base + ((threadIdx.x & 31) >> 3);
+      const bool valid = row < nv;
       double sacc = 0.0;
-      for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) sacc += val[k] * z[col[k]];
+      if (valid)
+        for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) sacc += val[k] * z[col[k]];
       sacc += __shfl_down_sync(0xffffffffu, sacc, 4, 8);
       sacc += __shfl_down_sync(0xffffffffu, sacc, 2, 8);
       sacc += __shfl_down_sync(0xffffffffu, sacc, 1, 8);
-      if (lane == 0) {
+      if (lane == 0 && valid) {
         w[row] = sacc;
         double zr = z[row];
         ag += r[row] * zr;
@@ -395,7 +402,7 @@ void timer_end(Mesh* m, KernelClassTimer& t, cudaEvent_t ev0, double work) {
   t.pending.push_back({ev0, ev1});
 }
 
-static void timer_flush(KernelClassTimer& t) {
+void timer_flush(KernelClassTimer& t) {
   for (auto& p : t.pending) {
     float ms = 0.f;
     cudaEventSynchronize(p.second);
@@ -511,6 +518,7 @@ static int jacobi(Mesh* m, double* dinv) {
 // (the constant mode of the exterior Dirichlet-to-Neumann map of a sphere of Gamma_s's area),
 // which keeps it positive definite when J = 0.
 static int prepare_block_precond(Mesh* m) {
+  if (m->no_coop) m->coop_blocks = -1;
   if (m->coop_blocks == 0) {
     int coop = 0, nsm = 0, per = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, m->dev);
@@ -1156,6 +1164,58 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   return PBFB_OK;
 }
 
+int solve_mesh(Mesh* m, double eps_in, double eps_out, double kappa, double T, const pbfb_newton_opts* opts,
+               double* x_out_dev, pbfb_result* res) {
+  PB_CUDA(cudaSetDevice(m->dev));
+  return solve(m, eps_in, eps_out, kappa, T, opts, x_out_dev, res);
+}
+
+int charges_set(Mesh* m, const double* xyz, const double* z, int n_q) {
+  if (!xyz || !z || n_q < 1) {
+    set_error("charges_set: need at least one charge");
+    return PBFB_ERR_INVALID;
+  }
+  std::vector<double> soa(3 * (size_t)n_q);
+  for (int k = 0; k < n_q; ++k) {
+    for (int d = 0; d < 3; ++d) {
+      if (!std::isfinite(xyz[3 * k + d])) {
+        set_error("charges_set: non-finite position");
+        return PBFB_ERR_INVALID;
+      }
+      soa[(size_t)d * n_q + k] = xyz[3 * k + d];
+    }
+    if (!std::isfinite(z[k])) {
+      set_error("charges_set: non-finite charge");
+      return PBFB_ERR_INVALID;
+    }
+  }
+  PB_TRY(m->qxyz.upload(soa.data(), soa.size(), m->stream));
+  PB_TRY(m->qz.upload(z, n_q, m->stream));
+  m->qz_h.assign(z, z + n_q);
+  m->nq = n_q;
+  PB_TRY(m->coul.alloc(m->sm.nv));
+  PB_TRY(launch_coulomb(m));
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
+    set_error("charges_set: %s", cudaGetErrorString(cudaGetLastError()));
+    return PBFB_ERR_CUDA;
+  }
+  m->charges = true;
+  return PBFB_OK;
+}
+
+void mesh_destroy(Mesh* m) {
+  if (!m) return;
+  cudaSetDevice(m->dev);
+  cudaStreamSynchronize(m->stream);
+  timer_flush(m->t_nbody);
+  timer_flush(m->t_nbody64);
+  timer_flush(m->t_nbodyff);
+  timer_flush(m->t_spmv);
+  timer_flush(m->t_elem);
+  if (m->pinned) cudaFreeHost(m->pinned);
+  delete m;
+}
+
 }  // namespace pbfb
 
 // ==================================================================== C ABI
@@ -1165,6 +1225,8 @@ using pbfb::Mesh;
 struct pbfb_mesh {
   Mesh* m;
 };
+
+pbfb::Mesh* pbfb_mesh_internal(pbfb_mesh* h) { return h ? h->m : nullptr; }
 
 #define PB_HANDLE(h)                                  \
   if (!(h) || !(h)->m) {                              \
@@ -1251,37 +1313,7 @@ int pbfb_surface_vertices(const pbfb_mesh* h, int which, int32_t* out) {
 
 int pbfb_charges_set(pbfb_mesh* h, const double* xyz, const double* z, int32_t n_q) {
   PB_HANDLE(h);
-  if (!xyz || !z || n_q < 1) {
-    pbfb::set_error("charges_set: need at least one charge");
-    return PBFB_ERR_INVALID;
-  }
-  std::vector<double> soa(3 * (size_t)n_q);
-  for (int k = 0; k < n_q; ++k) {
-    for (int d = 0; d < 3; ++d) {
-      if (!std::isfinite(xyz[3 * k + d])) {
-        pbfb::set_error("charges_set: non-finite position");
-        return PBFB_ERR_INVALID;
-      }
-      soa[(size_t)d * n_q + k] = xyz[3 * k + d];
-    }
-    if (!std::isfinite(z[k])) {
-      pbfb::set_error("charges_set: non-finite charge");
-      return PBFB_ERR_INVALID;
-    }
-  }
-  int st;
-  if ((st = m->qxyz.upload(soa.data(), soa.size(), m->stream))) return st;
-  if ((st = m->qz.upload(z, n_q, m->stream))) return st;
-  m->qz_h.assign(z, z + n_q);
-  m->nq = n_q;
-  if ((st = m->coul.alloc(m->sm.nv))) return st;
-  if ((st = pbfb::launch_coulomb(m))) return st;
-  if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
-    pbfb::set_error("charges_set: %s", cudaGetErrorString(cudaGetLastError()));
-    return PBFB_ERR_CUDA;
-  }
-  m->charges = true;
-  return PBFB_OK;
+  return pbfb::charges_set(m, xyz, z, n_q);
 }
 
 int pbfb_solve_device(pbfb_mesh* h, double eps_in, double eps_out, double kappa, double T,
@@ -1309,17 +1341,7 @@ int pbfb_solve(pbfb_mesh* h, double eps_in, double eps_out, double kappa, double
 
 int pbfb_mesh_destroy(pbfb_mesh* h) {
   if (!h) return PBFB_OK;
-  if (h->m) {
-    cudaSetDevice(h->m->dev);
-    cudaStreamSynchronize(h->m->stream);
-    pbfb::timer_flush(h->m->t_nbody);
-    pbfb::timer_flush(h->m->t_nbody64);
-    pbfb::timer_flush(h->m->t_nbodyff);
-    pbfb::timer_flush(h->m->t_spmv);
-    pbfb::timer_flush(h->m->t_elem);
-    if (h->m->pinned) cudaFreeHost(h->m->pinned);
-    delete h->m;
-  }
+  pbfb::mesh_destroy(h->m);
   delete h;
   return PBFB_OK;
 }

@@ -32,6 +32,8 @@ EXPORTS = [
     "pbfb_last_error", "pbfb_set_params", "pbfb_assemble", "pbfb_clear_jacobian",
     "pbfb_apply", "pbfb_bem_apply", "pbfb_fem_rows", "pbfb_gmres", "pbfb_omega_eval",
     "pbfb_energy", "pbfb_profile", "pbfb_bem_apply_noalloc", "pbfb_set_tuning",
+    "pbfb_server_create", "pbfb_server_submit", "pbfb_server_poll", "pbfb_server_stats",
+    "pbfb_server_destroy", "pbfb_solve_batch",
 ]
 
 
@@ -74,6 +76,32 @@ class Result(ctypes.Structure):
                     ms_linear=self.ms_linear, ms_newton=self.ms_newton, ms_energy=self.ms_energy)
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("n_v", ctypes.c_int32),
+                ("tets", ctypes.c_void_p), ("n_t", ctypes.c_int64), ("gm_tris", ctypes.c_void_p),
+                ("n_gm", ctypes.c_int32), ("gs_tris", ctypes.c_void_p), ("n_gs", ctypes.c_int32),
+                ("q_xyz", ctypes.c_void_p), ("q_z", ctypes.c_void_p), ("n_q", ctypes.c_int32),
+                ("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("T", ctypes.c_double), ("opts", ctypes.POINTER(NewtonOpts))]
+
+
+class Response(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int), ("result", Result),
+                ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double), ("error", ctypes.c_char * 256)]
+
+    def as_dict(self):
+        d = self.result.as_dict()
+        d.update(id=self.id, status=self.status, t_submit_ms=self.t_submit_ms, t_start_ms=self.t_start_ms,
+                 t_done_ms=self.t_done_ms, error=self.error.decode())
+        return d
+
+
+class BatchParams(ctypes.Structure):
+    _fields_ = [("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("T", ctypes.c_double), ("opts", ctypes.POINTER(NewtonOpts))]
+
+
 _lib = None
 
 
@@ -108,6 +136,12 @@ def load():
         "pbfb_energy": (I, [P, P, P, P]),
         "pbfb_profile": (I, [P, I, I, P]),
         "pbfb_set_tuning": (I, [P, I, I, I]),
+        "pbfb_server_create": (I, [I, ctypes.c_uint64, I, ctypes.POINTER(P)]),
+        "pbfb_server_submit": (I, [P, ctypes.POINTER(Request)]),
+        "pbfb_server_poll": (I, [P, P, I, I, ctypes.POINTER(ctypes.c_int)]),
+        "pbfb_server_stats": (I, [P, P]),
+        "pbfb_server_destroy": (I, [P]),
+        "pbfb_solve_batch": (I, [P, P, I, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -270,3 +304,60 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Owner of a pbfb_server: queued requests, HBM-budget admission, concurrent solves."""
+
+    def __init__(self, budget_bytes, max_inflight=4, device=0):
+        h = ctypes.c_void_p()
+        _check(load().pbfb_server_create(device, int(budget_bytes), max_inflight, ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, case, rid, eps_in=None, eps_out=None, kappa=None, T=None, opts=None):
+        """Queue a solve of an inputs.Case (arrays are copied by the call)."""
+        arrs = [np.ascontiguousarray(case.xyz, np.float64), np.ascontiguousarray(case.tets, np.int32),
+                np.ascontiguousarray(case.gm_tris, np.int32), np.ascontiguousarray(case.gs_tris, np.int32),
+                np.ascontiguousarray(case.q_xyz, np.float64), np.ascontiguousarray(case.q_z, np.float64)]
+        x, t, gm, gs, qx, qz = arrs
+        r = Request(rid, _ptr(x), x.shape[0], _ptr(t), t.shape[0], _ptr(gm), gm.shape[0], _ptr(gs), gs.shape[0],
+                    _ptr(qx), _ptr(qz), qz.shape[0],
+                    case.eps_in if eps_in is None else eps_in, case.eps_out if eps_out is None else eps_out,
+                    case.kappa if kappa is None else kappa, case.T if T is None else T,
+                    ctypes.pointer(opts) if opts is not None else None)
+        _check(load().pbfb_server_submit(self.h, ctypes.byref(r)))
+
+    def poll(self, max_n=64, timeout_us=0):
+        buf = (Response * max_n)()
+        n = ctypes.c_int()
+        _check(load().pbfb_server_poll(self.h, buf, max_n, timeout_us, ctypes.byref(n)))
+        return [buf[i].as_dict() for i in range(n.value)]
+
+    def stats(self):
+        st = np.zeros(6)
+        _check(load().pbfb_server_stats(self.h, _ptr(st)))
+        return dict(submitted=st[0], completed=st[1], queued=st[2], in_use=st[3], peak=st[4], budget=st[5])
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().pbfb_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(meshes, params, max_concurrent=4):
+    """Solve several meshes (charges set) concurrently; params: list of (eps_in, eps_out, kappa, T, opts)."""
+    n = len(meshes)
+    hs = (ctypes.c_void_p * n)(*[m.h.value for m in meshes])
+    keep = [p[4] for p in params]
+    bp = (BatchParams * n)(*[BatchParams(p[0], p[1], p[2], p[3],
+                                         ctypes.pointer(p[4]) if p[4] is not None else None) for p in params])
+    res = (Result * n)()
+    _check(load().pbfb_solve_batch(hs, bp, n, max_concurrent, res))
+    del keep
+    return [res[i].as_dict() for i in range(n)]
