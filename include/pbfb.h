@@ -68,15 +68,16 @@ enum { PBFB_FP64 = 0, PBFB_MIXED = 1, PBFB_FLOAT2 = 2 };
 enum { PBFB_LINEAR = 0, PBFB_T3 = 1, PBFB_HS = 2, PBFB_T5 = 3, PBFB_T7 = 4 };
 enum { PBFB_NEWTON = 0, PBFB_PICARD = 1 };
 enum { PBFB_GAMMA_M = 0, PBFB_GAMMA_S = 1 };
-enum { PBFB_PRECOND_JACOBI = 0, PBFB_PRECOND_BLOCK = 1 };
+enum { PBFB_PRECOND_JACOBI = 0, PBFB_PRECOND_BLOCK = 1, PBFB_PRECOND_BLOCK_DENSE = 2 };
 
 typedef struct pbfb_mesh pbfb_mesh;
 
 /* Newton options; the defaults (pbfb_default_opts) are the paper's best
  * Newton configuration (Appendix B: L_e = 0.35, Tol_omega = 0.1,
  * Tol_GR0 = 1e-3, Tol_GR = 1e-6, Tol_NL = 1e-3; omega_0 = 2 for the T3
- * iteration and 1 afterwards, Sec. 3.3), with the block preconditioner
- * (20 inner iterations; the paper does not state its preconditioner).
+ * iteration and 1 afterwards, Sec. 3.3), with the block preconditioner with
+ * dense single-layer inverses on the surface rows (20 inner iterations on the
+ * FEM block; the paper does not state its preconditioner).
  * In the PBFB_MIXED precision the GMRES operator (and the omega-search
  * direction p = -Acal(0) Delta, whose f_d root is needed only to Tol_omega)
  * evaluates the far field in float32, while the Newton residual
@@ -111,7 +112,16 @@ typedef struct pbfb_newton_opts {
   int precond;          /* PBFB_PRECOND_JACOBI: diagonal of the coupled operator;
                            PBFB_PRECOND_BLOCK: flexible GMRES whose preconditioner runs
                            inner_iters Jacobi-PCG iterations on the FEM block A + J and
-                           the diagonal on the surface rows */
+                           the diagonal on the surface rows;
+                           PBFB_PRECOND_BLOCK_DENSE (default): the same FEM block, and on
+                           the surface rows the inverses of the dense float32 single-layer
+                           matrices (-V_L on Gamma_m, V_Y on Gamma_s; see
+                           pbfb_single_layer_dense), which keep the GMRES iteration count
+                           flat under mesh refinement.  A surface of more than 16384
+                           vertices keeps the diagonal.  The inverse of V_L is built once
+                           per mesh, that of V_Y once per kappa: about 2 (n/128*128)^3
+                           float32 flops and 4 (n/128*128)^2 bytes of device memory per
+                           surface of n vertices (n rounded up to a multiple of 128). */
   int inner_iters;      /* PCG iterations per block-preconditioner application (1..500) */
 } pbfb_newton_opts;
 
@@ -228,14 +238,33 @@ int pbfb_bem_apply(pbfb_mesh* mesh, int which, int op, const double* x_dev, doub
  * results.  x, y: device, n_m or n_s float64, distinct. */
 int pbfb_bem_apply_noalloc(pbfb_mesh* mesh, int which, int op, const double* x_dev, double* y_dev);
 
+/* Dense single-layer matrix of one surface (which: PBFB_GAMMA_M, Laplace; or
+ * PBFB_GAMMA_S, Yukawa with the kappa of pbfb_set_params) in float32, or its
+ * inverse (inverse = 1).  The matrix is the Galerkin V_ij of Eq. KV (Sec. 2.2)
+ * assembled from the pieces of pbfb_bem_apply's op 0 (6 x 6-point rule over
+ * all point pairs plus the exact-minus-regular corrections of touching and
+ * near pairs), then symmetrised (V + V^T) / 2; the inverse is taken by the
+ * sweep operator in float32 (the paper has no counterpart: this is the
+ * surface block of the PBFB_PRECOND_BLOCK_DENSE preconditioner).
+ * out_dev: device float32, n_m or n_s rows of row stride ld_out >= that
+ * count, caller-owned.  Errors: INVALID for a bad argument or a surface of
+ * more than 16384 vertices, STATE before pbfb_set_params, NONFINITE when a
+ * pivot of the sweep is not positive (V not positive definite in float32).
+ * Allocates the matrix (4 ld^2 bytes, ld = n rounded up to 128, kept with
+ * the mesh) and a build scratch of at most 256 MiB, released before the call
+ * returns; with inverse = 0 the preconditioner's stored inverse is rebuilt at
+ * its next use. */
+int pbfb_single_layer_dense(pbfb_mesh* mesh, int which, int inverse, float* out_dev, int32_t ld_out);
+
 /* FEM rows in CSR over the full unknown vector: rowptr (n_v + 1), col and val
  * (nnz) copied to host buffers (val = A + J and the coupling masses). */
 int pbfb_fem_rows(const pbfb_mesh* mesh, int32_t* rowptr, int32_t* col, double* val);
 
 /* Step a5: GMRES (restarted, x0 = 0, right preconditioned, CGS2) on
  * Acal(J) x = b; stops when ||b - Acal x|| <= tol ||b||.  b, x: device (n).
- * precond: PBFB_PRECOND_JACOBI or PBFB_PRECOND_BLOCK (flexible GMRES with
- * inner_iters PCG iterations on the FEM block).  iters and relres: host
+ * precond: PBFB_PRECOND_JACOBI, PBFB_PRECOND_BLOCK or PBFB_PRECOND_BLOCK_DENSE
+ * (flexible GMRES with inner_iters PCG iterations on the FEM block; the last
+ * with the dense single-layer inverses on the surface rows).  iters and relres: host
  * outputs (may be NULL). */
 int pbfb_gmres(pbfb_mesh* mesh, const double* b_dev, double* x_dev, double tol, int restart,
                int maxit, int precond, int inner_iters, int* iters, double* relres);
@@ -274,7 +303,8 @@ int pbfb_set_tuning(pbfb_mesh* mesh, int nbody_targets_per_thread, int nbody_blo
  *   [6] element (assembly + omega) launches, [7] their ms,
  *   [8] float32 far-field flops (18 per Laplace pair, 24 per Yukawa pair),
  *   [9] float64 far-field launches, [10] their ms, [11] their pairs,
- *   [12] float-float far-field launches, [13] their ms, [14] their pairs.
+ *   [12] float-float far-field launches, [13] their ms, [14] their pairs,
+ *   [15] ms spent building dense single-layer matrices and inverses.
  * reset != 0 zeroes the counters after reading. */
 int pbfb_profile(pbfb_mesh* mesh, int enable, int reset, double* stats);
 

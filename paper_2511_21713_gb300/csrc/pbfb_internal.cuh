@@ -112,6 +112,11 @@ struct Surface {
   DBuf<double> val;             // nsplit * nq target potentials
   DBuf<float4> ffsrc, fftgt;    // float-float sources (4 float4) and targets (2 float4) per point
   int nsplit = 1;
+  // dense single layer (float32, ld x ld): -V^-1 once inverted (bem_dense.cu)
+  DBuf<float> vinv;
+  int vinv_ld = 0;
+  bool vinv_ok = false;
+  double vinv_kappa = -1.0;
 };
 
 struct KernelClassTimer {
@@ -177,13 +182,16 @@ struct Mesh {
   int tune_tpt = 0;                 // float32 far field: targets per thread (0 = heuristic)
   int tune_bps = 0;                 // float32 far field: target blocks per SM for the source split
   int tune_packed = 0;              // float32 far field: 1 = packed f32x2 kernel
+  bool dense_m = false, dense_s = false;  // surface rows of the block preconditioner use V^-1
+  DBuf<float> dwork;                // dense single-layer build: W chunk, sweep panels
+  DBuf<int> dflag;                  // sweep pivot status
   // Newton workspace
   DBuf<double> xL, xNL, phi, cvec, dvec, du, pvec, tmp, Nvec, bvec, xout, urb;
   std::vector<double> qz_h;  // charges (host copy)
   // statistics
   double launches = 0;
   bool timing = false;
-  KernelClassTimer t_nbody, t_nbody64, t_nbodyff, t_spmv, t_elem;
+  KernelClassTimer t_nbody, t_nbody64, t_nbodyff, t_spmv, t_elem, t_dense;
   DBuf<float2> ff_tab;      // float-float exp table of the Yukawa kernel
   double nbody_flops = 0.0;  // float32 far-field flops issued (18 per Laplace pair, 24 per Yukawa pair)
 };
@@ -231,6 +239,17 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
 int launch_coulomb(Mesh* m);
 int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev);
 int bem_apply_noalloc(Mesh* m, int which, int op, const double* x, double* y);
+
+// ---- bem_dense.cu: dense float32 single layer of a surface and its inverse
+constexpr int DENSE_V_MAX = 16384;  // surface vertices up to which the dense inverse is used
+int dense_ld(int n);
+size_t dense_bytes(int n);        // the matrix
+size_t dense_work_bytes(int n, int nt);  // build scratch (n vertices, nt triangles)
+// assemble V (kappa must be the kappa of the surface's corrections); invert: sweep to -V^-1
+int build_dense_single_layer(Mesh* m, Surface* s, double kappa, bool invert);
+// z = scale * (stored matrix) v over the surface's vertices
+int launch_dense_apply(Mesh* m, Surface* s, double scale, const double* v, double* z);
+int dense_copy_out(Mesh* m, Surface* s, float scale, float* out, int ld_out);
 
 // ---- blas (solver.cu)
 int dot(Mesh* m, const double* a, const double* b, int n, double* out_host);

@@ -23,7 +23,7 @@
 namespace pbfb {
 
 // Device bytes a solve of this size holds (buffers of mesh_create, the solve workspace, GMRES with
-// the flexible basis), with a 25% margin.
+// the flexible basis, the dense preconditioner blocks), with a 25% margin.
 size_t estimate_bytes(int64_t nv, int64_t nt, int64_t ngm, int64_t ngs, int restart) {
   const double nm = ngm / 2.0 + 2, ns = ngs / 2.0 + 2;  // closed triangulations: V = F/2 + 2
   const double n = nv + nm + ns;
@@ -38,6 +38,11 @@ size_t estimate_bytes(int64_t nv, int64_t nt, int64_t ngm, int64_t ngs, int rest
     b += npair * (9 * 8 * 4 + 16 * 4) + 40.0 * nqs / 6.0 * (4 + 8 * 3);
   }
   b += (2.0 * restart + 1 + 16) * n * 8;                          // Krylov V, Z, work vectors
+  // dense single-layer inverses of the block preconditioner and their build scratch
+  for (double nsv : {nm, ns})
+    if (nsv <= DENSE_V_MAX) b += (double)dense_bytes((int)nsv);
+  const double nbig = std::min(std::max(nm, ns), (double)DENSE_V_MAX);
+  b += (double)dense_work_bytes((int)nbig, (int)(2 * nbig));
   return (size_t)(1.25 * b) + (64u << 20);
 }
 

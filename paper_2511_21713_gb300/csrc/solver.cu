@@ -517,7 +517,15 @@ static int jacobi(Mesh* m, double* dinv) {
 // FEM block of the preconditioner: A + J plus the Robin term eps_s (kappa + 1/R) M_s on Gamma_s
 // (the constant mode of the exterior Dirichlet-to-Neumann map of a sphere of Gamma_s's area),
 // which keeps it positive definite when J = 0.
-static int prepare_block_precond(Mesh* m) {
+// With dense = true the surface rows use the dense float32 inverses of V_L and V_Y (built
+// once per mesh, and for Gamma_s again whenever kappa changes) on surfaces of at most
+// DENSE_V_MAX vertices, the diagonal otherwise.
+static int prepare_block_precond(Mesh* m, bool dense) {
+  m->dense_m = dense && m->sm.nv <= DENSE_V_MAX;
+  m->dense_s = dense && m->ss.nv <= DENSE_V_MAX;
+  if (m->dense_m && !m->sm.vinv_ok) PB_TRY(build_dense_single_layer(m, &m->sm, 0.0, true));
+  if (m->dense_s && (!m->ss.vinv_ok || m->ss.vinv_kappa != m->kappa))
+    PB_TRY(build_dense_single_layer(m, &m->ss, m->kappa, true));
   if (m->no_coop) m->coop_blocks = -1;
   if (m->coop_blocks == 0) {
     int coop = 0, nsm = 0, per = 0;
@@ -545,6 +553,26 @@ static int prepare_block_precond(Mesh* m) {
   return PBFB_OK;
 }
 
+// Surface rows of the block preconditioner: z_m = (-V_L)^-1 v_m and z_s = V_Y^-1 v_s from the
+// dense inverses (the stored matrices are -V^-1), else the diagonal.
+static int surface_rows_precond(Mesh* m, const double* v, double* z) {
+  const int nv = m->nv, n = m->n, c0 = m->sm.col0, c1 = m->ss.col0;
+  if (m->dense_m) {
+    PB_TRY(launch_dense_apply(m, &m->sm, 1.0, v + c0, z + c0));
+  } else {
+    k_scale_rows<<<blocks_for(c1 - c0, 256), 256, 0, m->stream>>>(c0, c1, v, m->gdiag.p, z);
+    PB_LAUNCHED(m);
+  }
+  if (m->dense_s) {
+    PB_TRY(launch_dense_apply(m, &m->ss, -1.0, v + c1, z + c1));
+  } else {
+    k_scale_rows<<<blocks_for(n - c1, 256), 256, 0, m->stream>>>(c1, n, v, m->gdiag.p, z);
+    PB_LAUNCHED(m);
+  }
+  (void)nv;
+  return PBFB_OK;
+}
+
 static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
   const int nv = m->nv, n = m->n;
   const int nb = std::min(152, std::max(1, blocks_for(nv, PCG_T)));
@@ -565,9 +593,7 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
     void* args[] = {&nvv, &iters, &sp, &sc2, &pv, (void*)&v, (void*)&dinv, &z, &pr, &pz, &pp, &pq, &pw, &part};
     PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_coop, dim3(nbc), dim3(PCG_T), args, 0, m->stream));
     PB_LAUNCHED(m);
-    k_scale_rows<<<blocks_for(n - nv, 256), 256, 0, m->stream>>>(nv, n, v, m->gdiag.p, z);
-    PB_LAUNCHED(m);
-    return PBFB_OK;
+    return surface_rows_precond(m, v, z);
   }
   k_pcg_init<<<nb, PCG_T, 0, m->stream>>>(nv, v, dinv, z, pr, pz, pp, part);
   PB_LAUNCHED(m);
@@ -585,9 +611,7 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
     k_pcg_direction<<<nb, PCG_T, 0, m->stream>>>(nv, sc + 1 + k, sc + 2 + k, pz, pp);
     PB_LAUNCHED(m);
   }
-  k_scale_rows<<<blocks_for(n - nv, 256), 256, 0, m->stream>>>(nv, n, v, m->gdiag.p, z);
-  PB_LAUNCHED(m);
-  return PBFB_OK;
+  return surface_rows_precond(m, v, z);
 }
 
 static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, int maxit, int precond,
@@ -597,11 +621,12 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
     set_error("restart must be in [1, 400]");
     return PBFB_ERR_INVALID;
   }
-  if ((precond != PBFB_PRECOND_JACOBI && precond != PBFB_PRECOND_BLOCK) || inner_iters < 1 || inner_iters > 500) {
+  if ((precond != PBFB_PRECOND_JACOBI && precond != PBFB_PRECOND_BLOCK && precond != PBFB_PRECOND_BLOCK_DENSE) ||
+      inner_iters < 1 || inner_iters > 500) {
     set_error("invalid preconditioner settings");
     return PBFB_ERR_INVALID;
   }
-  const bool flexible = precond == PBFB_PRECOND_BLOCK;
+  const bool flexible = precond != PBFB_PRECOND_JACOBI;
   if (flexible) {
     PB_TRY(ensure(m->gZ, (size_t)restart * n));
     if (m->gpcg.n < 6 * (size_t)n) {
@@ -618,7 +643,7 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
   const int nbr = std::min(152, std::max(1, blocks_for(n, MD_T)));
   PB_TRY(ensure(m->gpart, (size_t)(restart + 2) * nbr + 8));
   PB_TRY(jacobi(m, m->gdiag.p));
-  if (flexible) PB_TRY(prepare_block_precond(m));
+  if (flexible) PB_TRY(prepare_block_precond(m, precond == PBFB_PRECOND_BLOCK_DENSE));
   if (flexible && m->gones.n < (size_t)n) {
     PB_TRY(m->gones.alloc(n));
     std::vector<double> ones(n, 1.0);
@@ -1263,7 +1288,7 @@ void pbfb_default_opts(pbfb_newton_opts* o) {
   o->R_e = 1.4;
   o->omega_warm_start = 0;
   o->omega_search = 1;
-  o->precond = PBFB_PRECOND_BLOCK;
+  o->precond = PBFB_PRECOND_BLOCK_DENSE;
   o->inner_iters = 20;
 }
 
@@ -1410,6 +1435,23 @@ int pbfb_bem_apply(pbfb_mesh* h, int which, int op, const double* x_dev, double*
   return cudaStreamSynchronize(m->stream) == cudaSuccess ? PBFB_OK : PBFB_ERR_CUDA;
 }
 
+int pbfb_single_layer_dense(pbfb_mesh* h, int which, int inverse, float* out_dev, int32_t ld_out) {
+  PB_HANDLE(h);
+  PB_NEED_PARAMS;
+  pbfb::Surface* s = which == PBFB_GAMMA_M ? &m->sm : &m->ss;
+  if (!out_dev || (which != PBFB_GAMMA_M && which != PBFB_GAMMA_S) || (inverse != 0 && inverse != 1) ||
+      ld_out < s->nv) {
+    pbfb::set_error("single_layer_dense: bad argument");
+    return PBFB_ERR_INVALID;
+  }
+  const double kap = which == PBFB_GAMMA_M ? 0.0 : m->kappa;
+  const bool have = s->vinv_ok && s->vinv_kappa == kap;
+  if (!inverse || !have) PB_TRY(pbfb::build_dense_single_layer(m, s, kap, inverse != 0));
+  // the stored inverse is -V^-1
+  PB_TRY(pbfb::dense_copy_out(m, s, inverse ? -1.f : 1.f, out_dev, ld_out));
+  return cudaStreamSynchronize(m->stream) == cudaSuccess ? PBFB_OK : PBFB_ERR_CUDA;
+}
+
 int pbfb_bem_apply_noalloc(pbfb_mesh* h, int which, int op, const double* x_dev, double* y_dev) {
   PB_HANDLE(h);
   PB_NEED_PARAMS;
@@ -1506,6 +1548,7 @@ int pbfb_profile(pbfb_mesh* h, int enable, int reset, double* stats) {
   pbfb::timer_flush(m->t_nbodyff);
   pbfb::timer_flush(m->t_spmv);
   pbfb::timer_flush(m->t_elem);
+  pbfb::timer_flush(m->t_dense);
   if (stats) {
     stats[0] = m->launches;
     stats[1] = m->t_nbody.count;
@@ -1522,12 +1565,12 @@ int pbfb_profile(pbfb_mesh* h, int enable, int reset, double* stats) {
     stats[12] = m->t_nbodyff.count;
     stats[13] = m->t_nbodyff.ms;
     stats[14] = m->t_nbodyff.work;
-    stats[15] = 0.0;
+    stats[15] = m->t_dense.ms;
   }
   if (reset) {
     m->launches = 0;
     m->nbody_flops = 0.0;
-    for (auto* t : {&m->t_nbody, &m->t_nbody64, &m->t_nbodyff, &m->t_spmv, &m->t_elem}) {
+    for (auto* t : {&m->t_nbody, &m->t_nbody64, &m->t_nbodyff, &m->t_spmv, &m->t_elem, &m->t_dense}) {
       t->ms = 0;
       t->count = 0;
       t->work = 0;

@@ -22,7 +22,7 @@ FP64, MIXED, FLOAT2 = 0, 1, 2
 LINEAR, T3, HS, T5, T7 = 0, 1, 2, 3, 4
 NEWTON, PICARD = 0, 1
 GAMMA_M, GAMMA_S = 0, 1
-JACOBI, BLOCK = 0, 1
+JACOBI, BLOCK, BLOCK_DENSE = 0, 1, 2
 MAX_TRACE = 64
 
 # every symbol include/pbfb.h declares
@@ -33,7 +33,7 @@ EXPORTS = [
     "pbfb_apply", "pbfb_bem_apply", "pbfb_fem_rows", "pbfb_gmres", "pbfb_omega_eval",
     "pbfb_energy", "pbfb_profile", "pbfb_bem_apply_noalloc", "pbfb_set_tuning",
     "pbfb_server_create", "pbfb_server_submit", "pbfb_server_poll", "pbfb_server_stats",
-    "pbfb_server_destroy", "pbfb_solve_batch",
+    "pbfb_server_destroy", "pbfb_solve_batch", "pbfb_single_layer_dense",
 ]
 
 
@@ -142,6 +142,7 @@ def load():
         "pbfb_server_stats": (I, [P, P]),
         "pbfb_server_destroy": (I, [P]),
         "pbfb_solve_batch": (I, [P, P, I, I, P]),
+        "pbfb_single_layer_dense": (I, [P, I, I, P, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -257,6 +258,12 @@ class Mesh:
         (no allocation; at most 65,536 quadrature points per surface)."""
         _check(load().pbfb_bem_apply_noalloc(self.h, which, op, _ptr(x_dev), _ptr(y_dev)))
 
+    def single_layer_dense(self, which, inverse, out_dev, ld=None):
+        """Dense float32 single-layer matrix of a surface (or its inverse) into out_dev, a
+        device float32 array of shape (n_surface, ld)."""
+        n = self.n_m if which == GAMMA_M else self.n_s
+        _check(load().pbfb_single_layer_dense(self.h, which, int(inverse), _ptr(out_dev), ld or n))
+
     def fem_rows(self):
         rp = np.zeros(self.n_v + 1, np.int32)
         col = np.zeros(self.fem_nnz, np.int32)
@@ -292,7 +299,8 @@ class Mesh:
         return dict(launches=st[0], nbody_launches=st[1], nbody_ms=st[2], nbody_pairs=st[3],
                     spmv_launches=st[4], spmv_ms=st[5], elem_launches=st[6], elem_ms=st[7],
                     nbody_flops=st[8], nbody64_launches=st[9], nbody64_ms=st[10], nbody64_pairs=st[11],
-                    nbodyff_launches=st[12], nbodyff_ms=st[13], nbodyff_pairs=st[14])
+                    nbodyff_launches=st[12], nbodyff_ms=st[13], nbodyff_pairs=st[14],
+                    dense_build_ms=st[15])
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
