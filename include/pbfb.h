@@ -290,7 +290,10 @@ int pbfb_energy(pbfb_mesh* mesh, const double* xL_dev, const double* xNL_dev, do
  * evaluates two targets per f32x2 instruction (needs 2 or more targets per
  * thread).  0 restores the built-in heuristic.  The unpacked shapes change
  * results only in float64 rounding; the packed variant rounds the same float32
- * operations (no fused reassociation differences beyond FMA contraction). */
+ * operations (no fused reassociation differences beyond FMA contraction).
+ * Bit 1 of packed (packed = 2 or 3) selects the one-target-per-thread
+ * float-float far field instead of the default two-target packed one; both
+ * give bitwise identical results. */
 int pbfb_set_tuning(pbfb_mesh* mesh, int nbody_targets_per_thread, int nbody_blocks_per_sm,
                     int nbody_packed);
 

@@ -836,6 +836,191 @@ __global__ void __launch_bounds__(NT) k_nbody_ff(int nq, const float4* __restric
   if (i < nq) out[(int64_t)blockIdx.y * nq + i] = acc64;
 }
 
+// Packed float-float N-body: two targets per thread, every float-float operation applied to both
+// with the Blackwell float2 arithmetic (__fadd2_rn / __fmul2_rn / __ffma2_rn, per component the
+// same rounding as the scalar _rn operations), halving the issue slots of k_nbody_ff.  Each lane
+// performs exactly the scalar kernel's operation sequence, so the results are bitwise those of
+// k_nbody_ff under the same source split.  Sources are staged pre-duplicated; tiles holding one of
+// the thread's own targets take the scalar path for the coincident-point test.
+struct ffv { float2 h, l; };
+__device__ __forceinline__ float2 vdup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, vneg(b)); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ ffv v_two_sum(float2 a, float2 b) {
+  float2 s = vadd(a, b);
+  float2 bb = vsub(s, a);
+  float2 e = vadd(vsub(a, vsub(s, bb)), vsub(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ffv v_fast_two_sum(float2 a, float2 b) {
+  float2 s = vadd(a, b);
+  return {s, vsub(b, vsub(s, a))};
+}
+__device__ __forceinline__ ffv v_add(ffv a, ffv b) {
+  ffv s = v_two_sum(a.h, b.h);
+  float2 lo = vadd(s.l, vadd(a.l, b.l));
+  return v_fast_two_sum(s.h, lo);
+}
+__device__ __forceinline__ ffv v_mul(ffv a, ffv b) {
+  float2 p = vmul(a.h, b.h);
+  float2 e = vfma(a.h, b.h, vneg(p));
+  e = vfma(a.h, b.l, e);
+  e = vfma(a.l, b.h, e);
+  return v_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ffv v_sq(ffv a) {
+  float2 p = vmul(a.h, a.h);
+  float2 e = vfma(a.h, a.h, vneg(p));
+  e = vfma(vadd(a.h, a.h), a.l, e);
+  return v_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ffv v_diff(float2 xh, float2 xl, float2 yh, float2 yl) {
+  ffv s = v_two_sum(xh, vneg(yh));
+  return v_fast_two_sum(s.h, vadd(s.l, vsub(xl, yl)));
+}
+__device__ __forceinline__ ffv v_dot3(ffv a0, ffv a1, ffv a2, ffv b0, ffv b1, ffv b2) {
+  float2 p0 = vmul(a0.h, b0.h), p1 = vmul(a1.h, b1.h), p2 = vmul(a2.h, b2.h);
+  float2 e0 = vfma(a0.l, b0.h, vfma(a0.h, b0.l, vfma(a0.h, b0.h, vneg(p0))));
+  float2 e1 = vfma(a1.l, b1.h, vfma(a1.h, b1.l, vfma(a1.h, b1.h, vneg(p1))));
+  float2 e2 = vfma(a2.l, b2.h, vfma(a2.h, b2.l, vfma(a2.h, b2.h, vneg(p2))));
+  ffv s1 = v_two_sum(p0, p1);
+  ffv s2 = v_two_sum(s1.h, p2);
+  float2 lo = vadd(vadd(s1.l, s2.l), vadd(vadd(e0, e1), e2));
+  return v_fast_two_sum(s2.h, lo);
+}
+__device__ __forceinline__ ffv v_rsqrt(ffv r) {
+  float2 y0 = make_float2(rsqrtf(r.h.x), rsqrtf(r.h.y));
+  float2 t = vmul(y0, y0);
+  float2 te = vfma(y0, y0, vneg(t));
+  float2 a = vmul(r.h, t);
+  float2 ae = vfma(r.h, t, vneg(a));
+  float2 z = vadd(vsub(a, vdup(1.0f)), vfma(r.l, t, vfma(r.h, te, ae)));
+  return v_fast_two_sum(y0, vmul(vmul(vdup(-0.5f), y0), z));
+}
+// exp(-x) per lane as ff_expm; the table index is clamped and the lanes with x >= FF_XMAX give 0
+__device__ __forceinline__ ffv v_expm(ffv x, const float2* __restrict__ tab_hi) {
+  float2 xs = vmul(x.h, vdup(256.0f));
+  int k0 = __float2int_rd(xs.x), k1 = __float2int_rd(xs.y);
+  k0 = min(max(k0, 0), FF_TABLE_HI * 16 - 1);
+  k1 = min(max(k1, 0), FF_TABLE_HI * 16 - 1);
+  float2 kf = vmul(make_float2((float)k0, (float)k1), vdup(0.00390625f));
+  ffv f = v_fast_two_sum(vsub(x.h, kf), x.l);
+  ffv f2 = v_sq(f);
+  float2 p2 = vmul(f.h, vfma(f.h, vfma(f.h, vdup(-1.0f / 120.0f), vdup(1.0f / 24.0f)), vdup(-1.0f / 6.0f)));
+  ffv one_minus = v_two_sum(vdup(1.0f), vneg(f.h));
+  one_minus = v_fast_two_sum(one_minus.h, vsub(one_minus.l, f.l));
+  ffv tail = v_fast_two_sum(vmul(vdup(0.5f), f2.h), vfma(f2.h, p2, vmul(vdup(0.5f), f2.l)));
+  ffv ef = v_add(one_minus, tail);
+  const float2 a0 = tab_hi[k0 >> 4], a1 = tab_hi[k1 >> 4];
+  const float2 b0 = c_ff_exp_lo[k0 & 15], b1 = c_ff_exp_lo[k1 & 15];
+  ffv r = v_mul(v_mul(ef, ffv{make_float2(a0.x, a1.x), make_float2(a0.y, a1.y)}),
+                ffv{make_float2(b0.x, b1.x), make_float2(b0.y, b1.y)});
+  if (x.h.x >= FF_XMAX) r.h.x = r.l.x = 0.f;
+  if (x.h.y >= FF_XMAX) r.h.y = r.l.y = 0.f;
+  return r;
+}
+
+// per source, duplicated: yh.x yh.y | yh.z sh | yl.x yl.y | yl.z sl | mh.x mh.y | mh.z ml.x | ml.y ml.z
+template <bool YUK>
+__device__ __forceinline__ ffv v_pair(const float4* __restrict__ q, const float2 (&th)[3], const float2 (&tl)[3],
+                                      ffv kap, const float2* __restrict__ tab) {
+  const float4 c0 = q[0], c1 = q[1], c2 = q[2], c3 = q[3], c4 = q[4], c5 = q[5], c6 = q[6];
+  const float2 pxh = make_float2(c0.x, c0.y), pyh = make_float2(c0.z, c0.w);
+  const float2 pzh = make_float2(c1.x, c1.y), sh = make_float2(c1.z, c1.w);
+  const float2 pxl = make_float2(c2.x, c2.y), pyl = make_float2(c2.z, c2.w);
+  const float2 pzl = make_float2(c3.x, c3.y), sl = make_float2(c3.z, c3.w);
+  const ffv mx{make_float2(c4.x, c4.y), make_float2(c5.z, c5.w)};
+  const ffv my{make_float2(c4.z, c4.w), make_float2(c6.x, c6.y)};
+  const ffv mz{make_float2(c5.x, c5.y), make_float2(c6.z, c6.w)};
+  ffv d0 = v_diff(th[0], tl[0], pxh, pxl);
+  ffv d1 = v_diff(th[1], tl[1], pyh, pyl);
+  ffv d2 = v_diff(th[2], tl[2], pzh, pzl);
+  ffv r2 = v_dot3(d0, d1, d2, d0, d1, d2);
+  ffv ri = v_rsqrt(r2);
+  ffv nd = v_dot3(mx, my, mz, d0, d1, d2);
+  ffv ri2 = v_sq(ri);
+  if (YUK) {
+    ffv r = v_mul(r2, ri);
+    ffv x = v_mul(kap, r);
+    ffv e = v_expm(x, tab);
+    ffv one_x = v_two_sum(vdup(1.0f), x.h);
+    one_x = v_fast_two_sum(one_x.h, vadd(one_x.l, x.l));
+    ffv t = v_add(ffv{sh, sl}, v_mul(v_mul(nd, one_x), ri2));
+    return v_mul(t, v_mul(e, ri));
+  }
+  ffv t = v_add(ffv{sh, sl}, v_mul(nd, ri2));
+  return v_mul(t, ri);
+}
+
+template <int NT, bool YUK>
+__global__ void __launch_bounds__(NT) k_nbody_ff2(int nq, const float4* __restrict__ tgt,
+                                                  const float4* __restrict__ src, float kh, float kl,
+                                                  const float2* __restrict__ tab_hi, int per_split,
+                                                  double* __restrict__ out) {
+  __shared__ float4 shv[NT][7];   // duplicated (packed) copies
+  __shared__ float4 shs[4][NT];   // scalar copies for the tiles that hold the thread's own targets
+  __shared__ float2 tab[YUK ? FF_TABLE_HI : 1];
+  if (YUK)
+    for (int k = threadIdx.x; k < FF_TABLE_HI; k += NT) tab[k] = tab_hi[k];
+  const int t0 = blockIdx.x * 2 * NT;
+  const int i0 = t0 + threadIdx.x, i1 = t0 + NT + threadIdx.x;
+  const int c0 = i0 < nq ? i0 : 0, c1 = i1 < nq ? i1 : 0;
+  const float4 a0 = tgt[2 * c0], b0 = tgt[2 * c0 + 1];
+  const float4 a1 = tgt[2 * c1], b1 = tgt[2 * c1 + 1];
+  const float2 th[3] = {make_float2(a0.x, a1.x), make_float2(a0.y, a1.y), make_float2(a0.z, a1.z)};
+  const float2 tl[3] = {make_float2(b0.x, b1.x), make_float2(b0.y, b1.y), make_float2(b0.z, b1.z)};
+  const float ths0[3] = {a0.x, a0.y, a0.z}, tls0[3] = {b0.x, b0.y, b0.z};
+  const float ths1[3] = {a1.x, a1.y, a1.z}, tls1[3] = {b1.x, b1.y, b1.z};
+  const ffv kapv{vdup(kh), vdup(kl)};
+  const ff kap{kh, kl};
+  const int sb = blockIdx.y * per_split;
+  const int se = min(nq, sb + per_split);
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int s0 = sb; s0 < se; s0 += NT) {
+    const int j = s0 + threadIdx.x;
+    float4 c[4];
+    if (j < se) {
+      for (int k = 0; k < 4; ++k) c[k] = src[4 * j + k];
+    } else {  // never read: the loops below stop at se
+      c[0] = c[1] = c[2] = c[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int k = 0; k < 4; ++k) shs[k][threadIdx.x] = c[k];
+    shv[threadIdx.x][0] = make_float4(c[0].x, c[0].x, c[0].y, c[0].y);
+    shv[threadIdx.x][1] = make_float4(c[0].z, c[0].z, c[0].w, c[0].w);
+    shv[threadIdx.x][2] = make_float4(c[1].x, c[1].x, c[1].y, c[1].y);
+    shv[threadIdx.x][3] = make_float4(c[1].z, c[1].z, c[1].w, c[1].w);
+    shv[threadIdx.x][4] = make_float4(c[2].x, c[2].x, c[2].y, c[2].y);
+    shv[threadIdx.x][5] = make_float4(c[2].z, c[2].z, c[3].x, c[3].x);
+    shv[threadIdx.x][6] = make_float4(c[3].y, c[3].y, c[3].z, c[3].z);
+    __syncthreads();
+    const int cnt = min(NT, se - s0);
+    const bool diag = (s0 < t0 + 2 * NT) && (s0 + NT > t0);
+    if (!diag) {
+      ffv acc{vdup(0.f), vdup(0.f)};
+      for (int jj = 0; jj < cnt; ++jj) acc = v_add(acc, v_pair<YUK>(shv[jj], th, tl, kapv, tab));
+      acc0 += (double)acc.h.x + (double)acc.l.x;
+      acc1 += (double)acc.h.y + (double)acc.l.y;
+    } else {
+      ff s0acc{0.f, 0.f}, s1acc{0.f, 0.f};
+      for (int jj = 0; jj < cnt; ++jj) {
+        if (s0 + jj != i0)
+          s0acc = ff_add(s0acc, ff_pair<YUK>(shs[0][jj], shs[1][jj], shs[2][jj], shs[3][jj], ths0, tls0, kap, tab));
+        if (s0 + jj != i1)
+          s1acc = ff_add(s1acc, ff_pair<YUK>(shs[0][jj], shs[1][jj], shs[2][jj], shs[3][jj], ths1, tls1, kap, tab));
+      }
+      acc0 += (double)s0acc.h + (double)s0acc.l;
+      acc1 += (double)s1acc.h + (double)s1acc.l;
+    }
+    __syncthreads();
+  }
+  if (i0 < nq) out[(int64_t)blockIdx.y * nq + i0] = acc0;
+  if (i1 < nq) out[(int64_t)blockIdx.y * nq + i1] = acc1;
+}
+
 // val[0][j] = sum over the source splits of val[split][j] (fixed order)
 __global__ void k_split_sum(int nq, int nsplit, double* __restrict__ val) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1141,9 +1326,12 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
   cudaEvent_t ev;
   timer_begin(m, m->t_nbodyff, &ev);
   constexpr int NT = 128;
-  const int ntb = blocks_for(nq, NT);
+  const bool pk = !m->tune_ff_scalar;   // two targets per thread (k_nbody_ff2) unless tuned off
+  const int ntb = blocks_for(nq, pk ? 2 * NT : NT);
+  // source splits from the packed grid in both variants, so that they sum in the same order
+  const int ntb2 = blocks_for(nq, 2 * NT);
   const int bps = m->tune_bps > 0 ? m->tune_bps : 8;  // GB300 sweep: 8 blocks per SM of source splits
-  int nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * NT)));
+  int nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb2), blocks_for(nq, 4 * NT)));
   const int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
   nsplit = blocks_for(nq, per);
   if ((size_t)nsplit * nq > s->val.n) {
@@ -1152,7 +1340,11 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
   }
   const float kh = (float)kappa, kl = (float)(kappa - (double)kh);
   dim3 grid(ntb, nsplit);
-  if (yuk)
+  if (pk && yuk)
+    k_nbody_ff2<NT, true><<<grid, NT, 0, m->stream>>>(nq, s->fftgt.p, s->ffsrc.p, kh, kl, m->ff_tab.p, per, s->val.p);
+  else if (pk)
+    k_nbody_ff2<NT, false><<<grid, NT, 0, m->stream>>>(nq, s->fftgt.p, s->ffsrc.p, kh, kl, m->ff_tab.p, per, s->val.p);
+  else if (yuk)
     k_nbody_ff<NT, true><<<grid, NT, 0, m->stream>>>(nq, s->fftgt.p, s->ffsrc.p, kh, kl, m->ff_tab.p, per, s->val.p);
   else
     k_nbody_ff<NT, false><<<grid, NT, 0, m->stream>>>(nq, s->fftgt.p, s->ffsrc.p, kh, kl, m->ff_tab.p, per, s->val.p);

@@ -182,6 +182,7 @@ struct Mesh {
   int tune_tpt = 0;                 // float32 far field: targets per thread (0 = heuristic)
   int tune_bps = 0;                 // float32 far field: target blocks per SM for the source split
   int tune_packed = 0;              // float32 far field: 1 = packed f32x2 kernel
+  int tune_ff_scalar = 0;           // float-float far field: 1 = one target per thread (k_nbody_ff)
   bool dense_m = false, dense_s = false;  // surface rows of the block preconditioner use V^-1
   DBuf<float> dwork;                // dense single-layer build: W chunk, sweep panels
   DBuf<int> dflag;                  // sweep pivot status

@@ -1521,11 +1521,12 @@ int pbfb_energy(pbfb_mesh* h, const double* xL_dev, const double* xNL_dev, doubl
 
 int pbfb_set_tuning(pbfb_mesh* h, int nbody_targets_per_thread, int nbody_blocks_per_sm, int nbody_packed) {
   PB_HANDLE(h);
-  if (nbody_packed < 0 || nbody_packed > 1) {
-    pbfb::set_error("set_tuning: packed must be 0 or 1");
+  if (nbody_packed < 0 || nbody_packed > 3) {
+    pbfb::set_error("set_tuning: packed must be in 0..3");
     return PBFB_ERR_INVALID;
   }
-  m->tune_packed = nbody_packed;
+  m->tune_packed = nbody_packed & 1;
+  m->tune_ff_scalar = (nbody_packed >> 1) & 1;
   if (nbody_targets_per_thread != 0 && nbody_targets_per_thread != 1 && nbody_targets_per_thread != 2 &&
       nbody_targets_per_thread != 4 && nbody_targets_per_thread != 8) {
     pbfb::set_error("set_tuning: targets per thread must be 0, 1, 2, 4 or 8");

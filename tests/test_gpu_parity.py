@@ -286,3 +286,25 @@ def test_error_statuses(tiny_case):
     _, res = m.solve(c.eps_in, c.eps_out, c.kappa, c.T)
     assert res["status"] == 0
     m.close()
+
+
+def test_float_float_packed_kernel_is_bitwise_scalar(pair):
+    """The two-targets-per-thread float-float far field performs each lane's operations in
+    the scalar kernel's order: identical results, ragged tails included."""
+    import torch
+    from paper_2511_21713_gb300 import pbfb
+    case, m, P = pair
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.FLOAT2)
+    rng = np.random.default_rng(21)
+    try:
+        for which, n in ((pbfb.GAMMA_M, P.nm), (pbfb.GAMMA_S, P.ns)):
+            x = dev(rng.standard_normal(n) + 0.5)
+            for op in (0, 1):
+                ya, yb = dev(np.zeros(n)), dev(np.zeros(n))
+                m.set_tuning(0, 0, 0)
+                m.bem_apply(which, op, x, ya)
+                m.set_tuning(0, 0, 2)
+                m.bem_apply(which, op, x, yb)
+                assert torch.equal(ya, yb), (which, op)
+    finally:
+        m.set_tuning(0, 0, 0)
