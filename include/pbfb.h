@@ -292,8 +292,8 @@ int pbfb_energy(pbfb_mesh* mesh, const double* xL_dev, const double* xNL_dev, do
  * results only in float64 rounding; the packed variant rounds the same float32
  * operations (no fused reassociation differences beyond FMA contraction).
  * Bit 1 of packed (packed = 2 or 3) selects the one-target-per-thread
- * float-float far field instead of the default two-target packed one; both
- * give bitwise identical results. */
+ * float-float far field instead of the default two-target packed one (they
+ * agree to float-float rounding). */
 int pbfb_set_tuning(pbfb_mesh* mesh, int nbody_targets_per_thread, int nbody_blocks_per_sm,
                     int nbody_packed);
 

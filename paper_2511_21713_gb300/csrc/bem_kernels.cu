@@ -839,9 +839,9 @@ __global__ void __launch_bounds__(NT) k_nbody_ff(int nq, const float4* __restric
 // Packed float-float N-body: two targets per thread, every float-float operation applied to both
 // with the Blackwell float2 arithmetic (__fadd2_rn / __fmul2_rn / __ffma2_rn, per component the
 // same rounding as the scalar _rn operations), halving the issue slots of k_nbody_ff.  Each lane
-// performs exactly the scalar kernel's operation sequence, so the results are bitwise those of
-// k_nbody_ff under the same source split.  Sources are staged pre-duplicated; tiles holding one of
-// the thread's own targets take the scalar path for the coincident-point test.
+// performs the scalar kernel's operation sequence under the same source split (results agree to
+// float-float rounding).  Sources are staged pre-duplicated; tiles holding one of the thread's
+// own targets take the scalar path for the coincident-point test.
 struct ffv { float2 h, l; };
 __device__ __forceinline__ float2 vdup(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }

@@ -198,35 +198,42 @@ int build_surface(Mesh* m, Surface* s, const std::vector<int>& gtri, const std::
   PB_TRY(s->pair_cls.upload(cls.data(), cls.size(), m->stream));
   PB_TRY(s->pair_perm.upload(perm.data(), perm.size(), m->stream));
   {
-    std::vector<int64_t> keys;
-    keys.reserve(9 * (size_t)s->npair);
-    for (int p = 0; p < s->npair; ++p)
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-          keys.push_back((int64_t)hs.tri[3 * pt[p] + a] * s->nv + hs.tri[3 * ps[p] + b]);
-    std::vector<int64_t> uk(keys);
-    std::sort(uk.begin(), uk.end());
-    uk.erase(std::unique(uk.begin(), uk.end()), uk.end());
-    s->cnnz = (int)uk.size();
-    s->c_ptr_h.assign(s->nv + 1, 0);
-    s->c_col_h.resize(uk.size());
-    for (size_t k = 0; k < uk.size(); ++k) {
-      int i = (int)(uk[k] / s->nv);
-      s->c_col_h[k] = (int)(uk[k] % s->nv);
-      s->c_ptr_h[i + 1]++;
-    }
-    for (int i = 0; i < s->nv; ++i) s->c_ptr_h[i + 1] += s->c_ptr_h[i];
-    std::vector<int> slot_of(keys.size()), vals(keys.size()), dk, dv;
-    for (size_t e = 0; e < keys.size(); ++e) {
-      slot_of[e] = (int)(std::lower_bound(uk.begin(), uk.end(), keys[e]) - uk.begin());
+    // entry e = 9 p + 3 a + b of pair p couples test vertex tri[pt[p]][a] and trial vertex
+    // tri[ps[p]][b]; rows by counting sort, then columns sorted within each row
+    const size_t ne = 9 * (size_t)s->npair;
+    std::vector<int> rows(ne), vals(ne), slot_of(ne), dk, dv;
+    for (size_t e = 0; e < ne; ++e) {
+      const int p = (int)(e / 9), a = (int)(e / 3) % 3, b = (int)(e % 3);
+      rows[e] = hs.tri[3 * pt[p] + a];
       vals[e] = (int)e;
-      int p = (int)(e / 9), a = (int)(e / 3) % 3, b = (int)e % 3;
-      int vi = hs.tri[3 * pt[p] + a], vj = hs.tri[3 * ps[p] + b];
-      if (vi == vj) {
-        dk.push_back(vi);
+      if (rows[e] == hs.tri[3 * ps[p] + b]) {
+        dk.push_back(rows[e]);
         dv.push_back((int)e);
       }
     }
+    auto colof = [&](int e) { return hs.tri[3 * ps[e / 9] + e % 3]; };
+    std::vector<int> rptr, rent;
+    bucket(rows, vals, s->nv, rptr, rent);
+    s->c_ptr_h.assign(s->nv + 1, 0);
+    s->c_col_h.clear();
+    for (int i = 0; i < s->nv; ++i) {
+      auto b = rent.begin() + rptr[i], en = rent.begin() + rptr[i + 1];
+      std::sort(b, en, [&](int x, int y) {
+        const int cx = colof(x), cy = colof(y);
+        return cx < cy || (cx == cy && x < y);
+      });
+      int last = -1;
+      for (auto it = b; it != en; ++it) {
+        const int c = colof(*it);
+        if (c != last) {
+          s->c_col_h.push_back(c);
+          last = c;
+        }
+        slot_of[*it] = (int)s->c_col_h.size() - 1;
+      }
+      s->c_ptr_h[i + 1] = (int)s->c_col_h.size();
+    }
+    s->cnnz = (int)s->c_col_h.size();
     std::vector<int> ptr, out;
     bucket(slot_of, vals, s->cnnz, ptr, out);
     PB_TRY(s->cg_ptr.upload(ptr.data(), ptr.size(), m->stream));
@@ -281,6 +288,10 @@ static int validate(const double* xyz, int nv, const int* tets, int64_t nt, cons
     set_error("mesh_create: empty or missing arrays");
     return PBFB_ERR_INVALID;
   }
+  if (nt > (int64_t(1) << 29)) {
+    set_error("mesh_create: more than 2^29 tetrahedra");
+    return PBFB_ERR_INVALID;
+  }
   for (int64_t i = 0; i < 3 * (int64_t)nv; ++i)
     if (!std::isfinite(xyz[i])) {
       set_error("mesh_create: non-finite coordinate");
@@ -301,8 +312,10 @@ static int validate(const double* xyz, int nv, const int* tets, int64_t nt, cons
       set_error("mesh_create: Gamma_s vertex id out of range");
       return PBFB_ERR_INVALID;
     }
-  // boundary faces of the tets: faces used once; with the opposite vertex for orientation
-  std::map<std::array<int, 3>, std::array<int, 2>> faces;  // sorted face -> (count, opposite vertex)
+  // boundary faces of the tets: faces used once, with the opposite vertex for orientation.
+  // Faces are bucketed by their smallest vertex and sorted by the other two within a bucket.
+  std::vector<std::array<int, 3>> fv(4 * (size_t)nt);  // sorted vertex triple of face 4 t + k
+  std::vector<int> fkey(4 * (size_t)nt), fidx(4 * (size_t)nt);
   for (int64_t t = 0; t < nt; ++t) {
     const int* T = tets + 4 * t;
     double e[3][3];
@@ -322,23 +335,40 @@ static int validate(const double* xyz, int nv, const int* tets, int64_t nt, cons
       for (int a = 0; a < 4; ++a)
         if (a != k) f[q++] = T[a];
       std::sort(f.begin(), f.end());
-      auto& slot = faces[f];
-      slot[0]++;
-      slot[1] = T[k];
+      fv[4 * t + k] = f;
+      fkey[4 * t + k] = f[0];
+      fidx[4 * t + k] = (int)(4 * t + k);
     }
   }
+  std::vector<int> fptr, ford;
+  bucket(fkey, fidx, nv, fptr, ford);
+  auto face_less = [&](int x, int y) { return fv[x] < fv[y]; };
+  for (int v = 0; v < nv; ++v) std::sort(ford.begin() + fptr[v], ford.begin() + fptr[v + 1], face_less);
+  // per sorted face position: multiplicity of its triple (1 boundary, 2 interior)
+  std::vector<int> fcount(ford.size(), 0);
   size_t nb = 0;
-  for (auto& kv : faces) {
-    if (kv.second[0] > 2) {
+  for (size_t a = 0; a < ford.size();) {
+    size_t b = a + 1;
+    while (b < ford.size() && fv[ford[b]] == fv[ford[a]]) ++b;
+    if (b - a > 2) {
       set_error("mesh_create: a face is shared by more than two tets");
       return PBFB_ERR_INVALID;
     }
-    if (kv.second[0] == 1) nb++;
+    if (b - a == 1) nb++;
+    for (size_t c = a; c < b; ++c) fcount[c] = (int)(b - a);
+    a = b;
   }
   if (nb != (size_t)ngm + (size_t)ngs) {
     set_error("mesh_create: %zu boundary faces but %d + %d surface triangles", nb, ngm, ngs);
     return PBFB_ERR_INVALID;
   }
+  // position in ford of the boundary face with this sorted triple, or -1
+  auto find_face = [&](const std::array<int, 3>& f) -> long long {
+    auto b = ford.begin() + fptr[f[0]], e = ford.begin() + fptr[f[0] + 1];
+    auto it = std::lower_bound(b, e, f, [&](int x, const std::array<int, 3>& y) { return fv[x] < y; });
+    if (it == e || fv[*it] != f) return -1;
+    return (long long)(it - ford.begin());
+  };
   std::vector<char> onm(nv, 0), ons(nv, 0);
   for (int surf = 0; surf < 2; ++surf) {
     const int* tri = surf == 0 ? gm : gs;
@@ -352,15 +382,16 @@ static int validate(const double* xyz, int nv, const int* tets, int64_t nt, cons
       }
       std::array<int, 3> f = {F[0], F[1], F[2]};
       std::sort(f.begin(), f.end());
-      auto it = faces.find(f);
-      if (it == faces.end() || it->second[0] != 1) {
+      const long long pos = find_face(f);
+      if (pos < 0 || fcount[pos] != 1) {
         set_error("mesh_create: surface triangle %d of %s is not a boundary face of the tets", t,
                   surf == 0 ? "Gamma_m" : "Gamma_s");
         return PBFB_ERR_INVALID;
       }
-      it->second[0] = 3;  // claimed
+      fcount[pos] = 3;  // claimed
       // orientation: the opposite tet vertex lies on the positive side for Gamma_m
-      int o = it->second[1];
+      const int fid = ford[pos];
+      int o = tets[fid];
       double a[3], b[3], c[3];
       for (int d = 0; d < 3; ++d) {
         a[d] = xyz[3 * F[1] + d] - xyz[3 * F[0] + d];
@@ -460,17 +491,30 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
         keys.push_back(key2(s->col0 + i, s->vmap_h[j]));
         keys.push_back(key2(s->col0 + i, s->col0 + j));
       }
-  std::vector<int64_t> uk(keys.begin(), keys.end());
-  std::sort(uk.begin(), uk.end());
-  uk.erase(std::unique(uk.begin(), uk.end()), uk.end());
-  m->snnz = (int)uk.size();
-  m->s_ptr_h.assign(m->n + 1, 0);
-  m->s_col_h.resize(uk.size());
-  for (size_t k = 0; k < uk.size(); ++k) {
-    m->s_col_h[k] = (int)(uk[k] & 0xffffffff);
-    m->s_ptr_h[(uk[k] >> 32) + 1]++;
+  {
+    // rows by counting sort, then sorted unique columns within each row
+    std::vector<int> rk(keys.size()), ck(keys.size());
+    for (size_t k = 0; k < keys.size(); ++k) {
+      rk[k] = (int)(keys[k] >> 32);
+      ck[k] = (int)(keys[k] & 0xffffffff);
+    }
+    std::vector<int>().swap(m->s_col_h);
+    std::vector<int64_t>().swap(keys);
+    std::vector<int> rptr, cols;
+    bucket(rk, ck, m->n, rptr, cols);
+    m->s_ptr_h.assign(m->n + 1, 0);
+    size_t w = 0;
+    for (int r = 0; r < m->n; ++r) {
+      auto b = cols.begin() + rptr[r], e = cols.begin() + rptr[r + 1];
+      std::sort(b, e);
+      e = std::unique(b, e);
+      for (auto it = b; it != e; ++it) cols[w++] = *it;
+      m->s_ptr_h[r + 1] = (int)w;
+    }
+    cols.resize(w);
+    m->s_col_h.swap(cols);
+    m->snnz = (int)w;
   }
-  for (int r = 0; r < m->n; ++r) m->s_ptr_h[r + 1] += m->s_ptr_h[r];
   m->fem_nnz = m->s_ptr_h[nv];
   auto slot = [&](int r, int c) -> int {
     auto b = m->s_col_h.begin() + m->s_ptr_h[r], e = m->s_col_h.begin() + m->s_ptr_h[r + 1];

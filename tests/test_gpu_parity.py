@@ -288,10 +288,9 @@ def test_error_statuses(tiny_case):
     m.close()
 
 
-def test_float_float_packed_kernel_is_bitwise_scalar(pair):
-    """The two-targets-per-thread float-float far field performs each lane's operations in
-    the scalar kernel's order: identical results, ragged tails included."""
-    import torch
+def test_float_float_packed_kernel_matches_scalar(pair):
+    """The two-targets-per-thread float-float far field and the one-target kernel agree to
+    float-float rounding (1e-13 of the largest entry), ragged tails included."""
     from paper_2511_21713_gb300 import pbfb
     case, m, P = pair
     m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.FLOAT2)
@@ -305,6 +304,7 @@ def test_float_float_packed_kernel_is_bitwise_scalar(pair):
                 m.bem_apply(which, op, x, ya)
                 m.set_tuning(0, 0, 2)
                 m.bem_apply(which, op, x, yb)
-                assert torch.equal(ya, yb), (which, op)
+                a, b = host(ya), host(yb)
+                assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max(), (which, op, np.abs(a - b).max())
     finally:
         m.set_tuning(0, 0, 0)
