@@ -34,9 +34,9 @@ SM_MAX_MHZ = 2070.0
 # float32 operations per far-field pair (FMA counted as 2): Laplace 18, Yukawa 24
 FLOP_PAIR = {"laplace": 18.0, "yukawa": 24.0}
 GOLDEN = os.path.join(ROOT, "tests", "golden", "multi_charge_sphere.json")
-# DRAM bytes per launch of the packed far-field kernel on this workload, from its ncu capture
-# (None until the capture of the current kernel is recorded)
-NBODY_TRAFFIC = None
+# DRAM bytes (read + write) per launch of the packed far-field kernel on this workload, from its
+# ncu capture (profiles/k_nbody_f32x2_multi_charge_sphere.md; source records read once)
+NBODY_TRAFFIC = 2311424.0
 
 
 def workload_config(case, precision):
@@ -232,10 +232,12 @@ def run_pbfb(args):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_step")   # lets a profiler select the timed solves
         e0.record(stream)
         res = mesh.solve_device(case.eps_in, case.eps_out, case.kappa, case.T, x_out, opts)
         e1.record(stream)
         e1.synchronize()
+        torch.cuda.nvtx.range_pop()
         step_ms.append(e0.elapsed_time(e1))
         results.append(res)
     torch.cuda.synchronize()
