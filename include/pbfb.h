@@ -117,7 +117,7 @@ typedef struct pbfb_newton_opts {
                            the surface rows the inverses of the dense float32 single-layer
                            matrices (-V_L on Gamma_m, V_Y on Gamma_s; see
                            pbfb_single_layer_dense), which keep the GMRES iteration count
-                           flat under mesh refinement.  A surface of more than 16384
+                           flat under mesh refinement.  A surface of more than 32768
                            vertices keeps the diagonal.  The inverse of V_L is built once
                            per mesh, that of V_Y once per kappa: about 2 (n/128*128)^3
                            float32 flops and 4 (n/128*128)^2 bytes of device memory per
@@ -248,7 +248,7 @@ int pbfb_bem_apply_noalloc(pbfb_mesh* mesh, int which, int op, const double* x_d
  * surface block of the PBFB_PRECOND_BLOCK_DENSE preconditioner).
  * out_dev: device float32, n_m or n_s rows of row stride ld_out >= that
  * count, caller-owned.  Errors: INVALID for a bad argument or a surface of
- * more than 16384 vertices, STATE before pbfb_set_params, NONFINITE when a
+ * more than 32768 vertices, STATE before pbfb_set_params, NONFINITE when a
  * pivot of the sweep is not positive (V not positive definite in float32).
  * Allocates the matrix (4 ld^2 bytes, ld = n rounded up to 128, kept with
  * the mesh) and a build scratch of at most 256 MiB, released before the call

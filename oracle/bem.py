@@ -88,22 +88,25 @@ def kernels(x, y, ny, kappa):
     return g, dl
 
 
-def classify_pairs(s: Surface, near_factor: float = 2.0):
+def classify_pairs(s: Surface, near_factor: float = 2.0, test_tris=None):
     """Ordered triangle pairs by class.
 
     Returns dict with 'identical' (m,), 'edge' (m,2), 'vertex' (m,2) and
     'near' (m,2) arrays of (test, trial) triangle indices.  Pairs in none of
-    these lists are regular.
+    these lists are regular.  With test_tris (a subset of test triangles) only
+    the pairs whose test triangle is in the subset are listed: the same lists
+    as the full classification filtered to those rows.
     """
     nt = s.nt
+    rows = np.arange(nt) if test_tris is None else np.unique(np.asarray(test_tris, dtype=np.int64))
     # triangles incident to each vertex
     inc = [[] for _ in range(s.n)]
     for t in range(nt):
         for v in s.tl[t]:
             inc[v].append(t)
     shared = {}
-    for v in range(s.n):
-        for t in inc[v]:
+    for t in rows:
+        for v in s.tl[t]:
             for u in inc[v]:
                 shared[(t, u)] = shared.get((t, u), 0) + 1
     edge, vert = [], []
@@ -117,16 +120,17 @@ def classify_pairs(s: Surface, near_factor: float = 2.0):
     tree = cKDTree(s.cen)
     rad = near_factor * s.h.max()
     near = []
-    for t, u in tree.query_pairs(rad, output_type='ndarray'):
-        for a, b in ((t, u), (u, t)):
+    for a, cand in zip(rows, tree.query_ball_point(s.cen[rows], rad)):
+        for b in cand:
             if (a, b) in shared:
                 continue
             d = s.cen[a] - s.cen[b]
             lim = near_factor * max(s.h[a], s.h[b])
             if d @ d < lim * lim:
                 near.append((a, b))
+    ident = rows if test_tris is not None else np.arange(nt)
     srt = lambda L: np.array(sorted(L), dtype=np.int64).reshape(-1, 2)
-    return {'identical': np.arange(nt), 'edge': srt(edge), 'vertex': srt(vert), 'near': srt(near)}
+    return {'identical': ident, 'edge': srt(edge), 'vertex': srt(vert), 'near': srt(near)}
 
 
 def _pair_local(Pt, Ps, ns, bx, by, w, kappa):
@@ -170,7 +174,7 @@ def assemble(s: Surface, kappa: float, n_ss: int = 5, chunk: int = 64, classes=N
     a sample of rows of a large surface.
     """
     if classes is None:
-        classes = classify_pairs(s)
+        classes = classify_pairs(s, test_tris=test_tris)
     if test_tris is not None:
         test_tris = np.asarray(test_tris, dtype=np.int64)
         keep = np.zeros(s.nt, dtype=bool)

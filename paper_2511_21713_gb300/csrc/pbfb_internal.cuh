@@ -242,7 +242,7 @@ int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev);
 int bem_apply_noalloc(Mesh* m, int which, int op, const double* x, double* y);
 
 // ---- bem_dense.cu: dense float32 single layer of a surface and its inverse
-constexpr int DENSE_V_MAX = 16384;  // surface vertices up to which the dense inverse is used
+constexpr int DENSE_V_MAX = 32768;  // surface vertices up to which the dense inverse is used
 int dense_ld(int n);
 size_t dense_bytes(int n);        // the matrix
 size_t dense_work_bytes(int n, int nt);  // build scratch (n vertices, nt triangles)

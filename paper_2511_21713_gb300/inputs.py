@@ -238,3 +238,187 @@ def multi_charge_sphere(nu=20, layers=17, seed=2000, n_charges=200, n_pos=90):
     return sphere_case(nu=nu, a=12.0, R=24.0, layers=layers, q_xyz=q, q_z=z,
                        eps_in=2.0, eps_out=80.0, ionic=0.1, T=300.0,
                        name=f"multi_charge_sphere_nu{nu}_L{layers}")
+
+
+# ----------------------------------------------------------------------------- double helix
+#
+# A synthetic, highly charged double helix standing in for the paper's RNA structures:
+# phosphate charges of -1 e on two backbone strands and interior partial charges, a molecular
+# surface at the level set 1 of a Gaussian density of the atoms, and a graded P1 shell from it to
+# a sphere three Debye lengths further out.
+#
+# Surface and shell are built radially: ray directions d_i are the vertices of a geodesic
+# icosphere stretched along the helix axis (so that triangles spread evenly over the elongated
+# surface) and renormalised; along each ray the surface radius R_i is the outermost crossing of
+# the density level set (which makes the enclosed region star-shaped around the centre, filling
+# any overhang or interior cavity), after crevices narrower than a few rays are filled the way a
+# rolling probe sphere fills them; layer l of the shell sits at R_i (R_out / R_i)^(l / L).  Every
+# tetrahedron of the prism split has two vertices on one ray, so its volume has the sign of the
+# ray triangle's orientation: the shell is valid for any radial profile.
+
+
+def _normal(rng: SplitMix64) -> float:
+    """Standard normal deviate by the Box-Muller transform of two splitmix64 uniforms."""
+    u1 = 1.0 - rng.uniform()
+    u2 = rng.uniform()
+    return float(np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2))
+
+
+def helix_atoms(n_bp=24, seed=3000, n_interior=1500, twist_deg=32.727, rise=2.8, r_phos=9.0,
+                strand_offset_deg=144.0, r_core=8.0):
+    """Atom centres (N,3), radii (N,) and charges (N,) of the synthetic double helix.
+
+    Phosphates: two strands, one per base pair each, at radius r_phos, rotated by twist_deg per
+    base pair and offset by strand_offset_deg between strands, rise per base pair along z (the
+    helix is centred at the origin); radius 1.9, charge -1.  Interior atoms: uniform in the
+    cylinder of radius r_core over the helix length (rejection sampling), radii U(1.4, 1.9),
+    charges N(0, 0.3) shifted to zero sum.  Net charge -2 n_bp.
+    """
+    rng = SplitMix64(seed)
+    z0 = -0.5 * (n_bp - 1) * rise
+    cen, rad, q = [], [], []
+    for s in range(2):
+        for k in range(n_bp):
+            ang = np.deg2rad(k * twist_deg + s * strand_offset_deg)
+            cen.append([r_phos * np.cos(ang), r_phos * np.sin(ang), z0 + k * rise])
+            rad.append(1.9)
+            q.append(-1.0)
+    half = 0.5 * n_bp * rise
+    qi = []
+    while len(qi) < n_interior:
+        x, y = (2 * rng.uniform() - 1) * r_core, (2 * rng.uniform() - 1) * r_core
+        z = (2 * rng.uniform() - 1) * half
+        if x * x + y * y < r_core * r_core:
+            cen.append([x, y, z])
+            rad.append(1.4 + 0.5 * rng.uniform())
+            qi.append(0.3 * _normal(rng))
+    qi = np.array(qi) - np.mean(qi)
+    return np.array(cen), np.array(rad), np.concatenate([np.array(q), qi])
+
+
+def _gaussian_density_grid(cen, rad, spacing, pad):
+    """rho = sum_i exp(-2 (|x - c_i|^2 / r_i^2 - 1)) sampled on a regular grid (each atom summed
+    within 3 r_i, where its term is below 1e-6).  Returns (origin, spacing, rho)."""
+    lo = cen.min(axis=0) - pad
+    hi = cen.max(axis=0) + pad
+    shape = np.ceil((hi - lo) / spacing).astype(int) + 1
+    rho = np.zeros(shape)
+    for c, r in zip(cen, rad):
+        w = 3.0 * r
+        i0 = np.maximum(np.floor((c - w - lo) / spacing).astype(int), 0)
+        i1 = np.minimum(np.ceil((c + w - lo) / spacing).astype(int) + 1, shape)
+        ax = [lo[d] + spacing * np.arange(i0[d], i1[d]) - c[d] for d in range(3)]
+        d2 = ax[0][:, None, None] ** 2 + ax[1][None, :, None] ** 2 + ax[2][None, None, :] ** 2
+        rho[i0[0]:i1[0], i0[1]:i1[1], i0[2]:i1[2]] += np.exp(-2.0 * (d2 / (r * r) - 1.0))
+    return lo, spacing, rho
+
+
+def _outermost_crossing(dirs, lo, spacing, rho, level=1.0, step=0.2, iters=40):
+    """Largest t with rho(t d) = level along each unit direction d (trilinear rho)."""
+    from scipy.ndimage import map_coordinates
+    shape = np.array(rho.shape)
+    hi = lo + spacing * (shape - 1)
+    t_max = float(np.linalg.norm(np.maximum(np.abs(lo), np.abs(hi)))) + step
+
+    def f(t):
+        p = (t[:, None] * dirs - lo) / spacing
+        return map_coordinates(rho, p.T, order=1, mode='constant', cval=0.0) - level
+
+    n = dirs.shape[0]
+    t_in = np.full(n, np.nan)
+    t = t_max
+    while t > 0 and np.isnan(t_in).any():
+        todo = np.isnan(t_in)
+        hit = f(np.full(n, t))[todo] >= 0
+        idx = np.nonzero(todo)[0][hit]
+        t_in[idx] = t
+        t -= step
+    if np.isnan(t_in).any():
+        raise ValueError("a ray from the centre does not meet the density level set")
+    a, b = t_in.copy(), t_in + step          # f(a) >= 0 > f(b)
+    for _ in range(iters):
+        m = 0.5 * (a + b)
+        inside = f(m) >= 0
+        a = np.where(inside, m, a)
+        b = np.where(inside, b, m)
+    return 0.5 * (a + b)
+
+
+def _close_crevices(r, tri, k_close=40, k_soft=3):
+    """Fill narrow crevices of a radial surface, as a probe sphere rolling over the atoms would:
+    r <- max(r, r smoothed by k_close Laplacian passes), then k_soft light passes.  Raising r only
+    enlarges the enclosed region; the light passes move peaks by a fraction of an Angstrom."""
+    import scipy.sparse as sp
+    n = r.shape[0]
+    e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]])
+    A = sp.csr_matrix((np.ones(2 * len(e)), (np.r_[e[:, 0], e[:, 1]], np.r_[e[:, 1], e[:, 0]])), shape=(n, n))
+    A.data[:] = 1.0
+    deg = np.asarray(A.sum(axis=1)).ravel()
+
+    def smooth(x, k, w):
+        for _ in range(k):
+            x = (1.0 - w) * x + w * (A @ x) / deg
+        return x
+
+    return smooth(np.maximum(r, smooth(r, k_close, 0.5)), k_soft, 0.3)
+
+
+def _radial_shell(dirs, tri, r_in, r_out, layers):
+    """Shell between the star-shaped surfaces r_in(d) and r_out(d) over the ray triangulation
+    (dirs, tri): layer radii r_in (r_out / r_in)^(l / layers), prisms cut as in spherical_shell."""
+    ns = dirs.shape[0]
+    big = 4 * ns
+    pattern = []                              # per triangle: 3 tets of (local id + big * top)
+    for f in tri:
+        pattern.append(_prism_tets([f[0], f[1], f[2], f[0] + big, f[1] + big, f[2] + big]))
+    pattern = np.array(pattern, dtype=np.int64)             # (m, 3, 4)
+    top = pattern >= big
+    local = np.where(top, pattern - big, pattern)
+    frac = np.arange(layers + 1) / layers
+    radii = r_in[None, :] * (r_out / r_in)[None, :] ** frac[:, None]        # (layers+1, ns)
+    xyz = (radii[:, :, None] * dirs[None, :, :]).reshape(-1, 3)
+    tets = np.concatenate([local + ns * (lay + top) for lay in range(layers)], axis=0).reshape(-1, 4)
+    gm = tri.astype(np.int32)
+    gs = (tri + layers * ns).astype(np.int32)
+    return xyz, tets.astype(np.int32), gm, gs
+
+
+def double_helix(n_bp=24, nu=45, layers=16, seed=3000, n_interior=1500, ionic=0.15, eps_in=2.0,
+                 eps_out=80.0, T=300.0, grid=0.35):
+    """Synthetic double helix (see above): 24 base pairs, nu = 45 (40,500 triangles per surface,
+    20,252 rays), 16 shell layers (1.94M tets, 344,284 vertices), 0.15 M, outer sphere at the
+    largest surface radius + 3 Debye lengths."""
+    cen, rad, q = helix_atoms(n_bp, seed, n_interior)
+    u, tri = icosphere(nu)
+    half = 0.5 * n_bp * 2.8
+    stretch = np.array([11.0, 11.0, half + 3.0])
+    dirs = u * stretch
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    lo, h, rho = _gaussian_density_grid(cen, rad, grid, 6.0)
+    r_in = _close_crevices(_outermost_crossing(dirs, lo, h, rho), tri)
+    kappa = kappa_from_ionic_strength(ionic, eps_out, T)
+    R_out = float(r_in.max()) + 3.0 / kappa
+    xyz, tets, gm, gs = _radial_shell(dirs, tri, r_in, np.full_like(r_in, R_out), layers)
+    _check_charges_inside(cen, xyz, gm, dirs, tri, r_in, margin=0.3)
+    return Case(f"double_helix_{n_bp}bp_nu{nu}_L{layers}", xyz, tets, gm, gs, cen, q,
+                eps_in, eps_out, kappa, T)
+
+
+def _check_charges_inside(pts, xyz, gm, dirs, tri, r_in, margin):
+    """Every charge lies inside Gamma_m, at least ``margin`` below it along its own ray."""
+    d = pts / np.linalg.norm(pts, axis=1)[:, None]
+    A, B, C = dirs[tri[:, 0]], dirs[tri[:, 1]], dirs[tri[:, 2]]
+    nAB, nBC, nCA = np.cross(A, B), np.cross(B, C), np.cross(C, A)
+    for k in range(0, d.shape[0], 64):
+        dk = d[k:k + 64]
+        inside = (dk @ nAB.T >= -1e-12) & (dk @ nBC.T >= -1e-12) & (dk @ nCA.T >= -1e-12)
+        for j in range(dk.shape[0]):
+            t = np.nonzero(inside[j])[0]
+            if t.size == 0:
+                raise ValueError("a charge direction is in no ray triangle")
+            f = tri[t[0]]
+            P = xyz[gm[t[0]]]
+            n = np.cross(P[1] - P[0], P[2] - P[0])
+            t_surf = (n @ P[0]) / (n @ dk[j])
+            if not np.linalg.norm(pts[k + j]) < t_surf - margin:
+                raise ValueError(f"charge {k + j} is not inside the molecular surface by {margin} A")

@@ -109,3 +109,21 @@ def test_layer_potential_inside_reproduces_harmonic_field(sphere_ops):
     lam = xyz[:, 0] / r
     got = bem.layer_potentials_at(s, pts, lam, phi)
     assert np.abs(got - (1.0 + pts[:, 0])).max() < 2e-2
+
+
+def test_classification_restricted_to_test_triangles():
+    """The classification of a subset of test triangles lists exactly the pairs of the full
+    classification whose test triangle is in the subset (used for sampled rows of large
+    surfaces)."""
+    from paper_2511_21713_gb300 import inputs
+    c = inputs.double_helix(n_bp=6, nu=10, layers=3, n_interior=375)
+    s = bem.Surface(c.xyz, c.gm_tris)
+    full = bem.classify_pairs(s)
+    tt = np.sort(np.random.default_rng(4).choice(s.nt, 40, replace=False))
+    part = bem.classify_pairs(s, test_tris=tt)
+    keep = np.isin(np.arange(s.nt), tt)
+    assert np.array_equal(part['identical'], tt)
+    for k in ('edge', 'vertex', 'near'):
+        ref = full[k][keep[full[k][:, 0]]]
+        assert np.array_equal(part[k], ref), k
+    assert len(full['near']) > 0 and len(part['near']) > 0
