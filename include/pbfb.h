@@ -297,6 +297,40 @@ int pbfb_energy(pbfb_mesh* mesh, const double* xL_dev, const double* xNL_dev, do
 int pbfb_set_tuning(pbfb_mesh* mesh, int nbody_targets_per_thread, int nbody_blocks_per_sm,
                     int nbody_packed);
 
+/* Launch shapes of the far-field and SpMV kernels.  Zero in a field means the
+ * built-in choice.  Shapes change the order of floating-point sums only
+ * (results agree to rounding), never the discrete operator. */
+typedef struct pbfb_tuning {
+  int32_t nbody_targets_per_thread;  /* float32 far field: 1, 2, 4 or 8 */
+  int32_t nbody_blocks_per_sm;       /* float32 far field source splits: 1..64 */
+  int32_t nbody_packed;              /* 1: f32x2 kernel (needs 2+ targets per thread) */
+  int32_t ff_blocks_per_sm;          /* float-float far field source splits: 1..64 */
+  int32_t ff_one_target;             /* 1: one-target float-float kernel */
+  int32_t spmv_lanes;                /* lanes per row of the operator's SpMV: 4, 8, 16 */
+  int32_t spmv_block;                /* threads per block of that SpMV: 128, 256, 512 */
+} pbfb_tuning;
+
+/* Current launch shapes of a mesh (zeros where the built-in choice applies). */
+int pbfb_get_tuning(const pbfb_mesh* mesh, pbfb_tuning* out);
+
+/* Sets all launch shapes at once (e.g. a cached autotuner result); INVALID if
+ * a field is outside the ranges above. */
+int pbfb_apply_tuning(pbfb_mesh* mesh, const pbfb_tuning* t);
+
+/* Autotuner (the paper has no counterpart: launch shapes are a property of
+ * this implementation).  Times, with CUDA events on the mesh's stream, every
+ * candidate shape of the float32 far field (targets per thread 1/2/4, packed
+ * or not, 8/16/32 blocks per SM of source splits) and of the float-float far
+ * field (4/8/16 blocks per SM, one or two targets per thread) on both
+ * surfaces of this mesh at the current parameters, and of the operator's
+ * SpMV (4/8/16 lanes per row x 128/256/512 threads), each over reps
+ * repetitions after one untimed run, and applies the fastest.  best (host,
+ * may be NULL) receives the chosen shapes; ms (host, 3 doubles, may be NULL)
+ * the best time per repetition of the three kernels.  Needs pbfb_set_params
+ * (STATE otherwise); reps in 1..20.  Allocates two work vectors of n
+ * doubles for the duration of the call. */
+int pbfb_autotune(pbfb_mesh* mesh, int reps, pbfb_tuning* best, double* ms);
+
 /* Per-kernel-class timing (CUDA events around each launch of the class) and
  * launch counters.  enable != 0 turns event timing on (it adds a little host
  * overhead per launch).  stats (host, 16 doubles):

@@ -1330,7 +1330,7 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
   const int ntb = blocks_for(nq, pk ? 2 * NT : NT);
   // source splits from the packed grid in both variants, so that they sum in the same order
   const int ntb2 = blocks_for(nq, 2 * NT);
-  const int bps = m->tune_bps > 0 ? m->tune_bps : 8;  // GB300 sweep: 8 blocks per SM of source splits
+  const int bps = m->tune_ff_bps > 0 ? m->tune_ff_bps : 8;  // GB300 sweep: 8 blocks per SM of source splits
   int nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb2), blocks_for(nq, 4 * NT)));
   const int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
   nsplit = blocks_for(nq, per);

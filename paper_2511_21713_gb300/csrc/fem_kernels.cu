@@ -137,18 +137,18 @@ __global__ void k_element_nl(int scheme, const double* __restrict__ u, const int
   for (int a = 0; a < 4; ++a) loc[(10 + a) * nt + t] = s * N[a];
 }
 
-// Sparse part of the coupled operator: y = S x, 8 lanes per row.
+// Sparse part of the coupled operator: y = S x, L lanes per row (L = 4, 8 or 16).
+template <int L>
 __global__ void k_spmv(int nrows, const int* __restrict__ ptr, const int* __restrict__ col,
                        const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
-  int lane = threadIdx.x & 7;
-  int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int lane = threadIdx.x & (L - 1);
+  int row = (blockIdx.x * blockDim.x + threadIdx.x) / L;
   const bool valid = row < nrows;  // all lanes reach the shuffles
   double acc = 0.0;
   if (valid)
-    for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) acc += val[k] * __ldg(&x[col[k]]);
-  acc += __shfl_down_sync(0xffffffffu, acc, 4, 8);
-  acc += __shfl_down_sync(0xffffffffu, acc, 2, 8);
-  acc += __shfl_down_sync(0xffffffffu, acc, 1, 8);
+    for (int k = ptr[row] + lane; k < ptr[row + 1]; k += L) acc += val[k] * __ldg(&x[col[k]]);
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, L);
   if (lane == 0 && valid) y[row] = acc;
 }
 
@@ -348,7 +348,15 @@ int launch_spmv(Mesh* m, const double* x, double* y) {
   cudaEvent_t ev;
   timer_begin(m, m->t_spmv, &ev);
   int n = m->n;
-  k_spmv<<<blocks_for((int64_t)n * 8, 256), 256, 0, m->stream>>>(n, m->s_ptr.p, m->s_col.p, m->s_val.p, x, y);
+  const int L = m->spmv_lanes > 0 ? m->spmv_lanes : 8;
+  const int B = m->spmv_block > 0 ? m->spmv_block : 256;
+  const int g = blocks_for((int64_t)n * L, B);
+  if (L == 4)
+    k_spmv<4><<<g, B, 0, m->stream>>>(n, m->s_ptr.p, m->s_col.p, m->s_val.p, x, y);
+  else if (L == 16)
+    k_spmv<16><<<g, B, 0, m->stream>>>(n, m->s_ptr.p, m->s_col.p, m->s_val.p, x, y);
+  else
+    k_spmv<8><<<g, B, 0, m->stream>>>(n, m->s_ptr.p, m->s_col.p, m->s_val.p, x, y);
   PB_LAUNCHED(m);
   timer_end(m, m->t_spmv, ev, (double)m->snnz);
   return PBFB_OK;

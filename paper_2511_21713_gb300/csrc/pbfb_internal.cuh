@@ -183,6 +183,9 @@ struct Mesh {
   int tune_bps = 0;                 // float32 far field: target blocks per SM for the source split
   int tune_packed = 0;              // float32 far field: 1 = packed f32x2 kernel
   int tune_ff_scalar = 0;           // float-float far field: 1 = one target per thread (k_nbody_ff)
+  int tune_ff_bps = 0;              // float-float far field: target blocks per SM (0 = 8)
+  int spmv_lanes = 0;               // lanes per row of the operator's sparse part (0 = 8; 4, 8, 16)
+  int spmv_block = 0;               // threads per block of that SpMV (0 = 256; 128, 256, 512)
   bool dense_m = false, dense_s = false;  // surface rows of the block preconditioner use V^-1
   DBuf<float> dwork;                // dense single-layer build: W chunk, sweep panels
   DBuf<int> dflag;                  // sweep pivot status

@@ -34,6 +34,7 @@ EXPORTS = [
     "pbfb_energy", "pbfb_profile", "pbfb_bem_apply_noalloc", "pbfb_set_tuning",
     "pbfb_server_create", "pbfb_server_submit", "pbfb_server_poll", "pbfb_server_stats",
     "pbfb_server_destroy", "pbfb_solve_batch", "pbfb_single_layer_dense",
+    "pbfb_get_tuning", "pbfb_apply_tuning", "pbfb_autotune",
 ]
 
 
@@ -97,6 +98,16 @@ class Response(ctypes.Structure):
         return d
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("nbody_targets_per_thread", ctypes.c_int32), ("nbody_blocks_per_sm", ctypes.c_int32),
+                ("nbody_packed", ctypes.c_int32), ("ff_blocks_per_sm", ctypes.c_int32),
+                ("ff_one_target", ctypes.c_int32), ("spmv_lanes", ctypes.c_int32),
+                ("spmv_block", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 class BatchParams(ctypes.Structure):
     _fields_ = [("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("T", ctypes.c_double), ("opts", ctypes.POINTER(NewtonOpts))]
@@ -143,6 +154,9 @@ def load():
         "pbfb_server_destroy": (I, [P]),
         "pbfb_solve_batch": (I, [P, P, I, I, P]),
         "pbfb_single_layer_dense": (I, [P, I, I, P, ctypes.c_int32]),
+        "pbfb_get_tuning": (I, [P, ctypes.POINTER(Tuning)]),
+        "pbfb_apply_tuning": (I, [P, ctypes.POINTER(Tuning)]),
+        "pbfb_autotune": (I, [P, I, ctypes.POINTER(Tuning), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -292,6 +306,40 @@ class Mesh:
 
     def set_tuning(self, targets_per_thread=0, blocks_per_sm=0, packed=0):
         _check(load().pbfb_set_tuning(self.h, targets_per_thread, blocks_per_sm, packed))
+
+    def get_tuning(self):
+        t = Tuning()
+        _check(load().pbfb_get_tuning(self.h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def apply_tuning(self, d):
+        t = Tuning(**{k: int(v) for k, v in d.items()})
+        _check(load().pbfb_apply_tuning(self.h, ctypes.byref(t)))
+
+    def autotune(self, reps=3, cache_file=None):
+        """Time the candidate launch shapes on this mesh (pbfb_autotune) and apply the fastest.
+        With cache_file (JSON), a result stored for the same GPU and size bucket is applied
+        instead of timing, and new results are added to the file.  Returns (shapes, ms)."""
+        import json
+        key = None
+        if cache_file is not None:
+            import torch
+            b = lambda v: int(round(np.log2(max(int(v), 1))))
+            key = f"{torch.cuda.get_device_name()}|nm{b(self.n_m)}|ns{b(self.n_s)}|nv{b(self.n_v)}"
+            cache = json.load(open(cache_file)) if os.path.exists(cache_file) else {}
+            if key in cache:
+                self.apply_tuning(cache[key]["shapes"])
+                return cache[key]["shapes"], cache[key]["ms"]
+        t = Tuning()
+        ms = np.zeros(3)
+        _check(load().pbfb_autotune(self.h, int(reps), ctypes.byref(t), _ptr(ms)))
+        shapes, times = t.as_dict(), dict(nbody_f32=ms[0], nbody_ff=ms[1], spmv=ms[2])
+        if key is not None:
+            cache = json.load(open(cache_file)) if os.path.exists(cache_file) else {}
+            cache[key] = {"shapes": shapes, "ms": times}
+            with open(cache_file, "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+        return shapes, times
 
     def profile(self, enable=True, reset=False):
         st = np.zeros(16)

@@ -124,5 +124,5 @@ def test_helix_mixed_solve_residual(helix, sampled_rows):
     print("helix residual / max|b|: FEM rows %.3e, Gamma_m rows %.3e, Gamma_s rows %.3e; Newton %d, GMRES %s"
           % (np.abs(yu).max() / scale, np.abs(dm).max() / scale, np.abs(ds).max() / scale,
              res["newton_iters"], res["gmres"]))
-    assert np.abs(yu).max() < 1e-7 * scale
-    assert np.abs(dm).max() < 1e-7 * scale and np.abs(ds).max() < 1e-7 * scale
+    assert np.abs(yu).max() < 1e-10 * scale
+    assert np.abs(dm).max() < 1e-10 * scale and np.abs(ds).max() < 1e-10 * scale
