@@ -292,8 +292,8 @@ int pbfb_energy(pbfb_mesh* mesh, const double* xL_dev, const double* xNL_dev, do
  * results only in float64 rounding; the packed variant rounds the same float32
  * operations (no fused reassociation differences beyond FMA contraction).
  * Bit 1 of packed (packed = 2 or 3) selects the one-target-per-thread
- * float-float far field instead of the default two-target packed one (they
- * agree to float-float rounding). */
+ * float-float far field instead of the built-in choice (they agree to
+ * float-float rounding). */
 int pbfb_set_tuning(pbfb_mesh* mesh, int nbody_targets_per_thread, int nbody_blocks_per_sm,
                     int nbody_packed);
 
@@ -305,9 +305,12 @@ typedef struct pbfb_tuning {
   int32_t nbody_blocks_per_sm;       /* float32 far field source splits: 1..64 */
   int32_t nbody_packed;              /* 1: f32x2 kernel (needs 2+ targets per thread) */
   int32_t ff_blocks_per_sm;          /* float-float far field source splits: 1..64 */
-  int32_t ff_one_target;             /* 1: one-target float-float kernel */
+  int32_t ff_kernel;                 /* float-float far field: 1 one target per thread,
+                                        2 two per thread (float2), 3 mutual pairs */
   int32_t spmv_lanes;                /* lanes per row of the operator's SpMV: 4, 8, 16 */
   int32_t spmv_block;                /* threads per block of that SpMV: 128, 256, 512 */
+  int32_t pcg_blocks_per_sm;         /* blocks per SM of the cooperative inner PCG: 1..32
+                                        (0: as many as fit) */
 } pbfb_tuning;
 
 /* Current launch shapes of a mesh (zeros where the built-in choice applies). */
@@ -321,14 +324,19 @@ int pbfb_apply_tuning(pbfb_mesh* mesh, const pbfb_tuning* t);
  * this implementation).  Times, with CUDA events on the mesh's stream, every
  * candidate shape of the float32 far field (targets per thread 1/2/4, packed
  * or not, 8/16/32 blocks per SM of source splits) and of the float-float far
- * field (4/8/16 blocks per SM, one or two targets per thread) on both
+ * field (4/8/16 blocks per SM; one or two targets per thread, or mutual
+ * pairs evaluated once for both directions) on both
  * surfaces of this mesh at the current parameters, and of the operator's
- * SpMV (4/8/16 lanes per row x 128/256/512 threads), each over reps
+ * SpMV (4/8/16 lanes per row x 128/256/512 threads) and of the cooperative
+ * inner PCG of the block preconditioner (1/2/4/8 blocks per SM or all that
+ * fit; 20 iterations at the current Jacobian), each over reps
  * repetitions after one untimed run, and applies the fastest.  best (host,
  * may be NULL) receives the chosen shapes; ms (host, 3 doubles, may be NULL)
  * the best time per repetition of the three kernels.  Needs pbfb_set_params
  * (STATE otherwise); reps in 1..20.  Allocates two work vectors of n
- * doubles for the duration of the call. */
+ * doubles for the duration of the call (and the block preconditioner's
+ * workspace, kept for later solves).  ms: 4 doubles (float32 far field,
+ * float-float far field, SpMV, inner PCG). */
 int pbfb_autotune(pbfb_mesh* mesh, int reps, pbfb_tuning* best, double* ms);
 
 /* Per-kernel-class timing (CUDA events around each launch of the class) and

@@ -16,9 +16,10 @@ void read_tuning(const Mesh* m, pbfb_tuning* t) {
   t->nbody_blocks_per_sm = m->tune_bps;
   t->nbody_packed = m->tune_packed;
   t->ff_blocks_per_sm = m->tune_ff_bps;
-  t->ff_one_target = m->tune_ff_scalar;
+  t->ff_kernel = m->tune_ff_kernel;
   t->spmv_lanes = m->spmv_lanes;
   t->spmv_block = m->spmv_block;
+  t->pcg_blocks_per_sm = m->tune_pcg_bps;
 }
 
 bool valid_tuning(const pbfb_tuning* t) {
@@ -26,11 +27,12 @@ bool valid_tuning(const pbfb_tuning* t) {
   const int tp = t->nbody_targets_per_thread;
   if (!(tp == 0 || tp == 1 || tp == 2 || tp == 4 || tp == 8)) return false;
   if (!in(t->nbody_blocks_per_sm, 1, 64) || !in(t->ff_blocks_per_sm, 1, 64)) return false;
-  if (t->nbody_packed < 0 || t->nbody_packed > 1 || t->ff_one_target < 0 || t->ff_one_target > 1) return false;
+  if (t->nbody_packed < 0 || t->nbody_packed > 1 || t->ff_kernel < 0 || t->ff_kernel > 3) return false;
   if (t->nbody_packed && tp != 0 && tp < 2) return false;
   const int L = t->spmv_lanes, B = t->spmv_block;
   if (!(L == 0 || L == 4 || L == 8 || L == 16)) return false;
   if (!(B == 0 || B == 128 || B == 256 || B == 512)) return false;
+  if (!in(t->pcg_blocks_per_sm, 1, 32)) return false;
   return true;
 }
 
@@ -39,9 +41,11 @@ void write_tuning(Mesh* m, const pbfb_tuning* t) {
   m->tune_bps = t->nbody_blocks_per_sm;
   m->tune_packed = t->nbody_packed;
   m->tune_ff_bps = t->ff_blocks_per_sm;
-  m->tune_ff_scalar = t->ff_one_target;
+  m->tune_ff_kernel = t->ff_kernel;
   m->spmv_lanes = t->spmv_lanes;
   m->spmv_block = t->spmv_block;
+  if (m->tune_pcg_bps != t->pcg_blocks_per_sm) m->coop_blocks = 0;  // re-derive the grid
+  m->tune_pcg_bps = t->pcg_blocks_per_sm;
 }
 
 // milliseconds per repetition of fn (one untimed run first)
@@ -113,10 +117,10 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
       }
     }
   // float-float far field
-  for (int one : {0, 1})
+  for (int kind : {1, 2, 3})
     for (int bps : {4, 8, 16}) {
       pbfb_tuning t = best;
-      t.ff_one_target = one;
+      t.ff_kernel = kind;
       t.ff_blocks_per_sm = bps;
       write_tuning(m, &t);
       double ms;
@@ -127,7 +131,7 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
       }
       if (ms < t_best[1]) {
         t_best[1] = ms;
-        best.ff_one_target = one;
+        best.ff_kernel = kind;
         best.ff_blocks_per_sm = bps;
       }
     }
@@ -153,12 +157,34 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
         best.spmv_block = B;
       }
     }
+  // cooperative inner PCG of the block preconditioner (20 iterations); skipped on meshes solved
+  // without the grid-barrier kernel
+  double t_pcg = 0.0;
+  if (!m->no_coop) {
+    t_pcg = 1e300;
+    for (int bps : {1, 2, 4, 8, 0}) {
+      pbfb_tuning t = best;
+      t.pcg_blocks_per_sm = bps;
+      write_tuning(m, &t);
+      double ms;
+      int st = time_ms(m, reps, [&]() -> int { return block_precond_apply(m, x.p, y.p, 20, true); }, &ms);
+      if (st) {
+        write_tuning(m, &cur);
+        return st;
+      }
+      if (ms < t_pcg) {
+        t_pcg = ms;
+        best.pcg_blocks_per_sm = bps;
+      }
+    }
+  }
   write_tuning(m, &best);
   if (best_out) *best_out = best;
   if (ms_out) {
     ms_out[0] = t_best[0];
     ms_out[1] = t_best[1];
     ms_out[2] = t_best[2] / 10.0;
+    ms_out[3] = t_pcg;
   }
   return PBFB_OK;
 }

@@ -1021,6 +1021,142 @@ __global__ void __launch_bounds__(NT) k_nbody_ff2(int nq, const float4* __restri
   if (i1 < nq) out[(int64_t)blockIdx.y * nq + i1] = acc1;
 }
 
+// Mutual float-float N-body: every unordered pair of points is evaluated once for both
+// directions.  The pair (i, j) shares d = x_i - y_j, 1/r and, for the Yukawa kernel, exp(-kappa r);
+// with f = (1 + kappa r) / r^2 and g = exp(-kappa r) / r it contributes
+//   (s_j + (m_j . d) f) g  to target i   and   (s_i - (m_i . d) f) g  to target j,
+// saving the shared part of the float-float work (about 30% of the operations).
+//
+// Points are cut into tiles of MT = 128 and the tiles into G groups; block (rg, cg), rg <= cg, takes
+// every tile pair (I in rg, J in cg, I < J) and the diagonal tiles I = J (one direction, coincident
+// point skipped).  Target-side sums stay in registers and go to PI[cg][i]; source-side sums are
+// accumulated in shared memory per tile pair and added to PJ[rg][j], which only this block touches.
+// Within a tile pair, step s of the 128 takes source 32 ((w + s / 32) mod 4) + (lane + s) mod 32 in
+// warp w: the warps work on disjoint quarters of the source tile between barriers and the lanes of
+// a warp on distinct sources, so the shared-memory sums have no races and a fixed order.  The
+// final value of a point is the fixed-order sum of its 2 G partials (k_mutual_sum).
+constexpr int MT = 128;
+
+template <bool YUK>
+__device__ __forceinline__ void ff_mutual(const float4& ah, const float4& al, const float4& amh, const float4& aml,
+                                          const float4& bh, const float4& bl, const float4& bmh, const float4& bml,
+                                          ff kap, const float2* __restrict__ tab, ff& to_a, ff& to_b) {
+  // a = target (x, s, m), b = source (y, s, m); float4 (x, y, z, s) hi / lo, (mx, my, mz, -) hi / lo
+  ff d0 = ff_diff(ah.x, al.x, bh.x, bl.x);
+  ff d1 = ff_diff(ah.y, al.y, bh.y, bl.y);
+  ff d2 = ff_diff(ah.z, al.z, bh.z, bl.z);
+  ff r2 = ff_dot3(d0, d1, d2, d0, d1, d2);
+  ff ri = ff_rsqrt(r2);
+  ff ri2 = ff_sq(ri);
+  ff f, g;
+  if (YUK) {
+    ff r = ff_mul(r2, ri);
+    ff x = ff_mul(kap, r);
+    ff e = ff_expm(x, tab);
+    ff one_x = two_sum(1.0f, x.h);
+    one_x = fast_two_sum(one_x.h, __fadd_rn(one_x.l, x.l));
+    f = ff_mul(one_x, ri2);
+    g = ff_mul(e, ri);
+  } else {
+    f = ri2;
+    g = ri;
+  }
+  ff ndb = ff_dot3(ff{bmh.x, bml.x}, ff{bmh.y, bml.y}, ff{bmh.z, bml.z}, d0, d1, d2);
+  ff nda = ff_dot3(ff{amh.x, aml.x}, ff{amh.y, aml.y}, ff{amh.z, aml.z}, d0, d1, d2);
+  ff fb = ff_mul(ndb, f), fa = ff_mul(nda, f);
+  to_a = ff_mul(ff_add(ff{bh.w, bl.w}, fb), g);
+  to_b = ff_mul(ff_add(ff{ah.w, al.w}, ff{-fa.h, -fa.l}), g);
+}
+
+template <bool YUK>
+__global__ void __launch_bounds__(MT) k_nbody_ffm(int nq, int G, const float4* __restrict__ src, float kh, float kl,
+                                                  const float2* __restrict__ tab_hi, double* __restrict__ PI,
+                                                  double* __restrict__ PJ) {
+  __shared__ float4 sb[4][MT];              // source tile: (y, s) hi, (y, s) lo, m hi, m lo
+  __shared__ float2 acc_j[MT];              // source-side float-float sums of the current tile pair
+  __shared__ float2 tab[YUK ? FF_TABLE_HI : 1];
+  if (YUK)
+    for (int k = threadIdx.x; k < FF_TABLE_HI; k += MT) tab[k] = tab_hi[k];
+  // block -> (rg, cg), rg <= cg
+  int t = blockIdx.x, rg = 0;
+  while (t >= G - rg) {
+    t -= G - rg;
+    ++rg;
+  }
+  const int cg = rg + t;
+  const int nT = (nq + MT - 1) / MT;
+  const int tpg = (nT + G - 1) / G;
+  const int i0g = rg * tpg, i1g = min(nT, (rg + 1) * tpg);
+  const int j0g = cg * tpg, j1g = min(nT, (cg + 1) * tpg);
+  const ff kap{kh, kl};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int I = i0g; I < i1g; ++I) {
+    const int i = I * MT + threadIdx.x;
+    const bool iv = i < nq;
+    // invalid targets sit far away with zero strength
+    float4 ah = iv ? src[4 * i] : make_float4(2e15f, 0.f, 0.f, 0.f);
+    float4 al = iv ? src[4 * i + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 amh = iv ? src[4 * i + 2] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 aml = iv ? src[4 * i + 3] : make_float4(0.f, 0.f, 0.f, 0.f);
+    double acc64 = 0.0;
+    for (int J = max(I, j0g); J < j1g; ++J) {
+      const int jl = J * MT + threadIdx.x;
+      __syncthreads();  // the previous tile's readers are done
+      if (jl < nq) {
+        for (int c = 0; c < 4; ++c) sb[c][threadIdx.x] = src[4 * jl + c];
+      } else {
+        sb[0][threadIdx.x] = make_float4(1e15f, 0.f, 0.f, 0.f);
+        sb[1][threadIdx.x] = sb[2][threadIdx.x] = sb[3][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      acc_j[threadIdx.x] = make_float2(0.f, 0.f);
+      __syncthreads();
+      const int cnt = min(MT, nq - J * MT);
+      ff acc{0.f, 0.f};
+      if (J == I) {
+        // diagonal tile: target side only, coincident point skipped
+        const float th[3] = {ah.x, ah.y, ah.z}, tl[3] = {al.x, al.y, al.z};
+        for (int jj = 0; jj < cnt; ++jj) {
+          if (jj == (int)threadIdx.x) continue;
+          acc = ff_add(acc, ff_pair<YUK>(sb[0][jj], sb[1][jj], sb[2][jj], sb[3][jj], th, tl, kap, tab));
+        }
+      } else {
+        for (int ph = 0; ph < 4; ++ph) {
+          const int base = 32 * ((warp + ph) & 3);
+          for (int k = 0; k < 32; ++k) {
+            const int jj = base + ((lane + k) & 31);
+            ff ta, tb;
+            ff_mutual<YUK>(ah, al, amh, aml, sb[0][jj], sb[1][jj], sb[2][jj], sb[3][jj], kap, tab, ta, tb);
+            acc = ff_add(acc, ta);
+            const float2 o = acc_j[jj];
+            const ff nb = ff_add(ff{o.x, o.y}, tb);
+            acc_j[jj] = make_float2(nb.h, nb.l);
+            __syncwarp();
+          }
+          __syncthreads();
+        }
+        // source-side sums of this tile pair into PJ[rg][j]
+        if (jl < nq) {
+          const float2 o = acc_j[threadIdx.x];
+          PJ[(int64_t)rg * nq + jl] += (double)o.x + (double)o.y;
+        }
+      }
+      acc64 += (double)acc.h + (double)acc.l;
+    }
+    if (iv) PI[(int64_t)cg * nq + i] = acc64;
+  }
+}
+
+// out[i] = sum over c of PI[c][i] + sum over r of PJ[r][i] (fixed order)
+__global__ void k_mutual_sum(int nq, int G, const double* __restrict__ PI, const double* __restrict__ PJ,
+                             double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  double v = 0.0;
+  for (int c = 0; c < G; ++c) v += PI[(int64_t)c * nq + i];
+  for (int r = 0; r < G; ++r) v += PJ[(int64_t)r * nq + i];
+  out[i] = v;
+}
+
 // val[0][j] = sum over the source splits of val[split][j] (fixed order)
 __global__ void k_split_sum(int nq, int nsplit, double* __restrict__ val) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1326,11 +1462,39 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
   cudaEvent_t ev;
   timer_begin(m, m->t_nbodyff, &ev);
   constexpr int NT = 128;
-  const bool pk = !m->tune_ff_scalar;   // two targets per thread (k_nbody_ff2) unless tuned off
+  // kernel: 1 one target per thread, 2 two targets per thread (float2), 3 mutual pairs;
+  // built-in choice: mutual for large surfaces, two targets per thread otherwise
+  const int kind = m->tune_ff_kernel > 0 ? m->tune_ff_kernel : (nq >= 16384 ? 3 : 2);
+  const int bps = m->tune_ff_bps > 0 ? m->tune_ff_bps : 8;  // GB300 sweep: 8 blocks per SM of source splits
+  const float kh = (float)kappa, kl = (float)(kappa - (double)kh);
+  if (kind == 3) {
+    // tile groups: G (G + 1) / 2 blocks, about bps per SM; 2 G + 1 partial rows of val
+    const int nT = blocks_for(nq, MT);
+    int G = (int)std::sqrt(2.0 * bps * 152.0);
+    G = std::max(1, std::min({G, nT, (int)((s->val.n / (size_t)nq - 1) / 2)}));
+    if ((size_t)(2 * G + 1) * nq > s->val.n) {
+      set_error("far-field split buffer too small");
+      return PBFB_ERR_STATE;
+    }
+    double* PI = s->val.p;
+    double* PJ = s->val.p + (size_t)G * nq;
+    double* out = s->val.p + (size_t)2 * G * nq;
+    PB_CUDA(cudaMemsetAsync(s->val.p, 0, (size_t)2 * G * nq * sizeof(double), m->stream));
+    const int nblk = G * (G + 1) / 2;
+    if (yuk)
+      k_nbody_ffm<true><<<nblk, MT, 0, m->stream>>>(nq, G, s->ffsrc.p, kh, kl, m->ff_tab.p, PI, PJ);
+    else
+      k_nbody_ffm<false><<<nblk, MT, 0, m->stream>>>(nq, G, s->ffsrc.p, kh, kl, m->ff_tab.p, PI, PJ);
+    PB_LAUNCHED(m);
+    k_mutual_sum<<<blocks_for(nq, 256), 256, 0, m->stream>>>(nq, G, PI, PJ, out);
+    PB_LAUNCHED(m);
+    timer_end(m, m->t_nbodyff, ev, (double)nq * (double)nq);
+    return test_reduce(m, s, out, 1, y, accumulate);
+  }
+  const bool pk = kind == 2;
   const int ntb = blocks_for(nq, pk ? 2 * NT : NT);
   // source splits from the packed grid in both variants, so that they sum in the same order
   const int ntb2 = blocks_for(nq, 2 * NT);
-  const int bps = m->tune_ff_bps > 0 ? m->tune_ff_bps : 8;  // GB300 sweep: 8 blocks per SM of source splits
   int nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb2), blocks_for(nq, 4 * NT)));
   const int per = blocks_for(blocks_for(nq, nsplit), NT) * NT;
   nsplit = blocks_for(nq, per);
@@ -1338,7 +1502,6 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
     set_error("far-field split buffer too small");
     return PBFB_ERR_STATE;
   }
-  const float kh = (float)kappa, kl = (float)(kappa - (double)kh);
   dim3 grid(ntb, nsplit);
   if (pk && yuk)
     k_nbody_ff2<NT, true><<<grid, NT, 0, m->stream>>>(nq, s->fftgt.p, s->ffsrc.p, kh, kl, m->ff_tab.p, per, s->val.p);

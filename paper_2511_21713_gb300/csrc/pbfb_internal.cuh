@@ -182,10 +182,12 @@ struct Mesh {
   int tune_tpt = 0;                 // float32 far field: targets per thread (0 = heuristic)
   int tune_bps = 0;                 // float32 far field: target blocks per SM for the source split
   int tune_packed = 0;              // float32 far field: 1 = packed f32x2 kernel
-  int tune_ff_scalar = 0;           // float-float far field: 1 = one target per thread (k_nbody_ff)
+  int tune_ff_kernel = 0;           // float-float far field: 1 one target per thread, 2 two (float2),
+                                    // 3 mutual pairs (0 = mutual for large surfaces, else 2)
   int tune_ff_bps = 0;              // float-float far field: target blocks per SM (0 = 8)
   int spmv_lanes = 0;               // lanes per row of the operator's sparse part (0 = 8; 4, 8, 16)
   int spmv_block = 0;               // threads per block of that SpMV (0 = 256; 128, 256, 512)
+  int tune_pcg_bps = 0;             // blocks per SM of the cooperative inner PCG (0 = all that fit)
   bool dense_m = false, dense_s = false;  // surface rows of the block preconditioner use V^-1
   DBuf<float> dwork;                // dense single-layer build: W chunk, sweep panels
   DBuf<int> dflag;                  // sweep pivot status
@@ -254,6 +256,10 @@ int build_dense_single_layer(Mesh* m, Surface* s, double kappa, bool invert);
 // z = scale * (stored matrix) v over the surface's vertices
 int launch_dense_apply(Mesh* m, Surface* s, double scale, const double* v, double* z);
 int dense_copy_out(Mesh* m, Surface* s, float scale, float* out, int ld_out);
+
+// ---- one application of the block preconditioner (solver.cu), for the autotuner: prepares it at
+// the current Jacobian (dense surface blocks if requested) and applies it to v
+int block_precond_apply(Mesh* m, const double* v, double* z, int inner_iters, bool dense);
 
 // ---- blas (solver.cu)
 int dot(Mesh* m, const double* a, const double* b, int n, double* out_host);

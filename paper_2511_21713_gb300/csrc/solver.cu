@@ -534,7 +534,7 @@ static int prepare_block_precond(Mesh* m, bool dense) {
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_coop, PCG_T, 0));
     // all resident blocks (memory-level parallelism for the SpMV phases), but no more than
     // one pass of 8 lanes per row needs
-    int want = per * nsm;
+    int want = (m->tune_pcg_bps > 0 ? std::min(per, m->tune_pcg_bps) : per) * nsm;
     want = std::min(want, std::max(1, blocks_for((int64_t)m->nv * 8, PCG_T)));
     m->coop_blocks = (coop && per > 0) ? want : -1;
   }
@@ -612,6 +612,18 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
     PB_LAUNCHED(m);
   }
   return surface_rows_precond(m, v, z);
+}
+
+int block_precond_apply(Mesh* m, const double* v, double* z, int inner_iters, bool dense) {
+  const int n = m->n;
+  PB_TRY(ensure(m->gdiag, n));
+  if (m->gpcg.n < 6 * (size_t)n) {
+    PB_TRY(m->gpcg.alloc(6 * (size_t)n));
+    PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 6 * (size_t)n * sizeof(double), m->stream));
+  }
+  PB_TRY(jacobi(m, m->gdiag.p));
+  PB_TRY(prepare_block_precond(m, dense));
+  return block_precond(m, v, z, inner_iters);
 }
 
 static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, int maxit, int precond,
@@ -1526,7 +1538,7 @@ int pbfb_set_tuning(pbfb_mesh* h, int nbody_targets_per_thread, int nbody_blocks
     return PBFB_ERR_INVALID;
   }
   m->tune_packed = nbody_packed & 1;
-  m->tune_ff_scalar = (nbody_packed >> 1) & 1;
+  m->tune_ff_kernel = ((nbody_packed >> 1) & 1) ? 1 : 0;
   if (nbody_targets_per_thread != 0 && nbody_targets_per_thread != 1 && nbody_targets_per_thread != 2 &&
       nbody_targets_per_thread != 4 && nbody_targets_per_thread != 8) {
     pbfb::set_error("set_tuning: targets per thread must be 0, 1, 2, 4 or 8");

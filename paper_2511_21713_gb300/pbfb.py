@@ -101,8 +101,8 @@ class Response(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("nbody_targets_per_thread", ctypes.c_int32), ("nbody_blocks_per_sm", ctypes.c_int32),
                 ("nbody_packed", ctypes.c_int32), ("ff_blocks_per_sm", ctypes.c_int32),
-                ("ff_one_target", ctypes.c_int32), ("spmv_lanes", ctypes.c_int32),
-                ("spmv_block", ctypes.c_int32)]
+                ("ff_kernel", ctypes.c_int32), ("spmv_lanes", ctypes.c_int32),
+                ("spmv_block", ctypes.c_int32), ("pcg_blocks_per_sm", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -331,9 +331,9 @@ class Mesh:
                 self.apply_tuning(cache[key]["shapes"])
                 return cache[key]["shapes"], cache[key]["ms"]
         t = Tuning()
-        ms = np.zeros(3)
+        ms = np.zeros(4)
         _check(load().pbfb_autotune(self.h, int(reps), ctypes.byref(t), _ptr(ms)))
-        shapes, times = t.as_dict(), dict(nbody_f32=ms[0], nbody_ff=ms[1], spmv=ms[2])
+        shapes, times = t.as_dict(), dict(nbody_f32=ms[0], nbody_ff=ms[1], spmv=ms[2], inner_pcg=ms[3])
         if key is not None:
             cache = json.load(open(cache_file)) if os.path.exists(cache_file) else {}
             cache[key] = {"shapes": shapes, "ms": times}

@@ -288,23 +288,27 @@ def test_error_statuses(tiny_case):
     m.close()
 
 
-def test_float_float_packed_kernel_matches_scalar(pair):
-    """The two-targets-per-thread float-float far field and the one-target kernel agree to
-    float-float rounding (1e-13 of the largest entry), ragged tails included."""
+def test_float_float_kernels_agree(pair):
+    """The float-float far-field variants -- one target per thread, two per thread on float2
+    instructions, and mutual pairs evaluated once for both directions -- agree to float-float
+    rounding (1e-13 of the largest entry), ragged tails included."""
     from paper_2511_21713_gb300 import pbfb
     case, m, P = pair
     m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.FLOAT2)
     rng = np.random.default_rng(21)
+    base = m.get_tuning()
     try:
         for which, n in ((pbfb.GAMMA_M, P.nm), (pbfb.GAMMA_S, P.ns)):
             x = dev(rng.standard_normal(n) + 0.5)
             for op in (0, 1):
-                ya, yb = dev(np.zeros(n)), dev(np.zeros(n))
-                m.set_tuning(0, 0, 0)
-                m.bem_apply(which, op, x, ya)
-                m.set_tuning(0, 0, 2)
-                m.bem_apply(which, op, x, yb)
-                a, b = host(ya), host(yb)
-                assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max(), (which, op, np.abs(a - b).max())
+                ys = {}
+                for kind in (1, 2, 3):
+                    m.apply_tuning(dict(base, ff_kernel=kind))
+                    ys[kind] = dev(np.zeros(n))
+                    m.bem_apply(which, op, x, ys[kind])
+                b = host(ys[1])
+                for kind in (2, 3):
+                    a = host(ys[kind])
+                    assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max(), (which, op, kind, np.abs(a - b).max())
     finally:
-        m.set_tuning(0, 0, 0)
+        m.apply_tuning(base)
