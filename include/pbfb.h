@@ -303,7 +303,10 @@ int pbfb_set_tuning(pbfb_mesh* mesh, int nbody_targets_per_thread, int nbody_blo
 typedef struct pbfb_tuning {
   int32_t nbody_targets_per_thread;  /* float32 far field: 1, 2, 4 or 8 */
   int32_t nbody_blocks_per_sm;       /* float32 far field source splits: 1..64 */
-  int32_t nbody_packed;              /* 1: f32x2 kernel (needs 2+ targets per thread) */
+  int32_t nbody_packed;              /* 1: f32x2 kernel (needs 2+ targets per thread);
+                                        2: mutual pairs, each point pair evaluated once for
+                                        both directions (4 targets per thread; blocks_per_sm
+                                        counts one-warp blocks) */
   int32_t ff_blocks_per_sm;          /* float-float far field source splits: 1..64 */
   int32_t ff_kernel;                 /* float-float far field: 1 one target per thread,
                                         2 two per thread (float2), 3 mutual pairs */
@@ -323,7 +326,8 @@ int pbfb_apply_tuning(pbfb_mesh* mesh, const pbfb_tuning* t);
 /* Autotuner (the paper has no counterpart: launch shapes are a property of
  * this implementation).  Times, with CUDA events on the mesh's stream, every
  * candidate shape of the float32 far field (targets per thread 1/2/4, packed
- * or not, 8/16/32 blocks per SM of source splits) and of the float-float far
+ * or not, 8/16/32 blocks per SM of source splits; or mutual pairs with
+ * 16/32/64 one-warp blocks per SM) and of the float-float far
  * field (4/8/16 blocks per SM; one or two targets per thread, or mutual
  * pairs evaluated once for both directions) on both
  * surfaces of this mesh at the current parameters, and of the operator's

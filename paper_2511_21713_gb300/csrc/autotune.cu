@@ -3,6 +3,7 @@
 // mesh's own surfaces and sparse pattern; the fastest is applied to the mesh.
 #include <cuda_runtime.h>
 
+#include <initializer_list>
 #include <vector>
 
 #include "pbfb_internal.cuh"
@@ -27,8 +28,9 @@ bool valid_tuning(const pbfb_tuning* t) {
   const int tp = t->nbody_targets_per_thread;
   if (!(tp == 0 || tp == 1 || tp == 2 || tp == 4 || tp == 8)) return false;
   if (!in(t->nbody_blocks_per_sm, 1, 64) || !in(t->ff_blocks_per_sm, 1, 64)) return false;
-  if (t->nbody_packed < 0 || t->nbody_packed > 1 || t->ff_kernel < 0 || t->ff_kernel > 3) return false;
-  if (t->nbody_packed && tp != 0 && tp < 2) return false;
+  if (t->nbody_packed < 0 || t->nbody_packed > 2 || t->ff_kernel < 0 || t->ff_kernel > 3) return false;
+  if (t->nbody_packed == 1 && tp != 0 && tp < 2) return false;
+  if (t->nbody_packed == 2 && tp != 4) return false;
   const int L = t->spmv_lanes, B = t->spmv_block;
   if (!(L == 0 || L == 4 || L == 8 || L == 16)) return false;
   if (!(B == 0 || B == 128 || B == 256 || B == 512)) return false;
@@ -94,9 +96,10 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
   double t_best[3] = {1e300, 1e300, 1e300};
   // float32 far field
   for (int tpt : {1, 2, 4})
-    for (int packed : {0, 1}) {
-      if (packed && tpt < 2) continue;
-      for (int bps : {8, 16, 32}) {
+    for (int packed : {0, 1, 2}) {
+      if (packed == 1 && tpt < 2) continue;
+      if (packed == 2 && tpt != 4) continue;
+      for (int bps : packed == 2 ? std::initializer_list<int>{16, 32, 64} : std::initializer_list<int>{8, 16, 32}) {
         pbfb_tuning t = best;
         t.nbody_targets_per_thread = tpt;
         t.nbody_packed = packed;

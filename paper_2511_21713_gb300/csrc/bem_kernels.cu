@@ -603,6 +603,163 @@ __global__ void __launch_bounds__(NT) k_nbody_f32x2(int nq, const float4* __rest
     if (ti[k] < nq) out[(int64_t)blockIdx.y * nq + ti[k]] = acc64[k];
 }
 
+// Mutual float32 N-body for the GMRES operator: every unordered pair of points evaluated once
+// for both directions (the organisation of k_nbody_ffm, with one-warp blocks).  Block (rg, cg)
+// is one warp; it holds 4 targets per lane (I * 128 + lane + 32 k) as two f32x2 pairs, streams
+// the 128 points of tile J through shared memory, and at step s lane l takes point (l + s) mod
+// 128, so the 32 lanes update distinct source-side sums (warp-synchronous, fixed order).  Pair
+// (i, j): d = x_i - x_j, f = (1 + kappa r) / r^2, g = exp(-kappa r) / r;
+//   to i: (s_j + (m_j . d) f) g,   to j: (s_i - (m_i . d) f) g.
+constexpr int FM_T = 128;
+
+template <bool YUK>
+__global__ void __launch_bounds__(32) k_nbody_f32m(int nq, int G, const float4* __restrict__ spos,
+                                                   const float4* __restrict__ sdl, float kappa,
+                                                   double* __restrict__ PI, double* __restrict__ PJ) {
+  __shared__ float4 sp[FM_T], sd[FM_T];
+  __shared__ float accj[FM_T];
+  int t = blockIdx.x, rg = 0;
+  while (t >= G - rg) {
+    t -= G - rg;
+    ++rg;
+  }
+  const int cg = rg + t;
+  const int nT = (nq + FM_T - 1) / FM_T;
+  const int tpg = (nT + G - 1) / G;
+  const int i0g = rg * tpg, i1g = min(nT, (rg + 1) * tpg);
+  const int j0g = cg * tpg, j1g = min(nT, (cg + 1) * tpg);
+  const int lane = threadIdx.x;
+  const float nk = -kappa * 1.4426950408889634f;
+  const f32x2 nk2 = pk2(nk, nk), kap2 = pk2(kappa, kappa), one2 = pk2(1.f, 1.f);
+  for (int I = i0g; I < i1g; ++I) {
+    float tx[4], ty[4], tz[4], ts[4], tmx[4], tmy[4], tmz[4];
+    int ti[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ti[k] = I * FM_T + lane + 32 * k;
+      const bool v = ti[k] < nq;
+      const float4 p = v ? spos[ti[k]] : make_float4(2e15f, 0.f, 0.f, 0.f);
+      const float4 d = v ? sdl[ti[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      tx[k] = p.x;
+      ty[k] = p.y;
+      tz[k] = p.z;
+      ts[k] = p.w;
+      tmx[k] = -d.x;  // negated: the source-side term needs -(m_i . d)
+      tmy[k] = -d.y;
+      tmz[k] = -d.z;
+    }
+    f32x2 TX[2], TY[2], TZ[2], TS[2], NMX[2], NMY[2], NMZ[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      TX[c] = pk2(tx[2 * c], tx[2 * c + 1]);
+      TY[c] = pk2(ty[2 * c], ty[2 * c + 1]);
+      TZ[c] = pk2(tz[2 * c], tz[2 * c + 1]);
+      TS[c] = pk2(ts[2 * c], ts[2 * c + 1]);
+      NMX[c] = pk2(tmx[2 * c], tmx[2 * c + 1]);
+      NMY[c] = pk2(tmy[2 * c], tmy[2 * c + 1]);
+      NMZ[c] = pk2(tmz[2 * c], tmz[2 * c + 1]);
+    }
+    double acc64[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int J = max(I, j0g); J < j1g; ++J) {
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int jl = J * FM_T + lane + 32 * k;
+        if (jl < nq) {
+          sp[lane + 32 * k] = spos[jl];
+          sd[lane + 32 * k] = sdl[jl];
+        } else {
+          sp[lane + 32 * k] = make_float4(1e15f, 0.f, 0.f, 0.f);
+          sd[lane + 32 * k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        accj[lane + 32 * k] = 0.f;
+      }
+      __syncwarp();
+      const int cnt = min(FM_T, nq - J * FM_T);
+      if (J == I) {
+        // diagonal tile: target side only, coincident point skipped
+        float a[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int jj = 0; jj < cnt; ++jj) {
+          const float4 p = sp[jj], d = sd[jj];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (jj == lane + 32 * k) continue;
+            const float dx = tx[k] - p.x, dy = ty[k] - p.y, dz = tz[k] - p.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrt_approx(r2);
+            const float nd = fmaf(d.x, dx, fmaf(d.y, dy, d.z * dz));
+            const float ri2 = ri * ri;
+            if (YUK) {
+              const float r = r2 * ri;
+              const float e = ex2_approx(nk * r);
+              const float tt = fmaf(nd * fmaf(kappa, r, 1.f), ri2, p.w);
+              a[k] = fmaf(tt, e * ri, a[k]);
+            } else {
+              a[k] = fmaf(fmaf(nd, ri2, p.w), ri, a[k]);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc64[k] += (double)a[k];
+      } else {
+        f32x2 acc[2] = {0ull, 0ull};
+#pragma unroll 2
+        for (int st = 0; st < FM_T; ++st) {
+          const int jj = (lane + st) & (FM_T - 1);
+          const float4 p = sp[jj], d = sd[jj];
+          const f32x2 PX = pk2(p.x, p.x), PY = pk2(p.y, p.y), PZ = pk2(p.z, p.z), PS = pk2(p.w, p.w);
+          const f32x2 MX = pk2(d.x, d.x), MY = pk2(d.y, d.y), MZ = pk2(d.z, d.z);
+          float cj = 0.f;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const f32x2 dx = sub2(TX[c], PX), dy = sub2(TY[c], PY), dz = sub2(TZ[c], PZ);
+            const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+            float ra, rb;
+            upk2(r2, ra, rb);
+            const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
+            const f32x2 ri2 = mul2(ri, ri);
+            f32x2 f, g;
+            if (YUK) {
+              const f32x2 r = mul2(r2, ri);
+              float xa, xb;
+              upk2(mul2(nk2, r), xa, xb);
+              const f32x2 e = pk2(ex2_approx(xa), ex2_approx(xb));
+              f = mul2(fma2(kap2, r, one2), ri2);
+              g = mul2(e, ri);
+            } else {
+              f = ri2;
+              g = ri;
+            }
+            const f32x2 ndj = fma2(MZ, dz, fma2(MY, dy, mul2(MX, dx)));
+            acc[c] = fma2(fma2(ndj, f, PS), g, acc[c]);
+            const f32x2 ndi = fma2(NMZ[c], dz, fma2(NMY[c], dy, mul2(NMX[c], dx)));
+            float u0, u1;
+            upk2(mul2(fma2(ndi, f, TS[c]), g), u0, u1);
+            cj += u0 + u1;
+          }
+          accj[jj] += cj;
+          __syncwarp();
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          float a0, a1;
+          upk2(acc[c], a0, a1);
+          acc64[2 * c] += (double)a0;
+          acc64[2 * c + 1] += (double)a1;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int jl = J * FM_T + lane + 32 * k;
+          if (jl < nq) PJ[(int64_t)rg * nq + jl] += (double)accj[lane + 32 * k];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (ti[k] < nq) PI[(int64_t)cg * nq + ti[k]] = acc64[k];
+  }
+}
+
 // float64 N-body, same organisation (one target per thread).
 template <int NT, bool YUK>
 __global__ void __launch_bounds__(NT) k_nbody_f64(int nq, const double* __restrict__ s64, double kappa,
@@ -1413,6 +1570,7 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
   KernelClassTimer& tm = f64 ? m->t_nbody64 : m->t_nbody;
   timer_begin(m, tm, &ev);
   int nsplit;
+  double* vals = s->val.p;
   if (f64) {
     constexpr int NT = 128;
     int ntb = blocks_for(nq, NT);
@@ -1431,20 +1589,41 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
   } else {
     int tpt, packed, bps;
     f32_shape(m, nq, &tpt, &packed, &bps);
-    const int ntb = blocks_for(nq, F32_NT * tpt);
-    nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * F32_NT)));
-    const int per = blocks_for(blocks_for(nq, nsplit), F32_NT) * F32_NT;
-    nsplit = blocks_for(nq, per);
-    if ((size_t)nsplit * nq > s->val.n) {
-      set_error("far-field split buffer too small");
-      return PBFB_ERR_STATE;
+    if (packed == 2) {
+      // mutual pairs: G tile groups, G (G + 1) / 2 one-warp blocks (about bps per SM)
+      const int nT = blocks_for(nq, FM_T);
+      int G = (int)std::sqrt(2.0 * bps * 152.0);
+      G = std::max(1, std::min(G, nT));
+      PB_TRY(ensure(s->mval, (size_t)(2 * G + 1) * nq));
+      double* PI = s->mval.p;
+      double* PJ = PI + (size_t)G * nq;
+      double* out = PJ + (size_t)G * nq;
+      PB_CUDA(cudaMemsetAsync(PI, 0, (size_t)2 * G * nq * sizeof(double), m->stream));
+      const int nblk = G * (G + 1) / 2;
+      if (yuk)
+        k_nbody_f32m<true><<<nblk, 32, 0, m->stream>>>(nq, G, s->spos.p, s->sdl.p, (float)kappa, PI, PJ);
+      else
+        k_nbody_f32m<false><<<nblk, 32, 0, m->stream>>>(nq, G, s->spos.p, s->sdl.p, (float)kappa, PI, PJ);
+      PB_LAUNCHED(m);
+      k_mutual_sum<<<blocks_for(nq, 256), 256, 0, m->stream>>>(nq, G, PI, PJ, out);
+      nsplit = 1;
+      vals = out;
+    } else {
+      const int ntb = blocks_for(nq, F32_NT * tpt);
+      nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * F32_NT)));
+      const int per = blocks_for(blocks_for(nq, nsplit), F32_NT) * F32_NT;
+      nsplit = blocks_for(nq, per);
+      if ((size_t)nsplit * nq > s->val.n) {
+        set_error("far-field split buffer too small");
+        return PBFB_ERR_STATE;
+      }
+      launch_nbody_f32(m, s, kappa, tpt, packed, nsplit, per, s->spos.p, s->sdl.p, s->val.p);
     }
-    launch_nbody_f32(m, s, kappa, tpt, packed, nsplit, per, s->spos.p, s->sdl.p, s->val.p);
   }
   PB_LAUNCHED(m);
   timer_end(m, tm, ev, (double)nq * (double)nq);
   if (!f64) m->nbody_flops += (yuk ? 24.0 : 18.0) * (double)nq * (double)nq;
-  return test_reduce(m, s, s->val.p, nsplit, y, accumulate);
+  return test_reduce(m, s, vals, nsplit, y, accumulate);
 }
 
 int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, double cs, double cd,

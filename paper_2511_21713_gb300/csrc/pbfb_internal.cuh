@@ -112,6 +112,7 @@ struct Surface {
   DBuf<double> val;             // nsplit * nq target potentials
   DBuf<float4> ffsrc, fftgt;    // float-float sources (4 float4) and targets (2 float4) per point
   int nsplit = 1;
+  DBuf<double> mval;            // mutual float32 far field: 2 G partial rows + the sum
   // dense single layer (float32, ld x ld): -V^-1 once inverted (bem_dense.cu)
   DBuf<float> vinv;
   int vinv_ld = 0;

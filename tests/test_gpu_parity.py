@@ -90,6 +90,29 @@ def test_boundary_operators(pair, precision):
             assert rel(host(y), Mo @ x) < tol, (which, op)
 
 
+@pytest.mark.parametrize("shape", [dict(nbody_targets_per_thread=4, nbody_packed=2, nbody_blocks_per_sm=32),
+                                   dict(nbody_targets_per_thread=1, nbody_packed=0, nbody_blocks_per_sm=16),
+                                   dict(nbody_targets_per_thread=2, nbody_packed=1, nbody_blocks_per_sm=32)])
+def test_float32_far_field_variants(pair, shape):
+    """Every float32 far-field variant (mutual pairs, one target per thread, packed f32x2)
+    within 3e-6 of the oracle's operators, ragged tails included."""
+    from paper_2511_21713_gb300 import pbfb
+    case, m, P = pair
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.MIXED)
+    base = m.get_tuning()
+    rng = np.random.default_rng(8)
+    try:
+        m.apply_tuning(dict(base, **shape))
+        for which, Vo, Ko, n in ((pbfb.GAMMA_M, P.VL, P.KL, P.nm), (pbfb.GAMMA_S, P.VY, P.KY, P.ns)):
+            for op, Mo in ((0, Vo), (1, Ko)):
+                x = rng.standard_normal(n) + 1.0
+                y = dev(np.zeros(n))
+                m.bem_apply(which, op, dev(x), y)
+                assert rel(host(y), Mo @ x) < 3e-6, (which, op)
+    finally:
+        m.apply_tuning(base)
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_coupled_apply(pair, precision):
     from paper_2511_21713_gb300 import pbfb
