@@ -3,7 +3,6 @@
 // mesh's own surfaces and sparse pattern; the fastest is applied to the mesh.
 #include <cuda_runtime.h>
 
-#include <initializer_list>
 #include <vector>
 
 #include "pbfb_internal.cuh"
@@ -99,7 +98,9 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
     for (int packed : {0, 1, 2}) {
       if (packed == 1 && tpt < 2) continue;
       if (packed == 2 && tpt != 4) continue;
-      for (int bps : packed == 2 ? std::initializer_list<int>{16, 32, 64} : std::initializer_list<int>{8, 16, 32}) {
+      static const int bps_split[3] = {8, 16, 32}, bps_mutual[3] = {16, 32, 64};
+      for (int bi = 0; bi < 3; ++bi) {
+        const int bps = packed == 2 ? bps_mutual[bi] : bps_split[bi];
         pbfb_tuning t = best;
         t.nbody_targets_per_thread = tpt;
         t.nbody_packed = packed;
