@@ -113,9 +113,11 @@ class Clocks:
 
 
 def serving_cases(n, seed=5000):
-    """Seeded serving requests: spheres of 2000-8000 triangles per surface (log-uniform in the
-    count), radius 12, shell to 24, 1-200 unit charges in r < 9.6, ionic strength U(0.01, 1) M,
-    eps_in in {2, 4}.  Meshes of the same frequency are reused."""
+    """Seeded serving requests, sphere or double helix by a fair coin, 2000-8000 triangles per
+    surface (log-uniform), ionic strength U(0.01, 1) M, eps_in in {2, 4}.  Spheres: radius 12,
+    shell to 24, 1-200 unit charges in r < 9.6; meshes of the same frequency are shared, so
+    repeated geometries occur (as for repeated requests on one molecule).  Helices: 8-24 base
+    pairs with their atoms' charges, shell to three Debye lengths beyond the surface."""
     import numpy as np
     from paper_2511_21713_gb300 import inputs
     rng = inputs.SplitMix64(seed)
@@ -123,15 +125,21 @@ def serving_cases(n, seed=5000):
     for i in range(n):
         tri = 2000.0 * 4.0 ** rng.uniform()
         nu = max(10, min(20, int(round((tri / 20.0) ** 0.5))))
-        nq = 1 + rng.below(200)
-        q, z = inputs.ball_charges(nq, 9.6, rng.below(nq + 1), seed + 17 * i)
         ionic = 0.01 + 0.99 * rng.uniform()
         eps_in = (2.0, 4.0)[rng.below(2)]
-        if nu not in meshes:
-            meshes[nu] = inputs.spherical_shell(nu, 12.0, 24.0, max(8, int(0.85 * nu)))
-        xyz, tets, gm, gs = meshes[nu]
         kappa = inputs.kappa_from_ionic_strength(ionic, 80.0, 300.0)
-        cases.append(inputs.Case(f"serve{i}", xyz, tets, gm, gs, q, z, eps_in, 80.0, kappa, 300.0))
+        if rng.below(2) == 0:
+            nq = 1 + rng.below(200)
+            q, z = inputs.ball_charges(nq, 9.6, rng.below(nq + 1), seed + 17 * i)
+            if nu not in meshes:
+                meshes[nu] = inputs.spherical_shell(nu, 12.0, 24.0, max(8, int(0.85 * nu)))
+            xyz, tets, gm, gs = meshes[nu]
+            cases.append(inputs.Case(f"serve{i}", xyz, tets, gm, gs, q, z, eps_in, 80.0, kappa, 300.0))
+        else:
+            nbp = 8 + rng.below(17)
+            h = inputs.double_helix(n_bp=nbp, nu=nu, layers=max(8, int(0.6 * nu)), seed=seed + 31 * i,
+                                    n_interior=62 * nbp, ionic=ionic, eps_in=eps_in)
+            cases.append(h)
     return cases
 
 
@@ -148,7 +156,7 @@ def run_serving(pbfb, cases, max_inflight, budget):
         return got
 
     opts = pbfb.default_opts(precision=pbfb.MIXED)
-    sv = pbfb.Server(budget, max_inflight)
+    sv = pbfb.Server(budget, max_inflight, cached_meshes=16)
     t0 = time.perf_counter()
     for i, c in enumerate(cases):
         sv.submit(c, i, opts=opts)
@@ -160,7 +168,7 @@ def run_serving(pbfb, cases, max_inflight, budget):
     rate = 0.8 * cap
     rng = inputs.SplitMix64(77)
     arrivals = np.cumsum([-np.log(1.0 - rng.uniform()) / rate for _ in cases])
-    sv = pbfb.Server(budget, max_inflight)
+    sv = pbfb.Server(budget, max_inflight, cached_meshes=16)
     t0 = time.perf_counter()
     got = []
     for i, c in enumerate(cases):
@@ -169,6 +177,7 @@ def run_serving(pbfb, cases, max_inflight, budget):
         sv.submit(c, i, opts=opts)
     got += drain(sv, len(cases) - len(got))
     span = time.perf_counter() - t0
+    st2 = sv.stats()
     sv.close()
     lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in got])
     ok = all(r["status"] == 0 for r in res + got)
@@ -176,9 +185,10 @@ def run_serving(pbfb, cases, max_inflight, budget):
             "saturation_solves_per_s": cap, "peak_bytes": st["peak"],
             "open_loop_rate_per_s": rate, "open_loop_solves_per_s": len(cases) / span,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "all_ok": ok,
-            "workload": "spheres of 2000-8000 triangles per surface (log-uniform), 1-200 charges, "
-                        "0.01-1 M, eps_in 2 or 4; mixed precision, paper tolerances"}
+            "all_ok": ok, "resident_mesh_hits": [int(st["mesh_hits"]), int(st2["mesh_hits"])],
+            "workload": "sphere (1-200 charges) or double helix (8-24 bp) by a fair coin, 2000-8000 "
+                        "triangles per surface (log-uniform), 0.01-1 M, eps_in 2 or 4; mixed precision, "
+                        "paper tolerances; up to 16 meshes kept resident between requests"}
 
 
 def run_pbfb(args):

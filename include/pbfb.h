@@ -396,9 +396,16 @@ typedef struct pbfb_response {
  * the sum of their estimated device memory stays within hbm_budget_bytes (a
  * request alone is always admitted), and run mesh creation, charges and the
  * full solve; requests that arrive while others run start as memory frees and
- * their work overlaps on the GPU.  Each request is solved on its own buffers
- * with deterministic kernels: its result is identical to solving it alone. */
-int pbfb_server_create(int device, uint64_t hbm_budget_bytes, int max_inflight, pbfb_server** out);
+ * their work overlaps on the GPU.  Up to cached_meshes (0..1024) meshes stay
+ * resident after their request (counted in the budget; idle ones are evicted,
+ * least recently used first, when a new request needs the memory): a request
+ * whose geometry equals a resident mesh's (coordinates, tets and surfaces
+ * compared exactly) reuses it, skipping mesh creation, the Laplace near-field
+ * corrections and dense inverse, and, at the same kappa, the Yukawa ones.
+ * Each request is solved with deterministic kernels on buffers no other
+ * request uses meanwhile: its result is identical to solving it alone. */
+int pbfb_server_create(int device, uint64_t hbm_budget_bytes, int max_inflight, int cached_meshes,
+                       pbfb_server** out);
 
 /* Queues a request (copies its arrays; returns at once).  PBFB_ERR_OOM if its
  * estimated memory exceeds the whole budget. */
@@ -408,8 +415,9 @@ int pbfb_server_submit(pbfb_server* server, const pbfb_request* request);
  * timeout_us microseconds for the first one; *n_out = how many. */
 int pbfb_server_poll(pbfb_server* server, pbfb_response* out, int max, int timeout_us, int* n_out);
 
-/* stats (host, 6 doubles): submitted, completed, queued, bytes in use, peak
- * bytes in use, budget. */
+/* stats (host, 8 doubles): submitted, completed, queued, bytes in use
+ * (running requests and resident meshes), peak bytes in use, budget,
+ * requests served on a resident mesh, resident meshes. */
 int pbfb_server_stats(pbfb_server* server, double* stats);
 
 /* Finishes the requests already admitted, drops the queued ones, frees all. */

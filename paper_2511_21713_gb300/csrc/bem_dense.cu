@@ -382,6 +382,9 @@ int build_dense_single_layer(Mesh* m, Surface* s, double kappa, bool invert) {
     set_error("dense single layer: a pivot of the float32 sweep was not positive");
     return PBFB_ERR_NONFINITE;
   }
+  // the apply kernel stages a vector of ld floats in shared memory
+  const int smem = ld * (int)sizeof(float);
+  if (smem > 48 * 1024) PB_CUDA(cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   s->vinv_ok = invert;
   s->vinv_kappa = kappa;
   return PBFB_OK;
@@ -392,8 +395,7 @@ int launch_dense_apply(Mesh* m, Surface* s, double scale, const double* v, doubl
     set_error("dense single-layer inverse not built");
     return PBFB_ERR_STATE;
   }
-  const int smem = s->vinv_ld * (int)sizeof(float);
-  if (smem > 48 * 1024) PB_CUDA(cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int smem = s->vinv_ld * (int)sizeof(float);  // attribute set when the matrix was built
   k_dense_apply<<<(s->nv + 7) / 8, 256, smem, m->stream>>>(s->nv, s->vinv_ld, s->vinv.p, scale, v, z);
   PB_LAUNCHED(m);
   return PBFB_OK;

@@ -171,7 +171,15 @@ struct Mesh {
   int gm_restart = 0;
   DBuf<double> gV, gw, gz, gr, gdiag, gh, gpart, gtmp;
   DBuf<double> gZ;          // flexible GMRES: preconditioned basis (restart x n)
-  DBuf<double> gpcg;        // inner PCG vectors (6 x n)
+  DBuf<double> gpcg;        // inner PCG vectors (6 x n), then the fixed input and output of the
+                            // captured preconditioner graph (n each)
+  // non-cooperative block preconditioner captured as a CUDA graph (launch-bound: ~100 small
+  // kernels per application); rebuilt when a buffer or setting it was captured with changes
+  cudaGraphExec_t pcg_graph = nullptr;
+  const void* pcg_graph_key[9] = {};
+  int pcg_graph_iters = -1;
+  double pcg_graph_nodes = 0;
+  bool pcg_graph_off = false;       // capture not possible on this stream (e.g. the legacy stream)
   DBuf<double> gones;       // n ones
   // block preconditioner: FEM block + Robin term on Gamma_s, and its Jacobi diagonal
   int nrobin = 0;
@@ -201,6 +209,9 @@ struct Mesh {
   KernelClassTimer t_nbody, t_nbody64, t_nbodyff, t_spmv, t_elem, t_dense;
   DBuf<float2> ff_tab;      // float-float exp table of the Yukawa kernel
   double nbody_flops = 0.0;  // float32 far-field flops issued (18 per Laplace pair, 24 per Yukawa pair)
+  ~Mesh() {
+    if (pcg_graph) cudaGraphExecDestroy(pcg_graph);
+  }
 };
 
 // ---- whole-solve entry points shared by the C ABI, the batch call and the server

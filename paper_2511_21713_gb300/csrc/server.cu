@@ -6,7 +6,9 @@
 // GPU work of different requests overlap.  Every request is solved on its own mesh, stream and
 // buffers with deterministic kernels, so its result does not depend on what else is in flight.
 // Meshes solved concurrently use the multi-kernel inner PCG (no grid-wide barrier, which could
-// not be guaranteed co-resident when several run at once).
+// not be guaranteed co-resident when several run at once).  Up to `cached_meshes` meshes stay on
+// the device after their request; a later request with the same geometry (compared exactly)
+// reuses one instead of building it again.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,8 +57,43 @@ struct Request {
   double eps_in = 0, eps_out = 0, kappa = 0, T = 0;
   pbfb_newton_opts opts;
   size_t bytes = 0;
+  uint64_t hash = 0;  // of the geometry (coordinates, tets, both surfaces)
   double t_submit = 0;
 };
+
+// A mesh kept on the device between requests with the same geometry (its topology, geometry,
+// near-field corrections, dense single-layer inverses and solve workspace stay resident).
+struct Cached {
+  uint64_t hash = 0;
+  std::vector<double> xyz;
+  std::vector<int> tets, gm, gs;
+  Mesh* m = nullptr;
+  size_t bytes = 0;
+  bool busy = false;
+  uint64_t last_use = 0;
+};
+
+// FNV-1a over the bytes of the geometry arrays
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+uint64_t geometry_hash(const Request& r) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv(h, r.xyz.data(), r.xyz.size() * sizeof(double));
+  h = fnv(h, r.tets.data(), r.tets.size() * sizeof(int));
+  h = fnv(h, r.gm.data(), r.gm.size() * sizeof(int));
+  return fnv(h, r.gs.data(), r.gs.size() * sizeof(int));
+}
+
+bool same_geometry(const Request& r, const Cached& c) {
+  return r.xyz == c.xyz && r.tets == c.tets && r.gm == c.gm && r.gs == c.gs;
+}
 
 double now_ms() {
   using namespace std::chrono;
@@ -69,13 +106,39 @@ struct Server {
   int dev = 0;
   size_t budget = 0, in_use = 0, peak = 0;
   int nworkers = 0;
+  int max_cached = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> queue;
   std::deque<pbfb_response> done;
   std::vector<std::thread> workers;
+  std::vector<Cached*> cache;   // in_use counts every cached mesh, busy or idle
+  uint64_t tick = 0;
   bool stop = false;
-  int64_t submitted = 0, completed = 0;
+  int64_t submitted = 0, completed = 0, hits = 0;
+
+  // an idle cached mesh of this geometry's hash, or null (under mu)
+  Cached* find_idle(const Request* r) {
+    for (Cached* c : cache)
+      if (!c->busy && c->hash == r->hash && c->xyz.size() == r->xyz.size() && c->tets.size() == r->tets.size())
+        return c;
+    return nullptr;
+  }
+
+  // drop idle cached meshes, least recently used first, until `need` more bytes fit (under mu);
+  // the meshes are destroyed by the caller after releasing the lock
+  void evict_for(size_t need, std::vector<Mesh*>& dead) {
+    while (in_use > 0 && in_use + need > budget) {
+      Cached* lru = nullptr;
+      for (Cached* c : cache)
+        if (!c->busy && (!lru || c->last_use < lru->last_use)) lru = c;
+      if (!lru) return;
+      cache.erase(std::find(cache.begin(), cache.end(), lru));
+      in_use -= lru->bytes;
+      dead.push_back(lru->m);
+      delete lru;
+    }
+  }
 
   void run_worker() {
     cudaSetDevice(dev);
@@ -83,21 +146,34 @@ struct Server {
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     while (true) {
       Request* r = nullptr;
+      Cached* hit = nullptr;
+      std::vector<Mesh*> dead;
       {
-        // take the head of the queue once its memory fits (a request alone always fits);
-        // cv_work is signalled on new requests, on completions and on shutdown
+        // take the head of the queue once it fits: on an idle cached mesh of its geometry (no new
+        // memory), or in the budget after evicting idle cached meshes (a request alone always
+        // fits); cv_work is signalled on new requests, on completions and on shutdown
         std::unique_lock<std::mutex> lk(mu);
         while (!stop) {
-          if (!queue.empty() && (in_use == 0 || in_use + queue.front()->bytes <= budget)) {
-            r = queue.front();
-            queue.pop_front();
-            in_use += r->bytes;
-            peak = std::max(peak, in_use);
-            break;
+          if (!queue.empty()) {
+            Request* head = queue.front();
+            hit = find_idle(head);
+            if (!hit) evict_for(head->bytes, dead);
+            if (hit || in_use == 0 || in_use + head->bytes <= budget) {
+              r = head;
+              queue.pop_front();
+              if (hit) {
+                hit->busy = true;
+              } else {
+                in_use += r->bytes;
+                peak = std::max(peak, in_use);
+              }
+              break;
+            }
           }
           cv_work.wait(lk);
         }
       }
+      for (Mesh* dm : dead) mesh_destroy(dm);
       if (!r) break;
       pbfb_response resp;
       std::memset(&resp, 0, sizeof(resp));
@@ -105,24 +181,55 @@ struct Server {
       resp.t_submit_ms = r->t_submit;
       resp.t_start_ms = now_ms();
       Mesh* m = nullptr;
-      int st = mesh_create(r->xyz.data(), (int)(r->xyz.size() / 3), r->tets.data(), (int64_t)(r->tets.size() / 4),
-                           r->gm.data(), (int)(r->gm.size() / 3), r->gs.data(), (int)(r->gs.size() / 3), s, &m);
-      if (st == PBFB_OK) {
-        m->no_coop = true;
-        st = charges_set(m, r->qxyz.data(), r->qz.data(), (int)r->qz.size());
+      int st = PBFB_OK;
+      if (hit && !same_geometry(*r, *hit)) {
+        // a hash collision: solve on a fresh mesh of the request's own size estimate
+        std::lock_guard<std::mutex> lk(mu);
+        hit->busy = false;
+        hit = nullptr;
+        in_use += r->bytes;
+        peak = std::max(peak, in_use);
       }
+      if (hit) {
+        m = hit->m;
+        m->stream = s;  // the mesh is idle: its earlier work ended with a synchronisation
+      } else {
+        st = mesh_create(r->xyz.data(), (int)(r->xyz.size() / 3), r->tets.data(), (int64_t)(r->tets.size() / 4),
+                         r->gm.data(), (int)(r->gm.size() / 3), r->gs.data(), (int)(r->gs.size() / 3), s, &m);
+        if (st == PBFB_OK) m->no_coop = true;
+      }
+      if (st == PBFB_OK) st = charges_set(m, r->qxyz.data(), r->qz.data(), (int)r->qz.size());
       if (st == PBFB_OK) st = solve_mesh(m, r->eps_in, r->eps_out, r->kappa, r->T, &r->opts, nullptr, &resp.result);
       if (st != PBFB_OK) std::strncpy(resp.error, last_error(), sizeof(resp.error) - 1);
       resp.status = st;
       resp.result.status = st;
-      mesh_destroy(m);
-      resp.t_done_ms = now_ms();
+      Mesh* drop = nullptr;
       {
         std::lock_guard<std::mutex> lk(mu);
-        in_use -= r->bytes;
+        if (hit) {
+          hit->busy = false;
+          hit->last_use = ++tick;
+          ++hits;
+        } else if (st == PBFB_OK && m && (int)cache.size() < max_cached) {
+          Cached* c = new Cached();
+          c->hash = r->hash;
+          c->xyz.swap(r->xyz);
+          c->tets.swap(r->tets);
+          c->gm.swap(r->gm);
+          c->gs.swap(r->gs);
+          c->m = m;
+          c->bytes = r->bytes;
+          c->last_use = ++tick;
+          cache.push_back(c);
+        } else {
+          drop = m;
+          in_use -= r->bytes;
+        }
+        resp.t_done_ms = now_ms();
         done.push_back(resp);
         ++completed;
       }
+      if (drop) mesh_destroy(drop);
       delete r;
       cv_done.notify_all();
       cv_work.notify_all();
@@ -141,9 +248,11 @@ struct pbfb_server {
 
 extern "C" {
 
-int pbfb_server_create(int device, uint64_t hbm_budget_bytes, int max_inflight, pbfb_server** out) {
+int pbfb_server_create(int device, uint64_t hbm_budget_bytes, int max_inflight, int cached_meshes,
+                       pbfb_server** out) {
   pbfb::set_error("");
-  if (!out || max_inflight < 1 || max_inflight > 64 || hbm_budget_bytes == 0) {
+  if (!out || max_inflight < 1 || max_inflight > 64 || hbm_budget_bytes == 0 || cached_meshes < 0 ||
+      cached_meshes > 1024) {
     pbfb::set_error("server_create: bad argument");
     return PBFB_ERR_INVALID;
   }
@@ -157,6 +266,7 @@ int pbfb_server_create(int device, uint64_t hbm_budget_bytes, int max_inflight, 
   sv->dev = device;
   sv->budget = hbm_budget_bytes;
   sv->nworkers = max_inflight;
+  sv->max_cached = cached_meshes;
   for (int i = 0; i < max_inflight; ++i) sv->workers.emplace_back([sv] { sv->run_worker(); });
   *out = new pbfb_server{sv};
   return PBFB_OK;
@@ -184,6 +294,7 @@ int pbfb_server_submit(pbfb_server* h, const pbfb_request* q) {
   pbfb_default_opts(&r->opts);
   if (q->opts) r->opts = *q->opts;
   r->bytes = pbfb::estimate_bytes(q->n_v, q->n_t, q->n_gm, q->n_gs, r->opts.restart);
+  r->hash = pbfb::geometry_hash(*r);
   r->t_submit = pbfb::now_ms();
   if (r->bytes > sv->budget) {
     pbfb::set_error("server_submit: request needs about %zu bytes, more than the budget %zu", r->bytes, sv->budget);
@@ -235,6 +346,8 @@ int pbfb_server_stats(pbfb_server* h, double* stats) {
   stats[3] = (double)sv->in_use;
   stats[4] = (double)sv->peak;
   stats[5] = (double)sv->budget;
+  stats[6] = (double)sv->hits;
+  stats[7] = (double)sv->cache.size();
   return PBFB_OK;
 }
 
@@ -249,6 +362,10 @@ int pbfb_server_destroy(pbfb_server* h) {
     sv->cv_work.notify_all();
     for (auto& t : sv->workers) t.join();
     for (auto* r : sv->queue) delete r;
+    for (auto* c : sv->cache) {
+      pbfb::mesh_destroy(c->m);
+      delete c;
+    }
     delete sv;
   }
   delete h;

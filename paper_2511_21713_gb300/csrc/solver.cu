@@ -573,10 +573,10 @@ static int surface_rows_precond(Mesh* m, const double* v, double* z) {
   return PBFB_OK;
 }
 
-static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
+// Inner Jacobi-PCG on the FEM block as separate kernels (no grid barrier), then the surface rows.
+static int block_precond_launches(Mesh* m, const double* v, double* z, int inner_iters, int nb) {
   const int nv = m->nv, n = m->n;
-  const int nb = std::min(152, std::max(1, blocks_for(nv, PCG_T)));
-  double* pb = m->gpcg.p;            // pcg vectors (each n long; surface part of p stays 0)
+  double* pb = m->gpcg.p;
   double* pr = pb + (size_t)n;
   double* pz = pb + 2 * (size_t)n;
   double* pp = pb + 3 * (size_t)n;
@@ -584,17 +584,6 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
   double* part = m->gpart.p;
   double* sc = m->scal.p + 5000;     // [0] pq, [1 + k] rz_k
   const double* dinv = m->pdinv.p;
-  if (m->coop_blocks > 0) {
-    int nbc = m->coop_blocks, iters = inner_iters, nvv = nv;
-    const int* sp = m->s_ptr.p;
-    const int* sc2 = m->s_col.p;
-    const double* pv = m->pval.p;
-    double* pw = pb + 5 * (size_t)n;
-    void* args[] = {&nvv, &iters, &sp, &sc2, &pv, (void*)&v, (void*)&dinv, &z, &pr, &pz, &pp, &pq, &pw, &part};
-    PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_coop, dim3(nbc), dim3(PCG_T), args, 0, m->stream));
-    PB_LAUNCHED(m);
-    return surface_rows_precond(m, v, z);
-  }
   k_pcg_init<<<nb, PCG_T, 0, m->stream>>>(nv, v, dinv, z, pr, pz, pp, part);
   PB_LAUNCHED(m);
   k_sum_to<<<1, 32, 0, m->stream>>>(part, nb, sc + 1);
@@ -614,12 +603,73 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
   return surface_rows_precond(m, v, z);
 }
 
+static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
+  const int nv = m->nv, n = m->n;
+  const int nb = std::min(152, std::max(1, blocks_for(nv, PCG_T)));
+  double* pb = m->gpcg.p;            // pcg vectors (each n long; surface part of p stays 0)
+  double* pr = pb + (size_t)n;
+  double* pz = pb + 2 * (size_t)n;
+  double* pp = pb + 3 * (size_t)n;
+  double* pq = pb + 4 * (size_t)n;
+  double* part = m->gpart.p;
+  const double* dinv = m->pdinv.p;
+  if (m->coop_blocks > 0) {
+    int nbc = m->coop_blocks, iters = inner_iters, nvv = nv;
+    const int* sp = m->s_ptr.p;
+    const int* sc2 = m->s_col.p;
+    const double* pv = m->pval.p;
+    double* pw = pb + 5 * (size_t)n;
+    void* args[] = {&nvv, &iters, &sp, &sc2, &pv, (void*)&v, (void*)&dinv, &z, &pr, &pz, &pp, &pq, &pw, &part};
+    PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_coop, dim3(nbc), dim3(PCG_T), args, 0, m->stream));
+    PB_LAUNCHED(m);
+    return surface_rows_precond(m, v, z);
+  }
+  // the ~5 inner_iters + 4 small launches replayed as one CUDA graph on fixed buffers
+  double* gin = pb + 6 * (size_t)n;
+  double* gout = pb + 7 * (size_t)n;
+  const void* key[9] = {m->gpcg.p, m->gpart.p, m->pval.p, m->pdinv.p, m->scal.p, m->gdiag.p,
+                        m->dense_m ? (const void*)m->sm.vinv.p : nullptr,
+                        m->dense_s ? (const void*)m->ss.vinv.p : nullptr, m->s_ptr.p};
+  if (!m->pcg_graph_off && m->gpcg.n >= 8 * (size_t)n &&
+      (!m->pcg_graph || m->pcg_graph_iters != inner_iters || !std::equal(key, key + 9, m->pcg_graph_key))) {
+    if (m->pcg_graph) cudaGraphExecDestroy(m->pcg_graph);
+    m->pcg_graph = nullptr;
+    const double launches0 = m->launches;
+    cudaGraph_t g = nullptr;
+    int st = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess ? PBFB_OK : -1;
+    if (st == PBFB_OK) {
+      st = block_precond_launches(m, gin, gout, inner_iters, nb);
+      const cudaError_t e = cudaStreamEndCapture(m->stream, &g);
+      if (st == PBFB_OK && e == cudaSuccess && g &&
+          cudaGraphInstantiate(&m->pcg_graph, g, 0) == cudaSuccess) {
+        m->pcg_graph_nodes = m->launches - launches0;
+        m->pcg_graph_iters = inner_iters;
+        std::copy(key, key + 9, m->pcg_graph_key);
+      } else {
+        m->pcg_graph = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();  // a refused capture leaves no error behind
+    m->launches = launches0;
+    if (!m->pcg_graph) m->pcg_graph_off = true;
+  }
+  if (m->pcg_graph) {
+    PB_CUDA(cudaMemcpyAsync(gin, v, n * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+    PB_CUDA(cudaGraphLaunch(m->pcg_graph, m->stream));
+    PB_CUDA(cudaMemcpyAsync(z, gout, n * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+    m->launches += m->pcg_graph_nodes;
+    return PBFB_OK;
+  }
+  return block_precond_launches(m, v, z, inner_iters, nb);
+}
+
 int block_precond_apply(Mesh* m, const double* v, double* z, int inner_iters, bool dense) {
   const int n = m->n;
   PB_TRY(ensure(m->gdiag, n));
-  if (m->gpcg.n < 6 * (size_t)n) {
-    PB_TRY(m->gpcg.alloc(6 * (size_t)n));
-    PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 6 * (size_t)n * sizeof(double), m->stream));
+  if (m->gpcg.n < 8 * (size_t)n) {
+    PB_TRY(m->gpcg.alloc(8 * (size_t)n));
+    PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 8 * (size_t)n * sizeof(double), m->stream));
   }
   PB_TRY(jacobi(m, m->gdiag.p));
   PB_TRY(prepare_block_precond(m, dense));
@@ -641,9 +691,9 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
   const bool flexible = precond != PBFB_PRECOND_JACOBI;
   if (flexible) {
     PB_TRY(ensure(m->gZ, (size_t)restart * n));
-    if (m->gpcg.n < 6 * (size_t)n) {
-      PB_TRY(m->gpcg.alloc(6 * (size_t)n));
-      PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 6 * (size_t)n * sizeof(double), m->stream));
+    if (m->gpcg.n < 8 * (size_t)n) {
+      PB_TRY(m->gpcg.alloc(8 * (size_t)n));
+      PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 8 * (size_t)n * sizeof(double), m->stream));
     }
   }
   PB_TRY(ensure(m->gV, (size_t)(restart + 1) * n));

@@ -396,12 +396,47 @@ def double_helix(n_bp=24, nu=45, layers=16, seed=3000, n_interior=1500, ionic=0.
     dirs /= np.linalg.norm(dirs, axis=1)[:, None]
     lo, h, rho = _gaussian_density_grid(cen, rad, grid, 6.0)
     r_in = _close_crevices(_outermost_crossing(dirs, lo, h, rho), tri)
+    r_in = _enclose_charges(cen, dirs, tri, r_in, margin=0.3)
     kappa = kappa_from_ionic_strength(ionic, eps_out, T)
     R_out = float(r_in.max()) + 3.0 / kappa
     xyz, tets, gm, gs = _radial_shell(dirs, tri, r_in, np.full_like(r_in, R_out), layers)
     _check_charges_inside(cen, xyz, gm, dirs, tri, r_in, margin=0.3)
     return Case(f"double_helix_{n_bp}bp_nu{nu}_L{layers}", xyz, tets, gm, gs, cen, q,
                 eps_in, eps_out, kappa, T)
+
+
+def _ray_triangle_of(d, dirs, tri):
+    """Index of the ray triangle containing each unit direction d (first match)."""
+    A, B, C = dirs[tri[:, 0]], dirs[tri[:, 1]], dirs[tri[:, 2]]
+    nAB, nBC, nCA = np.cross(A, B), np.cross(B, C), np.cross(C, A)
+    out = np.empty(d.shape[0], dtype=np.int64)
+    for k in range(0, d.shape[0], 64):
+        dk = d[k:k + 64]
+        inside = (dk @ nAB.T >= -1e-12) & (dk @ nBC.T >= -1e-12) & (dk @ nCA.T >= -1e-12)
+        if not inside.any(axis=1).all():
+            raise ValueError("a charge direction is in no ray triangle")
+        out[k:k + 64] = np.argmax(inside, axis=1)
+    return out
+
+
+def _enclose_charges(pts, dirs, tri, r, margin, iters=50):
+    """Raise the ray radii of the triangles that would cut a charge off (a coarse triangle over an
+    atom's bump) until every charge lies ``margin`` inside the surface along its ray."""
+    rho = np.linalg.norm(pts, axis=1)
+    d = pts / rho[:, None]
+    t = _ray_triangle_of(d, dirs, tri)
+    r = r.copy()
+    for _ in range(iters):
+        P = r[tri[t]][:, :, None] * dirs[tri[t]]                   # (nq, 3, 3) triangle corners
+        n = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+        t_surf = np.einsum('ij,ij->i', n, P[:, 0]) / np.einsum('ij,ij->i', n, d)
+        short = rho + margin - t_surf
+        if not (short > 0).any():
+            break
+        for q in np.nonzero(short > 0)[0]:
+            f = tri[t[q]]
+            r[f] = np.maximum(r[f], r[f] * (rho[q] + margin + 1e-3) / t_surf[q])
+    return r
 
 
 def _check_charges_inside(pts, xyz, gm, dirs, tri, r_in, margin):

@@ -147,7 +147,7 @@ def load():
         "pbfb_energy": (I, [P, P, P, P]),
         "pbfb_profile": (I, [P, I, I, P]),
         "pbfb_set_tuning": (I, [P, I, I, I]),
-        "pbfb_server_create": (I, [I, ctypes.c_uint64, I, ctypes.POINTER(P)]),
+        "pbfb_server_create": (I, [I, ctypes.c_uint64, I, I, ctypes.POINTER(P)]),
         "pbfb_server_submit": (I, [P, ctypes.POINTER(Request)]),
         "pbfb_server_poll": (I, [P, P, I, I, ctypes.POINTER(ctypes.c_int)]),
         "pbfb_server_stats": (I, [P, P]),
@@ -365,9 +365,10 @@ class Mesh:
 class Server:
     """Owner of a pbfb_server: queued requests, HBM-budget admission, concurrent solves."""
 
-    def __init__(self, budget_bytes, max_inflight=4, device=0):
+    def __init__(self, budget_bytes, max_inflight=4, device=0, cached_meshes=0):
         h = ctypes.c_void_p()
-        _check(load().pbfb_server_create(device, int(budget_bytes), max_inflight, ctypes.byref(h)))
+        _check(load().pbfb_server_create(device, int(budget_bytes), max_inflight, int(cached_meshes),
+                                         ctypes.byref(h)))
         self.h = h
 
     def submit(self, case, rid, eps_in=None, eps_out=None, kappa=None, T=None, opts=None):
@@ -390,9 +391,10 @@ class Server:
         return [buf[i].as_dict() for i in range(n.value)]
 
     def stats(self):
-        st = np.zeros(6)
+        st = np.zeros(8)
         _check(load().pbfb_server_stats(self.h, _ptr(st)))
-        return dict(submitted=st[0], completed=st[1], queued=st[2], in_use=st[3], peak=st[4], budget=st[5])
+        return dict(submitted=st[0], completed=st[1], queued=st[2], in_use=st[3], peak=st[4], budget=st[5],
+                    mesh_hits=st[6], resident_meshes=st[7])
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -125,3 +125,41 @@ def test_solve_batch_matches_individual_solves():
         r1 = pbfb.solve_batch([m], [(c.eps_in, c.eps_out, c.kappa, c.T, None)], 1)[0]
         assert r["status"] == 0 and r1["total"] == r["total"] and r1["gmres"] == r["gmres"]
         m.close()
+
+
+def test_resident_meshes_reused_with_identical_results():
+    """A server that keeps meshes resident serves repeated geometries without rebuilding them;
+    every result equals the one of a server that builds each mesh afresh."""
+    from paper_2511_21713_gb300 import inputs, pbfb
+    base = _mix()
+    cases = []
+    for k in range(8):                      # three geometries, new charges and salt each time
+        c = base[k % 3]
+        q, z = inputs.ball_charges(2 + k, 3.0, 1 + k // 2, 500 + k)
+        cases.append(inputs.Case(f"rep{k}", c.xyz, c.tets, c.gm_tris, c.gs_tris, q, z, c.eps_in,
+                                 c.eps_out, inputs.kappa_from_ionic_strength((0.05, 0.3)[k % 2], 80.0, 300.0),
+                                 c.T))
+    fresh = pbfb.Server(budget_bytes=8 << 30, max_inflight=2)
+    for i, c in enumerate(cases):
+        fresh.submit(c, i)
+    ref = _collect(fresh, len(cases))
+    fresh.close()
+    sv = pbfb.Server(budget_bytes=8 << 30, max_inflight=2, cached_meshes=2)
+    for i, c in enumerate(cases):
+        sv.submit(c, i)
+    got = _collect(sv, len(cases))
+    st = sv.stats()
+    sv.close()
+    assert st["mesh_hits"] >= 3 and st["resident_meshes"] <= 2
+    for i in range(len(cases)):
+        assert got[i]["status"] == 0
+        assert got[i]["total"] == ref[i]["total"] and got[i]["gmres"] == ref[i]["gmres"]
+    # a budget of about two meshes: resident meshes are evicted to admit new geometries
+    sv = pbfb.Server(budget_bytes=150 << 20, max_inflight=2, cached_meshes=8)
+    for i, c in enumerate(cases):
+        sv.submit(c, i)
+    got = _collect(sv, len(cases))
+    st = sv.stats()
+    sv.close()
+    assert all(got[i]["status"] == 0 and got[i]["total"] == ref[i]["total"] for i in range(len(cases)))
+    assert st["peak"] <= 150 << 20
