@@ -362,7 +362,10 @@ int pbfb_server_destroy(pbfb_server* h) {
     sv->cv_work.notify_all();
     for (auto& t : sv->workers) t.join();
     for (auto* r : sv->queue) delete r;
+    // the workers have finished every solve and destroyed their streams: the resident meshes
+    // still name one of those streams, so they are released on the legacy stream instead
     for (auto* c : sv->cache) {
+      c->m->stream = nullptr;
       pbfb::mesh_destroy(c->m);
       delete c;
     }

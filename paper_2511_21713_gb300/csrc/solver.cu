@@ -1299,6 +1299,7 @@ void mesh_destroy(Mesh* m) {
   timer_flush(m->t_nbodyff);
   timer_flush(m->t_spmv);
   timer_flush(m->t_elem);
+  timer_flush(m->t_dense);
   if (m->pinned) cudaFreeHost(m->pinned);
   delete m;
 }
