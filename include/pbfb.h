@@ -110,9 +110,10 @@ typedef struct pbfb_newton_opts {
                            |d omega| < 0.05 (Sec. 3.5); 0 = start from omega0_first */
   int omega_search;     /* 1: automatic omega; 0: constant omega0_first / omega0_rest */
   int precond;          /* PBFB_PRECOND_JACOBI: diagonal of the coupled operator;
-                           PBFB_PRECOND_BLOCK: flexible GMRES whose preconditioner runs
-                           inner_iters Jacobi-PCG iterations on the FEM block A + J and
-                           the diagonal on the surface rows;
+                           PBFB_PRECOND_BLOCK: flexible GMRES with a block-triangular
+                           preconditioner: the diagonal on the surface rows, then
+                           inner_iters Jacobi-PCG iterations on the FEM block A + J for
+                           the FEM right-hand side minus its coupling to those rows;
                            PBFB_PRECOND_BLOCK_DENSE (default): the same FEM block, and on
                            the surface rows the inverses of the dense float32 single-layer
                            matrices (-V_L on Gamma_m, V_Y on Gamma_s; see

@@ -364,6 +364,19 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int
   }
 }
 
+// FEM rows of the block-triangular preconditioner: out_i = v_i - sum over the coupling columns
+// (>= nv: the surface unknowns) of S_ij z_j, with z_j already preconditioned; columns are sorted,
+// so the coupling entries close each row
+__global__ void k_couple_sub(int nv, const int* __restrict__ ptr, const int* __restrict__ col,
+                             const double* __restrict__ val, const double* __restrict__ v,
+                             const double* __restrict__ z, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv) return;
+  double acc = 0.0;
+  for (int k = ptr[i + 1] - 1; k >= ptr[i] && col[k] >= nv; --k) acc += val[k] * z[col[k]];
+  out[i] = v[i] - acc;
+}
+
 // surface rows of the block preconditioner: z = dinv v
 __global__ void k_scale_rows(int r0, int r1, const double* __restrict__ v, const double* __restrict__ dinv,
                              double* __restrict__ z) {
@@ -512,8 +525,10 @@ static int jacobi(Mesh* m, double* dinv) {
 
 // ------------------------------------------------------------------ GMRES
 
-// Block preconditioner z = P(v): inner_iters Jacobi-PCG iterations on (A + J) z_u = v_u from
-// z_u = 0, and z = diag^-1 v on the surface rows.  Deterministic (fixed reductions, fixed count).
+// Block preconditioner z = P(v), block triangular: the surface rows first (z = diag^-1 v, or the
+// dense single-layer inverses), then inner_iters Jacobi-PCG iterations from z_u = 0 on
+// (A + J) z_u = v_u - S_{u,lam} z_lam, the FEM rows' right-hand side minus their (sparse, mass)
+// coupling to the surface unknowns just computed.  Deterministic (fixed reductions, fixed count).
 // FEM block of the preconditioner: A + J plus the Robin term eps_s (kappa + 1/R) M_s on Gamma_s
 // (the constant mode of the exterior Dirichlet-to-Neumann map of a sphere of Gamma_s's area),
 // which keeps it positive definite when J = 0.
@@ -581,10 +596,14 @@ static int block_precond_launches(Mesh* m, const double* v, double* z, int inner
   double* pz = pb + 2 * (size_t)n;
   double* pp = pb + 3 * (size_t)n;
   double* pq = pb + 4 * (size_t)n;
+  double* vu = pb + 8 * (size_t)n;   // FEM right-hand side minus the coupling to z's surface part
   double* part = m->gpart.p;
   double* sc = m->scal.p + 5000;     // [0] pq, [1 + k] rz_k
   const double* dinv = m->pdinv.p;
-  k_pcg_init<<<nb, PCG_T, 0, m->stream>>>(nv, v, dinv, z, pr, pz, pp, part);
+  PB_TRY(surface_rows_precond(m, v, z));
+  k_couple_sub<<<blocks_for(nv, 256), 256, 0, m->stream>>>(nv, m->s_ptr.p, m->s_col.p, m->s_val.p, v, z, vu);
+  PB_LAUNCHED(m);
+  k_pcg_init<<<nb, PCG_T, 0, m->stream>>>(nv, vu, dinv, z, pr, pz, pp, part);
   PB_LAUNCHED(m);
   k_sum_to<<<1, 32, 0, m->stream>>>(part, nb, sc + 1);
   PB_LAUNCHED(m);
@@ -600,7 +619,7 @@ static int block_precond_launches(Mesh* m, const double* v, double* z, int inner
     k_pcg_direction<<<nb, PCG_T, 0, m->stream>>>(nv, sc + 1 + k, sc + 2 + k, pz, pp);
     PB_LAUNCHED(m);
   }
-  return surface_rows_precond(m, v, z);
+  return PBFB_OK;
 }
 
 static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
@@ -614,23 +633,28 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
   double* part = m->gpart.p;
   const double* dinv = m->pdinv.p;
   if (m->coop_blocks > 0) {
+    // surface rows first, then the FEM block on v_u minus the coupling to them
+    PB_TRY(surface_rows_precond(m, v, z));
+    double* vu = pb + 8 * (size_t)n;
+    k_couple_sub<<<blocks_for(nv, 256), 256, 0, m->stream>>>(nv, m->s_ptr.p, m->s_col.p, m->s_val.p, v, z, vu);
+    PB_LAUNCHED(m);
     int nbc = m->coop_blocks, iters = inner_iters, nvv = nv;
     const int* sp = m->s_ptr.p;
     const int* sc2 = m->s_col.p;
     const double* pv = m->pval.p;
     double* pw = pb + 5 * (size_t)n;
-    void* args[] = {&nvv, &iters, &sp, &sc2, &pv, (void*)&v, (void*)&dinv, &z, &pr, &pz, &pp, &pq, &pw, &part};
+    void* args[] = {&nvv, &iters, &sp, &sc2, &pv, (void*)&vu, (void*)&dinv, &z, &pr, &pz, &pp, &pq, &pw, &part};
     PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_coop, dim3(nbc), dim3(PCG_T), args, 0, m->stream));
     PB_LAUNCHED(m);
-    return surface_rows_precond(m, v, z);
+    return PBFB_OK;
   }
   // the ~5 inner_iters + 4 small launches replayed as one CUDA graph on fixed buffers
   double* gin = pb + 6 * (size_t)n;
   double* gout = pb + 7 * (size_t)n;
-  const void* key[9] = {m->gpcg.p, m->gpart.p, m->pval.p, m->pdinv.p, m->scal.p, m->gdiag.p,
+  const void* key[9] = {m->gpcg.p, m->gpart.p, m->pval.p, m->pdinv.p, m->s_val.p, m->gdiag.p,
                         m->dense_m ? (const void*)m->sm.vinv.p : nullptr,
                         m->dense_s ? (const void*)m->ss.vinv.p : nullptr, m->s_ptr.p};
-  if (!m->pcg_graph_off && m->gpcg.n >= 8 * (size_t)n &&
+  if (!m->pcg_graph_off && m->gpcg.n >= 9 * (size_t)n &&
       (!m->pcg_graph || m->pcg_graph_iters != inner_iters || !std::equal(key, key + 9, m->pcg_graph_key))) {
     if (m->pcg_graph) cudaGraphExecDestroy(m->pcg_graph);
     m->pcg_graph = nullptr;
@@ -667,9 +691,9 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
 int block_precond_apply(Mesh* m, const double* v, double* z, int inner_iters, bool dense) {
   const int n = m->n;
   PB_TRY(ensure(m->gdiag, n));
-  if (m->gpcg.n < 8 * (size_t)n) {
-    PB_TRY(m->gpcg.alloc(8 * (size_t)n));
-    PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 8 * (size_t)n * sizeof(double), m->stream));
+  if (m->gpcg.n < 9 * (size_t)n) {
+    PB_TRY(m->gpcg.alloc(9 * (size_t)n));
+    PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 9 * (size_t)n * sizeof(double), m->stream));
   }
   PB_TRY(jacobi(m, m->gdiag.p));
   PB_TRY(prepare_block_precond(m, dense));
@@ -691,9 +715,9 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
   const bool flexible = precond != PBFB_PRECOND_JACOBI;
   if (flexible) {
     PB_TRY(ensure(m->gZ, (size_t)restart * n));
-    if (m->gpcg.n < 8 * (size_t)n) {
-      PB_TRY(m->gpcg.alloc(8 * (size_t)n));
-      PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 8 * (size_t)n * sizeof(double), m->stream));
+    if (m->gpcg.n < 9 * (size_t)n) {
+      PB_TRY(m->gpcg.alloc(9 * (size_t)n));
+      PB_CUDA(cudaMemsetAsync(m->gpcg.p, 0, 9 * (size_t)n * sizeof(double), m->stream));
     }
   }
   PB_TRY(ensure(m->gV, (size_t)(restart + 1) * n));
