@@ -54,8 +54,9 @@ def workload_config(case, precision):
         "T_K": case.T, "precision": precision,
         "newton": "T3 first iteration, automatic omega (Newton on f_d), L_e 0.35, Tol_omega 0.1, "
                   "Tol_GR0 1e-3 -> Tol_GR 1e-6, Tol_NL 1e-3",
-        "preconditioner": "flexible GMRES; 20 Jacobi-PCG iterations on the FEM block, dense float32 "
-                          "single-layer inverses on the surface rows (built once per mesh and kappa)",
+        "preconditioner": "flexible GMRES, block-triangular: dense float32 single-layer inverses on the "
+                          "surface rows (built once per mesh and kappa), then 30 Jacobi-PCG iterations on "
+                          "the FEM block",
         "l2": "flushed between timed steps (256 MiB write)",
     }
 

@@ -76,7 +76,7 @@ typedef struct pbfb_mesh pbfb_mesh;
  * Newton configuration (Appendix B: L_e = 0.35, Tol_omega = 0.1,
  * Tol_GR0 = 1e-3, Tol_GR = 1e-6, Tol_NL = 1e-3; omega_0 = 2 for the T3
  * iteration and 1 afterwards, Sec. 3.3), with the block preconditioner with
- * dense single-layer inverses on the surface rows (20 inner iterations on the
+ * dense single-layer inverses on the surface rows (30 inner iterations on the
  * FEM block; the paper does not state its preconditioner).
  * In the PBFB_MIXED precision the GMRES operator (and the omega-search
  * direction p = -Acal(0) Delta, whose f_d root is needed only to Tol_omega)

@@ -1376,7 +1376,7 @@ void pbfb_default_opts(pbfb_newton_opts* o) {
   o->omega_warm_start = 0;
   o->omega_search = 1;
   o->precond = PBFB_PRECOND_BLOCK_DENSE;
-  o->inner_iters = 20;
+  o->inner_iters = 30;
 }
 
 const char* pbfb_last_error(void) { return pbfb::last_error(); }
