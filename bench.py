@@ -37,6 +37,10 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "multi_charge_sphere.json")
 # DRAM bytes (read + write) per launch of the packed far-field kernel on this workload, from its
 # ncu capture (profiles/k_nbody_f32x2_multi_charge_sphere.md; source records read once)
 NBODY_TRAFFIC = 2311424.0
+# float32 flops (FMA = 2) per ordered point pair of the mutual float-float kernel and its DRAM bytes
+# per launch, from its ncu capture (profiles/k_nbody_ffm_multi_charge_sphere.md)
+FF_FLOP_PAIR = {"laplace": 132.1, "yukawa": 191.3}
+FF_TRAFFIC = 12.25e6
 
 
 def workload_config(case, precision):
@@ -279,23 +283,47 @@ def run_pbfb(args):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_val = ws * len(e2e_ms) / (sum(e2e_ms) / 1e3) if e2e_ms else None
 
-    # roofline of the dominant kernel (the far-field N-body) from its live CUDA-event timing
-    # the float32 far field (GMRES operator) in the mixed precision; float64 otherwise
+    # roofline of the dominant kernel from its live CUDA-event timing (in the timed region): in the
+    # mixed precision the float32 far field of the GMRES operator or the float-float far field of
+    # the Newton residual, whichever takes the larger share of the step; float64 otherwise
+    peak32 = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    cands = []
     if prec == pbfb.MIXED:
-        launches, kms, pairs = prof["nbody_launches"], prof["nbody_ms"], prof["nbody_pairs"]
-        flops = prof["nbody_flops"]
-        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        peak_note = "fp32 non-tensor: 152 SM x 128 lanes x 2 flop x 2070 MHz (18 flop/Laplace pair, 24/Yukawa)"
-        kname = "k_nbody_f32x2 (packed, 2 targets per thread)"
+        l32, ms32 = prof["nbody_launches"], prof["nbody_ms"]
+        if l32:
+            cands.append(dict(kernel="k_nbody_f32x2 (float32 far field of the GMRES operator, packed, 2 targets "
+                                     "per thread)", launches=l32, ms=ms32, pairs=prof["nbody_pairs"],
+                              flops=prof["nbody_flops"], peak=peak32, traffic=NBODY_TRAFFIC,
+                              peak_basis="fp32 non-tensor: 152 SM x 128 lanes x 2 flop x 2070 MHz; "
+                                         "18 flop per Laplace pair, 24 per Yukawa pair"))
+        lff, msff = prof["nbodyff_launches"], prof["nbodyff_ms"]
+        if lff:
+            cands.append(dict(kernel="k_nbody_ffm (float-float far field of the Newton residual, mutual pairs)",
+                              launches=lff, ms=msff, pairs=prof["nbodyff_pairs"],
+                              flops=prof["nbodyff_pairs"] * 0.5 * (FF_FLOP_PAIR["laplace"] + FF_FLOP_PAIR["yukawa"]),
+                              peak=peak32, traffic=FF_TRAFFIC,
+                              peak_basis="fp32 non-tensor: 152 SM x 128 lanes x 2 flop x 2070 MHz; float32 flops "
+                                         "of the float-float pair evaluation per ordered pair (FMA = 2), "
+                                         "%.1f Laplace / %.1f Yukawa, counted by ncu"
+                                         % (FF_FLOP_PAIR["laplace"], FF_FLOP_PAIR["yukawa"])))
     else:
-        launches, kms, pairs = prof["nbody64_launches"], prof["nbody64_ms"], prof["nbody64_pairs"]
-        flops = pairs * 0.5 * (FLOP_PAIR["laplace"] + FLOP_PAIR["yukawa"])
-        peak = 1.25
-        peak_note = "fp64 nominal 1.25 TFLOP/s"
-        kname = "k_nbody_f64"
-    pairs_per_launch = pairs / max(launches, 1)
-    avg_ms = kms / max(launches, 1)
-    achieved = (flops / max(launches, 1)) / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else None
+        l64, ms64 = prof["nbody64_launches"], prof["nbody64_ms"]
+        cands.append(dict(kernel="k_nbody_f64", launches=l64, ms=ms64, pairs=prof["nbody64_pairs"],
+                          flops=prof["nbody64_pairs"] * 0.5 * (FLOP_PAIR["laplace"] + FLOP_PAIR["yukawa"]),
+                          peak=1.25, traffic=None, peak_basis="fp64 nominal 1.25 TFLOP/s"))
+
+    def roofline_of(c):
+        launches = max(c["launches"], 1)
+        avg_ms = c["ms"] / launches
+        achieved = (c["flops"] / launches) / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else None
+        return {"bound": "alu", "kernel": c["kernel"], "achieved": achieved, "peak": c["peak"],
+                "unit": "TFLOP/s", "frac": (achieved / c["peak"]) if achieved else None,
+                "traffic": c["traffic"] if args.workload == "multi_charge_sphere" else None,
+                "peak_basis": c["peak_basis"], "avg_launch_ms": avg_ms,
+                "pairs_per_launch": c["pairs"] / launches, "launches": c["launches"],
+                "share_of_step": c["ms"] / total_ms if total_ms else None}
+
+    rooflines = sorted((roofline_of(c) for c in cands), key=lambda r: -(r["share_of_step"] or 0))
 
     out = {
         "metric": METRIC, "value": ws * args.steps / (total_ms_max / 1e3), "unit": "solves/s",
@@ -309,19 +337,8 @@ def run_pbfb(args):
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(prof["launches"]),
-        "roofline": {"bound": "alu", "kernel": f"far-field N-body ({kname})",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None,
-                     # dram__bytes_read + write per launch from the ncu capture in
-                     # profiles/k_nbody_f32x2_multi_charge_sphere.md (source records read once)
-                     "traffic": (NBODY_TRAFFIC if (prec == pbfb.MIXED and args.workload == "multi_charge_sphere")
-                                 else None),
-                     "peak_basis": peak_note, "avg_launch_ms": avg_ms,
-                     "pairs_per_launch": pairs_per_launch, "launches": launches,
-                     "share_of_step": kms / total_ms if total_ms else None,
-                     "residual_farfield_share": (prof["nbody64_ms"] + prof["nbodyff_ms"]) / total_ms if total_ms else None,
-                     "residual_farfield_ms_per_launch": ((prof["nbodyff_ms"] / prof["nbodyff_launches"])
-                                                         if prof["nbodyff_launches"] else None)},
+        "roofline": rooflines[0],
+        "roofline_next": rooflines[1] if len(rooflines) > 1 else None,
         "clocks": clk,
         "autotune": {"shapes": tuned, "best_ms": tuned_ms, "seconds": tune_s},
         "setup": {"mesh_create_and_charges_ms": create_ms, "first_solve_ms": first_ms,
