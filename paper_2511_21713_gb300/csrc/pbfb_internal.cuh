@@ -170,6 +170,7 @@ struct Mesh {
   // GMRES workspace
   int gm_restart = 0;
   DBuf<double> gV, gw, gz, gr, gdiag, gh, gpart, gtmp;
+  bool gw_is_ax = false;    // after gmres: gw holds Acal x for the returned x (its final true residual)
   DBuf<double> gZ;          // flexible GMRES: preconditioned basis (restart x n)
   DBuf<double> gpcg;        // inner PCG vectors (6 x n), then the fixed input and output of the
                             // captured preconditioner graph (n each)

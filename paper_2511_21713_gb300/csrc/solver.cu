@@ -748,6 +748,7 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
   PB_TRY(dot(m, b, b, n, &bn2));
   double bn = std::sqrt(bn2);
   PB_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), m->stream));
+  m->gw_is_ax = false;
   if (iters_out) *iters_out = 0;
   if (rel_out) *rel_out = 0.0;
   if (!(bn > 0)) {
@@ -843,8 +844,9 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
       k_update_solution<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, mk, V, ydev, m->gdiag.p, x);
     }
     PB_LAUNCHED(m);
-    // true residual
+    // true residual (w = Acal x stays available to the caller)
     PB_TRY(apply(m, x, w));
+    m->gw_is_ax = true;
     PB_TRY(launch_axpby(m, n, 1.0, b, -1.0, w, r));
     double rn2;
     PB_TRY(dot(m, r, r, n, &rn2));
@@ -1206,10 +1208,20 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
       // R_e rule (Appendix B): keep omega while the error still falls by R_e per step
       om = om_last;
     } else {
-      // p = -Acal(0) Delta with the GMRES operator (the root of f_d is needed only to Tol_omega)
-      PB_TRY(clear_jacobian(m));
-      PB_TRY(apply(m, m->du.p, m->pvec.p));
-      PB_TRY(launch_axpby(m, n, -1.0, m->pvec.p, 0.0, nullptr, m->pvec.p));
+      // p = -Acal(0) Delta with the GMRES operator (the root of f_d is needed only to Tol_omega):
+      // GMRES's final true residual left Acal(J) Delta in gw, and Acal(0) Delta differs from it
+      // only by the Jacobian's sparse rows, J Delta = (S_J - S_0) Delta
+      if (m->gw_is_ax) {
+        PB_TRY(launch_csr_spmv(m, n, m->s_ptr.p, m->s_col.p, m->s_val.p, m->du.p, m->pvec.p, false));
+        PB_TRY(launch_csr_spmv(m, n, m->s_ptr.p, m->s_col.p, m->s_base.p, m->du.p, m->tmp.p, false));
+        PB_TRY(launch_axpby(m, n, 1.0, m->pvec.p, -1.0, m->tmp.p, m->pvec.p));
+        PB_TRY(launch_axpby(m, n, 1.0, m->pvec.p, -1.0, m->gw.p, m->pvec.p));
+        PB_TRY(clear_jacobian(m));
+      } else {
+        PB_TRY(clear_jacobian(m));
+        PB_TRY(apply(m, m->du.p, m->pvec.p));
+        PB_TRY(launch_axpby(m, n, -1.0, m->pvec.p, 0.0, nullptr, m->pvec.p));
+      }
       double om0 = k == 0 ? o.omega0_first : o.omega0_rest;
       int warm_evals = 0;
       if (k == 0 && o.omega_warm_start && !picard)
