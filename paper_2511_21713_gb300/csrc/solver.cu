@@ -760,7 +760,14 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
   }
   PB_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
   std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), y(restart);
-  int its = 0;
+  std::vector<double> Hraw((size_t)(restart + 1) * restart), u(restart + 1);  // Hessenberg before rotations
+  if (m->gones.n < (size_t)n) {
+    PB_TRY(m->gones.alloc(n));
+    std::vector<double> ones(n, 1.0);
+    PB_CUDA(cudaMemcpyAsync(m->gones.p, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    PB_CUDA(cudaStreamSynchronize(m->stream));
+  }
+  int its = 0, cycle = 0;
   double rel = 1.0;
   double beta = bn;
   while (true) {
@@ -808,6 +815,7 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
       double* col = &H[(size_t)k * (restart + 1)];
       for (int i = 0; i <= k; ++i) col[i] = H1[i] + H2[i];
       col[k + 1] = hn;
+      std::copy(col, col + k + 2, &Hraw[(size_t)k * (restart + 1)]);
       for (int i = 0; i < k; ++i) {
         double t = cs[i] * col[i] + sn[i] * col[i + 1];
         col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
@@ -844,7 +852,31 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
       k_update_solution<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, mk, V, ydev, m->gdiag.p, x);
     }
     PB_LAUNCHED(m);
-    // true residual (w = Acal x stays available to the caller)
+    if (cycle == 0 && (rel <= tol || its >= maxit)) {
+      // done in the first cycle: the Arnoldi relation Acal Z_k = V_{k+1} Hbar_k (flexible) or
+      // Acal D V_k = V_{k+1} Hbar_k gives Acal x = V_{k+1} (Hbar_k y) without applying Acal, and the
+      // residual norm is the least-squares one, |g_{k+1}| (the operator is deterministic and CGS2
+      // keeps the basis orthogonal)
+      for (int i = 0; i <= mk; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < mk; ++j)
+          if (i <= j + 1) t += Hraw[(size_t)j * (restart + 1) + i] * y[j];
+        u[i] = t;
+      }
+      // staged through the second half of the pinned buffer: the first half may still be in flight
+      std::memcpy(m->pinned + 2048, u.data(), (mk + 1) * sizeof(double));
+      double* udev = ydev;  // stream order: the x update above has consumed y already
+      PB_CUDA(cudaMemcpyAsync(udev, m->pinned + 2048, (mk + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                              m->stream));
+      PB_CUDA(cudaMemsetAsync(w, 0, n * sizeof(double), m->stream));
+      k_update_solution<<<blocks_for(n, 256), 256, 0, m->stream>>>(n, mk + 1, V, udev, m->gones.p, w);
+      PB_LAUNCHED(m);
+      PB_CUDA(cudaStreamSynchronize(m->stream));  // both pinned staging areas are reused later
+      m->gw_is_ax = true;
+      break;
+    }
+    ++cycle;
+    // restart: true residual (w = Acal x stays available to the caller)
     PB_TRY(apply(m, x, w));
     m->gw_is_ax = true;
     PB_TRY(launch_axpby(m, n, 1.0, b, -1.0, w, r));
