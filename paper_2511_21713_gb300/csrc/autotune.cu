@@ -122,7 +122,7 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
     }
   // float-float far field
   for (int kind : {1, 2, 3})
-    for (int bps : {4, 8, 16}) {
+    for (int bps : {0, 4, 8, 16}) {
       pbfb_tuning t = best;
       t.ff_kernel = kind;
       t.ff_blocks_per_sm = bps;

@@ -848,10 +848,11 @@ __device__ __forceinline__ ff ff_sq(ff a) {
   e = __fmaf_rn(__fadd_rn(a.h, a.h), a.l, e);
   return fast_two_sum(p, e);
 }
-// difference of two float-float coordinates
+// difference of two float-float coordinates whose high parts lie on a common grid q, fine enough
+// that xh - yh is exact: (xh - yh) + (xl - yl) with |xl - yl| <= q <= |xh - yh| unless xh = yh,
+// so a FastTwoSum renormalises it
 __device__ __forceinline__ ff ff_diff(float xh, float xl, float yh, float yl) {
-  ff s = two_sum(xh, -yh);
-  return fast_two_sum(s.h, __fadd_rn(s.l, __fsub_rn(xl, yl)));
+  return fast_two_sum(__fsub_rn(xh, yh), __fsub_rn(xl, yl));
 }
 // a.x + b.y + c.z for float-float vectors
 __device__ __forceinline__ ff ff_dot3(ff a0, ff a1, ff a2, ff b0, ff b1, ff b2) {
@@ -893,12 +894,14 @@ __device__ __forceinline__ ff ff_expm(ff x, const float2* __restrict__ tab_hi) {
 }
 
 // Float-float sources: 4 float4 per point: (y hi, s hi), (y lo, s lo), (m hi, 0), (m lo, 0),
-// with y relative to the surface centre, s = cs w lam_h, m = cd w u_h n.
+// with y relative to the surface centre, s = cs w lam_h, m = cd w u_h n.  The coordinates' high
+// parts lie on `grid` (a power of 2) with every difference of two of them exact in float32,
+// the low parts are the remainders (|y lo| <= grid / 2).
 __global__ void k_sources_ff(int nt, const int* __restrict__ tri, const int* __restrict__ vmap,
                              const double* __restrict__ lam, const double* __restrict__ u, int u_local,
                              const double* __restrict__ qw, const double* __restrict__ nrm,
                              const double* __restrict__ qx, double cx, double cy, double cz, double cs, double cd,
-                             float4* __restrict__ src, float4* __restrict__ tgt) {
+                             double grid, float4* __restrict__ src, float4* __restrict__ tgt) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int nq = QS * nt;
   if (j >= nq) return;
@@ -916,8 +919,9 @@ __global__ void k_sources_ff(int nt, const int* __restrict__ tri, const int* __r
   double mm[3] = {mu * nrm[t], mu * nrm[nt + t], mu * nrm[2 * nt + t]};
   float yh[3], yl[3], mh[3], ml[3];
   for (int d = 0; d < 3; ++d) {
-    yh[d] = (float)y[d];
-    yl[d] = (float)(y[d] - (double)yh[d]);
+    const double yq = rint(y[d] / grid) * grid;  // on the grid: exact in float32
+    yh[d] = (float)yq;
+    yl[d] = (float)(y[d] - yq);
     mh[d] = (float)mm[d];
     ml[d] = (float)(mm[d] - (double)mh[d]);
   }
@@ -1036,8 +1040,7 @@ __device__ __forceinline__ ffv v_sq(ffv a) {
   return v_fast_two_sum(p, e);
 }
 __device__ __forceinline__ ffv v_diff(float2 xh, float2 xl, float2 yh, float2 yl) {
-  ffv s = v_two_sum(xh, vneg(yh));
-  return v_fast_two_sum(s.h, vadd(s.l, vsub(xl, yl)));
+  return v_fast_two_sum(vsub(xh, yh), vsub(xl, yl));
 }
 __device__ __forceinline__ ffv v_dot3(ffv a0, ffv a1, ffv a2, ffv b0, ffv b1, ffv b2) {
   float2 p0 = vmul(a0.h, b0.h), p1 = vmul(a1.h, b1.h), p2 = vmul(a2.h, b2.h);
@@ -1283,10 +1286,13 @@ __global__ void __launch_bounds__(MT) k_nbody_ffm(int nq, int G, const float4* _
             const int jj = base + ((lane + k) & 31);
             ff ta, tb;
             ff_mutual<YUK>(ah, al, amh, aml, sb[0][jj], sb[1][jj], sb[2][jj], sb[3][jj], kap, tab, ta, tb);
-            acc = ff_add(acc, ta);
+            // running sums kept as (high, low) with the low parts and TwoSum errors added plainly
+            // (at most 128 terms per tile pair, converted to float64 at its end)
+            const ff sa = two_sum(acc.h, ta.h);
+            acc = ff{sa.h, __fadd_rn(acc.l, __fadd_rn(sa.l, ta.l))};
             const float2 o = acc_j[jj];
-            const ff nb = ff_add(ff{o.x, o.y}, tb);
-            acc_j[jj] = make_float2(nb.h, nb.l);
+            const ff sj = two_sum(o.x, tb.h);
+            acc_j[jj] = make_float2(sj.h, __fadd_rn(o.y, __fadd_rn(sj.l, tb.l)));
             __syncwarp();
           }
           __syncthreads();
@@ -1636,7 +1642,7 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
   if (s->fftgt.n < 2 * (size_t)nq) PB_TRY(s->fftgt.alloc(2 * (size_t)nq));
   k_sources_ff<<<blocks_for(nq, 256), 256, 0, m->stream>>>(
       s->nt, s->tri.p, s->vmap.p, cs != 0.0 ? lam : nullptr, cd != 0.0 ? x : nullptr, u_local, s->qw.p, s->nrm.p,
-      s->qx.p, s->ctr[0], s->ctr[1], s->ctr[2], cs * INV4PI, cd * INV4PI, s->ffsrc.p, s->fftgt.p);
+      s->qx.p, s->ctr[0], s->ctr[1], s->ctr[2], cs * INV4PI, cd * INV4PI, s->ff_q, s->ffsrc.p, s->fftgt.p);
   PB_LAUNCHED(m);
   cudaEvent_t ev;
   timer_begin(m, m->t_nbodyff, &ev);
@@ -1647,18 +1653,31 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
   const int bps = m->tune_ff_bps > 0 ? m->tune_ff_bps : 8;  // GB300 sweep: 8 blocks per SM of source splits
   const float kh = (float)kappa, kl = (float)(kappa - (double)kh);
   if (kind == 3) {
-    // tile groups: G (G + 1) / 2 blocks, about bps per SM; 2 G + 1 partial rows of val
+    // tile groups: G (G + 1) / 2 blocks; built-in: the largest G whose blocks fit in one wave of
+    // resident blocks (the kernel is issue-bound: a partial second wave or an underfilled first one
+    // leaves issue slots idle); tuned: about bps blocks per SM.  2 G + 1 partial rows of val.
     const int nT = blocks_for(nq, MT);
-    int G = (int)std::sqrt(2.0 * bps * 152.0);
-    G = std::max(1, std::min({G, nT, (int)((s->val.n / (size_t)nq - 1) / 2)}));
-    if ((size_t)(2 * G + 1) * nq > s->val.n) {
-      set_error("far-field split buffer too small");
-      return PBFB_ERR_STATE;
+    int G;
+    if (m->tune_ff_bps > 0) {
+      G = (int)std::sqrt(2.0 * bps * 152.0);
+    } else {
+      if (m->ffm_wave_blocks == 0) {
+        int per = 0, nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->dev);
+        if (yuk)
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nbody_ffm<true>, MT, 0);
+        else
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nbody_ffm<false>, MT, 0);
+        m->ffm_wave_blocks = std::max(1, per) * std::max(1, nsm);
+      }
+      G = (int)((std::sqrt(8.0 * m->ffm_wave_blocks + 1.0) - 1.0) / 2.0);
     }
-    double* PI = s->val.p;
-    double* PJ = s->val.p + (size_t)G * nq;
-    double* out = s->val.p + (size_t)2 * G * nq;
-    PB_CUDA(cudaMemsetAsync(s->val.p, 0, (size_t)2 * G * nq * sizeof(double), m->stream));
+    G = std::max(1, std::min(G, nT));
+    PB_TRY(ensure(s->mval, (size_t)(2 * G + 1) * nq));
+    double* PI = s->mval.p;
+    double* PJ = s->mval.p + (size_t)G * nq;
+    double* out = s->mval.p + (size_t)2 * G * nq;
+    PB_CUDA(cudaMemsetAsync(s->mval.p, 0, (size_t)2 * G * nq * sizeof(double), m->stream));
     const int nblk = G * (G + 1) / 2;
     if (yuk)
       k_nbody_ffm<true><<<nblk, MT, 0, m->stream>>>(nq, G, s->ffsrc.p, kh, kl, m->ff_tab.p, PI, PJ);

@@ -169,6 +169,22 @@ int build_surface(Mesh* m, Surface* s, const std::vector<int>& gtri, const std::
   for (int v : verts)
     for (int d = 0; d < 3; ++d) c[d] += xyz_h[3 * (size_t)v + d];
   for (int d = 0; d < 3; ++d) s->ctr[d] = c[d] / verts.size();
+  {
+    // float-float coordinates: high parts on the grid 2^-k with every difference of two high
+    // parts below 2^24 steps, hence exact in float32 (quadrature points lie within the
+    // triangles, so within the largest vertex distance from the centre)
+    double rmax = 0.0;
+    for (int v : verts) {
+      double r2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double x = xyz_h[3 * (size_t)v + d] - s->ctr[d];
+        r2 += x * x;
+      }
+      rmax = std::max(rmax, std::sqrt(r2));
+    }
+    const int k = (int)std::floor(24.0 - std::log2(2.0 * rmax * 1.01 + 1e-300)) - 1;
+    s->ff_q = std::ldexp(1.0, -k);
+  }
   s->nt = nt;
   s->nv = (int)verts.size();
   s->nq = QS * nt;
