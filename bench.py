@@ -39,8 +39,8 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "multi_charge_sphere.json")
 NBODY_TRAFFIC = 2311424.0
 # float32 flops (FMA = 2) per ordered point pair of the mutual float-float kernel and its DRAM bytes
 # per launch, from its ncu capture (profiles/k_nbody_ffm_multi_charge_sphere.md)
-FF_FLOP_PAIR = {"laplace": 132.1, "yukawa": 191.3}
-FF_TRAFFIC = 12.25e6
+FF_FLOP_PAIR = {"laplace": 120.1, "yukawa": 179.3}
+FF_TRAFFIC = 12.3e6
 
 
 def workload_config(case, precision):

@@ -98,8 +98,9 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
     for (int packed : {0, 1, 2}) {
       if (packed == 1 && tpt < 2) continue;
       if (packed == 2 && tpt != 4) continue;
-      static const int bps_split[3] = {8, 16, 32}, bps_mutual[3] = {16, 32, 64};
-      for (int bi = 0; bi < 3; ++bi) {
+      // split kernels: 0 = whole waves of resident blocks
+      static const int bps_split[4] = {0, 8, 16, 32}, bps_mutual[4] = {16, 32, 64, 64};
+      for (int bi = 0; bi < (packed == 2 ? 3 : 4); ++bi) {
         const int bps = packed == 2 ? bps_mutual[bi] : bps_split[bi];
         pbfb_tuning t = best;
         t.nbody_targets_per_thread = tpt;
@@ -122,7 +123,7 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
     }
   // float-float far field
   for (int kind : {1, 2, 3})
-    for (int bps : {0, 4, 8, 16}) {
+    for (int bps : {4, 8, 16, 24}) {
       pbfb_tuning t = best;
       t.ff_kernel = kind;
       t.ff_blocks_per_sm = bps;

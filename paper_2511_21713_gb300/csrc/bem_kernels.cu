@@ -1513,12 +1513,33 @@ constexpr int F32_NT = 128;
 // Launch shape of the float32 far field: tuning knobs if set, else 2 targets per thread with
 // the packed kernel and 32 blocks per SM of source splits for large surfaces (GB300 sweep on
 // the multi-charge sphere), one target per thread unpacked for small ones.
+// With explicit targets per thread and blocks_per_sm 0, *bps = 0 asks the caller for a source
+// split that fills whole waves of resident blocks.
 void f32_shape(const Mesh* m, int nq, int* tpt, int* packed, int* bps) {
   const bool big = nq >= 16384;
   *tpt = m->tune_tpt > 0 ? m->tune_tpt : (big ? 2 : 1);
   *packed = m->tune_tpt > 0 ? m->tune_packed : (big ? 1 : 0);
-  if (*tpt < 2) *packed = 0;
-  *bps = m->tune_bps > 0 ? m->tune_bps : (big ? 32 : 16);
+  if (*tpt < 2 && *packed == 1) *packed = 0;
+  *bps = m->tune_bps > 0 ? m->tune_bps : (m->tune_tpt > 0 ? 0 : (big ? 32 : 16));
+}
+
+// resident blocks per SM of the split float32 kernel variant
+static int f32_blocks_per_sm(int tpt, int packed, bool yuk) {
+  constexpr int NT = F32_NT;
+  const void* f = nullptr;
+  if (packed) {
+    if (tpt == 2) f = yuk ? (const void*)k_nbody_f32x2<NT, 1, true> : (const void*)k_nbody_f32x2<NT, 1, false>;
+    else if (tpt == 8) f = yuk ? (const void*)k_nbody_f32x2<NT, 4, true> : (const void*)k_nbody_f32x2<NT, 4, false>;
+    else f = yuk ? (const void*)k_nbody_f32x2<NT, 2, true> : (const void*)k_nbody_f32x2<NT, 2, false>;
+  } else {
+    if (tpt == 1) f = yuk ? (const void*)k_nbody_f32<NT, 1, true> : (const void*)k_nbody_f32<NT, 1, false>;
+    else if (tpt == 2) f = yuk ? (const void*)k_nbody_f32<NT, 2, true> : (const void*)k_nbody_f32<NT, 2, false>;
+    else if (tpt == 8) f = yuk ? (const void*)k_nbody_f32<NT, 8, true> : (const void*)k_nbody_f32<NT, 8, false>;
+    else f = yuk ? (const void*)k_nbody_f32<NT, 4, true> : (const void*)k_nbody_f32<NT, 4, false>;
+  }
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, NT, 0);
+  return std::max(1, per);
 }
 
 void launch_nbody_f32(Mesh* m, Surface* s, double kappa, int tpt, int packed, int nsplit, int per,
@@ -1598,7 +1619,7 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
     if (packed == 2) {
       // mutual pairs: G tile groups, G (G + 1) / 2 one-warp blocks (about bps per SM)
       const int nT = blocks_for(nq, FM_T);
-      int G = (int)std::sqrt(2.0 * bps * 152.0);
+      int G = (int)std::sqrt(2.0 * (bps > 0 ? bps : 32) * 152.0);
       G = std::max(1, std::min(G, nT));
       PB_TRY(ensure(s->mval, (size_t)(2 * G + 1) * nq));
       double* PI = s->mval.p;
@@ -1616,7 +1637,13 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
       vals = out;
     } else {
       const int ntb = blocks_for(nq, F32_NT * tpt);
-      nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * F32_NT)));
+      if (bps == 0) {
+        // whole waves: the largest split with at most 3 waves of resident blocks
+        const int cap = f32_blocks_per_sm(tpt, packed, yuk) * 152;
+        nsplit = std::max(1, std::min(3 * cap / ntb, blocks_for(nq, 4 * F32_NT)));
+      } else {
+        nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * F32_NT)));
+      }
       const int per = blocks_for(blocks_for(nq, nsplit), F32_NT) * F32_NT;
       nsplit = blocks_for(nq, per);
       if ((size_t)nsplit * nq > s->val.n) {
@@ -1653,25 +1680,10 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
   const int bps = m->tune_ff_bps > 0 ? m->tune_ff_bps : 8;  // GB300 sweep: 8 blocks per SM of source splits
   const float kh = (float)kappa, kl = (float)(kappa - (double)kh);
   if (kind == 3) {
-    // tile groups: G (G + 1) / 2 blocks; built-in: the largest G whose blocks fit in one wave of
-    // resident blocks (the kernel is issue-bound: a partial second wave or an underfilled first one
-    // leaves issue slots idle); tuned: about bps blocks per SM.  2 G + 1 partial rows of val.
+    // tile groups: G (G + 1) / 2 blocks, about bps blocks per SM (built-in 16: two waves, which
+    // measured faster than one full wave or fewer, larger tiles); 2 G + 1 partial rows
     const int nT = blocks_for(nq, MT);
-    int G;
-    if (m->tune_ff_bps > 0) {
-      G = (int)std::sqrt(2.0 * bps * 152.0);
-    } else {
-      if (m->ffm_wave_blocks == 0) {
-        int per = 0, nsm = 0;
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->dev);
-        if (yuk)
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nbody_ffm<true>, MT, 0);
-        else
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nbody_ffm<false>, MT, 0);
-        m->ffm_wave_blocks = std::max(1, per) * std::max(1, nsm);
-      }
-      G = (int)((std::sqrt(8.0 * m->ffm_wave_blocks + 1.0) - 1.0) / 2.0);
-    }
+    int G = (int)std::sqrt(2.0 * (m->tune_ff_bps > 0 ? m->tune_ff_bps : 16) * 152.0);
     G = std::max(1, std::min(G, nT));
     PB_TRY(ensure(s->mval, (size_t)(2 * G + 1) * nq));
     double* PI = s->mval.p;

@@ -196,7 +196,6 @@ struct Mesh {
   int tune_ff_kernel = 0;           // float-float far field: 1 one target per thread, 2 two (float2),
                                     // 3 mutual pairs (0 = mutual for large surfaces, else 2)
   int tune_ff_bps = 0;              // float-float far field: target blocks per SM (0 = built-in)
-  int ffm_wave_blocks = 0;          // resident blocks of the mutual float-float kernel (one wave)
   int spmv_lanes = 0;               // lanes per row of the operator's sparse part (0 = 8; 4, 8, 16)
   int spmv_block = 0;               // threads per block of that SpMV (0 = 256; 128, 256, 512)
   int tune_pcg_bps = 0;             // blocks per SM of the cooperative inner PCG (0 = all that fit)
