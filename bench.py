@@ -40,7 +40,7 @@ NBODY_TRAFFIC = 2311424.0
 # float32 flops (FMA = 2) per ordered point pair of the mutual float-float kernel and its DRAM bytes
 # per launch, from its ncu capture (profiles/k_nbody_ffm_multi_charge_sphere.md)
 FF_FLOP_PAIR = {"laplace": 120.1, "yukawa": 179.3}
-FF_TRAFFIC = 12.3e6
+FF_TRAFFIC = 15.2e6
 
 
 def workload_config(case, precision):
