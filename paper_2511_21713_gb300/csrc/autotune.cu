@@ -20,6 +20,7 @@ void read_tuning(const Mesh* m, pbfb_tuning* t) {
   t->spmv_lanes = m->spmv_lanes;
   t->spmv_block = m->spmv_block;
   t->pcg_blocks_per_sm = m->tune_pcg_bps;
+  t->pcg_lanes = m->pcg_lanes;
 }
 
 bool valid_tuning(const pbfb_tuning* t) {
@@ -34,6 +35,7 @@ bool valid_tuning(const pbfb_tuning* t) {
   if (!(L == 0 || L == 4 || L == 8 || L == 16)) return false;
   if (!(B == 0 || B == 128 || B == 256 || B == 512)) return false;
   if (!in(t->pcg_blocks_per_sm, 1, 32)) return false;
+  if (!(t->pcg_lanes == 0 || t->pcg_lanes == 4 || t->pcg_lanes == 8)) return false;
   return true;
 }
 
@@ -47,6 +49,7 @@ void write_tuning(Mesh* m, const pbfb_tuning* t) {
   m->spmv_block = t->spmv_block;
   if (m->tune_pcg_bps != t->pcg_blocks_per_sm) m->coop_blocks = 0;  // re-derive the grid
   m->tune_pcg_bps = t->pcg_blocks_per_sm;
+  m->pcg_lanes = t->pcg_lanes;
 }
 
 // milliseconds per repetition of fn (one untimed run first)
@@ -167,9 +170,11 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
   double t_pcg = 0.0;
   if (!m->no_coop) {
     t_pcg = 1e300;
+    for (int lanes : {8, 4})
     for (int bps : {1, 2, 4, 8, 0}) {
       pbfb_tuning t = best;
       t.pcg_blocks_per_sm = bps;
+      t.pcg_lanes = lanes;
       write_tuning(m, &t);
       double ms;
       int st = time_ms(m, reps, [&]() -> int { return block_precond_apply(m, x.p, y.p, 20, true); }, &ms);
@@ -180,6 +185,7 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
       if (ms < t_pcg) {
         t_pcg = ms;
         best.pcg_blocks_per_sm = bps;
+        best.pcg_lanes = lanes;
       }
     }
   }

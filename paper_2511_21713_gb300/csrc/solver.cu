@@ -288,6 +288,7 @@ __device__ __forceinline__ double coop_sum(const double* part, int nb) {
 // gamma = r.z, delta = z.w: beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old),
 // p = z + beta p, q = w + beta q (= A p), x += alpha p, r -= alpha q, z = M r.  Same iterates as
 // standard PCG in exact arithmetic, two grid-wide barriers per step instead of three.
+template <int L>
 __global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int* __restrict__ ptr,
                                                      const int* __restrict__ col, const double* __restrict__ val,
                                                      const double* __restrict__ b, const double* __restrict__ dinv,
@@ -301,7 +302,8 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int
   double* part_g = part;
   double* part_d = part + nb;
   const int tid = blockIdx.x * PCG_T + threadIdx.x, stride = nb * PCG_T;
-  const int lane = threadIdx.x & 7;
+  const int lane = threadIdx.x & (L - 1);
+  constexpr int RW = 32 / L;  // rows per warp pass
   for (int i = tid; i < nv; i += stride) {
     double bi = b[i];
     x[i] = 0.0;
@@ -315,16 +317,15 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int
   for (int it = 0; it < iters; ++it) {
     // w = A z; partial r.z and z.w
     double ag = 0.0, ad = 0.0;
-    // warp-uniform trip count: every lane of a warp executes every shuffle (4 rows per warp pass)
-    for (int base = 4 * (tid >> 5); base < nv; base += 4 * (stride >> 5)) {
-      const int row = base + ((threadIdx.x & 31) >> 3);
+    // warp-uniform trip count: every lane of a warp executes every shuffle (RW rows per warp pass)
+    for (int base = RW * (tid >> 5); base < nv; base += RW * (stride >> 5)) {
+      const int row = base + (threadIdx.x & 31) / L;
       const bool valid = row < nv;
       double sacc = 0.0;
       if (valid)
-        for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 8) sacc += val[k] * z[col[k]];
-      sacc += __shfl_down_sync(0xffffffffu, sacc, 4, 8);
-      sacc += __shfl_down_sync(0xffffffffu, sacc, 2, 8);
-      sacc += __shfl_down_sync(0xffffffffu, sacc, 1, 8);
+        for (int k = ptr[row] + lane; k < ptr[row + 1]; k += L) sacc += val[k] * z[col[k]];
+#pragma unroll
+      for (int o = L / 2; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o, L);
       if (lane == 0 && valid) {
         w[row] = sacc;
         double zr = z[row];
@@ -546,7 +547,10 @@ static int prepare_block_precond(Mesh* m, bool dense) {
     int coop = 0, nsm = 0, per = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, m->dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->dev);
-    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_coop, PCG_T, 0));
+    int per4 = 0;
+    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_coop<8>, PCG_T, 0));
+    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, k_pcg_coop<4>, PCG_T, 0));
+    per = std::min(per, per4);  // co-resident with either variant
     // all resident blocks (memory-level parallelism for the SpMV phases), but no more than
     // one pass of 8 lanes per row needs
     int want = (m->tune_pcg_bps > 0 ? std::min(per, m->tune_pcg_bps) : per) * nsm;
@@ -644,7 +648,8 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
     const double* pv = m->pval.p;
     double* pw = pb + 5 * (size_t)n;
     void* args[] = {&nvv, &iters, &sp, &sc2, &pv, (void*)&vu, (void*)&dinv, &z, &pr, &pz, &pp, &pq, &pw, &part};
-    PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_coop, dim3(nbc), dim3(PCG_T), args, 0, m->stream));
+    const void* kfn = m->pcg_lanes == 4 ? (const void*)k_pcg_coop<4> : (const void*)k_pcg_coop<8>;
+    PB_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(nbc), dim3(PCG_T), args, 0, m->stream));
     PB_LAUNCHED(m);
     return PBFB_OK;
   }

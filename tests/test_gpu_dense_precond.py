@@ -123,3 +123,25 @@ def test_dense_errors(tiny_case):
     m.single_layer_dense(pbfb.GAMMA_M, 1, out)
     assert torch.isfinite(out).all()
     m.close()
+
+
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_inner_pcg_lane_variants(pair, lanes):
+    """Both sparse-product widths of the cooperative inner PCG give a preconditioner with which
+    flexible GMRES reaches the direct solution."""
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T)
+    base = m.get_tuning()
+    try:
+        m.apply_tuning(dict(base, pcg_lanes=lanes))
+        u = 3.0 * np.exp(-0.3 * (np.linalg.norm(P.xyz, axis=1) - 4.0))
+        m.assemble(pbfb.HS, dev(u))
+        b = np.random.default_rng(14).standard_normal(P.n)
+        xd = pb.linear_solve(P, P.J(u, "HS"), b, 0, pb.Opts(linear_solver="direct"))[0]
+        x = dev(np.zeros(P.n))
+        its, r = m.gmres(dev(b), x, 1e-11, precond=pbfb.BLOCK_DENSE, inner_iters=30)
+        assert r <= 1e-11 and rel(x.cpu().numpy(), xd) < 1e-8
+    finally:
+        m.apply_tuning(base)
