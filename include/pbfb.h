@@ -315,7 +315,7 @@ typedef struct pbfb_tuning {
   int32_t spmv_block;                /* threads per block of that SpMV: 128, 256, 512 */
   int32_t pcg_blocks_per_sm;         /* blocks per SM of the cooperative inner PCG: 1..32
                                         (0: as many as fit) */
-  int32_t pcg_lanes;                 /* lanes per row of its sparse product: 4 or 8 */
+  int32_t pcg_lanes;                 /* lanes per row of its sparse product: 2, 4 or 8 */
 } pbfb_tuning;
 
 /* Current launch shapes of a mesh (zeros where the built-in choice applies). */
@@ -335,7 +335,7 @@ int pbfb_apply_tuning(pbfb_mesh* mesh, const pbfb_tuning* t);
  * surfaces of this mesh at the current parameters, and of the operator's
  * SpMV (4/8/16 lanes per row x 128/256/512 threads) and of the cooperative
  * inner PCG of the block preconditioner (1/2/4/8 blocks per SM or all that
- * fit, 4 or 8 lanes per row; 20 iterations at the current Jacobian), each
+ * fit, 2, 4 or 8 lanes per row; 20 iterations at the current Jacobian), each
  * over reps
  * repetitions after one untimed run, and applies the fastest.  best (host,
  * may be NULL) receives the chosen shapes; ms (host, 3 doubles, may be NULL)

@@ -547,10 +547,11 @@ static int prepare_block_precond(Mesh* m, bool dense) {
     int coop = 0, nsm = 0, per = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, m->dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->dev);
-    int per4 = 0;
+    int per4 = 0, per2 = 0;
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_coop<8>, PCG_T, 0));
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, k_pcg_coop<4>, PCG_T, 0));
-    per = std::min(per, per4);  // co-resident with either variant
+    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_pcg_coop<2>, PCG_T, 0));
+    per = std::min({per, per4, per2});  // co-resident with every variant
     // all resident blocks (memory-level parallelism for the SpMV phases), but no more than
     // one pass of 8 lanes per row needs
     int want = (m->tune_pcg_bps > 0 ? std::min(per, m->tune_pcg_bps) : per) * nsm;
@@ -648,7 +649,9 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
     const double* pv = m->pval.p;
     double* pw = pb + 5 * (size_t)n;
     void* args[] = {&nvv, &iters, &sp, &sc2, &pv, (void*)&vu, (void*)&dinv, &z, &pr, &pz, &pp, &pq, &pw, &part};
-    const void* kfn = m->pcg_lanes == 4 ? (const void*)k_pcg_coop<4> : (const void*)k_pcg_coop<8>;
+    const void* kfn = m->pcg_lanes == 2   ? (const void*)k_pcg_coop<2>
+                      : m->pcg_lanes == 4 ? (const void*)k_pcg_coop<4>
+                                          : (const void*)k_pcg_coop<8>;
     PB_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(nbc), dim3(PCG_T), args, 0, m->stream));
     PB_LAUNCHED(m);
     return PBFB_OK;

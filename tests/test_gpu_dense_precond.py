@@ -125,7 +125,7 @@ def test_dense_errors(tiny_case):
     m.close()
 
 
-@pytest.mark.parametrize("lanes", [4, 8])
+@pytest.mark.parametrize("lanes", [2, 4, 8])
 def test_inner_pcg_lane_variants(pair, lanes):
     """Both sparse-product widths of the cooperative inner PCG give a preconditioner with which
     flexible GMRES reaches the direct solution."""
