@@ -61,7 +61,7 @@ def test_radial_reference_matches_kirkwood_in_linear_limit():
     # the BVP machinery itself: tiny charge -> ion term ~ z^4, energy -> Kirkwood
     tot, dG = radial_nonlinear(0.01, 4.0, 10.0, 4.0, 80.0, 0.125, 300.0)
     assert abs(tot - kirkwood(0.01, 4.0, 4.0, 80.0, 0.125)) < 1e-6 * abs(tot)
-    # the survey-quoted nonlinear value for this geometry (kappa = 0.125): -251.7472 kcal/mol
+    # the radial BVP's nonlinear value for this geometry (kappa = 0.125), recorded once: -251.7472 kcal/mol
     tot5, dG5 = radial_nonlinear(5.0, 4.0, 10.0, 4.0, 80.0, 0.125, 300.0)
     assert abs(tot5 + 251.7472) < 1e-3 and abs(dG5 - 0.7964) < 1e-4
 
