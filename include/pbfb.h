@@ -348,7 +348,7 @@ int pbfb_autotune(pbfb_mesh* mesh, int reps, pbfb_tuning* best, double* ms);
 
 /* Per-kernel-class timing (CUDA events around each launch of the class) and
  * launch counters.  enable != 0 turns event timing on (it adds a little host
- * overhead per launch).  stats (host, 16 doubles):
+ * overhead per launch).  stats (host, 20 doubles):
  *   [0] launches of all kernels since the last reset,
  *   [1] float32 BEM far-field (N-body) launches, [2] their total ms, [3] their
  *       pair interactions, [4] FEM SpMV launches, [5] their ms,
@@ -356,8 +356,12 @@ int pbfb_autotune(pbfb_mesh* mesh, int reps, pbfb_tuning* best, double* ms);
  *   [8] float32 far-field flops (18 per Laplace pair, 24 per Yukawa pair),
  *   [9] float64 far-field launches, [10] their ms, [11] their pairs,
  *   [12] float-float far-field launches, [13] their ms, [14] their pairs,
- *   [15] ms spent building dense single-layer matrices and inverses.
- * reset != 0 zeroes the counters after reading. */
+ *   [15] ms spent building dense single-layer matrices and inverses,
+ *   [16..19] host ms of pbfb_mesh_create: validation, surfaces (pair classes and
+ *       correction patterns), operator pattern and gather lists, and the device
+ *       set-up (geometry, stiffness, Laplace corrections) until synchronised.
+ * reset != 0 zeroes the counters after reading (not the
+ * set-up times). */
 int pbfb_profile(pbfb_mesh* mesh, int enable, int reset, double* stats);
 
 /* ---- Serving and batching (the paper has no counterpart; the solves are the same). */

@@ -7,10 +7,13 @@
 
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <map>
+#include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -227,26 +230,32 @@ int build_surface(Mesh* m, Surface* s, const std::vector<int>& gtri, const std::
         dv.push_back((int)e);
       }
     }
-    auto colof = [&](int e) { return hs.tri[3 * ps[e / 9] + e % 3]; };
+    std::vector<int> colv(ne);
+    for (size_t e = 0; e < ne; ++e) colv[e] = hs.tri[3 * ps[e / 9] + e % 3];
     std::vector<int> rptr, rent;
     bucket(rows, vals, s->nv, rptr, rent);
     s->c_ptr_h.assign(s->nv + 1, 0);
     s->c_col_h.clear();
+    // per row: the distinct columns in first-seen order (a marker per column), sorted, then every
+    // entry's slot is its column's rank in the row
+    std::vector<int> mark(s->nv, -1), distinct;
     for (int i = 0; i < s->nv; ++i) {
-      auto b = rent.begin() + rptr[i], en = rent.begin() + rptr[i + 1];
-      std::sort(b, en, [&](int x, int y) {
-        const int cx = colof(x), cy = colof(y);
-        return cx < cy || (cx == cy && x < y);
-      });
-      int last = -1;
-      for (auto it = b; it != en; ++it) {
-        const int c = colof(*it);
-        if (c != last) {
-          s->c_col_h.push_back(c);
-          last = c;
+      distinct.clear();
+      for (int q = rptr[i]; q < rptr[i + 1]; ++q) {
+        const int c = colv[rent[q]];
+        if (mark[c] < 0) {
+          mark[c] = 0;
+          distinct.push_back(c);
         }
-        slot_of[*it] = (int)s->c_col_h.size() - 1;
       }
+      std::sort(distinct.begin(), distinct.end());
+      const int base = (int)s->c_col_h.size();
+      for (size_t r = 0; r < distinct.size(); ++r) {
+        mark[distinct[r]] = base + (int)r;
+        s->c_col_h.push_back(distinct[r]);
+      }
+      for (int q = rptr[i]; q < rptr[i + 1]; ++q) slot_of[rent[q]] = mark[colv[rent[q]]];
+      for (int c : distinct) mark[c] = -1;
       s->c_ptr_h[i + 1] = (int)s->c_col_h.size();
     }
     s->cnnz = (int)s->c_col_h.size();
@@ -443,9 +452,16 @@ static int validate(const double* xyz, int nv, const int* tets, int64_t nt, cons
   return PBFB_OK;
 }
 
+static double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const int* gm, int ngm, const int* gs,
                 int ngs, cudaStream_t stream, Mesh** out) {
+  auto tc = std::chrono::steady_clock::now();
   PB_TRY(validate(xyz, nv, tets, nt, gm, ngm, gs, ngs));
+  const double t_validate = ms_since(tc);
+  tc = std::chrono::steady_clock::now();
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     set_error("no CUDA device");
@@ -474,10 +490,28 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
     if ((st = m->tets.upload(tsoa.data(), tsoa.size(), stream))) return fail(st);
   }
   std::vector<int> gmv(gm, gm + 3 * (size_t)ngm), gsv(gs, gs + 3 * (size_t)ngs);
-  if ((st = build_surface(m, &m->sm, gmv, xyz_h))) return fail(st);
-  if ((st = build_surface(m, &m->ss, gsv, xyz_h))) return fail(st);
+  {
+    // the two surfaces are independent: Gamma_s on a second host thread (its own error text)
+    int st_s = PBFB_OK;
+    std::string err_s;
+    std::thread th([&] {
+      cudaSetDevice(m->dev);
+      st_s = build_surface(m, &m->ss, gsv, xyz_h);
+      if (st_s != PBFB_OK) err_s = last_error();
+    });
+    st = build_surface(m, &m->sm, gmv, xyz_h);
+    th.join();
+    if (st) return fail(st);
+    if (st_s) {
+      set_error("%s", err_s.c_str());
+      return fail(st_s);
+    }
+  }
   Surface& sm = m->sm;
   Surface& ss = m->ss;
+  m->setup_ms[0] = t_validate;
+  m->setup_ms[1] = ms_since(tc);
+  tc = std::chrono::steady_clock::now();
   sm.col0 = nv;
   ss.col0 = nv + sm.nv;
   m->n = nv + sm.nv + ss.nv;
@@ -520,11 +554,19 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
     bucket(rk, ck, m->n, rptr, cols);
     m->s_ptr_h.assign(m->n + 1, 0);
     size_t w = 0;
+    std::vector<char> seen(m->n, 0);
     for (int r = 0; r < m->n; ++r) {
-      auto b = cols.begin() + rptr[r], e = cols.begin() + rptr[r + 1];
-      std::sort(b, e);
-      e = std::unique(b, e);
-      for (auto it = b; it != e; ++it) cols[w++] = *it;
+      // distinct columns of the row (a marker per column), then sorted in place
+      const size_t w0 = w;
+      for (int q = rptr[r]; q < rptr[r + 1]; ++q) {
+        const int c = cols[q];
+        if (!seen[c]) {
+          seen[c] = 1;
+          cols[w++] = c;
+        }
+      }
+      std::sort(cols.begin() + w0, cols.begin() + w);
+      for (size_t q = w0; q < w; ++q) seen[cols[q]] = 0;
       m->s_ptr_h[r + 1] = (int)w;
     }
     cols.resize(w);
@@ -634,6 +676,8 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
     set_error("cudaMallocHost failed");
     return fail(PBFB_ERR_OOM);
   }
+  m->setup_ms[2] = ms_since(tc);
+  tc = std::chrono::steady_clock::now();
   // ---- device geometry and constant operator parts
   if ((st = launch_tet_volumes(m))) return fail(st);
   if ((st = launch_stiffness_local(m, m->tloc.p))) return fail(st);
@@ -647,6 +691,7 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
     set_error("mesh_create: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(PBFB_ERR_CUDA);
   }
+  m->setup_ms[3] = ms_since(tc);
   *out = m;
   return PBFB_OK;
 }

@@ -212,6 +212,7 @@ struct Mesh {
   KernelClassTimer t_nbody, t_nbody64, t_nbodyff, t_spmv, t_elem, t_dense;
   DBuf<float2> ff_tab;      // float-float exp table of the Yukawa kernel
   double nbody_flops = 0.0;  // float32 far-field flops issued (18 per Laplace pair, 24 per Yukawa pair)
+  double setup_ms[4] = {0, 0, 0, 0};  // mesh_create: validation, surfaces, operator pattern, device set-up
   ~Mesh() {
     if (pcg_graph) cudaGraphExecDestroy(pcg_graph);
   }

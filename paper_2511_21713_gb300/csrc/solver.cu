@@ -1706,6 +1706,7 @@ int pbfb_profile(pbfb_mesh* h, int enable, int reset, double* stats) {
     stats[13] = m->t_nbodyff.ms;
     stats[14] = m->t_nbodyff.work;
     stats[15] = m->t_dense.ms;
+    for (int k = 0; k < 4; ++k) stats[16 + k] = m->setup_ms[k];
   }
   if (reset) {
     m->launches = 0;

@@ -343,13 +343,14 @@ class Mesh:
         return shapes, times
 
     def profile(self, enable=True, reset=False):
-        st = np.zeros(16)
+        st = np.zeros(20)
         _check(load().pbfb_profile(self.h, int(enable), int(reset), _ptr(st)))
         return dict(launches=st[0], nbody_launches=st[1], nbody_ms=st[2], nbody_pairs=st[3],
                     spmv_launches=st[4], spmv_ms=st[5], elem_launches=st[6], elem_ms=st[7],
                     nbody_flops=st[8], nbody64_launches=st[9], nbody64_ms=st[10], nbody64_pairs=st[11],
                     nbodyff_launches=st[12], nbodyff_ms=st[13], nbodyff_pairs=st[14],
-                    dense_build_ms=st[15])
+                    dense_build_ms=st[15], setup_validate_ms=st[16], setup_surfaces_ms=st[17],
+                    setup_pattern_ms=st[18], setup_device_ms=st[19])
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
