@@ -137,7 +137,8 @@ typedef struct pbfb_result {
   int omega_fallbacks;                 /* omega searches that needed the scan */
   int gmres_iters[PBFB_MAX_TRACE];
   double omega[PBFB_MAX_TRACE];
-  double e[PBFB_MAX_TRACE];            /* e_{k+1} = omega ||Delta||_2 */
+  double e[PBFB_MAX_TRACE];            /* e_{k+1} = omega ||Delta||_2; a step whose residual d is
+                                          exactly zero (no charges) stops with omega = e = 0 */
   int omega_evals[PBFB_MAX_TRACE];     /* batched residual evaluations per step */
   double ms_linear, ms_newton, ms_energy;
 } pbfb_result;

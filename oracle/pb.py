@@ -454,6 +454,13 @@ def solve(P: Problem, opts: Opts = None, linear_only=False):
         Nu = P.N(u, scheme)
         c = P.b - P.apply(Phi)                                  # b - Acal(0) Phi
         d = c - P.pad(Nu)
+        if not d.any():
+            # the iterate solves Eq. NR_main's system exactly (e.g. no charges): Delta = 0 for every
+            # omega, so e_k = 0 < Tol_NL (Sec. 3.5) and no relaxation factor is searched for
+            for key, v in (('gmres', 0), ('scheme', scheme), ('dnorm', 0.0), ('omega', 0.0), ('e', 0.0),
+                           ('omega_evals', 0)):
+                trace[key].append(v)
+            break
         # Newton: Acal(J) Delta = d (Eq. NR_main); Picard: Acal(0) Delta = d, Delta = Phi~ - Phi_NL
         # (Eq. Ec_NL_Previo2 written for the increment)
         Jm = None if picard else P.J(u, scheme)

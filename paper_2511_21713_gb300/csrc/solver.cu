@@ -1226,6 +1226,16 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
       if (res) *res = R;
       return R.status;
     }
+    if (d2 == 0.0) {
+      // the iterate solves the system exactly (e.g. no charges): Delta = 0 for every omega, so
+      // e_k = 0 < Tol_NL (Sec. 3.5) without a relaxation-factor search
+      if (k < PBFB_MAX_TRACE) {
+        R.gmres_iters[k] = R.omega_evals[k] = 0;
+        R.omega[k] = R.e[k] = 0.0;
+      }
+      converged = true;
+      break;
+    }
     // Newton: Acal(J) Delta = d (Eq. NR_main).  Picard: Acal(0) Delta = d, the increment form of
     // Eq. Ec_NL_Previo2 (Delta = Phi~_NL - Phi_NL)
     if (picard) PB_TRY(clear_jacobian(m));

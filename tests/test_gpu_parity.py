@@ -285,6 +285,21 @@ def test_kappa_zero_born_limit(tiny_case, bem_cache):
     m.close()
 
 
+def test_zero_charges(tiny_case):
+    """No charge: the solution is exactly zero, the first Newton residual is zero and the
+    iteration stops there (e_0 = 0), every energy term zero, as in the oracle."""
+    from paper_2511_21713_gb300 import pbfb
+    c = tiny_case
+    m = pbfb.Mesh.from_case(c)
+    m.charges_set(c.q_xyz, 0.0 * c.q_z)
+    for precision in (pbfb.FP64, pbfb.MIXED):
+        x, res = m.solve(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.default_opts(precision=precision))
+        assert res["status"] == 0 and res["newton_iters"] == 1 and res["linear_gmres"] == 0
+        assert not np.any(x) and res["e"][0] == 0.0
+        assert (res["total"], res["LC"], res["NC"], res["dG_ion"]) == (0.0, 0.0, 0.0, 0.0)
+    m.close()
+
+
 def test_error_statuses(tiny_case):
     from paper_2511_21713_gb300 import pbfb
     c = tiny_case

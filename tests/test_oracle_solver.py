@@ -182,6 +182,18 @@ def test_small_charge_scaling(tiny_case, bem_cache):
     assert abs(out[0.5].dG_ion / out[0.05].dG_ion / 1e4 - 1) < 2e-2
 
 
+def test_zero_charges_give_the_zero_solution(tiny_case, bem_cache):
+    """With no charge the system Acal(0) Phi + N(Phi) = 0 is homogeneous and sinh is monotone, so
+    Phi = 0 is its only solution: the linear part is zero, the first Newton residual is exactly
+    zero and the iteration stops there with e_0 = 0 and every energy term zero."""
+    import dataclasses
+    c = dataclasses.replace(tiny_case, q_z=0.0 * tiny_case.q_z)
+    r = pb.solve(pb.Problem(c, bem_cache=bem_cache), TIGHT)
+    assert not r.x.any() and r.newton_iters == 1
+    assert r.trace["e"] == [0.0] and r.trace["gmres"] == [0] and r.trace["linear_gmres"] == 0
+    assert (r.total, r.LC, r.NC, r.dG_ion) == (0.0, 0.0, 0.0, 0.0)
+
+
 def test_paper_default_options_trace(small_problem):
     """Paper-default tolerances: converges in a handful of Newton steps with omega > 0
     and the final energy within Tol-level of the tight solve."""
