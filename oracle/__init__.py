@@ -20,6 +20,10 @@ Modules:
                  optimal relaxation factor (Eqs. NR_main, Ec_NL_NR, fd=0,
                  Appendix A), and the solvation energy (Eqs. Esolv,
                  Potential_in_Omega_m).
+  solute      -- the paper's own formulation: FEM over Omega_m and Omega_i
+                 with the charges as point loads, Yukawa BEM on Gamma_s
+                 (Eq. fembem_matrix), and the reaction potential from the
+                 Gamma_m boundary integral equation (Sec. 2.3.1).
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 closed form, a library routine used as an independent check, an invariant or

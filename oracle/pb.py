@@ -421,8 +421,13 @@ def energy(P: Problem, xL, xNL):
     (the paper's (1/2) eps_s kappa^2 prefactor expressed in reduced units).
     """
     z = P.case.q_z
-    LC = 0.5 * P.kT * float(z @ reaction_potential(P, xL))
-    NC = 0.5 * P.kT * float(z @ reaction_potential(P, xNL))
+    if hasattr(P, 'reaction_potentials'):
+        # a problem whose unknowns hold no lam_m computes u_r itself (solute.SoluteProblem)
+        urL, urNL = P.reaction_potentials(xL, xNL)
+    else:
+        urL, urNL = reaction_potential(P, xL), reaction_potential(P, xNL)
+    LC = 0.5 * P.kT * float(z @ urL)
+    NC = 0.5 * P.kT * float(z @ urNL)
     c0 = P.coef / (8.0 * np.pi * P.lB)
     u = (xL + xNL)[:P.nv]
     dG = P.kT * c0 * fem.ion_energy_integral(P.xyz, P.tets, u)

@@ -78,6 +78,8 @@ class Case:
     eps_out: float
     kappa: float
     T: float
+    tet_region: np.ndarray = None   # (n_t,) int32 for a mesh of Omega_m and Omega_i: 0 in Omega_m,
+                                    # 1 in Omega_i (Gamma_m interior); None for a shell mesh
 
     @property
     def n_v(self):
@@ -181,6 +183,70 @@ def spherical_shell(nu: int, a: float, R: float, layers: int):
     gs = (tri + layers * ns).astype(np.int32)     # outward of the outer sphere = into the far field
     # fix xyz radii exactly on the two surfaces (already exact by construction)
     return xyz, tets, gm, gs
+
+
+def spherical_solute(nu: int, a: float, R: float, layers: int, core_layers: int, r_core: float):
+    """Mesh of the ball r < R with the interface Gamma_m at r = a inside it.
+
+    Layers of the same icosphere at radii r_core (a / r_core)^(l / core_layers), l = 0..core_layers,
+    then a (R / a)^(l / layers), cut into prisms and tets as in ``spherical_shell``, and a core of
+    one tet per icosphere triangle of the innermost layer with apex at the centre.  Returns
+    (xyz, tets, region, gm, gs): region 0 for the tets inside Gamma_m (Omega_m), 1 outside
+    (Omega_i); gm oriented away from the centre (into Omega_i), gs out of the ball.
+    """
+    u, tri = icosphere(nu)
+    ns = u.shape[0]
+    r_in = r_core * (a / r_core) ** (np.arange(core_layers + 1) / core_layers)
+    r_out = a * (R / a) ** (np.arange(1, layers + 1) / layers)
+    radii = np.concatenate([r_in, r_out])
+    nl = radii.size
+    xyz = np.concatenate([(radii[:, None, None] * u[None, :, :]).reshape(-1, 3), np.zeros((1, 3))])
+    centre = nl * ns
+    tets, region = [], []
+    for f in tri:
+        tets.append((centre, f[0], f[1], f[2]))
+        region.append(0)
+    for lay in range(nl - 1):
+        off0, off1 = lay * ns, (lay + 1) * ns
+        for f in tri:
+            v = [off0 + f[0], off0 + f[1], off0 + f[2], off1 + f[0], off1 + f[1], off1 + f[2]]
+            tets.extend(_prism_tets(v))
+            region.extend([0 if lay < core_layers else 1] * 3)
+    gm = (tri + core_layers * ns).astype(np.int32)
+    gs = (tri + (nl - 1) * ns).astype(np.int32)
+    return xyz, np.array(tets, dtype=np.int32), np.array(region, dtype=np.int32), gm, gs
+
+
+def solute_sphere_case(nu=5, a=4.0, R=10.0, layers=13, core_layers=12, r_core=None, q_xyz=None,
+                       q_z=None, eps_in=4.0, eps_out=80.0, kappa=None, ionic=0.15, T=300.0, name=None):
+    """A sphere case meshed inside Gamma_m too (FEM over Omega_m and Omega_i).  The core layers
+    are graded geometrically towards r_core (default a / 16), where the central cone starts."""
+    r_core = a / 16.0 if r_core is None else r_core
+    xyz, tets, region, gm, gs = spherical_solute(nu, a, R, layers, core_layers, r_core)
+    if q_xyz is None:
+        q_xyz = np.zeros((1, 3))
+        q_z = np.array([5.0])
+    if kappa is None:
+        kappa = kappa_from_ionic_strength(ionic, eps_out, T)
+    return Case(name or f"solute_sphere_nu{nu}_L{layers}_C{core_layers}", xyz, tets, gm, gs,
+                np.asarray(q_xyz, np.float64).reshape(-1, 3), np.asarray(q_z, np.float64),
+                eps_in, eps_out, kappa, T, tet_region=region)
+
+
+def single_charge_solute_sphere(nu=5, layers=13, core_layers=12, kappa=None):
+    """The single-charge sphere (radius 4, shell to 10, +5 e at the centre, eps 4/80, 0.15 M),
+    meshed inside Gamma_m as well."""
+    return solute_sphere_case(nu=nu, a=4.0, R=10.0, layers=layers, core_layers=core_layers, kappa=kappa,
+                              name=f"single_charge_solute_sphere_nu{nu}_L{layers}_C{core_layers}")
+
+
+def multi_charge_solute_sphere(nu=20, layers=17, core_layers=24, seed=2000, n_charges=200, n_pos=90):
+    """The multi-charge sphere (radius 12, shell to 24, 200 +-1 e charges in r < 10, eps 2/80,
+    0.1 M), meshed inside Gamma_m as well."""
+    q, z = ball_charges(n_charges, 10.0, n_pos, seed)
+    return solute_sphere_case(nu=nu, a=12.0, R=24.0, layers=layers, core_layers=core_layers, q_xyz=q, q_z=z,
+                              eps_in=2.0, eps_out=80.0, ionic=0.1,
+                              name=f"multi_charge_solute_sphere_nu{nu}_L{layers}_C{core_layers}")
 
 
 def ball_charges(n: int, radius: float, n_pos: int, seed: int):

@@ -31,3 +31,15 @@ def tiny_case():
 def small_case():
     from paper_2511_21713_gb300 import inputs
     return inputs.single_charge_sphere(nu=5, layers=13)
+
+
+@pytest.fixture(scope="session")
+def tiny_solute_case():
+    from paper_2511_21713_gb300 import inputs
+    return inputs.single_charge_solute_sphere(nu=3, layers=5, core_layers=6)
+
+
+@pytest.fixture(scope="session")
+def small_solute_case():
+    from paper_2511_21713_gb300 import inputs
+    return inputs.single_charge_solute_sphere(nu=5, layers=13, core_layers=12)

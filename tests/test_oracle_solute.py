@@ -1,0 +1,112 @@
+"""Pins for the oracle's FEM(Omega_m and Omega_i)-BEM(Gamma_s) formulation with the Gamma_m
+post-process (Sec. 2.2, Eq. fembem_matrix; Sec. 2.3.1), no GPU.
+
+Independent references: the partition of unity and linear precision of the P1 hat functions
+(point load), the exact discrete Gauss law (row sums of the stiffness vanish), the continuum
+Gauss law on Gamma_m, Kirkwood's closed form, the radial boundary-value solve of the nonlinear
+sphere, and the separately pinned three-region formulation on the same surfaces and shell.
+"""
+import numpy as np
+import pytest
+
+from oracle import pb, solute
+from test_oracle_solver import kirkwood, radial_nonlinear
+
+TIGHT = pb.Opts(tol_gmres0=1e-13, tol_gmres=1e-13, tol_nl=1e-9, linear_solver="direct")
+
+
+@pytest.fixture(scope="module")
+def small_solute(small_solute_case, bem_cache):
+    P = solute.SoluteProblem(small_solute_case, bem_cache=bem_cache)
+    return P, pb.solve(P, TIGHT)
+
+
+@pytest.fixture(scope="module")
+def small_shell(small_case, bem_cache):
+    P = pb.Problem(small_case, bem_cache=bem_cache)
+    return P, pb.solve(P, pb.Opts(tol_gmres0=1e-13, tol_gmres=1e-13, tol_nl=1e-11, linear_solver="direct"))
+
+
+def test_mesh_regions(tiny_solute_case):
+    from oracle import fem
+    c = tiny_solute_case
+    vol, _ = fem.tet_geometry(c.xyz, c.tets)
+    # the tets inside Gamma_m fill the polyhedron Gamma_m bounds (divergence theorem on its faces)
+    x = c.xyz[c.gm_tris]
+    enclosed = np.einsum("ij,ij->i", x[:, 0], np.cross(x[:, 1], x[:, 2])).sum() / 6.0
+    assert abs(vol[c.tet_region == 0].sum() - enclosed) < 1e-12 * enclosed
+
+
+def test_point_load_moments(tiny_solute_case):
+    from paper_2511_21713_gb300 import inputs
+    c = tiny_solute_case
+    tm = c.tets[c.tet_region == 0]
+    q, z = inputs.ball_charges(25, 3.0, 10, seed=5)
+    z = z * np.linspace(0.5, 1.5, z.size)
+    load = solute.point_load(c.xyz, tm, q, z)
+    # partition of unity and linear precision of the P1 hat functions
+    assert abs(load.sum() - z.sum()) < 1e-12 * np.abs(z).sum()
+    assert np.abs(load @ c.xyz - z @ q).max() < 1e-12 * np.abs(z).sum() * 4.0
+    # a charge on a vertex loads that vertex alone; one outside Omega_m is refused
+    v = int(tm[7, 2])
+    one = solute.point_load(c.xyz, tm, c.xyz[v][None], [2.0])
+    assert abs(one[v] - 2.0) < 1e-12 and np.abs(np.delete(one, v)).max() < 1e-12
+    with pytest.raises(ValueError):
+        solute.point_load(c.xyz, tm, np.array([[0.0, 0.0, 5.0]]), [1.0])
+
+
+def test_discrete_gauss_law(small_solute):
+    """Summing every FEM row of the converged system: the stiffness rows sum to zero, so
+    eps_s kappa^2 int F(u) - eps_s int_Gamma_s lam_s = 4 pi l_B sum z (to solver precision)."""
+    P, R = small_solute
+    u, ls = P.split(R.x)
+    lhs = P.N(u, "HS").sum() - P.eps_s * (P.Ms @ ls).sum()
+    rhs = 4.0 * np.pi * P.lB * P.case.q_z.sum()
+    assert abs(lhs - rhs) < 1e-10 * abs(rhs)
+    assert R.newton_iters <= 8 and R.trace["e"][-1] < 1e-9
+
+
+def test_linear_energy_near_kirkwood(small_solute):
+    P, _ = small_solute
+    R = pb.solve(P, TIGHT, linear_only=True)
+    ref = kirkwood(5.0, 4.0, P.eps_m, P.eps_s, P.kappa)
+    assert abs(R.total / ref - 1) < 1e-2     # nu = 5 surfaces: discretisation error 0.8 %
+
+
+def test_nonlinear_energy_near_radial_solution(small_solute):
+    P, R = small_solute
+    total, dG = radial_nonlinear(5.0, 4.0, 10.0, P.eps_m, P.eps_s, P.kappa, P.T)
+    assert abs(R.total / total - 1) < 1.5e-2
+    assert abs(R.dG_ion / dG - 1) < 3e-2
+    assert abs(R.total - (R.LC + R.NC + R.dG_ion)) < 1e-12 * abs(R.total)
+
+
+def test_formulations_agree(small_solute, small_shell):
+    """Same surfaces and shell; Omega_m by FEM with a point load here, by the Laplace BIE there:
+    the energies agree to a few parts in 1e6, far inside either's discretisation error."""
+    P, R = small_solute
+    Ps, Rs = small_shell
+    assert abs(R.LC / Rs.LC - 1) < 1e-4
+    assert abs(R.NC / Rs.NC - 1) < 1e-3
+    assert abs(R.dG_ion / Rs.dG_ion - 1) < 1e-3
+    # the potentials on the shell differ by the two discretisations of Omega_m (1.4 % of the
+    # largest; the energies, Galerkin functionals, much less), lam_m by 0.09 %
+    off = P.nv - Ps.nv - 1                  # core vertices come first, the centre last
+    u = R.x[:P.nv]
+    us = Rs.x[:Ps.nv]
+    assert np.abs(u[off:off + Ps.nv] - us).max() < 2e-2 * np.abs(us).max()
+    lm = P.lam_m(u)
+    lms = Rs.x[Ps.nv:Ps.nv + Ps.nm]
+    assert np.linalg.norm(lm - lms) < 2e-3 * np.linalg.norm(lms)
+
+
+def test_post_processed_flux(small_solute):
+    """eps_m int_Gamma_m lam_m = -4 pi l_B sum z (Gauss's law in Omega_m), within the
+    discretisation error; without the Coulomb term the nonlinear part's flux is small."""
+    P, R = small_solute
+    u = R.x[:P.nv]
+    lm = P.lam_m(u)
+    ref = -4.0 * np.pi * P.lB * P.case.q_z.sum()
+    assert abs(P.eps_m * (P.Mm @ lm).sum() / ref - 1) < 1e-3
+    x = P.expand(R.x)
+    assert np.array_equal(x[P.nv:P.nv + P.nm], lm) and np.array_equal(x[P.nv + P.nm:], R.x[P.nv:])
