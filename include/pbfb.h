@@ -164,6 +164,36 @@ int pbfb_mesh_create(const double* xyz, int32_t n_v, const int32_t* tets, int64_
                      const int32_t* gm_tris, int32_t n_gm, const int32_t* gs_tris, int32_t n_gs,
                      uintptr_t stream, pbfb_mesh** out);
 
+/* Creates a mesh of Omega_m and Omega_i together: the paper's own formulation (Sec. 2.2,
+ * Eq. fembem_matrix), with FEM over both regions (eps_m in Omega_m, eps_s and the ions in
+ * Omega_i), the charges as point loads 4 pi l_B sum_k z_k v_i(x_k) of the P1 hat functions,
+ * and the Yukawa BEM on Gamma_s.
+ *   tet_region  host, n_t int32: 0 for a tet of Omega_m, 1 for one of Omega_i.
+ *   gm_tris     the faces between Omega_m and Omega_i tets (every one of them, each once),
+ *               oriented with the normal into Omega_i.
+ *   gs_tris     the boundary faces of the tets (all of them), normal out of Omega_i.
+ * Other arguments as pbfb_mesh_create.  The unknowns keep the layout [u; lam_m; lam_s]: during
+ * the solve the lam_m rows are the identity (lam_m = 0, no coupling); a converged solve then
+ * fills lam_m from the Gamma_m boundary integral equation of Sec. 2.3.1 (pbfb_gamma_m_flux) and
+ * takes the energy as for a shell mesh (Eq. Esolv, Eq. Potential_in_Omega_m), Delta G_Omega_i
+ * over the Omega_i tets.  pbfb_charges_set then requires every charge to lie in an Omega_m tet
+ * (barycentric coordinates >= -1e-12; PBFB_ERR_INVALID otherwise).  The request server and the
+ * batch call take shell meshes only. */
+int pbfb_mesh_create_full(const double* xyz, int32_t n_v, const int32_t* tets, int64_t n_t,
+                          const int32_t* tet_region, const int32_t* gm_tris, int32_t n_gm,
+                          const int32_t* gs_tris, int32_t n_gs, uintptr_t stream, pbfb_mesh** out);
+
+/* Flux lam_m on Gamma_m from the trace of u (Sec. 2.3.1, the Gamma_m limit of
+ * Eq. Potential_in_Omega_m): solves V_L lam = (M_m/2 + K_L) u|Gamma_m
+ * - c (l_B/eps_m) <u_coul, psi>, c = coulomb (0 or 1), by preconditioned CG on V_L (dense
+ * float32 V_L^-1 as preconditioner up to 32768 vertices, else its diagonal; far field in float64
+ * for FP64, float-float otherwise) to a relative residual of 1e-13.  x_dev: device, n float64
+ * (only the u part is read); lam_dev: device, n_m float64 (may point into x_dev's lam_m part).
+ * Needs pbfb_set_params, and pbfb_charges_set when coulomb = 1 (PBFB_ERR_STATE).  On a shell
+ * mesh it reproduces a solution's own lam_m (the same Gamma_m row).  PBFB_ERR_GMRES_NOCONV if
+ * CG stalls. */
+int pbfb_gamma_m_flux(pbfb_mesh* mesh, const double* x_dev, int coulomb, double* lam_dev);
+
 /* sizes[0..7] = n_v, n_t, n_m, n_s, n = n_v + n_m + n_s, nnz of the FEM rows,
  * nnz of the Gamma_m and Gamma_s BEM-row sparse parts.  sizes: host. */
 int pbfb_mesh_sizes(const pbfb_mesh* mesh, int64_t* sizes);

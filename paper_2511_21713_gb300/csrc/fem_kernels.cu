@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(RED_T) k_ion_energy(const double* __restrict__
 
 // Values of the sparse operator with J = 0 from the slot descriptors.
 __global__ void k_fill_operator(int nnz, const int* __restrict__ kind, const int* __restrict__ ref,
-                                const double* __restrict__ a1, double eps_m, double eps_s,
+                                const double* __restrict__ a1, const double* __restrict__ a1m, double eps_m,
+                                double eps_s,
                                 const double* __restrict__ mass_m, const double* __restrict__ corrV_m,
                                 const double* __restrict__ corrK_m, const double* __restrict__ mass_s,
                                 const double* __restrict__ corrV_s, const double* __restrict__ corrK_s,
@@ -299,13 +300,15 @@ __global__ void k_fill_operator(int nnz, const int* __restrict__ kind, const int
   int r = ref[s];
   double v = 0.0;
   switch (kind[s]) {
-    case 0: v = eps_s * a1[s]; break;                          // stiffness
+    case 0: v = eps_s * a1[s] + (a1m ? eps_m * a1m[s] : 0.0); break;  // stiffness (Omega_i, Omega_m)
     case 1: v = eps_m * mass_m[r]; break;                      // eps_m R_m' M_m
     case 2: v = -eps_s * mass_s[r]; break;                     // -eps_s R_s' M_s
     case 3: v = 0.5 * mass_m[r] + corrK_m[r]; break;           // (M_m/2 + K_L) near part
     case 4: v = -corrV_m[r]; break;                            // -V_L near part
     case 5: v = 0.5 * mass_s[r] - corrK_s[r]; break;           // (M_s/2 - K_Y) near part
     case 6: v = corrV_s[r]; break;                             // V_Y near part
+    case 7: v = 1.0; break;                                    // lam_m rows of Eq. fembem_matrix's
+                                                               // solve (Gamma_m interior)
   }
   base[s] = v;
 }
@@ -314,15 +317,16 @@ inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-int launch_tet_volumes(Mesh* m) {
-  k_tet_volumes<<<blocks_for(m->nt, 256), 256, 0, m->stream>>>(m->xyz.p, m->nv, m->tets.p, m->nt, m->vol.p);
+int launch_tet_volumes(Mesh* m, const int* tets, int64_t nt, double* vol) {
+  if (nt == 0) return PBFB_OK;
+  k_tet_volumes<<<blocks_for(nt, 256), 256, 0, m->stream>>>(m->xyz.p, m->nv, tets, nt, vol);
   PB_LAUNCHED(m);
   return PBFB_OK;
 }
 
-int launch_stiffness_local(Mesh* m, double* loc10) {
-  k_stiffness_local<<<blocks_for(m->nt, 256), 256, 0, m->stream>>>(m->xyz.p, m->nv, m->tets.p, m->nt, m->vol.p,
-                                                                    loc10);
+int launch_stiffness_local(Mesh* m, const int* tets, int64_t nt, const double* vol, double* loc10) {
+  if (nt == 0) return PBFB_OK;
+  k_stiffness_local<<<blocks_for(nt, 256), 256, 0, m->stream>>>(m->xyz.p, m->nv, tets, nt, vol, loc10);
   PB_LAUNCHED(m);
   return PBFB_OK;
 }
@@ -403,7 +407,7 @@ int launch_ion_energy(Mesh* m, const double* u, double* out_dev) {
 
 int launch_fill_operator(Mesh* m) {
   k_fill_operator<<<blocks_for(m->snnz, 256), 256, 0, m->stream>>>(
-      m->snnz, m->s_kind.p, m->s_ref.p, m->a1.p, m->eps_m, m->eps_s, m->sm.mass.p, m->sm.corrV.p, m->sm.corrK.p,
+      m->snnz, m->s_kind.p, m->s_ref.p, m->a1.p, m->full ? m->a1m.p : nullptr, m->eps_m, m->eps_s, m->sm.mass.p, m->sm.corrV.p, m->sm.corrK.p,
       m->ss.mass.p, m->ss.corrV.p, m->ss.corrK.p, m->s_base.p);
   PB_LAUNCHED(m);
   return PBFB_OK;

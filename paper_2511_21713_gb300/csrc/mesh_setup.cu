@@ -307,8 +307,10 @@ void set_error(const char* fmt, ...) {
 const char* last_error() { return g_err.c_str(); }
 
 // Validation of the shell mesh and its two boundary surfaces (host).
+// With region (per tet 0 = Omega_m, 1 = Omega_i), Gamma_m must be the interface between the two
+// regions (interior faces, normal into Omega_i) and Gamma_s the whole boundary.
 static int validate(const double* xyz, int nv, const int* tets, int64_t nt, const int* gm, int ngm, const int* gs,
-                    int ngs) {
+                    int ngs, const int* region) {
   if (!xyz || !tets || !gm || !gs || nv < 4 || nt < 1 || ngm < 4 || ngs < 4) {
     set_error("mesh_create: empty or missing arrays");
     return PBFB_ERR_INVALID;
@@ -327,6 +329,20 @@ static int validate(const double* xyz, int nv, const int* tets, int64_t nt, cons
       set_error("mesh_create: tet vertex id out of range");
       return PBFB_ERR_INVALID;
     }
+  if (region) {
+    int64_t cnt[2] = {0, 0};
+    for (int64_t t = 0; t < nt; ++t) {
+      if (region[t] != 0 && region[t] != 1) {
+        set_error("mesh_create: tet region must be 0 (Omega_m) or 1 (Omega_i)");
+        return PBFB_ERR_INVALID;
+      }
+      cnt[region[t]]++;
+    }
+    if (!cnt[0] || !cnt[1]) {
+      set_error("mesh_create: both Omega_m and Omega_i need tets");
+      return PBFB_ERR_INVALID;
+    }
+  }
   for (int i = 0; i < 3 * ngm; ++i)
     if (gm[i] < 0 || gm[i] >= nv) {
       set_error("mesh_create: Gamma_m vertex id out of range");
@@ -371,7 +387,7 @@ static int validate(const double* xyz, int nv, const int* tets, int64_t nt, cons
   for (int v = 0; v < nv; ++v) std::sort(ford.begin() + fptr[v], ford.begin() + fptr[v + 1], face_less);
   // per sorted face position: multiplicity of its triple (1 boundary, 2 interior)
   std::vector<int> fcount(ford.size(), 0);
-  size_t nb = 0;
+  size_t nb = 0, nif = 0;
   for (size_t a = 0; a < ford.size();) {
     size_t b = a + 1;
     while (b < ford.size() && fv[ford[b]] == fv[ford[a]]) ++b;
@@ -380,11 +396,17 @@ static int validate(const double* xyz, int nv, const int* tets, int64_t nt, cons
       return PBFB_ERR_INVALID;
     }
     if (b - a == 1) nb++;
+    if (b - a == 2 && region && region[ford[a] / 4] != region[ford[a + 1] / 4]) nif++;
     for (size_t c = a; c < b; ++c) fcount[c] = (int)(b - a);
     a = b;
   }
-  if (nb != (size_t)ngm + (size_t)ngs) {
+  if (!region && nb != (size_t)ngm + (size_t)ngs) {
     set_error("mesh_create: %zu boundary faces but %d + %d surface triangles", nb, ngm, ngs);
+    return PBFB_ERR_INVALID;
+  }
+  if (region && (nb != (size_t)ngs || nif != (size_t)ngm)) {
+    set_error("mesh_create: %zu boundary faces and %zu Omega_m/Omega_i faces but %d Gamma_s and %d Gamma_m "
+              "triangles", nb, nif, ngs, ngm);
     return PBFB_ERR_INVALID;
   }
   // position in ford of the boundary face with this sorted triple, or -1
@@ -408,14 +430,21 @@ static int validate(const double* xyz, int nv, const int* tets, int64_t nt, cons
       std::array<int, 3> f = {F[0], F[1], F[2]};
       std::sort(f.begin(), f.end());
       const long long pos = find_face(f);
-      if (pos < 0 || fcount[pos] != 1) {
+      const bool interface = region && surf == 0;  // Gamma_m between the regions
+      if (interface) {
+        if (pos < 0 || fcount[pos] != 2 || region[ford[pos] / 4] == region[ford[pos + 1] / 4]) {
+          set_error("mesh_create: Gamma_m triangle %d is not a face between Omega_m and Omega_i tets", t);
+          return PBFB_ERR_INVALID;
+        }
+      } else if (pos < 0 || fcount[pos] != 1) {
         set_error("mesh_create: surface triangle %d of %s is not a boundary face of the tets", t,
                   surf == 0 ? "Gamma_m" : "Gamma_s");
         return PBFB_ERR_INVALID;
       }
       fcount[pos] = 3;  // claimed
-      // orientation: the opposite tet vertex lies on the positive side for Gamma_m
-      const int fid = ford[pos];
+      // orientation: the opposite tet vertex lies on the positive side for Gamma_m (of the
+      // Omega_i tet for an interface), on the negative side for Gamma_s
+      const int fid = interface && region[ford[pos] / 4] != 1 ? ford[pos + 1] : ford[pos];
       int o = tets[fid];
       double a[3], b[3], c[3];
       for (int d = 0; d < 3; ++d) {
@@ -452,14 +481,136 @@ static int validate(const double* xyz, int nv, const int* tets, int64_t nt, cons
   return PBFB_OK;
 }
 
+// Uniform grid over the bounding boxes of the Omega_m tets (about four tets per cell), each cell
+// listing, in ascending order, the tets whose box meets it: a point's candidates are its cell's.
+static void build_charge_grid(Mesh* m, const std::vector<int>& tm) {
+  const int64_t nt = (int64_t)tm.size() / 4;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t k = 0; k < 4 * nt; ++k)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], m->grid_xyz[3 * (size_t)tm[k] + d]);
+      hi[d] = std::max(hi[d], m->grid_xyz[3 * (size_t)tm[k] + d]);
+    }
+  double vol = 1.0;
+  for (int d = 0; d < 3; ++d) vol *= std::max(hi[d] - lo[d], 1e-12);
+  double h = std::cbrt(vol / std::max<int64_t>(1, nt / 4));
+  int dim[3];
+  for (int d = 0; d < 3; ++d) dim[d] = std::max(1, std::min(1024, (int)std::ceil((hi[d] - lo[d]) / h)));
+  for (int d = 0; d < 3; ++d) {
+    m->cell_lo[d] = lo[d];
+    m->cell_dim[d] = dim[d];
+  }
+  m->cell_h = h;
+  auto cell_range = [&](int64_t t, int* c0, int* c1) {
+    for (int d = 0; d < 3; ++d) {
+      double a = 1e300, b = -1e300;
+      for (int v = 0; v < 4; ++v) {
+        a = std::min(a, m->grid_xyz[3 * (size_t)tm[4 * t + v] + d]);
+        b = std::max(b, m->grid_xyz[3 * (size_t)tm[4 * t + v] + d]);
+      }
+      c0[d] = std::max(0, std::min(dim[d] - 1, (int)std::floor((a - lo[d]) / h)));
+      c1[d] = std::max(0, std::min(dim[d] - 1, (int)std::floor((b - lo[d]) / h)));
+    }
+  };
+  const size_t ncell = (size_t)dim[0] * dim[1] * dim[2];
+  m->cell_ptr.assign(ncell + 1, 0);
+  int c0[3], c1[3];
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int> pos;
+    if (pass == 1) {
+      for (size_t c = 0; c < ncell; ++c) m->cell_ptr[c + 1] += m->cell_ptr[c];
+      m->cell_tet.assign(m->cell_ptr[ncell], 0);
+      pos.assign(m->cell_ptr.begin(), m->cell_ptr.end() - 1);
+    }
+    for (int64_t t = 0; t < nt; ++t) {
+      cell_range(t, c0, c1);
+      for (int i = c0[0]; i <= c1[0]; ++i)
+        for (int j = c0[1]; j <= c1[1]; ++j)
+          for (int k = c0[2]; k <= c1[2]; ++k) {
+            const size_t c = ((size_t)i * dim[1] + j) * dim[2] + k;
+            if (pass == 0)
+              m->cell_ptr[c + 1]++;
+            else
+              m->cell_tet[pos[c]++] = (int)t;
+          }
+    }
+  }
+}
+
+int point_load(Mesh* m, const double* q_xyz, const double* z, int nq, std::vector<double>& rho) {
+  rho.assign(m->nv, 0.0);
+  const std::vector<int>& tm = m->tets_m_h;
+  const std::vector<double>& X = m->grid_xyz;
+  for (int k = 0; k < nq; ++k) {
+    const double* x = q_xyz + 3 * (size_t)k;
+    // the cell, clamped like the tets' boxes (a point outside every box meets no tet there)
+    int c[3];
+    bool finite = true;
+    for (int d = 0; d < 3; ++d) {
+      const double f = std::floor((x[d] - m->cell_lo[d]) / m->cell_h);
+      if (!std::isfinite(f)) finite = false;
+      c[d] = finite ? (int)std::max(0.0, std::min((double)(m->cell_dim[d] - 1), f)) : 0;
+    }
+    int found = -1;
+    double lam[4] = {0, 0, 0, 0};
+    if (finite) {
+      const size_t cell = ((size_t)c[0] * m->cell_dim[1] + c[1]) * m->cell_dim[2] + c[2];
+      for (int q = m->cell_ptr[cell]; q < m->cell_ptr[cell + 1] && found < 0; ++q) {
+        const int t = m->cell_tet[q];
+        const int* T = &tm[4 * (size_t)t];
+        // barycentric coordinates by Cramer's rule on the edge matrix E (columns x_a - x_0)
+        double e[3][3], r[3];
+        for (int d = 0; d < 3; ++d) {
+          for (int a = 0; a < 3; ++a) e[d][a] = X[3 * (size_t)T[a + 1] + d] - X[3 * (size_t)T[0] + d];
+          r[d] = x[d] - X[3 * (size_t)T[0] + d];
+        }
+        auto det3 = [](double a[3][3]) {
+          return a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                 a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+        };
+        const double det = det3(e);
+        double l[4];
+        for (int a = 0; a < 3; ++a) {
+          double ea[3][3];
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) ea[i][j] = j == a ? r[i] : e[i][j];
+          l[a + 1] = det3(ea) / det;
+        }
+        l[0] = 1.0 - l[1] - l[2] - l[3];
+        if (std::min(std::min(l[0], l[1]), std::min(l[2], l[3])) >= -1e-12) {
+          found = t;
+          for (int a = 0; a < 4; ++a) lam[a] = l[a];
+        }
+      }
+    }
+    if (found < 0) {
+      set_error("charges_set: charge %d lies in no tet of Omega_m", k);
+      return PBFB_ERR_INVALID;
+    }
+    for (int a = 0; a < 4; ++a) rho[tm[4 * (size_t)found + a]] += z[k] * lam[a];
+  }
+  return PBFB_OK;
+}
+
 static double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
 int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const int* gm, int ngm, const int* gs,
-                int ngs, cudaStream_t stream, Mesh** out) {
+                int ngs, cudaStream_t stream, Mesh** out, const int* region) {
   auto tc = std::chrono::steady_clock::now();
-  PB_TRY(validate(xyz, nv, tets, nt, gm, ngm, gs, ngs));
+  PB_TRY(validate(xyz, nv, tets, nt, gm, ngm, gs, ngs, region));
+  // tets of Omega_i (all of a shell mesh) and of Omega_m, AoS, in input order
+  std::vector<int> ti_h, tm_h;
+  if (region) {
+    for (int64_t t = 0; t < nt; ++t) {
+      std::vector<int>& dst = region[t] ? ti_h : tm_h;
+      dst.insert(dst.end(), tets + 4 * t, tets + 4 * t + 4);
+    }
+  }
+  const int* ti = region ? ti_h.data() : tets;
+  const int64_t nti = region ? (int64_t)ti_h.size() / 4 : nt;
+  const int64_t ntm = (int64_t)tm_h.size() / 4;
   const double t_validate = ms_since(tc);
   tc = std::chrono::steady_clock::now();
   int ndev = 0;
@@ -477,17 +628,23 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
   cudaGetDevice(&m->dev);
   m->stream = stream;
   m->nv = nv;
-  m->nt = nt;
+  m->nt = nti;
+  m->nt_m = ntm;
+  m->full = region != nullptr;
   std::vector<double> xyz_h(xyz, xyz + 3 * (size_t)nv);
   {
     std::vector<double> soa(3 * (size_t)nv);
     for (int v = 0; v < nv; ++v)
       for (int d = 0; d < 3; ++d) soa[(size_t)d * nv + v] = xyz[3 * (size_t)v + d];
     if ((st = m->xyz.upload(soa.data(), soa.size(), stream))) return fail(st);
-    std::vector<int> tsoa(4 * (size_t)nt);
-    for (int64_t t = 0; t < nt; ++t)
-      for (int a = 0; a < 4; ++a) tsoa[(size_t)a * nt + t] = tets[4 * t + a];
-    if ((st = m->tets.upload(tsoa.data(), tsoa.size(), stream))) return fail(st);
+    for (int r = 0; r < (ntm ? 2 : 1); ++r) {
+      const int* src = r == 0 ? ti : tm_h.data();
+      const int64_t cnt = r == 0 ? nti : ntm;
+      std::vector<int> tsoa(4 * (size_t)cnt);
+      for (int64_t t = 0; t < cnt; ++t)
+        for (int a = 0; a < 4; ++a) tsoa[(size_t)a * cnt + t] = src[4 * t + a];
+      if ((st = (r == 0 ? m->tets : m->tets_m).upload(tsoa.data(), tsoa.size(), stream))) return fail(st);
+    }
   }
   std::vector<int> gmv(gm, gm + 3 * (size_t)ngm), gsv(gs, gs + 3 * (size_t)ngs);
   {
@@ -518,9 +675,13 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
   // ---- sparse-part pattern of the coupled operator
   std::vector<int64_t> keys;
   keys.reserve(16 * (size_t)nt + 4 * (size_t)(sm.cnnz + ss.cnnz));
-  for (int64_t t = 0; t < nt; ++t)
-    for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) keys.push_back(key2(tets[4 * t + a], tets[4 * t + b]));
+  for (int r = 0; r < 2; ++r) {
+    const int* tt = r == 0 ? ti : tm_h.data();
+    const int64_t cnt = r == 0 ? nti : ntm;
+    for (int64_t t = 0; t < cnt; ++t)
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) keys.push_back(key2(tt[4 * t + a], tt[4 * t + b]));
+  }
   // mass pattern (vertices sharing a triangle) for the FEM coupling entries
   auto mass_pairs = [](const Surface& s, std::vector<std::pair<int, int>>& mp) {
     for (int t = 0; t < s.nt; ++t)
@@ -529,18 +690,24 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
     std::sort(mp.begin(), mp.end());
     mp.erase(std::unique(mp.begin(), mp.end()), mp.end());
   };
+  // (an interior Gamma_m couples nothing: its lam_m rows are the identity)
   std::vector<std::pair<int, int>> mpm, mps;
-  mass_pairs(sm, mpm);
+  if (!m->full) mass_pairs(sm, mpm);
   mass_pairs(ss, mps);
   for (auto& e : mpm) keys.push_back(key2(sm.vmap_h[e.first], sm.col0 + e.second));
   for (auto& e : mps) keys.push_back(key2(ss.vmap_h[e.first], ss.col0 + e.second));
-  for (const Surface* s : {&sm, &ss})
+  for (const Surface* s : {&sm, &ss}) {
+    if (m->full && s == &sm) {
+      for (int i = 0; i < s->nv; ++i) keys.push_back(key2(s->col0 + i, s->col0 + i));
+      continue;
+    }
     for (int i = 0; i < s->nv; ++i)
       for (int k = s->c_ptr_h[i]; k < s->c_ptr_h[i + 1]; ++k) {
         int j = s->c_col_h[k];
         keys.push_back(key2(s->col0 + i, s->vmap_h[j]));
         keys.push_back(key2(s->col0 + i, s->col0 + j));
       }
+  }
   {
     // rows by counting sort, then sorted unique columns within each row
     std::vector<int> rk(keys.size()), ck(keys.size());
@@ -579,27 +746,33 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
     return (int)(std::lower_bound(b, e, c) - m->s_col_h.begin());
   };
   std::vector<int> kind(m->snnz, -1), ref(m->snnz, 0);
+  DBuf<int> jm_ptr, jm_idx;  // Omega_m stiffness gather (set-up only)
   {
-    std::vector<int> jk, jv;
-    jk.reserve(16 * (size_t)nt);
-    jv.reserve(16 * (size_t)nt);
-    for (int64_t t = 0; t < nt; ++t)
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) {
-          int sl = slot(tets[4 * t + a], tets[4 * t + b]);
-          kind[sl] = 0;
-          jk.push_back(sl);
-          jv.push_back((int)(sym10(a, b) * nt + t));
-        }
+    // per slot: tet-local entries (k * cnt + t) of the Omega_i tets, and of the Omega_m tets
     std::vector<int> ptr, outv;
-    bucket(jk, jv, m->snnz, ptr, outv);
-    if ((st = m->jg_ptr.upload(ptr.data(), ptr.size(), stream))) return fail(st);
-    if ((st = m->jg_idx.upload(outv.data(), outv.size(), stream))) return fail(st);
+    for (int r = 0; r < (ntm ? 2 : 1); ++r) {
+      const int* tt = r == 0 ? ti : tm_h.data();
+      const int64_t cnt = r == 0 ? nti : ntm;
+      std::vector<int> jk, jv;
+      jk.reserve(16 * (size_t)cnt);
+      jv.reserve(16 * (size_t)cnt);
+      for (int64_t t = 0; t < cnt; ++t)
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            int sl = slot(tt[4 * t + a], tt[4 * t + b]);
+            kind[sl] = 0;
+            jk.push_back(sl);
+            jv.push_back((int)(sym10(a, b) * cnt + t));
+          }
+      bucket(jk, jv, m->snnz, ptr, outv);
+      if ((st = (r == 0 ? m->jg_ptr : jm_ptr).upload(ptr.data(), ptr.size(), stream))) return fail(st);
+      if ((st = (r == 0 ? m->jg_idx : jm_idx).upload(outv.data(), outv.size(), stream))) return fail(st);
+    }
     std::vector<int> nk, nvv;
-    for (int64_t t = 0; t < nt; ++t)
+    for (int64_t t = 0; t < nti; ++t)
       for (int a = 0; a < 4; ++a) {
-        nk.push_back(tets[4 * t + a]);
-        nvv.push_back((int)(a * nt + t));
+        nk.push_back(ti[4 * t + a]);
+        nvv.push_back((int)(a * nti + t));
       }
     bucket(nk, nvv, nv, ptr, outv);
     if ((st = m->ng_ptr.upload(ptr.data(), ptr.size(), stream))) return fail(st);
@@ -644,6 +817,10 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
   }
   for (int si = 0; si < 2; ++si) {
     const Surface& s = si == 0 ? sm : ss;
+    if (m->full && si == 0) {
+      for (int i = 0; i < s.nv; ++i) kind[slot(s.col0 + i, s.col0 + i)] = 7;
+      continue;
+    }
     for (int i = 0; i < s.nv; ++i)
       for (int k = s.c_ptr_h[i]; k < s.c_ptr_h[i + 1]; ++k) {
         int j = s.c_col_h[k];
@@ -667,8 +844,8 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
   if ((st = m->s_val.alloc(m->snnz))) return fail(st);
   if ((st = m->s_base.alloc(m->snnz))) return fail(st);
   if ((st = m->a1.alloc(m->snnz))) return fail(st);
-  if ((st = m->vol.alloc(nt))) return fail(st);
-  if ((st = m->tloc.alloc(14 * (size_t)nt))) return fail(st);
+  if ((st = m->vol.alloc(nti))) return fail(st);
+  if ((st = m->tloc.alloc(14 * (size_t)nti))) return fail(st);
   if ((st = m->red.alloc((size_t)152 * 7 * 64 + 1024))) return fail(st);
   if ((st = m->scal.alloc(8192))) return fail(st);
   if ((st = m->red2.alloc(9 * (size_t)std::max(sm.npair, ss.npair)))) return fail(st);
@@ -679,9 +856,20 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
   m->setup_ms[2] = ms_since(tc);
   tc = std::chrono::steady_clock::now();
   // ---- device geometry and constant operator parts
-  if ((st = launch_tet_volumes(m))) return fail(st);
-  if ((st = launch_stiffness_local(m, m->tloc.p))) return fail(st);
+  if ((st = launch_tet_volumes(m, m->tets.p, m->nt, m->vol.p))) return fail(st);
+  if ((st = launch_stiffness_local(m, m->tets.p, m->nt, m->vol.p, m->tloc.p))) return fail(st);
   if ((st = launch_gather(m, m->snnz, m->jg_ptr.p, m->jg_idx.p, m->tloc.p, nullptr, 1.0, m->a1.p))) return fail(st);
+  DBuf<double> locm;
+  if (m->full) {
+    if ((st = m->vol_m.alloc(ntm)) || (st = m->a1m.alloc(m->snnz)) || (st = locm.alloc(10 * (size_t)ntm)))
+      return fail(st);
+    if ((st = launch_tet_volumes(m, m->tets_m.p, ntm, m->vol_m.p))) return fail(st);
+    if ((st = launch_stiffness_local(m, m->tets_m.p, ntm, m->vol_m.p, locm.p))) return fail(st);
+    if ((st = launch_gather(m, m->snnz, jm_ptr.p, jm_idx.p, locm.p, nullptr, 1.0, m->a1m.p))) return fail(st);
+    m->grid_xyz.swap(xyz_h);
+    build_charge_grid(m, tm_h);
+    m->tets_m_h.swap(tm_h);
+  }
   if ((st = launch_surface_geometry(m, &sm))) return fail(st);
   if ((st = launch_surface_geometry(m, &ss))) return fail(st);
   if ((st = launch_pair_corrections(m, &sm, 0.0))) return fail(st);

@@ -213,19 +213,40 @@ struct Mesh {
   DBuf<float2> ff_tab;      // float-float exp table of the Yukawa kernel
   double nbody_flops = 0.0;  // float32 far-field flops issued (18 per Laplace pair, 24 per Yukawa pair)
   double setup_ms[4] = {0, 0, 0, 0};  // mesh_create: validation, surfaces, operator pattern, device set-up
+  // FEM over Omega_m and Omega_i (Sec. 2.2, Eq. fembem_matrix): `tets` holds the tets of Omega_i
+  // (the nonlinear term and the ion energy), tets_m those of Omega_m (eps_m, no ions).  Gamma_m is
+  // an interior interface: its lam_m rows are the identity during the solve, and lam_m is filled
+  // afterwards from the Gamma_m boundary integral equation of Sec. 2.3.1
+  bool full = false;
+  int64_t nt_m = 0;
+  DBuf<int> tets_m;                 // 4*nt_m SoA
+  DBuf<double> vol_m, a1m;          // Omega_m volumes; per slot: its stiffness (eps_m applied at fill)
+  std::vector<double> grid_xyz;     // 3*nv AoS (host), for locating the charges
+  std::vector<int> tets_m_h;        // 4*nt_m AoS (host)
+  std::vector<int> cell_ptr, cell_tet;  // uniform grid over the Omega_m tets' bounding boxes
+  double cell_lo[3] = {0, 0, 0}, cell_h = 1.0;
+  int cell_dim[3] = {0, 0, 0};
+  DBuf<double> rho;                 // nv: sum_k z_k v_i(x_k) (no 4 pi l_B)
+  DBuf<double> pp_val;              // Gamma_m correction pattern: M_m / 2 + corrK_m
+  DBuf<double> pp_work;             // post-process vectors: 6 * nm
   ~Mesh() {
     if (pcg_graph) cudaGraphExecDestroy(pcg_graph);
   }
 };
 
 // ---- whole-solve entry points shared by the C ABI, the batch call and the server
+// region: null for a shell mesh (every tet in Omega_i, Gamma_m a boundary), else per tet 0 (Omega_m)
+// or 1 (Omega_i) with Gamma_m the interface between them
 int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const int* gm, int ngm, const int* gs,
-                int ngs, cudaStream_t stream, Mesh** out);
+                int ngs, cudaStream_t stream, Mesh** out, const int* region = nullptr);
 void mesh_destroy(Mesh* m);
 int charges_set(Mesh* m, const double* xyz, const double* z, int nq);
 int solve_mesh(Mesh* m, double eps_in, double eps_out, double kappa, double T, const pbfb_newton_opts* opts,
                double* x_out_dev, pbfb_result* res);
 size_t estimate_bytes(int64_t nv, int64_t nt, int64_t ngm, int64_t ngs, int restart);
+// sum_k z_k v_i(x_k) over the Omega_m tets (a mesh with Omega_m); PBFB_ERR_INVALID for a charge
+// in none of them
+int point_load(Mesh* m, const double* q_xyz, const double* z, int nq, std::vector<double>& rho);
 }  // namespace pbfb
 pbfb::Mesh* pbfb_mesh_internal(pbfb_mesh* h);
 namespace pbfb {
@@ -234,8 +255,8 @@ namespace pbfb {
 int init_quadrature();
 
 // ---- fem_kernels.cu
-int launch_tet_volumes(Mesh* m);
-int launch_stiffness_local(Mesh* m, double* loc10);
+int launch_tet_volumes(Mesh* m, const int* tets, int64_t nt, double* vol);
+int launch_stiffness_local(Mesh* m, const int* tets, int64_t nt, const double* vol, double* loc10);
 int launch_gather(Mesh* m, int nslots, const int* ptr, const int* idx, const double* local,
                   const double* base, double scale, double* out);
 int launch_element_nl(Mesh* m, int scheme, const double* u, double coef, double* loc);

@@ -157,7 +157,7 @@ __global__ void k_jacobi(int nv, int nm, int ns, const int* __restrict__ ptr, co
     for (int k = ptr[r]; k < ptr[r + 1]; ++k)
       if (col[k] == r) d = val[k];
   } else if (r < nv + nm) {
-    d = -dVm[r - nv];
+    d = dVm ? -dVm[r - nv] : 1.0;  // no dVm: identity rows of an interior Gamma_m
   } else {
     d = dVs[r - nv - nm];
   }
@@ -395,6 +395,16 @@ __global__ void k_sub_load(int nv, const double* __restrict__ N, double* __restr
   if (i < nv) d[i] -= N[i];
 }
 
+__global__ void k_trace(int ns, const int* __restrict__ vmap, const double* __restrict__ u, double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ns) out[i] = u[vmap[i]];
+}
+
+__global__ void k_div(int n, const double* __restrict__ x, const double* __restrict__ d, double* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x[i] / d[i];
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ small BLAS
@@ -504,8 +514,9 @@ static int apply_prec(Mesh* m, const double* x, double* y, int precision) {
   PB_TRY(launch_spmv(m, x, y));
   Surface* sm = &m->sm;
   Surface* ss = &m->ss;
-  // Gamma_m rows: (M/2 + K_L) u - V_L lam_m; Gamma_s rows: (M/2 - K_Y) u + V_Y lam_s
-  PB_TRY(launch_bem_far(m, sm, x, x + sm->col0, -1.0, 1.0, 0.0, precision, y + sm->col0, true));
+  // Gamma_m rows: (M/2 + K_L) u - V_L lam_m (the identity when Gamma_m is interior); Gamma_s
+  // rows: (M/2 - K_Y) u + V_Y lam_s
+  if (!m->full) PB_TRY(launch_bem_far(m, sm, x, x + sm->col0, -1.0, 1.0, 0.0, precision, y + sm->col0, true));
   PB_TRY(launch_bem_far(m, ss, x, x + ss->col0, 1.0, -1.0, m->kappa, precision, y + ss->col0, true));
   return PBFB_OK;
 }
@@ -519,7 +530,8 @@ int ensure(DBuf<double>& b, size_t n) {
 
 static int jacobi(Mesh* m, double* dinv) {
   k_jacobi<<<blocks_for(m->n, 256), 256, 0, m->stream>>>(m->nv, m->sm.nv, m->ss.nv, m->s_ptr.p, m->s_col.p,
-                                                          m->s_val.p, m->sm.diagV.p, m->ss.diagV.p, dinv);
+                                                          m->s_val.p, m->full ? nullptr : m->sm.diagV.p,
+                                                          m->ss.diagV.p, dinv);
   PB_LAUNCHED(m);
   return PBFB_OK;
 }
@@ -537,7 +549,7 @@ static int jacobi(Mesh* m, double* dinv) {
 // once per mesh, and for Gamma_s again whenever kappa changes) on surfaces of at most
 // DENSE_V_MAX vertices, the diagonal otherwise.
 static int prepare_block_precond(Mesh* m, bool dense) {
-  m->dense_m = dense && m->sm.nv <= DENSE_V_MAX;
+  m->dense_m = dense && !m->full && m->sm.nv <= DENSE_V_MAX;
   m->dense_s = dense && m->ss.nv <= DENSE_V_MAX;
   if (m->dense_m && !m->sm.vinv_ok) PB_TRY(build_dense_single_layer(m, &m->sm, 0.0, true));
   if (m->dense_s && (!m->ss.vinv_ok || m->ss.vinv_kappa != m->kappa))
@@ -1116,6 +1128,89 @@ static int omega_search(Mesh* m, int scheme, const double* u, const double* du, 
 
 // ------------------------------------------------------------------ energy
 
+// Flux lam on Gamma_m from the trace of u (Sec. 2.3.1): V_L lam = (M_m/2 + K_L) u|Gamma_m
+// - c (l_B/eps_m) <u_coul, psi>, c = 1 with the Coulomb term and 0 without.  Flexible
+// preconditioned CG on V_L (symmetric positive definite), preconditioned by the dense float32
+// V_L^-1 (its diagonal above DENSE_V_MAX vertices), far field in float64 (FP64) or float-float
+// (MIXED), to a relative residual of 1e-13.  x is a full vector (only its u part is read); lam
+// may alias x's lam_m slots.
+static int gamma_m_flux(Mesh* m, const double* x, bool coulomb, double* lam) {
+  Surface* s = &m->sm;
+  const int nm = s->nv;
+  const int prec = m->precision == PBFB_FP64 ? PBFB_FP64 : PBFB_FLOAT2;
+  if (coulomb && !m->charges) {
+    set_error("Gamma_m flux: charges not set");
+    return PBFB_ERR_STATE;
+  }
+  PB_TRY(ensure(m->pp_val, s->cnnz));
+  PB_TRY(ensure(m->pp_work, 7 * (size_t)nm));
+  double* rhs = m->pp_work.p;
+  double* r = rhs + nm;
+  double* z = rhs + 2 * (size_t)nm;
+  double* p = rhs + 3 * (size_t)nm;
+  double* q = rhs + 4 * (size_t)nm;
+  double* ug = rhs + 5 * (size_t)nm;
+  double* rold = rhs + 6 * (size_t)nm;
+  const bool dense = nm <= DENSE_V_MAX;
+  if (dense && !s->vinv_ok) PB_TRY(build_dense_single_layer(m, s, 0.0, true));
+  auto precond = [&](const double* v, double* out) -> int {
+    if (dense) return launch_dense_apply(m, s, -1.0, v, out);  // the stored matrix is -V^-1
+    k_div<<<blocks_for(nm, 256), 256, 0, m->stream>>>(nm, v, s->diagV.p, out);
+    PB_LAUNCHED(m);
+    return PBFB_OK;
+  };
+  auto applyV = [&](const double* v, double* out) -> int {
+    PB_TRY(launch_bem_far(m, s, v, v, 1.0, 0.0, 0.0, prec, out, false));
+    return launch_csr_spmv(m, nm, s->c_ptr.p, s->c_col.p, s->corrV.p, v, out, true);
+  };
+  // right-hand side
+  PB_TRY(launch_axpby(m, s->cnnz, 0.5, s->mass.p, 1.0, s->corrK.p, m->pp_val.p));
+  k_trace<<<blocks_for(nm, 256), 256, 0, m->stream>>>(nm, s->vmap.p, x, ug);
+  PB_LAUNCHED(m);
+  PB_TRY(launch_bem_far(m, s, x, x + s->col0, 0.0, 1.0, 0.0, prec, rhs, false));
+  PB_TRY(launch_csr_spmv(m, nm, s->c_ptr.p, s->c_col.p, m->pp_val.p, ug, rhs, true));
+  if (coulomb) PB_TRY(launch_axpby(m, nm, 1.0, rhs, -m->lB / m->eps_m, m->coul.p, rhs));
+  double bb;
+  PB_TRY(dot(m, rhs, rhs, nm, &bb));
+  PB_CUDA(cudaMemsetAsync(lam, 0, nm * sizeof(double), m->stream));
+  if (!(bb > 0)) {
+    if (!std::isfinite(bb)) {
+      set_error("Gamma_m flux: non-finite right-hand side");
+      return PBFB_ERR_NONFINITE;
+    }
+    return PBFB_OK;
+  }
+  PB_CUDA(cudaMemcpyAsync(r, rhs, nm * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  PB_TRY(precond(r, z));
+  PB_CUDA(cudaMemcpyAsync(p, z, nm * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  double rz;
+  PB_TRY(dot(m, r, z, nm, &rz));
+  for (int it = 0; it < 500; ++it) {
+    PB_TRY(applyV(p, q));
+    double pq;
+    PB_TRY(dot(m, p, q, nm, &pq));
+    if (!(pq > 0)) break;
+    const double alpha = rz / pq;
+    PB_TRY(launch_axpby(m, nm, alpha, p, 1.0, lam, lam));
+    PB_CUDA(cudaMemcpyAsync(rold, r, nm * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+    PB_TRY(launch_axpby(m, nm, -alpha, q, 1.0, r, r));
+    double rr;
+    PB_TRY(dot(m, r, r, nm, &rr));
+    if (!std::isfinite(rr)) break;
+    if (rr <= 1e-26 * bb) return PBFB_OK;
+    // flexible (Polak-Ribiere) beta: robust to the float32 preconditioner's asymmetry
+    PB_TRY(precond(r, z));
+    double rz_new, roz;
+    PB_TRY(dot(m, r, z, nm, &rz_new));
+    PB_TRY(dot(m, rold, z, nm, &roz));
+    const double beta = (rz_new - roz) / rz;
+    rz = rz_new;
+    PB_TRY(launch_axpby(m, nm, 1.0, z, beta, p, p));
+  }
+  set_error("Gamma_m flux: CG on V_L did not reach a relative residual of 1e-13");
+  return PBFB_ERR_GMRES_NOCONV;
+}
+
 static int energy(Mesh* m, const double* xL, const double* xNL, double* out4) {
   PB_TRY(ensure(m->tmp, m->n));
   PB_TRY(ensure(m->urb, 2 * (size_t)m->nq));
@@ -1180,12 +1275,17 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   const int n = m->n, nv = m->nv;
   for (auto* b : {&m->xL, &m->xNL, &m->phi, &m->cvec, &m->dvec, &m->du, &m->pvec, &m->Nvec, &m->tmp, &m->bvec})
     PB_TRY(ensure(*b, n));
-  // right-hand side [0; (l_B/eps_m) <u_coul, psi>; 0]
+  // right-hand side [0; (l_B/eps_m) <u_coul, psi>; 0], or with Omega_m meshed the point loads
+  // [4 pi l_B sum_k z_k v_i(x_k); 0; 0] (Eq. fembem_matrix)
   double* bvec = m->bvec.p;
   PB_CUDA(cudaMemsetAsync(bvec, 0, n * sizeof(double), m->stream));
-  k_set_rhs<<<blocks_for(m->sm.nv, 256), 256, 0, m->stream>>>(m->sm.nv, m->sm.col0, m->lB / m->eps_m, m->coul.p,
-                                                               bvec);
-  PB_LAUNCHED(m);
+  if (m->full) {
+    PB_TRY(launch_axpby(m, nv, 4.0 * M_PI * m->lB, m->rho.p, 0.0, nullptr, bvec));
+  } else {
+    k_set_rhs<<<blocks_for(m->sm.nv, 256), 256, 0, m->stream>>>(m->sm.nv, m->sm.col0, m->lB / m->eps_m, m->coul.p,
+                                                                 bvec);
+    PB_LAUNCHED(m);
+  }
   auto t0 = clk::now();
   double tol = o.tol_gmres0;
   // linear part: J = eps_s kappa^2 M (F' = 1)
@@ -1320,6 +1420,12 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
     if (res) *res = R;
     return R.status;
   }
+  if (m->full) {
+    // lam_m from the Gamma_m equation of Sec. 2.3.1, affine in u: the linear part takes the
+    // Coulomb term, the nonlinear part none, so that x_L + x_NL carries lam_m of the solution
+    PB_TRY(gamma_m_flux(m, m->xL.p, true, m->xL.p + m->sm.col0));
+    PB_TRY(gamma_m_flux(m, m->xNL.p, false, m->xNL.p + m->sm.col0));
+  }
   double E[4];
   PB_TRY(energy(m, m->xL.p, m->xNL.p, E));
   auto t3 = clk::now();
@@ -1361,6 +1467,12 @@ int charges_set(Mesh* m, const double* xyz, const double* z, int n_q) {
       set_error("charges_set: non-finite charge");
       return PBFB_ERR_INVALID;
     }
+  }
+  if (m->full) {
+    // point loads of the charges on the Omega_m tets (Eq. fembem_matrix's right-hand side)
+    std::vector<double> rho;
+    PB_TRY(point_load(m, xyz, z, n_q, rho));
+    PB_TRY(m->rho.upload(rho.data(), rho.size(), m->stream));
   }
   PB_TRY(m->qxyz.upload(soa.data(), soa.size(), m->stream));
   PB_TRY(m->qz.upload(z, n_q, m->stream));
@@ -1458,6 +1570,38 @@ int pbfb_mesh_create(const double* xyz, int32_t n_v, const int32_t* tets, int64_
   return PBFB_OK;
 }
 
+int pbfb_mesh_create_full(const double* xyz, int32_t n_v, const int32_t* tets, int64_t n_t,
+                          const int32_t* tet_region, const int32_t* gm_tris, int32_t n_gm, const int32_t* gs_tris,
+                          int32_t n_gs, uintptr_t stream, pbfb_mesh** out) {
+  pbfb::set_error("");
+  if (!out || !tet_region) {
+    pbfb::set_error("mesh_create_full: out or tet_region is NULL");
+    return PBFB_ERR_INVALID;
+  }
+  *out = nullptr;
+  Mesh* m = nullptr;
+  int st = pbfb::mesh_create(xyz, n_v, tets, n_t, gm_tris, n_gm, gs_tris, n_gs, (cudaStream_t)stream, &m,
+                             tet_region);
+  if (st) return st;
+  *out = new pbfb_mesh{m};
+  return PBFB_OK;
+}
+
+int pbfb_gamma_m_flux(pbfb_mesh* h, const double* x_dev, int coulomb, double* lam_dev) {
+  PB_HANDLE(h);
+  if (!m->params) {
+    pbfb::set_error("call pbfb_set_params first");
+    return PBFB_ERR_STATE;
+  }
+  if (!x_dev || !lam_dev || (coulomb != 0 && coulomb != 1)) {
+    pbfb::set_error("gamma_m_flux: bad argument");
+    return PBFB_ERR_INVALID;
+  }
+  int st = pbfb::gamma_m_flux(m, x_dev, coulomb != 0, lam_dev);
+  if (st) return st;
+  return cudaStreamSynchronize(m->stream) == cudaSuccess ? PBFB_OK : PBFB_ERR_CUDA;
+}
+
 int pbfb_mesh_sizes(const pbfb_mesh* h, int64_t* s) {
   if (!h || !h->m || !s) {
     pbfb::set_error("mesh_sizes: null argument");
@@ -1465,7 +1609,7 @@ int pbfb_mesh_sizes(const pbfb_mesh* h, int64_t* s) {
   }
   const Mesh* m = h->m;
   s[0] = m->nv;
-  s[1] = m->nt;
+  s[1] = m->nt + m->nt_m;
   s[2] = m->sm.nv;
   s[3] = m->ss.nv;
   s[4] = m->n;

@@ -34,7 +34,8 @@ EXPORTS = [
     "pbfb_energy", "pbfb_profile", "pbfb_bem_apply_noalloc", "pbfb_set_tuning",
     "pbfb_server_create", "pbfb_server_submit", "pbfb_server_poll", "pbfb_server_stats",
     "pbfb_server_destroy", "pbfb_solve_batch", "pbfb_single_layer_dense",
-    "pbfb_get_tuning", "pbfb_apply_tuning", "pbfb_autotune",
+    "pbfb_get_tuning", "pbfb_apply_tuning", "pbfb_autotune", "pbfb_mesh_create_full",
+    "pbfb_gamma_m_flux",
 ]
 
 
@@ -129,6 +130,8 @@ def load():
     sig = {
         "pbfb_default_opts": (None, [ctypes.POINTER(NewtonOpts)]),
         "pbfb_mesh_create": (I, [P, I, P, I64, P, I, P, I, U, ctypes.POINTER(P)]),
+        "pbfb_mesh_create_full": (I, [P, I, P, I64, P, P, I, P, I, U, ctypes.POINTER(P)]),
+        "pbfb_gamma_m_flux": (I, [P, P, I, P]),
         "pbfb_mesh_sizes": (I, [P, P]),
         "pbfb_surface_vertices": (I, [P, I, P]),
         "pbfb_charges_set": (I, [P, P, P, I]),
@@ -203,15 +206,24 @@ def current_stream() -> int:
 class Mesh:
     """Owner of a pbfb_mesh handle."""
 
-    def __init__(self, xyz, tets, gm_tris, gs_tris, stream=None):
+    def __init__(self, xyz, tets, gm_tris, gs_tris, stream=None, tet_region=None):
+        """tet_region None: a shell mesh of Omega_i (pbfb_mesh_create); else per tet 0 (Omega_m)
+        or 1 (Omega_i), the mesh of both regions (pbfb_mesh_create_full)."""
         L = load()
         self._keep = [np.ascontiguousarray(xyz, np.float64), np.ascontiguousarray(tets, np.int32),
                       np.ascontiguousarray(gm_tris, np.int32), np.ascontiguousarray(gs_tris, np.int32)]
         x, t, gm, gs = self._keep
         h = ctypes.c_void_p()
         s = current_stream() if stream is None else stream
-        _check(L.pbfb_mesh_create(_ptr(x), x.shape[0], _ptr(t), t.shape[0], _ptr(gm), gm.shape[0],
-                                  _ptr(gs), gs.shape[0], s, ctypes.byref(h)))
+        self.full = tet_region is not None
+        if self.full:
+            reg = np.ascontiguousarray(tet_region, np.int32)
+            self._keep.append(reg)
+            _check(L.pbfb_mesh_create_full(_ptr(x), x.shape[0], _ptr(t), t.shape[0], _ptr(reg), _ptr(gm),
+                                           gm.shape[0], _ptr(gs), gs.shape[0], s, ctypes.byref(h)))
+        else:
+            _check(L.pbfb_mesh_create(_ptr(x), x.shape[0], _ptr(t), t.shape[0], _ptr(gm), gm.shape[0],
+                                      _ptr(gs), gs.shape[0], s, ctypes.byref(h)))
         self.h = h
         sz = np.zeros(8, np.int64)
         _check(L.pbfb_mesh_sizes(self.h, _ptr(sz)))
@@ -219,7 +231,8 @@ class Mesh:
 
     @classmethod
     def from_case(cls, case, stream=None):
-        return cls(case.xyz, case.tets, case.gm_tris, case.gs_tris, stream)
+        return cls(case.xyz, case.tets, case.gm_tris, case.gs_tris, stream,
+                   tet_region=getattr(case, "tet_region", None))
 
     def surface_vertices(self, which):
         out = np.zeros(self.n_m if which == GAMMA_M else self.n_s, np.int32)
@@ -267,6 +280,10 @@ class Mesh:
 
     def bem_apply(self, which, op, x_dev, y_dev):
         _check(load().pbfb_bem_apply(self.h, which, op, _ptr(x_dev), _ptr(y_dev)))
+
+    def gamma_m_flux(self, x_dev, coulomb, lam_dev):
+        """lam_m from the trace of u on Gamma_m (pbfb_gamma_m_flux); x_dev n-long, lam_dev n_m."""
+        _check(load().pbfb_gamma_m_flux(self.h, _ptr(x_dev), int(coulomb), _ptr(lam_dev)))
 
     def bem_apply_noalloc(self, which, op, x_dev, y_dev):
         """pbfb_bem_apply with its working memory in the library's fixed device array

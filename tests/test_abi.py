@@ -83,6 +83,50 @@ def test_mesh_validation_on_host(lib, tiny_case):
     assert pbfb.ERRORS[1] == "INVALID"
 
 
+def _create_full(lib, xyz, tets, region, gm, gs):
+    h = ctypes.c_void_p()
+    xyz = np.ascontiguousarray(xyz, np.float64)
+    tets = np.ascontiguousarray(tets, np.int32)
+    region = np.ascontiguousarray(region, np.int32)
+    gm = np.ascontiguousarray(gm, np.int32)
+    gs = np.ascontiguousarray(gs, np.int32)
+    code = lib.pbfb_mesh_create_full(xyz.ctypes.data, xyz.shape[0], tets.ctypes.data, tets.shape[0],
+                                     region.ctypes.data, gm.ctypes.data, gm.shape[0], gs.ctypes.data,
+                                     gs.shape[0], 0, ctypes.byref(h))
+    return code, h
+
+
+def test_full_mesh_validation_on_host(lib, tiny_solute_case):
+    import torch
+    c = tiny_solute_case
+    r = c.tet_region
+    # Gamma_m is interior here: as a shell mesh the boundary does not match the surfaces
+    code, _ = _create(lib, c.xyz, c.tets, c.gm_tris, c.gs_tris)
+    assert code == 1
+    bad = r.copy()
+    bad[3] = 2
+    code, _ = _create_full(lib, c.xyz, c.tets, bad, c.gm_tris, c.gs_tris)
+    assert code == 1 and b"region" in lib.pbfb_last_error()
+    code, _ = _create_full(lib, c.xyz, c.tets, np.ones_like(r), c.gm_tris, c.gs_tris)
+    assert code == 1 and b"both" in lib.pbfb_last_error()
+    # Gamma_m pointing into Omega_m, a missing interface triangle, a region flip that moves the
+    # interface, and the surfaces swapped
+    code, _ = _create_full(lib, c.xyz, c.tets, r, c.gm_tris[:, [0, 2, 1]], c.gs_tris)
+    assert code == 1 and b"orientation" in lib.pbfb_last_error()
+    code, _ = _create_full(lib, c.xyz, c.tets, r, c.gm_tris[1:], c.gs_tris)
+    assert code == 1
+    flip = r.copy()
+    flip[np.nonzero(r == 0)[0][-1]] = 1
+    code, _ = _create_full(lib, c.xyz, c.tets, flip, c.gm_tris, c.gs_tris)
+    assert code == 1
+    code, _ = _create_full(lib, c.xyz, c.tets, r, c.gs_tris, c.gm_tris)
+    assert code == 1
+    if not torch.cuda.is_available():
+        # the valid mesh passes validation and then needs the GPU: no CPU fallback
+        code, h = _create_full(lib, c.xyz, c.tets, r, c.gm_tris, c.gs_tris)
+        assert code == 2 and not h.value
+
+
 def test_valid_mesh_without_gpu_reports_cuda_error(lib, tiny_case):
     import torch
     if torch.cuda.is_available():
