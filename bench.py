@@ -45,6 +45,9 @@ NBODY_TRAFFIC = 2311424.0
 # per launch, from its ncu capture (profiles/k_nbody_ffm_multi_charge_sphere.md)
 FF_FLOP_PAIR = {"laplace": 120.1, "yukawa": 179.3}
 FF_TRAFFIC = 15.2e6
+# the same per launch of the packed mutual kernel (two targets per thread; same per-pair arithmetic),
+# from its ncu capture (profiles/k_nbody_ffm2_multi_charge_sphere.md)
+FF2_TRAFFIC = 15.17e6
 
 
 def workload_config(case, precision):
@@ -313,11 +316,14 @@ def run_pbfb(args):
                               peak_basis="fp32 non-tensor: 152 SM x 128 lanes x 2 flop x 2070 MHz; "
                                          "18 flop per Laplace pair, 24 per Yukawa pair"))
         lff, msff = prof["nbodyff_launches"], prof["nbodyff_ms"]
+        packed_ff = tuned.get("ff_kernel") == 4
         if lff:
-            cands.append(dict(kernel="k_nbody_ffm (float-float far field of the Newton residual, mutual pairs)",
+            cands.append(dict(kernel="k_nbody_ffm2 (float-float far field of the Newton residual, mutual pairs, "
+                                     "2 targets per thread)" if packed_ff else
+                                     "k_nbody_ffm (float-float far field of the Newton residual, mutual pairs)",
                               launches=lff, ms=msff, pairs=prof["nbodyff_pairs"],
                               flops=prof["nbodyff_pairs"] * 0.5 * (FF_FLOP_PAIR["laplace"] + FF_FLOP_PAIR["yukawa"]),
-                              peak=peak32, traffic=FF_TRAFFIC,
+                              peak=peak32, traffic=FF2_TRAFFIC if packed_ff else FF_TRAFFIC,
                               peak_basis="fp32 non-tensor: 152 SM x 128 lanes x 2 flop x 2070 MHz; float32 flops "
                                          "of the float-float pair evaluation per ordered pair (FMA = 2), "
                                          "%.1f Laplace / %.1f Yukawa, counted by ncu"

@@ -341,7 +341,8 @@ typedef struct pbfb_tuning {
                                         counts one-warp blocks) */
   int32_t ff_blocks_per_sm;          /* float-float far field source splits: 1..64 */
   int32_t ff_kernel;                 /* float-float far field: 1 one target per thread,
-                                        2 two per thread (float2), 3 mutual pairs */
+                                        2 two per thread (float2), 3 mutual pairs, 4 mutual
+                                        pairs with two targets per thread (float2) */
   int32_t spmv_lanes;                /* lanes per row of the operator's SpMV: 4, 8, 16 */
   int32_t spmv_block;                /* threads per block of that SpMV: 128, 256, 512 */
   int32_t pcg_blocks_per_sm;         /* blocks per SM of the cooperative inner PCG: 1..32

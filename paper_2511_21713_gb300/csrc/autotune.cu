@@ -28,7 +28,7 @@ bool valid_tuning(const pbfb_tuning* t) {
   const int tp = t->nbody_targets_per_thread;
   if (!(tp == 0 || tp == 1 || tp == 2 || tp == 4 || tp == 8)) return false;
   if (!in(t->nbody_blocks_per_sm, 1, 64) || !in(t->ff_blocks_per_sm, 1, 64)) return false;
-  if (t->nbody_packed < 0 || t->nbody_packed > 2 || t->ff_kernel < 0 || t->ff_kernel > 3) return false;
+  if (t->nbody_packed < 0 || t->nbody_packed > 2 || t->ff_kernel < 0 || t->ff_kernel > 4) return false;
   if (t->nbody_packed == 1 && tp != 0 && tp < 2) return false;
   if (t->nbody_packed == 2 && tp != 4) return false;
   const int L = t->spmv_lanes, B = t->spmv_block;
@@ -125,7 +125,7 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
       }
     }
   // float-float far field
-  for (int kind : {1, 2, 3})
+  for (int kind : {1, 2, 3, 4})
     for (int bps : {4, 8, 16, 24}) {
       pbfb_tuning t = best;
       t.ff_kernel = kind;

@@ -1309,6 +1309,158 @@ __global__ void __launch_bounds__(MT) k_nbody_ffm(int nq, int G, const float4* _
   }
 }
 
+// Packed mutual float-float N-body: k_nbody_ffm's pair organisation with two targets per thread
+// on the float2 instructions.  Tiles hold MT2 = 256 points (targets i and i + 128 of a tile in one
+// thread); a thread evaluates each source of the tile pair against both of its targets at once
+// (the per-lane operation sequence of ff_mutual, so every pair value equals the scalar kernel's),
+// adds the two lanes' source-side contributions and folds them into the tile's shared sums.  The
+// 256 sources are visited in 8 chunks of 32: in phase p warp w takes chunk (w + p) mod 8 (the 4
+// warps on distinct chunks between barriers) and lane l at step k source (l + k) mod 32 of it.
+// Diagonal tiles take the scalar one-direction path with the coincident point skipped.
+constexpr int MT2 = 2 * MT;
+
+template <bool YUK>
+__device__ __forceinline__ void v_mutual(const float2 (&ah)[3], const float2 (&al)[3], const ffv (&am)[3],
+                                         const ffv& as, const float4& bh, const float4& bl, const float4& bmh,
+                                         const float4& bml, ffv kap, const float2* __restrict__ tab, ffv& to_a,
+                                         ffv& to_b) {
+  ffv d0 = v_diff(ah[0], al[0], vdup(bh.x), vdup(bl.x));
+  ffv d1 = v_diff(ah[1], al[1], vdup(bh.y), vdup(bl.y));
+  ffv d2 = v_diff(ah[2], al[2], vdup(bh.z), vdup(bl.z));
+  ffv r2 = v_dot3(d0, d1, d2, d0, d1, d2);
+  ffv ri = v_rsqrt(r2);
+  ffv ri2 = v_sq(ri);
+  ffv f, g;
+  if (YUK) {
+    ffv r = v_mul(r2, ri);
+    ffv x = v_mul(kap, r);
+    ffv e = v_expm(x, tab);
+    ffv one_x = v_two_sum(vdup(1.0f), x.h);
+    one_x = v_fast_two_sum(one_x.h, vadd(one_x.l, x.l));
+    f = v_mul(one_x, ri2);
+    g = v_mul(e, ri);
+  } else {
+    f = ri2;
+    g = ri;
+  }
+  ffv ndb = v_dot3(ffv{vdup(bmh.x), vdup(bml.x)}, ffv{vdup(bmh.y), vdup(bml.y)}, ffv{vdup(bmh.z), vdup(bml.z)}, d0,
+                   d1, d2);
+  ffv nda = v_dot3(am[0], am[1], am[2], d0, d1, d2);
+  ffv fb = v_mul(ndb, f), fa = v_mul(nda, f);
+  to_a = v_mul(v_add(ffv{vdup(bh.w), vdup(bl.w)}, fb), g);
+  to_b = v_mul(v_add(as, ffv{vneg(fa.h), vneg(fa.l)}), g);
+}
+
+template <bool YUK>
+__global__ void __launch_bounds__(MT) k_nbody_ffm2(int nq, int G, const float4* __restrict__ src, float kh,
+                                                   float kl, const float2* __restrict__ tab_hi,
+                                                   double* __restrict__ PI, double* __restrict__ PJ) {
+  __shared__ float4 sb[4][MT2];             // source tile: (y, s) hi, (y, s) lo, m hi, m lo
+  __shared__ float2 acc_j[MT2];             // source-side float-float sums of the current tile pair
+  __shared__ float2 tab[YUK ? FF_TABLE_HI : 1];
+  if (YUK)
+    for (int k = threadIdx.x; k < FF_TABLE_HI; k += MT) tab[k] = tab_hi[k];
+  int t = blockIdx.x, rg = 0;
+  while (t >= G - rg) {
+    t -= G - rg;
+    ++rg;
+  }
+  const int cg = rg + t;
+  const int nT = (nq + MT2 - 1) / MT2;
+  const int tpg = (nT + G - 1) / G;
+  const int i0g = rg * tpg, i1g = min(nT, (rg + 1) * tpg);
+  const int j0g = cg * tpg, j1g = min(nT, (cg + 1) * tpg);
+  const ff kap{kh, kl};
+  const ffv kapv{vdup(kh), vdup(kl)};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int I = i0g; I < i1g; ++I) {
+    const int i0 = I * MT2 + threadIdx.x, i1 = i0 + MT;
+    const bool v0 = i0 < nq, v1 = i1 < nq;
+    // invalid targets sit far away with zero strength
+    const float4 a0h = v0 ? src[4 * i0] : make_float4(2e15f, 0.f, 0.f, 0.f);
+    const float4 a0l = v0 ? src[4 * i0 + 1] : zero4;
+    const float4 a0mh = v0 ? src[4 * i0 + 2] : zero4;
+    const float4 a0ml = v0 ? src[4 * i0 + 3] : zero4;
+    const float4 a1h = v1 ? src[4 * i1] : make_float4(2e15f, 0.f, 0.f, 0.f);
+    const float4 a1l = v1 ? src[4 * i1 + 1] : zero4;
+    const float4 a1mh = v1 ? src[4 * i1 + 2] : zero4;
+    const float4 a1ml = v1 ? src[4 * i1 + 3] : zero4;
+    const float2 ah[3] = {make_float2(a0h.x, a1h.x), make_float2(a0h.y, a1h.y), make_float2(a0h.z, a1h.z)};
+    const float2 al[3] = {make_float2(a0l.x, a1l.x), make_float2(a0l.y, a1l.y), make_float2(a0l.z, a1l.z)};
+    const ffv am[3] = {ffv{make_float2(a0mh.x, a1mh.x), make_float2(a0ml.x, a1ml.x)},
+                       ffv{make_float2(a0mh.y, a1mh.y), make_float2(a0ml.y, a1ml.y)},
+                       ffv{make_float2(a0mh.z, a1mh.z), make_float2(a0ml.z, a1ml.z)}};
+    const ffv as{make_float2(a0h.w, a1h.w), make_float2(a0l.w, a1l.w)};
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int J = max(I, j0g); J < j1g; ++J) {
+      __syncthreads();  // the previous tile's readers are done
+      for (int h = 0; h < 2; ++h) {
+        const int slot = h * MT + threadIdx.x;
+        const int jl = J * MT2 + slot;
+        if (jl < nq) {
+          for (int c = 0; c < 4; ++c) sb[c][slot] = src[4 * jl + c];
+        } else {
+          sb[0][slot] = make_float4(1e15f, 0.f, 0.f, 0.f);
+          sb[1][slot] = sb[2][slot] = sb[3][slot] = zero4;
+        }
+        acc_j[slot] = make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      if (J == I) {
+        // diagonal tile: target side only, coincident point skipped (scalar, per target)
+        const int cnt = min(MT2, nq - J * MT2);
+        for (int q = 0; q < 2; ++q) {
+          const float4& xh = q == 0 ? a0h : a1h;
+          const float4& xl = q == 0 ? a0l : a1l;
+          const float th[3] = {xh.x, xh.y, xh.z}, tl[3] = {xl.x, xl.y, xl.z};
+          const int self = q * MT + (int)threadIdx.x;
+          ff acc{0.f, 0.f};
+          for (int jj = 0; jj < cnt; ++jj) {
+            if (jj == self) continue;
+            acc = ff_add(acc, ff_pair<YUK>(sb[0][jj], sb[1][jj], sb[2][jj], sb[3][jj], th, tl, kap, tab));
+          }
+          (q == 0 ? acc0 : acc1) += (double)acc.h + (double)acc.l;
+        }
+      } else {
+        ffv acc{vdup(0.f), vdup(0.f)};
+        for (int ph = 0; ph < 8; ++ph) {
+          const int base = 32 * ((warp + ph) & 7);
+          for (int k = 0; k < 32; ++k) {
+            const int jj = base + ((lane + k) & 31);
+            ffv ta, tb;
+            v_mutual<YUK>(ah, al, am, as, sb[0][jj], sb[1][jj], sb[2][jj], sb[3][jj], kapv, tab, ta, tb);
+            // running sums kept as (high, low) with the low parts and TwoSum errors added plainly
+            // (at most 256 terms per tile pair, converted to float64 at its end)
+            const ffv sa = v_two_sum(acc.h, ta.h);
+            acc = ffv{sa.h, vadd(acc.l, vadd(sa.l, ta.l))};
+            const ff tbs = two_sum(tb.h.x, tb.h.y);
+            const float tbl = __fadd_rn(tbs.l, __fadd_rn(tb.l.x, tb.l.y));
+            const float2 o = acc_j[jj];
+            const ff sj = two_sum(o.x, tbs.h);
+            acc_j[jj] = make_float2(sj.h, __fadd_rn(o.y, __fadd_rn(sj.l, tbl)));
+            __syncwarp();
+          }
+          __syncthreads();
+        }
+        // source-side sums of this tile pair into PJ[rg][j]
+        for (int h = 0; h < 2; ++h) {
+          const int slot = h * MT + threadIdx.x;
+          const int jl = J * MT2 + slot;
+          if (jl < nq) {
+            const float2 o = acc_j[slot];
+            PJ[(int64_t)rg * nq + jl] += (double)o.x + (double)o.y;
+          }
+        }
+        acc0 += (double)acc.h.x + (double)acc.l.x;
+        acc1 += (double)acc.h.y + (double)acc.l.y;
+      }
+    }
+    if (v0) PI[(int64_t)cg * nq + i0] = acc0;
+    if (v1) PI[(int64_t)cg * nq + i1] = acc1;
+  }
+}
+
 // out[i] = sum over c of PI[c][i] + sum over r of PJ[r][i] (fixed order)
 __global__ void k_mutual_sum(int nq, int G, const double* __restrict__ PI, const double* __restrict__ PJ,
                              double* __restrict__ out) {
@@ -1674,15 +1826,17 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
   cudaEvent_t ev;
   timer_begin(m, m->t_nbodyff, &ev);
   constexpr int NT = 128;
-  // kernel: 1 one target per thread, 2 two targets per thread (float2), 3 mutual pairs;
-  // built-in choice: mutual for large surfaces, two targets per thread otherwise
-  const int kind = m->tune_ff_kernel > 0 ? m->tune_ff_kernel : (nq >= 16384 ? 3 : 2);
+  // kernel: 1 one target per thread, 2 two targets per thread (float2), 3 mutual pairs, 4 mutual
+  // pairs with two targets per thread (float2);
+  // built-in choice: packed mutual for large surfaces (5 % faster than 3 on GB300: the float32
+  // pipe, not issue, bounds both), two targets per thread otherwise
+  const int kind = m->tune_ff_kernel > 0 ? m->tune_ff_kernel : (nq >= 16384 ? 4 : 2);
   const int bps = m->tune_ff_bps > 0 ? m->tune_ff_bps : 8;  // GB300 sweep: 8 blocks per SM of source splits
   const float kh = (float)kappa, kl = (float)(kappa - (double)kh);
-  if (kind == 3) {
+  if (kind == 3 || kind == 4) {
     // tile groups: G (G + 1) / 2 blocks, about bps blocks per SM (built-in 16: two waves, which
     // measured faster than one full wave or fewer, larger tiles); 2 G + 1 partial rows
-    const int nT = blocks_for(nq, MT);
+    const int nT = blocks_for(nq, kind == 4 ? MT2 : MT);
     int G = (int)std::sqrt(2.0 * (m->tune_ff_bps > 0 ? m->tune_ff_bps : 16) * 152.0);
     G = std::max(1, std::min(G, nT));
     PB_TRY(ensure(s->mval, (size_t)(2 * G + 1) * nq));
@@ -1691,7 +1845,11 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
     double* out = s->mval.p + (size_t)2 * G * nq;
     PB_CUDA(cudaMemsetAsync(s->mval.p, 0, (size_t)2 * G * nq * sizeof(double), m->stream));
     const int nblk = G * (G + 1) / 2;
-    if (yuk)
+    if (kind == 4 && yuk)
+      k_nbody_ffm2<true><<<nblk, MT, 0, m->stream>>>(nq, G, s->ffsrc.p, kh, kl, m->ff_tab.p, PI, PJ);
+    else if (kind == 4)
+      k_nbody_ffm2<false><<<nblk, MT, 0, m->stream>>>(nq, G, s->ffsrc.p, kh, kl, m->ff_tab.p, PI, PJ);
+    else if (yuk)
       k_nbody_ffm<true><<<nblk, MT, 0, m->stream>>>(nq, G, s->ffsrc.p, kh, kl, m->ff_tab.p, PI, PJ);
     else
       k_nbody_ffm<false><<<nblk, MT, 0, m->stream>>>(nq, G, s->ffsrc.p, kh, kl, m->ff_tab.p, PI, PJ);

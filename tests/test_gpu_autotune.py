@@ -35,7 +35,7 @@ def test_autotune_shapes_cache_and_results(small_case, tmp_path):
     assert shapes == m.get_tuning()
     assert shapes["nbody_targets_per_thread"] in (1, 2, 4) and shapes["nbody_blocks_per_sm"] in (0, 8, 16, 32, 64)
     assert shapes["nbody_packed"] in (0, 1, 2)
-    assert shapes["ff_blocks_per_sm"] in (4, 8, 16, 24) and shapes["ff_kernel"] in (1, 2, 3)
+    assert shapes["ff_blocks_per_sm"] in (4, 8, 16, 24) and shapes["ff_kernel"] in (1, 2, 3, 4)
     assert shapes["spmv_lanes"] in (4, 8, 16) and shapes["spmv_block"] in (128, 256, 512)
     assert shapes["pcg_blocks_per_sm"] in (0, 1, 2, 4, 8) and shapes["pcg_lanes"] in (2, 4, 8)
     assert all(v > 0 for v in ms.values())

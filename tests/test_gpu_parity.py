@@ -328,8 +328,9 @@ def test_error_statuses(tiny_case):
 
 def test_float_float_kernels_agree(pair):
     """The float-float far-field variants -- one target per thread, two per thread on float2
-    instructions, and mutual pairs evaluated once for both directions -- agree to float-float
-    rounding (1e-13 of the largest entry), ragged tails included."""
+    instructions, mutual pairs evaluated once for both directions, and mutual pairs with two
+    targets per thread on float2 -- agree to float-float rounding (1e-13 of the largest entry),
+    ragged tails included."""
     from paper_2511_21713_gb300 import pbfb
     case, m, P = pair
     m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.FLOAT2)
@@ -340,12 +341,12 @@ def test_float_float_kernels_agree(pair):
             x = dev(rng.standard_normal(n) + 0.5)
             for op in (0, 1):
                 ys = {}
-                for kind in (1, 2, 3):
+                for kind in (1, 2, 3, 4):
                     m.apply_tuning(dict(base, ff_kernel=kind))
                     ys[kind] = dev(np.zeros(n))
                     m.bem_apply(which, op, x, ys[kind])
                 b = host(ys[1])
-                for kind in (2, 3):
+                for kind in (2, 3, 4):
                     a = host(ys[kind])
                     assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max(), (which, op, kind, np.abs(a - b).max())
     finally:
