@@ -48,6 +48,10 @@ FF_TRAFFIC = 15.2e6
 # the same per launch of the packed mutual kernel (two targets per thread; same per-pair arithmetic),
 # from its ncu capture (profiles/k_nbody_ffm2_multi_charge_sphere.md)
 FF2_TRAFFIC = 15.17e6
+# float32 lane operations (FADD, FMUL and FFMA each 1; a packed instruction 2) per ordered pair of
+# the float-float evaluation, counted by ncu on the packed mutual kernel: the float32 pipe's view,
+# against 152 SM x 128 lanes x 2070 MHz (three quarters of the operations are additions)
+FF_OPS_PAIR = {"laplace": 97.7, "yukawa": 145.7}
 
 
 def workload_config(case, precision):
@@ -323,6 +327,7 @@ def run_pbfb(args):
                                      "k_nbody_ffm (float-float far field of the Newton residual, mutual pairs)",
                               launches=lff, ms=msff, pairs=prof["nbodyff_pairs"],
                               flops=prof["nbodyff_pairs"] * 0.5 * (FF_FLOP_PAIR["laplace"] + FF_FLOP_PAIR["yukawa"]),
+                              lane_ops=prof["nbodyff_pairs"] * 0.5 * (FF_OPS_PAIR["laplace"] + FF_OPS_PAIR["yukawa"]),
                               peak=peak32, traffic=FF2_TRAFFIC if packed_ff else FF_TRAFFIC,
                               peak_basis="fp32 non-tensor: 152 SM x 128 lanes x 2 flop x 2070 MHz; float32 flops "
                                          "of the float-float pair evaluation per ordered pair (FMA = 2), "
@@ -338,8 +343,14 @@ def run_pbfb(args):
         launches = max(c["launches"], 1)
         avg_ms = c["ms"] / launches
         achieved = (c["flops"] / launches) / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else None
+        lanes = None
+        if c.get("lane_ops") and avg_ms > 0:
+            peak_lanes = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+            a = (c["lane_ops"] / launches) / (avg_ms * 1e-3) / 1e12
+            lanes = {"achieved": a, "peak": peak_lanes, "unit": "T float32 lane-ops/s", "frac": a / peak_lanes}
         return {"bound": "alu", "kernel": c["kernel"], "achieved": achieved, "peak": c["peak"],
                 "unit": "TFLOP/s", "frac": (achieved / c["peak"]) if achieved else None,
+                "fp32_pipe_view": lanes,
                 "traffic": c["traffic"] if args.workload == "multi_charge_sphere" else None,
                 "peak_basis": c["peak_basis"], "avg_launch_ms": avg_ms,
                 "pairs_per_launch": c["pairs"] / launches, "launches": c["launches"],
