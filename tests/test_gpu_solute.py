@@ -160,6 +160,18 @@ def test_flux_reproduces_a_shell_solution(tiny_case):
     m.close()
 
 
+def test_zero_charges(tiny_solute_case):
+    """No charge: no point load, a zero first residual, the solution and every energy term zero."""
+    from paper_2511_21713_gb300 import pbfb
+    c = tiny_solute_case
+    m = pbfb.Mesh.from_case(c)
+    m.charges_set(c.q_xyz, 0.0 * c.q_z)
+    x, res = m.solve(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.default_opts(precision=pbfb.MIXED))
+    assert res["status"] == 0 and res["newton_iters"] == 1 and not np.any(x)
+    assert (res["total"], res["LC"], res["NC"], res["dG_ion"]) == (0.0, 0.0, 0.0, 0.0)
+    m.close()
+
+
 def test_charge_outside_omega_m(tiny_solute_case):
     from paper_2511_21713_gb300 import pbfb
     c = tiny_solute_case

@@ -110,3 +110,12 @@ def test_post_processed_flux(small_solute):
     assert abs(P.eps_m * (P.Mm @ lm).sum() / ref - 1) < 1e-3
     x = P.expand(R.x)
     assert np.array_equal(x[P.nv:P.nv + P.nm], lm) and np.array_equal(x[P.nv + P.nm:], R.x[P.nv:])
+
+
+def test_picard_reaches_the_newton_solution(small_solute):
+    """Picard (Sec. 2.4.1) on the same system converges to the same discrete solution."""
+    P, R = small_solute
+    Rp = pb.solve(P, pb.Opts(tol_gmres0=1e-13, tol_gmres=1e-13, tol_nl=1e-9, linear_solver="direct",
+                             method="picard", max_newton=200))
+    assert np.linalg.norm(Rp.x - R.x) < 1e-9 * np.linalg.norm(R.x)
+    assert abs(Rp.total - R.total) < 1e-10 * abs(R.total)
