@@ -177,8 +177,8 @@ int pbfb_mesh_create(const double* xyz, int32_t n_v, const int32_t* tets, int64_
  * fills lam_m from the Gamma_m boundary integral equation of Sec. 2.3.1 (pbfb_gamma_m_flux) and
  * takes the energy as for a shell mesh (Eq. Esolv, Eq. Potential_in_Omega_m), Delta G_Omega_i
  * over the Omega_i tets.  pbfb_charges_set then requires every charge to lie in an Omega_m tet
- * (barycentric coordinates >= -1e-12; PBFB_ERR_INVALID otherwise).  The request server and the
- * batch call take shell meshes only. */
+ * (barycentric coordinates >= -1e-12; PBFB_ERR_INVALID otherwise).  pbfb_solve_batch takes such
+ * meshes like any other; the request server builds them from requests with tet_region set. */
 int pbfb_mesh_create_full(const double* xyz, int32_t n_v, const int32_t* tets, int64_t n_t,
                           const int32_t* tet_region, const int32_t* gm_tris, int32_t n_gm,
                           const int32_t* gs_tris, int32_t n_gs, uintptr_t stream, pbfb_mesh** out);
@@ -418,6 +418,8 @@ typedef struct pbfb_request {
   int32_t n_q;
   double eps_in, eps_out, kappa, T;
   const pbfb_newton_opts* opts;
+  const int32_t* tet_region;  /* NULL: a shell mesh (as pbfb_mesh_create); else n_t entries, the
+                                 mesh of Omega_m and Omega_i (as pbfb_mesh_create_full) */
 } pbfb_request;
 
 /* Completed request: status and result of the solve; times in ms on the host's

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "pbfb_internal.cuh"
 #include "quad_tables.cuh"
@@ -362,8 +363,7 @@ int build_dense_single_layer(Mesh* m, Surface* s, double kappa, bool invert) {
   PB_LAUNCHED(m);
   if (invert) {
     PB_CUDA(cudaMemsetAsync(m->dflag.p, 0, sizeof(int), m->stream));
-    const int smem = 2 * SW_B * SW_TILE * (int)sizeof(float);
-    PB_CUDA(cudaFuncSetAttribute(k_sweep_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int smem = 2 * SW_B * SW_TILE * (int)sizeof(float);  // attribute set by init_dense_attributes
     const dim3 gu(ld / SW_TILE, ld / SW_TILE);
     for (int k0 = 0; k0 < ld; k0 += SW_B) {
       k_sweep_pivot<<<1, 256, 0, m->stream>>>(ld, k0, A, S, m->dflag.p);
@@ -382,11 +382,28 @@ int build_dense_single_layer(Mesh* m, Surface* s, double kappa, bool invert) {
     set_error("dense single layer: a pivot of the float32 sweep was not positive");
     return PBFB_ERR_NONFINITE;
   }
-  // the apply kernel stages a vector of ld floats in shared memory
-  const int smem = ld * (int)sizeof(float);
-  if (smem > 48 * 1024) PB_CUDA(cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   s->vinv_ok = invert;
   s->vinv_kappa = kappa;
+  return PBFB_OK;
+}
+
+// Dynamic shared-memory limits of the dense kernels, set once per device by the first mesh
+// creation, before any solve: the largest sweep tile pair, and the apply kernel's vector of
+// dense_ld(DENSE_V_MAX) floats (every surface's fits).  Solves running on several host threads
+// then never change a kernel's attributes while another thread launches or captures it, and a
+// smaller matrix never lowers the limit a larger one needs.
+int init_dense_attributes() {
+  static std::mutex mu;
+  static uint64_t done = 0;
+  int dev = 0;
+  PB_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 64 && ((done >> dev) & 1)) return PBFB_OK;
+  PB_CUDA(cudaFuncSetAttribute(k_sweep_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               2 * SW_B * SW_TILE * (int)sizeof(float)));
+  PB_CUDA(cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               dense_ld(DENSE_V_MAX) * (int)sizeof(float)));
+  if (dev < 64) done |= 1ull << dev;
   return PBFB_OK;
 }
 
@@ -395,7 +412,7 @@ int launch_dense_apply(Mesh* m, Surface* s, double scale, const double* v, doubl
     set_error("dense single-layer inverse not built");
     return PBFB_ERR_STATE;
   }
-  const int smem = s->vinv_ld * (int)sizeof(float);  // attribute set when the matrix was built
+  const int smem = s->vinv_ld * (int)sizeof(float);  // within the limit of init_dense_attributes
   k_dense_apply<<<(s->nv + 7) / 8, 256, smem, m->stream>>>(s->nv, s->vinv_ld, s->vinv.p, scale, v, z);
   PB_LAUNCHED(m);
   return PBFB_OK;

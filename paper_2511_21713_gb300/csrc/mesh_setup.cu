@@ -619,6 +619,7 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
     return PBFB_ERR_CUDA;
   }
   PB_TRY(init_quadrature());
+  PB_TRY(init_dense_attributes());
   Mesh* m = new Mesh();
   int st = PBFB_OK;
   auto fail = [&](int s) {

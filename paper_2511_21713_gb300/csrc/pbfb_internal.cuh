@@ -293,6 +293,8 @@ int build_dense_single_layer(Mesh* m, Surface* s, double kappa, bool invert);
 // z = scale * (stored matrix) v over the surface's vertices
 int launch_dense_apply(Mesh* m, Surface* s, double scale, const double* v, double* z);
 int dense_copy_out(Mesh* m, Surface* s, float scale, float* out, int ld_out);
+// launch attributes of the dense kernels, once per device (called by mesh creation)
+int init_dense_attributes();
 
 // ---- one application of the block preconditioner (solver.cu), for the autotuner: prepares it at
 // the current Jacobian (dense surface blocks if requested) and applies it to v

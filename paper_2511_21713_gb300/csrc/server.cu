@@ -54,10 +54,11 @@ struct Request {
   int64_t id = 0;
   std::vector<double> xyz, qxyz, qz;
   std::vector<int> tets, gm, gs;
+  std::vector<int> region;  // per tet 0 (Omega_m) / 1 (Omega_i); empty for a shell mesh
   double eps_in = 0, eps_out = 0, kappa = 0, T = 0;
   pbfb_newton_opts opts;
   size_t bytes = 0;
-  uint64_t hash = 0;  // of the geometry (coordinates, tets, both surfaces)
+  uint64_t hash = 0;  // of the geometry (coordinates, tets, both surfaces, tet regions)
   double t_submit = 0;
 };
 
@@ -66,7 +67,7 @@ struct Request {
 struct Cached {
   uint64_t hash = 0;
   std::vector<double> xyz;
-  std::vector<int> tets, gm, gs;
+  std::vector<int> tets, gm, gs, region;
   Mesh* m = nullptr;
   size_t bytes = 0;
   bool busy = false;
@@ -88,11 +89,12 @@ uint64_t geometry_hash(const Request& r) {
   h = fnv(h, r.xyz.data(), r.xyz.size() * sizeof(double));
   h = fnv(h, r.tets.data(), r.tets.size() * sizeof(int));
   h = fnv(h, r.gm.data(), r.gm.size() * sizeof(int));
+  h = fnv(h, r.region.data(), r.region.size() * sizeof(int));
   return fnv(h, r.gs.data(), r.gs.size() * sizeof(int));
 }
 
 bool same_geometry(const Request& r, const Cached& c) {
-  return r.xyz == c.xyz && r.tets == c.tets && r.gm == c.gm && r.gs == c.gs;
+  return r.xyz == c.xyz && r.tets == c.tets && r.gm == c.gm && r.gs == c.gs && r.region == c.region;
 }
 
 double now_ms() {
@@ -195,7 +197,8 @@ struct Server {
         m->stream = s;  // the mesh is idle: its earlier work ended with a synchronisation
       } else {
         st = mesh_create(r->xyz.data(), (int)(r->xyz.size() / 3), r->tets.data(), (int64_t)(r->tets.size() / 4),
-                         r->gm.data(), (int)(r->gm.size() / 3), r->gs.data(), (int)(r->gs.size() / 3), s, &m);
+                         r->gm.data(), (int)(r->gm.size() / 3), r->gs.data(), (int)(r->gs.size() / 3), s, &m,
+                         r->region.empty() ? nullptr : r->region.data());
         if (st == PBFB_OK) m->no_coop = true;
       }
       if (st == PBFB_OK) st = charges_set(m, r->qxyz.data(), r->qz.data(), (int)r->qz.size());
@@ -217,6 +220,7 @@ struct Server {
           c->tets.swap(r->tets);
           c->gm.swap(r->gm);
           c->gs.swap(r->gs);
+          c->region.swap(r->region);
           c->m = m;
           c->bytes = r->bytes;
           c->last_use = ++tick;
@@ -285,6 +289,7 @@ int pbfb_server_submit(pbfb_server* h, const pbfb_request* q) {
   r->tets.assign(q->tets, q->tets + 4 * (size_t)q->n_t);
   r->gm.assign(q->gm_tris, q->gm_tris + 3 * (size_t)q->n_gm);
   r->gs.assign(q->gs_tris, q->gs_tris + 3 * (size_t)q->n_gs);
+  if (q->tet_region) r->region.assign(q->tet_region, q->tet_region + q->n_t);
   r->qxyz.assign(q->q_xyz, q->q_xyz + 3 * (size_t)q->n_q);
   r->qz.assign(q->q_z, q->q_z + q->n_q);
   r->eps_in = q->eps_in;

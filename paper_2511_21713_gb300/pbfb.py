@@ -84,7 +84,7 @@ class Request(ctypes.Structure):
                 ("n_gm", ctypes.c_int32), ("gs_tris", ctypes.c_void_p), ("n_gs", ctypes.c_int32),
                 ("q_xyz", ctypes.c_void_p), ("q_z", ctypes.c_void_p), ("n_q", ctypes.c_int32),
                 ("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double), ("kappa", ctypes.c_double),
-                ("T", ctypes.c_double), ("opts", ctypes.POINTER(NewtonOpts))]
+                ("T", ctypes.c_double), ("opts", ctypes.POINTER(NewtonOpts)), ("tet_region", ctypes.c_void_p)]
 
 
 class Response(ctypes.Structure):
@@ -396,11 +396,13 @@ class Server:
                 np.ascontiguousarray(case.gm_tris, np.int32), np.ascontiguousarray(case.gs_tris, np.int32),
                 np.ascontiguousarray(case.q_xyz, np.float64), np.ascontiguousarray(case.q_z, np.float64)]
         x, t, gm, gs, qx, qz = arrs
+        region = getattr(case, "tet_region", None)
+        reg = None if region is None else np.ascontiguousarray(region, np.int32)
         r = Request(rid, _ptr(x), x.shape[0], _ptr(t), t.shape[0], _ptr(gm), gm.shape[0], _ptr(gs), gs.shape[0],
                     _ptr(qx), _ptr(qz), qz.shape[0],
                     case.eps_in if eps_in is None else eps_in, case.eps_out if eps_out is None else eps_out,
                     case.kappa if kappa is None else kappa, case.T if T is None else T,
-                    ctypes.pointer(opts) if opts is not None else None)
+                    ctypes.pointer(opts) if opts is not None else None, None if reg is None else _ptr(reg))
         _check(load().pbfb_server_submit(self.h, ctypes.byref(r)))
 
     def poll(self, max_n=64, timeout_us=0):

@@ -141,3 +141,33 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.pbfb_apply(None, z.ctypes.data, z.ctypes.data) == 1
     assert lib.pbfb_solve(None, 1.0, 1.0, 0.1, 300.0, None, None, None, None, None) == 1
     assert lib.pbfb_mesh_destroy(None) == 0
+
+
+def test_ctypes_mirrors_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the C header's size and field offsets (a plain C
+    program compiled against include/pbfb.h prints them), so arrays of them index alike."""
+    import shutil
+    import subprocess
+    from paper_2511_21713_gb300 import pbfb
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"pbfb_newton_opts": pbfb.NewtonOpts, "pbfb_result": pbfb.Result, "pbfb_request": pbfb.Request,
+               "pbfb_response": pbfb.Response, "pbfb_tuning": pbfb.Tuning, "pbfb_batch_params": pbfb.BatchParams}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pbfb.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "sizes"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])

@@ -163,3 +163,43 @@ def test_resident_meshes_reused_with_identical_results():
     sv.close()
     assert all(got[i]["status"] == 0 and got[i]["total"] == ref[i]["total"] for i in range(len(cases)))
     assert st["peak"] <= 150 << 20
+
+
+def test_meshes_of_omega_m_and_omega_i_served_and_batched():
+    """Requests carrying tet regions are built as meshes of Omega_m and Omega_i (the paper's own
+    formulation) and give the single-solve entry point's result; so does pbfb_solve_batch."""
+    import torch
+    from paper_2511_21713_gb300 import inputs, pbfb
+    cases = []
+    for i in range(3):
+        q, z = inputs.ball_charges(2 + 2 * i, 3.0, 1 + i, 700 + i)
+        cases.append(inputs.solute_sphere_case(nu=3 + i % 2, layers=5, core_layers=6, q_xyz=q, q_z=z,
+                                               ionic=(0.05, 0.15, 0.5)[i], name=f"solute{i}"))
+    tight = pbfb.default_opts(tol_gmres0=1e-11, tol_gmres=1e-11, tol_nl=1e-8)
+    sv = pbfb.Server(budget_bytes=8 << 30, max_inflight=3, cached_meshes=4)
+    for i, c in enumerate(cases):
+        sv.submit(c, i, opts=tight)
+    got = _collect(sv, len(cases))
+    sv.submit(cases[0], len(cases), opts=tight)          # served on the resident mesh
+    got.update(_collect(sv, 1))
+    st = sv.stats()
+    sv.close()
+    assert st["mesh_hits"] == 1
+    streams = [torch.cuda.Stream() for _ in cases]
+    meshes = []
+    for c, s in zip(cases, streams):
+        m = pbfb.Mesh.from_case(c, stream=s.cuda_stream)
+        m.charges_set(c.q_xyz, c.q_z)
+        meshes.append(m)
+    batch = pbfb.solve_batch(meshes, [(c.eps_in, c.eps_out, c.kappa, c.T, tight) for c in cases], 3)
+    for m in meshes:
+        m.close()
+    for i, c in enumerate(cases):
+        m = pbfb.Mesh.from_case(c)
+        assert m.full
+        m.charges_set(c.q_xyz, c.q_z)
+        _, s = m.solve(c.eps_in, c.eps_out, c.kappa, c.T, tight)
+        m.close()
+        for r in (got[i], batch[i]):
+            assert r["status"] == 0 and abs(r["total"] - s["total"]) < 1e-9 * abs(s["total"])
+    assert got[len(cases)]["total"] == got[0]["total"]
