@@ -313,7 +313,9 @@ int pbfb_omega_eval(pbfb_mesh* mesh, int scheme, const double* u_dev, const doub
                     int n_omega, double* dots);
 
 /* Step a9: energies (kcal/mol) of x_L and x_NL (device, n each) into
- * out[0..3] = Total, LC, NC, dG_Omega_i (host) (Eq. Esolv). */
+ * out[0..3] = Total, LC, NC, dG_Omega_i (host) (Eq. Esolv).  The reaction potential takes
+ * lam_m from the vectors as given: on a mesh of Omega_m and Omega_i fill it first with
+ * pbfb_gamma_m_flux (coulomb = 1 for x_L, 0 for x_NL), as a solve does. */
 int pbfb_energy(pbfb_mesh* mesh, const double* xL_dev, const double* xNL_dev, double* out);
 
 /* Launch-shape knobs of the float32 far field (an autotuner sets them):
