@@ -54,7 +54,8 @@ enum {
   PBFB_ERR_OMEGA = 5,          /* no relaxation factor reduced ||d|| */
   PBFB_ERR_NONFINITE = 6,      /* NaN / Inf in a residual, update or energy */
   PBFB_ERR_OOM = 7,            /* device allocation failed */
-  PBFB_ERR_STATE = 8           /* call out of order (e.g. solve before charges) */
+  PBFB_ERR_STATE = 8,          /* call out of order (e.g. solve before charges) */
+  PBFB_ERR_TIMEOUT = 9         /* a bounded wait ended without a result (pbfb_server_poll) */
 };
 
 /* Precisions.  PBFB_FP64: everything float64.  PBFB_MIXED: GMRES operator far
@@ -204,8 +205,23 @@ int pbfb_surface_vertices(const pbfb_mesh* mesh, int which, int32_t* out);
 
 /* Sets the point charges (host, n_q x 3 positions in Angstrom, n_q charges in
  * units of e) and computes <sum_k z_k / |x - x_k|, psi_i> on Gamma_m
- * (the Coulomb data of Sec. 2.3.1).  Charges must be finite; n_q >= 1. */
+ * (the Coulomb data of Sec. 2.3.1).  Charges must be finite; n_q >= 1.  On a
+ * shell mesh every charge must lie strictly inside Gamma_m (in Omega_m, as the
+ * three-region model of Sec. 2.1 places them), checked on the host by the
+ * winding number of pbfb_check_charges before any GPU work; PBFB_ERR_INVALID
+ * otherwise, the mesh keeping its previous charges. */
 int pbfb_charges_set(pbfb_mesh* mesh, const double* xyz, const double* z, int32_t n_q);
+
+/* Host-only input check (no GPU needed): the generalised winding number
+ * w(x) = (1/4 pi) sum over Gamma_m's triangles of their signed solid angles at
+ * each charge (1 inside, 0 outside, 1/2 on the surface, for the orientation of
+ * pbfb_mesh_create: normal out of the solute).  xyz: host, n_v x 3 float64;
+ * gm_tris: host, n_gm x 3 int32; q_xyz: host, n_q x 3 float64; winding_out:
+ * host, n_q float64 or NULL.  Returns PBFB_ERR_INVALID (with the first
+ * offending charge in pbfb_last_error) unless every w > 3/4, or for a bad
+ * argument (vertex id out of range, non-finite position). */
+int pbfb_check_charges(const double* xyz, int32_t n_v, const int32_t* gm_tris, int32_t n_gm,
+                       const double* q_xyz, int32_t n_q, double* winding_out);
 
 /* Full solve (Sec. 2.4): linear part, Newton with the omega search, energy.
  * eps_in = eps_m, eps_out = eps_s (> 0), kappa >= 0 in 1/Angstrom, T > 0 K.
@@ -256,9 +272,13 @@ int pbfb_bem_apply(pbfb_mesh* mesh, int which, int op, const double* x_dev, doub
  * For callers that may not allocate GPU memory while they run -- for example
  * a host that has handed all device memory to its own pool, or a request
  * loop that must not call cudaMalloc/cudaFree (which synchronise the device)
- * between requests.  Computes V x or K x on surface `which` exactly as
+ * between requests.  Computes V x or K x on surface `which` as
  * pbfb_bem_apply does with the float32 far field (whatever precision
- * pbfb_set_params chose) plus the float64 near-field correction, but its
+ * pbfb_set_params chose) plus the float64 near-field correction: the same
+ * split kernel, targets per thread and split rule, with at most 8 source
+ * splits (results equal to float64 rounding), except that a mesh tuned to the
+ * mutual-pair kernel (pbfb_tuning.nbody_packed = 2) runs the packed split
+ * kernel instead (equal to float32 rounding).  Its
  * working memory is one fixed library-wide device array of 6 MiB (float32
  * source records and float64 partial sums), present on every device that
  * loads the library until the process exits; the call allocates nothing.
@@ -455,7 +475,10 @@ int pbfb_server_create(int device, uint64_t hbm_budget_bytes, int max_inflight, 
 int pbfb_server_submit(pbfb_server* server, const pbfb_request* request);
 
 /* Moves up to `max` completed responses to out (host), waiting up to
- * timeout_us microseconds for the first one; *n_out = how many. */
+ * timeout_us microseconds for the first one; *n_out = how many.  With
+ * timeout_us > 0 and no response by then: *n_out = 0 and PBFB_ERR_TIMEOUT
+ * (the server is unaffected); timeout_us = 0 returns at once, PBFB_OK with
+ * *n_out = 0 when nothing is ready. */
 int pbfb_server_poll(pbfb_server* server, pbfb_response* out, int max, int timeout_us, int* n_out);
 
 /* stats (host, 8 doubles): submitted, completed, queued, bytes in use

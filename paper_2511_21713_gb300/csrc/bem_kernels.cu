@@ -13,6 +13,7 @@
 //     Boundary Element Methods, 2011, Sec. 5.2), 5 Gauss-Legendre points per variable;
 //   near (no shared vertex, centroid distance < 2 max(h_tau, h_sigma)): 6 points on
 //     the test triangle x 6 points on each of the 16 sub-triangles of the trial one.
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1923,25 +1924,27 @@ constexpr size_t NOALLOC_BYTES =
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 // Device address of g_noalloc_scratch per device, looked up on the first call on that device.
-// (In host code the symbol's name is only a host-side handle, not the device address.)
+// (In host code the symbol's name is only a host-side handle, not the device address.)  The
+// entries are atomic: first calls from several host threads (server workers) may race to fill
+// one; they all store the same address.
 constexpr int NOALLOC_MAX_DEV = 64;
-void* g_noalloc_addr[NOALLOC_MAX_DEV] = {nullptr};
+std::atomic<void*> g_noalloc_addr[NOALLOC_MAX_DEV];
 
 int noalloc_scratch(int dev, unsigned char** out) {
   if (dev < 0 || dev >= NOALLOC_MAX_DEV) {
     set_error("bem_apply_noalloc: device ordinal %d out of range", dev);
     return PBFB_ERR_INVALID;
   }
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
+  void* p = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!p) {
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       set_error("bem_apply_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
       return PBFB_ERR_CUDA;
     }
-    g_noalloc_addr[dev] = p;
+    g_noalloc_addr[dev].store(p, std::memory_order_release);
   }
-  *out = (unsigned char*)g_noalloc_addr[dev];
+  *out = (unsigned char*)p;
   return PBFB_OK;
 }
 
@@ -1966,11 +1969,27 @@ int bem_apply_noalloc(Mesh* m, int which, int op, const double* x, double* y) {
                                                         cd != 0.0 ? x : nullptr, 1, s->qw.p, s->nrm.p, s->qpf.p,
                                                         s->qx.p, cs * INV4PI, cd * INV4PI, 0, spos, sdl, nullptr);
   PB_LAUNCHED(m);
-  // same kernel and targets per thread as pbfb_bem_apply; at most NOALLOC_SPLITS source splits
+  // The split kernels and targets per thread of pbfb_bem_apply (launch_bem_far), with its split
+  // rules (whole waves of resident blocks when blocks_per_sm is 0), capped at NOALLOC_SPLITS
+  // source splits.  The mutual-pair variant (packed = 2) needs partial rows for every tile group,
+  // more than the fixed array holds: it is replaced by the packed split kernel with the same
+  // targets per thread, whose float32 sums run in another order.
   int tpt, packed, bps;
   f32_shape(m, nq, &tpt, &packed, &bps);
+  if (packed == 2) {
+    packed = tpt >= 2 ? 1 : 0;
+    bps = 0;
+  }
+  const bool yuk = kappa != 0.0;
   const int ntb = blocks_for(nq, F32_NT * tpt);
-  int nsplit = std::max(1, std::min(std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * F32_NT)), NOALLOC_SPLITS));
+  int nsplit;
+  if (bps == 0) {
+    const int cap = f32_blocks_per_sm(tpt, packed, yuk) * 152;
+    nsplit = std::max(1, std::min(3 * cap / ntb, blocks_for(nq, 4 * F32_NT)));
+  } else {
+    nsplit = std::max(1, std::min(blocks_for(bps * 152, ntb), blocks_for(nq, 4 * F32_NT)));
+  }
+  nsplit = std::min(nsplit, NOALLOC_SPLITS);
   const int per = blocks_for(blocks_for(nq, nsplit), F32_NT) * F32_NT;
   nsplit = blocks_for(nq, per);
   launch_nbody_f32(m, s, kappa, tpt, packed, nsplit, per, spos, sdl, val);

@@ -816,6 +816,14 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
     }
     m->gs_radius = std::sqrt(area / (4.0 * M_PI));
   }
+  if (!m->full) {
+    // Gamma_m's triangles (as stored: normal out of the solute) for the charges' winding numbers
+    m->gm_tri_xyz.resize(9 * (size_t)sm.nt);
+    for (int t = 0; t < sm.nt; ++t)
+      for (int a = 0; a < 3; ++a)
+        for (int d = 0; d < 3; ++d)
+          m->gm_tri_xyz[9 * (size_t)t + 3 * a + d] = xyz_h[3 * (size_t)sm.vmap_h[sm.tri_h[3 * t + a]] + d];
+  }
   for (int si = 0; si < 2; ++si) {
     const Surface& s = si == 0 ? sm : ss;
     if (m->full && si == 0) {
@@ -885,4 +893,97 @@ int mesh_create(const double* xyz, int nv, const int* tets, int64_t nt, const in
   return PBFB_OK;
 }
 
+// Generalised winding number of a closed triangulated surface at points q (n of them):
+// w(x) = (1/4 pi) sum_tau Omega_tau(x), with the signed solid angle of each triangle from the formula
+// of Van Oosterom and Strackee (1983),
+//   tan(Omega/2) = a.(b x c) / (|a||b||c| + (a.b)|c| + (b.c)|a| + (c.a)|b|),  a, b, c = corners - x.
+// With the normals pointing out of the enclosed region, w = 1 inside, 0 outside and 1/2 on the
+// surface.  A point on a triangle (a corner, or coplanar to 1e-12 relative with the formula's
+// denominator not positive, i.e. within the triangle) makes that triangle's solid angle +-2 pi by
+// the sign of a rounded zero; such points are reported as on the surface, w = 1/2.
+// tri9: 9 coordinates per triangle.  Host threads over the points.
+void winding_numbers(const double* tri9, size_t nt, const double* q, int nq, double* w) {
+  auto work = [&](int k0, int k1) {
+    for (int k = k0; k < k1; ++k) {
+      const double x = q[3 * k], y = q[3 * k + 1], z = q[3 * k + 2];
+      double sum = 0.0;
+      bool on = false;
+      for (size_t t = 0; t < nt; ++t) {
+        const double* P = tri9 + 9 * t;
+        const double a0 = P[0] - x, a1 = P[1] - y, a2 = P[2] - z;
+        const double b0 = P[3] - x, b1 = P[4] - y, b2 = P[5] - z;
+        const double c0 = P[6] - x, c1 = P[7] - y, c2 = P[8] - z;
+        const double la = std::sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+        const double lb = std::sqrt(b0 * b0 + b1 * b1 + b2 * b2);
+        const double lc = std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+        const double det = a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0);
+        const double den = la * lb * lc + (a0 * b0 + a1 * b1 + a2 * b2) * lc + (b0 * c0 + b1 * c1 + b2 * c2) * la +
+                           (c0 * a0 + c1 * a1 + c2 * a2) * lb;
+        const double s3 = la * lb * lc;
+        if (s3 == 0.0 || (std::fabs(det) <= 1e-12 * s3 && den <= 0.0)) on = true;
+        sum += 2.0 * std::atan2(det, den);
+      }
+      w[k] = on ? 0.5 : sum / (4.0 * M_PI);
+    }
+  };
+  const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (nth == 1 || nq < 2 || (double)nq * (double)nt < 2e5) {
+    work(0, nq);
+    return;
+  }
+  const int nuse = std::min(nth, nq);
+  std::vector<std::thread> th;
+  for (int i = 0; i < nuse; ++i)
+    th.emplace_back(work, (int)((int64_t)nq * i / nuse), (int)((int64_t)nq * (i + 1) / nuse));
+  for (auto& t : th) t.join();
+}
+
+// Every charge strictly inside the closed surface (the charges of the three-region model lie in
+// Omega_m, Sec. 2.1): winding number above 3/4.  w (may be null) receives the winding numbers.
+int check_charges_inside(const double* tri9, size_t nt, const double* q, int nq, double* w_out) {
+  std::vector<double> w(nq, 0.0);
+  winding_numbers(tri9, nt, q, nq, w.data());
+  if (w_out) std::copy(w.begin(), w.end(), w_out);
+  for (int k = 0; k < nq; ++k)
+    if (!(w[k] > 0.75)) {
+      set_error("charge %d at (%g, %g, %g) is not strictly inside Gamma_m (winding number %.3f)", k, q[3 * k],
+                q[3 * k + 1], q[3 * k + 2], w[k]);
+      return PBFB_ERR_INVALID;
+    }
+  return PBFB_OK;
+}
+
+int charges_inside_gamma_m(const Mesh* m, const double* q, int nq) {
+  const size_t nt = m->gm_tri_xyz.size() / 9;
+  if (nt == 0) return PBFB_OK;
+  return check_charges_inside(m->gm_tri_xyz.data(), nt, q, nq, nullptr);
+}
+
 }  // namespace pbfb
+
+// ==================================================================== C ABI (host only)
+
+extern "C" int pbfb_check_charges(const double* xyz, int32_t n_v, const int32_t* gm_tris, int32_t n_gm,
+                                  const double* q_xyz, int32_t n_q, double* winding_out) {
+  pbfb::set_error("");
+  if (!xyz || !gm_tris || !q_xyz || n_v < 3 || n_gm < 4 || n_q < 1) {
+    pbfb::set_error("check_charges: bad argument");
+    return PBFB_ERR_INVALID;
+  }
+  std::vector<double> tri9(9 * (size_t)n_gm);
+  for (int32_t t = 0; t < n_gm; ++t)
+    for (int a = 0; a < 3; ++a) {
+      const int32_t v = gm_tris[3 * (size_t)t + a];
+      if (v < 0 || v >= n_v) {
+        pbfb::set_error("check_charges: vertex id %d out of range", v);
+        return PBFB_ERR_INVALID;
+      }
+      for (int d = 0; d < 3; ++d) tri9[9 * (size_t)t + 3 * a + d] = xyz[3 * (size_t)v + d];
+    }
+  for (int32_t k = 0; k < 3 * n_q; ++k)
+    if (!std::isfinite(q_xyz[k])) {
+      pbfb::set_error("check_charges: non-finite position");
+      return PBFB_ERR_INVALID;
+    }
+  return pbfb::check_charges_inside(tri9.data(), (size_t)n_gm, q_xyz, n_q, winding_out);
+}

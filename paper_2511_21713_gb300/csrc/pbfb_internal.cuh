@@ -221,6 +221,7 @@ struct Mesh {
   int64_t nt_m = 0;
   DBuf<int> tets_m;                 // 4*nt_m SoA
   DBuf<double> vol_m, a1m;          // Omega_m volumes; per slot: its stiffness (eps_m applied at fill)
+  std::vector<double> gm_tri_xyz;   // shell meshes: 9 per Gamma_m triangle (host), for the winding number
   std::vector<double> grid_xyz;     // 3*nv AoS (host), for locating the charges
   std::vector<int> tets_m_h;        // 4*nt_m AoS (host)
   std::vector<int> cell_ptr, cell_tet;  // uniform grid over the Omega_m tets' bounding boxes
@@ -247,6 +248,8 @@ size_t estimate_bytes(int64_t nv, int64_t nt, int64_t ngm, int64_t ngs, int rest
 // sum_k z_k v_i(x_k) over the Omega_m tets (a mesh with Omega_m); PBFB_ERR_INVALID for a charge
 // in none of them
 int point_load(Mesh* m, const double* q_xyz, const double* z, int nq, std::vector<double>& rho);
+int charges_inside_gamma_m(const Mesh* m, const double* q_xyz, int nq);
+int check_charges_inside(const double* tri9, size_t nt, const double* q, int nq, double* w_out);
 }  // namespace pbfb
 pbfb::Mesh* pbfb_mesh_internal(pbfb_mesh* h);
 namespace pbfb {

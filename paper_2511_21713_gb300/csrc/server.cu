@@ -119,11 +119,12 @@ struct Server {
   bool stop = false;
   int64_t submitted = 0, completed = 0, hits = 0;
 
-  // an idle cached mesh of this geometry's hash, or null (under mu)
+  // an idle cached mesh of exactly this geometry, or null (under mu): the hash selects the
+  // candidates and the arrays are compared in full, so that a hash collision is never taken for
+  // a hit (admission would then not account for the fresh mesh the request needs)
   Cached* find_idle(const Request* r) {
     for (Cached* c : cache)
-      if (!c->busy && c->hash == r->hash && c->xyz.size() == r->xyz.size() && c->tets.size() == r->tets.size())
-        return c;
+      if (!c->busy && c->hash == r->hash && same_geometry(*r, *c)) return c;
     return nullptr;
   }
 
@@ -184,14 +185,6 @@ struct Server {
       resp.t_start_ms = now_ms();
       Mesh* m = nullptr;
       int st = PBFB_OK;
-      if (hit && !same_geometry(*r, *hit)) {
-        // a hash collision: solve on a fresh mesh of the request's own size estimate
-        std::lock_guard<std::mutex> lk(mu);
-        hit->busy = false;
-        hit = nullptr;
-        in_use += r->bytes;
-        peak = std::max(peak, in_use);
-      }
       if (hit) {
         m = hit->m;
         m->stream = s;  // the mesh is idle: its earlier work ended with a synchronisation
@@ -335,6 +328,10 @@ int pbfb_server_poll(pbfb_server* h, pbfb_response* out, int max, int timeout_us
     sv->done.pop_front();
   }
   *n_out = n;
+  if (n == 0 && timeout_us > 0) {
+    pbfb::set_error("server_poll: no response within %d us", timeout_us);
+    return PBFB_ERR_TIMEOUT;
+  }
   return PBFB_OK;
 }
 

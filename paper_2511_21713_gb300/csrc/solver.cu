@@ -1468,6 +1468,7 @@ int charges_set(Mesh* m, const double* xyz, const double* z, int n_q) {
       return PBFB_ERR_INVALID;
     }
   }
+  if (!m->full) PB_TRY(charges_inside_gamma_m(m, xyz, n_q));
   if (m->full) {
     // point loads of the charges on the Omega_m tets (Eq. fembem_matrix's right-hand side)
     std::vector<double> rho;

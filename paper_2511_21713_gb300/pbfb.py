@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libpbfb.so")
 
 PBFB_OK = 0
 ERRORS = {1: "INVALID", 2: "CUDA", 3: "GMRES_NOCONV", 4: "NEWTON_NOCONV", 5: "OMEGA",
-          6: "NONFINITE", 7: "OOM", 8: "STATE"}
+          6: "NONFINITE", 7: "OOM", 8: "STATE", 9: "TIMEOUT"}
+ERR_TIMEOUT = 9
 FP64, MIXED, FLOAT2 = 0, 1, 2
 LINEAR, T3, HS, T5, T7 = 0, 1, 2, 3, 4
 NEWTON, PICARD = 0, 1
@@ -35,7 +36,7 @@ EXPORTS = [
     "pbfb_server_create", "pbfb_server_submit", "pbfb_server_poll", "pbfb_server_stats",
     "pbfb_server_destroy", "pbfb_solve_batch", "pbfb_single_layer_dense",
     "pbfb_get_tuning", "pbfb_apply_tuning", "pbfb_autotune", "pbfb_mesh_create_full",
-    "pbfb_gamma_m_flux",
+    "pbfb_gamma_m_flux", "pbfb_check_charges",
 ]
 
 
@@ -135,6 +136,7 @@ def load():
         "pbfb_mesh_sizes": (I, [P, P]),
         "pbfb_surface_vertices": (I, [P, I, P]),
         "pbfb_charges_set": (I, [P, P, P, I]),
+        "pbfb_check_charges": (I, [P, I, P, I, P, I, P]),
         "pbfb_solve": (I, [P, D, D, D, D, P, P, P, P, P]),
         "pbfb_solve_device": (I, [P, D, D, D, D, P, P, P]),
         "pbfb_mesh_destroy": (I, [P]),
@@ -196,6 +198,17 @@ def default_opts(**kw) -> NewtonOpts:
             v = (ctypes.c_int * 4)(*(v + [0] * (4 - len(v))))
         setattr(o, k, v)
     return o
+
+
+def check_charges(xyz, gm_tris, q_xyz):
+    """Winding numbers of Gamma_m at the charges (pbfb_check_charges, host only); raises
+    PbfbError (INVALID) when a charge is not strictly inside.  Returns the winding numbers."""
+    x = np.ascontiguousarray(xyz, np.float64)
+    t = np.ascontiguousarray(gm_tris, np.int32)
+    q = np.ascontiguousarray(q_xyz, np.float64).reshape(-1, 3)
+    w = np.zeros(q.shape[0])
+    _check(load().pbfb_check_charges(_ptr(x), x.shape[0], _ptr(t), t.shape[0], _ptr(q), q.shape[0], _ptr(w)))
+    return w
 
 
 def current_stream() -> int:
@@ -406,9 +419,14 @@ class Server:
         _check(load().pbfb_server_submit(self.h, ctypes.byref(r)))
 
     def poll(self, max_n=64, timeout_us=0):
+        """Completed responses (at most max_n), waiting up to timeout_us for the first; [] when the
+        wait ends empty (PBFB_ERR_TIMEOUT)."""
         buf = (Response * max_n)()
         n = ctypes.c_int()
-        _check(load().pbfb_server_poll(self.h, buf, max_n, timeout_us, ctypes.byref(n)))
+        code = load().pbfb_server_poll(self.h, buf, max_n, timeout_us, ctypes.byref(n))
+        if code == ERR_TIMEOUT:
+            return []
+        _check(code)
         return [buf[i].as_dict() for i in range(n.value)]
 
     def stats(self):

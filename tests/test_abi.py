@@ -171,3 +171,41 @@ def test_ctypes_mirrors_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f in py._fields_:
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
+
+
+def test_charges_must_lie_strictly_inside_gamma_m(lib, tiny_case):
+    """pbfb_check_charges (the host check pbfb_charges_set runs before any GPU work): the winding
+    number of the closed Gamma_m is 1 at a point inside, 0 outside and 1/2 on a face, and a charge
+    on Gamma_m or outside it is refused with PBFB_ERR_INVALID naming that charge."""
+    c = tiny_case
+    xyz = np.ascontiguousarray(c.xyz, np.float64)
+    gm = np.ascontiguousarray(c.gm_tris, np.int32)
+
+    def check(q):
+        q = np.ascontiguousarray(q, np.float64).reshape(-1, 3)
+        w = np.full(q.shape[0], np.nan)
+        code = lib.pbfb_check_charges(xyz.ctypes.data, xyz.shape[0], gm.ctypes.data, gm.shape[0],
+                                      q.ctypes.data, q.shape[0], w.ctypes.data)
+        return code, w
+
+    # radius of the largest ball about the centre inside the polyhedron (distance to the face planes)
+    P = xyz[gm]
+    nrm = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+    r_in = np.abs(np.einsum("ij,ij->i", nrm, P[:, 0]) / np.linalg.norm(nrm, axis=1)).min()
+    inside = np.array([[0.0, 0.0, 0.0], [0.5 * r_in, 0.1, -0.2], [0.0, 0.0, 0.999 * r_in]])
+    code, w = check(inside)
+    assert code == 0 and np.allclose(w, 1.0, atol=1e-12, rtol=0)
+    face = xyz[gm[7]].mean(axis=0)                       # the centroid of a Gamma_m triangle
+    outside = 0.5 * (c.xyz[c.gs_tris[0, 0]] + face)      # in the shell, between the surfaces
+    code, w = check(np.vstack([inside, face, outside]))
+    assert code == 1 and b"charge 3" in lib.pbfb_last_error()
+    assert abs(w[3] - 0.5) < 1e-12 and abs(w[4]) < 1e-12 and np.allclose(w[:3], 1.0, atol=1e-12, rtol=0)
+    code, _ = check(outside)
+    assert code == 1 and b"charge 0" in lib.pbfb_last_error()
+    # the oracle's seeded workloads all pass
+    assert check(c.q_xyz)[0] == 0
+    bad = gm.copy()
+    bad[0, 0] = xyz.shape[0]
+    q = np.zeros(3)
+    assert lib.pbfb_check_charges(xyz.ctypes.data, xyz.shape[0], bad.ctypes.data, bad.shape[0],
+                                  q.ctypes.data, 1, None) == 1

@@ -123,18 +123,18 @@ def test_picard_reaches_the_newton_solution(small_solute):
 
 def test_born_limit(small_solute_case, bem_cache):
     """kappa = 0: no ions (Delta G_Omega_i = 0, no nonlinear part) and Born's energy of a central
-    charge within the nu = 5 discretisation error (0.8 %, as for Kirkwood)."""
+    charge within the nu = 5 discretisation error (measured 0.77 %, as for Kirkwood; bound 0.9 %)."""
     P = solute.SoluteProblem(small_solute_case, kappa=0.0, bem_cache=bem_cache)
     R = pb.solve(P, TIGHT)
     born = 332.0637 * 25.0 / (2 * 4.0) * (1 / P.eps_s - 1 / P.eps_m)
-    assert abs(R.total / born - 1) < 1e-2
+    assert abs(R.total / born - 1) < 9e-3
     assert R.dG_ion == 0.0 and abs(R.NC) < 1e-9 * abs(R.total)
 
 
 def test_uniform_dielectric_has_no_reaction_field(small_solute_case, bem_cache):
     """eps_m = eps_s and no salt: the potential is the charge's own Coulomb field, so the reaction
-    potential and the energy vanish up to the discretisation (0.4 % of the Born scale
-    C z^2 / (2 a eps) on nu = 5)."""
+    potential and the energy vanish up to the discretisation (measured 0.41 % of the Born scale
+    C z^2 / (2 a eps) on nu = 5; bound 0.5 %)."""
     P = solute.SoluteProblem(small_solute_case, eps_in=80.0, eps_out=80.0, kappa=0.0, bem_cache=bem_cache)
     R = pb.solve(P, TIGHT, linear_only=True)
-    assert abs(R.total) < 1e-2 * 332.0637 * 25.0 / (2 * 4.0) / 80.0
+    assert abs(R.total) < 5e-3 * 332.0637 * 25.0 / (2 * 4.0) / 80.0
