@@ -94,7 +94,7 @@ typedef struct pbfb_newton_opts {
   double L_e;           /* reuse the previous omega once e_k < L_e (0 = never) */
   double omega0_first;  /* start of the omega search in the first iteration */
   double omega0_rest;   /* start afterwards */
-  double omega_max;     /* admissible omega in (0, omega_max] */
+  double omega_max;     /* admissible omega in (0, omega_max], finite */
   int max_newton;
   int max_gmres;        /* GMRES iterations per linear solve */
   int restart;          /* GMRES restart length (<= 400) */
@@ -125,6 +125,11 @@ typedef struct pbfb_newton_opts {
                            float32 flops and 4 (n/128*128)^2 bytes of device memory per
                            surface of n vertices (n rounded up to a multiple of 128). */
   int inner_iters;      /* PCG iterations per block-preconditioner application (1..500) */
+  double accept_ratio;  /* a relaxation factor is accepted when ||d(omega)||^2 < accept_ratio
+                           ||d(0)||^2, in [0, 1]; 1 (default) is the paper's global convergence
+                           condition ||d(omega)|| < ||d(0)|| (Sec. 2.5.2), smaller values ask for
+                           a sufficient decrease, and 0 makes every search fail (PBFB_ERR_OMEGA),
+                           which tests use to force that path */
 } pbfb_newton_opts;
 
 #define PBFB_MAX_TRACE 64

@@ -58,6 +58,7 @@ class Opts:
     method: str = 'newton'        # 'newton' (Sec. 2.4.2) or 'picard' (Sec. 2.4.1)
     omega_warm_start: bool = False  # Newton, first iteration: bisection + secant start (Sec. 3.5)
     R_e: float = 1.4              # Picard: recompute omega only when e_{k-1} / e_k < R_e (0 = always)
+    accept_ratio: float = 1.0     # accept omega when ||d(omega)||^2 < accept_ratio ||d(0)||^2 (1: Sec. 2.5.2)
 
 
 class Problem:
@@ -437,7 +438,7 @@ def energy(P: Problem, xL, xNL):
 def solve(P: Problem, opts: Opts = None, linear_only=False):
     """Full solve: linear part, Newton loop with the omega search, energy."""
     opts = opts or Opts()
-    trace = dict(gmres=[], omega=[], e=[], omega_evals=[], scheme=[], dnorm=[])
+    trace = dict(gmres=[], omega=[], e=[], omega_evals=[], scheme=[], dnorm=[], tol_gmres=[])
     tol = opts.tol_gmres0
     Mlin = P.J(np.zeros(P.nv), 'linear')                      # eps_s kappa^2 M (F' = 1)
     xL, its = linear_solve(P, Mlin, P.b, tol, opts)
@@ -463,7 +464,7 @@ def solve(P: Problem, opts: Opts = None, linear_only=False):
             # the iterate solves Eq. NR_main's system exactly (e.g. no charges): Delta = 0 for every
             # omega, so e_k = 0 < Tol_NL (Sec. 3.5) and no relaxation factor is searched for
             for key, v in (('gmres', 0), ('scheme', scheme), ('dnorm', 0.0), ('omega', 0.0), ('e', 0.0),
-                           ('omega_evals', 0)):
+                           ('omega_evals', 0), ('tol_gmres', tol)):
                 trace[key].append(v)
             break
         # Newton: Acal(J) Delta = d (Eq. NR_main); Picard: Acal(0) Delta = d, Delta = Phi~ - Phi_NL
@@ -471,6 +472,7 @@ def solve(P: Problem, opts: Opts = None, linear_only=False):
         Jm = None if picard else P.J(u, scheme)
         du, its = linear_solve(P, Jm, d, tol, opts)
         trace['gmres'].append(its)
+        trace['tol_gmres'].append(tol)
         trace['scheme'].append(scheme)
         trace['dnorm'].append(float(np.linalg.norm(d)))
         if not opts.omega_search:
@@ -488,10 +490,13 @@ def solve(P: Problem, opts: Opts = None, linear_only=False):
             om0 = opts.omega0_first if k == 0 else opts.omega0_rest
             if k == 0 and opts.omega_warm_start and not picard:
                 om0 = warm_start_omega(P, u, du[:P.nv], c, p, scheme, opts, trace)
+            # the global convergence condition of Sec. 2.5.2, ||d(omega)|| < ||d(0)||, scaled by
+            # accept_ratio (1: the paper's condition; below 1 a sufficient decrease)
+            d0n2 = opts.accept_ratio * float(d @ d)
             if picard:
-                om = picard_omega(P, u, du[:P.nv], c, p, float(d @ d), scheme, om0, opts, trace)
+                om = picard_omega(P, u, du[:P.nv], c, p, d0n2, scheme, om0, opts, trace)
             else:
-                om = omega_search(P, u, du[:P.nv], c, p, float(d @ d), scheme, om0, opts, trace)
+                om = omega_search(P, u, du[:P.nv], c, p, d0n2, scheme, om0, opts, trace)
         om_last = om
         xNL = xNL + om * du
         e = om * float(np.linalg.norm(du))

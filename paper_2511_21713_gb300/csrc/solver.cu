@@ -1259,7 +1259,8 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
     return PBFB_ERR_STATE;
   }
   if (!(o.tol_nl > 0) || !(o.tol_gmres > 0) || !(o.tol_gmres0 > 0) || !(o.tol_omega > 0) || o.max_newton < 1 ||
-      o.max_gmres < 1 || !(o.omega_max > 0) || o.max_omega_iters < 1 ||
+      o.max_gmres < 1 || !(o.omega_max > 0) || !std::isfinite(o.omega_max) || o.max_omega_iters < 1 ||
+      !(o.accept_ratio >= 0.0 && o.accept_ratio <= 1.0) ||
       o.n_taylor < 0 || o.n_taylor > 4 || (o.method != PBFB_NEWTON && o.method != PBFB_PICARD) || !(o.R_e >= 0) ||
       (o.precision != PBFB_FP64 && o.precision != PBFB_MIXED)) {
     set_error("solve: invalid options");
@@ -1376,9 +1377,11 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
       int warm_evals = 0;
       if (k == 0 && o.omega_warm_start && !picard)
         PB_TRY(warm_start_omega(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, o, &om0, &warm_evals));
-      st = picard ? picard_omega(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, d2, om0, o, &om, &evals,
+      // the global convergence condition of Sec. 2.5.2, ||d(omega)|| < ||d(0)||, scaled by accept_ratio
+      const double d0n2 = o.accept_ratio * d2;
+      st = picard ? picard_omega(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, d0n2, om0, o, &om, &evals,
                                  &R.omega_fallbacks)
-                  : omega_search(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, d2, om0, o, &om, &evals,
+                  : omega_search(m, scheme, m->phi.p, m->du.p, m->cvec.p, m->pvec.p, d0n2, om0, o, &om, &evals,
                                  &R.omega_fallbacks);
       evals += warm_evals;
       if (st) {
@@ -1552,6 +1555,7 @@ void pbfb_default_opts(pbfb_newton_opts* o) {
   o->omega_search = 1;
   o->precond = PBFB_PRECOND_BLOCK_DENSE;
   o->inner_iters = 30;
+  o->accept_ratio = 1.0;
 }
 
 const char* pbfb_last_error(void) { return pbfb::last_error(); }

@@ -57,7 +57,7 @@ class NewtonOpts(ctypes.Structure):
                 ("taylor", ctypes.c_int * 4), ("method", ctypes.c_int), ("R_e", ctypes.c_double),
                 ("omega_warm_start", ctypes.c_int),
                 ("omega_search", ctypes.c_int), ("precond", ctypes.c_int),
-                ("inner_iters", ctypes.c_int)]
+                ("inner_iters", ctypes.c_int), ("accept_ratio", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):

@@ -262,6 +262,31 @@ def test_picard_and_taylor_schedules(pair):
         assert np.allclose(rp["omega"], Ro.trace["omega"], rtol=1e-3, atol=1e-3)
 
 
+def test_forced_fallback_and_picard_secant_follow_the_oracle(pair):
+    """The omega search's scan-and-bisect fallback (forced: one Newton step on f_d, unreachable
+    Tol_omega) for Newton and Picard, and Picard's direct secant (Eq. SEC_FD) with its R_e reuse
+    rule, through pbfb_solve at tight GMRES tolerances: the oracle's omega sequence to 1e-9, the
+    same number of fallbacks, and the same discrete solution (1e-8 L2, 1e-9 energy)."""
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    tight = dict(tol_gmres0=1e-12, tol_gmres=1e-12, tol_nl=1e-10)
+    forced = dict(max_omega_iters=1, tol_omega=1e-14)
+    pic = dict(omega0_first=0.5, omega0_rest=0.5)
+    for gkw, okw in ((forced, forced),
+                     (dict(method=pbfb.PICARD, **pic, **forced), dict(method="picard", **pic, **forced)),
+                     (dict(method=pbfb.PICARD, **pic), dict(method="picard", **pic))):
+        x, res = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.default_opts(**gkw, **tight))
+        R = pb.solve(P, pb.Opts(**okw, **tight))
+        assert res["newton_iters"] == R.newton_iters, okw
+        assert np.abs(np.array(res["omega"]) - np.array(R.trace["omega"])).max() < 1e-9, okw
+        assert res["omega_fallbacks"] == R.trace.get("fallback", 0), okw
+        if "max_omega_iters" in okw:
+            assert res["omega_fallbacks"] >= 1
+        assert abs(res["total"] - R.total) < 1e-9 * abs(R.total)
+        assert rel(x, R.x) < 1e-8
+
+
 def test_deterministic(pair):
     from paper_2511_21713_gb300 import pbfb
     case, m, _ = pair
@@ -320,9 +345,29 @@ def test_error_statuses(tiny_case):
     with pytest.raises(pbfb.PbfbError) as e:
         m.solve(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.default_opts(max_gmres=3, tol_gmres0=1e-12))
     assert e.value.code == 3                       # GMRES_NOCONV
-    # the handle stays usable after errors
+    _, ref = m.solve(c.eps_in, c.eps_out, c.kappa, c.T)
+    # no relaxation factor may be accepted (||d(omega)||^2 < 0 ||d(0)||^2): the search and its
+    # fallback both refuse
+    with pytest.raises(pbfb.PbfbError) as e:
+        m.solve(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.default_opts(accept_ratio=0.0))
+    assert e.value.code == 5                       # OMEGA
+    # a constant omega of 1e300 overflows the update or the next residual's sinh
+    with pytest.raises(pbfb.PbfbError) as e:
+        m.solve(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.default_opts(omega_search=0, omega0_first=1e300))
+    assert e.value.code == 6                       # NONFINITE
+    for bad in (dict(omega_max=float("inf")), dict(accept_ratio=1.5), dict(accept_ratio=-0.1)):
+        with pytest.raises(pbfb.PbfbError) as e:
+            m.solve(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.default_opts(**bad))
+        assert e.value.code == 1, bad
+    # a charge on Gamma_m or outside it: refused on the host, the mesh keeps its charges
+    face = c.xyz[c.gm_tris[3]].mean(axis=0)
+    for q in (np.vstack([c.q_xyz, face]), np.vstack([c.q_xyz, [0.0, 0.0, 7.0]])):
+        with pytest.raises(pbfb.PbfbError) as e:
+            m.charges_set(q, np.ones(q.shape[0]))
+        assert e.value.code == 1 and "not strictly inside" in str(e.value)
+    # the handle stays usable after errors, with the same result
     _, res = m.solve(c.eps_in, c.eps_out, c.kappa, c.T)
-    assert res["status"] == 0
+    assert res["status"] == 0 and res["total"] == ref["total"]
     m.close()
 
 

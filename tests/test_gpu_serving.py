@@ -203,3 +203,23 @@ def test_meshes_of_omega_m_and_omega_i_served_and_batched():
         for r in (got[i], batch[i]):
             assert r["status"] == 0 and abs(r["total"] - s["total"]) < 1e-9 * abs(s["total"])
     assert got[len(cases)]["total"] == got[0]["total"]
+
+
+def test_poll_times_out_without_a_response():
+    """pbfb_server_poll's bounded wait: with nothing submitted a 20 ms wait ends with
+    PBFB_ERR_TIMEOUT and no response; the server then serves a request normally."""
+    import ctypes
+    from paper_2511_21713_gb300 import pbfb
+    sv = pbfb.Server(budget_bytes=8 << 30, max_inflight=1)
+    buf = (pbfb.Response * 4)()
+    n = ctypes.c_int(-1)
+    t0 = time.time()
+    code = pbfb.load().pbfb_server_poll(sv.h, buf, 4, 20000, ctypes.byref(n))
+    assert code == pbfb.ERR_TIMEOUT and n.value == 0 and time.time() - t0 >= 0.015
+    assert b"no response" in pbfb.load().pbfb_last_error()
+    assert pbfb.load().pbfb_server_poll(sv.h, buf, 4, 0, ctypes.byref(n)) == 0 and n.value == 0
+    c = _mix()[0]
+    sv.submit(c, 7)
+    r = _collect(sv, 1)[7]
+    assert r["status"] == 0
+    sv.close()

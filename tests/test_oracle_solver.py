@@ -6,7 +6,10 @@ central charge in a sphere, Born's formula at kappa = 0, a high-resolution
 radial boundary-value solve of the nonlinear spherical problem
 (scipy.integrate.solve_bvp), a sparse direct solve for GMRES, Gauss's law,
 finite differences for f_d', quadratic Newton convergence and the small-charge
-scaling of the nonlinear terms.
+scaling of the nonlinear terms.  The omega search's fallback is pinned by a
+brute-force minimisation of the residual norm itself, Picard's first secant step
+by Eq. SEC_FD and f_d(0) = 1, and the reuse rules (R_e, L_e) and the GMRES
+tolerance schedule on the recorded traces.
 """
 import numpy as np
 import pytest
@@ -261,3 +264,146 @@ def test_taylor_schemes_are_sinh_series():
     # higher degree is closer to sinh
     errs = [np.abs(fem.F_scheme(n, u)[0] - np.sinh(u)).max() for n in ('T3', 'T5', 'T7')]
     assert errs[0] > errs[1] > errs[2]
+
+
+def _step_inputs(P, Phi, scheme, picard=False):
+    """u, c = b - Acal(0) Phi, d = c - [N(u); 0; 0], the exact increment Delta (sparse direct solve
+    of Acal(J) Delta = d, J = 0 for Picard) and p = -Acal(0) Delta at the iterate Phi."""
+    u = Phi[:P.nv]
+    c = P.b - P.apply(Phi)
+    d = c - P.pad(P.N(u, scheme))
+    J = None if picard else P.J(u, scheme)
+    du = pb.linear_solve(P, J, d, 0.0, pb.Opts(linear_solver="direct"))[0]
+    return u, c, d, du, -P.apply(du)
+
+
+def _golden_min(f, a, b, tol=1e-10):
+    """Minimiser of a unimodal f on [a, b] by golden-section search (function values only)."""
+    g = (np.sqrt(5.0) - 1.0) / 2.0
+    x1, x2 = b - g * (b - a), a + g * (b - a)
+    f1, f2 = f(x1), f(x2)
+    while b - a > tol:
+        if f1 < f2:
+            b, x2, f2 = x2, x1, f1
+            x1 = b - g * (b - a)
+            f1 = f(x1)
+        else:
+            a, x1, f1 = x1, x2, f2
+            x2 = a + g * (b - a)
+            f2 = f(x2)
+    return 0.5 * (a + b)
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_fallback_returns_the_minimiser_of_the_residual_norm(tiny_problem, k):
+    """The scan-and-bisect fallback of the omega search (reading R10 of the global convergence
+    condition of Sec. 2.5.2) returns the minimiser of ||d(omega)||^2 on (0, omega_max]: checked
+    against a brute-force search on the residual itself, d(omega) = b - Acal(0)(Phi + omega Delta)
+    - [N(u + omega Delta_u); 0; 0] (a 1000-point grid, then golden section), not on the dot
+    products the fallback uses.  k = 0: the T3 step from x_L; k = 1: the sinh step after it."""
+    P = tiny_problem
+    Phi = pb.solve(P, TIGHT, linear_only=True).x
+    if k == 1:
+        u, c, d, du, p = _step_inputs(P, Phi, "T3")
+        om = pb.omega_search(P, u, du[:P.nv], c, p, float(d @ d), "T3", 2.0, pb.Opts(), dict(omega_evals=[]))
+        Phi = Phi + om * du
+    scheme = "T3" if k == 0 else "HS"
+    u, c, d, du, p = _step_inputs(P, Phi, scheme)
+    om_fb = pb._fallback(P, u, du[:P.nv], c, p, float(d @ d), scheme, pb.Opts())
+    ADelta = P.apply(du)
+
+    def dn2(o):
+        dv = c - o * ADelta - P.pad(P.N(u + o * du[:P.nv], scheme))
+        return float(dv @ dv)
+
+    grid = np.linspace(0.0, 4.0, 1001)[1:]
+    vals = np.array([dn2(o) for o in grid])
+    j = int(np.argmin(vals))
+    om_bf = _golden_min(dn2, grid[max(j - 1, 0)], grid[min(j + 1, grid.size - 1)])
+    # bisection accuracy (omega_max / 16) / 2^20 = 2.4e-7; the minimum is flat, so golden section
+    # on function values locates it to about sqrt(rounding) of the curvature scale
+    assert abs(om_fb - om_bf) < 2e-6, (om_fb, om_bf)
+    assert dn2(om_fb) < dn2(0.0) and dn2(om_fb) <= vals.min() * (1 + 1e-12)
+
+
+def test_forced_fallback_solves_reach_the_same_solution(tiny_problem):
+    """max_omega_iters = 1 with an unreachable Tol_omega sends every omega search to the
+    fallback (Newton and Picard); the iteration still converges to the discrete solution."""
+    P = tiny_problem
+    ref = pb.solve(P, TIGHT)
+    tight = dict(tol_gmres0=1e-12, tol_gmres=1e-12, tol_nl=1e-10, max_omega_iters=1, tol_omega=1e-14)
+    for o in (pb.Opts(**tight), pb.Opts(method="picard", omega0_first=0.5, omega0_rest=0.5, **tight)):
+        R = pb.solve(P, o)
+        searches = sum(1 for n in R.trace["omega_evals"] if n > 0)
+        assert R.trace.get("fallback", 0) == searches >= 1
+        assert abs(R.total - ref.total) < 1e-10 * abs(ref.total)
+
+
+def test_picard_direct_secant(tiny_problem):
+    """Appendix A for Picard: f_d(0) = 1 (Delta solves Acal(0) Delta = d, so p + r(0) = 0), and the
+    first secant step through (0, f_d(0) = 1) and (omega0, f_d(omega0)) is the direct formula
+    Eq. SEC_FD, omega = omega0 / (1 - f_d(omega0)).  With Tol_omega between |f_d(omega0)| and
+    |f_d| at that point, picard_omega returns exactly that omega after two evaluations."""
+    P = tiny_problem
+    xL = pb.solve(P, TIGHT, linear_only=True).x
+    u, c, d, du, p = _step_inputs(P, xL, "T3", picard=True)
+    f = lambda o: pb.fd_and_derivative(pb.omega_dots(P, u, du[:P.nv], c, p, o, "T3"), o)[0]
+    assert abs(f(0.0) - 1.0) < 1e-12
+    om0 = 0.5
+    f0 = f(om0)
+    om1 = om0 / (1.0 - f0)
+    f1 = f(om1)
+    assert abs(f1) < 0.5 * abs(f0)
+    tr = dict(omega_evals=[])
+    om = pb.picard_omega(P, u, du[:P.nv], c, p, float(d @ d), "T3", om0,
+                         pb.Opts(tol_omega=np.sqrt(abs(f0 * f1))), tr)
+    assert om == om1 and tr["omega_evals"] == [2] and "fallback" not in tr
+
+
+@pytest.mark.parametrize("R_e", [1.4, 3.0])
+def test_picard_R_e_rule_on_the_trace(tiny_problem, R_e):
+    """Appendix B: a Picard step keeps the previous omega exactly when the last two errors fell by
+    at least R_e (e_{k-1} / e_k >= R_e in the paper's indexing; with trace index j, e[j-2] / e[j-1]),
+    and recomputes it otherwise (always in the first two steps, which have no such ratio)."""
+    P = tiny_problem
+    R = pb.solve(P, pb.Opts(method="picard", omega0_first=0.5, omega0_rest=0.5, R_e=R_e))
+    e, ev, om = R.trace["e"], R.trace["omega_evals"], R.trace["omega"]
+    kinds = set()
+    for j in range(len(e)):
+        reuse = j >= 2 and e[j - 2] / e[j - 1] >= R_e
+        kinds.add(reuse)
+        assert (ev[j] == 0) == reuse, (j, e[j - 2:j], ev[j])
+        if reuse:
+            assert om[j] == om[j - 1]
+    assert kinds == {True, False}
+
+
+def test_accept_ratio_zero_fails_the_search(tiny_problem):
+    """accept_ratio = 0 leaves no omega satisfying ||d(omega)||^2 < 0: the search and its fallback
+    both refuse, which is how the omega-search failure is forced on the host."""
+    P = tiny_problem
+    with pytest.raises(RuntimeError, match="omega search failed"):
+        pb.solve(P, pb.Opts(accept_ratio=0.0))
+
+
+def test_newton_L_e_rule_and_tolerance_schedule_on_the_trace(small_problem):
+    """Appendix B: once the last update e_{k-1} < L_e the Newton step reuses the previous omega
+    without a search, and otherwise searches; the GMRES tolerance starts at Tol_GR0 and after a
+    step with e < 1250 tol drops tenfold, not below Tol_GR (reading R12)."""
+    P = small_problem
+    o = pb.Opts()
+    R = pb.solve(P, o)
+    e, ev, om, tol = R.trace["e"], R.trace["omega_evals"], R.trace["omega"], R.trace["tol_gmres"]
+    kinds = set()
+    for k in range(len(e)):
+        reuse = k > 0 and e[k - 1] < o.L_e
+        kinds.add(reuse)
+        assert (ev[k] == 0) == reuse, (k, e[k - 1:k + 1], ev[k])
+        if reuse:
+            assert om[k] == om[k - 1]
+    assert kinds == {True, False}
+    assert tol[0] == o.tol_gmres0
+    for k in range(1, len(tol)):
+        expect = max(0.1 * tol[k - 1], o.tol_gmres) if e[k - 1] < 1250.0 * tol[k - 1] else tol[k - 1]
+        assert tol[k] == expect
+    assert tol[-1] < tol[0]
