@@ -9,15 +9,19 @@ charges set before timing (inputs resident in HBM).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
                   [--impl pbfb|reference]
+  python bench.py --step farfield_f32|farfield_ff|farfield_f64|assemble|omega|gmres [--reps R]
+                  [--workload small]   (one step of the solve, for profiler captures)
 
-Beside the headline line's workload, "full_formulation" times the paper's own formulation (FEM
-over Omega_m and Omega_i, charges as point loads, lam_m from the Gamma_m equation) on the same
-sphere meshed inside Gamma_m too.
+Beside the headline line's workload: the plain float64 GPU path timed over the same
+number of solves ("fp64_gpu"), "full_formulation" (the paper's own formulation: FEM
+over Omega_m and Omega_i, charges as point loads, lam_m from the Gamma_m equation, on
+the same sphere meshed inside Gamma_m too), a serving run, and the CPU oracle.
 
 --impl reference times the CPU oracle (the plain float64 restatement of the
-method under oracle/) on a bounded sample of the same workload, scaled to
-solves/s.  Under torchrun (N > 1) every rank runs independent replicas of the
-solve (no collective on the data path); rank 0 prints.
+method under oracle/) on bounded samples of the same workload, scaled to
+solves/s with the oracle's own iteration counts.  Under torchrun (N > 1) every
+rank runs independent replicas of the solve (no collective on the data path);
+rank 0 prints.
 """
 import argparse
 import json
@@ -32,26 +36,28 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "nonlinear PB solves/s and p99 ms, mixed vs FP64 GPU at ≤1e-5 rel energy err"
-SM_COUNT = 152
-FP32_LANES = 128
-SM_MAX_MHZ = 2070.0
-# float32 operations per far-field pair (FMA counted as 2): Laplace 18, Yukawa 24
-FLOP_PAIR = {"laplace": 18.0, "yukawa": 24.0}
+FP32_LANES = 128          # float32 FMA lanes per SM (Blackwell)
+SM_MAX_MHZ = 2070.0       # GB300 maximum SM clock, used when nvidia-smi reports none
+# algorithmic float32 work of one ordered far-field pair (FMA = 2): the fused single + double
+# layer, about 20 flops for the Laplace kernel and 28 for the Yukawa kernel (its exponential
+# factor and (1 + kappa r) term), with one rsqrt (and one exp) on the special-function unit
+FLOP_PAIR = {"laplace": 20.0, "yukawa": 28.0}
 GOLDEN = os.path.join(ROOT, "tests", "golden", "multi_charge_sphere.json")
-# DRAM bytes (read + write) per launch of the packed far-field kernel on this workload, from its
-# ncu capture (profiles/k_nbody_f32x2_multi_charge_sphere.md; source records read once)
+# DRAM bytes (read + write) per launch on this workload, each from an ncu capture of the kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum): the packed float32 far field (source records
+# read once) and the packed mutual float-float far field
 NBODY_TRAFFIC = 2311424.0
-# float32 flops (FMA = 2) per ordered point pair of the mutual float-float kernel and its DRAM bytes
-# per launch, from its ncu capture (profiles/k_nbody_ffm_multi_charge_sphere.md)
-FF_FLOP_PAIR = {"laplace": 120.1, "yukawa": 179.3}
-FF_TRAFFIC = 15.2e6
-# the same per launch of the packed mutual kernel (two targets per thread; same per-pair arithmetic),
-# from its ncu capture (profiles/k_nbody_ffm2_multi_charge_sphere.md)
 FF2_TRAFFIC = 15.17e6
-# float32 lane operations (FADD, FMUL and FFMA each 1; a packed instruction 2) per ordered pair of
-# the float-float evaluation, counted by ncu on the packed mutual kernel: the float32 pipe's view,
-# against 152 SM x 128 lanes x 2070 MHz (three quarters of the operations are additions)
+FF_TRAFFIC = 15.2e6
+# float32 lane operations (FADD, FMUL, FFMA each 1; a packed instruction 2) per ordered pair that
+# the float-float evaluation issues, counted by ncu on the packed mutual kernel: the emulation's
+# cost, against 20 / 28 flops of the method's own arithmetic
 FF_OPS_PAIR = {"laplace": 97.7, "yukawa": 145.7}
+# the oracle's measured full solve of this workload on one host (x86-64, 8 cores: dense BEM
+# set-up and the default-tolerance solve, written by tests/golden/make_golden.py), against which
+# the sampled CPU model was checked once on that host
+ORACLE_C2_MEASURED_HOST = "x86-64, 8 cores"
+ORACLE_C2_MODEL_ON_THAT_HOST = float("nan")
 
 
 def workload_config(case, precision):
@@ -308,17 +314,26 @@ def run_pbfb(args):
 
     # roofline of the dominant kernel from its live CUDA-event timing (in the timed region): in the
     # mixed precision the float32 far field of the GMRES operator or the float-float far field of
-    # the Newton residual, whichever takes the larger share of the step; float64 otherwise
-    peak32 = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    # the Newton residual, whichever takes the larger share of the step; float64 otherwise.  Work =
+    # the method's float32 flops per ordered pair (20 Laplace, 28 Yukawa; the two surfaces have
+    # equal point counts here, so 24 per pair on average) x the pairs a launch evaluates; peak =
+    # SMs (read from the device) x 128 lanes x 2 flops x the maximum SM clock
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk.get("sm_max_mhz") or SM_MAX_MHZ
+    peak32 = sm_count * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    peak_basis = (f"fp32 non-tensor: {sm_count} SMs (device attribute) x {FP32_LANES} lanes x 2 flops (FMA) x "
+                  f"{sm_mhz:.0f} MHz (maximum SM clock) = {peak32:.2f} TFLOP/s; work = "
+                  f"{FLOP_PAIR['laplace']:.0f} flops per ordered Laplace pair and {FLOP_PAIR['yukawa']:.0f} per "
+                  f"Yukawa pair x the (6 N_t)^2 pairs of each launch")
+    fpair = 0.5 * (FLOP_PAIR["laplace"] + FLOP_PAIR["yukawa"])
     cands = []
     if prec == pbfb.MIXED:
         l32, ms32 = prof["nbody_launches"], prof["nbody_ms"]
         if l32:
             cands.append(dict(kernel="k_nbody_f32x2 (float32 far field of the GMRES operator, packed, 2 targets "
                                      "per thread)", launches=l32, ms=ms32, pairs=prof["nbody_pairs"],
-                              flops=prof["nbody_flops"], peak=peak32, traffic=NBODY_TRAFFIC,
-                              peak_basis="fp32 non-tensor: 152 SM x 128 lanes x 2 flop x 2070 MHz; "
-                                         "18 flop per Laplace pair, 24 per Yukawa pair"))
+                              flops=prof["nbody_pairs"] * fpair, peak=peak32, traffic=NBODY_TRAFFIC,
+                              peak_basis=peak_basis))
         lff, msff = prof["nbodyff_launches"], prof["nbodyff_ms"]
         packed_ff = tuned.get("ff_kernel") == 4
         if lff:
@@ -326,35 +341,35 @@ def run_pbfb(args):
                                      "2 targets per thread)" if packed_ff else
                                      "k_nbody_ffm (float-float far field of the Newton residual, mutual pairs)",
                               launches=lff, ms=msff, pairs=prof["nbodyff_pairs"],
-                              flops=prof["nbodyff_pairs"] * 0.5 * (FF_FLOP_PAIR["laplace"] + FF_FLOP_PAIR["yukawa"]),
+                              flops=prof["nbodyff_pairs"] * fpair,
                               lane_ops=prof["nbodyff_pairs"] * 0.5 * (FF_OPS_PAIR["laplace"] + FF_OPS_PAIR["yukawa"]),
                               peak=peak32, traffic=FF2_TRAFFIC if packed_ff else FF_TRAFFIC,
-                              peak_basis="fp32 non-tensor: 152 SM x 128 lanes x 2 flop x 2070 MHz; float32 flops "
-                                         "of the float-float pair evaluation per ordered pair (FMA = 2), "
-                                         "%.1f Laplace / %.1f Yukawa, counted by ncu"
-                                         % (FF_FLOP_PAIR["laplace"], FF_FLOP_PAIR["yukawa"])))
+                              peak_basis=peak_basis))
     else:
         l64, ms64 = prof["nbody64_launches"], prof["nbody64_ms"]
         cands.append(dict(kernel="k_nbody_f64", launches=l64, ms=ms64, pairs=prof["nbody64_pairs"],
-                          flops=prof["nbody64_pairs"] * 0.5 * (FLOP_PAIR["laplace"] + FLOP_PAIR["yukawa"]),
-                          peak=1.25, traffic=None, peak_basis="fp64 nominal 1.25 TFLOP/s"))
+                          flops=prof["nbody64_pairs"] * fpair,
+                          peak=1.25, traffic=None, peak_basis="fp64 nominal 1.25 TFLOP/s (GB300)"))
 
     def roofline_of(c):
         launches = max(c["launches"], 1)
         avg_ms = c["ms"] / launches
         achieved = (c["flops"] / launches) / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else None
-        lanes = None
+        emu = None
         if c.get("lane_ops") and avg_ms > 0:
-            peak_lanes = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+            peak_lanes = sm_count * FP32_LANES * sm_mhz * 1e6 / 1e12
             a = (c["lane_ops"] / launches) / (avg_ms * 1e-3) / 1e12
-            lanes = {"achieved": a, "peak": peak_lanes, "unit": "T float32 lane-ops/s", "frac": a / peak_lanes}
+            emu = {"note": "float-float emulation: float32 lane operations issued per ordered pair (ncu) "
+                           f"{FF_OPS_PAIR['laplace']} Laplace / {FF_OPS_PAIR['yukawa']} Yukawa against the "
+                           "method's 20 / 28 flops",
+                   "achieved": a, "peak": peak_lanes, "unit": "T float32 lane-ops/s", "frac": a / peak_lanes}
         return {"bound": "alu", "kernel": c["kernel"], "achieved": achieved, "peak": c["peak"],
                 "unit": "TFLOP/s", "frac": (achieved / c["peak"]) if achieved else None,
-                "fp32_pipe_view": lanes,
                 "traffic": c["traffic"] if args.workload == "multi_charge_sphere" else None,
                 "peak_basis": c["peak_basis"], "avg_launch_ms": avg_ms,
                 "pairs_per_launch": c["pairs"] / launches, "launches": c["launches"],
-                "share_of_step": c["ms"] / total_ms if total_ms else None}
+                "share_of_step": c["ms"] / total_ms if total_ms else None,
+                "float_float_emulation": emu}
 
     rooflines = sorted((roofline_of(c) for c in cands), key=lambda r: -(r["share_of_step"] or 0))
 
@@ -381,23 +396,39 @@ def run_pbfb(args):
                   "gmres": res["gmres"], "omega": [round(w, 4) for w in res["omega"]],
                   "total_kcal_mol": res["total"], "LC": res["LC"], "NC": res["NC"], "dG_ion": res["dG_ion"]},
     }
-    # the plain float64 GPU path on the same input (one solve, outside the timed region)
+    # the plain float64 GPU path on the same input and mesh: one untimed solve, then as many solves
+    # as the mixed arm timed, each with CUDA events after an L2 flush (after the mixed arm's timed
+    # region, so that its clock record covers the headline number alone)
     if args.fp64_compare and prec == pbfb.MIXED:
         o64 = pbfb.default_opts(precision=pbfb.FP64)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        n64 = args.steps if args.fp64_steps < 0 else args.fp64_steps
         r64 = mesh.solve_device(case.eps_in, case.eps_out, case.kappa, case.T, x_out, o64)
-        e1.record(stream)
-        e1.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        out["fp64_gpu"] = {"ms_per_solve": ms64, "solves_per_s": 1e3 / ms64,
-                           "mixed_speedup": ms64 / (total_ms_max / args.steps),
-                           "mixed_energy_rel_diff": abs(res["total"] - r64["total"]) / abs(r64["total"]),
-                           "newton_iters": r64["newton_iters"], "gmres": r64["gmres"]}
+        ms64 = []
+        for _ in range(n64):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r64 = mesh.solve_device(case.eps_in, case.eps_out, case.kappa, case.T, x_out, o64)
+            e1.record(stream)
+            e1.synchronize()
+            ms64.append(e0.elapsed_time(e1))
+        if ms64:
+            m64 = sum(ms64) / len(ms64)
+            out["fp64_gpu"] = {"steps": len(ms64), "warmup": 1, "ms_per_solve": m64,
+                               "solves_per_s": len(ms64) / (sum(ms64) / 1e3),
+                               "p50_ms": statistics.median(ms64), "p99_ms": float(np.percentile(ms64, 99)),
+                               "mixed_speedup": m64 / (total_ms_max / args.steps),
+                               "mixed_energy_rel_diff": abs(res["total"] - r64["total"]) / abs(r64["total"]),
+                               "newton_iters": r64["newton_iters"], "gmres": r64["gmres"],
+                               "total_kcal_mol": r64["total"]}
+            if os.path.exists(GOLDEN):
+                ref = json.load(open(GOLDEN))["tight"]["total"]
+                out["fp64_gpu"]["energy_rel_err_vs_oracle"] = abs(r64["total"] - ref) / abs(ref)
     if args.full_formulation and ws == 1 and args.workload == "multi_charge_sphere":
         out["full_formulation"] = run_full_formulation(pbfb, inputs, tuned, opts, res, flush, stream)
+    if args.helix > 0 and ws == 1 and args.workload == "multi_charge_sphere":
+        out["double_helix"] = run_helix(pbfb, inputs, opts, flush, stream, args.helix)
     if args.serving > 0 and args.workload == "multi_charge_sphere":
         cases = serving_cases(args.serving)
         out["serving"] = run_serving(pbfb, cases, 4, 64 << 30)
@@ -406,7 +437,7 @@ def run_pbfb(args):
         ref = g["tight"]["total"]
         out["energy_rel_err_vs_oracle"] = abs(res["total"] - ref) / abs(ref)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "multi_charge_sphere":
-        out["cpu_baseline"] = oracle_sample(case, res, args.cpu_sample)
+        out["cpu_baseline"] = cpu_baseline(case, args.cpu_sample)
     if ws > 1:
         tdist.destroy_process_group()
     mesh.close()
@@ -448,22 +479,88 @@ def run_full_formulation(pbfb, inputs, shapes, opts, shell_res, flush, stream, s
     return out
 
 
-def oracle_sample(case, gpu_res, frac_rows, newton=None):
-    """Time the oracle on a bounded sample of the workload and scale to one solve.
+def run_helix(pbfb, inputs, opts, flush, stream, steps=2):
+    """The synthetic double helix (24 base pairs, 40,500 triangles per surface, 1,944,000 tets,
+    1548 charges, 0.15 M; surface potentials above 10 kT/e): mesh creation and charges, one untimed
+    solve (it builds the Gamma_s corrections, the dense single-layer inverses and the far-field
+    trees), then `steps` solves timed with CUDA events after an L2 flush."""
+    import torch
+    t0 = time.perf_counter()
+    case = inputs.double_helix()
+    gen_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m = pbfb.Mesh.from_case(case)
+    m.charges_set(case.q_xyz, case.q_z)
+    torch.cuda.synchronize()
+    create_ms = 1e3 * (time.perf_counter() - t0)
+    x = torch.empty(m.n, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    r = m.solve_device(case.eps_in, case.eps_out, case.kappa, case.T, x, opts)
+    torch.cuda.synchronize()
+    first_ms = 1e3 * (time.perf_counter() - t0)
+    m.profile(enable=True, reset=True)
+    ms = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = m.solve_device(case.eps_in, case.eps_out, case.kappa, case.T, x, opts)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    prof = m.profile(enable=False, reset=True)
+    tot = sum(ms)
+    out = {"workload": case.name, "n_v": m.n_v, "n_t": m.n_t, "gamma_m_triangles": int(case.gm_tris.shape[0]),
+           "gamma_s_triangles": int(case.gs_tris.shape[0]), "charges": int(len(case.q_z)),
+           "net_charge_e": float(case.q_z.sum()), "kappa_per_A": case.kappa, "steps": steps,
+           "solves_per_s": steps / (tot / 1e3), "ms_per_solve": tot / steps,
+           "input_generation_s": gen_s, "mesh_create_and_charges_ms": create_ms, "first_solve_ms": first_ms,
+           "newton_iters": r["newton_iters"], "gmres": r["gmres"], "linear_gmres": r["linear_gmres"],
+           "omega": [round(w, 4) for w in r["omega"]], "total_kcal_mol": r["total"], "LC": r["LC"],
+           "NC": r["NC"], "dG_ion": r["dG_ion"], "tuning": m.get_tuning(),
+           "share_float32_far_field": prof["nbody_ms"] / tot if tot else None,
+           "share_float_float_far_field": prof["nbodyff_ms"] / tot if tot else None,
+           "float32_pairs_per_launch": prof["nbody_pairs"] / max(prof["nbody_launches"], 1)}
+    m.close()
+    return out
 
-    Sample: dense Galerkin assembly of 1/frac_rows of the test triangles of each
-    surface (both operators, all quadrature classes), one nonlinear load + Jacobian
-    assembly over all tets, one omega evaluation, and one coupled dense apply.  A
-    full oracle solve is modelled as frac_rows x the assembly sample + (Newton steps)
-    x (assembly + omega evaluations) + (matvecs) x apply, with the Newton, omega and
-    GMRES counts of the GPU solve.
+
+def oracle_counts():
+    """Work counts of the oracle's own solve of the bench workload at the paper's tolerances
+    (tests/golden/multi_charge_sphere.json, written by the oracle alone): Newton steps,
+    operator applications (GMRES iterations, one true residual per restart cycle, one residual
+    c and one search direction p per Newton step) and batched omega evaluations."""
+    import math
+    g = json.load(open(GOLDEN))
+    d = g["default"]
+    k = d["newton_iters"]
+    cyc = lambda its: max(1, math.ceil(its / 200))
+    applies = d["linear_gmres"] + cyc(d["linear_gmres"])
+    applies += sum(its + cyc(its) + 1 for its in d["gmres"])
+    applies += sum(1 for ev in d["omega_evals"] if ev > 0)
+    return {"newton_iters": k, "assemblies": k + 1, "applies": applies, "omega_evals": sum(d["omega_evals"]),
+            "measured_setup_s": g["setup_s"], "measured_solve_s": d["seconds"]}
+
+
+def oracle_sample(case, counts, frac_rows):
+    """Time the oracle on a bounded sample of the workload and scale it to one solve.
+
+    Sample: dense Galerkin BEM assembly of 1/frac_rows of the test triangles of each surface
+    (both operators, all quadrature classes), the sparse FEM set-up and Coulomb data, one
+    nonlinear load + Jacobian assembly over all tets, one omega evaluation, one coupled dense
+    apply and one energy evaluation.  One solve is modelled as set-up + frac_rows x the BEM
+    sample + assemblies x assembly + omega evaluations x evaluation + applies x apply + energy,
+    with the oracle's own counts (oracle_counts).
     """
     import numpy as np
-    from oracle import bem, pb
+    import scipy.sparse as sp
+    from oracle import bem, fem, pb
     t = {}
     t0 = time.perf_counter()
     P = object.__new__(pb.Problem)
-    # build the problem pieces without the full dense assembly
+    # the problem's pieces without the full dense assembly
     P.case = case
     P.eps_m, P.eps_s, P.kappa, P.T = case.eps_in, case.eps_out, case.kappa, case.T
     P.kT = pb.KB * P.T
@@ -473,79 +570,178 @@ def oracle_sample(case, gpu_res, frac_rows, newton=None):
     P.sm, P.ss = bem.Surface(case.xyz, case.gm_tris), bem.Surface(case.xyz, case.gs_tris)
     P.nm, P.ns = P.sm.n, P.ss.n
     P.n = P.nv + P.nm + P.ns
-    from oracle import fem
-    import scipy.sparse as sp
     P.A = fem.stiffness(case.xyz, case.tets, P.eps_s)
     P.Mm, P.Ms = bem.mass_matrix(P.sm), bem.mass_matrix(P.ss)
     P.Rm = sp.csr_matrix((np.ones(P.nm), (np.arange(P.nm), P.sm.verts)), shape=(P.nm, P.nv))
     P.Rs = sp.csr_matrix((np.ones(P.ns), (np.arange(P.ns), P.ss.verts)), shape=(P.ns, P.nv))
     P.B_um = P.eps_m * (P.Rm.T @ P.Mm)
     P.B_us = -P.eps_s * (P.Rs.T @ P.Ms)
+    P.b = np.zeros(P.n)
+    P.b[P.nv:P.nv + P.nm] = (P.lB / P.eps_m) * bem.coulomb_rhs(P.sm, case.q_xyz, case.q_z)
     t["setup_fem_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     sub_m = np.arange(0, P.sm.nt, frac_rows)
     sub_s = np.arange(0, P.ss.nt, frac_rows)
+    # dense matrices of the full size with the sampled rows filled: the apply below costs what it
+    # costs on the complete matrices
     P.VL, P.KL = bem.assemble(P.sm, 0.0, test_tris=sub_m)
     P.VY, P.KY = bem.assemble(P.ss, P.kappa, test_tris=sub_s)
     t["bem_sample_s"] = time.perf_counter() - t0
     u = np.zeros(P.nv) + 0.5
     t0 = time.perf_counter()
-    N = P.N(u, "HS")
+    P.N(u, "HS")
     Jm = P.J(u, "HS")
     t["assembly_s"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
     x = np.ones(P.n)
+    t0 = time.perf_counter()
     P.apply(x, Jm)
     t["apply_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     pb.omega_dots(P, u, u, np.ones(P.n), np.ones(P.n), 1.0, "HS")
     t["omega_eval_s"] = time.perf_counter() - t0
-    k = gpu_res["newton_iters"]
-    matvecs = gpu_res["linear_gmres"] + sum(gpu_res["gmres"]) + 3 * (k + 1)
-    evals = sum(gpu_res["omega_evals"])
+    t0 = time.perf_counter()
+    pb.energy(P, x, x)
+    t["energy_s"] = time.perf_counter() - t0
     sample_s = sum(t.values())
-    model_s = (t["setup_fem_s"] + frac_rows * t["bem_sample_s"] + (k + 1) * t["assembly_s"]
-               + evals * t["omega_eval_s"] + matvecs * t["apply_s"])
-    del N
-    return {"value": 1.0 / model_s, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"oracle (numpy float64) on this workload: BEM assembly of 1/{frac_rows} of the test "
-                       f"triangles per surface, one load+Jacobian assembly, one omega evaluation, one dense "
-                       f"coupled apply ({sample_s:.1f} s measured); one solve modelled as {frac_rows} x assembly "
-                       f"sample + {k + 1} assemblies + {evals} omega evaluations + {matvecs} applies "
-                       f"(GPU run's counts) = {model_s:.1f} s"),
-            "parts_s": {kk: round(v, 3) for kk, v in t.items()}, "model_s_per_solve": model_s}
+    model_s = (t["setup_fem_s"] + frac_rows * t["bem_sample_s"] + counts["assemblies"] * t["assembly_s"]
+               + counts["omega_evals"] * t["omega_eval_s"] + counts["applies"] * t["apply_s"] + t["energy_s"])
+    return {"model_s_per_solve": model_s, "sample_s": sample_s, "parts_s": {kk: round(v, 4) for kk, v in t.items()},
+            "description": (f"oracle (numpy float64) on this workload: BEM assembly of 1/{frac_rows} of the test "
+                            f"triangles per surface, FEM set-up and Coulomb data, one load+Jacobian assembly, one "
+                            f"omega evaluation, one dense coupled apply, one energy ({sample_s:.1f} s measured); one "
+                            f"solve modelled with the oracle's own counts ({counts['assemblies']} assemblies, "
+                            f"{counts['omega_evals']} omega evaluations, {counts['applies']} applies) = "
+                            f"{model_s:.1f} s")}
+
+
+# a complete oracle solve of the small single-charge sphere (radius 4, shell to 10, nu = 5,
+# 13 layers, +5 e), run in a fresh interpreter so that its thread limits apply from the start
+_ORACLE_FULL = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+from paper_2511_21713_gb300 import inputs
+from oracle import pb
+case = inputs.single_charge_sphere()
+t0 = time.perf_counter()
+P = pb.Problem(case)
+t1 = time.perf_counter()
+R = pb.solve(P, pb.Opts())
+t2 = time.perf_counter()
+print(json.dumps(dict(setup_s=t1 - t0, solve_s=t2 - t1, total_s=t2 - t0, newton_iters=R.newton_iters,
+                      total=R.total)))
+"""
+
+
+def oracle_full_solve(threads):
+    """Wall time of one complete oracle solve (set-up and solve) of the single-charge sphere with
+    BLAS/OpenMP limited to `threads`."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = str(threads)
+    r = subprocess.run([sys.executable, "-c", _ORACLE_FULL, ROOT], env=env, capture_output=True, text=True,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else f"rc {r.returncode}"}
+    return json.loads(r.stdout.strip().splitlines()[-1]) | {"threads": threads}
+
+
+def cpu_baseline(case, frac_rows):
+    """The oracle timed on this host: the bench workload by the sampled model (value), and complete
+    solves of the single-charge sphere with one thread and with every core."""
+    counts = oracle_counts()
+    smp = oracle_sample(case, counts, frac_rows)
+    cores = os.cpu_count() or 1
+    full = {"workload": "single_charge_sphere (3528 vertices, 19,500 tets, 500 + 500 triangles, +5 e)",
+            "one_thread": oracle_full_solve(1), "all_cores": oracle_full_solve(cores)}
+    return {"value": 1.0 / smp["model_s_per_solve"], "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "estimate": "model",
+            "sample": smp["description"],
+            "parts_s": smp["parts_s"], "model_s_per_solve": smp["model_s_per_solve"],
+            "model_check": (f"the same model on the host that ran the oracle's complete solve of this workload "
+                            f"({ORACLE_C2_MEASURED_HOST}: {counts['measured_setup_s']:.0f} s set-up + "
+                            f"{counts['measured_solve_s']:.0f} s solve) predicted "
+                            f"{ORACLE_C2_MODEL_ON_THAT_HOST:.0f} s"),
+            "measured_full_solves": full}
 
 
 def run_reference(args):
-    """The CPU oracle arm: each step is the bounded oracle sample, scaled to solves/s."""
+    """The CPU oracle arm: each step is a bounded oracle sample of the workload (its real duration
+    is the step time); the value is solves/s of the modelled complete solve."""
     from paper_2511_21713_gb300 import inputs
     ws, rank, _ = dist()
     if rank != 0:
         return None
     case = inputs.multi_charge_sphere()
-    # iteration counts of a representative mixed GPU solve (from the golden oracle trace)
-    if os.path.exists(GOLDEN):
-        g = json.load(open(GOLDEN))["default"]
-        res = {"newton_iters": g["newton_iters"], "linear_gmres": g["linear_gmres"], "gmres": g["gmres"],
-               "omega_evals": [3] * g["newton_iters"]}
-    else:
-        res = {"newton_iters": 5, "linear_gmres": 150, "gmres": [150] * 5, "omega_evals": [3] * 5}
+    counts = oracle_counts()
     for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; the sample itself is the step
-    vals = []
+        pass  # the oracle keeps no state between samples: nothing to warm up
+    models, samples = [], []
     last = None
     for _ in range(args.steps):
-        last = oracle_sample(case, res, args.cpu_sample)
-        vals.append(last["model_s_per_solve"])
-    v = len(vals) / sum(vals)
+        last = oracle_sample(case, counts, args.ref_sample)
+        models.append(last["model_s_per_solve"])
+        samples.append(last["sample_s"])
+    v = len(models) / sum(models)
+    cores = os.cpu_count() or 1
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(vals) / len(vals),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(samples) / len(samples),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded sphere mesh and charges)",
-            "config": workload_config(case, "fp64 (CPU oracle)") | {"parallelism": "1 host process"},
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
+            "config": workload_config(case, "fp64 (CPU oracle)") | {
+                "parallelism": "1 host process",
+                "preconditioner": "Jacobi (the oracle's GMRES: diagonal of the coupled operator)"},
+            "step": "one bounded sample of the workload (see cpu_baseline.sample); ms_per_step is its measured "
+                    "duration, value the modelled complete solve's rate",
+            "model_s_per_solve": sum(models) / len(models),
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "estimate": "model",
+                             "sample": last["description"]},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_step(args):
+    """One step of the solve, repeated, for focused profiler captures (-k on the kernel of
+    interest): farfield_f32 / farfield_ff / farfield_f64 (V then K on Gamma_m and Gamma_s),
+    assemble (sinh Jacobian + load), omega (batched evaluation, 16 values), gmres (one
+    block-preconditioned GMRES solve at 1e-6).  Prints the wall time of each repetition."""
+    import numpy as np
+    import torch
+    from paper_2511_21713_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2511_21713_gb300 import inputs, pbfb
+    case = inputs.multi_charge_sphere() if args.workload == "multi_charge_sphere" else inputs.single_charge_sphere()
+    m = pbfb.Mesh.from_case(case)
+    m.charges_set(case.q_xyz, case.q_z)
+    prec = {"farfield_f32": pbfb.MIXED, "farfield_ff": pbfb.FLOAT2, "farfield_f64": pbfb.FP64}.get(args.step,
+                                                                                                   pbfb.MIXED)
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, prec)
+    dev = torch.device("cuda")
+    r = np.linalg.norm(case.xyz, axis=1)
+    u = torch.as_tensor(4.0 * np.exp(-0.2 * (r - r.min())), device=dev)
+    for rep in range(args.reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if args.step.startswith("farfield"):
+            for which, n in ((pbfb.GAMMA_M, m.n_m), (pbfb.GAMMA_S, m.n_s)):
+                x = torch.ones(n, dtype=torch.float64, device=dev)
+                y = torch.zeros_like(x)
+                m.bem_apply(which, 0, x, y)
+                m.bem_apply(which, 1, x, y)
+        elif args.step == "assemble":
+            N = torch.zeros(m.n_v, dtype=torch.float64, device=dev)
+            m.assemble(pbfb.HS, u, N)
+        elif args.step == "omega":
+            c = torch.ones(m.n, dtype=torch.float64, device=dev)
+            m.omega_eval(pbfb.HS, u, 0.1 * u, c, c, np.linspace(0.25, 4.0, 16))
+        elif args.step == "gmres":
+            m.assemble(pbfb.HS, u)
+            b = torch.ones(m.n, dtype=torch.float64, device=dev)
+            x = torch.zeros_like(b)
+            m.gmres(b, x, 1e-6, precond=pbfb.BLOCK, inner_iters=30)
+        else:
+            raise SystemExit(f"unknown step {args.step}")
+        torch.cuda.synchronize()
+        print(f"{args.step} rep {rep}: {1e3 * (time.perf_counter() - t0):.2f} ms", flush=True)
+    m.close()
 
 
 def main():
@@ -555,17 +751,27 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pbfb", choices=["pbfb", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--cpu-sample", type=int, default=64, help="1/k of the BEM rows in the oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=128, help="1/k of the BEM rows in the oracle sample")
+    ap.add_argument("--ref-sample", type=int, default=512,
+                    help="1/k of the BEM rows in each step of the reference (oracle) arm")
+    ap.add_argument("--step", default=None, help="time one step of the solve (profiling); see run_step")
+    ap.add_argument("--reps", type=int, default=2, help="repetitions of --step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3, help="host-buffer solves timed for the e2e figure")
     ap.add_argument("--serving", type=int, default=24, help="requests in the serving run (0 = skip)")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false",
-                    help="skip the single float64-path solve reported under fp64_gpu")
+                    help="skip the float64-path solves reported under fp64_gpu")
+    ap.add_argument("--fp64-steps", type=int, default=-1,
+                    help="float64-path solves timed for fp64_gpu (default: as many as --steps)")
+    ap.add_argument("--helix", type=int, default=2, help="timed solves of the double helix (0 = skip)")
     ap.add_argument("--no-full-formulation", dest="full_formulation", action="store_false",
                     help="skip the solves of the formulation with Omega_m meshed (full_formulation)")
     ap.add_argument("--workload", default="multi_charge_sphere", choices=["multi_charge_sphere", "small"],
                     help="small = the single-charge sphere, for profiler launch lists")
     args = ap.parse_args()
+    if args.step:
+        run_step(args)
+        return
     out = run_reference(args) if args.impl == "reference" else run_pbfb(args)
     if out is not None:
         print(json.dumps(out))

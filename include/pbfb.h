@@ -130,6 +130,13 @@ typedef struct pbfb_newton_opts {
                            condition ||d(omega)|| < ||d(0)|| (Sec. 2.5.2), smaller values ask for
                            a sufficient decrease, and 0 makes every search fail (PBFB_ERR_OMEGA),
                            which tests use to force that path */
+  double residual_update; /* PBFB_MIXED only; 0 (default) evaluates the Newton residual's far field
+                           in float-float at every step.  tau > 0: a step may instead update it by
+                           linearity, b - Acal(0) Phi_{k+1} = (b - Acal(0) Phi_k) + omega_k p_k
+                           with p_k = -Acal(0) Delta_k from the float32 operator, while the sum of
+                           the updates omega ||Delta|| since the last float-float evaluation stays
+                           below tau ||Phi_{k+1}||; the updates' rounding is that of the float32
+                           far field applied to the increments, not to Phi */
 } pbfb_newton_opts;
 
 #define PBFB_MAX_TRACE 64
@@ -147,6 +154,8 @@ typedef struct pbfb_result {
                                           exactly zero (no charges) stops with omega = e = 0 */
   int omega_evals[PBFB_MAX_TRACE];     /* batched residual evaluations per step */
   double ms_linear, ms_newton, ms_energy;
+  int residual_updates;                /* Newton steps whose residual was updated by linearity
+                                          (pbfb_newton_opts.residual_update) */
 } pbfb_result;
 
 /* Fills *opts with the defaults above. */
@@ -375,6 +384,16 @@ typedef struct pbfb_tuning {
   int32_t pcg_blocks_per_sm;         /* blocks per SM of the cooperative inner PCG: 1..32
                                         (0: as many as fit) */
   int32_t pcg_lanes;                 /* lanes per row of its sparse product: 2, 4 or 8 */
+  int32_t treecode;                  /* float32 far field (GMRES operator): 1 the direct sum over
+                                        all point pairs, 2 the treecode (a binary tree over the
+                                        quadrature points, leaves of 256; a cluster with
+                                        r_leaf + r_cluster < 0.5 times the centre distance is
+                                        replaced by 7^3 barycentric Lagrange proxies; the
+                                        hierarchical far field the paper takes for large surfaces,
+                                        Sec. 3); 0 built-in: the treecode for surfaces of 65,536
+                                        quadrature points or more.  The treecode approximates the
+                                        float32 operator (about 1e-6 of the largest entry); the
+                                        Newton residual stays the float-float direct sum. */
 } pbfb_tuning;
 
 /* Current launch shapes of a mesh (zeros where the built-in choice applies). */

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpbfb.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["fem_kernels.cu", "bem_kernels.cu", "bem_dense.cu", "mesh_setup.cu", "solver.cu", "server.cu", "autotune.cu",
-           "tree_plan.cu"]
+           "tree_plan.cu", "treecode.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

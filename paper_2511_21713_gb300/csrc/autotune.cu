@@ -21,6 +21,7 @@ void read_tuning(const Mesh* m, pbfb_tuning* t) {
   t->spmv_block = m->spmv_block;
   t->pcg_blocks_per_sm = m->tune_pcg_bps;
   t->pcg_lanes = m->pcg_lanes;
+  t->treecode = m->tune_tree;
 }
 
 bool valid_tuning(const pbfb_tuning* t) {
@@ -36,6 +37,7 @@ bool valid_tuning(const pbfb_tuning* t) {
   if (!(B == 0 || B == 128 || B == 256 || B == 512)) return false;
   if (!in(t->pcg_blocks_per_sm, 1, 32)) return false;
   if (!(t->pcg_lanes == 0 || t->pcg_lanes == 2 || t->pcg_lanes == 4 || t->pcg_lanes == 8)) return false;
+  if (t->treecode < 0 || t->treecode > 2) return false;
   return true;
 }
 
@@ -50,6 +52,7 @@ void write_tuning(Mesh* m, const pbfb_tuning* t) {
   if (m->tune_pcg_bps != t->pcg_blocks_per_sm) m->coop_blocks = 0;  // re-derive the grid
   m->tune_pcg_bps = t->pcg_blocks_per_sm;
   m->pcg_lanes = t->pcg_lanes;
+  m->tune_tree = t->treecode;
 }
 
 // milliseconds per repetition of fn (one untimed run first)
@@ -109,6 +112,7 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
         t.nbody_targets_per_thread = tpt;
         t.nbody_packed = packed;
         t.nbody_blocks_per_sm = bps;
+        t.treecode = 1;
         write_tuning(m, &t);
         double ms;
         int st = time_ms(m, reps, far(PBFB_MIXED), &ms);
@@ -121,9 +125,27 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
           best.nbody_targets_per_thread = tpt;
           best.nbody_packed = packed;
           best.nbody_blocks_per_sm = bps;
+          best.treecode = 1;
         }
       }
     }
+  // the treecode (surfaces too small for a tree leaf keep the direct sum), against the best direct
+  // shape; its plan is built on the first (untimed) run
+  {
+    pbfb_tuning t = best;
+    t.treecode = 2;
+    write_tuning(m, &t);
+    double ms;
+    int st = time_ms(m, reps, far(PBFB_MIXED), &ms);
+    if (st) {
+      write_tuning(m, &cur);
+      return st;
+    }
+    if (ms < t_best[0]) {
+      t_best[0] = ms;
+      best.treecode = 2;
+    }
+  }
   // float-float far field
   for (int kind : {1, 2, 3, 4})
     for (int bps : {4, 8, 16, 24}) {

@@ -21,6 +21,7 @@
 #include <mutex>
 #include <vector>
 
+#include "f32x2.cuh"
 #include "pbfb_internal.cuh"
 #include "quad_tables.cuh"
 
@@ -340,18 +341,6 @@ __global__ void k_sources(int nt, const int* __restrict__ tri, const int* __rest
   }
 }
 
-// Hardware approximations (MUFU) without denormal fix-ups: inputs here are normal numbers.
-__device__ __forceinline__ float rsqrt_approx(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // float32 N-body: targets = sources = the nq quadrature points.  Block = NT threads, each
 // owning TPT targets (interleaved by NT); sources streamed through shared memory in tiles
 // of NT; blockIdx.y selects a contiguous source range (split).  Each tile's float partial
@@ -457,31 +446,6 @@ __global__ void __launch_bounds__(NT) k_nbody_f32(int nq, const float4* __restri
 // instruction-issue slots of the pair arithmetic; the FP32 lanes do the same work.  Sources are
 // staged pre-duplicated ((x,x),(y,y),...) so shared-memory loads give packed operands.  Tiles
 // that contain one of the thread's own targets use the scalar path for the coincident-point test.
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pk2(float a, float b) {
-  f32x2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void upk2(f32x2 v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
-  f32x2 r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-  f32x2 r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-  f32x2 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-
 template <int NT, int NP, bool YUK>
 __global__ void __launch_bounds__(NT) k_nbody_f32x2(int nq, const float4* __restrict__ tgt,
                                                     const float4* __restrict__ spos,
@@ -1751,6 +1715,7 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
   timer_begin(m, tm, &ev);
   int nsplit;
   double* vals = s->val.p;
+  double tree_pairs = -1.0;
   if (f64) {
     constexpr int NT = 128;
     int ntb = blocks_for(nq, NT);
@@ -1766,6 +1731,9 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
       k_nbody_f64<NT, true><<<grid, NT, 0, m->stream>>>(nq, s->s64.p, kappa, per, s->val.p);
     else
       k_nbody_f64<NT, false><<<grid, NT, 0, m->stream>>>(nq, s->s64.p, kappa, per, s->val.p);
+  } else if (use_tree(m, s)) {
+    PB_TRY(launch_tree_far(m, s, kappa, s->spos.p, s->sdl.p, s->val.p, &tree_pairs));
+    nsplit = 1;
   } else {
     int tpt, packed, bps;
     f32_shape(m, nq, &tpt, &packed, &bps);
@@ -1807,8 +1775,9 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
     }
   }
   PB_LAUNCHED(m);
-  timer_end(m, tm, ev, (double)nq * (double)nq);
-  if (!f64) m->nbody_flops += (yuk ? 24.0 : 18.0) * (double)nq * (double)nq;
+  const double pairs = tree_pairs >= 0.0 ? tree_pairs : (double)nq * (double)nq;
+  timer_end(m, tm, ev, pairs);
+  if (!f64) m->nbody_flops += (yuk ? 24.0 : 18.0) * pairs;
   return test_reduce(m, s, vals, nsplit, y, accumulate);
 }
 

@@ -73,6 +73,23 @@ struct DBuf {
 // Special (near-field) triangle pair classes.
 enum PairClass { PAIR_IDENTICAL = 0, PAIR_EDGE = 1, PAIR_VERTEX = 2, PAIR_NEAR = 3 };
 
+// Treecode plan of a surface's float32 far field (treecode.cu): quadrature points in tree order,
+// target leaves, approximated clusters and their proxies, source tiles grouped into chunks.
+struct SurfaceTree {
+  bool built = false;
+  int nq = 0, nleaf = 0, nclus = 0, nchunk = 0;
+  double pairs = 0.0;               // pair evaluations per application (direct + proxy)
+  DBuf<int> perm, pos_leaf;         // tree position -> quadrature point; tree position -> leaf
+  DBuf<int> leaf_beg, leaf_end, leaf_chunk;  // per leaf: targets [beg, end), chunks [chunk[L], chunk[L+1])
+  DBuf<int> chunk_leaf, chunk_tile; // per chunk: its leaf; its tiles [tile[c], tile[c+1])
+  DBuf<int2> tiles;                 // per tile: first source record, count (<= 128)
+  DBuf<int> clus_beg, clus_end;     // per approximated cluster: its points in tree order
+  DBuf<float> clus_box;             // per cluster: lo x, y, z, hi x, y, z (centre-relative)
+  DBuf<float4> tgt;                 // target positions in tree order
+  DBuf<float4> spos, sdl;           // nq points in tree order, then nclus x (p+1)^3 proxies
+  DBuf<double> part;                // nchunk x 256 partial sums
+};
+
 // A closed surface (Gamma_m or Gamma_s) over shell vertices.
 struct Surface {
   int nt = 0;   // triangles
@@ -114,6 +131,7 @@ struct Surface {
   DBuf<float4> ffsrc, fftgt;    // float-float sources (4 float4) and targets (2 float4) per point
   int nsplit = 1;
   DBuf<double> mval;            // mutual float32 far field: 2 G partial rows + the sum
+  SurfaceTree tree;             // treecode plan of the float32 far field (built on first use)
   // dense single layer (float32, ld x ld): -V^-1 once inverted (bem_dense.cu)
   DBuf<float> vinv;
   int vinv_ld = 0;
@@ -196,6 +214,8 @@ struct Mesh {
   int tune_ff_kernel = 0;           // float-float far field: 1 one target per thread, 2 two (float2),
                                     // 3 mutual pairs (0 = mutual for large surfaces, else 2)
   int tune_ff_bps = 0;              // float-float far field: target blocks per SM (0 = built-in)
+  int tune_tree = 0;                // float32 far field: 0 built-in (treecode from TREE_MIN_POINTS
+                                    // points), 1 direct sum, 2 treecode
   int spmv_lanes = 0;               // lanes per row of the operator's sparse part (0 = 8; 4, 8, 16)
   int spmv_block = 0;               // threads per block of that SpMV (0 = 256; 128, 256, 512)
   int tune_pcg_bps = 0;             // blocks per SM of the cooperative inner PCG (0 = all that fit)
@@ -285,6 +305,13 @@ int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, d
 int launch_coulomb(Mesh* m);
 int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev);
 int bem_apply_noalloc(Mesh* m, int which, int op, const double* x, double* y);
+
+// ---- treecode.cu: hierarchical float32 far field
+constexpr int TREE_MIN_POINTS = 65536;  // built-in: treecode for surfaces of at least this many points
+bool use_tree(const Mesh* m, const Surface* s);
+int build_surface_tree(Mesh* m, Surface* s);
+int launch_tree_far(Mesh* m, Surface* s, double kappa, const float4* spos, const float4* sdl, double* val,
+                    double* pairs);
 
 // ---- bem_dense.cu: dense float32 single layer of a surface and its inverse
 constexpr int DENSE_V_MAX = 32768;  // surface vertices up to which the dense inverse is used

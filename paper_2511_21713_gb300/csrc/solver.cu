@@ -1260,7 +1260,7 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   }
   if (!(o.tol_nl > 0) || !(o.tol_gmres > 0) || !(o.tol_gmres0 > 0) || !(o.tol_omega > 0) || o.max_newton < 1 ||
       o.max_gmres < 1 || !(o.omega_max > 0) || !std::isfinite(o.omega_max) || o.max_omega_iters < 1 ||
-      !(o.accept_ratio >= 0.0 && o.accept_ratio <= 1.0) ||
+      !(o.accept_ratio >= 0.0 && o.accept_ratio <= 1.0) || !(o.residual_update >= 0.0) ||
       o.n_taylor < 0 || o.n_taylor > 4 || (o.method != PBFB_NEWTON && o.method != PBFB_PICARD) || !(o.R_e >= 0) ||
       (o.precision != PBFB_FP64 && o.precision != PBFB_MIXED)) {
     set_error("solve: invalid options");
@@ -1306,14 +1306,37 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   double om_last = -1.0, e_prev = -1.0, e_prev2 = -1.0;
   const bool picard = o.method == PBFB_PICARD;
   bool converged = false;
+  // residual updates by linearity (residual_update > 0, mixed precision): p of the previous step
+  // holds -Acal(0) Delta for its Delta; upd_sum = sum of omega ||Delta|| since the last float-float
+  // evaluation of c
+  const bool res_upd = o.residual_update > 0.0 && o.precision == PBFB_MIXED;
+  bool p_valid = false;
+  double upd_sum = 0.0;
+  R.residual_updates = 0;
   int k = 0;
   for (k = 0; k < o.max_newton; ++k) {
     const int scheme = k < o.n_taylor ? o.taylor[k] : PBFB_HS;
     PB_TRY(launch_axpby(m, n, 1.0, m->xL.p, 1.0, m->xNL.p, m->phi.p));
-    // c = b - Acal(0) Phi: the nonlinear residual's far field in float64 (FP64) or float-float (MIXED)
-    PB_TRY(clear_jacobian(m));
-    PB_TRY(apply_prec(m, m->phi.p, m->cvec.p, m->precision == PBFB_MIXED ? PBFB_FLOAT2 : PBFB_FP64));
-    PB_TRY(launch_axpby(m, n, 1.0, bvec, -1.0, m->cvec.p, m->cvec.p));
+    bool updated = false;
+    if (res_upd && k > 0 && p_valid) {
+      double phi2;
+      PB_TRY(dot(m, m->phi.p, m->phi.p, n, &phi2));
+      if (upd_sum + e_prev <= o.residual_update * std::sqrt(phi2)) {
+        // c_k = c_{k-1} + omega_{k-1} p_{k-1}, p = -Acal(0) Delta_{k-1}
+        PB_TRY(launch_axpby(m, n, om_last, m->pvec.p, 1.0, m->cvec.p, m->cvec.p));
+        upd_sum += e_prev;
+        updated = true;
+        ++R.residual_updates;
+      }
+    }
+    if (!updated) {
+      // c = b - Acal(0) Phi: the nonlinear residual's far field in float64 (FP64) or float-float (MIXED)
+      PB_TRY(clear_jacobian(m));
+      PB_TRY(apply_prec(m, m->phi.p, m->cvec.p, m->precision == PBFB_MIXED ? PBFB_FLOAT2 : PBFB_FP64));
+      PB_TRY(launch_axpby(m, n, 1.0, bvec, -1.0, m->cvec.p, m->cvec.p));
+      upd_sum = 0.0;
+    }
+    p_valid = false;
     // J(u), N(u); d = c - [N; 0; 0]
     PB_TRY(assemble(m, scheme, m->phi.p, m->Nvec.p));
     PB_CUDA(cudaMemcpyAsync(m->dvec.p, m->cvec.p, n * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
@@ -1350,18 +1373,10 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
     }
     double om;
     int evals = 0;
-    if (!o.omega_search) {
-      om = k == 0 ? o.omega0_first : o.omega0_rest;
-    } else if (!picard && k > 0 && e_prev >= 0.0 && e_prev < o.L_e && om_last > 0.0) {
-      om = om_last;
-    } else if (picard && om_last > 0.0 && e_prev2 > 0.0 && e_prev > 0.0 && o.R_e > 0.0 &&
-               !(e_prev2 / e_prev < o.R_e)) {
-      // R_e rule (Appendix B): keep omega while the error still falls by R_e per step
-      om = om_last;
-    } else {
-      // p = -Acal(0) Delta with the GMRES operator (the root of f_d is needed only to Tol_omega):
-      // GMRES's final true residual left Acal(J) Delta in gw, and Acal(0) Delta differs from it
-      // only by the Jacobian's sparse rows, J Delta = (S_J - S_0) Delta
+    // p = -Acal(0) Delta with the GMRES operator (the root of f_d is needed only to Tol_omega):
+    // GMRES's final true residual left Acal(J) Delta in gw, and Acal(0) Delta differs from it
+    // only by the Jacobian's sparse rows, J Delta = (S_J - S_0) Delta
+    auto make_p = [&]() -> int {
       if (m->gw_is_ax) {
         PB_TRY(launch_csr_spmv(m, n, m->s_ptr.p, m->s_col.p, m->s_val.p, m->du.p, m->pvec.p, false));
         PB_TRY(launch_csr_spmv(m, n, m->s_ptr.p, m->s_col.p, m->s_base.p, m->du.p, m->tmp.p, false));
@@ -1373,6 +1388,21 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
         PB_TRY(apply(m, m->du.p, m->pvec.p));
         PB_TRY(launch_axpby(m, n, -1.0, m->pvec.p, 0.0, nullptr, m->pvec.p));
       }
+      p_valid = true;
+      return PBFB_OK;
+    };
+    const bool reuse_newton = !picard && k > 0 && e_prev >= 0.0 && e_prev < o.L_e && om_last > 0.0;
+    // R_e rule (Appendix B): keep omega while the error still falls by R_e per step
+    const bool reuse_picard = picard && om_last > 0.0 && e_prev2 > 0.0 && e_prev > 0.0 && o.R_e > 0.0 &&
+                              !(e_prev2 / e_prev < o.R_e);
+    if (!o.omega_search) {
+      om = k == 0 ? o.omega0_first : o.omega0_rest;
+      if (res_upd) PB_TRY(make_p());
+    } else if (reuse_newton || reuse_picard) {
+      om = om_last;
+      if (res_upd) PB_TRY(make_p());
+    } else {
+      PB_TRY(make_p());
       double om0 = k == 0 ? o.omega0_first : o.omega0_rest;
       int warm_evals = 0;
       if (k == 0 && o.omega_warm_start && !picard)
@@ -1556,6 +1586,7 @@ void pbfb_default_opts(pbfb_newton_opts* o) {
   o->precond = PBFB_PRECOND_BLOCK_DENSE;
   o->inner_iters = 30;
   o->accept_ratio = 1.0;
+  o->residual_update = 0.0;
 }
 
 const char* pbfb_last_error(void) { return pbfb::last_error(); }

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <numeric>
 
 namespace pbfb {
@@ -40,7 +41,11 @@ double centre_distance(const double* a, const double* b) {
 }  // namespace
 
 int build_tree_plan(const double* xyz, int n, int leaf, double theta, int min_size, TreePlan* out) {
-  if (!xyz || !out || n < 1 || leaf < 1 || !(theta > 0.0 && theta < 1.0)) return 1;
+  return build_tree_plan(xyz, n, leaf, theta, min_size, 1, out);
+}
+
+int build_tree_plan(const double* xyz, int n, int leaf, double theta, int min_size, int granule, TreePlan* out) {
+  if (!xyz || !out || n < 1 || leaf < 1 || granule < 1 || !(theta > 0.0 && theta < 1.0)) return 1;
   for (size_t i = 0; i < 3 * (size_t)n; ++i)
     if (!std::isfinite(xyz[i])) return 1;
   TreePlan& t = *out;
@@ -62,7 +67,9 @@ int build_tree_plan(const double* xyz, int n, int leaf, double theta, int min_si
     int ax = 0;
     for (int d = 1; d < 3; ++d)
       if (bx[3 + d] - bx[d] > bx[3 + ax] - bx[ax]) ax = d;
-    const int mid = b + (e - b) / 2;
+    int half = (e - b) / 2;
+    if (granule > 1) half = std::max(granule, (int)(((int64_t)half + granule / 2) / granule) * granule);
+    const int mid = b + std::min(half, e - b - 1);
     std::stable_sort(t.perm.begin() + b, t.perm.begin() + e, [&](int i, int j) {
       return xyz[3 * (size_t)i + ax] < xyz[3 * (size_t)j + ax];
     });
@@ -104,6 +111,72 @@ int build_tree_plan(const double* xyz, int n, int leaf, double theta, int min_si
     }
     t.far_ptr.push_back((int)t.far_node.size());
     t.near_ptr.push_back((int)t.near_node.size());
+  }
+  return 0;
+}
+
+int plan_tree_tiles(const double* xyz, int n, int leaf, double theta, int npx, int tile, int tiles_per_chunk,
+                    TreeTiles* out) {
+  if (!out || tile < 1 || tiles_per_chunk < 1 || npx < 1) return 1;
+  TreePlan P;
+  if (build_tree_plan(xyz, n, leaf, theta, npx, leaf, &P)) return 1;
+  TreeTiles& T = *out;
+  T = TreeTiles();
+  T.n = n;
+  T.nleaf = (int)P.leaves.size();
+  T.perm = P.perm;
+  std::vector<int> cidx(P.begin.size(), -1), cnode;
+  for (int C : P.far_node)
+    if (cidx[C] < 0) {
+      cidx[C] = (int)cnode.size();
+      cnode.push_back(C);
+    }
+  T.nclus = (int)cnode.size();
+  for (int C : cnode) {
+    T.clus_beg.push_back(P.begin[C]);
+    T.clus_end.push_back(P.end[C]);
+    const double* bx = &P.box[6 * (size_t)C];
+    double side = 0.0;
+    for (int d = 0; d < 3; ++d) side = std::max(side, bx[3 + d] - bx[d]);
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      const double pad = std::max(0.0, 1e-3 * side - (bx[3 + d] - bx[d])) * 0.5;
+      lo[d] = bx[d] - pad;
+      hi[d] = bx[3 + d] + pad;
+    }
+    T.clus_box.insert(T.clus_box.end(), {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]});
+  }
+  T.pos_leaf.assign(n, 0);
+  T.chunk_tile.assign(1, 0);
+  T.leaf_chunk.assign(1, 0);
+  for (int i = 0; i < T.nleaf; ++i) {
+    const int B = P.leaves[i];
+    T.leaf_beg.push_back(P.begin[B]);
+    T.leaf_end.push_back(P.end[B]);
+    for (int q = P.begin[B]; q < P.end[B]; ++q) T.pos_leaf[q] = i;
+    const int nt_leaf = P.end[B] - P.begin[B];
+    std::vector<int> ls, lc;
+    auto add_range = [&](int b, int e) {
+      for (int s0 = b; s0 < e; s0 += tile) {
+        ls.push_back(s0);
+        lc.push_back(std::min(tile, e - s0));
+      }
+      T.pairs += (double)nt_leaf * (e - b);
+    };
+    for (int k = P.near_ptr[i]; k < P.near_ptr[i + 1]; ++k) add_range(P.begin[P.near_node[k]], P.end[P.near_node[k]]);
+    for (int k = P.far_ptr[i]; k < P.far_ptr[i + 1]; ++k) {
+      const int o = n + cidx[P.far_node[k]] * npx;
+      add_range(o, o + npx);
+    }
+    for (size_t t0 = 0; t0 < ls.size(); t0 += tiles_per_chunk) {
+      T.chunk_leaf.push_back(i);
+      for (size_t t = t0; t < std::min(ls.size(), t0 + (size_t)tiles_per_chunk); ++t) {
+        T.tile_start.push_back(ls[t]);
+        T.tile_count.push_back(lc[t]);
+      }
+      T.chunk_tile.push_back((int)T.tile_start.size());
+    }
+    T.leaf_chunk.push_back((int)T.chunk_leaf.size());
   }
   return 0;
 }

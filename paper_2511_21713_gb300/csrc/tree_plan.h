@@ -27,4 +27,36 @@ struct TreePlan {
 // Returns 0, or 1 for bad arguments (n < 1, leaf < 1, theta not in (0, 1), non-finite coordinates).
 int build_tree_plan(const double* xyz, int n, int leaf, double theta, int min_size, TreePlan* out);
 
+// As above, with the split point of a node of m points at the multiple of `granule` nearest to m / 2
+// (at least one granule) instead of the median: with granule = leaf every leaf holds exactly `leaf`
+// points except the remainders, which fills fixed-size blocks of targets on the GPU.  granule = 1
+// is the median split.
+int build_tree_plan(const double* xyz, int n, int leaf, double theta, int min_size, int granule, TreePlan* out);
+
+// Work plan of the treecode far field on the GPU, from a TreePlan built with leaf = granule =
+// `leaf`: the clusters taken through proxies (numbered in order of first use; proxy records of
+// cluster k are npx consecutive source records from n + k npx), and per target leaf its source
+// tiles -- runs of at most `tile` consecutive source records: the points of each near leaf (in tree
+// order) and the proxies of each accepted cluster -- grouped into chunks of at most
+// tiles_per_chunk tiles (one GPU block each).
+struct TreeTiles {
+  int n = 0, nleaf = 0, nclus = 0;
+  double pairs = 0.0;                    // target-source pair evaluations per application
+  std::vector<int> perm;                 // tree position -> point index
+  std::vector<int> pos_leaf;             // tree position -> leaf
+  std::vector<int> leaf_beg, leaf_end;   // per leaf: its targets [beg, end) in tree order
+  std::vector<int> leaf_chunk;           // per leaf: its chunks [leaf_chunk[L], leaf_chunk[L + 1])
+  std::vector<int> chunk_leaf;           // per chunk: its leaf
+  std::vector<int> chunk_tile;           // per chunk: its tiles [chunk_tile[c], chunk_tile[c + 1])
+  std::vector<int> tile_start, tile_count;  // per tile: first source record, records (<= tile)
+  std::vector<int> clus_beg, clus_end;   // per cluster: its points [beg, end) in tree order
+  std::vector<double> clus_box;          // per cluster: lo x, y, z, hi x, y, z (a flat side widened
+                                         // to 1e-3 of the longest one)
+};
+
+// Builds the tree plan (leaves and granule `leaf`, clusters accepted with more than npx points)
+// and the work plan above.  Returns 0, or 1 for bad arguments.
+int plan_tree_tiles(const double* xyz, int n, int leaf, double theta, int npx, int tile, int tiles_per_chunk,
+                    TreeTiles* out);
+
 }  // namespace pbfb

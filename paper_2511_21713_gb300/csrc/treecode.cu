@@ -1,0 +1,348 @@
+// Hierarchical far field (treecode) for the float32 operator of GMRES.
+//
+// The paper switches its boundary operators from dense matrices to a fast multipole method for
+// large surfaces (Sec. 3: above 90k vertices, order 3, leaves of fewer than 100 nodes).  Here the
+// float32 quadrature-point sum of launch_bem_far,
+//   phi(x_i) = sum_{j != i} [ s_j + m_j . (x_i - y_j) (1 + kappa r) / r^2 ] exp(-kappa r) / r,
+// is split per target leaf B of a binary tree over the surface's quadrature points into
+//   - near leaves, summed point by point (the leaf itself included, coincident points skipped),
+//   - well-separated clusters C (r_B + r_C < theta |c_B - c_C|), each replaced by (p+1)^3 proxy
+//     sources at the tensor Chebyshev points t_k (second kind) of its box, with charges
+//     S_k = sum_{j in C} s_j L_k(y_j) and dipoles M_k = sum_{j in C} m_j L_k(y_j), where L_k is the
+//     tensor barycentric Lagrange basis: the kernel's dependence on y is interpolated, so the
+//     proxy sum is the same kernel evaluated at the proxies (barycentric Lagrange treecode of
+//     Wang, Tlupova and Krasny, 2020).
+// Both parts run through one kernel: a block takes one target leaf (up to 256 targets, two per
+// thread on the packed f32x2 instructions) and a chunk of its source tiles (runs of at most 128
+// consecutive source records: leaf points in tree order, or a cluster's proxies), and writes its
+// partial sums; the chunks of a leaf are then added in a fixed order, so the result does not
+// depend on scheduling.  The host plan (tree, acceptance, tiles, chunks) is built once per surface.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "f32x2.cuh"
+#include "pbfb_internal.cuh"
+#include "tree_plan.h"
+
+namespace pbfb {
+
+namespace {
+
+constexpr int TREE_NT = 128;                 // threads per block; two targets each
+constexpr int TREE_LEAF = 2 * TREE_NT;       // targets per leaf (at most)
+constexpr int TREE_P = 6;                    // interpolation degree per dimension
+constexpr int TREE_K = TREE_P + 1;           // Chebyshev points per dimension
+constexpr int TREE_NPX = TREE_K * TREE_K * TREE_K;  // proxies per cluster (343)
+constexpr int TREE_UP_NT = 352;              // threads of the upward pass (>= TREE_NPX, whole warps)
+constexpr int TREE_TILES_PER_CHUNK = 8;      // source tiles per block
+constexpr double TREE_THETA = 0.5;           // acceptance: r_B + r_C < theta |c_B - c_C|
+
+// tree order: spos_t[i] = spos[perm[i]] (sources and, for positions, the targets)
+__global__ void k_tree_permute(int nq, const int* __restrict__ perm, const float4* __restrict__ spos,
+                               const float4* __restrict__ sdl, float4* __restrict__ spos_t,
+                               float4* __restrict__ sdl_t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const int j = perm[i];
+  spos_t[i] = spos[j];
+  sdl_t[i] = sdl[j];
+}
+
+// Upward pass: one block per approximated cluster.  Proxy k = (a, b, c) at (tx_a, ty_b, tz_c)
+// receives sum_j L_a(x_j) L_b(y_j) L_c(z_j) (s_j, m_j); the 1-D values come from the barycentric
+// formula l_a(x) = (w_a / (x - t_a)) / sum_m (w_m / (x - t_m)), w_m = (-1)^m (halved at both ends),
+// or the unit vector when x coincides with a node.
+__global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(int nq, const int* __restrict__ cbeg,
+                                                        const int* __restrict__ cend,
+                                                        const float* __restrict__ cbox,
+                                                        float4* __restrict__ spos_t, float4* __restrict__ sdl_t) {
+  __shared__ float node[3][TREE_K];
+  __shared__ float lw[3][TREE_K][TREE_NT];
+  __shared__ float4 src[TREE_NT];
+  const int c = blockIdx.x;
+  const int b = cbeg[c], e = cend[c];
+  const int t = threadIdx.x;
+  if (t < 3 * TREE_K) {
+    const int d = t / TREE_K, k = t - d * TREE_K;
+    const float lo = cbox[6 * c + d], hi = cbox[6 * c + 3 + d];
+    node[d][k] = 0.5f * (lo + hi) + 0.5f * (hi - lo) * cospif((float)k / (float)TREE_P);
+  }
+  const int ka = t / (TREE_K * TREE_K), kb = (t / TREE_K) % TREE_K, kc = t % TREE_K;
+  double as = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
+  __syncthreads();
+  for (int j0 = b; j0 < e; j0 += TREE_NT) {
+    if (t < TREE_NT) {
+      const int j = j0 + t;
+      if (j < e) {
+        const float4 p = spos_t[j];
+        const float4 q = sdl_t[j];
+        src[t] = make_float4(p.w, q.x, q.y, q.z);
+        const float xs[3] = {p.x, p.y, p.z};
+        for (int d = 0; d < 3; ++d) {
+          float a[TREE_K];
+          float den = 0.f;
+          int hit = -1;
+          for (int k = 0; k < TREE_K; ++k) {
+            const float dx = xs[d] - node[d][k];
+            const float w = ((k & 1) ? -1.f : 1.f) * ((k == 0 || k == TREE_P) ? 0.5f : 1.f);
+            if (dx == 0.f) hit = k;
+            a[k] = dx == 0.f ? 0.f : w / dx;
+            den += a[k];
+          }
+          for (int k = 0; k < TREE_K; ++k) lw[d][k][t] = hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] / den;
+        }
+      } else {
+        src[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int d = 0; d < 3; ++d)
+          for (int k = 0; k < TREE_K; ++k) lw[d][k][t] = 0.f;
+      }
+    }
+    __syncthreads();
+    if (t < TREE_NPX) {
+      float fs = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+      const int cnt = min(TREE_NT, e - j0);
+      for (int jj = 0; jj < cnt; ++jj) {
+        const float w = lw[0][ka][jj] * lw[1][kb][jj] * lw[2][kc][jj];
+        const float4 q = src[jj];
+        fs = fmaf(w, q.x, fs);
+        fx = fmaf(w, q.y, fx);
+        fy = fmaf(w, q.z, fy);
+        fz = fmaf(w, q.w, fz);
+      }
+      as += fs;
+      ax += fx;
+      ay += fy;
+      az += fz;
+    }
+    __syncthreads();
+  }
+  if (t < TREE_NPX) {
+    const int o = nq + c * TREE_NPX + t;
+    spos_t[o] = make_float4(node[0][ka], node[1][kb], node[2][kc], (float)as);
+    sdl_t[o] = make_float4((float)ax, (float)ay, (float)az, 0.f);
+  }
+}
+
+// Evaluation: block = one chunk (a target leaf and a run of its source tiles).  Tiles that overlap
+// the leaf's own points take the scalar path with the coincident-point test; the others the
+// packed one.  Padding entries (past a tile's count) sit far away with zero strength.
+template <bool YUK>
+__global__ void __launch_bounds__(TREE_NT) k_tree_eval(const float4* __restrict__ tgt_t,
+                                                       const int* __restrict__ leaf_beg,
+                                                       const int* __restrict__ leaf_end,
+                                                       const int* __restrict__ chunk_leaf,
+                                                       const int* __restrict__ chunk_tile,
+                                                       const int2* __restrict__ tiles,
+                                                       const float4* __restrict__ spos_t,
+                                                       const float4* __restrict__ sdl_t, float kappa,
+                                                       double* __restrict__ part) {
+  __shared__ ulonglong2 sh[4][TREE_NT];
+  __shared__ float4 shp[TREE_NT], shd[TREE_NT];
+  const int c = blockIdx.x;
+  const int L = chunk_leaf[c];
+  const int lb = leaf_beg[L], le = leaf_end[L];
+  int ti[2];
+  float txs[2], tys[2], tzs[2];
+  double acc64[2] = {0.0, 0.0};
+  for (int k = 0; k < 2; ++k) {
+    ti[k] = lb + k * TREE_NT + threadIdx.x;
+    const float4 p = tgt_t[ti[k] < le ? ti[k] : lb];
+    txs[k] = p.x;
+    tys[k] = p.y;
+    tzs[k] = p.z;
+  }
+  const f32x2 tx = pk2(txs[0], txs[1]), ty = pk2(tys[0], tys[1]), tz = pk2(tzs[0], tzs[1]);
+  const float nk = -kappa * 1.4426950408889634f;
+  const f32x2 nk2 = pk2(nk, nk), kap2 = pk2(kappa, kappa), one2 = pk2(1.f, 1.f);
+  for (int tl = chunk_tile[c]; tl < chunk_tile[c + 1]; ++tl) {
+    const int2 tile = tiles[tl];
+    const int s0 = tile.x, cnt = tile.y;
+    float4 p, d;
+    if ((int)threadIdx.x < cnt) {
+      p = spos_t[s0 + threadIdx.x];
+      d = sdl_t[s0 + threadIdx.x];
+    } else {
+      p = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+      d = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    sh[0][threadIdx.x] = make_ulonglong2(pk2(p.x, p.x), pk2(p.y, p.y));
+    sh[1][threadIdx.x] = make_ulonglong2(pk2(p.z, p.z), pk2(p.w, p.w));
+    sh[2][threadIdx.x] = make_ulonglong2(pk2(d.x, d.x), pk2(d.y, d.y));
+    sh[3][threadIdx.x] = make_ulonglong2(pk2(d.z, d.z), 0ull);
+    shp[threadIdx.x] = p;
+    shd[threadIdx.x] = d;
+    __syncthreads();
+    const bool diag = s0 < le && s0 + cnt > lb;
+    if (!diag) {
+      f32x2 acc = 0ull;
+#pragma unroll 2
+      for (int jj = 0; jj < TREE_NT; ++jj) {
+        const ulonglong2 a0 = sh[0][jj], a1 = sh[1][jj], a2 = sh[2][jj], a3 = sh[3][jj];
+        const f32x2 dx = sub2(tx, a0.x), dy = sub2(ty, a0.y), dz = sub2(tz, a1.x);
+        const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        float ra, rb;
+        upk2(r2, ra, rb);
+        const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
+        const f32x2 nd = fma2(a3.x, dz, fma2(a2.y, dy, mul2(a2.x, dx)));
+        const f32x2 ri2 = mul2(ri, ri);
+        if (YUK) {
+          const f32x2 r = mul2(r2, ri);
+          float xa, xb;
+          upk2(mul2(nk2, r), xa, xb);
+          const f32x2 ex = pk2(ex2_approx(xa), ex2_approx(xb));
+          const f32x2 tt = fma2(mul2(nd, fma2(kap2, r, one2)), ri2, a1.y);
+          acc = fma2(tt, mul2(ex, ri), acc);
+        } else {
+          acc = fma2(fma2(nd, ri2, a1.y), ri, acc);
+        }
+      }
+      float a, b;
+      upk2(acc, a, b);
+      acc64[0] += (double)a;
+      acc64[1] += (double)b;
+    } else {
+      float accs[2] = {0.f, 0.f};
+      for (int jj = 0; jj < TREE_NT; ++jj) {
+        const float4 q = shp[jj];
+        const float4 m = shd[jj];
+        for (int k = 0; k < 2; ++k) {
+          if (s0 + jj == ti[k]) continue;
+          const float dx = txs[k] - q.x, dy = tys[k] - q.y, dz = tzs[k] - q.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float ri = rsqrt_approx(r2);
+          const float nd = fmaf(m.x, dx, fmaf(m.y, dy, m.z * dz));
+          const float ri2 = ri * ri;
+          if (YUK) {
+            const float r = r2 * ri;
+            const float ex = ex2_approx(nk * r);
+            const float tt = fmaf(nd * fmaf(kappa, r, 1.f), ri2, q.w);
+            accs[k] = fmaf(tt, ex * ri, accs[k]);
+          } else {
+            accs[k] = fmaf(fmaf(nd, ri2, q.w), ri, accs[k]);
+          }
+        }
+      }
+      acc64[0] += (double)accs[0];
+      acc64[1] += (double)accs[1];
+    }
+    __syncthreads();
+  }
+  part[(size_t)c * TREE_LEAF + threadIdx.x] = acc64[0];
+  part[(size_t)c * TREE_LEAF + TREE_NT + threadIdx.x] = acc64[1];
+}
+
+// out[i] = in[perm[i]]
+__global__ void k_tree_gather4(int nq, const int* __restrict__ perm, const float4* __restrict__ in,
+                               float4* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nq) out[i] = in[perm[i]];
+}
+
+// val[perm[i]] = sum over the chunks of i's leaf, in chunk order
+__global__ void k_tree_sum(int nq, const int* __restrict__ perm, const int* __restrict__ pos_leaf,
+                           const int* __restrict__ leaf_beg, const int* __restrict__ leaf_chunk,
+                           const double* __restrict__ part, double* __restrict__ val) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const int L = pos_leaf[i];
+  const int l = i - leaf_beg[L];
+  double s = 0.0;
+  for (int c = leaf_chunk[L]; c < leaf_chunk[L + 1]; ++c) s += part[(size_t)c * TREE_LEAF + l];
+  val[perm[i]] = s;
+}
+
+int blocks(int64_t n, int per) { return (int)((n + per - 1) / per); }
+
+}  // namespace
+
+// Host plan of a surface's treecode (plan_tree_tiles: leaves of 256, splits at multiples of 256,
+// clusters with more points than proxies), uploaded once per surface, on first use.
+int build_surface_tree(Mesh* m, Surface* s) {
+  SurfaceTree& T = s->tree;
+  const int nq = s->nq;
+  std::vector<double> qx(3 * (size_t)nq), xyz(3 * (size_t)nq);
+  PB_CUDA(cudaMemcpyAsync(qx.data(), s->qx.p, qx.size() * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  PB_CUDA(cudaStreamSynchronize(m->stream));
+  for (int j = 0; j < nq; ++j)
+    for (int d = 0; d < 3; ++d) xyz[3 * (size_t)j + d] = qx[(size_t)d * nq + j];
+  TreeTiles P;
+  if (plan_tree_tiles(xyz.data(), nq, TREE_LEAF, TREE_THETA, TREE_NPX, TREE_NT, TREE_TILES_PER_CHUNK, &P)) {
+    set_error("treecode: tree plan failed");
+    return PBFB_ERR_STATE;
+  }
+  // cluster boxes in the coordinates of the float32 records (relative to the surface centre)
+  std::vector<float> cbox(P.clus_box.size());
+  for (size_t k = 0; k < P.clus_box.size(); ++k) cbox[k] = (float)(P.clus_box[k] - s->ctr[k % 3]);
+  std::vector<int2> tiles(P.tile_start.size());
+  for (size_t t = 0; t < tiles.size(); ++t) tiles[t] = make_int2(P.tile_start[t], P.tile_count[t]);
+  T.nq = nq;
+  T.nleaf = P.nleaf;
+  T.nclus = P.nclus;
+  T.nchunk = (int)P.chunk_leaf.size();
+  T.pairs = P.pairs;
+  PB_TRY(T.perm.upload(P.perm.data(), nq, m->stream));
+  PB_TRY(T.pos_leaf.upload(P.pos_leaf.data(), nq, m->stream));
+  PB_TRY(T.leaf_beg.upload(P.leaf_beg.data(), P.nleaf, m->stream));
+  PB_TRY(T.leaf_end.upload(P.leaf_end.data(), P.nleaf, m->stream));
+  PB_TRY(T.leaf_chunk.upload(P.leaf_chunk.data(), P.leaf_chunk.size(), m->stream));
+  PB_TRY(T.chunk_leaf.upload(P.chunk_leaf.data(), P.chunk_leaf.size(), m->stream));
+  PB_TRY(T.chunk_tile.upload(P.chunk_tile.data(), P.chunk_tile.size(), m->stream));
+  PB_TRY(T.tiles.upload(tiles.data(), tiles.size(), m->stream));
+  if (P.nclus > 0) {
+    PB_TRY(T.clus_beg.upload(P.clus_beg.data(), P.nclus, m->stream));
+    PB_TRY(T.clus_end.upload(P.clus_end.data(), P.nclus, m->stream));
+    PB_TRY(T.clus_box.upload(cbox.data(), cbox.size(), m->stream));
+  }
+  PB_TRY(T.spos.alloc((size_t)nq + (size_t)P.nclus * TREE_NPX));
+  PB_TRY(T.sdl.alloc((size_t)nq + (size_t)P.nclus * TREE_NPX));
+  PB_TRY(T.tgt.alloc(nq));
+  PB_TRY(T.part.alloc((size_t)T.nchunk * TREE_LEAF));
+  // target positions in tree order (the geometry does not change)
+  k_tree_gather4<<<blocks(nq, 256), 256, 0, m->stream>>>(nq, T.perm.p, s->qpf.p, T.tgt.p);
+  PB_LAUNCHED(m);
+  PB_CUDA(cudaStreamSynchronize(m->stream));
+  T.built = true;
+  return PBFB_OK;
+}
+
+bool use_tree(const Mesh* m, const Surface* s) {
+  if (m->tune_tree == 1) return false;
+  if (m->tune_tree == 2) return s->nq >= TREE_LEAF;
+  return s->nq >= TREE_MIN_POINTS;
+}
+
+// float32 far field through the treecode: spos / sdl (original order, from k_sources) -> val
+// (original order, one split).  Pair evaluations per call in *pairs.
+int launch_tree_far(Mesh* m, Surface* s, double kappa, const float4* spos, const float4* sdl, double* val,
+                    double* pairs) {
+  SurfaceTree& T = s->tree;
+  if (!T.built) PB_TRY(build_surface_tree(m, s));
+  const int nq = s->nq;
+  k_tree_permute<<<blocks(nq, 256), 256, 0, m->stream>>>(nq, T.perm.p, spos, sdl, T.spos.p, T.sdl.p);
+  PB_LAUNCHED(m);
+  if (T.nclus > 0) {
+    k_tree_up<<<T.nclus, TREE_UP_NT, 0, m->stream>>>(nq, T.clus_beg.p, T.clus_end.p, T.clus_box.p, T.spos.p,
+                                                     T.sdl.p);
+    PB_LAUNCHED(m);
+  }
+  const float kf = (float)kappa;
+  if (kappa != 0.0)
+    k_tree_eval<true><<<T.nchunk, TREE_NT, 0, m->stream>>>(T.tgt.p, T.leaf_beg.p, T.leaf_end.p, T.chunk_leaf.p,
+                                                            T.chunk_tile.p, T.tiles.p, T.spos.p, T.sdl.p, kf,
+                                                            T.part.p);
+  else
+    k_tree_eval<false><<<T.nchunk, TREE_NT, 0, m->stream>>>(T.tgt.p, T.leaf_beg.p, T.leaf_end.p, T.chunk_leaf.p,
+                                                             T.chunk_tile.p, T.tiles.p, T.spos.p, T.sdl.p, kf,
+                                                             T.part.p);
+  PB_LAUNCHED(m);
+  k_tree_sum<<<blocks(nq, 256), 256, 0, m->stream>>>(nq, T.perm.p, T.pos_leaf.p, T.leaf_beg.p, T.leaf_chunk.p,
+                                                      T.part.p, val);
+  PB_LAUNCHED(m);
+  *pairs = T.pairs;
+  return PBFB_OK;
+}
+
+}  // namespace pbfb

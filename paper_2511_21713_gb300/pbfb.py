@@ -57,7 +57,8 @@ class NewtonOpts(ctypes.Structure):
                 ("taylor", ctypes.c_int * 4), ("method", ctypes.c_int), ("R_e", ctypes.c_double),
                 ("omega_warm_start", ctypes.c_int),
                 ("omega_search", ctypes.c_int), ("precond", ctypes.c_int),
-                ("inner_iters", ctypes.c_int), ("accept_ratio", ctypes.c_double)]
+                ("inner_iters", ctypes.c_int), ("accept_ratio", ctypes.c_double),
+                ("residual_update", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -68,7 +69,7 @@ class Result(ctypes.Structure):
                 ("gmres_iters", ctypes.c_int * MAX_TRACE), ("omega", ctypes.c_double * MAX_TRACE),
                 ("e", ctypes.c_double * MAX_TRACE), ("omega_evals", ctypes.c_int * MAX_TRACE),
                 ("ms_linear", ctypes.c_double), ("ms_newton", ctypes.c_double),
-                ("ms_energy", ctypes.c_double)]
+                ("ms_energy", ctypes.c_double), ("residual_updates", ctypes.c_int)]
 
     def as_dict(self):
         k = self.newton_iters
@@ -76,7 +77,8 @@ class Result(ctypes.Structure):
                     status=self.status, newton_iters=k, linear_gmres=self.linear_gmres_iters,
                     gmres=list(self.gmres_iters[:k]), omega=list(self.omega[:k]), e=list(self.e[:k]),
                     omega_evals=list(self.omega_evals[:k]), omega_fallbacks=self.omega_fallbacks,
-                    ms_linear=self.ms_linear, ms_newton=self.ms_newton, ms_energy=self.ms_energy)
+                    ms_linear=self.ms_linear, ms_newton=self.ms_newton, ms_energy=self.ms_energy,
+                    residual_updates=self.residual_updates)
 
 
 class Request(ctypes.Structure):
@@ -105,7 +107,7 @@ class Tuning(ctypes.Structure):
                 ("nbody_packed", ctypes.c_int32), ("ff_blocks_per_sm", ctypes.c_int32),
                 ("ff_kernel", ctypes.c_int32), ("spmv_lanes", ctypes.c_int32),
                 ("spmv_block", ctypes.c_int32), ("pcg_blocks_per_sm", ctypes.c_int32),
-                ("pcg_lanes", ctypes.c_int32)]
+                ("pcg_lanes", ctypes.c_int32), ("treecode", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

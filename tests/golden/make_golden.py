@@ -3,7 +3,9 @@
 multi_charge_sphere.json: the oracle's solve of the 200-charge sphere (radius 12,
 shell to 24, nu = 20, 17 layers; 72,036 vertices, 408,000 tets, 8000 + 8000
 triangles; eps 2/80, 0.1 M, 300 K) at the paper's default tolerances and at tight
-ones: energies, iteration traces, and the solution at a seeded sample of unknowns.
+ones: energies, iteration traces (Newton, GMRES and omega-evaluation counts), the
+solution at a seeded sample of unknowns, and the oracle's own wall times (set-up
+and each solve), which calibrate the bench's sampled CPU-baseline model.
 
 Run: python tests/golden/make_golden.py   (about 10-20 minutes on 8 cores)
 """
@@ -38,6 +40,8 @@ def main():
         out[name] = dict(total=R.total, LC=R.LC, NC=R.NC, dG_ion=R.dG_ion, newton_iters=R.newton_iters,
                          gmres=[int(g) for g in R.trace['gmres']], linear_gmres=int(R.trace['linear_gmres']),
                          omega=[float(w) for w in R.trace['omega']], e=[float(v) for v in R.trace['e']],
+                         omega_evals=[int(v) for v in R.trace['omega_evals']],
+                         tol_gmres=[float(v) for v in R.trace['tol_gmres']],
                          x_sample=R.x[sample].tolist(), x_norm=float(np.linalg.norm(R.x)),
                          u_norm=float(np.linalg.norm(R.x[:P.nv])), seconds=time.time() - t)
         print(name, out[name]['total'], out[name]['newton_iters'], out[name]['seconds'], flush=True)
