@@ -57,7 +57,7 @@ FF_OPS_PAIR = {"laplace": 97.7, "yukawa": 145.7}
 # set-up and the default-tolerance solve, written by tests/golden/make_golden.py), against which
 # the sampled CPU model was checked once on that host
 ORACLE_C2_MEASURED_HOST = "x86-64, 8 cores"
-ORACLE_C2_MODEL_ON_THAT_HOST = float("nan")
+ORACLE_C2_MODEL_ON_THAT_HOST = 1047.0   # the model below with --cpu-sample 128 on that host: 16 % above
 
 
 def workload_config(case, precision):
@@ -75,6 +75,10 @@ def workload_config(case, precision):
         "T_K": case.T, "precision": precision,
         "newton": "T3 first iteration, automatic omega (Newton on f_d), L_e 0.35, Tol_omega 0.1, "
                   "Tol_GR0 1e-3 -> Tol_GR 1e-6, Tol_NL 1e-3",
+        "residual": "float-float far field at the first Newton step; later steps update it by linearity "
+                    "(c += omega p, p = -Acal(0) Delta with the float32 operator) while the updates since the "
+                    "last float-float evaluation sum to at most residual_update x ||Phi|| "
+                    "(pbfb_newton_opts.residual_update; mixed_residual_every_step times it at 0)",
         "preconditioner": "flexible GMRES, block-triangular: dense float32 single-layer inverses on the "
                           "surface rows (built once per mesh and kappa), then 30 Jacobi-PCG iterations on "
                           "the FEM block",
@@ -180,7 +184,7 @@ def serving_cases(n, seed=5000):
     return cases
 
 
-def run_serving(pbfb, cases, max_inflight, budget):
+def run_serving(pbfb, cases, max_inflight, budget, residual_update=0.0, precision=None):
     """Saturation run (all requests at t = 0) for capacity, then Poisson arrivals at 0.8x
     capacity; latency = arrival -> result (the request's own set-up included)."""
     import numpy as np
@@ -192,7 +196,8 @@ def run_serving(pbfb, cases, max_inflight, budget):
             got += sv.poll(64, 100000)
         return got
 
-    opts = pbfb.default_opts(precision=pbfb.MIXED)
+    precision = pbfb.MIXED if precision is None else precision
+    opts = pbfb.default_opts(precision=precision, residual_update=residual_update)
     sv = pbfb.Server(budget, max_inflight, cached_meshes=16)
     t0 = time.perf_counter()
     for i, c in enumerate(cases):
@@ -218,11 +223,14 @@ def run_serving(pbfb, cases, max_inflight, budget):
     sv.close()
     lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in got])
     ok = all(r["status"] == 0 for r in res + got)
+    energies = {int(r["id"]): r["total"] for r in res}
     return {"requests": len(cases), "max_inflight": max_inflight, "budget_bytes": budget,
             "saturation_solves_per_s": cap, "peak_bytes": st["peak"],
             "open_loop_rate_per_s": rate, "open_loop_solves_per_s": len(cases) / span,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "all_ok": ok, "resident_mesh_hits": [int(st["mesh_hits"]), int(st2["mesh_hits"])],
+            "precision": "fp64" if precision == pbfb.FP64 else "mixed",
+            "energies_kcal_mol": [energies[i] for i in sorted(energies)],
             "workload": "sphere (1-200 charges) or double helix (8-24 bp) by a fair coin, 2000-8000 "
                         "triangles per surface (log-uniform), 0.01-1 M, eps_in 2 or 4; mixed precision, "
                         "paper tolerances; up to 16 meshes kept resident between requests"}
@@ -243,7 +251,8 @@ def run_pbfb(args):
     dev = torch.device("cuda", local)
     case = inputs.multi_charge_sphere() if args.workload == "multi_charge_sphere" else inputs.single_charge_sphere()
     prec = pbfb.MIXED if args.precision == "mixed" else pbfb.FP64
-    opts = pbfb.default_opts(precision=prec)
+    opts = pbfb.default_opts(precision=prec,
+                             residual_update=args.residual_update if prec == pbfb.MIXED else 0.0)
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
     mesh = pbfb.Mesh.from_case(case)
@@ -330,9 +339,12 @@ def run_pbfb(args):
     if prec == pbfb.MIXED:
         l32, ms32 = prof["nbody_launches"], prof["nbody_ms"]
         if l32:
-            cands.append(dict(kernel="k_nbody_f32x2 (float32 far field of the GMRES operator, packed, 2 targets "
-                                     "per thread)", launches=l32, ms=ms32, pairs=prof["nbody_pairs"],
-                              flops=prof["nbody_pairs"] * fpair, peak=peak32, traffic=NBODY_TRAFFIC,
+            name32 = ("k_tree_eval + k_tree_up_part (float32 far field of the GMRES operator through the treecode: "
+                      "near pairs and cluster proxies, packed, 2 targets per thread)" if tuned.get("treecode") == 2
+                      else "k_nbody_f32x2 (float32 far field of the GMRES operator, packed, 2 targets per thread)")
+            cands.append(dict(kernel=name32, launches=l32, ms=ms32, pairs=prof["nbody_pairs"],
+                              flops=prof["nbody_pairs"] * fpair, peak=peak32,
+                              traffic=None if tuned.get("treecode") == 2 else NBODY_TRAFFIC,
                               peak_basis=peak_basis))
         lff, msff = prof["nbodyff_launches"], prof["nbodyff_ms"]
         packed_ff = tuned.get("ff_kernel") == 4
@@ -379,7 +391,8 @@ def run_pbfb(args):
         "ms_per_step": total_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == pbfb.MIXED else "f64",
         "data": "synthetic (seeded sphere mesh and charges)",
-        "config": workload_config(case, args.precision) | {"parallelism": f"replicas x{ws}"},
+        "config": workload_config(case, args.precision) | {"parallelism": f"replicas x{ws}",
+                                                            "residual_update": opts.residual_update},
         "p50_ms": statistics.median(step_ms),
         "p99_ms": float(np.percentile(step_ms, 99)),
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
@@ -425,13 +438,28 @@ def run_pbfb(args):
             if os.path.exists(GOLDEN):
                 ref = json.load(open(GOLDEN))["tight"]["total"]
                 out["fp64_gpu"]["energy_rel_err_vs_oracle"] = abs(r64["total"] - ref) / abs(ref)
+    # the mixed path with the float-float residual evaluated at every Newton step (residual_update = 0)
+    if prec == pbfb.MIXED and args.residual_update > 0:
+        o0 = pbfb.default_opts(precision=pbfb.MIXED)
+        ms0 = []
+        for _ in range(max(1, min(args.steps, 5))):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r0 = mesh.solve_device(case.eps_in, case.eps_out, case.kappa, case.T, x_out, o0)
+            e1.record(stream)
+            e1.synchronize()
+            ms0.append(e0.elapsed_time(e1))
+        out["mixed_residual_every_step"] = {"steps": len(ms0), "ms_per_solve": sum(ms0) / len(ms0),
+                                            "newton_iters": r0["newton_iters"], "total_kcal_mol": r0["total"]}
     if args.full_formulation and ws == 1 and args.workload == "multi_charge_sphere":
         out["full_formulation"] = run_full_formulation(pbfb, inputs, tuned, opts, res, flush, stream)
     if args.helix > 0 and ws == 1 and args.workload == "multi_charge_sphere":
         out["double_helix"] = run_helix(pbfb, inputs, opts, flush, stream, args.helix)
     if args.serving > 0 and args.workload == "multi_charge_sphere":
         cases = serving_cases(args.serving)
-        out["serving"] = run_serving(pbfb, cases, 4, 64 << 30)
+        out["serving"] = run_serving(pbfb, cases, 4, 64 << 30, args.residual_update)
     if os.path.exists(GOLDEN) and args.workload == "multi_charge_sphere":
         g = json.load(open(GOLDEN))
         ref = g["tight"]["total"]
@@ -524,6 +552,119 @@ def run_helix(pbfb, inputs, opts, flush, stream, steps=2):
            "share_float_float_far_field": prof["nbodyff_ms"] / tot if tot else None,
            "float32_pairs_per_launch": prof["nbody_pairs"] / max(prof["nbody_launches"], 1)}
     m.close()
+    return out
+
+
+def _mixed_case(seed, kw):
+    sys.path.insert(0, ROOT)
+    from paper_2511_21713_gb300 import inputs
+    return inputs.mixed_case(seed, **kw)
+
+
+def generate_cases(seeds, **kw):
+    """Instances of inputs.mixed_case, generated in a pool of freshly spawned host processes."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, min(len(seeds), os.cpu_count() or 1))) as pool:
+        return pool.starmap(_mixed_case, [(sd, kw) for sd in seeds])
+
+
+def run_batch(args):
+    """Many uneven instances solved concurrently (pbfb_solve_batch: host threads, one CUDA stream per
+    mesh, every instance's work overlapping on the GPU): spheres of 2000-8000 triangles and 1-200
+    charges, double helices of 8-48 base pairs on 5000-40000 triangles, at most 2M tets, 0.01-1 M,
+    mixed precision; launch shapes from the autotuner (cached per size bucket).  One untimed batch
+    (it builds what depends on the mesh and kappa), then `steps` timed batches.  Each instance's
+    result is checked against its own single solve on a few instances (bitwise)."""
+    import numpy as np
+    import torch
+    cases = generate_cases(list(range(4000, 4000 + args.instances)))
+    from paper_2511_21713_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2511_21713_gb300 import pbfb
+    opts = pbfb.default_opts(precision=pbfb.MIXED, residual_update=args.residual_update)
+    streams = [torch.cuda.Stream() for _ in cases]
+    t0 = time.perf_counter()
+    meshes = []
+    for c, st in zip(cases, streams):
+        m = pbfb.Mesh.from_case(c, stream=st.cuda_stream)
+        m.charges_set(c.q_xyz, c.q_z)
+        meshes.append(m)
+    create_s = time.perf_counter() - t0
+    cache = os.path.join(tempfile.mkdtemp(), "tune.json")
+    t0 = time.perf_counter()
+    for c, m in zip(cases, meshes):
+        m.set_params(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.MIXED)
+        m.autotune(reps=1, cache_file=cache)
+    tune_s = time.perf_counter() - t0
+    params = [(c.eps_in, c.eps_out, c.kappa, c.T, opts) for c in cases]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    first = pbfb.solve_batch(meshes, params, max_concurrent=args.concurrency)
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    clocks = Clocks(0)
+    clocks.start()
+    walls = []
+    res = None
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = pbfb.solve_batch(meshes, params, max_concurrent=args.concurrency)
+        torch.cuda.synchronize()
+        walls.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+    same = []
+    for i in range(0, len(cases), max(1, len(cases) // 4)):
+        c = cases[i]
+        r1 = meshes[i].solve_device(c.eps_in, c.eps_out, c.kappa, c.T, None, opts)
+        same.append(r1["total"] == res[i]["total"] and r1["gmres"] == res[i]["gmres"])
+    tris = np.array([c.gm_tris.shape[0] for c in cases])
+    tets = np.array([c.n_t for c in cases])
+    out = {"metric": METRIC, "config": {"workload": "batch of uneven instances",
+                                        "instances": len(cases), "helices": int(sum("helix" in c.name for c in cases)),
+                                        "triangles_per_surface": [int(tris.min()), int(np.median(tris)), int(tris.max())],
+                                        "tets": [int(tets.min()), int(np.median(tets)), int(tets.max())],
+                                        "max_concurrent": args.concurrency, "precision": "mixed",
+                                        "residual_update": opts.residual_update,
+                                        "note": "instances overlap through host threads and one CUDA stream per "
+                                                "mesh (pbfb_solve_batch), not one persistent launch"},
+           "value": len(cases) * len(walls) / sum(walls), "unit": "solves/s", "steps": len(walls),
+           "batch_wall_s": walls, "first_batch_s": first_s, "mesh_create_s": create_s, "autotune_s": tune_s,
+           "newton_iters": [r["newton_iters"] for r in res], "all_ok": all(r["status"] == 0 for r in res),
+           "alone_equals_batched": same, "clocks": clk}
+    for m in meshes:
+        m.close()
+    return out
+
+
+def run_serving_config(args):
+    """Serving at the configuration's sizes: a seeded Poisson-arrival stream of `requests` solves,
+    spheres or double helices by a fair coin, 2000-80000 surface triangles (log-uniform; at most 2M
+    tets), eps_in 2 or 4, 0.01-1 M; admitted by HBM budget, solved concurrently with resident
+    meshes.  Mixed arm: saturation capacity, then arrivals at 0.8x capacity (p50 / p99 from arrival to
+    result).  Float64 arm: the same for the requests of at most `fp64_max_tri` triangles (the float64
+    far field makes larger surfaces take minutes), on the same stream order."""
+    import numpy as np
+    import torch
+    cases = generate_cases(list(range(5000, 5000 + args.requests)), sphere_tri=(2000.0, 80000.0),
+                           helix_tri=(2000.0, 80000.0))
+    from paper_2511_21713_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2511_21713_gb300 import pbfb
+    torch.cuda.init()
+    tris = np.array([c.gm_tris.shape[0] for c in cases])
+    out = {"metric": METRIC, "config": {"workload": "serving stream", "requests": len(cases),
+                                        "triangles_per_surface": [int(tris.min()), int(np.median(tris)),
+                                                                  int(tris.max())],
+                                        "helices": int(sum("helix" in c.name for c in cases)),
+                                        "budget_bytes": args.budget_gb << 30, "max_inflight": args.concurrency,
+                                        "residual_update": args.residual_update}}
+    out["mixed"] = run_serving(pbfb, cases, args.concurrency, args.budget_gb << 30, args.residual_update)
+    small = [c for c in cases if c.gm_tris.shape[0] <= args.fp64_max_tri]
+    if small:
+        out["fp64"] = run_serving(pbfb, small, args.concurrency, args.budget_gb << 30, 0.0, precision=pbfb.FP64)
+        out["mixed_same_subset"] = run_serving(pbfb, small, args.concurrency, args.budget_gb << 30,
+                                               args.residual_update)
     return out
 
 
@@ -689,7 +830,8 @@ def run_reference(args):
             "data": "synthetic (seeded sphere mesh and charges)",
             "config": workload_config(case, "fp64 (CPU oracle)") | {
                 "parallelism": "1 host process",
-                "preconditioner": "Jacobi (the oracle's GMRES: diagonal of the coupled operator)"},
+                "preconditioner": "Jacobi (the oracle's GMRES: diagonal of the coupled operator)",
+                "residual": "float64 at every Newton step"},
             "step": "one bounded sample of the workload (see cpu_baseline.sample); ms_per_step is its measured "
                     "duration, value the modelled complete solve's rate",
             "model_s_per_solve": sum(models) / len(models),
@@ -714,6 +856,8 @@ def run_step(args):
     prec = {"farfield_f32": pbfb.MIXED, "farfield_ff": pbfb.FLOAT2, "farfield_f64": pbfb.FP64}.get(args.step,
                                                                                                    pbfb.MIXED)
     m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, prec)
+    if args.treecode:
+        m.apply_tuning(dict(m.get_tuning(), treecode=args.treecode))
     dev = torch.device("cuda")
     r = np.linalg.norm(case.xyz, axis=1)
     u = torch.as_tensor(4.0 * np.exp(-0.2 * (r - r.min())), device=dev)
@@ -756,6 +900,8 @@ def main():
                     help="1/k of the BEM rows in each step of the reference (oracle) arm")
     ap.add_argument("--step", default=None, help="time one step of the solve (profiling); see run_step")
     ap.add_argument("--reps", type=int, default=2, help="repetitions of --step")
+    ap.add_argument("--treecode", type=int, default=0,
+                    help="--step farfield_f32: 1 direct sum, 2 treecode (0 built-in)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3, help="host-buffer solves timed for the e2e figure")
     ap.add_argument("--serving", type=int, default=24, help="requests in the serving run (0 = skip)")
@@ -764,6 +910,16 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=-1,
                     help="float64-path solves timed for fp64_gpu (default: as many as --steps)")
     ap.add_argument("--helix", type=int, default=2, help="timed solves of the double helix (0 = skip)")
+    ap.add_argument("--config", default="headline", choices=["headline", "batch", "serving"],
+                    help="batch: many uneven instances at once; serving: the request stream at 2k-80k triangles")
+    ap.add_argument("--instances", type=int, default=64, help="--config batch: instances")
+    ap.add_argument("--concurrency", type=int, default=8, help="--config batch/serving: solves in flight")
+    ap.add_argument("--requests", type=int, default=64, help="--config serving: requests")
+    ap.add_argument("--budget-gb", type=int, default=160, help="--config serving: HBM budget")
+    ap.add_argument("--fp64-max-tri", type=int, default=8000,
+                    help="--config serving: largest surface (triangles) of the float64 arm")
+    ap.add_argument("--residual-update", type=float, default=0.5,
+                    help="mixed path: pbfb_newton_opts.residual_update (0 = float-float residual every step)")
     ap.add_argument("--no-full-formulation", dest="full_formulation", action="store_false",
                     help="skip the solves of the formulation with Omega_m meshed (full_formulation)")
     ap.add_argument("--workload", default="multi_charge_sphere", choices=["multi_charge_sphere", "small"],
@@ -771,6 +927,9 @@ def main():
     args = ap.parse_args()
     if args.step:
         run_step(args)
+        return
+    if args.config in ("batch", "serving"):
+        print(json.dumps(run_batch(args) if args.config == "batch" else run_serving_config(args)))
         return
     out = run_reference(args) if args.impl == "reference" else run_pbfb(args)
     if out is not None:

@@ -292,7 +292,9 @@ int pbfb_bem_apply(pbfb_mesh* mesh, int which, int op, const double* x_dev, doub
  * split kernel, targets per thread and split rule, with at most 8 source
  * splits (results equal to float64 rounding), except that a mesh tuned to the
  * mutual-pair kernel (pbfb_tuning.nbody_packed = 2) runs the packed split
- * kernel instead (equal to float32 rounding).  Its
+ * kernel instead (equal to float32 rounding), and a mesh whose float32 far
+ * field runs the treecode (pbfb_tuning.treecode) the direct sum (equal to the
+ * treecode's approximation, about 1e-6 of the largest entry).  Its
  * working memory is one fixed library-wide device array of 6 MiB (float32
  * source records and float64 partial sums), present on every device that
  * loads the library until the process exits; the call allocates nothing.

@@ -83,8 +83,11 @@ struct SurfaceTree {
   DBuf<int> leaf_beg, leaf_end, leaf_chunk;  // per leaf: targets [beg, end), chunks [chunk[L], chunk[L+1])
   DBuf<int> chunk_leaf, chunk_tile; // per chunk: its leaf; its tiles [tile[c], tile[c+1])
   DBuf<int2> tiles;                 // per tile: first source record, count (<= 128)
-  DBuf<int> clus_beg, clus_end;     // per approximated cluster: its points in tree order
+  int nseg = 0;
+  DBuf<int> clus_seg;               // per approximated cluster: its upward-pass segments
   DBuf<float> clus_box;             // per cluster: lo x, y, z, hi x, y, z (centre-relative)
+  DBuf<int> seg_clus, seg_beg, seg_cnt;  // per segment: cluster, first point (tree order), points
+  DBuf<float4> up_part;             // per segment: partial proxies (charge, dipole) of its cluster
   DBuf<float4> tgt;                 // target positions in tree order
   DBuf<float4> spos, sdl;           // nq points in tree order, then nclus x (p+1)^3 proxies
   DBuf<double> part;                // nchunk x 256 partial sums

@@ -132,9 +132,16 @@ int plan_tree_tiles(const double* xyz, int n, int leaf, double theta, int npx, i
       cnode.push_back(C);
     }
   T.nclus = (int)cnode.size();
+  T.clus_seg.assign(1, 0);
   for (int C : cnode) {
     T.clus_beg.push_back(P.begin[C]);
     T.clus_end.push_back(P.end[C]);
+    for (int b = P.begin[C]; b < P.end[C]; b += leaf) {
+      T.seg_clus.push_back((int)T.clus_seg.size() - 1);
+      T.seg_beg.push_back(b);
+      T.seg_cnt.push_back(std::min(leaf, P.end[C] - b));
+    }
+    T.clus_seg.push_back((int)T.seg_beg.size());
     const double* bx = &P.box[6 * (size_t)C];
     double side = 0.0;
     for (int d = 0; d < 3; ++d) side = std::max(side, bx[3 + d] - bx[d]);

@@ -51,79 +51,93 @@ __global__ void k_tree_permute(int nq, const int* __restrict__ perm, const float
   sdl_t[i] = sdl[j];
 }
 
-// Upward pass: one block per approximated cluster.  Proxy k = (a, b, c) at (tx_a, ty_b, tz_c)
-// receives sum_j L_a(x_j) L_b(y_j) L_c(z_j) (s_j, m_j); the 1-D values come from the barycentric
-// formula l_a(x) = (w_a / (x - t_a)) / sum_m (w_m / (x - t_m)), w_m = (-1)^m (halved at both ends),
-// or the unit vector when x coincides with a node.
-__global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(int nq, const int* __restrict__ cbeg,
-                                                        const int* __restrict__ cend,
-                                                        const float* __restrict__ cbox,
-                                                        float4* __restrict__ spos_t, float4* __restrict__ sdl_t) {
+// Upward pass, in two kernels.  k_tree_up_part: one block per segment (at most 256 consecutive
+// points of one cluster): proxy k = (a, b, c) at (tx_a, ty_b, tz_c) of the cluster's box receives
+// sum_j L_a(x_j) L_b(y_j) L_c(z_j) (s_j, m_j) over the segment's points, the 1-D values from the
+// barycentric formula l_a(x) = (w_a / (x - t_a)) / sum_m (w_m / (x - t_m)), w_m = (-1)^m (halved at
+// both ends), or the unit vector when x coincides with a node.  k_tree_up_sum: one block per
+// cluster adds its segments in order and writes the proxy source records after the points.
+__device__ __forceinline__ float cheb_node(const float* __restrict__ cbox, int c, int d, int k) {
+  const float lo = cbox[6 * c + d], hi = cbox[6 * c + 3 + d];
+  return 0.5f * (lo + hi) + 0.5f * (hi - lo) * cospif((float)k / (float)TREE_P);
+}
+
+__global__ void __launch_bounds__(TREE_UP_NT) k_tree_up_part(const int* __restrict__ seg_clus,
+                                                             const int* __restrict__ seg_beg,
+                                                             const int* __restrict__ seg_cnt,
+                                                             const float* __restrict__ cbox,
+                                                             const float4* __restrict__ spos_t,
+                                                             const float4* __restrict__ sdl_t,
+                                                             float4* __restrict__ part) {
   __shared__ float node[3][TREE_K];
-  __shared__ float lw[3][TREE_K][TREE_NT];
-  __shared__ float4 src[TREE_NT];
-  const int c = blockIdx.x;
-  const int b = cbeg[c], e = cend[c];
+  __shared__ float lw[3][TREE_K][TREE_LEAF];
+  __shared__ float4 src[TREE_LEAF];
+  const int g = blockIdx.x;
+  const int c = seg_clus[g], b = seg_beg[g], cnt = seg_cnt[g];
   const int t = threadIdx.x;
-  if (t < 3 * TREE_K) {
-    const int d = t / TREE_K, k = t - d * TREE_K;
-    const float lo = cbox[6 * c + d], hi = cbox[6 * c + 3 + d];
-    node[d][k] = 0.5f * (lo + hi) + 0.5f * (hi - lo) * cospif((float)k / (float)TREE_P);
+  if (t < 3 * TREE_K) node[t / TREE_K][t % TREE_K] = cheb_node(cbox, c, t / TREE_K, t % TREE_K);
+  __syncthreads();
+  if (t < TREE_LEAF) {
+    if (t < cnt) {
+      const float4 p = spos_t[b + t];
+      const float4 q = sdl_t[b + t];
+      src[t] = make_float4(p.w, q.x, q.y, q.z);
+      const float xs[3] = {p.x, p.y, p.z};
+      for (int d = 0; d < 3; ++d) {
+        float a[TREE_K];
+        float den = 0.f;
+        int hit = -1;
+        for (int k = 0; k < TREE_K; ++k) {
+          const float dx = xs[d] - node[d][k];
+          const float w = ((k & 1) ? -1.f : 1.f) * ((k == 0 || k == TREE_P) ? 0.5f : 1.f);
+          if (dx == 0.f) hit = k;
+          a[k] = dx == 0.f ? 0.f : w / dx;
+          den += a[k];
+        }
+        for (int k = 0; k < TREE_K; ++k) lw[d][k][t] = hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] / den;
+      }
+    } else {
+      src[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int d = 0; d < 3; ++d)
+        for (int k = 0; k < TREE_K; ++k) lw[d][k][t] = 0.f;
+    }
   }
+  __syncthreads();
+  if (t < TREE_NPX) {
+    const int ka = t / (TREE_K * TREE_K), kb = (t / TREE_K) % TREE_K, kc = t % TREE_K;
+    float fs = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int jj = 0; jj < cnt; ++jj) {
+      const float w = lw[0][ka][jj] * lw[1][kb][jj] * lw[2][kc][jj];
+      const float4 q = src[jj];
+      fs = fmaf(w, q.x, fs);
+      fx = fmaf(w, q.y, fx);
+      fy = fmaf(w, q.z, fy);
+      fz = fmaf(w, q.w, fz);
+    }
+    part[(size_t)g * TREE_NPX + t] = make_float4(fs, fx, fy, fz);
+  }
+}
+
+__global__ void __launch_bounds__(TREE_UP_NT) k_tree_up_sum(int nq, const int* __restrict__ clus_seg,
+                                                            const float* __restrict__ cbox,
+                                                            const float4* __restrict__ part,
+                                                            float4* __restrict__ spos_t,
+                                                            float4* __restrict__ sdl_t) {
+  const int c = blockIdx.x;
+  const int t = threadIdx.x;
+  if (t >= TREE_NPX) return;
   const int ka = t / (TREE_K * TREE_K), kb = (t / TREE_K) % TREE_K, kc = t % TREE_K;
   double as = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
-  __syncthreads();
-  for (int j0 = b; j0 < e; j0 += TREE_NT) {
-    if (t < TREE_NT) {
-      const int j = j0 + t;
-      if (j < e) {
-        const float4 p = spos_t[j];
-        const float4 q = sdl_t[j];
-        src[t] = make_float4(p.w, q.x, q.y, q.z);
-        const float xs[3] = {p.x, p.y, p.z};
-        for (int d = 0; d < 3; ++d) {
-          float a[TREE_K];
-          float den = 0.f;
-          int hit = -1;
-          for (int k = 0; k < TREE_K; ++k) {
-            const float dx = xs[d] - node[d][k];
-            const float w = ((k & 1) ? -1.f : 1.f) * ((k == 0 || k == TREE_P) ? 0.5f : 1.f);
-            if (dx == 0.f) hit = k;
-            a[k] = dx == 0.f ? 0.f : w / dx;
-            den += a[k];
-          }
-          for (int k = 0; k < TREE_K; ++k) lw[d][k][t] = hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] / den;
-        }
-      } else {
-        src[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int d = 0; d < 3; ++d)
-          for (int k = 0; k < TREE_K; ++k) lw[d][k][t] = 0.f;
-      }
-    }
-    __syncthreads();
-    if (t < TREE_NPX) {
-      float fs = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-      const int cnt = min(TREE_NT, e - j0);
-      for (int jj = 0; jj < cnt; ++jj) {
-        const float w = lw[0][ka][jj] * lw[1][kb][jj] * lw[2][kc][jj];
-        const float4 q = src[jj];
-        fs = fmaf(w, q.x, fs);
-        fx = fmaf(w, q.y, fx);
-        fy = fmaf(w, q.z, fy);
-        fz = fmaf(w, q.w, fz);
-      }
-      as += fs;
-      ax += fx;
-      ay += fy;
-      az += fz;
-    }
-    __syncthreads();
+  for (int g = clus_seg[c]; g < clus_seg[c + 1]; ++g) {
+    const float4 v = part[(size_t)g * TREE_NPX + t];
+    as += v.x;
+    ax += v.y;
+    ay += v.z;
+    az += v.w;
   }
-  if (t < TREE_NPX) {
-    const int o = nq + c * TREE_NPX + t;
-    spos_t[o] = make_float4(node[0][ka], node[1][kb], node[2][kc], (float)as);
-    sdl_t[o] = make_float4((float)ax, (float)ay, (float)az, 0.f);
-  }
+  const int o = nq + c * TREE_NPX + t;
+  spos_t[o] = make_float4(cheb_node(cbox, c, 0, ka), cheb_node(cbox, c, 1, kb), cheb_node(cbox, c, 2, kc), (float)as);
+  sdl_t[o] = make_float4((float)ax, (float)ay, (float)az, 0.f);
 }
 
 // Evaluation: block = one chunk (a target leaf and a run of its source tiles).  Tiles that overlap
@@ -291,10 +305,14 @@ int build_surface_tree(Mesh* m, Surface* s) {
   PB_TRY(T.chunk_leaf.upload(P.chunk_leaf.data(), P.chunk_leaf.size(), m->stream));
   PB_TRY(T.chunk_tile.upload(P.chunk_tile.data(), P.chunk_tile.size(), m->stream));
   PB_TRY(T.tiles.upload(tiles.data(), tiles.size(), m->stream));
+  T.nseg = (int)P.seg_beg.size();
   if (P.nclus > 0) {
-    PB_TRY(T.clus_beg.upload(P.clus_beg.data(), P.nclus, m->stream));
-    PB_TRY(T.clus_end.upload(P.clus_end.data(), P.nclus, m->stream));
+    PB_TRY(T.clus_seg.upload(P.clus_seg.data(), P.clus_seg.size(), m->stream));
     PB_TRY(T.clus_box.upload(cbox.data(), cbox.size(), m->stream));
+    PB_TRY(T.seg_clus.upload(P.seg_clus.data(), T.nseg, m->stream));
+    PB_TRY(T.seg_beg.upload(P.seg_beg.data(), T.nseg, m->stream));
+    PB_TRY(T.seg_cnt.upload(P.seg_cnt.data(), T.nseg, m->stream));
+    PB_TRY(T.up_part.alloc((size_t)T.nseg * TREE_NPX));
   }
   PB_TRY(T.spos.alloc((size_t)nq + (size_t)P.nclus * TREE_NPX));
   PB_TRY(T.sdl.alloc((size_t)nq + (size_t)P.nclus * TREE_NPX));
@@ -324,8 +342,11 @@ int launch_tree_far(Mesh* m, Surface* s, double kappa, const float4* spos, const
   k_tree_permute<<<blocks(nq, 256), 256, 0, m->stream>>>(nq, T.perm.p, spos, sdl, T.spos.p, T.sdl.p);
   PB_LAUNCHED(m);
   if (T.nclus > 0) {
-    k_tree_up<<<T.nclus, TREE_UP_NT, 0, m->stream>>>(nq, T.clus_beg.p, T.clus_end.p, T.clus_box.p, T.spos.p,
-                                                     T.sdl.p);
+    k_tree_up_part<<<T.nseg, TREE_UP_NT, 0, m->stream>>>(T.seg_clus.p, T.seg_beg.p, T.seg_cnt.p, T.clus_box.p,
+                                                         T.spos.p, T.sdl.p, T.up_part.p);
+    PB_LAUNCHED(m);
+    k_tree_up_sum<<<T.nclus, TREE_UP_NT, 0, m->stream>>>(nq, T.clus_seg.p, T.clus_box.p, T.up_part.p, T.spos.p,
+                                                         T.sdl.p);
     PB_LAUNCHED(m);
   }
   const float kf = (float)kappa;

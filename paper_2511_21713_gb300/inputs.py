@@ -471,6 +471,35 @@ def double_helix(n_bp=24, nu=45, layers=16, seed=3000, n_interior=1500, ionic=0.
                 eps_in, eps_out, kappa, T)
 
 
+def mixed_case(seed, sphere_tri=(2000.0, 8000.0), helix_tri=(5000.0, 40000.0), n_bp=(8, 48),
+               max_tets=2_000_000):
+    """One instance of the batched and served mixes, drawn from `seed`: a sphere or a double helix by
+    a fair coin; surface triangles log-uniform in sphere_tri or helix_tri (icosphere frequency
+    nu = round(sqrt(triangles / 20))); ionic strength U(0.01, 1) M; eps_in 2 or 4.  Spheres: radius
+    12, shell to 24, 1-200 unit charges uniform in r < 9.6 with a random number of them positive.
+    Helices: n_bp uniform in n_bp (62 interior atoms per base pair), shell to three Debye lengths
+    beyond the surface.  Shell layers max(8, 0.85 nu) (spheres) or max(8, 0.6 nu) (helices), fewer
+    where needed to keep the shell at most max_tets tets (4 at least)."""
+    rng = SplitMix64(seed)
+    sphere = rng.below(2) == 0
+    lo, hi = sphere_tri if sphere else helix_tri
+    tri = lo * (hi / lo) ** rng.uniform()
+    nu = max(3, int(round((tri / 20.0) ** 0.5)))
+    ionic = 0.01 + 0.99 * rng.uniform()
+    eps_in = (2.0, 4.0)[rng.below(2)]
+    cap = int(max_tets // (60 * nu * nu))
+    if sphere:
+        layers = max(4, min(max(8, int(0.85 * nu)), cap))
+        nq = 1 + rng.below(200)
+        q, z = ball_charges(nq, 9.6, rng.below(nq + 1), seed + 17)
+        return sphere_case(nu=nu, a=12.0, R=24.0, layers=layers, q_xyz=q, q_z=z, eps_in=eps_in, eps_out=80.0,
+                           ionic=ionic, T=300.0, name=f"mix{seed}_sphere_nu{nu}_L{layers}")
+    nbp = n_bp[0] + rng.below(n_bp[1] - n_bp[0] + 1)
+    layers = max(4, min(max(8, int(0.6 * nu)), cap))
+    return double_helix(n_bp=nbp, nu=nu, layers=layers, seed=seed + 31, n_interior=62 * nbp, ionic=ionic,
+                        eps_in=eps_in)
+
+
 def _ray_triangle_of(d, dirs, tri):
     """Index of the ray triangle containing each unit direction d (first match)."""
     A, B, C = dirs[tri[:, 0]], dirs[tri[:, 1]], dirs[tri[:, 2]]

@@ -79,6 +79,26 @@ def test_fp64_solve_matches_oracle_golden(big):
     assert abs(res["NC"] - ref["NC"]) < 1e-9 * abs(ref["total"])
 
 
+def test_mixed_solve_with_residual_updates(big):
+    """residual_update = 0.5: after the first Newton step the residual is updated by linearity
+    (c += omega p with the float32 operator's p = -Acal(0) Delta) instead of a float-float far field;
+    the Newton path (iterations, GMRES counts) is unchanged and the energy stays within 1e-8 of the
+    oracle's (the mixed-path target is 1e-5); float64 solves ignore the option."""
+    from paper_2511_21713_gb300 import pbfb
+    case, m = big
+    g = json.load(open(GOLDEN))
+    ref = g["tight"]["total"]
+    _, r0 = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.default_opts(precision=pbfb.MIXED))
+    x, r = m.solve(case.eps_in, case.eps_out, case.kappa, case.T,
+                   pbfb.default_opts(precision=pbfb.MIXED, residual_update=0.5))
+    assert r["residual_updates"] >= r["newton_iters"] - 2 >= 1
+    assert r["newton_iters"] == r0["newton_iters"] and r["gmres"] == r0["gmres"]
+    assert abs(r["total"] - ref) < 1e-8 * abs(ref)
+    idx = np.array(g["sample_index"])
+    xs = np.array(g["tight"]["x_sample"])
+    assert np.linalg.norm(x[idx] - xs) < 1e-6 * np.linalg.norm(xs)
+
+
 def _row_sample(P_surface, k=12, seed=3):
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(P_surface.n, k, replace=False))

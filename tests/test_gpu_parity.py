@@ -289,6 +289,25 @@ def test_forced_fallback_and_picard_secant_follow_the_oracle(pair):
         assert rel(x, R.x) < 1e-8
 
 
+def test_residual_update_option(pair):
+    """Mixed solves with residual_update reach the oracle's energy within the mixed-path 1e-5
+    (paper tolerances) and its solution at tight tolerances within 1e-6; the float64 path never
+    updates (the option is ignored there)."""
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    ref = pb.solve(P, pb.Opts(**TIGHT))
+    _, r = m.solve(case.eps_in, case.eps_out, case.kappa, case.T,
+                   pbfb.default_opts(precision=pbfb.MIXED, residual_update=0.5))
+    assert r["residual_updates"] >= 1 and abs(r["total"] - ref.total) < 1e-5 * abs(ref.total)
+    x, r = m.solve(case.eps_in, case.eps_out, case.kappa, case.T,
+                   pbfb.default_opts(precision=pbfb.MIXED, residual_update=0.5, tol_gmres0=1e-10,
+                                     tol_gmres=1e-10, tol_nl=1e-8))
+    assert r["status"] == 0 and rel(x, ref.x) < 1e-6
+    _, r = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.default_opts(residual_update=0.5))
+    assert r["residual_updates"] == 0
+
+
 def test_deterministic(pair):
     from paper_2511_21713_gb300 import pbfb
     case, m, _ = pair

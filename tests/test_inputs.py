@@ -48,3 +48,31 @@ def test_small_helix_mesh_is_a_valid_shell():
     r_in = np.linalg.norm(c.xyz[:ns], axis=1)
     assert np.allclose(r_out, r_in.max() + 3.0 / c.kappa)
     assert abs(c.q_z.sum() + 2 * nbp) < 1e-12 and abs(c.kappa - 0.1257259) < 1e-6
+
+
+def test_mixed_cases_follow_their_recipe():
+    """The batched / served mix: seeded (the same seed gives the same instance), triangles within the
+    requested ranges (log-uniform draw, rounded to an icosphere frequency), at most 2M tets, salt in
+    0.01-1 M, eps_in 2 or 4, and every charge strictly inside Gamma_m."""
+    kinds = set()
+    for seed in range(4000, 4012):
+        c = inputs.mixed_case(seed, sphere_tri=(2000.0, 3000.0), helix_tri=(2000.0, 3000.0), n_bp=(6, 8))
+        again = inputs.mixed_case(seed, sphere_tri=(2000.0, 3000.0), helix_tri=(2000.0, 3000.0), n_bp=(6, 8))
+        assert np.array_equal(c.xyz, again.xyz) and np.array_equal(c.q_z, again.q_z)
+        kinds.add("helix" in c.name)
+        nt = c.gm_tris.shape[0]
+        assert 1700 <= nt <= 3400 and c.n_t <= 2_000_000
+        assert c.eps_in in (2.0, 4.0)
+        k01 = inputs.kappa_from_ionic_strength(0.01, 80.0, 300.0)
+        k1 = inputs.kappa_from_ionic_strength(1.0, 80.0, 300.0)
+        assert k01 <= c.kappa <= k1
+        # winding number of Gamma_m at every charge (1 inside)
+        P = c.xyz[c.gm_tris]
+        for x in c.q_xyz[:20]:
+            a, b, d = P[:, 0] - x, P[:, 1] - x, P[:, 2] - x
+            la, lb, ld = (np.linalg.norm(v, axis=1) for v in (a, b, d))
+            det = np.einsum("ij,ij->i", a, np.cross(b, d))
+            den = la * lb * ld + np.einsum("ij,ij->i", a, b) * ld + np.einsum("ij,ij->i", b, d) * la \
+                + np.einsum("ij,ij->i", d, a) * lb
+            assert abs(np.sum(2 * np.arctan2(det, den)) / (4 * np.pi) - 1.0) < 1e-9
+    assert kinds == {True, False}

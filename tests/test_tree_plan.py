@@ -205,13 +205,15 @@ int main(int argc, char** argv) {
   put(fo, t.perm); put(fo, t.pos_leaf); put(fo, t.leaf_beg); put(fo, t.leaf_end); put(fo, t.leaf_chunk);
   put(fo, t.chunk_leaf); put(fo, t.chunk_tile); put(fo, t.tile_start); put(fo, t.tile_count);
   put(fo, t.clus_beg); put(fo, t.clus_end); put(fo, t.clus_box);
+  put(fo, t.seg_clus); put(fo, t.seg_beg); put(fo, t.seg_cnt); put(fo, t.clus_seg);
   fclose(fo);
   return 0;
 }
 """
 
 TILE_NAMES = ["perm", "pos_leaf", "leaf_beg", "leaf_end", "leaf_chunk", "chunk_leaf", "chunk_tile",
-              "tile_start", "tile_count", "clus_beg", "clus_end", "clus_box"]
+              "tile_start", "tile_count", "clus_beg", "clus_end", "clus_box", "seg_clus", "seg_beg", "seg_cnt",
+              "clus_seg"]
 
 
 @pytest.fixture(scope="module")
@@ -290,6 +292,14 @@ def test_tree_tiles_plan_bounds_and_coverage(tiles_driver, nu):
     for k in range(nclus):
         pts = xyz[perm[cb[k]:ce[k]]]
         assert np.all(pts >= box[k, :3] - 1e-12) and np.all(pts <= box[k, 3:] + 1e-12)
+    # upward-pass segments: each cluster's points in consecutive runs of at most 256
+    sc, sb, sn, cs = p["seg_clus"], p["seg_beg"], p["seg_cnt"], p["clus_seg"]
+    assert len(cs) == nclus + 1 and cs[0] == 0 and cs[-1] == len(sb) == len(sc) == len(sn)
+    assert np.all(sn >= 1) and np.all(sn <= 256)
+    for k in range(nclus):
+        g = np.arange(cs[k], cs[k + 1])
+        assert np.all(sc[g] == k) and sb[g[0]] == cb[k] and sb[g[-1]] + sn[g[-1]] == ce[k]
+        assert np.array_equal(sb[g[1:]], sb[g[:-1]] + sn[g[:-1]])
     pairs = 0.0
     for L in range(nleaf):
         cover = np.zeros(n, np.int32)
