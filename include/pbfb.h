@@ -385,7 +385,9 @@ typedef struct pbfb_tuning {
   int32_t spmv_block;                /* threads per block of that SpMV: 128, 256, 512 */
   int32_t pcg_blocks_per_sm;         /* blocks per SM of the cooperative inner PCG: 1..32
                                         (0: as many as fit) */
-  int32_t pcg_lanes;                 /* lanes per row of its sparse product: 2, 4 or 8 */
+  int32_t pcg_lanes;                 /* lanes per row of its sparse product: 2, 4 or 8 (CSR), or
+                                        1: one lane per row over a sliced-ELL copy of the block
+                                        (slices of 32 rows, coalesced column-by-column storage) */
   int32_t treecode;                  /* float32 far field (GMRES operator): 1 the direct sum over
                                         all point pairs, 2 the treecode (a binary tree over the
                                         quadrature points, leaves of 256; a cluster with

@@ -36,7 +36,8 @@ bool valid_tuning(const pbfb_tuning* t) {
   if (!(L == 0 || L == 4 || L == 8 || L == 16)) return false;
   if (!(B == 0 || B == 128 || B == 256 || B == 512)) return false;
   if (!in(t->pcg_blocks_per_sm, 1, 32)) return false;
-  if (!(t->pcg_lanes == 0 || t->pcg_lanes == 2 || t->pcg_lanes == 4 || t->pcg_lanes == 8)) return false;
+  if (!(t->pcg_lanes == 0 || t->pcg_lanes == 1 || t->pcg_lanes == 2 || t->pcg_lanes == 4 || t->pcg_lanes == 8))
+    return false;
   if (t->treecode < 0 || t->treecode > 2) return false;
   return true;
 }
@@ -192,7 +193,7 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
   double t_pcg = 0.0;
   if (!m->no_coop) {
     t_pcg = 1e300;
-    for (int lanes : {8, 4, 2})
+    for (int lanes : {8, 4, 2, 1})
     for (int bps : {1, 2, 4, 8, 0}) {
       pbfb_tuning t = best;
       t.pcg_blocks_per_sm = bps;

@@ -222,7 +222,12 @@ struct Mesh {
   int spmv_lanes = 0;               // lanes per row of the operator's sparse part (0 = 8; 4, 8, 16)
   int spmv_block = 0;               // threads per block of that SpMV (0 = 256; 128, 256, 512)
   int tune_pcg_bps = 0;             // blocks per SM of the cooperative inner PCG (0 = all that fit)
-  int pcg_lanes = 0;                // lanes per row of its sparse product (0 = 8; 4 or 8)
+  int pcg_lanes = 0;                // lanes per row of its sparse product (0 = 8; 4 or 8; 1: the
+                                    // sliced-ELL copy, a lane per row)
+  bool sell_ok = false;             // sliced-ELL copy of the preconditioner's FEM block built
+  int sell_nslice = 0, sell_ne = 0;
+  DBuf<int> sell_ptr, sell_col, sell_map;
+  DBuf<double> sell_val;
   bool dense_m = false, dense_s = false;  // surface rows of the block preconditioner use V^-1
   DBuf<float> dwork;                // dense single-layer build: W chunk, sweep panels
   DBuf<int> dflag;                  // sweep pivot status

@@ -268,22 +268,35 @@ __global__ void k_diag_inv(int nv, const int* __restrict__ ptr, const int* __res
   dinv[r] = 1.0 / d;
 }
 
+// Both scalars of a step at once: warp 0 of every block reads the per-block partials lane-strided
+// (lane l sums entries l, l + 32, ... in that order), then a butterfly over the 32 lanes; the order
+// of every addition is fixed, so each block obtains the same two values.
+__device__ __forceinline__ void coop_sum2(const double* pa, const double* pb, int nb, double* a, double* b) {
+  __shared__ double tot[2];
+  if (threadIdx.x < 32) {
+    double sa = 0.0, sb = 0.0;
+    for (int k = threadIdx.x; k < nb; k += 32) {
+      sa += pa[k];
+      sb += pb[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if (threadIdx.x == 0) {
+      tot[0] = sa;
+      tot[1] = sb;
+    }
+  }
+  __syncthreads();
+  *a = tot[0];
+  *b = tot[1];
+  __syncthreads();
+}
+
 // The whole inner PCG in one cooperative launch (all blocks resident; grid-wide barriers between
 // the dependent phases).  Every block sums the per-block partials itself in the same fixed order,
 // so all blocks see identical scalars and the result is deterministic.  part: 2 * gridDim.x.
-__device__ __forceinline__ double coop_sum(const double* part, int nb) {
-  __shared__ double tot;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[b];
-    tot = s;
-  }
-  __syncthreads();
-  double v = tot;
-  __syncthreads();
-  return v;
-}
-
 // Chronopoulos-Gear form of preconditioned CG (one fused reduction per step): with w = A z,
 // gamma = r.z, delta = z.w: beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old),
 // p = z + beta p, q = w + beta q (= A p), x += alpha p, r -= alpha q, z = M r.  Same iterates as
@@ -336,8 +349,8 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int
     block_sum_store(ag, part_g + blockIdx.x);
     block_sum_store(ad, part_d + blockIdx.x);
     grid.sync();
-    const double gamma = coop_sum(part_g, nb);
-    const double delta = coop_sum(part_d, nb);
+    double gamma, delta;
+    coop_sum2(part_g, part_d, nb, &gamma, &delta);
     // zero residual (e.g. a right-hand side that vanishes on the FEM rows): nothing left to do
     double beta = 0.0, alpha = 0.0;
     if (gamma != 0.0) {
@@ -363,6 +376,90 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int
     }
     grid.sync();
   }
+}
+
+// The same iteration with the FEM block in sliced ELL form (slices of 32 consecutive rows, each
+// stored column by column at the slice's largest row length, padding entries with value 0): a
+// warp takes a slice, a lane a row, so the value and column loads are coalesced and the products
+// of a row are independent loads rather than a chain.  Sums in a row run in stored column order.
+__global__ void __launch_bounds__(PCG_T) k_pcg_coop_sell(int nv, int nslice, int iters, const int* __restrict__ sptr,
+                                                          const int* __restrict__ scol,
+                                                          const double* __restrict__ sval,
+                                                          const double* __restrict__ b, const double* __restrict__ dinv,
+                                                          double* __restrict__ x, double* __restrict__ r,
+                                                          double* __restrict__ z, double* __restrict__ p,
+                                                          double* __restrict__ q, double* __restrict__ w,
+                                                          double* __restrict__ part) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int nb = gridDim.x;
+  double* part_g = part;
+  double* part_d = part + nb;
+  const int tid = blockIdx.x * PCG_T + threadIdx.x, stride = nb * PCG_T;
+  const int lane = threadIdx.x & 31, gw = tid >> 5, nw = stride >> 5;
+  for (int i = tid; i < nv; i += stride) {
+    double bi = b[i];
+    x[i] = 0.0;
+    r[i] = bi;
+    z[i] = dinv[i] * bi;
+    p[i] = 0.0;
+    q[i] = 0.0;
+  }
+  grid.sync();
+  double gamma_old = 1.0, alpha_old = 1.0;
+  for (int it = 0; it < iters; ++it) {
+    double ag = 0.0, ad = 0.0;
+    for (int sl = gw; sl < nslice; sl += nw) {
+      const int e0 = sptr[sl], wd = (sptr[sl + 1] - e0) >> 5;
+      const int* cp = scol + e0 + lane;
+      const double* vp = sval + e0 + lane;
+      double sacc = 0.0;
+#pragma unroll 4
+      for (int j = 0; j < wd; ++j) sacc += vp[32 * j] * z[cp[32 * j]];
+      const int row = 32 * sl + lane;
+      if (row < nv) {
+        w[row] = sacc;
+        const double zr = z[row];
+        ag += r[row] * zr;
+        ad += zr * sacc;
+      }
+    }
+    block_sum_store(ag, part_g + blockIdx.x);
+    block_sum_store(ad, part_d + blockIdx.x);
+    grid.sync();
+    double gamma, delta;
+    coop_sum2(part_g, part_d, nb, &gamma, &delta);
+    double beta = 0.0, alpha = 0.0;
+    if (gamma != 0.0) {
+      if (it == 0 || gamma_old == 0.0 || alpha_old == 0.0) {
+        alpha = delta != 0.0 ? gamma / delta : 0.0;
+      } else {
+        beta = gamma / gamma_old;
+        const double den = delta - beta * gamma / alpha_old;
+        alpha = den != 0.0 ? gamma / den : 0.0;
+      }
+    }
+    gamma_old = gamma;
+    alpha_old = alpha;
+    for (int i = tid; i < nv; i += stride) {
+      double pi = z[i] + beta * p[i];
+      double qi = w[i] + beta * q[i];
+      p[i] = pi;
+      q[i] = qi;
+      x[i] += alpha * pi;
+      double ri = r[i] - alpha * qi;
+      r[i] = ri;
+      z[i] = dinv[i] * ri;
+    }
+    grid.sync();
+  }
+}
+
+// sliced-ELL values of the preconditioner's FEM block from its CSR values (padding: 0)
+__global__ void k_sell_gather(int ne, const int* __restrict__ map, const double* __restrict__ val,
+                              double* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < ne) out[e] = map[e] >= 0 ? val[map[e]] : 0.0;
 }
 
 // FEM rows of the block-triangular preconditioner: out_i = v_i - sum over the coupling columns
@@ -548,6 +645,50 @@ static int jacobi(Mesh* m, double* dinv) {
 // With dense = true the surface rows use the dense float32 inverses of V_L and V_Y (built
 // once per mesh, and for Gamma_s again whenever kappa changes) on surfaces of at most
 // DENSE_V_MAX vertices, the diagonal otherwise.
+// Sliced-ELL pattern of the FEM block (rows < nv, columns < nv) from the host CSR pattern: per slice
+// of 32 rows the largest row length, entries stored column by column; map[e] = the CSR slot of entry
+// e, or -1 for padding (whose column is the row itself).
+static int build_sell(Mesh* m) {
+  const int nv = m->nv;
+  const int nslice = (nv + 31) / 32;
+  std::vector<int> ptr(nslice + 1, 0), col, map;
+  for (int sl = 0; sl < nslice; ++sl) {
+    int wd = 0;
+    for (int r = 32 * sl; r < std::min(nv, 32 * sl + 32); ++r) {
+      int c = 0;
+      for (int k = m->s_ptr_h[r]; k < m->s_ptr_h[r + 1]; ++k) c += m->s_col_h[k] < nv;
+      wd = std::max(wd, c);
+    }
+    ptr[sl + 1] = ptr[sl] + 32 * wd;
+  }
+  col.assign(ptr[nslice], 0);
+  map.assign(ptr[nslice], -1);
+  for (int sl = 0; sl < nslice; ++sl) {
+    const int wd = (ptr[sl + 1] - ptr[sl]) / 32;
+    for (int l = 0; l < 32; ++l) {
+      const int r = 32 * sl + l;
+      int j = 0;
+      if (r < nv)
+        for (int k = m->s_ptr_h[r]; k < m->s_ptr_h[r + 1]; ++k)
+          if (m->s_col_h[k] < nv) {
+            col[ptr[sl] + 32 * j + l] = m->s_col_h[k];
+            map[ptr[sl] + 32 * j + l] = k;
+            ++j;
+          }
+      for (; j < wd; ++j) col[ptr[sl] + 32 * j + l] = r < nv ? r : 0;
+    }
+  }
+  m->sell_nslice = nslice;
+  m->sell_ne = ptr[nslice];
+  PB_TRY(m->sell_ptr.upload(ptr.data(), ptr.size(), m->stream));
+  PB_TRY(m->sell_col.upload(col.data(), col.size(), m->stream));
+  PB_TRY(m->sell_map.upload(map.data(), map.size(), m->stream));
+  PB_TRY(m->sell_val.alloc(ptr[nslice]));
+  PB_CUDA(cudaStreamSynchronize(m->stream));
+  m->sell_ok = true;
+  return PBFB_OK;
+}
+
 static int prepare_block_precond(Mesh* m, bool dense) {
   m->dense_m = dense && !m->full && m->sm.nv <= DENSE_V_MAX;
   m->dense_s = dense && m->ss.nv <= DENSE_V_MAX;
@@ -563,7 +704,9 @@ static int prepare_block_precond(Mesh* m, bool dense) {
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_coop<8>, PCG_T, 0));
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, k_pcg_coop<4>, PCG_T, 0));
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_pcg_coop<2>, PCG_T, 0));
-    per = std::min({per, per4, per2});  // co-resident with every variant
+    int per1 = 0;
+    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_pcg_coop_sell, PCG_T, 0));
+    per = std::min({per, per4, per2, per1});  // co-resident with every variant
     // all resident blocks (memory-level parallelism for the SpMV phases), but no more than
     // one pass of 8 lanes per row needs
     int want = (m->tune_pcg_bps > 0 ? std::min(per, m->tune_pcg_bps) : per) * nsm;
@@ -582,6 +725,12 @@ static int prepare_block_precond(Mesh* m, bool dense) {
   }
   k_diag_inv<<<blocks_for(m->nv, 256), 256, 0, m->stream>>>(m->nv, m->s_ptr.p, m->s_col.p, m->pval.p, m->pdinv.p);
   PB_LAUNCHED(m);
+  if (m->coop_blocks > 0 && m->pcg_lanes == 1) {
+    if (!m->sell_ok) PB_TRY(build_sell(m));
+    k_sell_gather<<<blocks_for(m->sell_ne, 256), 256, 0, m->stream>>>(m->sell_ne, m->sell_map.p, m->pval.p,
+                                                                      m->sell_val.p);
+    PB_LAUNCHED(m);
+  }
   return PBFB_OK;
 }
 
@@ -660,6 +809,17 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
     const int* sc2 = m->s_col.p;
     const double* pv = m->pval.p;
     double* pw = pb + 5 * (size_t)n;
+    if (m->pcg_lanes == 1 && m->sell_ok) {
+      int nsl = m->sell_nslice;
+      const int* sp1 = m->sell_ptr.p;
+      const int* sc1 = m->sell_col.p;
+      const double* sv1 = m->sell_val.p;
+      void* args1[] = {&nvv, &nsl, &iters, &sp1, &sc1, &sv1, (void*)&vu, (void*)&dinv, &z, &pr, &pz, &pp, &pq,
+                       &pw, &part};
+      PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_coop_sell, dim3(nbc), dim3(PCG_T), args1, 0, m->stream));
+      PB_LAUNCHED(m);
+      return PBFB_OK;
+    }
     void* args[] = {&nvv, &iters, &sp, &sc2, &pv, (void*)&vu, (void*)&dinv, &z, &pr, &pz, &pp, &pq, &pw, &part};
     const void* kfn = m->pcg_lanes == 2   ? (const void*)k_pcg_coop<2>
                       : m->pcg_lanes == 4 ? (const void*)k_pcg_coop<4>

@@ -125,10 +125,11 @@ def test_dense_errors(tiny_case):
     m.close()
 
 
-@pytest.mark.parametrize("lanes", [2, 4, 8])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
 def test_inner_pcg_lane_variants(pair, lanes):
-    """Both sparse-product widths of the cooperative inner PCG give a preconditioner with which
-    flexible GMRES reaches the direct solution."""
+    """Every sparse-product form of the cooperative inner PCG (2, 4 or 8 lanes per CSR row, or one
+    lane per row of the sliced-ELL copy, ragged last slice included) gives a preconditioner with
+    which flexible GMRES reaches the direct solution."""
     from paper_2511_21713_gb300 import pbfb
     from oracle import pb
     case, m, P = pair
