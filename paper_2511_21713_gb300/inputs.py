@@ -380,7 +380,9 @@ def _gaussian_density_grid(cen, rad, spacing, pad):
 
 
 def _outermost_crossing(dirs, lo, spacing, rho, level=1.0, step=0.2, iters=40):
-    """Largest t with rho(t d) = level along each unit direction d (trilinear rho)."""
+    """Largest t with rho(t d) = level along each unit direction d (trilinear rho).  A ray that meets
+    the level set nowhere (it leaves through a gap between atoms near the centre) gets t = step;
+    the crevice closing that follows raises it to its neighbours' smoothed radius."""
     from scipy.ndimage import map_coordinates
     shape = np.array(rho.shape)
     hi = lo + spacing * (shape - 1)
@@ -399,9 +401,8 @@ def _outermost_crossing(dirs, lo, spacing, rho, level=1.0, step=0.2, iters=40):
         idx = np.nonzero(todo)[0][hit]
         t_in[idx] = t
         t -= step
-    if np.isnan(t_in).any():
-        raise ValueError("a ray from the centre does not meet the density level set")
-    a, b = t_in.copy(), t_in + step          # f(a) >= 0 > f(b)
+    t_in[np.isnan(t_in)] = step
+    a, b = t_in.copy(), t_in + step          # f(a) >= 0 > f(b) where the ray met the level set
     for _ in range(iters):
         m = 0.5 * (a + b)
         inside = f(m) >= 0
