@@ -184,7 +184,7 @@ def serving_cases(n, seed=5000):
     return cases
 
 
-def run_serving(pbfb, cases, max_inflight, budget, residual_update=0.0, precision=None):
+def run_serving(pbfb, cases, max_inflight, budget, residual_update=0.0, precision=None, detail=False):
     """Saturation run (all requests at t = 0) for capacity, then Poisson arrivals at 0.8x
     capacity; latency = arrival -> result (the request's own set-up included)."""
     import numpy as np
@@ -224,6 +224,12 @@ def run_serving(pbfb, cases, max_inflight, budget, residual_update=0.0, precisio
     lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in got])
     ok = all(r["status"] == 0 for r in res + got)
     energies = {int(r["id"]): r["total"] for r in res}
+    tri = {i: int(c.gm_tris.shape[0]) for i, c in enumerate(cases)}
+    failed = [{"id": int(r["id"]), "triangles": tri[int(r["id"])], "status": int(r["status"]),
+               "error": r["error"][:160]} for r in res + got if r["status"] != 0]
+    per_request = [{"id": int(r["id"]), "triangles": tri[int(r["id"])], "latency_ms": round(r["t_done_ms"] - r["t_submit_ms"], 1),
+                    "service_ms": round(r["t_done_ms"] - r["t_start_ms"], 1), "newton": int(r["newton_iters"]),
+                    "gmres": r["gmres"]} for r in sorted(got, key=lambda r: int(r["id"]))]
     return {"requests": len(cases), "max_inflight": max_inflight, "budget_bytes": budget,
             "saturation_solves_per_s": cap, "peak_bytes": st["peak"],
             "open_loop_rate_per_s": rate, "open_loop_solves_per_s": len(cases) / span,
@@ -231,6 +237,7 @@ def run_serving(pbfb, cases, max_inflight, budget, residual_update=0.0, precisio
             "all_ok": ok, "resident_mesh_hits": [int(st["mesh_hits"]), int(st2["mesh_hits"])],
             "precision": "fp64" if precision == pbfb.FP64 else "mixed",
             "energies_kcal_mol": [energies[i] for i in sorted(energies)],
+            "failed": failed, "per_request": per_request if detail else None,
             "workload": "sphere (1-200 charges) or double helix (8-24 bp) by a fair coin, 2000-8000 "
                         "triangles per surface (log-uniform), 0.01-1 M, eps_in 2 or 4; mixed precision, "
                         "paper tolerances; up to 16 meshes kept resident between requests"}
@@ -659,9 +666,10 @@ def run_serving_config(args):
                                         "helices": int(sum("helix" in c.name for c in cases)),
                                         "budget_bytes": args.budget_gb << 30, "max_inflight": args.concurrency,
                                         "residual_update": args.residual_update}}
-    out["mixed"] = run_serving(pbfb, cases, args.concurrency, args.budget_gb << 30, args.residual_update)
+    out["mixed"] = run_serving(pbfb, cases, args.concurrency, args.budget_gb << 30, args.residual_update,
+                               detail=True)
     small = [c for c in cases if c.gm_tris.shape[0] <= args.fp64_max_tri]
-    if small:
+    if small and args.fp64_max_tri > 0:
         out["fp64"] = run_serving(pbfb, small, args.concurrency, args.budget_gb << 30, 0.0, precision=pbfb.FP64)
         out["mixed_same_subset"] = run_serving(pbfb, small, args.concurrency, args.budget_gb << 30,
                                                args.residual_update)

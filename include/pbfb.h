@@ -119,7 +119,7 @@ typedef struct pbfb_newton_opts {
                            the surface rows the inverses of the dense float32 single-layer
                            matrices (-V_L on Gamma_m, V_Y on Gamma_s; see
                            pbfb_single_layer_dense), which keep the GMRES iteration count
-                           flat under mesh refinement.  A surface of more than 32768
+                           flat under mesh refinement.  A surface of more than 40960
                            vertices keeps the diagonal.  The inverse of V_L is built once
                            per mesh, that of V_Y once per kappa: about 2 (n/128*128)^3
                            float32 flops and 4 (n/128*128)^2 bytes of device memory per
@@ -201,7 +201,7 @@ int pbfb_mesh_create_full(const double* xyz, int32_t n_v, const int32_t* tets, i
 /* Flux lam_m on Gamma_m from the trace of u (Sec. 2.3.1, the Gamma_m limit of
  * Eq. Potential_in_Omega_m): solves V_L lam = (M_m/2 + K_L) u|Gamma_m
  * - c (l_B/eps_m) <u_coul, psi>, c = coulomb (0 or 1), by preconditioned CG on V_L (dense
- * float32 V_L^-1 as preconditioner up to 32768 vertices, else its diagonal; far field in float64
+ * float32 V_L^-1 as preconditioner up to 40960 vertices, else its diagonal; far field in float64
  * for FP64, float-float otherwise) to a relative residual of 1e-13.  x_dev: device, n float64
  * (only the u part is read); lam_dev: device, n_m float64 (may point into x_dev's lam_m part).
  * Needs pbfb_set_params, and pbfb_charges_set when coulomb = 1 (PBFB_ERR_STATE).  On a shell
@@ -316,7 +316,7 @@ int pbfb_bem_apply_noalloc(pbfb_mesh* mesh, int which, int op, const double* x_d
  * surface block of the PBFB_PRECOND_BLOCK_DENSE preconditioner).
  * out_dev: device float32, n_m or n_s rows of row stride ld_out >= that
  * count, caller-owned.  Errors: INVALID for a bad argument or a surface of
- * more than 32768 vertices, STATE before pbfb_set_params, NONFINITE when a
+ * more than 40960 vertices, STATE before pbfb_set_params, NONFINITE when a
  * pivot of the sweep is not positive (V not positive definite in float32).
  * Allocates the matrix (4 ld^2 bytes, ld = n rounded up to 128, kept with
  * the mesh) and a build scratch of at most 256 MiB, released before the call
@@ -391,7 +391,7 @@ typedef struct pbfb_tuning {
   int32_t treecode;                  /* float32 far field (GMRES operator): 1 the direct sum over
                                         all point pairs, 2 the treecode (a binary tree over the
                                         quadrature points, leaves of 256; a cluster with
-                                        r_leaf + r_cluster < 0.5 times the centre distance is
+                                        r_leaf + r_cluster < 0.6 times the centre distance is
                                         replaced by 7^3 barycentric Lagrange proxies; the
                                         hierarchical far field the paper takes for large surfaces,
                                         Sec. 3); 0 built-in: the treecode for surfaces of 65,536

@@ -13,6 +13,8 @@
 // entries in a fixed order.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "pbfb_internal.cuh"
 #include "quad_tables.cuh"
 
@@ -47,6 +49,88 @@ __device__ __forceinline__ void scheme_F(int scheme, double u, double& F, double
     Fp = 0.5 * (e + ei);
     Fpp = F;
   }
+}
+
+// exp(u) and exp(-u) on the float32 pipes (the mixed precision's sinh / cosh; GB300's float64
+// rate is 1/64 of its float32 rate).  Float-float arithmetic (pairs hi + lo of float32 values,
+// error-free sums and FMA products, Ogita, Rump & Oishi 2005), about 1e-13 relative:
+//   u = m ln2 + r, |r| <= ln2 / 2, with ln2 = L1 + L2 + L3 (L1 of 16 significant bits, so m L1 is
+//   exact for |m| <= 128 and u_hi - m L1 exact by Sterbenz' lemma);
+//   r = j / 32 + f, |f| <= 1/64;  e^{+-f} = A +- B with the even and odd parts of the series,
+//   A = 1 + f^2/2 + f^4/24 + f^6/720 and B = f (1 + f^2/6 + f^4/120 + f^6/5040) (truncation < 1e-17);
+//   e^{+-u} = 2^{+-m} e^{+-j/32} (A +- B), the e^{j/32} (|j| <= 12) from a float-float table.
+// Used for |u| <= 80 (2^m within float range); larger arguments take the float64 exp.
+struct f2 { float h, l; };
+__device__ __forceinline__ f2 f2_fast(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ f2 f2_two(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  const f2 s = f2_two(a.h, b.h);
+  return f2_fast(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+  return f2_fast(p, e);
+}
+
+constexpr int FX_J = 12;  // table of e^{j/32}, j = -12..12
+
+__device__ __forceinline__ void exp_pm(double u, const float2* __restrict__ tab, double& ep, double& em) {
+  if (!(fabs(u) <= 80.0)) {
+    ep = exp(u);
+    em = exp(-u);
+    return;
+  }
+  constexpr float L1 = 0.693145751953125f;                  // 45426 / 65536
+  constexpr float L2 = 1.42860682030941723212e-06f;         // (ln 2 - L1) rounded to float
+  constexpr double L3d = 0.69314718055994530942 - 0.693145751953125 - (double)1.42860682030941723212e-06f;
+  const float uh = (float)u, ul = (float)(u - (double)uh);
+  const float mf = rintf(__fmul_rn(uh, 1.44269504088896340736f));
+  // r = u - m (L1 + L2 + L3) in float-float
+  f2 r = f2_two(__fsub_rn(uh, __fmul_rn(mf, L1)), ul);
+  const float p2 = __fmul_rn(mf, L2), e2 = __fmaf_rn(mf, L2, -p2);
+  r = f2_add(r, f2{-p2, -e2});
+  r = f2_add(r, f2{-(float)(mf * L3d), 0.f});
+  const float jf = rintf(__fmul_rn(r.h, 32.f));
+  const f2 f = f2_two(__fsub_rn(r.h, __fmul_rn(jf, 0.03125f)), r.l);
+  const f2 s = f2_mul(f, f);
+  // A = 1 + s/2 + s^2 (1/24 + s/720)
+  const float sa = __fmul_rn(__fmul_rn(s.h, s.h), __fmaf_rn(s.h, 1.f / 720.f, 1.f / 24.f));
+  const f2 A = f2_fast(1.f, 0.f);
+  const f2 Ah = f2_add(A, f2{__fmul_rn(0.5f, s.h), __fmaf_rn(0.5f, s.l, sa)});
+  // B = f (1 + s/6 + s^2 (1/120 + s/5040))
+  const float sb = __fmul_rn(__fmul_rn(s.h, s.h), __fmaf_rn(s.h, 1.f / 5040.f, 1.f / 120.f));
+  const float s6 = __fmul_rn(s.h, 1.f / 6.f);
+  const f2 q = f2_fast(1.f, __fadd_rn(s6, __fadd_rn(__fmaf_rn(s.h, 1.f / 6.f, -s6), __fmaf_rn(s.l, 1.f / 6.f, sb))));
+  const f2 B = f2_mul(f, q);
+  const f2 Ep = f2_add(Ah, B), Em = f2_add(Ah, f2{-B.h, -B.l});
+  const int j = (int)jf + FX_J, m = (int)mf;
+  const float2 tp = tab[j], tm = tab[2 * FX_J - j];
+  const f2 Pp = f2_mul(Ep, f2{tp.x, tp.y}), Pm = f2_mul(Em, f2{tm.x, tm.y});
+  ep = ldexp((double)Pp.h + (double)Pp.l, m);
+  em = ldexp((double)Pm.h + (double)Pm.l, -m);
+}
+
+// F, F', F'' of the sinh scheme from exp_pm (the other schemes as scheme_F)
+__device__ __forceinline__ void scheme_F_fx(int scheme, double u, const float2* __restrict__ tab, double& F,
+                                            double& Fp, double& Fpp) {
+  if (scheme != PBFB_HS) {
+    scheme_F(scheme, u, F, Fp, Fpp);
+    return;
+  }
+  double ep, em;
+  exp_pm(u, tab, ep, em);
+  F = 0.5 * (ep - em);
+  Fp = 0.5 * (ep + em);
+  Fpp = F;
 }
 
 __global__ void k_tet_volumes(const double* __restrict__ xyz, int nv, const int* __restrict__ tets,
@@ -110,8 +194,10 @@ __global__ void k_gather(int nslots, const int* __restrict__ ptr, const int* __r
 }
 
 // Jacobian (10 entries, k = 0..9) and load (4 entries, k = 10..13) of F on one tet.
+template <bool FX>
 __global__ void k_element_nl(int scheme, const double* __restrict__ u, const int* __restrict__ tets, int64_t nt,
-                             const double* __restrict__ vol, double coef, double* __restrict__ loc) {
+                             const double* __restrict__ vol, double coef, const float2* __restrict__ tab,
+                             double* __restrict__ loc) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double ua[4];
@@ -122,7 +208,10 @@ __global__ void k_element_nl(int scheme, const double* __restrict__ u, const int
     double l0 = c_tet_l[q][0], l1 = c_tet_l[q][1], l2 = c_tet_l[q][2], l3 = c_tet_l[q][3];
     double uq = l0 * ua[0] + l1 * ua[1] + l2 * ua[2] + l3 * ua[3];
     double F, Fp, Fpp;
-    scheme_F(scheme, uq, F, Fp, Fpp);
+    if (FX)
+      scheme_F_fx(scheme, uq, tab, F, Fp, Fpp);
+    else
+      scheme_F(scheme, uq, F, Fp, Fpp);
     double w = c_tet_w[q];
     double f = w * F, g = w * Fp;
     double l[4] = {l0, l1, l2, l3};
@@ -170,10 +259,11 @@ __global__ void k_csr_acc(int nrows, const int* __restrict__ ptr, const int* __r
 
 // Omega batch: per tet and omega, local load of F(w), of F'(w) du and of F''(w) du^2 at
 // w = u + omega du; layout ((o * 3 + quantity) * 4 + a) * nt + t.
+template <bool FX>
 __global__ void k_omega_elements(int scheme, const double* __restrict__ u, const double* __restrict__ du,
                                  const double* __restrict__ omegas, int nomega, const int* __restrict__ tets,
                                  int64_t nt, const double* __restrict__ vol, double coef,
-                                 double* __restrict__ loc) {
+                                 const float2* __restrict__ tab, double* __restrict__ loc) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double ua[4], da[4];
@@ -191,7 +281,10 @@ __global__ void k_omega_elements(int scheme, const double* __restrict__ u, const
       double uq = l[0] * ua[0] + l[1] * ua[1] + l[2] * ua[2] + l[3] * ua[3];
       double dq = l[0] * da[0] + l[1] * da[1] + l[2] * da[2] + l[3] * da[3];
       double F, Fp, Fpp;
-      scheme_F(scheme, uq + om * dq, F, Fp, Fpp);
+      if (FX)
+        scheme_F_fx(scheme, uq + om * dq, tab, F, Fp, Fpp);
+      else
+        scheme_F(scheme, uq + om * dq, F, Fp, Fpp);
       double w = c_tet_w[q];
       double f0 = w * F, f1 = w * Fp * dq, f2 = w * Fpp * dq * dq;
       for (int a = 0; a < 4; ++a) {
@@ -339,10 +432,32 @@ int launch_gather(Mesh* m, int nslots, const int* ptr, const int* idx, const dou
   return PBFB_OK;
 }
 
+// float-float table e^{j/32}, j = -FX_J..FX_J, for exp_pm (once per mesh)
+static int fx_table(Mesh* m) {
+  if (m->fx_tab.n) return PBFB_OK;
+  float2 t[2 * FX_J + 1];
+  for (int j = -FX_J; j <= FX_J; ++j) {
+    const double v = std::exp(j / 32.0);
+    const float h = (float)v;
+    t[j + FX_J] = make_float2(h, (float)(v - (double)h));
+  }
+  return m->fx_tab.upload(t, 2 * FX_J + 1, m->stream);
+}
+
+// sinh / cosh on the float32 pipes (exp_pm) in the mixed precision, float64 exp otherwise
+static bool use_fx(const Mesh* m) { return m->precision != PBFB_FP64; }
+
 int launch_element_nl(Mesh* m, int scheme, const double* u, double coef, double* loc) {
   cudaEvent_t ev;
+  const bool fx = use_fx(m);
+  if (fx) PB_TRY(fx_table(m));
   timer_begin(m, m->t_elem, &ev);
-  k_element_nl<<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(scheme, u, m->tets.p, m->nt, m->vol.p, coef, loc);
+  if (fx)
+    k_element_nl<true><<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(scheme, u, m->tets.p, m->nt, m->vol.p, coef,
+                                                                      m->fx_tab.p, loc);
+  else
+    k_element_nl<false><<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(scheme, u, m->tets.p, m->nt, m->vol.p, coef,
+                                                                       nullptr, loc);
   PB_LAUNCHED(m);
   timer_end(m, m->t_elem, ev, (double)m->nt);
   return PBFB_OK;
@@ -378,9 +493,15 @@ int launch_csr_spmv(Mesh* m, int nrows, const int* ptr, const int* col, const do
 int launch_omega_elements(Mesh* m, int scheme, const double* u, const double* du, const double* omegas_dev,
                           int nomega, double coef, double* loc) {
   cudaEvent_t ev;
+  const bool fx = use_fx(m);
+  if (fx) PB_TRY(fx_table(m));
   timer_begin(m, m->t_elem, &ev);
-  k_omega_elements<<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(scheme, u, du, omegas_dev, nomega, m->tets.p,
-                                                                   m->nt, m->vol.p, coef, loc);
+  if (fx)
+    k_omega_elements<true><<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(
+        scheme, u, du, omegas_dev, nomega, m->tets.p, m->nt, m->vol.p, coef, m->fx_tab.p, loc);
+  else
+    k_omega_elements<false><<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(
+        scheme, u, du, omegas_dev, nomega, m->tets.p, m->nt, m->vol.p, coef, nullptr, loc);
   PB_LAUNCHED(m);
   timer_end(m, m->t_elem, ev, (double)m->nt * nomega);
   return PBFB_OK;

@@ -284,10 +284,8 @@ int build_surface(Mesh* m, Surface* s, const std::vector<int>& gtri, const std::
   PB_TRY(s->spos.alloc(s->nq));
   PB_TRY(s->sdl.alloc(s->nq));
   PB_TRY(s->s64.alloc(7 * (size_t)s->nq));
-  // far-field partial-sum buffer: enough splits for either precision's launch shape
-  // (at most ceil(nq / 512) source splits; see launch_bem_far)
-  size_t maxsplit = (size_t)(s->nq / 512 + 2);
-  PB_TRY(s->val.alloc(maxsplit * s->nq));
+  // far-field partial-sum buffer: enough source splits for every launch shape of launch_bem_far
+  PB_TRY(s->val.alloc(far_splits_max(s->nq) * (size_t)s->nq));
   return PBFB_OK;
 }
 

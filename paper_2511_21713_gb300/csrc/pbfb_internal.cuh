@@ -239,6 +239,7 @@ struct Mesh {
   bool timing = false;
   KernelClassTimer t_nbody, t_nbody64, t_nbodyff, t_spmv, t_elem, t_dense;
   DBuf<float2> ff_tab;      // float-float exp table of the Yukawa kernel
+  DBuf<float2> fx_tab;      // float-float e^{j/32} table of the element kernels' sinh / cosh
   double nbody_flops = 0.0;  // float32 far-field flops issued (18 per Laplace pair, 24 per Yukawa pair)
   double setup_ms[4] = {0, 0, 0, 0};  // mesh_create: validation, surfaces, operator pattern, device set-up
   // FEM over Omega_m and Omega_i (Sec. 2.2, Eq. fembem_matrix): `tets` holds the tets of Omega_i
@@ -262,6 +263,15 @@ struct Mesh {
     if (pcg_graph) cudaGraphExecDestroy(pcg_graph);
   }
 };
+
+// Source splits any far-field launch shape of launch_bem_far can take on nq points: at most
+// ceil(nq / 512), and at most one per target block of a 64-blocks-per-SM grid on 152 SMs (the split
+// float32 kernels have at least nq / 1024 target blocks, the float-float and float64 ones more).
+inline size_t far_splits_max(int64_t nq) {
+  const int64_t a = nq / 512 + 2;
+  const int64_t b = nq > 0 ? (int64_t)64 * 152 * 1024 / nq + 2 : 2;
+  return (size_t)(a < b ? a : b);
+}
 
 // ---- whole-solve entry points shared by the C ABI, the batch call and the server
 // region: null for a shell mesh (every tet in Omega_i, Gamma_m a boundary), else per tet 0 (Omega_m)
@@ -322,7 +332,7 @@ int launch_tree_far(Mesh* m, Surface* s, double kappa, const float4* spos, const
                     double* pairs);
 
 // ---- bem_dense.cu: dense float32 single layer of a surface and its inverse
-constexpr int DENSE_V_MAX = 32768;  // surface vertices up to which the dense inverse is used
+constexpr int DENSE_V_MAX = 40960;  // surface vertices up to which the dense inverse is used
 int dense_ld(int n);
 size_t dense_bytes(int n);        // the matrix
 size_t dense_work_bytes(int n, int nt);  // build scratch (n vertices, nt triangles)

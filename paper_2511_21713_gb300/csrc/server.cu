@@ -36,8 +36,10 @@ size_t estimate_bytes(int64_t nv, int64_t nt, int64_t ngm, int64_t ngs, int rest
   b += nnz_fem * (4 + 8 * 4 + 4 * 2);                             // CSR, values, base, a1, pval, descriptors
   for (double nqs : {6.0 * ngm, 6.0 * ngs}) {
     const double npair = nqs / 6.0 * 60.0;                        // special pairs (touching + near)
-    b += nqs * (3 * 8 + 8 + 16 + 32 + 7 * 8 + 96) + (nqs / 512 + 2) * nqs * 8;
+    b += nqs * (3 * 8 + 8 + 16 + 32 + 7 * 8 + 96) + (double)far_splits_max((int64_t)nqs) * nqs * 8;
     b += npair * (9 * 8 * 4 + 16 * 4) + 40.0 * nqs / 6.0 * (4 + 8 * 3);
+    b += nqs * 140.0 * 8;                                         // mutual float-float partial rows
+    b += nqs * 500.0;                                             // treecode: tree-order records, proxies, partials
   }
   b += (2.0 * restart + 1 + 16) * n * 8;                          // Krylov V, Z, work vectors
   // dense single-layer inverses of the block preconditioner and their build scratch

@@ -38,7 +38,7 @@ constexpr int TREE_K = TREE_P + 1;           // Chebyshev points per dimension
 constexpr int TREE_NPX = TREE_K * TREE_K * TREE_K;  // proxies per cluster (343)
 constexpr int TREE_UP_NT = 352;              // threads of the upward pass (>= TREE_NPX, whole warps)
 constexpr int TREE_TILES_PER_CHUNK = 8;      // source tiles per block
-constexpr double TREE_THETA = 0.5;           // acceptance: r_B + r_C < theta |c_B - c_C|
+constexpr double TREE_THETA = 0.6;           // acceptance: r_B + r_C < theta |c_B - c_C|
 
 // tree order: spos_t[i] = spos[perm[i]] (sources and, for positions, the targets)
 __global__ void k_tree_permute(int nq, const int* __restrict__ perm, const float4* __restrict__ spos,

@@ -58,10 +58,13 @@ def test_surface_vertex_order(pair):
 SCHEMES = {"linear": 0, "T3": 1, "HS": 2, "T5": 3, "T7": 4}
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("scheme", ["linear", "T3", "T5", "T7", "HS"])
-def test_fem_rows_and_load(pair, scheme):
+def test_fem_rows_and_load(pair, scheme, precision):
+    """FEM rows of A + J and the load N against the oracle; the mixed precision (1) takes sinh and
+    cosh from the float-float exponential on the float32 pipes, the same tolerances."""
     case, m, P = pair
-    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T)
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, precision)
     u = _u_field(P, 1)
     N_dev = dev(np.zeros(P.nv))
     m.assemble(SCHEMES[scheme], dev(u), N_dev)
@@ -169,11 +172,15 @@ def test_block_preconditioned_gmres(pair):
     assert its_b < its_j
 
 
-def test_omega_batch(pair):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_omega_batch(pair, precision):
+    """The batched omega dots against the oracle's, 1e-11 of the largest, in float64 and in the
+    mixed precision (sinh / cosh from the float-float exponential); omega 3.9 puts the sinh
+    arguments well beyond the table's central range."""
     from paper_2511_21713_gb300 import pbfb
     from oracle import pb
     case, m, P = pair
-    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T)
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, precision)
     rng = np.random.default_rng(7)
     u = _u_field(P, 8)
     du = 0.3 * rng.standard_normal(P.nv)
