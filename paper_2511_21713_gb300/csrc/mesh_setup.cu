@@ -43,77 +43,149 @@ struct HostSurface {
   std::vector<double> P;   // nt*9 corner coordinates
 };
 
-// Triangle-pair classification (ordered pairs: test t, trial s).
+// Triangle-pair classification (ordered pairs: test t, trial s): touching pairs (identical, common
+// edge, common vertex) from the vertex incidence, near pairs (no common vertex, centroid distance
+// below 2 max(h_t, h_s), h the longest edge) from a uniform grid over the centroids with cells of
+// twice the median h.  A near pair is looked for from its triangle with the larger h (ties: the
+// smaller index), within radius 2 h of that triangle, so every pair is found once whatever the
+// spread of triangle sizes; host threads over the triangles.  Each row (test t) lists its trial
+// triangles in ascending order.
 void classify_pairs(const HostSurface& hs, std::vector<int>& pt, std::vector<int>& ps, std::vector<int>& cls,
                     std::vector<int>& perm) {
   const int nt = (int)hs.tri.size() / 3;
   const int nv = (int)hs.verts.size();
-  std::vector<std::vector<int>> inc(nv);
+  std::vector<int> iptr(nv + 1, 0), inc(3 * (size_t)nt);
   for (int t = 0; t < nt; ++t)
-    for (int a = 0; a < 3; ++a) inc[hs.tri[3 * t + a]].push_back(t);
-  std::vector<double> cen(3 * nt), h(nt);
-  double hmax = 0.0;
+    for (int a = 0; a < 3; ++a) ++iptr[hs.tri[3 * t + a] + 1];
+  for (int v = 0; v < nv; ++v) iptr[v + 1] += iptr[v];
+  {
+    std::vector<int> fill(iptr.begin(), iptr.end() - 1);
+    for (int t = 0; t < nt; ++t)
+      for (int a = 0; a < 3; ++a) inc[fill[hs.tri[3 * t + a]]++] = t;
+  }
+  std::vector<double> cen(3 * (size_t)nt), h(nt);
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   for (int t = 0; t < nt; ++t) {
-    const double* P = &hs.P[9 * t];
+    const double* P = &hs.P[9 * (size_t)t];
     double hh = 0.0;
-    for (int d = 0; d < 3; ++d) cen[3 * t + d] = (P[d] + P[3 + d] + P[6 + d]) / 3.0;
+    for (int d = 0; d < 3; ++d) cen[3 * (size_t)t + d] = (P[d] + P[3 + d] + P[6 + d]) / 3.0;
     for (int k = 0; k < 3; ++k) {
       const double* A = P + 3 * k;
       const double* B = P + 3 * ((k + 1) % 3);
-      double dx = B[0] - A[0], dy = B[1] - A[1], dz = B[2] - A[2];
+      const double dx = B[0] - A[0], dy = B[1] - A[1], dz = B[2] - A[2];
       hh = std::max(hh, std::sqrt(dx * dx + dy * dy + dz * dz));
     }
     h[t] = hh;
-    hmax = std::max(hmax, hh);
     for (int d = 0; d < 3; ++d) {
-      lo[d] = std::min(lo[d], cen[3 * t + d]);
-      hi[d] = std::max(hi[d], cen[3 * t + d]);
+      lo[d] = std::min(lo[d], cen[3 * (size_t)t + d]);
+      hi[d] = std::max(hi[d], cen[3 * (size_t)t + d]);
     }
   }
-  // uniform grid of cell 2 hmax over the centroids
-  const double cell = 2.0 * hmax;
+  std::vector<double> hsort(h);
+  std::nth_element(hsort.begin(), hsort.begin() + nt / 2, hsort.end());
+  double cell = 2.0 * std::max(hsort[nt / 2], 1e-300);
   int dims[3];
-  for (int d = 0; d < 3; ++d) dims[d] = std::max(1, (int)std::floor((hi[d] - lo[d]) / cell) + 1);
-  auto cid = [&](const double* c, int* ijk) {
-    for (int d = 0; d < 3; ++d) ijk[d] = std::min(dims[d] - 1, (int)std::floor((c[d] - lo[d]) / cell));
-  };
-  std::unordered_map<int64_t, std::vector<int>> grid;
+  for (;;) {
+    int64_t cells = 1;
+    for (int d = 0; d < 3; ++d) {
+      dims[d] = std::max(1, (int)std::floor((hi[d] - lo[d]) / cell) + 1);
+      cells *= dims[d];
+    }
+    if (cells <= 8 * (int64_t)nt + 64) break;
+    cell *= 2.0;
+  }
+  const int64_t ncell = (int64_t)dims[0] * dims[1] * dims[2];
+  auto cidx = [&](double x, int d) { return std::min(dims[d] - 1, std::max(0, (int)std::floor((x - lo[d]) / cell))); };
+  std::vector<int64_t> cptr(ncell + 1, 0);
+  std::vector<int> ctri(nt), cof(nt);
   for (int t = 0; t < nt; ++t) {
-    int ijk[3];
-    cid(&cen[3 * t], ijk);
-    grid[((int64_t)ijk[0] * dims[1] + ijk[1]) * dims[2] + ijk[2]].push_back(t);
+    const double* c = &cen[3 * (size_t)t];
+    cof[t] = (int)(((int64_t)cidx(c[0], 0) * dims[1] + cidx(c[1], 1)) * dims[2] + cidx(c[2], 2));
+    ++cptr[cof[t] + 1];
+  }
+  for (int64_t k = 0; k < ncell; ++k) cptr[k + 1] += cptr[k];
+  {
+    std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int t = 0; t < nt; ++t) ctri[fill[cof[t]]++] = t;
+  }
+  // near pairs, both orientations, from per-thread buffers merged in thread (= triangle) order
+  const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::vector<int>> found(nth);
+  auto search = [&](int k) {
+    std::vector<int> stamp(nt, -1);
+    std::vector<int>& out = found[k];
+    const int t0 = (int)((int64_t)nt * k / nth), t1 = (int)((int64_t)nt * (k + 1) / nth);
+    for (int t = t0; t < t1; ++t) {
+      for (int a = 0; a < 3; ++a) {
+        const int v = hs.tri[3 * t + a];
+        for (int q = iptr[v]; q < iptr[v + 1]; ++q) stamp[inc[q]] = t;
+      }
+      const double* c = &cen[3 * (size_t)t];
+      const double r = 2.0 * h[t];
+      int a0[3], a1[3];
+      for (int d = 0; d < 3; ++d) {
+        a0[d] = cidx(c[d] - r, d);
+        a1[d] = cidx(c[d] + r, d);
+      }
+      for (int x = a0[0]; x <= a1[0]; ++x)
+        for (int y = a0[1]; y <= a1[1]; ++y)
+          for (int z = a0[2]; z <= a1[2]; ++z) {
+            const int64_t cc = ((int64_t)x * dims[1] + y) * dims[2] + z;
+            for (int64_t q = cptr[cc]; q < cptr[cc + 1]; ++q) {
+              const int u = ctri[q];
+              if (stamp[u] == t) continue;  // itself and the touching triangles
+              if (h[u] > h[t] || (h[u] == h[t] && u < t)) continue;  // found from u's side
+              const double dx = c[0] - cen[3 * (size_t)u], dy = c[1] - cen[3 * (size_t)u + 1],
+                           dz = c[2] - cen[3 * (size_t)u + 2];
+              if (dx * dx + dy * dy + dz * dz < r * r) {
+                out.push_back(t);
+                out.push_back(u);
+              }
+            }
+          }
+    }
+  };
+  {
+    std::vector<std::thread> th;
+    for (int k = 1; k < nth; ++k) th.emplace_back(search, k);
+    search(0);
+    for (auto& x : th) x.join();
+  }
+  // rows: near partners of every triangle (both orientations), counting sort by row
+  std::vector<int> nptr(nt + 1, 0);
+  for (const auto& f : found)
+    for (size_t q = 0; q < f.size(); q += 2) {
+      ++nptr[f[q] + 1];
+      ++nptr[f[q + 1] + 1];
+    }
+  for (int t = 0; t < nt; ++t) nptr[t + 1] += nptr[t];
+  std::vector<int> near(nptr[nt]);
+  {
+    std::vector<int> fill(nptr.begin(), nptr.end() - 1);
+    for (const auto& f : found)
+      for (size_t q = 0; q < f.size(); q += 2) {
+        near[fill[f[q]]++] = f[q + 1];
+        near[fill[f[q + 1]]++] = f[q];
+      }
   }
   std::vector<int> cnt(nt, 0), touched;
+  std::vector<std::array<int, 2>> row;  // (s, class)
   for (int t = 0; t < nt; ++t) {
     touched.clear();
-    for (int a = 0; a < 3; ++a)
-      for (int u : inc[hs.tri[3 * t + a]]) {
+    row.clear();
+    for (int a = 0; a < 3; ++a) {
+      const int v = hs.tri[3 * t + a];
+      for (int q = iptr[v]; q < iptr[v + 1]; ++q) {
+        const int u = inc[q];
         if (cnt[u] == 0) touched.push_back(u);
         cnt[u]++;
       }
-    std::vector<std::array<int, 2>> row;  // (s, class)
+    }
     for (int u : touched) {
-      int c = cnt[u];
+      const int c = cnt[u];
       row.push_back({u, c == 3 ? PAIR_IDENTICAL : (c == 2 ? PAIR_EDGE : PAIR_VERTEX)});
     }
-    int ijk[3];
-    cid(&cen[3 * t], ijk);
-    for (int di = -1; di <= 1; ++di)
-      for (int dj = -1; dj <= 1; ++dj)
-        for (int dk = -1; dk <= 1; ++dk) {
-          int a = ijk[0] + di, b = ijk[1] + dj, c = ijk[2] + dk;
-          if (a < 0 || b < 0 || c < 0 || a >= dims[0] || b >= dims[1] || c >= dims[2]) continue;
-          auto it = grid.find(((int64_t)a * dims[1] + b) * dims[2] + c);
-          if (it == grid.end()) continue;
-          for (int u : it->second) {
-            if (cnt[u] > 0) continue;  // touching pairs are handled above
-            double dx = cen[3 * t] - cen[3 * u], dy = cen[3 * t + 1] - cen[3 * u + 1],
-                   dz = cen[3 * t + 2] - cen[3 * u + 2];
-            double lim = 2.0 * std::max(h[t], h[u]);
-            if (dx * dx + dy * dy + dz * dz < lim * lim) row.push_back({u, PAIR_NEAR});
-          }
-        }
+    for (int q = nptr[t]; q < nptr[t + 1]; ++q) row.push_back({near[q], PAIR_NEAR});
     std::sort(row.begin(), row.end());
     for (auto& e : row) {
       int u = e[0], c = e[1];
