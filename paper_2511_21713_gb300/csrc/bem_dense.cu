@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(256) k_sweep_pivot(int ld, int k0, const float
 }
 
 // Row panel of the pivot: P = A[K, :] (old values) and U = D P with D = -S; one column per thread.
+// Only the tiles on and below the diagonal are kept current during the sweep (the matrix stays
+// symmetric), so row K beyond its diagonal tile is read from column K: A[K][j] = A[j][K].
 __global__ void __launch_bounds__(128) k_sweep_panel(int ld, int k0, const float* __restrict__ A,
                                                      const float* __restrict__ S, float* __restrict__ P,
                                                      float* __restrict__ U) {
@@ -184,12 +186,24 @@ __global__ void __launch_bounds__(128) k_sweep_panel(int ld, int k0, const float
   for (int e = threadIdx.x; e < SW_B * SW_B; e += 128) sD[e / SW_B][e % SW_B] = -S[e];
   __syncthreads();
   const int j = blockIdx.x * 128 + threadIdx.x;  // ld is a multiple of 128
+  const int kend = (k0 / SW_TILE + 1) * SW_TILE;  // end of the pivot's diagonal tile
   float pv[SW_B];
+  if (j < kend) {
 #pragma unroll
-  for (int p = 0; p < SW_B; ++p) {
-    pv[p] = A[(size_t)(k0 + p) * ld + j];
-    P[(size_t)p * ld + j] = pv[p];
+    for (int p = 0; p < SW_B; ++p) pv[p] = A[(size_t)(k0 + p) * ld + j];
+  } else {
+    const float4* col = reinterpret_cast<const float4*>(A + (size_t)j * ld + k0);
+#pragma unroll
+    for (int q = 0; q < SW_B / 4; ++q) {
+      const float4 v = col[q];
+      pv[4 * q] = v.x;
+      pv[4 * q + 1] = v.y;
+      pv[4 * q + 2] = v.z;
+      pv[4 * q + 3] = v.w;
+    }
   }
+#pragma unroll
+  for (int p = 0; p < SW_B; ++p) P[(size_t)p * ld + j] = pv[p];
   for (int p = 0; p < SW_B; ++p) {
     float acc = 0.f;
 #pragma unroll
@@ -198,7 +212,9 @@ __global__ void __launch_bounds__(128) k_sweep_panel(int ld, int k0, const float
   }
 }
 
-// Trailing update of one sweep step, 128 x 128 tiles, 8 x 8 per thread:
+// Trailing update of one sweep step, 128 x 128 tiles on and below the diagonal (tile row >= tile
+// column; the swept matrix is symmetric, the upper tiles are mirrored after the last step), 8 x 8
+// per thread:
 //   A[i][j] -= sum_p P[p][i] U[p][j]   (i, j outside K)
 //   A[K][j] = U[:, j],  A[i][K] = U[:, i]^T,  A[K][K] = S
 __global__ void __launch_bounds__(256) k_sweep_update(int ld, int k0, float* __restrict__ A,
@@ -208,7 +224,12 @@ __global__ void __launch_bounds__(256) k_sweep_update(int ld, int k0, float* __r
   float* Ps = reinterpret_cast<float*>(sm4);
   float* Us = Ps + SW_B * SW_TILE;
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.y * SW_TILE, j0 = blockIdx.x * SW_TILE;
+  // blockIdx.x = I (I + 1) / 2 + J, J <= I
+  int I = (int)((sqrtf(8.f * (float)blockIdx.x + 1.f) - 1.f) * 0.5f);
+  while ((I + 1) * (I + 2) / 2 <= (int)blockIdx.x) ++I;
+  while (I * (I + 1) / 2 > (int)blockIdx.x) --I;
+  const int J = (int)blockIdx.x - I * (I + 1) / 2;
+  const int i0 = I * SW_TILE, j0 = J * SW_TILE;
   for (int e = tid; e < SW_B * SW_TILE / 4; e += 256) {
     const int p = e / (SW_TILE / 4), c4 = e % (SW_TILE / 4);
     reinterpret_cast<float4*>(Ps)[e] = *reinterpret_cast<const float4*>(P + (size_t)p * ld + i0 + 4 * c4);
@@ -260,6 +281,22 @@ __global__ void __launch_bounds__(256) k_sweep_update(int ld, int k0, float* __r
       *dst = make_float4(v[0], v[1], v[2], v[3]);
     }
   }
+}
+
+// Upper tiles from the lower ones after the sweep: A[j][i] = A[i][j] for tile row I > tile column J,
+// through a 32 x 33 shared-memory transpose; block = one 32 x 32 sub-tile of a lower tile.
+__global__ void k_sweep_mirror(int ld, float* __restrict__ A) {
+  __shared__ float t[32][33];
+  const int nt = ld / 32;
+  const int b = blockIdx.x;  // lower sub-tiles (I > J) in row-major order
+  int I = (int)((sqrtf(8.f * (float)b + 1.f) + 1.f) * 0.5f);
+  while (I * (I - 1) / 2 > b) --I;
+  while ((I + 1) * I / 2 <= b) ++I;
+  const int J = b - I * (I - 1) / 2;
+  if (I >= nt || J >= I) return;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) t[r][threadIdx.x] = A[(size_t)(32 * I + r) * ld + 32 * J + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) A[(size_t)(32 * J + r) * ld + 32 * I + threadIdx.x] = t[threadIdx.x][r];
 }
 
 // z[i] = scale * sum_j A[i][j] v[j], i < n: one warp per row, v staged in shared memory as float
@@ -364,7 +401,8 @@ int build_dense_single_layer(Mesh* m, Surface* s, double kappa, bool invert) {
   if (invert) {
     PB_CUDA(cudaMemsetAsync(m->dflag.p, 0, sizeof(int), m->stream));
     const int smem = 2 * SW_B * SW_TILE * (int)sizeof(float);  // attribute set by init_dense_attributes
-    const dim3 gu(ld / SW_TILE, ld / SW_TILE);
+    const int ntile = ld / SW_TILE;
+    const int gu = ntile * (ntile + 1) / 2;  // tiles on and below the diagonal
     for (int k0 = 0; k0 < ld; k0 += SW_B) {
       k_sweep_pivot<<<1, 256, 0, m->stream>>>(ld, k0, A, S, m->dflag.p);
       PB_LAUNCHED(m);
@@ -373,6 +411,9 @@ int build_dense_single_layer(Mesh* m, Surface* s, double kappa, bool invert) {
       k_sweep_update<<<gu, 256, smem, m->stream>>>(ld, k0, A, P, U, S);
       PB_LAUNCHED(m);
     }
+    const int n32 = ld / 32;
+    k_sweep_mirror<<<n32 * (n32 - 1) / 2, dim3(32, 8), 0, m->stream>>>(ld, A);
+    PB_LAUNCHED(m);
     PB_CUDA(cudaMemcpyAsync(m->pinned, m->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
   }
   timer_end(m, m->t_dense, ev, invert ? 2.0 * (double)ld * ld * ld : 0.0);
