@@ -51,15 +51,13 @@ __device__ __forceinline__ void scheme_F(int scheme, double u, double& F, double
   }
 }
 
-// exp(u) and exp(-u) on the float32 pipes (the mixed precision's sinh / cosh; GB300's float64
-// rate is 1/64 of its float32 rate).  Float-float arithmetic (pairs hi + lo of float32 values,
-// error-free sums and FMA products, Ogita, Rump & Oishi 2005), about 1e-13 relative:
-//   u = m ln2 + r, |r| <= ln2 / 2, with ln2 = L1 + L2 + L3 (L1 of 16 significant bits, so m L1 is
-//   exact for |m| <= 128 and u_hi - m L1 exact by Sterbenz' lemma);
-//   r = j / 32 + f, |f| <= 1/64;  e^{+-f} = A +- B with the even and odd parts of the series,
-//   A = 1 + f^2/2 + f^4/24 + f^6/720 and B = f (1 + f^2/6 + f^4/120 + f^6/5040) (truncation < 1e-17);
-//   e^{+-u} = 2^{+-m} e^{+-j/32} (A +- B), the e^{j/32} (|j| <= 12) from a float-float table.
-// Used for |u| <= 80 (2^m within float range); larger arguments take the float64 exp.
+// ------------------------------------------------------------ float-float sinh scheme
+// The mixed precision evaluates the sinh scheme's element integrals on the float32 pipes
+// (GB300's float64 rate is 1/64 of its float32 rate) in float-float arithmetic: a value is a
+// pair hi + lo of float32 numbers with |lo| <= ulp(hi) / 2, sums by Knuth's two-sum and products
+// by the FMA two-product (Dekker 1971; Ogita, Rump & Oishi 2005), about 2^-47 relative per
+// operation.  Only the scaling by eps_s kappa^2 |T| and the conversion of the final sums to
+// float64 (in the gather kernels) use the float64 pipes.
 struct f2 { float h, l; };
 __device__ __forceinline__ f2 f2_fast(float a, float b) {  // |a| >= |b|
   const float s = __fadd_rn(a, b);
@@ -74,63 +72,94 @@ __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
   const f2 s = f2_two(a.h, b.h);
   return f2_fast(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
 }
+__device__ __forceinline__ f2 f2_neg(f2 a) { return {-a.h, -a.l}; }
 __device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
   const float p = __fmul_rn(a.h, b.h);
   float e = __fmaf_rn(a.h, b.h, -p);
   e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
   return f2_fast(p, e);
 }
+__device__ __forceinline__ f2 f2_split(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double f2_val(f2 a) { return (double)a.h + (double)a.l; }
 
-constexpr int FX_J = 12;  // table of e^{j/32}, j = -12..12
+// Constants as float-float pairs, split at compile time from their float64 values.
+#define PBFB_FF(name, x)                                 \
+  constexpr float name##_h = (float)(x);                 \
+  constexpr float name##_l = (float)((x) - (double)(float)(x))
+#define PBFB_FFV(name) (f2{name##_h, name##_l})
 
-__device__ __forceinline__ void exp_pm(double u, const float2* __restrict__ tab, double& ep, double& em) {
-  if (!(fabs(u) <= 80.0)) {
-    ep = exp(u);
-    em = exp(-u);
-    return;
-  }
-  constexpr float L1 = 0.693145751953125f;                  // 45426 / 65536
-  constexpr float L2 = 1.42860682030941723212e-06f;         // (ln 2 - L1) rounded to float
-  constexpr double L3d = 0.69314718055994530942 - 0.693145751953125 - (double)1.42860682030941723212e-06f;
-  const float uh = (float)u, ul = (float)(u - (double)uh);
-  const float mf = rintf(__fmul_rn(uh, 1.44269504088896340736f));
-  // r = u - m (L1 + L2 + L3) in float-float
-  f2 r = f2_two(__fsub_rn(uh, __fmul_rn(mf, L1)), ul);
-  const float p2 = __fmul_rn(mf, L2), e2 = __fmaf_rn(mf, L2, -p2);
-  r = f2_add(r, f2{-p2, -e2});
-  r = f2_add(r, f2{-(float)(mf * L3d), 0.f});
+// exp = 2^m e^{j/32} e^f: ln 2 = L1 + L2 + L3, L1 with 16 significant bits (m L1 exact for
+// |m| <= 128; u_hi - m L1 exact by Sterbenz' lemma), m L2 as an exact FMA two-product.
+constexpr float FX_L1 = 0.693145751953125f;
+constexpr float FX_L2 = 1.42860682030941723212e-06f;
+constexpr float FX_L3 = (float)(0.69314718055994530942 - 0.693145751953125 - (double)FX_L2);
+PBFB_FF(FX_SIXTH, 1.0 / 6.0);
+
+// Quadrature orbits of the 14-point tet rule: S31 orbits k = 1, 2 (three barycentrics alpha_k,
+// one beta_k, delta_k = beta_k - alpha_k) and the S22 orbit (two c, two d, e = d - c), with
+// u_q = alpha_k sum(u) + delta_k u_i and u_P = c sum(u) + e (u_p + u_q) for the pair P = {p, q}.
+// The element sums reduce to orbit sums (l_{q,a} l_{q,b} expanded): the products of the weights
+// with the orbit parameters below.
+PBFB_FF(OR_A1, PBFB_T_A1);
+PBFB_FF(OR_D1, PBFB_T_B1 - PBFB_T_A1);
+PBFB_FF(OR_A2, PBFB_T_A2);
+PBFB_FF(OR_D2, PBFB_T_B2 - PBFB_T_A2);
+PBFB_FF(OR_C3, PBFB_T_C3);
+PBFB_FF(OR_E3, PBFB_T_D3 - PBFB_T_C3);
+PBFB_FF(OR_WA1, PBFB_T_W1 * PBFB_T_A1);
+PBFB_FF(OR_WD1, PBFB_T_W1 * (PBFB_T_B1 - PBFB_T_A1));
+PBFB_FF(OR_WAA1, PBFB_T_W1 * PBFB_T_A1 * PBFB_T_A1);
+PBFB_FF(OR_WAD1, PBFB_T_W1 * PBFB_T_A1 * (PBFB_T_B1 - PBFB_T_A1));
+PBFB_FF(OR_WDD1, PBFB_T_W1 * (PBFB_T_B1 - PBFB_T_A1) * (PBFB_T_B1 - PBFB_T_A1));
+PBFB_FF(OR_WA2, PBFB_T_W2 * PBFB_T_A2);
+PBFB_FF(OR_WD2, PBFB_T_W2 * (PBFB_T_B2 - PBFB_T_A2));
+PBFB_FF(OR_WAA2, PBFB_T_W2 * PBFB_T_A2 * PBFB_T_A2);
+PBFB_FF(OR_WAD2, PBFB_T_W2 * PBFB_T_A2 * (PBFB_T_B2 - PBFB_T_A2));
+PBFB_FF(OR_WDD2, PBFB_T_W2 * (PBFB_T_B2 - PBFB_T_A2) * (PBFB_T_B2 - PBFB_T_A2));
+PBFB_FF(OR_WC3, PBFB_T_W3 * PBFB_T_C3);
+PBFB_FF(OR_WE3, PBFB_T_W3 * (PBFB_T_D3 - PBFB_T_C3));
+PBFB_FF(OR_WCC3, PBFB_T_W3 * PBFB_T_C3 * PBFB_T_C3);
+PBFB_FF(OR_WCE3, PBFB_T_W3 * PBFB_T_C3 * (PBFB_T_D3 - PBFB_T_C3));
+PBFB_FF(OR_WEE3, PBFB_T_W3 * (PBFB_T_D3 - PBFB_T_C3) * (PBFB_T_D3 - PBFB_T_C3));
+
+constexpr int FX_J = 12;        // tables for j = -FX_J..FX_J
+constexpr double FX_UMAX = 60.0;  // float-float path for |u| <= FX_UMAX (e^60 ~ 1.1e26)
+
+// sinh u and cosh u for |u_hi| <= FX_UMAX.  u = m ln2 + j/32 + f with |f| <= 1/64 and
+// e^{+-f} = A +- B, A = 1 + f^2/2 + f^4/24 + f^6/720, B = f (1 + f^2/6 + f^4/120 + f^6/5040)
+// (truncation below 1e-19).  With v = m ln2 + j/32: sinh u = A sinh v + B cosh v and
+// cosh u = A cosh v + B sinh v; sinh v and cosh v come from the float-float table of
+// sinh(j/32), cosh(j/32) when m = 0 (so that sinh keeps its relative accuracy near 0) and from
+// (2^m e^{j/32} -+ 2^-m e^{-j/32}) / 2 otherwise (|v| > 0.34, no cancellation).
+// tab[2 (j + FX_J)] = (e^{j/32}, e^{-j/32}), tab[2 (j + FX_J) + 1] = (sinh(j/32), cosh(j/32)).
+__device__ __forceinline__ void ff_sinh_cosh(f2 u, const float4* __restrict__ tab, f2& S, f2& C) {
+  const float mf = rintf(__fmul_rn(u.h, 1.44269504088896340736f));
+  f2 r = f2_two(__fsub_rn(u.h, __fmul_rn(mf, FX_L1)), u.l);
+  const float p2 = __fmul_rn(mf, FX_L2);
+  r = f2_add(r, f2{-p2, -__fmaf_rn(mf, FX_L2, -p2)});
+  r = f2_add(r, f2{-__fmul_rn(mf, FX_L3), 0.f});
   const float jf = rintf(__fmul_rn(r.h, 32.f));
   const f2 f = f2_two(__fsub_rn(r.h, __fmul_rn(jf, 0.03125f)), r.l);
   const f2 s = f2_mul(f, f);
-  // A = 1 + s/2 + s^2 (1/24 + s/720)
-  const float sa = __fmul_rn(__fmul_rn(s.h, s.h), __fmaf_rn(s.h, 1.f / 720.f, 1.f / 24.f));
-  const f2 A = f2_fast(1.f, 0.f);
-  const f2 Ah = f2_add(A, f2{__fmul_rn(0.5f, s.h), __fmaf_rn(0.5f, s.l, sa)});
-  // B = f (1 + s/6 + s^2 (1/120 + s/5040))
-  const float sb = __fmul_rn(__fmul_rn(s.h, s.h), __fmaf_rn(s.h, 1.f / 5040.f, 1.f / 120.f));
-  const float s6 = __fmul_rn(s.h, 1.f / 6.f);
-  const f2 q = f2_fast(1.f, __fadd_rn(s6, __fadd_rn(__fmaf_rn(s.h, 1.f / 6.f, -s6), __fmaf_rn(s.l, 1.f / 6.f, sb))));
-  const f2 B = f2_mul(f, q);
-  const f2 Ep = f2_add(Ah, B), Em = f2_add(Ah, f2{-B.h, -B.l});
-  const int j = (int)jf + FX_J, m = (int)mf;
-  const float2 tp = tab[j], tm = tab[2 * FX_J - j];
-  const f2 Pp = f2_mul(Ep, f2{tp.x, tp.y}), Pm = f2_mul(Em, f2{tm.x, tm.y});
-  ep = ldexp((double)Pp.h + (double)Pp.l, m);
-  em = ldexp((double)Pm.h + (double)Pm.l, -m);
-}
-
-// F, F', F'' of the sinh scheme from exp_pm (the other schemes as scheme_F)
-__device__ __forceinline__ void scheme_F_fx(int scheme, double u, const float2* __restrict__ tab, double& F,
-                                            double& Fp, double& Fpp) {
-  if (scheme != PBFB_HS) {
-    scheme_F(scheme, u, F, Fp, Fpp);
-    return;
-  }
-  double ep, em;
-  exp_pm(u, tab, ep, em);
-  F = 0.5 * (ep - em);
-  Fp = 0.5 * (ep + em);
-  Fpp = F;
+  const float s2 = __fmul_rn(s.h, s.h);
+  const float sa = __fmul_rn(s2, __fmaf_rn(s.h, 1.f / 720.f, 1.f / 24.f));
+  const f2 A = f2_add(f2{1.f, 0.f}, f2{__fmul_rn(0.5f, s.h), __fmaf_rn(0.5f, s.l, sa)});
+  const float sb = __fmul_rn(s2, __fmaf_rn(s.h, 1.f / 5040.f, 1.f / 120.f));
+  const f2 s6 = f2_mul(s, PBFB_FFV(FX_SIXTH));
+  const f2 B = f2_mul(f, f2_add(f2{1.f, 0.f}, f2{s6.h, __fadd_rn(s6.l, sb)}));
+  const int jt = 2 * ((int)jf + FX_J);
+  const float4 te = __ldg(&tab[jt]), th = __ldg(&tab[jt + 1]);
+  const int m = (int)mf;
+  const float sp = __int_as_float((126 + m) << 23), sm = __int_as_float((126 - m) << 23);  // 2^(m-1), 2^(-m-1)
+  const f2 P{__fmul_rn(te.x, sp), __fmul_rn(te.y, sp)}, Q{__fmul_rn(te.z, sm), __fmul_rn(te.w, sm)};
+  const bool z = m == 0;
+  const f2 sv = z ? f2{th.x, th.y} : f2_add(P, f2_neg(Q));
+  const f2 cv = z ? f2{th.z, th.w} : f2_add(P, Q);
+  S = f2_add(f2_mul(A, sv), f2_mul(B, cv));
+  C = f2_add(f2_mul(A, cv), f2_mul(B, sv));
 }
 
 __global__ void k_tet_volumes(const double* __restrict__ xyz, int nv, const int* __restrict__ tets,
@@ -183,6 +212,47 @@ __global__ void k_stiffness_local(const double* __restrict__ xyz, int nv, const 
       loc[(int64_t)sym10(a, b) * nt + t] = V * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
 }
 
+// Jacobian (10 entries, k = 0..9) and load (4 entries) of F on one tet in float64.
+__device__ __forceinline__ void element_sums_f64(int scheme, const double (&ua)[4], double (&J)[10],
+                                                 double (&N)[4]) {
+  for (int k = 0; k < 10; ++k) J[k] = 0.0;
+  for (int a = 0; a < 4; ++a) N[a] = 0.0;
+  for (int q = 0; q < QT; ++q) {
+    double l0 = c_tet_l[q][0], l1 = c_tet_l[q][1], l2 = c_tet_l[q][2], l3 = c_tet_l[q][3];
+    double uq = l0 * ua[0] + l1 * ua[1] + l2 * ua[2] + l3 * ua[3];
+    double F, Fp, Fpp;
+    scheme_F(scheme, uq, F, Fp, Fpp);
+    double w = c_tet_w[q];
+    double f = w * F, g = w * Fp;
+    double l[4] = {l0, l1, l2, l3};
+    for (int a = 0; a < 4; ++a) {
+      N[a] += f * l[a];
+      double gl = g * l[a];
+      for (int b = a; b < 4; ++b) J[sym10(a, b)] += gl * l[b];
+    }
+  }
+}
+
+// The omega batch's three loads of one tet for one omega in float64.
+__device__ __forceinline__ void omega_sums_f64(int scheme, const double (&ua)[4], const double (&da)[4], double om,
+                                               double (&R0)[4], double (&R1)[4], double (&R2)[4]) {
+  for (int a = 0; a < 4; ++a) R0[a] = R1[a] = R2[a] = 0.0;
+  for (int q = 0; q < QT; ++q) {
+    double l[4] = {c_tet_l[q][0], c_tet_l[q][1], c_tet_l[q][2], c_tet_l[q][3]};
+    double uq = l[0] * ua[0] + l[1] * ua[1] + l[2] * ua[2] + l[3] * ua[3];
+    double dq = l[0] * da[0] + l[1] * da[1] + l[2] * da[2] + l[3] * da[3];
+    double F, Fp, Fpp;
+    scheme_F(scheme, uq + om * dq, F, Fp, Fpp);
+    double w = c_tet_w[q];
+    double f0 = w * F, f1 = w * Fp * dq, f2 = w * Fpp * dq * dq;
+    for (int a = 0; a < 4; ++a) {
+      R0[a] += f0 * l[a];
+      R1[a] += f1 * l[a];
+      R2[a] += f2 * l[a];
+    }
+  }
+}
+
 __global__ void k_gather(int nslots, const int* __restrict__ ptr, const int* __restrict__ idx,
                          const double* __restrict__ local, const double* __restrict__ base, double scale,
                          double* __restrict__ out) {
@@ -193,37 +263,140 @@ __global__ void k_gather(int nslots, const int* __restrict__ ptr, const int* __r
   out[s] = (base ? base[s] : 0.0) + scale * acc;
 }
 
-// Jacobian (10 entries, k = 0..9) and load (4 entries, k = 10..13) of F on one tet.
-template <bool FX>
+// The same over float-float tet-local entries (the float-float element kernels' output):
+// the sum in float-float, one conversion to float64 per slot.
+__global__ void k_gather_ff(int nslots, const int* __restrict__ ptr, const int* __restrict__ idx,
+                            const float2* __restrict__ local, const double* __restrict__ base, double scale,
+                            double* __restrict__ out) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nslots) return;
+  f2 acc{0.f, 0.f};
+  for (int k = ptr[s]; k < ptr[s + 1]; ++k) {
+    const float2 x = local[idx[k]];
+    acc = f2_add(acc, f2{x.x, x.y});
+  }
+  out[s] = (base ? base[s] : 0.0) + scale * f2_val(acc);
+}
+
+__device__ __forceinline__ float2 f2_store(f2 a) { return make_float2(a.h, a.l); }
+
+// Jacobian and load of F on one tet (layout k * nt + t: J at k = 0..9, N at k = 10..13).
 __global__ void k_element_nl(int scheme, const double* __restrict__ u, const int* __restrict__ tets, int64_t nt,
-                             const double* __restrict__ vol, double coef, const float2* __restrict__ tab,
-                             double* __restrict__ loc) {
+                             const double* __restrict__ vol, double coef, double* __restrict__ loc) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double ua[4];
   for (int a = 0; a < 4; ++a) ua[a] = u[tets[a * nt + t]];
-  double J[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double N[4] = {0, 0, 0, 0};
-  for (int q = 0; q < QT; ++q) {
-    double l0 = c_tet_l[q][0], l1 = c_tet_l[q][1], l2 = c_tet_l[q][2], l3 = c_tet_l[q][3];
-    double uq = l0 * ua[0] + l1 * ua[1] + l2 * ua[2] + l3 * ua[3];
-    double F, Fp, Fpp;
-    if (FX)
-      scheme_F_fx(scheme, uq, tab, F, Fp, Fpp);
-    else
-      scheme_F(scheme, uq, F, Fp, Fpp);
-    double w = c_tet_w[q];
-    double f = w * F, g = w * Fp;
-    double l[4] = {l0, l1, l2, l3};
-    for (int a = 0; a < 4; ++a) {
-      N[a] += f * l[a];
-      double gl = g * l[a];
-      for (int b = a; b < 4; ++b) J[sym10(a, b)] += gl * l[b];
-    }
-  }
+  double J[10], N[4];
+  element_sums_f64(scheme, ua, J, N);
   double s = coef * vol[t];
   for (int k = 0; k < 10; ++k) loc[k * nt + t] = s * J[k];
   for (int a = 0; a < 4; ++a) loc[(10 + a) * nt + t] = s * N[a];
+}
+
+// Tets outside the float-float range take the float64 sums (kept out of line).
+__device__ __noinline__ void element_hs_fallback(const double* ua4, double sc, int64_t nt, int64_t t,
+                                                 float2* __restrict__ loc) {
+  const double ua[4] = {ua4[0], ua4[1], ua4[2], ua4[3]};
+  double J[10], N[4];
+  element_sums_f64(PBFB_HS, ua, J, N);
+  for (int k = 0; k < 10; ++k) loc[k * nt + t] = f2_store(f2_split(sc * J[k]));
+  for (int a = 0; a < 4; ++a) loc[(10 + a) * nt + t] = f2_store(f2_split(sc * N[a]));
+}
+
+// Sinh-scheme Jacobian and load of one tet in float-float, from the orbit sums:
+//   N_a  = sum_k W_k (alpha_k FS_k + delta_k f_{k,a}) + W_3 (c FS_3 + e sum_{P ∋ a} f_P)
+//   J_ab = C + h_a + h_b + [a != b] W_3 e^2 g_{ab},  J_aa = C + 2 h_a + D_a
+// with f = sinh, g = cosh at the points, FS / GS the orbit sums, C = sum W alpha^2 GS,
+// h_a = sum W alpha delta g_{k,a} (+ W_3 c e sum_{P ∋ a} g_P), D_a = sum W delta^2 g_{k,a}
+// (+ W_3 e^2 sum_{P ∋ a} g_P): the 14-point sums of w F l_a and w F' l_a l_b regrouped.
+__global__ void __launch_bounds__(128) k_element_hs_ff(const double* __restrict__ u, const int* __restrict__ tets,
+                                                       int64_t nt, const double* __restrict__ vol, double coef,
+                                                       const float4* __restrict__ tab, float2* __restrict__ loc) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double ua[4];
+  double umax = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    ua[a] = u[tets[a * nt + t]];
+    umax = fmax(umax, fabs(ua[a]));
+  }
+  const double sc = coef * vol[t];
+  if (!(umax <= FX_UMAX && fabs(sc) <= 1e10)) {  // |u_q| <= max |u_a| (convex combination)
+    element_hs_fallback(ua, sc, nt, t, loc);
+    return;
+  }
+  f2 v[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) v[a] = f2_split(ua[a]);
+  const f2 su = f2_add(f2_add(v[0], v[1]), f2_add(v[2], v[3]));
+  f2 n[4], h[4], D[4], g3[6], T, C;
+  {  // S31 orbit 1
+    const f2 as = f2_mul(su, PBFB_FFV(OR_A1));
+    f2 fs, gs;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f2 F, G;
+      ff_sinh_cosh(f2_add(as, f2_mul(v[i], PBFB_FFV(OR_D1))), tab, F, G);
+      n[i] = f2_mul(F, PBFB_FFV(OR_WD1));
+      h[i] = f2_mul(G, PBFB_FFV(OR_WAD1));
+      D[i] = f2_mul(G, PBFB_FFV(OR_WDD1));
+      fs = i ? f2_add(fs, F) : F;
+      gs = i ? f2_add(gs, G) : G;
+    }
+    T = f2_mul(fs, PBFB_FFV(OR_WA1));
+    C = f2_mul(gs, PBFB_FFV(OR_WAA1));
+  }
+  {  // S31 orbit 2
+    const f2 as = f2_mul(su, PBFB_FFV(OR_A2));
+    f2 fs, gs;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f2 F, G;
+      ff_sinh_cosh(f2_add(as, f2_mul(v[i], PBFB_FFV(OR_D2))), tab, F, G);
+      n[i] = f2_add(n[i], f2_mul(F, PBFB_FFV(OR_WD2)));
+      h[i] = f2_add(h[i], f2_mul(G, PBFB_FFV(OR_WAD2)));
+      D[i] = f2_add(D[i], f2_mul(G, PBFB_FFV(OR_WDD2)));
+      fs = i ? f2_add(fs, F) : F;
+      gs = i ? f2_add(gs, G) : G;
+    }
+    T = f2_add(T, f2_mul(fs, PBFB_FFV(OR_WA2)));
+    C = f2_add(C, f2_mul(gs, PBFB_FFV(OR_WAA2)));
+  }
+  {  // S22 orbit: pairs (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
+    const f2 cs = f2_mul(su, PBFB_FFV(OR_C3));
+    f2 fs, gs;
+#pragma unroll
+    for (int p = 0, P = 0; p < 3; ++p)
+#pragma unroll
+      for (int q = p + 1; q < 4; ++q, ++P) {
+        f2 F, G;
+        ff_sinh_cosh(f2_add(cs, f2_mul(f2_add(v[p], v[q]), PBFB_FFV(OR_E3))), tab, F, G);
+        const f2 fn = f2_mul(F, PBFB_FFV(OR_WE3)), gh = f2_mul(G, PBFB_FFV(OR_WCE3));
+        const f2 gd = f2_mul(G, PBFB_FFV(OR_WEE3));
+        n[p] = f2_add(n[p], fn);
+        n[q] = f2_add(n[q], fn);
+        h[p] = f2_add(h[p], gh);
+        h[q] = f2_add(h[q], gh);
+        D[p] = f2_add(D[p], gd);
+        D[q] = f2_add(D[q], gd);
+        g3[P] = gd;
+        fs = P ? f2_add(fs, F) : F;
+        gs = P ? f2_add(gs, G) : G;
+      }
+    T = f2_add(T, f2_mul(fs, PBFB_FFV(OR_WC3)));
+    C = f2_add(C, f2_mul(gs, PBFB_FFV(OR_WCC3)));
+  }
+  const f2 s = f2_split(sc);
+#pragma unroll
+  for (int a = 0, P = 0; a < 4; ++a) {
+    loc[sym10(a, a) * nt + t] = f2_store(f2_mul(s, f2_add(f2_add(C, D[a]), f2{2.f * h[a].h, 2.f * h[a].l})));
+#pragma unroll
+    for (int b = a + 1; b < 4; ++b, ++P)
+      loc[sym10(a, b) * nt + t] = f2_store(f2_mul(s, f2_add(f2_add(C, g3[P]), f2_add(h[a], h[b]))));
+    loc[(10 + a) * nt + t] = f2_store(f2_mul(s, f2_add(T, n[a])));
+  }
 }
 
 // Sparse part of the coupled operator: y = S x, L lanes per row (L = 4, 8 or 16).
@@ -259,11 +432,9 @@ __global__ void k_csr_acc(int nrows, const int* __restrict__ ptr, const int* __r
 
 // Omega batch: per tet and omega, local load of F(w), of F'(w) du and of F''(w) du^2 at
 // w = u + omega du; layout ((o * 3 + quantity) * 4 + a) * nt + t.
-template <bool FX>
 __global__ void k_omega_elements(int scheme, const double* __restrict__ u, const double* __restrict__ du,
                                  const double* __restrict__ omegas, int nomega, const int* __restrict__ tets,
-                                 int64_t nt, const double* __restrict__ vol, double coef,
-                                 const float2* __restrict__ tab, double* __restrict__ loc) {
+                                 int64_t nt, const double* __restrict__ vol, double coef, double* __restrict__ loc) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double ua[4], da[4];
@@ -274,31 +445,125 @@ __global__ void k_omega_elements(int scheme, const double* __restrict__ u, const
   }
   double s = coef * vol[t];
   for (int o = 0; o < nomega; ++o) {
-    double om = omegas[o];
-    double R0[4] = {0, 0, 0, 0}, R1[4] = {0, 0, 0, 0}, R2[4] = {0, 0, 0, 0};
-    for (int q = 0; q < QT; ++q) {
-      double l[4] = {c_tet_l[q][0], c_tet_l[q][1], c_tet_l[q][2], c_tet_l[q][3]};
-      double uq = l[0] * ua[0] + l[1] * ua[1] + l[2] * ua[2] + l[3] * ua[3];
-      double dq = l[0] * da[0] + l[1] * da[1] + l[2] * da[2] + l[3] * da[3];
-      double F, Fp, Fpp;
-      if (FX)
-        scheme_F_fx(scheme, uq + om * dq, tab, F, Fp, Fpp);
-      else
-        scheme_F(scheme, uq + om * dq, F, Fp, Fpp);
-      double w = c_tet_w[q];
-      double f0 = w * F, f1 = w * Fp * dq, f2 = w * Fpp * dq * dq;
-      for (int a = 0; a < 4; ++a) {
-        R0[a] += f0 * l[a];
-        R1[a] += f1 * l[a];
-        R2[a] += f2 * l[a];
-      }
-    }
+    double R0[4], R1[4], R2[4];
+    omega_sums_f64(scheme, ua, da, omegas[o], R0, R1, R2);
     int64_t base = (int64_t)o * 12 * nt;
     for (int a = 0; a < 4; ++a) {
       loc[base + (0 * 4 + a) * nt + t] = s * R0[a];
       loc[base + (1 * 4 + a) * nt + t] = s * R1[a];
       loc[base + (2 * 4 + a) * nt + t] = s * R2[a];
     }
+  }
+}
+
+// Out-of-range omegas of a tet take the float64 loads (kept out of line).
+__device__ __noinline__ void omega_hs_fallback(const double* ua4, const double* da4, double om, double sc,
+                                               int64_t nt, int64_t t, float2* __restrict__ loc) {
+  const double ua[4] = {ua4[0], ua4[1], ua4[2], ua4[3]}, da[4] = {da4[0], da4[1], da4[2], da4[3]};
+  double R0[4], R1[4], R2[4];
+  omega_sums_f64(PBFB_HS, ua, da, om, R0, R1, R2);
+  for (int a = 0; a < 4; ++a) {
+    loc[(0 * 4 + a) * nt + t] = f2_store(f2_split(sc * R0[a]));
+    loc[(1 * 4 + a) * nt + t] = f2_store(f2_split(sc * R1[a]));
+    loc[(2 * 4 + a) * nt + t] = f2_store(f2_split(sc * R2[a]));
+  }
+}
+
+// Orbit-sum accumulator of one load sum_q W_q x_q l_{q,a} = T + n_a (see k_element_hs_ff).
+struct OrbitLoad {
+  f2 T, n[4], s;
+};
+
+// Omega batch of the sinh scheme in float-float: per tet and omega the loads of F(w), F'(w) d
+// and F''(w) d^2 at w = u + omega du (F'' = F = sinh); same layout as k_omega_elements.
+__global__ void __launch_bounds__(128) k_omega_hs_ff(const double* __restrict__ u, const double* __restrict__ du,
+                                                     const double* __restrict__ omegas, int nomega,
+                                                     const int* __restrict__ tets, int64_t nt,
+                                                     const double* __restrict__ vol, double coef,
+                                                     const float4* __restrict__ tab, float2* __restrict__ loc) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double ua[4], da[4], dmax = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int vtx = tets[a * nt + t];
+    ua[a] = u[vtx];
+    da[a] = du[vtx];
+    dmax = fmax(dmax, fabs(da[a]));
+  }
+  const double sc = coef * vol[t];
+  const bool scale_ok = fabs(sc) * (1.0 + dmax) * (1.0 + dmax) <= 1e10;
+  f2 d[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) d[a] = f2_split(da[a]);
+  const f2 sd = f2_add(f2_add(d[0], d[1]), f2_add(d[2], d[3]));
+  const f2 s = f2_split(sc);
+  for (int o = 0; o < nomega; ++o) {
+    const double om = omegas[o];
+    float2* out = loc + (int64_t)o * 12 * nt;
+    double wmax = 0.0;
+    f2 w[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const double wa = fma(om, da[a], ua[a]);
+      wmax = fmax(wmax, fabs(wa));
+      w[a] = f2_split(wa);
+    }
+    if (!(wmax <= FX_UMAX && scale_ok)) {
+      omega_hs_fallback(ua, da, om, sc, nt, t, out);
+      continue;
+    }
+    const f2 sw = f2_add(f2_add(w[0], w[1]), f2_add(w[2], w[3]));
+    OrbitLoad L[3];
+    // one point: x = (sinh, cosh d, sinh d^2); an S31 point adds x W delta to n_i, an S22 point
+    // x W e to n_p and n_q; the orbit sums s enter T with W alpha (W c)
+    auto point = [&](f2 wq, f2 dq, bool init_n, bool init_s, int i, int j, f2 wn) {
+      f2 F, G;
+      ff_sinh_cosh(wq, tab, F, G);
+      const f2 fd = f2_mul(F, dq);
+      const f2 x[3] = {F, f2_mul(G, dq), f2_mul(fd, dq)};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const f2 m = f2_mul(x[k], wn);
+        L[k].n[i] = init_n ? m : f2_add(L[k].n[i], m);
+        if (j >= 0) L[k].n[j] = f2_add(L[k].n[j], m);
+        L[k].s = init_s ? x[k] : f2_add(L[k].s, x[k]);
+      }
+    };
+    {  // S31 orbit 1 (initialises the accumulators)
+      const f2 aw = f2_mul(sw, PBFB_FFV(OR_A1)), ad = f2_mul(sd, PBFB_FFV(OR_A1));
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        point(f2_add(aw, f2_mul(w[i], PBFB_FFV(OR_D1))), f2_add(ad, f2_mul(d[i], PBFB_FFV(OR_D1))), true, i == 0, i,
+              -1, PBFB_FFV(OR_WD1));
+#pragma unroll
+      for (int k = 0; k < 3; ++k) L[k].T = f2_mul(L[k].s, PBFB_FFV(OR_WA1));
+    }
+    {  // S31 orbit 2
+      const f2 aw = f2_mul(sw, PBFB_FFV(OR_A2)), ad = f2_mul(sd, PBFB_FFV(OR_A2));
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        point(f2_add(aw, f2_mul(w[i], PBFB_FFV(OR_D2))), f2_add(ad, f2_mul(d[i], PBFB_FFV(OR_D2))), false, i == 0, i,
+              -1, PBFB_FFV(OR_WD2));
+#pragma unroll
+      for (int k = 0; k < 3; ++k) L[k].T = f2_add(L[k].T, f2_mul(L[k].s, PBFB_FFV(OR_WA2)));
+    }
+    {  // S22 orbit
+      const f2 cw = f2_mul(sw, PBFB_FFV(OR_C3)), cd = f2_mul(sd, PBFB_FFV(OR_C3));
+#pragma unroll
+      for (int p = 0, P = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = p + 1; q < 4; ++q, ++P)
+          point(f2_add(cw, f2_mul(f2_add(w[p], w[q]), PBFB_FFV(OR_E3))),
+                f2_add(cd, f2_mul(f2_add(d[p], d[q]), PBFB_FFV(OR_E3))), false, P == 0, p, q,
+                PBFB_FFV(OR_WE3));
+#pragma unroll
+      for (int k = 0; k < 3; ++k) L[k].T = f2_add(L[k].T, f2_mul(L[k].s, PBFB_FFV(OR_WC3)));
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) out[(k * 4 + a) * nt + t] = f2_store(f2_mul(s, f2_add(L[k].T, L[k].n[a])));
   }
 }
 
@@ -323,21 +588,38 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* out)
 }
 
 // Per vertex: gather N(w), J(w) du, N''(w)[du,du] for one omega and accumulate the
-// seven FEM-row dot products; one partial row of 7 per block.
+// seven FEM-row dot products; one partial row of 7 per block.  FF: the tet-local entries are
+// float-float pairs (summed in float-float, converted once per vertex).
+template <bool FF>
 __global__ void __launch_bounds__(RED_T) k_omega_dots(int nv, const int* __restrict__ ptr, const int* __restrict__ idx,
                                                       const double* __restrict__ loc, int64_t nt,
                                                       const double* __restrict__ c, const double* __restrict__ p,
                                                       double* __restrict__ part) {
   int o = blockIdx.y;
   const double* L = loc + (int64_t)o * 12 * nt;
+  const float2* L2 = reinterpret_cast<const float2*>(L);
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int i = blockIdx.x * RED_T + threadIdx.x; i < nv; i += gridDim.x * RED_T) {
     double n0 = 0, n1 = 0, n2 = 0;
-    for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
-      int e = idx[k];
-      n0 += L[e];
-      n1 += L[4 * nt + e];
-      n2 += L[8 * nt + e];
+    if (FF) {
+      f2 a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f};
+      for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const int e = idx[k];
+        const float2 x0 = L2[e], x1 = L2[4 * nt + e], x2 = L2[8 * nt + e];
+        a0 = f2_add(a0, f2{x0.x, x0.y});
+        a1 = f2_add(a1, f2{x1.x, x1.y});
+        a2 = f2_add(a2, f2{x2.x, x2.y});
+      }
+      n0 = f2_val(a0);
+      n1 = f2_val(a1);
+      n2 = f2_val(a2);
+    } else {
+      for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+        int e = idx[k];
+        n0 += L[e];
+        n1 += L[4 * nt + e];
+        n2 += L[8 * nt + e];
+      }
     }
     double r = c[i] - n0, rp = -n1, rpp = -n2, pi = p[i];
     acc[0] += pi * r;     // p.r
@@ -425,39 +707,51 @@ int launch_stiffness_local(Mesh* m, const int* tets, int64_t nt, const double* v
 }
 
 int launch_gather(Mesh* m, int nslots, const int* ptr, const int* idx, const double* local, const double* base,
-                  double scale, double* out) {
+                  double scale, double* out, bool ff) {
   if (nslots == 0) return PBFB_OK;
-  k_gather<<<blocks_for(nslots, 256), 256, 0, m->stream>>>(nslots, ptr, idx, local, base, scale, out);
+  if (ff)
+    k_gather_ff<<<blocks_for(nslots, 256), 256, 0, m->stream>>>(
+        nslots, ptr, idx, reinterpret_cast<const float2*>(local), base, scale, out);
+  else
+    k_gather<<<blocks_for(nslots, 256), 256, 0, m->stream>>>(nslots, ptr, idx, local, base, scale, out);
   PB_LAUNCHED(m);
   return PBFB_OK;
 }
 
-// float-float table e^{j/32}, j = -FX_J..FX_J, for exp_pm (once per mesh)
+// float-float tables of exp(+-j/32) and sinh / cosh(j/32), j = -FX_J..FX_J (once per mesh)
 static int fx_table(Mesh* m) {
   if (m->fx_tab.n) return PBFB_OK;
-  float2 t[2 * FX_J + 1];
+  float4 t[2 * (2 * FX_J + 1)];
+  auto split = [](double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+  };
   for (int j = -FX_J; j <= FX_J; ++j) {
-    const double v = std::exp(j / 32.0);
-    const float h = (float)v;
-    t[j + FX_J] = make_float2(h, (float)(v - (double)h));
+    float4 e, c;
+    split(std::exp(j / 32.0), e.x, e.y);
+    split(std::exp(-j / 32.0), e.z, e.w);
+    split(std::sinh(j / 32.0), c.x, c.y);
+    split(std::cosh(j / 32.0), c.z, c.w);
+    t[2 * (j + FX_J)] = e;
+    t[2 * (j + FX_J) + 1] = c;
   }
-  return m->fx_tab.upload(t, 2 * FX_J + 1, m->stream);
+  return m->fx_tab.upload(t, 2 * (2 * FX_J + 1), m->stream);
 }
 
-// sinh / cosh on the float32 pipes (exp_pm) in the mixed precision, float64 exp otherwise
-static bool use_fx(const Mesh* m) { return m->precision != PBFB_FP64; }
+// The sinh scheme runs in float-float in the mixed precision; the other schemes (first
+// iterations) and the float64 precision run in float64.
+static bool use_ff(const Mesh* m, int scheme) { return m->precision != PBFB_FP64 && scheme == PBFB_HS; }
 
-int launch_element_nl(Mesh* m, int scheme, const double* u, double coef, double* loc) {
+int launch_element_nl(Mesh* m, int scheme, const double* u, double coef, double* loc, bool* ff) {
   cudaEvent_t ev;
-  const bool fx = use_fx(m);
-  if (fx) PB_TRY(fx_table(m));
+  *ff = use_ff(m, scheme);
+  if (*ff) PB_TRY(fx_table(m));
   timer_begin(m, m->t_elem, &ev);
-  if (fx)
-    k_element_nl<true><<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(scheme, u, m->tets.p, m->nt, m->vol.p, coef,
-                                                                      m->fx_tab.p, loc);
+  if (*ff)
+    k_element_hs_ff<<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(u, m->tets.p, m->nt, m->vol.p, coef,
+                                                                   m->fx_tab.p, reinterpret_cast<float2*>(loc));
   else
-    k_element_nl<false><<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(scheme, u, m->tets.p, m->nt, m->vol.p, coef,
-                                                                       nullptr, loc);
+    k_element_nl<<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(scheme, u, m->tets.p, m->nt, m->vol.p, coef, loc);
   PB_LAUNCHED(m);
   timer_end(m, m->t_elem, ev, (double)m->nt);
   return PBFB_OK;
@@ -491,26 +785,31 @@ int launch_csr_spmv(Mesh* m, int nrows, const int* ptr, const int* col, const do
 }
 
 int launch_omega_elements(Mesh* m, int scheme, const double* u, const double* du, const double* omegas_dev,
-                          int nomega, double coef, double* loc) {
+                          int nomega, double coef, double* loc, bool* ff) {
   cudaEvent_t ev;
-  const bool fx = use_fx(m);
-  if (fx) PB_TRY(fx_table(m));
+  *ff = use_ff(m, scheme);
+  if (*ff) PB_TRY(fx_table(m));
   timer_begin(m, m->t_elem, &ev);
-  if (fx)
-    k_omega_elements<true><<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(
-        scheme, u, du, omegas_dev, nomega, m->tets.p, m->nt, m->vol.p, coef, m->fx_tab.p, loc);
+  if (*ff)
+    k_omega_hs_ff<<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(u, du, omegas_dev, nomega, m->tets.p, m->nt,
+                                                                 m->vol.p, coef, m->fx_tab.p,
+                                                                 reinterpret_cast<float2*>(loc));
   else
-    k_omega_elements<false><<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(
-        scheme, u, du, omegas_dev, nomega, m->tets.p, m->nt, m->vol.p, coef, nullptr, loc);
+    k_omega_elements<<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(scheme, u, du, omegas_dev, nomega, m->tets.p,
+                                                                    m->nt, m->vol.p, coef, loc);
   PB_LAUNCHED(m);
   timer_end(m, m->t_elem, ev, (double)m->nt * nomega);
   return PBFB_OK;
 }
 
-int launch_omega_dots(Mesh* m, int nomega, const double* loc, const double* c, const double* p, double* dots_dev) {
+int launch_omega_dots(Mesh* m, int nomega, const double* loc, const double* c, const double* p, double* dots_dev,
+                      bool ff) {
   int nb = 152;
   dim3 grid(nb, nomega);
-  k_omega_dots<<<grid, RED_T, 0, m->stream>>>(m->nv, m->ng_ptr.p, m->ng_idx.p, loc, m->nt, c, p, m->red.p);
+  if (ff)
+    k_omega_dots<true><<<grid, RED_T, 0, m->stream>>>(m->nv, m->ng_ptr.p, m->ng_idx.p, loc, m->nt, c, p, m->red.p);
+  else
+    k_omega_dots<false><<<grid, RED_T, 0, m->stream>>>(m->nv, m->ng_ptr.p, m->ng_idx.p, loc, m->nt, c, p, m->red.p);
   PB_LAUNCHED(m);
   k_sum_partials<<<nomega, 32, 0, m->stream>>>(m->red.p, nb, 7, dots_dev);
   PB_LAUNCHED(m);

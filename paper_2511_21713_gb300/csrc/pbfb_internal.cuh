@@ -239,7 +239,7 @@ struct Mesh {
   bool timing = false;
   KernelClassTimer t_nbody, t_nbody64, t_nbodyff, t_spmv, t_elem, t_dense;
   DBuf<float2> ff_tab;      // float-float exp table of the Yukawa kernel
-  DBuf<float2> fx_tab;      // float-float e^{j/32} table of the element kernels' sinh / cosh
+  DBuf<float4> fx_tab;      // float-float exp / sinh / cosh (j/32) tables of the element kernels
   double nbody_flops = 0.0;  // float32 far-field flops issued (18 per Laplace pair, 24 per Yukawa pair)
   double setup_ms[4] = {0, 0, 0, 0};  // mesh_create: validation, surfaces, operator pattern, device set-up
   // FEM over Omega_m and Omega_i (Sec. 2.2, Eq. fembem_matrix): `tets` holds the tets of Omega_i
@@ -298,14 +298,16 @@ int init_quadrature();
 // ---- fem_kernels.cu
 int launch_tet_volumes(Mesh* m, const int* tets, int64_t nt, double* vol);
 int launch_stiffness_local(Mesh* m, const int* tets, int64_t nt, const double* vol, double* loc10);
+// ff: the tet-local entries are float-float pairs (the mixed precision's sinh-scheme kernels)
 int launch_gather(Mesh* m, int nslots, const int* ptr, const int* idx, const double* local,
-                  const double* base, double scale, double* out);
-int launch_element_nl(Mesh* m, int scheme, const double* u, double coef, double* loc);
+                  const double* base, double scale, double* out, bool ff = false);
+// *ff tells whether loc was written as float-float pairs
+int launch_element_nl(Mesh* m, int scheme, const double* u, double coef, double* loc, bool* ff);
 int launch_spmv(Mesh* m, const double* x, double* y);
 int launch_omega_elements(Mesh* m, int scheme, const double* u, const double* du,
-                          const double* omegas_dev, int nomega, double coef, double* loc);
+                          const double* omegas_dev, int nomega, double coef, double* loc, bool* ff);
 int launch_omega_dots(Mesh* m, int nomega, const double* loc, const double* c, const double* p,
-                      double* dots_dev);
+                      double* dots_dev, bool ff);
 int launch_ion_energy(Mesh* m, const double* u, double* out_dev);
 int launch_fill_operator(Mesh* m);
 int launch_csr_spmv(Mesh* m, int nrows, const int* ptr, const int* col, const double* val, const double* x,

@@ -593,10 +593,11 @@ static int set_params(Mesh* m, double eps_in, double eps_out, double kappa, doub
 
 // J(u) into the operator values; N(u) into N_out (may be null)
 static int assemble(Mesh* m, int scheme, const double* u, double* N_out) {
-  PB_TRY(launch_element_nl(m, scheme, u, m->coef, m->tloc.p));
-  PB_TRY(launch_gather(m, m->snnz, m->jg_ptr.p, m->jg_idx.p, m->tloc.p, m->s_base.p, 1.0, m->s_val.p));
+  bool ff = false;
+  PB_TRY(launch_element_nl(m, scheme, u, m->coef, m->tloc.p, &ff));
+  PB_TRY(launch_gather(m, m->snnz, m->jg_ptr.p, m->jg_idx.p, m->tloc.p, m->s_base.p, 1.0, m->s_val.p, ff));
   if (N_out)
-    PB_TRY(launch_gather(m, m->nv, m->ng_ptr.p, m->ng_idx.p, m->tloc.p + 10 * m->nt, nullptr, 1.0, N_out));
+    PB_TRY(launch_gather(m, m->nv, m->ng_ptr.p, m->ng_idx.p, m->tloc.p + 10 * m->nt, nullptr, 1.0, N_out, ff));
   return PBFB_OK;
 }
 
@@ -1094,8 +1095,9 @@ static int omega_eval(Mesh* m, int scheme, const double* u, const double* du, co
   double* dv = m->scal.p;  // [0, 64) omegas, [64, ...) results
   std::memcpy(m->pinned, omegas, nomega * sizeof(double));
   PB_CUDA(cudaMemcpyAsync(dv, m->pinned, nomega * sizeof(double), cudaMemcpyHostToDevice, m->stream));
-  PB_TRY(launch_omega_elements(m, scheme, u, du, dv, nomega, m->coef, m->wloc.p));
-  PB_TRY(launch_omega_dots(m, nomega, m->wloc.p, c, p, dv + 64));
+  bool ff = false;
+  PB_TRY(launch_omega_elements(m, scheme, u, du, dv, nomega, m->coef, m->wloc.p, &ff));
+  PB_TRY(launch_omega_dots(m, nomega, m->wloc.p, c, p, dv + 64, ff));
   PB_TRY(dot_dev(m, p + nv, c + nv, nb, dv + 64 + 7 * 64));
   PB_TRY(dot_dev(m, c + nv, c + nv, nb, dv + 64 + 7 * 64 + 1));
   PB_TRY(dot_dev(m, p, p, n, dv + 64 + 7 * 64 + 2));

@@ -77,6 +77,44 @@ def test_fem_rows_and_load(pair, scheme, precision):
     assert rel(host(N_dev), N_ref) < 1e-13
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sinh_rows_wide_range(pair, precision):
+    """The sinh scheme with potentials from -75 to 75 (linear in x): the mixed precision's
+    float-float kernels take the tets with all |u| <= 60 and the float64 sums the others, in the
+    same launch.  Every FEM entry within 1e-12 of |A| + |J| (entrywise), every load within 1e-12
+    of its row of J (cosh >= |sinh|), the omega dots within 1e-11 of the largest."""
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    m.set_params(case.eps_in, case.eps_out, case.kappa, case.T, precision)
+    x = P.xyz[:, 0]
+    u = -75.0 + 150.0 * (x - x.min()) / (x.max() - x.min())
+    assert (np.abs(u) > 60).any() and (np.abs(u) < 60).any()
+    N_dev = dev(np.zeros(P.nv))
+    m.assemble(SCHEMES["HS"], dev(u), N_dev)
+    rp, col, val = m.fem_rows()
+    G = sp.csr_matrix((val, col, rp), shape=(P.nv, P.n))
+    Jm = P.J(u, "HS")
+    O = sp.hstack([P.A + Jm, P.B_um, P.B_us]).tocsr()
+    S = sp.hstack([abs(P.A) + abs(Jm), abs(P.B_um), abs(P.B_us)]).toarray()
+    D = np.abs((G - O).toarray())
+    assert (D <= 1e-12 * S).all()
+    N_ref = P.N(u, "HS")
+    row = np.asarray(abs(Jm).sum(axis=1)).ravel()
+    assert (np.abs(host(N_dev) - N_ref) <= 1e-12 * row).all()
+    rng = np.random.default_rng(3)
+    du = 0.3 * rng.standard_normal(P.nv)
+    c = rng.standard_normal(P.n)
+    p = rng.standard_normal(P.n)
+    oms = np.array([0.0, 1.0, -2.0])
+    got = m.omega_eval(SCHEMES["HS"], dev(u), dev(du), dev(c), dev(p), oms)
+    for o, om in enumerate(oms):
+        Dd = pb.omega_dots(P, u, du, c, p, om, "HS")
+        ref = [Dd["PR"], Dd["PP"], Dd["PRp"], Dd["RRpp"], Dd["PRpp"], Dd["RR"], Dd["pr"], Dd["pp"]]
+        scale = max(abs(v) for v in ref)
+        assert np.isfinite(got[o]).all() and np.abs(got[o] - ref).max() < 1e-11 * scale, om
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_boundary_operators(pair, precision):
     """float64 (0) and float-float (2) far fields within 1e-11 of the oracle; float32 (1) 3e-6."""
