@@ -42,6 +42,8 @@ SM_MAX_MHZ = 2070.0       # GB300 maximum SM clock, used when nvidia-smi reports
 # layer, about 20 flops for the Laplace kernel and 28 for the Yukawa kernel (its exponential
 # factor and (1 + kappa r) term), with one rsqrt (and one exp) on the special-function unit
 FLOP_PAIR = {"laplace": 20.0, "yukawa": 28.0}
+# pbfb_newton_opts.residual_far: PBFB_FLOAT2 (float-float direct sum) or PBFB_MIXED (float32 operator)
+RESIDUAL_FAR = {"float2": 2, "f32": 1}
 GOLDEN = os.path.join(ROOT, "tests", "golden", "multi_charge_sphere.json")
 # DRAM bytes (read + write) per launch on this workload, each from an ncu capture of the kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum): the packed float32 far field (source records
@@ -184,7 +186,8 @@ def serving_cases(n, seed=5000):
     return cases
 
 
-def run_serving(pbfb, cases, max_inflight, budget, residual_update=0.0, precision=None, detail=False):
+def run_serving(pbfb, cases, max_inflight, budget, residual_update=0.0, precision=None, detail=False,
+                residual_far="float2"):
     """Saturation run (all requests at t = 0) for capacity, then Poisson arrivals at 0.8x
     capacity; latency = arrival -> result (the request's own set-up included)."""
     import numpy as np
@@ -197,7 +200,8 @@ def run_serving(pbfb, cases, max_inflight, budget, residual_update=0.0, precisio
         return got
 
     precision = pbfb.MIXED if precision is None else precision
-    opts = pbfb.default_opts(precision=precision, residual_update=residual_update)
+    opts = pbfb.default_opts(precision=precision, residual_update=residual_update,
+                             residual_far=RESIDUAL_FAR[residual_far])
     sv = pbfb.Server(budget, max_inflight, cached_meshes=16)
     t0 = time.perf_counter()
     for i, c in enumerate(cases):
@@ -259,7 +263,8 @@ def run_pbfb(args):
     case = inputs.multi_charge_sphere() if args.workload == "multi_charge_sphere" else inputs.single_charge_sphere()
     prec = pbfb.MIXED if args.precision == "mixed" else pbfb.FP64
     opts = pbfb.default_opts(precision=prec,
-                             residual_update=args.residual_update if prec == pbfb.MIXED else 0.0)
+                             residual_update=args.residual_update if prec == pbfb.MIXED else 0.0,
+                             residual_far=RESIDUAL_FAR[args.residual_far])
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
     mesh = pbfb.Mesh.from_case(case)
@@ -346,7 +351,7 @@ def run_pbfb(args):
     if prec == pbfb.MIXED:
         l32, ms32 = prof["nbody_launches"], prof["nbody_ms"]
         if l32:
-            name32 = ("k_tree_eval + k_tree_up_part (float32 far field of the GMRES operator through the treecode: "
+            name32 = ("k_tree_eval + k_tree_up (float32 far field of the GMRES operator through the treecode: "
                       "near pairs and cluster proxies, packed, 2 targets per thread)" if tuned.get("treecode") == 2
                       else "k_nbody_f32x2 (float32 far field of the GMRES operator, packed, 2 targets per thread)")
             cands.append(dict(kernel=name32, launches=l32, ms=ms32, pairs=prof["nbody_pairs"],
@@ -399,7 +404,8 @@ def run_pbfb(args):
         "vs_baseline": None, "dtype": "f32+f64" if prec == pbfb.MIXED else "f64",
         "data": "synthetic (seeded sphere mesh and charges)",
         "config": workload_config(case, args.precision) | {"parallelism": f"replicas x{ws}",
-                                                            "residual_update": opts.residual_update},
+                                                            "residual_update": opts.residual_update,
+                                                            "residual_far": args.residual_far},
         "p50_ms": statistics.median(step_ms),
         "p99_ms": float(np.percentile(step_ms, 99)),
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
@@ -460,13 +466,33 @@ def run_pbfb(args):
             ms0.append(e0.elapsed_time(e1))
         out["mixed_residual_every_step"] = {"steps": len(ms0), "ms_per_solve": sum(ms0) / len(ms0),
                                             "newton_iters": r0["newton_iters"], "total_kcal_mol": r0["total"]}
+    # the other far field of the Newton residual's full evaluations (float-float or float32)
+    if prec == pbfb.MIXED:
+        alt = "f32" if args.residual_far == "float2" else "float2"
+        oa = pbfb.default_opts(precision=pbfb.MIXED, residual_update=args.residual_update,
+                               residual_far=RESIDUAL_FAR[alt])
+        msa = []
+        for _ in range(max(1, min(args.steps, 5))):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ra = mesh.solve_device(case.eps_in, case.eps_out, case.kappa, case.T, x_out, oa)
+            e1.record(stream)
+            e1.synchronize()
+            msa.append(e0.elapsed_time(e1))
+        out["mixed_residual_far_" + alt] = {"steps": len(msa), "ms_per_solve": sum(msa) / len(msa),
+                                            "newton_iters": ra["newton_iters"], "total_kcal_mol": ra["total"],
+                                            "energy_rel_diff_vs_headline": abs(ra["total"] - res["total"]) /
+                                            abs(res["total"])}
     if args.full_formulation and ws == 1 and args.workload == "multi_charge_sphere":
         out["full_formulation"] = run_full_formulation(pbfb, inputs, tuned, opts, res, flush, stream)
     if args.helix > 0 and ws == 1 and args.workload == "multi_charge_sphere":
         out["double_helix"] = run_helix(pbfb, inputs, opts, flush, stream, args.helix)
     if args.serving > 0 and args.workload == "multi_charge_sphere":
         cases = serving_cases(args.serving)
-        out["serving"] = run_serving(pbfb, cases, 4, 64 << 30, args.residual_update)
+        out["serving"] = run_serving(pbfb, cases, 4, 64 << 30, args.residual_update,
+                                     residual_far=args.residual_far)
     if os.path.exists(GOLDEN) and args.workload == "multi_charge_sphere":
         g = json.load(open(GOLDEN))
         ref = g["tight"]["total"]
@@ -588,7 +614,8 @@ def run_batch(args):
     from paper_2511_21713_gb300 import build as pbuild
     pbuild.build()
     from paper_2511_21713_gb300 import pbfb
-    opts = pbfb.default_opts(precision=pbfb.MIXED, residual_update=args.residual_update)
+    opts = pbfb.default_opts(precision=pbfb.MIXED, residual_update=args.residual_update,
+                             residual_far=RESIDUAL_FAR[args.residual_far])
     streams = [torch.cuda.Stream() for _ in cases]
     t0 = time.perf_counter()
     meshes = []
@@ -665,14 +692,15 @@ def run_serving_config(args):
                                                                   int(tris.max())],
                                         "helices": int(sum("helix" in c.name for c in cases)),
                                         "budget_bytes": args.budget_gb << 30, "max_inflight": args.concurrency,
-                                        "residual_update": args.residual_update}}
+                                        "residual_update": args.residual_update,
+                                        "residual_far": args.residual_far}}
     out["mixed"] = run_serving(pbfb, cases, args.concurrency, args.budget_gb << 30, args.residual_update,
-                               detail=True)
+                               detail=True, residual_far=args.residual_far)
     small = [c for c in cases if c.gm_tris.shape[0] <= args.fp64_max_tri]
     if small and args.fp64_max_tri > 0:
         out["fp64"] = run_serving(pbfb, small, args.concurrency, args.budget_gb << 30, 0.0, precision=pbfb.FP64)
         out["mixed_same_subset"] = run_serving(pbfb, small, args.concurrency, args.budget_gb << 30,
-                                               args.residual_update)
+                                               args.residual_update, residual_far=args.residual_far)
     return out
 
 
@@ -926,6 +954,8 @@ def main():
     ap.add_argument("--budget-gb", type=int, default=160, help="--config serving: HBM budget")
     ap.add_argument("--fp64-max-tri", type=int, default=8000,
                     help="--config serving: largest surface (triangles) of the float64 arm")
+    ap.add_argument("--residual-far", default="f32", choices=["float2", "f32"],
+                    help="far field of the Newton residual's full evaluations (pbfb_newton_opts.residual_far)")
     ap.add_argument("--residual-update", type=float, default=0.5,
                     help="mixed path: pbfb_newton_opts.residual_update (0 = float-float residual every step)")
     ap.add_argument("--no-full-formulation", dest="full_formulation", action="store_false",

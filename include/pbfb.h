@@ -137,6 +137,12 @@ typedef struct pbfb_newton_opts {
                            the updates omega ||Delta|| since the last float-float evaluation stays
                            below tau ||Phi_{k+1}||; the updates' rounding is that of the float32
                            far field applied to the increments, not to Phi */
+  int residual_far;       /* PBFB_MIXED only: far field of the Newton residual b - Acal(0) Phi
+                           where it is evaluated in full.  PBFB_FLOAT2 (default): float-float
+                           direct sum; PBFB_MIXED: the GMRES operator's float32 far field (direct
+                           or treecode as tuned, about 1e-6 of the largest entry), the rounding
+                           the residual updates above already carry.  Any other value:
+                           PBFB_ERR_INVALID */
 } pbfb_newton_opts;
 
 #define PBFB_MAX_TRACE 64

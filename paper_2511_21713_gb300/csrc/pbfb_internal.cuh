@@ -88,6 +88,7 @@ struct SurfaceTree {
   DBuf<float> clus_box;             // per cluster: lo x, y, z, hi x, y, z (centre-relative)
   DBuf<int> seg_clus, seg_beg, seg_cnt;  // per segment: cluster, first point (tree order), points
   DBuf<float4> up_part;             // per segment: partial proxies (charge, dipole) of its cluster
+  DBuf<int> up_arrivals;            // per cluster: segments done in the running upward pass (0 between)
   DBuf<float4> tgt;                 // target positions in tree order
   DBuf<float4> spos, sdl;           // nq points in tree order, then nclus x (p+1)^3 proxies
   DBuf<double> part;                // nchunk x 256 partial sums

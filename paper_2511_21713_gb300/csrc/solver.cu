@@ -1423,6 +1423,7 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
   if (!(o.tol_nl > 0) || !(o.tol_gmres > 0) || !(o.tol_gmres0 > 0) || !(o.tol_omega > 0) || o.max_newton < 1 ||
       o.max_gmres < 1 || !(o.omega_max > 0) || !std::isfinite(o.omega_max) || o.max_omega_iters < 1 ||
       !(o.accept_ratio >= 0.0 && o.accept_ratio <= 1.0) || !(o.residual_update >= 0.0) ||
+      (o.residual_far != PBFB_FLOAT2 && o.residual_far != PBFB_MIXED) ||
       o.n_taylor < 0 || o.n_taylor > 4 || (o.method != PBFB_NEWTON && o.method != PBFB_PICARD) || !(o.R_e >= 0) ||
       (o.precision != PBFB_FP64 && o.precision != PBFB_MIXED)) {
     set_error("solve: invalid options");
@@ -1492,9 +1493,10 @@ static int solve(Mesh* m, double eps_in, double eps_out, double kappa, double T,
       }
     }
     if (!updated) {
-      // c = b - Acal(0) Phi: the nonlinear residual's far field in float64 (FP64) or float-float (MIXED)
+      // c = b - Acal(0) Phi: the nonlinear residual's far field in float64 (FP64), in float-float
+      // or with the GMRES operator's float32 far field (MIXED, residual_far)
       PB_TRY(clear_jacobian(m));
-      PB_TRY(apply_prec(m, m->phi.p, m->cvec.p, m->precision == PBFB_MIXED ? PBFB_FLOAT2 : PBFB_FP64));
+      PB_TRY(apply_prec(m, m->phi.p, m->cvec.p, m->precision == PBFB_MIXED ? o.residual_far : PBFB_FP64));
       PB_TRY(launch_axpby(m, n, 1.0, bvec, -1.0, m->cvec.p, m->cvec.p));
       upd_sum = 0.0;
     }
@@ -1749,6 +1751,7 @@ void pbfb_default_opts(pbfb_newton_opts* o) {
   o->inner_iters = 30;
   o->accept_ratio = 1.0;
   o->residual_update = 0.0;
+  o->residual_far = PBFB_FLOAT2;
 }
 
 const char* pbfb_last_error(void) { return pbfb::last_error(); }

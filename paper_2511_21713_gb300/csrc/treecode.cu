@@ -51,63 +51,68 @@ __global__ void k_tree_permute(int nq, const int* __restrict__ perm, const float
   sdl_t[i] = sdl[j];
 }
 
-// Upward pass, in two kernels.  k_tree_up_part: one block per segment (at most 256 consecutive
-// points of one cluster): proxy k = (a, b, c) at (tx_a, ty_b, tz_c) of the cluster's box receives
+// Upward pass, one kernel.  A block per segment (at most 256 consecutive points of one cluster):
+// proxy k = (a, b, c) at (tx_a, ty_b, tz_c) of the cluster's box receives
 // sum_j L_a(x_j) L_b(y_j) L_c(z_j) (s_j, m_j) over the segment's points, the 1-D values from the
 // barycentric formula l_a(x) = (w_a / (x - t_a)) / sum_m (w_m / (x - t_m)), w_m = (-1)^m (halved at
-// both ends), or the unit vector when x coincides with a node.  k_tree_up_sum: one block per
-// cluster adds its segments in order and writes the proxy source records after the points.
+// both ends), or the unit vector when x coincides with a node.  The basis values sit point-major
+// (lw[d][j][a]), so the 343 proxy threads of a warp read at most 7 consecutive words per point
+// (no bank conflicts).  The block that completes a cluster's last segment (a per-cluster arrival
+// counter) adds the cluster's segments in index order and writes its proxy source records, then
+// re-arms the counter: the result does not depend on which block arrives last.
 __device__ __forceinline__ float cheb_node(const float* __restrict__ cbox, int c, int d, int k) {
   const float lo = cbox[6 * c + d], hi = cbox[6 * c + 3 + d];
   return 0.5f * (lo + hi) + 0.5f * (hi - lo) * cospif((float)k / (float)TREE_P);
 }
 
-__global__ void __launch_bounds__(TREE_UP_NT) k_tree_up_part(const int* __restrict__ seg_clus,
-                                                             const int* __restrict__ seg_beg,
-                                                             const int* __restrict__ seg_cnt,
-                                                             const float* __restrict__ cbox,
-                                                             const float4* __restrict__ spos_t,
-                                                             const float4* __restrict__ sdl_t,
-                                                             float4* __restrict__ part) {
+__global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ seg_clus,
+                                                        const int* __restrict__ seg_beg,
+                                                        const int* __restrict__ seg_cnt,
+                                                        const int* __restrict__ clus_seg,
+                                                        const float* __restrict__ cbox,
+                                                        const float4* __restrict__ pts_pos,
+                                                        const float4* __restrict__ pts_dl,
+                                                        float4* __restrict__ part, int* __restrict__ arrivals,
+                                                        float4* __restrict__ prox_pos,
+                                                        float4* __restrict__ prox_dl) {
   __shared__ float node[3][TREE_K];
-  __shared__ float lw[3][TREE_K][TREE_LEAF];
+  __shared__ float lw[3][TREE_LEAF][TREE_K];
   __shared__ float4 src[TREE_LEAF];
+  __shared__ int last;
   const int g = blockIdx.x;
   const int c = seg_clus[g], b = seg_beg[g], cnt = seg_cnt[g];
   const int t = threadIdx.x;
   if (t < 3 * TREE_K) node[t / TREE_K][t % TREE_K] = cheb_node(cbox, c, t / TREE_K, t % TREE_K);
   __syncthreads();
-  if (t < TREE_LEAF) {
-    if (t < cnt) {
-      const float4 p = spos_t[b + t];
-      const float4 q = sdl_t[b + t];
-      src[t] = make_float4(p.w, q.x, q.y, q.z);
-      const float xs[3] = {p.x, p.y, p.z};
-      for (int d = 0; d < 3; ++d) {
-        float a[TREE_K];
-        float den = 0.f;
-        int hit = -1;
-        for (int k = 0; k < TREE_K; ++k) {
-          const float dx = xs[d] - node[d][k];
-          const float w = ((k & 1) ? -1.f : 1.f) * ((k == 0 || k == TREE_P) ? 0.5f : 1.f);
-          if (dx == 0.f) hit = k;
-          a[k] = dx == 0.f ? 0.f : w / dx;
-          den += a[k];
-        }
-        for (int k = 0; k < TREE_K; ++k) lw[d][k][t] = hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] / den;
+  if (t < cnt) {
+    const float4 p = pts_pos[b + t];
+    const float4 q = pts_dl[b + t];
+    src[t] = make_float4(p.w, q.x, q.y, q.z);
+    const float xs[3] = {p.x, p.y, p.z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float a[TREE_K];
+      float den = 0.f;
+      int hit = -1;
+#pragma unroll
+      for (int k = 0; k < TREE_K; ++k) {
+        const float dx = xs[d] - node[d][k];
+        const float w = ((k & 1) ? -1.f : 1.f) * ((k == 0 || k == TREE_P) ? 0.5f : 1.f);
+        if (dx == 0.f) hit = k;
+        a[k] = dx == 0.f ? 0.f : w * __frcp_rn(dx);
+        den += a[k];
       }
-    } else {
-      src[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int d = 0; d < 3; ++d)
-        for (int k = 0; k < TREE_K; ++k) lw[d][k][t] = 0.f;
+      const float rden = __frcp_rn(den);
+#pragma unroll
+      for (int k = 0; k < TREE_K; ++k) lw[d][t][k] = hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] * rden;
     }
   }
   __syncthreads();
+  const int ka = t / (TREE_K * TREE_K), kb = (t / TREE_K) % TREE_K, kc = t % TREE_K;
   if (t < TREE_NPX) {
-    const int ka = t / (TREE_K * TREE_K), kb = (t / TREE_K) % TREE_K, kc = t % TREE_K;
     float fs = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
     for (int jj = 0; jj < cnt; ++jj) {
-      const float w = lw[0][ka][jj] * lw[1][kb][jj] * lw[2][kc][jj];
+      const float w = lw[0][jj][ka] * lw[1][jj][kb] * lw[2][jj][kc];
       const float4 q = src[jj];
       fs = fmaf(w, q.x, fs);
       fx = fmaf(w, q.y, fx);
@@ -116,28 +121,28 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up_part(const int* __restri
     }
     part[(size_t)g * TREE_NPX + t] = make_float4(fs, fx, fy, fz);
   }
-}
-
-__global__ void __launch_bounds__(TREE_UP_NT) k_tree_up_sum(int nq, const int* __restrict__ clus_seg,
-                                                            const float* __restrict__ cbox,
-                                                            const float4* __restrict__ part,
-                                                            float4* __restrict__ spos_t,
-                                                            float4* __restrict__ sdl_t) {
-  const int c = blockIdx.x;
-  const int t = threadIdx.x;
-  if (t >= TREE_NPX) return;
-  const int ka = t / (TREE_K * TREE_K), kb = (t / TREE_K) % TREE_K, kc = t % TREE_K;
-  double as = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
-  for (int g = clus_seg[c]; g < clus_seg[c + 1]; ++g) {
-    const float4 v = part[(size_t)g * TREE_NPX + t];
-    as += v.x;
-    ax += v.y;
-    ay += v.z;
-    az += v.w;
+  // the last block of the cluster to arrive sums its segments (release: fence before the count)
+  __threadfence();
+  __syncthreads();
+  const int s0 = clus_seg[c], s1 = clus_seg[c + 1];
+  if (t == 0) last = atomicAdd(&arrivals[c], 1) == s1 - s0 - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();  // acquire: the other segments' partials are visible in L2
+  if (t < TREE_NPX) {
+    double as = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
+    for (int h = s0; h < s1; ++h) {
+      const float4 v = __ldcg(&part[(size_t)h * TREE_NPX + t]);
+      as += v.x;
+      ax += v.y;
+      ay += v.z;
+      az += v.w;
+    }
+    const int o = c * TREE_NPX + t;
+    prox_pos[o] = make_float4(node[0][ka], node[1][kb], node[2][kc], (float)as);
+    prox_dl[o] = make_float4((float)ax, (float)ay, (float)az, 0.f);
   }
-  const int o = nq + c * TREE_NPX + t;
-  spos_t[o] = make_float4(cheb_node(cbox, c, 0, ka), cheb_node(cbox, c, 1, kb), cheb_node(cbox, c, 2, kc), (float)as);
-  sdl_t[o] = make_float4((float)ax, (float)ay, (float)az, 0.f);
+  if (t == 0) arrivals[c] = 0;
 }
 
 // Evaluation: block = one chunk (a target leaf and a run of its source tiles).  Tiles that overlap
@@ -313,6 +318,8 @@ int build_surface_tree(Mesh* m, Surface* s) {
     PB_TRY(T.seg_beg.upload(P.seg_beg.data(), T.nseg, m->stream));
     PB_TRY(T.seg_cnt.upload(P.seg_cnt.data(), T.nseg, m->stream));
     PB_TRY(T.up_part.alloc((size_t)T.nseg * TREE_NPX));
+    PB_TRY(T.up_arrivals.alloc(P.nclus));
+    PB_CUDA(cudaMemsetAsync(T.up_arrivals.p, 0, P.nclus * sizeof(int), m->stream));
   }
   PB_TRY(T.spos.alloc((size_t)nq + (size_t)P.nclus * TREE_NPX));
   PB_TRY(T.sdl.alloc((size_t)nq + (size_t)P.nclus * TREE_NPX));
@@ -342,11 +349,9 @@ int launch_tree_far(Mesh* m, Surface* s, double kappa, const float4* spos, const
   k_tree_permute<<<blocks(nq, 256), 256, 0, m->stream>>>(nq, T.perm.p, spos, sdl, T.spos.p, T.sdl.p);
   PB_LAUNCHED(m);
   if (T.nclus > 0) {
-    k_tree_up_part<<<T.nseg, TREE_UP_NT, 0, m->stream>>>(T.seg_clus.p, T.seg_beg.p, T.seg_cnt.p, T.clus_box.p,
-                                                         T.spos.p, T.sdl.p, T.up_part.p);
-    PB_LAUNCHED(m);
-    k_tree_up_sum<<<T.nclus, TREE_UP_NT, 0, m->stream>>>(nq, T.clus_seg.p, T.clus_box.p, T.up_part.p, T.spos.p,
-                                                         T.sdl.p);
+    k_tree_up<<<T.nseg, TREE_UP_NT, 0, m->stream>>>(T.seg_clus.p, T.seg_beg.p, T.seg_cnt.p, T.clus_seg.p,
+                                                    T.clus_box.p, T.spos.p, T.sdl.p, T.up_part.p, T.up_arrivals.p,
+                                                    T.spos.p + nq, T.sdl.p + nq);
     PB_LAUNCHED(m);
   }
   const float kf = (float)kappa;

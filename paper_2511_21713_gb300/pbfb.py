@@ -58,7 +58,7 @@ class NewtonOpts(ctypes.Structure):
                 ("omega_warm_start", ctypes.c_int),
                 ("omega_search", ctypes.c_int), ("precond", ctypes.c_int),
                 ("inner_iters", ctypes.c_int), ("accept_ratio", ctypes.c_double),
-                ("residual_update", ctypes.c_double)]
+                ("residual_update", ctypes.c_double), ("residual_far", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

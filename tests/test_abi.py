@@ -40,6 +40,7 @@ def test_default_options_are_the_papers(lib):
     assert o.n_taylor == 1 and o.taylor[0] == pbfb.T3 and o.method == pbfb.NEWTON and o.R_e == 1.4
     assert o.omega_search == 1 and o.precision == pbfb.FP64 and o.precond == pbfb.BLOCK_DENSE
     assert o.accept_ratio == 1.0          # the global convergence condition ||d(omega)|| < ||d(0)||
+    assert o.residual_update == 0.0 and o.residual_far == pbfb.FLOAT2
 
 
 def _create(lib, xyz, tets, gm, gs):

@@ -353,6 +353,25 @@ def test_residual_update_option(pair):
     assert r["residual_updates"] == 0
 
 
+@pytest.mark.parametrize("residual_update", [0.0, 0.5])
+def test_residual_far_float32(pair, residual_update):
+    """The Newton residual's full evaluations with the GMRES operator's float32 far field
+    (residual_far = MIXED): the oracle's energy within the mixed-path 1e-5 at the paper's
+    tolerances, with and without residual updates; ignored by the float64 path (bitwise the same
+    solve)."""
+    from paper_2511_21713_gb300 import pbfb
+    from oracle import pb
+    case, m, P = pair
+    ref = pb.solve(P, pb.Opts(**TIGHT))
+    _, r = m.solve(case.eps_in, case.eps_out, case.kappa, case.T,
+                   pbfb.default_opts(precision=pbfb.MIXED, residual_update=residual_update,
+                                     residual_far=pbfb.MIXED))
+    assert r["status"] == 0 and abs(r["total"] - ref.total) < 1e-5 * abs(ref.total)
+    x1, r1 = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.default_opts(residual_far=pbfb.MIXED))
+    x2, r2 = m.solve(case.eps_in, case.eps_out, case.kappa, case.T, pbfb.default_opts())
+    assert np.array_equal(x1, x2) and r1["total"] == r2["total"]
+
+
 def test_deterministic(pair):
     from paper_2511_21713_gb300 import pbfb
     case, m, _ = pair
@@ -421,7 +440,8 @@ def test_error_statuses(tiny_case):
     with pytest.raises(pbfb.PbfbError) as e:
         m.solve(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.default_opts(omega_search=0, omega0_first=1e300))
     assert e.value.code == 6                       # NONFINITE
-    for bad in (dict(omega_max=float("inf")), dict(accept_ratio=1.5), dict(accept_ratio=-0.1)):
+    for bad in (dict(omega_max=float("inf")), dict(accept_ratio=1.5), dict(accept_ratio=-0.1),
+                dict(residual_far=0), dict(residual_far=3)):
         with pytest.raises(pbfb.PbfbError) as e:
             m.solve(c.eps_in, c.eps_out, c.kappa, c.T, pbfb.default_opts(**bad))
         assert e.value.code == 1, bad
