@@ -403,7 +403,13 @@ typedef struct pbfb_tuning {
                                         Sec. 3); 0 built-in: the treecode for surfaces of 65,536
                                         quadrature points or more.  The treecode approximates the
                                         float32 operator (about 1e-6 of the largest entry); the
-                                        Newton residual stays the float-float direct sum. */
+                                        Newton residual's far field follows
+                                        pbfb_newton_opts.residual_far. */
+  int32_t pcg_precision;             /* arithmetic of the cooperative inner PCG (CSR forms):
+                                        1 float64, 2 float32 (float32 matrix and vectors, float64
+                                        block and grid sums); 0 built-in: float32 in the
+                                        PBFB_MIXED precision, float64 otherwise.  The sliced-ELL
+                                        form (pcg_lanes 1) is float64 only. */
 } pbfb_tuning;
 
 /* Current launch shapes of a mesh (zeros where the built-in choice applies). */

@@ -22,6 +22,7 @@ void read_tuning(const Mesh* m, pbfb_tuning* t) {
   t->pcg_blocks_per_sm = m->tune_pcg_bps;
   t->pcg_lanes = m->pcg_lanes;
   t->treecode = m->tune_tree;
+  t->pcg_precision = m->tune_pcg_prec;
 }
 
 bool valid_tuning(const pbfb_tuning* t) {
@@ -39,6 +40,7 @@ bool valid_tuning(const pbfb_tuning* t) {
   if (!(t->pcg_lanes == 0 || t->pcg_lanes == 1 || t->pcg_lanes == 2 || t->pcg_lanes == 4 || t->pcg_lanes == 8))
     return false;
   if (t->treecode < 0 || t->treecode > 2) return false;
+  if (t->pcg_precision < 0 || t->pcg_precision > 2) return false;
   return true;
 }
 
@@ -54,6 +56,7 @@ void write_tuning(Mesh* m, const pbfb_tuning* t) {
   m->tune_pcg_bps = t->pcg_blocks_per_sm;
   m->pcg_lanes = t->pcg_lanes;
   m->tune_tree = t->treecode;
+  m->tune_pcg_prec = t->pcg_precision;
 }
 
 // milliseconds per repetition of fn (one untimed run first)

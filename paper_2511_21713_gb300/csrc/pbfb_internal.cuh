@@ -209,8 +209,13 @@ struct Mesh {
   int nrobin = 0;
   DBuf<int> robin_slot, robin_ref;  // FEM-row slot (u-u, both on Gamma_s) <- Gamma_s mass slot
   DBuf<double> pval, pdinv;
+  DBuf<float> pvalf, pdinvf;        // float32 copies for the mixed precision's cooperative PCG
+  DBuf<float> pcgf;                 // its vectors x, r, z, p, q, w (n each; z stays 0 past nv)
+  bool pcg_f32 = false;             // the cooperative PCG runs in float32
+  int tune_pcg_prec = 0;            // its arithmetic: 0 built-in (float32 in MIXED), 1 float64, 2 float32
   double gs_radius = 1.0;           // sqrt(|Gamma_s| / 4 pi)
   int coop_blocks = 0;              // grid of the cooperative inner PCG (-1: not available)
+  int coop_blocks_f32 = 0;          // grid of its float32 form (one block per SM; -1: not available)
   bool no_coop = false;             // never use the grid-barrier PCG (meshes solved concurrently)
   int tune_tpt = 0;                 // float32 far field: targets per thread (0 = heuristic)
   int tune_bps = 0;                 // float32 far field: target blocks per SM for the source split

@@ -250,6 +250,11 @@ __global__ void k_pcg_direction(int nv, const double* __restrict__ rz_old, const
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) p[i] = z[i] + beta * p[i];
 }
 
+__global__ void k_to_f32(int n, const double* __restrict__ a, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)a[i];
+}
+
 // preconditioner FEM block: pval += c M_s on the Gamma_s u-u slots
 __global__ void k_add_robin(int nr, const int* __restrict__ slot, const int* __restrict__ ref,
                             const double* __restrict__ mass, double c, double* __restrict__ pval) {
@@ -268,11 +273,20 @@ __global__ void k_diag_inv(int nv, const int* __restrict__ ptr, const int* __res
   dinv[r] = 1.0 / d;
 }
 
-// Both scalars of a step at once: warp 0 of every block reads the per-block partials lane-strided
-// (lane l sums entries l, l + 32, ... in that order), then a butterfly over the 32 lanes; the order
-// of every addition is fixed, so each block obtains the same two values.
-__device__ __forceinline__ void coop_sum2(const double* pa, const double* pb, int nb, double* a, double* b) {
-  __shared__ double tot[2];
+// The scalars of a Chronopoulos-Gear step from the two grid sums: warp 0 of every block reads the
+// per-block partials lane-strided (lane l sums entries l, l + 32, ... in that order), then a
+// butterfly over the 32 lanes, so every block obtains the same two sums; lane 0 alone takes the
+// divisions and the stop rules, and the block
+// reads alpha and beta from shared memory (GB300's float64 rate makes two divisions in every
+// thread of the grid the larger part of a step).  The recurrence state (gamma_old, alpha_old,
+// gamma_0) lives in shared memory, so every block evolves it identically.  f32_rules adds the
+// float32 form's stops: r.z at 1e-12 of its first value, or a non-positive or huge alpha.
+// Returns true when the iteration is to stop before this step's update.  A zero r.z (e.g. a
+// right-hand side that vanishes on the FEM rows) gives alpha = beta = 0: nothing left to do.
+__device__ __forceinline__ bool cg_step_scalars(const double* pa, const double* pb, int nb, int it, bool f32_rules,
+                                                double* alpha_out, double* beta_out) {
+  __shared__ double st[5];  // gamma_old, alpha_old, gamma_0, alpha, beta
+  __shared__ int stop;
   if (threadIdx.x < 32) {
     double sa = 0.0, sb = 0.0;
     for (int k = threadIdx.x; k < nb; k += 32) {
@@ -284,14 +298,38 @@ __device__ __forceinline__ void coop_sum2(const double* pa, const double* pb, in
       sb += __shfl_xor_sync(0xffffffffu, sb, o);
     }
     if (threadIdx.x == 0) {
-      tot[0] = sa;
-      tot[1] = sb;
+      const double gamma = sa, delta = sb;
+      if (it == 0) {
+        st[0] = 1.0;
+        st[1] = 1.0;
+        st[2] = gamma;
+      }
+      const double gamma_old = st[0], alpha_old = st[1];
+      double beta = 0.0, alpha = 0.0;
+      if (gamma != 0.0) {
+        if (it == 0 || gamma_old == 0.0 || alpha_old == 0.0) {
+          alpha = delta != 0.0 ? gamma / delta : 0.0;
+        } else {
+          beta = gamma / gamma_old;
+          const double den = delta - beta * gamma / alpha_old;
+          alpha = den != 0.0 ? gamma / den : 0.0;
+        }
+      }
+      int s = 0;
+      if (f32_rules && (!(gamma > 1e-12 * st[2]) || !(alpha > 0.0 && alpha < 3e38 && fabs(beta) < 3e38))) s = 1;
+      st[0] = gamma;
+      st[1] = alpha;
+      st[3] = alpha;
+      st[4] = beta;
+      stop = s;
     }
   }
   __syncthreads();
-  *a = tot[0];
-  *b = tot[1];
+  *alpha_out = st[3];
+  *beta_out = st[4];
+  const bool s = stop != 0;
   __syncthreads();
+  return s;
 }
 
 // The whole inner PCG in one cooperative launch (all blocks resident; grid-wide barriers between
@@ -326,7 +364,6 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int
     q[i] = 0.0;
   }
   grid.sync();
-  double gamma_old = 1.0, alpha_old = 1.0;
   for (int it = 0; it < iters; ++it) {
     // w = A z; partial r.z and z.w
     double ag = 0.0, ad = 0.0;
@@ -349,21 +386,8 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int
     block_sum_store(ag, part_g + blockIdx.x);
     block_sum_store(ad, part_d + blockIdx.x);
     grid.sync();
-    double gamma, delta;
-    coop_sum2(part_g, part_d, nb, &gamma, &delta);
-    // zero residual (e.g. a right-hand side that vanishes on the FEM rows): nothing left to do
-    double beta = 0.0, alpha = 0.0;
-    if (gamma != 0.0) {
-      if (it == 0 || gamma_old == 0.0 || alpha_old == 0.0) {
-        alpha = delta != 0.0 ? gamma / delta : 0.0;
-      } else {
-        beta = gamma / gamma_old;
-        const double den = delta - beta * gamma / alpha_old;
-        alpha = den != 0.0 ? gamma / den : 0.0;
-      }
-    }
-    gamma_old = gamma;
-    alpha_old = alpha;
+    double alpha, beta;
+    cg_step_scalars(part_g, part_d, nb, it, false, &alpha, &beta);
     for (int i = tid; i < nv; i += stride) {
       double pi = z[i] + beta * p[i];
       double qi = w[i] + beta * q[i];
@@ -376,6 +400,110 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop(int nv, int iters, const int
     }
     grid.sync();
   }
+}
+
+// The same iteration in float32 (the mixed precision's preconditioner: flexible GMRES needs no
+// exact inner solve, and GB300's float64 rate is 1/64 of its float32 rate): float32 matrix and
+// vectors, per-thread float32 dot partials, block and grid sums in float64, scalars in float64.
+// One block of PCG_F32_T threads per SM (at most 64 registers a thread), so that a grid barrier
+// waits on 152 blocks while 32 warps per SM hide the gathers' latency; the row products issue
+// four gathers before their FMAs.  b and the result x_out are float64.  The iteration stops
+// early at float32 rounding or before a non-finite or non-positive step: x keeps its last iterate.
+constexpr int PCG_F32_T = 1024;
+
+template <int L>
+__global__ void __launch_bounds__(PCG_F32_T, 1)
+    k_pcg_coop_f32(int nv, int iters, const int* __restrict__ ptr, const int* __restrict__ col,
+                   const float* __restrict__ val, const double* __restrict__ b, const float* __restrict__ dinv,
+                   double* __restrict__ x_out, float* __restrict__ x, float* __restrict__ r, float* __restrict__ z,
+                   float* __restrict__ p, float* __restrict__ q, float* __restrict__ w, double* __restrict__ part) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[2][PCG_F32_T / 32];
+  const int nb = gridDim.x;
+  double* part_g = part;
+  double* part_d = part + nb;
+  const int tid = blockIdx.x * PCG_F32_T + threadIdx.x, stride = nb * PCG_F32_T;
+  const int lane = threadIdx.x & (L - 1);
+  constexpr int RW = 32 / L;
+  for (int i = tid; i < nv; i += stride) {
+    const float bi = (float)b[i];
+    x[i] = 0.f;
+    r[i] = bi;
+    z[i] = dinv[i] * bi;
+    p[i] = 0.f;
+    q[i] = 0.f;
+  }
+  grid.sync();
+  for (int it = 0; it < iters; ++it) {
+    float ag = 0.f, ad = 0.f;
+    for (int base = RW * (tid >> 5); base < nv; base += RW * (stride >> 5)) {
+      const int row = base + (threadIdx.x & 31) / L;
+      const bool valid = row < nv;
+      float sacc = 0.f;
+      if (valid) {
+        int k = ptr[row] + lane;
+        const int e = ptr[row + 1];
+        for (; k + 3 * L < e; k += 4 * L) {
+          const int c0 = col[k], c1 = col[k + L], c2 = col[k + 2 * L], c3 = col[k + 3 * L];
+          const float v0 = val[k], v1 = val[k + L], v2 = val[k + 2 * L], v3 = val[k + 3 * L];
+          const float z0 = z[c0], z1 = z[c1], z2 = z[c2], z3 = z[c3];
+          sacc = fmaf(v0, z0, sacc);
+          sacc = fmaf(v1, z1, sacc);
+          sacc = fmaf(v2, z2, sacc);
+          sacc = fmaf(v3, z3, sacc);
+        }
+        for (; k < e; k += L) sacc = fmaf(val[k], z[col[k]], sacc);
+      }
+#pragma unroll
+      for (int o = L / 2; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o, L);
+      if (lane == 0 && valid) {
+        w[row] = sacc;
+        const float zr = z[row];
+        ag = fmaf(r[row], zr, ag);
+        ad = fmaf(zr, sacc, ad);
+      }
+    }
+    // block sums: warp shuffles in float32, the warps' values added in float64 in warp order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ag += __shfl_down_sync(0xffffffffu, ag, o);
+      ad += __shfl_down_sync(0xffffffffu, ad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = ag;
+      red[1][threadIdx.x >> 5] = ad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sg = 0.0, sd = 0.0;
+      for (int k = 0; k < PCG_F32_T / 32; ++k) {
+        sg += red[0][k];
+        sd += red[1][k];
+      }
+      part_g[blockIdx.x] = sg;
+      part_d[blockIdx.x] = sd;
+    }
+    grid.sync();
+    // the same decision in every block (identical sums): stop once r.z has fallen to float32
+    // rounding (1e-12 of its first value: the residual down by about 1e6), and before a
+    // non-finite or non-positive step (rounding past convergence)
+    double alpha, beta;
+    if (cg_step_scalars(part_g, part_d, nb, it, true, &alpha, &beta)) break;
+    const float a = (float)alpha, bt = (float)beta;
+    for (int i = tid; i < nv; i += stride) {
+      const float pi = fmaf(bt, p[i], z[i]);
+      const float qi = fmaf(bt, q[i], w[i]);
+      p[i] = pi;
+      q[i] = qi;
+      x[i] = fmaf(a, pi, x[i]);
+      const float ri = fmaf(-a, qi, r[i]);
+      r[i] = ri;
+      z[i] = dinv[i] * ri;
+    }
+    grid.sync();
+  }
+  for (int i = tid; i < nv; i += stride) x_out[i] = (double)x[i];
 }
 
 // The same iteration with the FEM block in sliced ELL form (slices of 32 consecutive rows, each
@@ -406,7 +534,6 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop_sell(int nv, int nslice, int
     q[i] = 0.0;
   }
   grid.sync();
-  double gamma_old = 1.0, alpha_old = 1.0;
   for (int it = 0; it < iters; ++it) {
     double ag = 0.0, ad = 0.0;
     for (int sl = gw; sl < nslice; sl += nw) {
@@ -427,20 +554,8 @@ __global__ void __launch_bounds__(PCG_T) k_pcg_coop_sell(int nv, int nslice, int
     block_sum_store(ag, part_g + blockIdx.x);
     block_sum_store(ad, part_d + blockIdx.x);
     grid.sync();
-    double gamma, delta;
-    coop_sum2(part_g, part_d, nb, &gamma, &delta);
-    double beta = 0.0, alpha = 0.0;
-    if (gamma != 0.0) {
-      if (it == 0 || gamma_old == 0.0 || alpha_old == 0.0) {
-        alpha = delta != 0.0 ? gamma / delta : 0.0;
-      } else {
-        beta = gamma / gamma_old;
-        const double den = delta - beta * gamma / alpha_old;
-        alpha = den != 0.0 ? gamma / den : 0.0;
-      }
-    }
-    gamma_old = gamma;
-    alpha_old = alpha;
+    double alpha, beta;
+    cg_step_scalars(part_g, part_d, nb, it, false, &alpha, &beta);
     for (int i = tid; i < nv; i += stride) {
       double pi = z[i] + beta * p[i];
       double qi = w[i] + beta * q[i];
@@ -626,6 +741,11 @@ int ensure(DBuf<double>& b, size_t n) {
   return b.alloc(n);
 }
 
+static int ensure_f(DBuf<float>& b, size_t n) {
+  if (b.n >= n) return PBFB_OK;
+  return b.alloc(n);
+}
+
 static int jacobi(Mesh* m, double* dinv) {
   k_jacobi<<<blocks_for(m->n, 256), 256, 0, m->stream>>>(m->nv, m->sm.nv, m->ss.nv, m->s_ptr.p, m->s_col.p,
                                                           m->s_val.p, m->full ? nullptr : m->sm.diagV.p,
@@ -705,9 +825,14 @@ static int prepare_block_precond(Mesh* m, bool dense) {
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_coop<8>, PCG_T, 0));
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, k_pcg_coop<4>, PCG_T, 0));
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_pcg_coop<2>, PCG_T, 0));
-    int per1 = 0;
+    int per1 = 0, perf8 = 0, perf4 = 0, perf2 = 0;
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_pcg_coop_sell, PCG_T, 0));
     per = std::min({per, per4, per2, per1});  // co-resident with every variant
+    // the float32 form: one block per SM
+    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf8, k_pcg_coop_f32<8>, PCG_F32_T, 0));
+    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf4, k_pcg_coop_f32<4>, PCG_F32_T, 0));
+    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf2, k_pcg_coop_f32<2>, PCG_F32_T, 0));
+    m->coop_blocks_f32 = (coop && std::min({perf8, perf4, perf2}) >= 1) ? nsm : -1;
     // all resident blocks (memory-level parallelism for the SpMV phases), but no more than
     // one pass of 8 lanes per row needs
     int want = (m->tune_pcg_bps > 0 ? std::min(per, m->tune_pcg_bps) : per) * nsm;
@@ -716,7 +841,7 @@ static int prepare_block_precond(Mesh* m, bool dense) {
   }
   PB_TRY(ensure(m->pval, m->fem_nnz));
   PB_TRY(ensure(m->pdinv, m->nv));
-  PB_TRY(ensure(m->gpart, 2 * (size_t)std::max(m->coop_blocks, 152) + 8));
+  PB_TRY(ensure(m->gpart, 2 * (size_t)std::max({m->coop_blocks, m->coop_blocks_f32, 152}) + 8));
   PB_CUDA(cudaMemcpyAsync(m->pval.p, m->s_val.p, m->fem_nnz * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
   const double c = m->eps_s * (m->kappa + 1.0 / m->gs_radius);
   if (m->nrobin) {
@@ -726,6 +851,22 @@ static int prepare_block_precond(Mesh* m, bool dense) {
   }
   k_diag_inv<<<blocks_for(m->nv, 256), 256, 0, m->stream>>>(m->nv, m->s_ptr.p, m->s_col.p, m->pval.p, m->pdinv.p);
   PB_LAUNCHED(m);
+  // the cooperative PCG in float32: by default in the mixed precision (not the sliced-ELL form)
+  const int pp = m->tune_pcg_prec;
+  m->pcg_f32 = m->coop_blocks > 0 && m->coop_blocks_f32 > 0 && m->pcg_lanes != 1 &&
+               (pp == 2 || (pp == 0 && m->precision == PBFB_MIXED));
+  if (m->pcg_f32) {
+    if (m->pcgf.n < 6 * (size_t)m->n) {
+      PB_TRY(m->pcgf.alloc(6 * (size_t)m->n));
+      PB_CUDA(cudaMemsetAsync(m->pcgf.p, 0, 6 * (size_t)m->n * sizeof(float), m->stream));
+    }
+    PB_TRY(ensure_f(m->pvalf, m->fem_nnz));
+    PB_TRY(ensure_f(m->pdinvf, m->nv));
+    k_to_f32<<<blocks_for(m->fem_nnz, 256), 256, 0, m->stream>>>(m->fem_nnz, m->pval.p, m->pvalf.p);
+    PB_LAUNCHED(m);
+    k_to_f32<<<blocks_for(m->nv, 256), 256, 0, m->stream>>>(m->nv, m->pdinv.p, m->pdinvf.p);
+    PB_LAUNCHED(m);
+  }
   if (m->coop_blocks > 0 && m->pcg_lanes == 1) {
     if (!m->sell_ok) PB_TRY(build_sell(m));
     k_sell_gather<<<blocks_for(m->sell_ne, 256), 256, 0, m->stream>>>(m->sell_ne, m->sell_map.p, m->pval.p,
@@ -818,6 +959,24 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
       void* args1[] = {&nvv, &nsl, &iters, &sp1, &sc1, &sv1, (void*)&vu, (void*)&dinv, &z, &pr, &pz, &pp, &pq,
                        &pw, &part};
       PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_coop_sell, dim3(nbc), dim3(PCG_T), args1, 0, m->stream));
+      PB_LAUNCHED(m);
+      return PBFB_OK;
+    }
+    if (m->pcg_f32) {
+      // float32 vectors, n each: the FEM rows' coupling columns (>= nv) read z there, which stays 0
+      float* fx = m->pcgf.p;
+      float* fr = fx + (size_t)n;
+      float* fz = fx + 2 * (size_t)n;
+      float* fp = fx + 3 * (size_t)n;
+      float* fq = fx + 4 * (size_t)n;
+      float* fw = fx + 5 * (size_t)n;
+      const float* fv = m->pvalf.p;
+      const float* fd = m->pdinvf.p;
+      void* argsf[] = {&nvv, &iters, &sp, &sc2, &fv, (void*)&vu, &fd, &z, &fx, &fr, &fz, &fp, &fq, &fw, &part};
+      const void* kf = m->pcg_lanes == 2   ? (const void*)k_pcg_coop_f32<2>
+                       : m->pcg_lanes == 4 ? (const void*)k_pcg_coop_f32<4>
+                                           : (const void*)k_pcg_coop_f32<8>;
+      PB_CUDA(cudaLaunchCooperativeKernel(kf, dim3(m->coop_blocks_f32), dim3(PCG_F32_T), argsf, 0, m->stream));
       PB_LAUNCHED(m);
       return PBFB_OK;
     }

@@ -107,7 +107,8 @@ class Tuning(ctypes.Structure):
                 ("nbody_packed", ctypes.c_int32), ("ff_blocks_per_sm", ctypes.c_int32),
                 ("ff_kernel", ctypes.c_int32), ("spmv_lanes", ctypes.c_int32),
                 ("spmv_block", ctypes.c_int32), ("pcg_blocks_per_sm", ctypes.c_int32),
-                ("pcg_lanes", ctypes.c_int32), ("treecode", ctypes.c_int32)]
+                ("pcg_lanes", ctypes.c_int32), ("treecode", ctypes.c_int32),
+                ("pcg_precision", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

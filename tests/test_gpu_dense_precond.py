@@ -125,18 +125,18 @@ def test_dense_errors(tiny_case):
     m.close()
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
-def test_inner_pcg_lane_variants(pair, lanes):
+@pytest.mark.parametrize("lanes,prec", [(1, 0), (2, 1), (4, 1), (8, 1), (2, 2), (4, 2), (8, 2)])
+def test_inner_pcg_lane_variants(pair, lanes, prec):
     """Every sparse-product form of the cooperative inner PCG (2, 4 or 8 lanes per CSR row, or one
-    lane per row of the sliced-ELL copy, ragged last slice included) gives a preconditioner with
-    which flexible GMRES reaches the direct solution."""
+    lane per row of the sliced-ELL copy, ragged last slice included), in float64 (1) and float32
+    (2), gives a preconditioner with which flexible GMRES reaches the direct solution."""
     from paper_2511_21713_gb300 import pbfb
     from oracle import pb
     case, m, P = pair
     m.set_params(case.eps_in, case.eps_out, case.kappa, case.T)
     base = m.get_tuning()
     try:
-        m.apply_tuning(dict(base, pcg_lanes=lanes))
+        m.apply_tuning(dict(base, pcg_lanes=lanes, pcg_precision=prec))
         u = 3.0 * np.exp(-0.3 * (np.linalg.norm(P.xyz, axis=1) - 4.0))
         m.assemble(pbfb.HS, dev(u))
         b = np.random.default_rng(14).standard_normal(P.n)
