@@ -1486,38 +1486,84 @@ __global__ void k_coulomb_qp(int nq, const double* __restrict__ qx, int ncharge,
 }
 
 // Reaction potential at the charges: (V_L lam)(x_k) - (K_L u)(x_k), 6-point rule (one block per charge).
-__global__ void k_reaction_potential(int nt, const int* __restrict__ tri, const int* __restrict__ vmap,
-                                     const double* __restrict__ qx, const double* __restrict__ qw,
-                                     const double* __restrict__ nrm, const double* __restrict__ lam,
-                                     const double* __restrict__ u, const double* __restrict__ cxyz, int ncharge,
-                                     double* __restrict__ out) {
-  int k = blockIdx.x;
-  int nq = QS * nt;
-  double px = cxyz[k], py = cxyz[ncharge + k], pz = cxyz[2 * ncharge + k];
-  double acc = 0.0;
-  for (int j = threadIdx.x; j < nq; j += blockDim.x) {
-    int t = j / QS, q = j - t * QS;
-    double lh = 0.0, uh = 0.0;
-    for (int a = 0; a < 3; ++a) {
-      int v = tri[3 * t + a];
-      lh += c_tri_b[q][a] * lam[v];
-      uh += c_tri_b[q][a] * u[vmap[v]];
-    }
-    double dx = px - qx[j], dy = py - qx[nq + j], dz = pz - qx[2 * nq + j];
-    double r2 = dx * dx + dy * dy + dz * dz;
-    double r = sqrt(r2);
-    double nd = nrm[t] * dx + nrm[nt + t] * dy + nrm[2 * nt + t] * dz;
-    acc += qw[j] * (lh / r - uh * nd / (r2 * r));
+// Reaction potentials of x_L and x_NL at the charges (Eq. Esolv's Gamma_m integral), both in one
+// pass.  k_reaction_sources: per quadrature point j of Gamma_m its position, the normal of its
+// triangle and, for both solutions, a_j = w_j lam_h(y_j) and c_j = w_j u_h(y_j) (9 values).
+// k_reaction_pairs: block (charge k, chunk of points) sums a_j / r - c_j (n_j . d) / r^3 with
+// d = x_k - y_j for both solutions (one float64 rsqrt per pair), one partial per block;
+// k_reaction_sum adds a charge's chunk partials in chunk order and scales by 1/(4 pi).
+constexpr int REAC_CHUNKS = 16;
+constexpr int REAC_T = 256;
+
+__global__ void k_reaction_sources(int nt, const int* __restrict__ tri, const int* __restrict__ vmap,
+                                   const double* __restrict__ qx, const double* __restrict__ qw,
+                                   const double* __restrict__ nrm, const double* __restrict__ lamL,
+                                   const double* __restrict__ uL, const double* __restrict__ lamN,
+                                   const double* __restrict__ uN, double* __restrict__ rec) {
+  const int nq = QS * nt;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nq) return;
+  const int t = j / QS, q = j - t * QS;
+  double lL = 0.0, lU = 0.0, nL = 0.0, nU = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const int v = tri[3 * t + a], sv = vmap[v];
+    const double b = c_tri_b[q][a];
+    lL += b * lamL[v];
+    lU += b * uL[sv];
+    nL += b * lamN[v];
+    nU += b * uN[sv];
   }
-  __shared__ double sh[32];
-  double v = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  const double w = qw[j];
+  rec[0 * (size_t)nq + j] = qx[j];
+  rec[1 * (size_t)nq + j] = qx[nq + j];
+  rec[2 * (size_t)nq + j] = qx[2 * nq + j];
+  rec[3 * (size_t)nq + j] = nrm[t];
+  rec[4 * (size_t)nq + j] = nrm[nt + t];
+  rec[5 * (size_t)nq + j] = nrm[2 * nt + t];
+  rec[6 * (size_t)nq + j] = w * lL;
+  rec[7 * (size_t)nq + j] = w * lU;
+  rec[8 * (size_t)nq + j] = w * nL;
+  rec[9 * (size_t)nq + j] = w * nU;
+}
+
+__global__ void __launch_bounds__(REAC_T) k_reaction_pairs(int nq, const double* __restrict__ rec,
+                                                           const double* __restrict__ cxyz, int ncharge,
+                                                           double* __restrict__ part) {
+  const int k = blockIdx.x, c = blockIdx.y;
+  const double px = cxyz[k], py = cxyz[ncharge + k], pz = cxyz[2 * ncharge + k];
+  const int per = (nq + REAC_CHUNKS - 1) / REAC_CHUNKS;
+  const int j0 = c * per, j1 = min(nq, j0 + per);
+  double accL = 0.0, accN = 0.0;
+  for (int j = j0 + threadIdx.x; j < j1; j += REAC_T) {
+    const double dx = px - rec[j], dy = py - rec[(size_t)nq + j], dz = pz - rec[2 * (size_t)nq + j];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double ri = rsqrt(r2);
+    const double ri3 = ri * ri * ri;
+    const double nd = rec[3 * (size_t)nq + j] * dx + rec[4 * (size_t)nq + j] * dy + rec[5 * (size_t)nq + j] * dz;
+    accL += rec[6 * (size_t)nq + j] * ri - rec[7 * (size_t)nq + j] * nd * ri3;
+    accN += rec[8 * (size_t)nq + j] * ri - rec[9 * (size_t)nq + j] * nd * ri3;
+  }
+  __shared__ double sh[2][REAC_T / 32];
+  accL = warp_sum(accL);
+  accN = warp_sum(accN);
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = accL;
+    sh[1][threadIdx.x >> 5] = accN;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 2) {
     double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    out[k] = s * INV4PI;
+    for (int w = 0; w < REAC_T / 32; ++w) s += sh[threadIdx.x][w];
+    part[((size_t)threadIdx.x * ncharge + k) * REAC_CHUNKS + c] = s;
   }
+}
+
+__global__ void k_reaction_sum(int n, const double* __restrict__ part, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < REAC_CHUNKS; ++c) s += part[(size_t)i * REAC_CHUNKS + c];
+  out[i] = s * INV4PI;
 }
 
 inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -1861,10 +1907,19 @@ int launch_coulomb(Mesh* m) {
   return test_reduce(m, s, s->val.p, 1, m->coul.p, false);
 }
 
-int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev) {
+int launch_reaction_potentials(Mesh* m, const double* xL, const double* xNL, double* ur_dev) {
   Surface* s = &m->sm;
-  k_reaction_potential<<<m->nq, 256, 0, m->stream>>>(s->nt, s->tri.p, s->vmap.p, s->qx.p, s->qw.p, s->nrm.p,
-                                                     x + s->col0, x, m->qxyz.p, m->nq, ur_dev);
+  if (m->nq == 0) return PBFB_OK;
+  PB_TRY(ensure(m->reac_rec, 10 * (size_t)s->nq));
+  PB_TRY(ensure(m->reac_part, 2 * (size_t)m->nq * REAC_CHUNKS));
+  k_reaction_sources<<<blocks_for(s->nq, 256), 256, 0, m->stream>>>(s->nt, s->tri.p, s->vmap.p, s->qx.p, s->qw.p,
+                                                                     s->nrm.p, xL + s->col0, xL, xNL + s->col0, xNL,
+                                                                     m->reac_rec.p);
+  PB_LAUNCHED(m);
+  k_reaction_pairs<<<dim3(m->nq, REAC_CHUNKS), REAC_T, 0, m->stream>>>(s->nq, m->reac_rec.p, m->qxyz.p, m->nq,
+                                                                       m->reac_part.p);
+  PB_LAUNCHED(m);
+  k_reaction_sum<<<blocks_for(2 * m->nq, 256), 256, 0, m->stream>>>(2 * m->nq, m->reac_part.p, ur_dev);
   PB_LAUNCHED(m);
   return PBFB_OK;
 }

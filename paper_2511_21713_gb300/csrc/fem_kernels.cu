@@ -212,6 +212,48 @@ __global__ void k_stiffness_local(const double* __restrict__ xyz, int nv, const 
       loc[(int64_t)sym10(a, b) * nt + t] = V * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
 }
 
+// F, F' and F'' of a scheme in float-float.  The Taylor schemes by Horner's rule on u^2 with the
+// ratios of consecutive coefficients (all terms of one sign, no cancellation):
+//   F = u (1 + u^2/6 (1 + u^2/20 (1 + u^2/42))), F' = 1 + u^2/2 (1 + u^2/12 (1 + u^2/30)),
+// cut at degree 3, 5 or 7; F'' is F one degree lower.  The sinh scheme from ff_sinh_cosh.
+PBFB_FF(FX_R6, 1.0 / 6.0);
+PBFB_FF(FX_R12, 1.0 / 12.0);
+PBFB_FF(FX_R20, 1.0 / 20.0);
+PBFB_FF(FX_R30, 1.0 / 30.0);
+PBFB_FF(FX_R42, 1.0 / 42.0);
+
+// 1 + u2 r (1 + ...): one Horner step on a float-float tail
+__device__ __forceinline__ f2 ff_horner(f2 u2, f2 r, f2 tail) {
+  return f2_add(f2{1.f, 0.f}, f2_mul(f2_mul(u2, r), tail));
+}
+
+template <int S>
+__device__ __forceinline__ void ff_scheme(f2 u, const float4* __restrict__ tab, f2& F, f2& G, f2& H) {
+  if (S == PBFB_HS) {
+    ff_sinh_cosh(u, tab, F, G);
+    H = F;
+  } else if (S == PBFB_LINEAR) {
+    F = u;
+    G = f2{1.f, 0.f};
+    H = f2{0.f, 0.f};
+  } else {
+    const f2 u2 = f2_mul(u, u);
+    const f2 one{1.f, 0.f};
+    const f2 half_u2{0.5f * u2.h, 0.5f * u2.l};
+    // odd part: degree 3 -> u (1 + u2/6); 5 -> u (1 + u2/6 (1 + u2/20)); 7 -> one more factor
+    const f2 o7 = S == PBFB_T7 ? ff_horner(u2, PBFB_FFV(FX_R42), one) : one;
+    const f2 o5 = S == PBFB_T3 ? one : ff_horner(u2, PBFB_FFV(FX_R20), o7);
+    F = f2_mul(u, ff_horner(u2, PBFB_FFV(FX_R6), o5));
+    // F'': the odd series one degree lower
+    const f2 p5 = S == PBFB_T7 ? ff_horner(u2, PBFB_FFV(FX_R20), one) : one;
+    H = S == PBFB_T3 ? u : f2_mul(u, ff_horner(u2, PBFB_FFV(FX_R6), p5));
+    // even part: 1 + u2/2 (1 + u2/12 (1 + u2/30)), cut at the scheme's degree - 1
+    const f2 e6 = S == PBFB_T7 ? ff_horner(u2, PBFB_FFV(FX_R30), one) : one;
+    const f2 e4 = S == PBFB_T3 ? one : ff_horner(u2, PBFB_FFV(FX_R12), e6);
+    G = f2_add(one, f2_mul(half_u2, e4));
+  }
+}
+
 // Jacobian (10 entries, k = 0..9) and load (4 entries) of F on one tet in float64.
 __device__ __forceinline__ void element_sums_f64(int scheme, const double (&ua)[4], double (&J)[10],
                                                  double (&N)[4]) {
@@ -295,24 +337,25 @@ __global__ void k_element_nl(int scheme, const double* __restrict__ u, const int
 }
 
 // Tets outside the float-float range take the float64 sums (kept out of line).
-__device__ __noinline__ void element_hs_fallback(const double* ua4, double sc, int64_t nt, int64_t t,
-                                                 float2* __restrict__ loc) {
+__device__ __noinline__ void element_fallback(int scheme, const double* ua4, double sc, int64_t nt, int64_t t,
+                                              float2* __restrict__ loc) {
   const double ua[4] = {ua4[0], ua4[1], ua4[2], ua4[3]};
   double J[10], N[4];
-  element_sums_f64(PBFB_HS, ua, J, N);
+  element_sums_f64(scheme, ua, J, N);
   for (int k = 0; k < 10; ++k) loc[k * nt + t] = f2_store(f2_split(sc * J[k]));
   for (int a = 0; a < 4; ++a) loc[(10 + a) * nt + t] = f2_store(f2_split(sc * N[a]));
 }
 
-// Sinh-scheme Jacobian and load of one tet in float-float, from the orbit sums:
+// Jacobian and load of one tet in float-float (scheme S), from the orbit sums:
 //   N_a  = sum_k W_k (alpha_k FS_k + delta_k f_{k,a}) + W_3 (c FS_3 + e sum_{P ∋ a} f_P)
 //   J_ab = C + h_a + h_b + [a != b] W_3 e^2 g_{ab},  J_aa = C + 2 h_a + D_a
-// with f = sinh, g = cosh at the points, FS / GS the orbit sums, C = sum W alpha^2 GS,
+// with f = F, g = F' at the points, FS / GS the orbit sums, C = sum W alpha^2 GS,
 // h_a = sum W alpha delta g_{k,a} (+ W_3 c e sum_{P ∋ a} g_P), D_a = sum W delta^2 g_{k,a}
 // (+ W_3 e^2 sum_{P ∋ a} g_P): the 14-point sums of w F l_a and w F' l_a l_b regrouped.
-__global__ void __launch_bounds__(128) k_element_hs_ff(const double* __restrict__ u, const int* __restrict__ tets,
-                                                       int64_t nt, const double* __restrict__ vol, double coef,
-                                                       const float4* __restrict__ tab, float2* __restrict__ loc) {
+template <int S>
+__global__ void __launch_bounds__(128) k_element_ff(const double* __restrict__ u, const int* __restrict__ tets,
+                                                    int64_t nt, const double* __restrict__ vol, double coef,
+                                                    const float4* __restrict__ tab, float2* __restrict__ loc) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double ua[4];
@@ -324,7 +367,7 @@ __global__ void __launch_bounds__(128) k_element_hs_ff(const double* __restrict_
   }
   const double sc = coef * vol[t];
   if (!(umax <= FX_UMAX && fabs(sc) <= 1e10)) {  // |u_q| <= max |u_a| (convex combination)
-    element_hs_fallback(ua, sc, nt, t, loc);
+    element_fallback(S, ua, sc, nt, t, loc);
     return;
   }
   f2 v[4];
@@ -337,8 +380,8 @@ __global__ void __launch_bounds__(128) k_element_hs_ff(const double* __restrict_
     f2 fs, gs;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      f2 F, G;
-      ff_sinh_cosh(f2_add(as, f2_mul(v[i], PBFB_FFV(OR_D1))), tab, F, G);
+      f2 F, G, H;
+      ff_scheme<S>(f2_add(as, f2_mul(v[i], PBFB_FFV(OR_D1))), tab, F, G, H);
       n[i] = f2_mul(F, PBFB_FFV(OR_WD1));
       h[i] = f2_mul(G, PBFB_FFV(OR_WAD1));
       D[i] = f2_mul(G, PBFB_FFV(OR_WDD1));
@@ -353,8 +396,8 @@ __global__ void __launch_bounds__(128) k_element_hs_ff(const double* __restrict_
     f2 fs, gs;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      f2 F, G;
-      ff_sinh_cosh(f2_add(as, f2_mul(v[i], PBFB_FFV(OR_D2))), tab, F, G);
+      f2 F, G, H;
+      ff_scheme<S>(f2_add(as, f2_mul(v[i], PBFB_FFV(OR_D2))), tab, F, G, H);
       n[i] = f2_add(n[i], f2_mul(F, PBFB_FFV(OR_WD2)));
       h[i] = f2_add(h[i], f2_mul(G, PBFB_FFV(OR_WAD2)));
       D[i] = f2_add(D[i], f2_mul(G, PBFB_FFV(OR_WDD2)));
@@ -371,8 +414,8 @@ __global__ void __launch_bounds__(128) k_element_hs_ff(const double* __restrict_
     for (int p = 0, P = 0; p < 3; ++p)
 #pragma unroll
       for (int q = p + 1; q < 4; ++q, ++P) {
-        f2 F, G;
-        ff_sinh_cosh(f2_add(cs, f2_mul(f2_add(v[p], v[q]), PBFB_FFV(OR_E3))), tab, F, G);
+        f2 F, G, H;
+        ff_scheme<S>(f2_add(cs, f2_mul(f2_add(v[p], v[q]), PBFB_FFV(OR_E3))), tab, F, G, H);
         const f2 fn = f2_mul(F, PBFB_FFV(OR_WE3)), gh = f2_mul(G, PBFB_FFV(OR_WCE3));
         const f2 gd = f2_mul(G, PBFB_FFV(OR_WEE3));
         n[p] = f2_add(n[p], fn);
@@ -457,11 +500,11 @@ __global__ void k_omega_elements(int scheme, const double* __restrict__ u, const
 }
 
 // Out-of-range omegas of a tet take the float64 loads (kept out of line).
-__device__ __noinline__ void omega_hs_fallback(const double* ua4, const double* da4, double om, double sc,
-                                               int64_t nt, int64_t t, float2* __restrict__ loc) {
+__device__ __noinline__ void omega_fallback(int scheme, const double* ua4, const double* da4, double om, double sc,
+                                            int64_t nt, int64_t t, float2* __restrict__ loc) {
   const double ua[4] = {ua4[0], ua4[1], ua4[2], ua4[3]}, da[4] = {da4[0], da4[1], da4[2], da4[3]};
   double R0[4], R1[4], R2[4];
-  omega_sums_f64(PBFB_HS, ua, da, om, R0, R1, R2);
+  omega_sums_f64(scheme, ua, da, om, R0, R1, R2);
   for (int a = 0; a < 4; ++a) {
     loc[(0 * 4 + a) * nt + t] = f2_store(f2_split(sc * R0[a]));
     loc[(1 * 4 + a) * nt + t] = f2_store(f2_split(sc * R1[a]));
@@ -469,14 +512,15 @@ __device__ __noinline__ void omega_hs_fallback(const double* ua4, const double* 
   }
 }
 
-// Orbit-sum accumulator of one load sum_q W_q x_q l_{q,a} = T + n_a (see k_element_hs_ff).
+// Orbit-sum accumulator of one load sum_q W_q x_q l_{q,a} = T + n_a (see k_element_ff).
 struct OrbitLoad {
   f2 T, n[4], s;
 };
 
-// Omega batch of the sinh scheme in float-float: per tet and omega the loads of F(w), F'(w) d
-// and F''(w) d^2 at w = u + omega du (F'' = F = sinh); same layout as k_omega_elements.
-__global__ void __launch_bounds__(128) k_omega_hs_ff(const double* __restrict__ u, const double* __restrict__ du,
+// Omega batch in float-float (scheme S): per tet and omega the loads of F(w), F'(w) d and
+// F''(w) d^2 at w = u + omega du; same layout as k_omega_elements.
+template <int S>
+__global__ void __launch_bounds__(128) k_omega_ff(const double* __restrict__ u, const double* __restrict__ du,
                                                      const double* __restrict__ omegas, int nomega,
                                                      const int* __restrict__ tets, int64_t nt,
                                                      const double* __restrict__ vol, double coef,
@@ -510,18 +554,18 @@ __global__ void __launch_bounds__(128) k_omega_hs_ff(const double* __restrict__ 
       w[a] = f2_split(wa);
     }
     if (!(wmax <= FX_UMAX && scale_ok)) {
-      omega_hs_fallback(ua, da, om, sc, nt, t, out);
+      omega_fallback(S, ua, da, om, sc, nt, t, out);
       continue;
     }
     const f2 sw = f2_add(f2_add(w[0], w[1]), f2_add(w[2], w[3]));
     OrbitLoad L[3];
-    // one point: x = (sinh, cosh d, sinh d^2); an S31 point adds x W delta to n_i, an S22 point
+    // one point: x = (F, F' d, F'' d^2); an S31 point adds x W delta to n_i, an S22 point
     // x W e to n_p and n_q; the orbit sums s enter T with W alpha (W c)
     auto point = [&](f2 wq, f2 dq, bool init_n, bool init_s, int i, int j, f2 wn) {
-      f2 F, G;
-      ff_sinh_cosh(wq, tab, F, G);
-      const f2 fd = f2_mul(F, dq);
-      const f2 x[3] = {F, f2_mul(G, dq), f2_mul(fd, dq)};
+      f2 F, G, H;
+      ff_scheme<S>(wq, tab, F, G, H);
+      const f2 hd = f2_mul(H, dq);
+      const f2 x[3] = {F, f2_mul(G, dq), f2_mul(hd, dq)};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const f2 m = f2_mul(x[k], wn);
@@ -738,19 +782,39 @@ static int fx_table(Mesh* m) {
   return m->fx_tab.upload(t, 2 * (2 * FX_J + 1), m->stream);
 }
 
-// The sinh scheme runs in float-float in the mixed precision; the other schemes (first
-// iterations) and the float64 precision run in float64.
-static bool use_ff(const Mesh* m, int scheme) { return m->precision != PBFB_FP64 && scheme == PBFB_HS; }
+// The mixed precision runs the element kernels in float-float, the float64 precision in float64.
+static bool use_ff(const Mesh* m, int scheme) {
+  return m->precision != PBFB_FP64 && scheme >= PBFB_LINEAR && scheme <= PBFB_T7;
+}
+
+template <int S>
+static void element_ff(Mesh* m, const double* u, double coef, float2* out) {
+  k_element_ff<S><<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(u, m->tets.p, m->nt, m->vol.p, coef, m->fx_tab.p,
+                                                                  out);
+}
+
+template <int S>
+static void omega_ff(Mesh* m, const double* u, const double* du, const double* omegas, int nomega, double coef,
+                     float2* out) {
+  k_omega_ff<S><<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(u, du, omegas, nomega, m->tets.p, m->nt, m->vol.p,
+                                                                coef, m->fx_tab.p, out);
+}
 
 int launch_element_nl(Mesh* m, int scheme, const double* u, double coef, double* loc, bool* ff) {
   cudaEvent_t ev;
   *ff = use_ff(m, scheme);
   if (*ff) PB_TRY(fx_table(m));
   timer_begin(m, m->t_elem, &ev);
-  if (*ff)
-    k_element_hs_ff<<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(u, m->tets.p, m->nt, m->vol.p, coef,
-                                                                   m->fx_tab.p, reinterpret_cast<float2*>(loc));
-  else
+  if (*ff) {
+    float2* out = reinterpret_cast<float2*>(loc);
+    switch (scheme) {
+      case PBFB_LINEAR: element_ff<PBFB_LINEAR>(m, u, coef, out); break;
+      case PBFB_T3: element_ff<PBFB_T3>(m, u, coef, out); break;
+      case PBFB_T5: element_ff<PBFB_T5>(m, u, coef, out); break;
+      case PBFB_T7: element_ff<PBFB_T7>(m, u, coef, out); break;
+      default: element_ff<PBFB_HS>(m, u, coef, out); break;
+    }
+  } else
     k_element_nl<<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(scheme, u, m->tets.p, m->nt, m->vol.p, coef, loc);
   PB_LAUNCHED(m);
   timer_end(m, m->t_elem, ev, (double)m->nt);
@@ -790,11 +854,16 @@ int launch_omega_elements(Mesh* m, int scheme, const double* u, const double* du
   *ff = use_ff(m, scheme);
   if (*ff) PB_TRY(fx_table(m));
   timer_begin(m, m->t_elem, &ev);
-  if (*ff)
-    k_omega_hs_ff<<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(u, du, omegas_dev, nomega, m->tets.p, m->nt,
-                                                                 m->vol.p, coef, m->fx_tab.p,
-                                                                 reinterpret_cast<float2*>(loc));
-  else
+  if (*ff) {
+    float2* out = reinterpret_cast<float2*>(loc);
+    switch (scheme) {
+      case PBFB_LINEAR: omega_ff<PBFB_LINEAR>(m, u, du, omegas_dev, nomega, coef, out); break;
+      case PBFB_T3: omega_ff<PBFB_T3>(m, u, du, omegas_dev, nomega, coef, out); break;
+      case PBFB_T5: omega_ff<PBFB_T5>(m, u, du, omegas_dev, nomega, coef, out); break;
+      case PBFB_T7: omega_ff<PBFB_T7>(m, u, du, omegas_dev, nomega, coef, out); break;
+      default: omega_ff<PBFB_HS>(m, u, du, omegas_dev, nomega, coef, out); break;
+    }
+  } else
     k_omega_elements<<<blocks_for(m->nt, 128), 128, 0, m->stream>>>(scheme, u, du, omegas_dev, nomega, m->tets.p,
                                                                     m->nt, m->vol.p, coef, loc);
   PB_LAUNCHED(m);

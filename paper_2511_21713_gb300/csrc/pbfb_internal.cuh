@@ -211,6 +211,7 @@ struct Mesh {
   DBuf<double> pval, pdinv;
   DBuf<float> pvalf, pdinvf;        // float32 copies for the mixed precision's cooperative PCG
   DBuf<float> pcgf;                 // its vectors x, r, z, p, q, w (n each; z stays 0 past nv)
+  DBuf<double> reac_rec, reac_part; // reaction potentials: Gamma_m point records, chunk partials
   bool pcg_f32 = false;             // the cooperative PCG runs in float32
   int tune_pcg_prec = 0;            // its arithmetic: 0 built-in (float32 in MIXED), 1 float64, 2 float32
   double gs_radius = 1.0;           // sqrt(|Gamma_s| / 4 pi)
@@ -329,7 +330,8 @@ int launch_bem_far(Mesh* m, Surface* s, const double* x, const double* lam, doub
 int launch_bem_far_ff(Mesh* m, Surface* s, const double* x, const double* lam, double cs, double cd,
                       double kappa, double* y, bool accumulate);
 int launch_coulomb(Mesh* m);
-int launch_reaction_potential(Mesh* m, const double* x, double* ur_dev);
+// reaction potentials of x_L and x_NL at the charges: ur_dev[0, nq) and ur_dev[nq, 2 nq)
+int launch_reaction_potentials(Mesh* m, const double* xL, const double* xNL, double* ur_dev);
 int bem_apply_noalloc(Mesh* m, int which, int op, const double* x, double* y);
 
 // ---- treecode.cu: hierarchical float32 far field

@@ -1535,8 +1535,7 @@ static int gamma_m_flux(Mesh* m, const double* x, bool coulomb, double* lam) {
 static int energy(Mesh* m, const double* xL, const double* xNL, double* out4) {
   PB_TRY(ensure(m->tmp, m->n));
   PB_TRY(ensure(m->urb, 2 * (size_t)m->nq));
-  PB_TRY(launch_reaction_potential(m, xL, m->urb.p));
-  PB_TRY(launch_reaction_potential(m, xNL, m->urb.p + m->nq));
+  PB_TRY(launch_reaction_potentials(m, xL, xNL, m->urb.p));
   std::vector<double> urh(2 * (size_t)m->nq);
   PB_CUDA(cudaMemcpyAsync(urh.data(), m->urb.p, urh.size() * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   // ion term on u = (x_L + x_NL) restricted to the shell
