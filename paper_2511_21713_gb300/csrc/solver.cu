@@ -506,6 +506,110 @@ __global__ void __launch_bounds__(PCG_F32_T, 1)
   for (int i = tid; i < nv; i += stride) x_out[i] = (double)x[i];
 }
 
+// The float32 form with everything but z resident in registers, for blocks of at most
+// PCG_RES_ROWS rows per SM: a pair of lanes owns one row for the whole solve (its row of the FEM
+// block, at most PCG_RES_CAP entries per lane, in registers; longer rows read the rest each step),
+// and lane 0 of the pair keeps the row's x, r, p, q and diagonal; only z goes through memory, for
+// the gathers of the other rows.  A step is then one round of gathers, the block and grid sums,
+// and the register update.  Columns past nv (the coupling to the surface rows) are dropped.
+constexpr int PCG_RES_CAP = 8;
+constexpr int PCG_RES_ROWS = PCG_F32_T / 2;
+
+__global__ void __launch_bounds__(PCG_F32_T, 1)
+    k_pcg_res_f32(int nv, int iters, const int* __restrict__ ptr, const int* __restrict__ col,
+                  const float* __restrict__ val, const double* __restrict__ b, const float* __restrict__ dinv,
+                  double* __restrict__ x_out, float* __restrict__ zg, double* __restrict__ part) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[2][PCG_F32_T / 32];
+  const int nb = gridDim.x;
+  const int lane = threadIdx.x & 1;
+  const int row = blockIdx.x * PCG_RES_ROWS + (threadIdx.x >> 1);
+  const bool valid = row < nv;
+  int cidx[PCG_RES_CAP];
+  float cval[PCG_RES_CAP];
+  int k_more = 0, k_end = 0;  // entries past the register capacity: [k_more, k_end) step 2
+  float x = 0.f, r = 0.f, p = 0.f, q = 0.f, di = 0.f, zi = 0.f;
+  if (valid) {
+    const int k0 = ptr[row] + lane, e = ptr[row + 1];
+#pragma unroll
+    for (int u = 0; u < PCG_RES_CAP; ++u) {
+      const int k = k0 + 2 * u;
+      const int c = k < e ? col[k] : nv;
+      cidx[u] = c < nv ? c : row;
+      cval[u] = c < nv ? val[k] : 0.f;
+    }
+    k_more = k0 + 2 * PCG_RES_CAP;
+    k_end = e;
+    if (lane == 0) {
+      r = (float)b[row];
+      di = dinv[row];
+      zi = di * r;
+      zg[row] = zi;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < PCG_RES_CAP; ++u) {
+      cidx[u] = 0;
+      cval[u] = 0.f;
+    }
+  }
+  grid.sync();
+  for (int it = 0; it < iters; ++it) {
+    float w = 0.f;
+    if (valid) {
+      float zv[PCG_RES_CAP];
+#pragma unroll
+      for (int u = 0; u < PCG_RES_CAP; ++u) zv[u] = zg[cidx[u]];
+#pragma unroll
+      for (int u = 0; u < PCG_RES_CAP; ++u) w = fmaf(cval[u], zv[u], w);
+      for (int k = k_more; k < k_end; k += 2) {
+        const int c = col[k];
+        if (c < nv) w = fmaf(val[k], zg[c], w);
+      }
+    }
+    w += __shfl_down_sync(0xffffffffu, w, 1);
+    float ag = 0.f, ad = 0.f;
+    if (valid && lane == 0) {
+      ag = r * zi;
+      ad = zi * w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ag += __shfl_down_sync(0xffffffffu, ag, o);
+      ad += __shfl_down_sync(0xffffffffu, ad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = ag;
+      red[1][threadIdx.x >> 5] = ad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sg = 0.0, sd = 0.0;
+      for (int k = 0; k < PCG_F32_T / 32; ++k) {
+        sg += red[0][k];
+        sd += red[1][k];
+      }
+      part[blockIdx.x] = sg;
+      part[nb + blockIdx.x] = sd;
+    }
+    grid.sync();
+    double alpha, beta;
+    if (cg_step_scalars(part, part + nb, nb, it, true, &alpha, &beta)) break;
+    if (valid && lane == 0) {
+      const float a = (float)alpha, bt = (float)beta;
+      p = fmaf(bt, p, zi);
+      q = fmaf(bt, q, w);
+      x = fmaf(a, p, x);
+      r = fmaf(-a, q, r);
+      zi = di * r;
+      zg[row] = zi;
+    }
+    grid.sync();
+  }
+  if (valid && lane == 0) x_out[row] = (double)x;
+}
+
 // The same iteration with the FEM block in sliced ELL form (slices of 32 consecutive rows, each
 // stored column by column at the slice's largest row length, padding entries with value 0): a
 // warp takes a slice, a lane a row, so the value and column loads are coalesced and the products
@@ -832,7 +936,9 @@ static int prepare_block_precond(Mesh* m, bool dense) {
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf8, k_pcg_coop_f32<8>, PCG_F32_T, 0));
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf4, k_pcg_coop_f32<4>, PCG_F32_T, 0));
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf2, k_pcg_coop_f32<2>, PCG_F32_T, 0));
-    m->coop_blocks_f32 = (coop && std::min({perf8, perf4, perf2}) >= 1) ? nsm : -1;
+    int perr = 0;
+    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perr, k_pcg_res_f32, PCG_F32_T, 0));
+    m->coop_blocks_f32 = (coop && std::min({perf8, perf4, perf2, perr}) >= 1) ? nsm : -1;
     // all resident blocks (memory-level parallelism for the SpMV phases), but no more than
     // one pass of 8 lanes per row needs
     int want = (m->tune_pcg_bps > 0 ? std::min(per, m->tune_pcg_bps) : per) * nsm;
@@ -973,6 +1079,14 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
       const float* fv = m->pvalf.p;
       const float* fd = m->pdinvf.p;
       void* argsf[] = {&nvv, &iters, &sp, &sc2, &fv, (void*)&vu, &fd, &z, &fx, &fr, &fz, &fp, &fq, &fw, &part};
+      if (nv <= PCG_RES_ROWS * m->coop_blocks_f32) {
+        int nbr = (nv + PCG_RES_ROWS - 1) / PCG_RES_ROWS;
+        void* argsr[] = {&nvv, &iters, &sp, &sc2, &fv, (void*)&vu, &fd, &z, &fz, &part};
+        PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_res_f32, dim3(nbr), dim3(PCG_F32_T), argsr, 0,
+                                            m->stream));
+        PB_LAUNCHED(m);
+        return PBFB_OK;
+      }
       const void* kf = m->pcg_lanes == 2   ? (const void*)k_pcg_coop_f32<2>
                        : m->pcg_lanes == 4 ? (const void*)k_pcg_coop_f32<4>
                                            : (const void*)k_pcg_coop_f32<8>;

@@ -35,8 +35,9 @@ constexpr int TREE_NT = 128;                 // threads per block; two targets e
 constexpr int TREE_LEAF = 2 * TREE_NT;       // targets per leaf (at most)
 constexpr int TREE_P = 6;                    // interpolation degree per dimension
 constexpr int TREE_K = TREE_P + 1;           // Chebyshev points per dimension
-constexpr int TREE_NPX = TREE_K * TREE_K * TREE_K;  // proxies per cluster (343)
+constexpr int TREE_NPX = TREE_K * TREE_K * TREE_K;  // proxies per cluster
 constexpr int TREE_UP_NT = 352;              // threads of the upward pass (>= TREE_NPX, whole warps)
+static_assert(TREE_UP_NT >= TREE_NPX && TREE_UP_NT % 32 == 0, "one upward-pass thread per proxy");
 constexpr int TREE_TILES_PER_CHUNK = 8;      // source tiles per block
 constexpr double TREE_THETA = 0.6;           // acceptance: r_B + r_C < theta |c_B - c_C|
 
@@ -56,7 +57,7 @@ __global__ void k_tree_permute(int nq, const int* __restrict__ perm, const float
 // sum_j L_a(x_j) L_b(y_j) L_c(z_j) (s_j, m_j) over the segment's points, the 1-D values from the
 // barycentric formula l_a(x) = (w_a / (x - t_a)) / sum_m (w_m / (x - t_m)), w_m = (-1)^m (halved at
 // both ends), or the unit vector when x coincides with a node.  The basis values sit point-major
-// (lw[d][j][a]), so the 343 proxy threads of a warp read at most 7 consecutive words per point
+// (lw[d][j][a]), so the (p+1)^3 proxy threads of a warp read at most p+1 consecutive words per point
 // (no bank conflicts).  The block that completes a cluster's last segment (a per-cluster arrival
 // counter) adds the cluster's segments in index order and writes its proxy source records, then
 // re-arms the counter: the result does not depend on which block arrives last.
@@ -84,10 +85,10 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ 
   const int t = threadIdx.x;
   if (t < 3 * TREE_K) node[t / TREE_K][t % TREE_K] = cheb_node(cbox, c, t / TREE_K, t % TREE_K);
   __syncthreads();
-  if (t < cnt) {
-    const float4 p = pts_pos[b + t];
-    const float4 q = pts_dl[b + t];
-    src[t] = make_float4(p.w, q.x, q.y, q.z);
+  for (int j = t; j < cnt; j += TREE_UP_NT) {
+    const float4 p = pts_pos[b + j];
+    const float4 q = pts_dl[b + j];
+    src[j] = make_float4(p.w, q.x, q.y, q.z);
     const float xs[3] = {p.x, p.y, p.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ 
       }
       const float rden = __frcp_rn(den);
 #pragma unroll
-      for (int k = 0; k < TREE_K; ++k) lw[d][t][k] = hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] * rden;
+      for (int k = 0; k < TREE_K; ++k) lw[d][j][k] = hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] * rden;
     }
   }
   __syncthreads();
