@@ -274,7 +274,7 @@ def run_pbfb(args):
     # launch shapes picked by the autotuner on this mesh (outside the timed region)
     mesh.set_params(case.eps_in, case.eps_out, case.kappa, case.T, prec)
     t_tune = time.perf_counter()
-    tuned, tuned_ms = mesh.autotune(reps=3)
+    tuned, tuned_ms = mesh.autotune(reps=3, cache_file=args.tune_cache)
     tune_s = time.perf_counter() - t_tune
     x_out = torch.empty(mesh.n, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
@@ -954,6 +954,9 @@ def main():
     ap.add_argument("--budget-gb", type=int, default=160, help="--config serving: HBM budget")
     ap.add_argument("--fp64-max-tri", type=int, default=8000,
                     help="--config serving: largest surface (triangles) of the float64 arm")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of autotuned shapes (read if it holds this GPU and size bucket, else "
+                         "written): a profiling run under ncu then uses the shapes of the plain run")
     ap.add_argument("--residual-far", default="f32", choices=["float2", "f32"],
                     help="far field of the Newton residual's full evaluations (pbfb_newton_opts.residual_far)")
     ap.add_argument("--residual-update", type=float, default=0.5,

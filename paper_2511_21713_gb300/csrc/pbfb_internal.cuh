@@ -217,6 +217,7 @@ struct Mesh {
   double gs_radius = 1.0;           // sqrt(|Gamma_s| / 4 pi)
   int coop_blocks = 0;              // grid of the cooperative inner PCG (-1: not available)
   int coop_blocks_f32 = 0;          // grid of its float32 form (one block per SM; -1: not available)
+  int coop_blocks_pipe = 0;         // blocks of its register-resident pipelined form (one per SM)
   bool no_coop = false;             // never use the grid-barrier PCG (meshes solved concurrently)
   int tune_tpt = 0;                 // float32 far field: targets per thread (0 = heuristic)
   int tune_bps = 0;                 // float32 far field: target blocks per SM for the source split

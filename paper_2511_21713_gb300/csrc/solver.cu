@@ -273,56 +273,72 @@ __global__ void k_diag_inv(int nv, const int* __restrict__ ptr, const int* __res
   dinv[r] = 1.0 / d;
 }
 
+// One thread's part of a step's scalars: alpha and beta from gamma = (r, z) and delta = (z, w) and
+// the recurrence state st = {gamma_old, alpha_old, gamma_0} (st[3], st[4] receive alpha and beta).
+// f32_rules adds the float32 forms' stops: r.z at 1e-12 of its first value, or a non-positive or
+// huge alpha.  A zero r.z (e.g. a right-hand side that vanishes on the FEM rows) gives
+// alpha = beta = 0: nothing left to do.  Returns 1 to stop before this step's update.
+__device__ __forceinline__ int cg_scalars_lane0(double gamma, double delta, int it, bool f32_rules, double* st) {
+  if (it == 0) {
+    st[0] = 1.0;
+    st[1] = 1.0;
+    st[2] = gamma;
+  }
+  const double gamma_old = st[0], alpha_old = st[1];
+  double beta = 0.0, alpha = 0.0;
+  if (gamma != 0.0) {
+    if (it == 0 || gamma_old == 0.0 || alpha_old == 0.0) {
+      alpha = delta != 0.0 ? gamma / delta : 0.0;
+    } else {
+      beta = gamma / gamma_old;
+      const double den = delta - beta * gamma / alpha_old;
+      alpha = den != 0.0 ? gamma / den : 0.0;
+    }
+  }
+  int s = 0;
+  if (f32_rules && (!(gamma > 1e-12 * st[2]) || !(alpha > 0.0 && alpha < 3e38 && fabs(beta) < 3e38))) s = 1;
+  st[0] = gamma;
+  st[1] = alpha;
+  st[3] = alpha;
+  st[4] = beta;
+  return s;
+}
+
 // The scalars of a Chronopoulos-Gear step from the two grid sums: warp 0 of every block reads the
 // per-block partials lane-strided (lane l sums entries l, l + 32, ... in that order), then a
 // butterfly over the 32 lanes, so every block obtains the same two sums; lane 0 alone takes the
-// divisions and the stop rules, and the block
-// reads alpha and beta from shared memory (GB300's float64 rate makes two divisions in every
-// thread of the grid the larger part of a step).  The recurrence state (gamma_old, alpha_old,
-// gamma_0) lives in shared memory, so every block evolves it identically.  f32_rules adds the
-// float32 form's stops: r.z at 1e-12 of its first value, or a non-positive or huge alpha.
-// Returns true when the iteration is to stop before this step's update.  A zero r.z (e.g. a
-// right-hand side that vanishes on the FEM rows) gives alpha = beta = 0: nothing left to do.
+// divisions and the stop rules (cg_scalars_lane0), and the block reads alpha and beta from shared
+// memory (GB300's float64 rate makes two divisions in every thread of the grid the larger part of
+// a step).  The recurrence state lives in shared memory, so every block evolves it identically.
+// Returns true when the iteration is to stop before this step's update.
 __device__ __forceinline__ bool cg_step_scalars(const double* pa, const double* pb, int nb, int it, bool f32_rules,
                                                 double* alpha_out, double* beta_out) {
   __shared__ double st[5];  // gamma_old, alpha_old, gamma_0, alpha, beta
   __shared__ int stop;
   if (threadIdx.x < 32) {
+    // lane l adds entries l, l + 32, ... in that order, loaded 8 at a time (independent loads)
     double sa = 0.0, sb = 0.0;
-    for (int k = threadIdx.x; k < nb; k += 32) {
-      sa += pa[k];
-      sb += pb[k];
+    for (int k0 = threadIdx.x; k0 < nb; k0 += 32 * 8) {
+      double va[8], vb[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + 32 * u;
+        va[u] = k < nb ? pa[k] : 0.0;
+        vb[u] = k < nb ? pb[k] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (k0 + 32 * u < nb) {
+          sa += va[u];
+          sb += vb[u];
+        }
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       sa += __shfl_xor_sync(0xffffffffu, sa, o);
       sb += __shfl_xor_sync(0xffffffffu, sb, o);
     }
-    if (threadIdx.x == 0) {
-      const double gamma = sa, delta = sb;
-      if (it == 0) {
-        st[0] = 1.0;
-        st[1] = 1.0;
-        st[2] = gamma;
-      }
-      const double gamma_old = st[0], alpha_old = st[1];
-      double beta = 0.0, alpha = 0.0;
-      if (gamma != 0.0) {
-        if (it == 0 || gamma_old == 0.0 || alpha_old == 0.0) {
-          alpha = delta != 0.0 ? gamma / delta : 0.0;
-        } else {
-          beta = gamma / gamma_old;
-          const double den = delta - beta * gamma / alpha_old;
-          alpha = den != 0.0 ? gamma / den : 0.0;
-        }
-      }
-      int s = 0;
-      if (f32_rules && (!(gamma > 1e-12 * st[2]) || !(alpha > 0.0 && alpha < 3e38 && fabs(beta) < 3e38))) s = 1;
-      st[0] = gamma;
-      st[1] = alpha;
-      st[3] = alpha;
-      st[4] = beta;
-      stop = s;
-    }
+    if (threadIdx.x == 0) stop = cg_scalars_lane0(sa, sb, it, f32_rules, st);
   }
   __syncthreads();
   *alpha_out = st[3];
@@ -506,108 +522,180 @@ __global__ void __launch_bounds__(PCG_F32_T, 1)
   for (int i = tid; i < nv; i += stride) x_out[i] = (double)x[i];
 }
 
-// The float32 form with everything but z resident in registers, for blocks of at most
-// PCG_RES_ROWS rows per SM: a pair of lanes owns one row for the whole solve (its row of the FEM
-// block, at most PCG_RES_CAP entries per lane, in registers; longer rows read the rest each step),
-// and lane 0 of the pair keeps the row's x, r, p, q and diagonal; only z goes through memory, for
-// the gathers of the other rows.  A step is then one round of gathers, the block and grid sums,
-// and the register update.  Columns past nv (the coupling to the surface rows) are dropped.
-constexpr int PCG_RES_CAP = 8;
-constexpr int PCG_RES_ROWS = PCG_F32_T / 2;
+// The float32 form with its state resident in registers, for meshes of at most PCG_RES_ROWS rows
+// per SM, in the pipelined form of Ghysels and Vanroose (2014): with u = M r, w = A u, m = M w and
+// n = A m, every vector is updated by its own recurrence (z = n + beta z, q = m + beta q,
+// s = w + beta s, p = u + beta p; x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z), so that
+// the dot products of the next step, (r, u) and (w, u), are taken right after an update and pass
+// the same grid barrier as m: one barrier per step instead of two.  Same iterates as the
+// Chronopoulos-Gear form in exact arithmetic.  Warp 0 of a block owns no rows: while warps 1..31
+// gather m for their row products, it adds the block partials of the step's two dots and takes
+// the scalars (cg_step_scalars' arithmetic), so the float64 sums and divisions stay off the
+// critical path.  A thread owns one row for the whole solve: its row of the FEM block (at most
+// PCG_RES_CAP entries in registers; longer rows read the rest each step; the coupling columns past
+// nv are dropped) and its x, r, u, w, m, z, q, s, p and diagonal.  Blocks of 1 + 15 warps, one
+// per SM (4 warps per SM sub-partition: up to 128 registers a thread).  m and the block partials are double-buffered by step parity: a step reads one buffer
+// while it writes the other, and the barrier separates the two uses.
+// one row's product with a vector in global memory: the register-held entries, then the rest
+__device__ __forceinline__ float pipe_row_product(const int (&cidx)[16], const float (&cval)[16], int k_more,
+                                                  int k_end, const int* __restrict__ col,
+                                                  const float* __restrict__ val, int nv,
+                                                  const float* __restrict__ v) {
+  float g[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) g[t] = v[cidx[t]];
+  float acc = 0.f;
+#pragma unroll
+  for (int t = 0; t < 16; ++t) acc = fmaf(cval[t], g[t], acc);
+  for (int k = k_more; k < k_end; ++k) {
+    const int c = col[k];
+    if (c < nv) acc = fmaf(val[k], v[c], acc);
+  }
+  return acc;
+}
 
-__global__ void __launch_bounds__(PCG_F32_T, 1)
-    k_pcg_res_f32(int nv, int iters, const int* __restrict__ ptr, const int* __restrict__ col,
-                  const float* __restrict__ val, const double* __restrict__ b, const float* __restrict__ dinv,
-                  double* __restrict__ x_out, float* __restrict__ zg, double* __restrict__ part) {
+constexpr int PCG_RES_CAP = 16;  // (pipe_row_product's register entries)
+constexpr int PCG_RES_ROWS = 480;
+constexpr int PCG_PIPE_T = 32 + PCG_RES_ROWS;
+
+__global__ void __launch_bounds__(PCG_PIPE_T, 1)
+    k_pcg_pipe_f32(int nv, int iters, const int* __restrict__ ptr, const int* __restrict__ col,
+                   const float* __restrict__ val, const double* __restrict__ b, const float* __restrict__ dinv,
+                   double* __restrict__ x_out, float* __restrict__ mbuf, float* __restrict__ ubuf,
+                   double* __restrict__ part) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  __shared__ double red[2][PCG_F32_T / 32];
+  __shared__ float red[2][PCG_PIPE_T / 32];
+  __shared__ double st[5];
+  __shared__ int stop;
   const int nb = gridDim.x;
-  const int lane = threadIdx.x & 1;
-  const int row = blockIdx.x * PCG_RES_ROWS + (threadIdx.x >> 1);
-  const bool valid = row < nv;
+  const int warp = threadIdx.x >> 5;
+  const int row = blockIdx.x * PCG_RES_ROWS + (int)threadIdx.x - 32;
+  const bool valid = warp > 0 && row < nv;
+  const bool owner = valid;
   int cidx[PCG_RES_CAP];
   float cval[PCG_RES_CAP];
-  int k_more = 0, k_end = 0;  // entries past the register capacity: [k_more, k_end) step 2
-  float x = 0.f, r = 0.f, p = 0.f, q = 0.f, di = 0.f, zi = 0.f;
+  int k_more = 0, k_end = 0;  // entries past the register capacity: [k_more, k_end)
+  float x = 0.f, r = 0.f, u = 0.f, w = 0.f, m = 0.f, z = 0.f, q = 0.f, sv = 0.f, p = 0.f, di = 0.f;
   if (valid) {
-    const int k0 = ptr[row] + lane, e = ptr[row + 1];
+    const int k0 = ptr[row], e = ptr[row + 1];
 #pragma unroll
-    for (int u = 0; u < PCG_RES_CAP; ++u) {
-      const int k = k0 + 2 * u;
+    for (int t = 0; t < PCG_RES_CAP; ++t) {
+      const int k = k0 + t;
       const int c = k < e ? col[k] : nv;
-      cidx[u] = c < nv ? c : row;
-      cval[u] = c < nv ? val[k] : 0.f;
+      cidx[t] = c < nv ? c : row;
+      cval[t] = c < nv ? val[k] : 0.f;
     }
-    k_more = k0 + 2 * PCG_RES_CAP;
+    k_more = k0 + PCG_RES_CAP;
     k_end = e;
-    if (lane == 0) {
-      r = (float)b[row];
-      di = dinv[row];
-      zi = di * r;
-      zg[row] = zi;
-    }
   } else {
 #pragma unroll
-    for (int u = 0; u < PCG_RES_CAP; ++u) {
-      cidx[u] = 0;
-      cval[u] = 0.f;
+    for (int t = 0; t < PCG_RES_CAP; ++t) {
+      cidx[t] = 0;
+      cval[t] = 0.f;
     }
   }
-  grid.sync();
-  for (int it = 0; it < iters; ++it) {
-    float w = 0.f;
-    if (valid) {
-      float zv[PCG_RES_CAP];
-#pragma unroll
-      for (int u = 0; u < PCG_RES_CAP; ++u) zv[u] = zg[cidx[u]];
-#pragma unroll
-      for (int u = 0; u < PCG_RES_CAP; ++u) w = fmaf(cval[u], zv[u], w);
-      for (int k = k_more; k < k_end; k += 2) {
-        const int c = col[k];
-        if (c < nv) w = fmaf(val[k], zg[c], w);
-      }
-    }
-    w += __shfl_down_sync(0xffffffffu, w, 1);
-    float ag = 0.f, ad = 0.f;
-    if (valid && lane == 0) {
-      ag = r * zi;
-      ad = zi * w;
-    }
+  // block sums of (r, u) and (w, u) into the partials of buffer `buf` (warp sums in float32, the
+  // warps' values added in float64 in warp order by warp 0)
+  auto block_dots = [&](int buf) {
+    float ag = owner ? r * u : 0.f, ad = owner ? w * u : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       ag += __shfl_down_sync(0xffffffffu, ag, o);
       ad += __shfl_down_sync(0xffffffffu, ad, o);
     }
     if ((threadIdx.x & 31) == 0) {
-      red[0][threadIdx.x >> 5] = ag;
-      red[1][threadIdx.x >> 5] = ad;
+      red[0][warp] = ag;
+      red[1][warp] = ad;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double sg = 0.0, sd = 0.0;
-      for (int k = 0; k < PCG_F32_T / 32; ++k) {
-        sg += red[0][k];
-        sd += red[1][k];
+    if (warp == 0) {
+      const bool in = threadIdx.x < PCG_PIPE_T / 32;
+      double sg = in ? red[0][threadIdx.x] : 0.0, sd = in ? red[1][threadIdx.x] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
       }
-      part[blockIdx.x] = sg;
-      part[nb + blockIdx.x] = sd;
+      if (threadIdx.x == 0) {
+        part[(size_t)buf * 2 * nb + blockIdx.x] = sg;
+        part[(size_t)buf * 2 * nb + nb + blockIdx.x] = sd;
+      }
     }
-    grid.sync();
-    double alpha, beta;
-    if (cg_step_scalars(part, part + nb, nb, it, true, &alpha, &beta)) break;
-    if (valid && lane == 0) {
-      const float a = (float)alpha, bt = (float)beta;
-      p = fmaf(bt, p, zi);
-      q = fmaf(bt, q, w);
-      x = fmaf(a, p, x);
-      r = fmaf(-a, q, r);
-      zi = di * r;
-      zg[row] = zi;
+  };
+  // warp 0: the grid sums of buffer `buf` and the scalars of step it into st[3], st[4]
+  auto scalars = [&](int buf, int it) {
+    const double* pa = part + (size_t)buf * 2 * nb;
+    const double* pb = pa + nb;
+    double sa = 0.0, sb = 0.0;
+    for (int k0 = threadIdx.x; k0 < nb; k0 += 32 * 8) {
+      double va[8], vb[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int k = k0 + 32 * t;
+        va[t] = k < nb ? pa[k] : 0.0;
+        vb[t] = k < nb ? pb[k] : 0.0;
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (k0 + 32 * t < nb) {
+          sa += va[t];
+          sb += vb[t];
+        }
+      }
     }
-    grid.sync();
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if (threadIdx.x == 0) stop = cg_scalars_lane0(sa, sb, it, true, st);
+  };
+  // x = 0, r = b, u = M r; w = A u; m = M w
+  if (owner) {
+    di = dinv[row];
+    r = (float)b[row];
+    u = di * r;
+    ubuf[row] = u;
   }
-  if (valid && lane == 0) x_out[row] = (double)x;
+  grid.sync();
+  {
+    const float wu = valid ? pipe_row_product(cidx, cval, k_more, k_end, col, val, nv, ubuf) : 0.f;
+    if (owner) {
+      w = wu;
+      m = di * w;
+      mbuf[row] = m;
+    }
+  }
+  block_dots(0);
+  grid.sync();
+  for (int it = 0; it < iters; ++it) {
+    const int cur = it & 1, nxt = cur ^ 1;
+    float n = 0.f;
+    if (warp == 0)
+      scalars(cur, it);
+    else
+      n = valid ? pipe_row_product(cidx, cval, k_more, k_end, col, val, nv, mbuf + (size_t)cur * nv) : 0.f;
+    __syncthreads();
+    if (stop) break;  // identical sums in every block: the same decision everywhere
+    if (owner) {
+      const float a = (float)st[3], bt = (float)st[4];
+      z = fmaf(bt, z, n);
+      q = fmaf(bt, q, m);
+      sv = fmaf(bt, sv, w);
+      p = fmaf(bt, p, u);
+      x = fmaf(a, p, x);
+      r = fmaf(-a, sv, r);
+      u = fmaf(-a, q, u);
+      w = fmaf(-a, z, w);
+      m = di * w;
+      mbuf[(size_t)nxt * nv + row] = m;
+    }
+    if (it + 1 < iters) {
+      block_dots(nxt);
+      grid.sync();
+    }
+  }
+  if (owner) x_out[row] = (double)x;
 }
 
 // The same iteration with the FEM block in sliced ELL form (slices of 32 consecutive rows, each
@@ -936,9 +1024,10 @@ static int prepare_block_precond(Mesh* m, bool dense) {
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf8, k_pcg_coop_f32<8>, PCG_F32_T, 0));
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf4, k_pcg_coop_f32<4>, PCG_F32_T, 0));
     PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf2, k_pcg_coop_f32<2>, PCG_F32_T, 0));
+    m->coop_blocks_f32 = (coop && std::min({perf8, perf4, perf2}) >= 1) ? nsm : -1;
     int perr = 0;
-    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perr, k_pcg_res_f32, PCG_F32_T, 0));
-    m->coop_blocks_f32 = (coop && std::min({perf8, perf4, perf2, perr}) >= 1) ? nsm : -1;
+    PB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perr, k_pcg_pipe_f32, PCG_PIPE_T, 0));
+    m->coop_blocks_pipe = (coop && perr >= 1) ? nsm : 0;
     // all resident blocks (memory-level parallelism for the SpMV phases), but no more than
     // one pass of 8 lanes per row needs
     int want = (m->tune_pcg_bps > 0 ? std::min(per, m->tune_pcg_bps) : per) * nsm;
@@ -947,7 +1036,7 @@ static int prepare_block_precond(Mesh* m, bool dense) {
   }
   PB_TRY(ensure(m->pval, m->fem_nnz));
   PB_TRY(ensure(m->pdinv, m->nv));
-  PB_TRY(ensure(m->gpart, 2 * (size_t)std::max({m->coop_blocks, m->coop_blocks_f32, 152}) + 8));
+  PB_TRY(ensure(m->gpart, 4 * (size_t)std::max({m->coop_blocks, m->coop_blocks_f32, 152}) + 8));
   PB_CUDA(cudaMemcpyAsync(m->pval.p, m->s_val.p, m->fem_nnz * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
   const double c = m->eps_s * (m->kappa + 1.0 / m->gs_radius);
   if (m->nrobin) {
@@ -966,6 +1055,7 @@ static int prepare_block_precond(Mesh* m, bool dense) {
       PB_TRY(m->pcgf.alloc(6 * (size_t)m->n));
       PB_CUDA(cudaMemsetAsync(m->pcgf.p, 0, 6 * (size_t)m->n * sizeof(float), m->stream));
     }
+
     PB_TRY(ensure_f(m->pvalf, m->fem_nnz));
     PB_TRY(ensure_f(m->pdinvf, m->nv));
     k_to_f32<<<blocks_for(m->fem_nnz, 256), 256, 0, m->stream>>>(m->fem_nnz, m->pval.p, m->pvalf.p);
@@ -1079,10 +1169,12 @@ static int block_precond(Mesh* m, const double* v, double* z, int inner_iters) {
       const float* fv = m->pvalf.p;
       const float* fd = m->pdinvf.p;
       void* argsf[] = {&nvv, &iters, &sp, &sc2, &fv, (void*)&vu, &fd, &z, &fx, &fr, &fz, &fp, &fq, &fw, &part};
-      if (nv <= PCG_RES_ROWS * m->coop_blocks_f32) {
+      if (nv <= PCG_RES_ROWS * m->coop_blocks_pipe) {
         int nbr = (nv + PCG_RES_ROWS - 1) / PCG_RES_ROWS;
-        void* argsr[] = {&nvv, &iters, &sp, &sc2, &fv, (void*)&vu, &fd, &z, &fz, &part};
-        PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_res_f32, dim3(nbr), dim3(PCG_F32_T), argsr, 0,
+        float* mb = fx;  // m, two buffers of nv (the x and r vectors of the form below)
+        float* ub = fq;
+        void* argsr[] = {&nvv, &iters, &sp, &sc2, &fv, (void*)&vu, &fd, &z, &mb, &ub, &part};
+        PB_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg_pipe_f32, dim3(nbr), dim3(PCG_PIPE_T), argsr, 0,
                                             m->stream));
         PB_LAUNCHED(m);
         return PBFB_OK;

@@ -36,8 +36,9 @@ constexpr int TREE_LEAF = 2 * TREE_NT;       // targets per leaf (at most)
 constexpr int TREE_P = 6;                    // interpolation degree per dimension
 constexpr int TREE_K = TREE_P + 1;           // Chebyshev points per dimension
 constexpr int TREE_NPX = TREE_K * TREE_K * TREE_K;  // proxies per cluster
-constexpr int TREE_UP_NT = 352;              // threads of the upward pass (>= TREE_NPX, whole warps)
-static_assert(TREE_UP_NT >= TREE_NPX && TREE_UP_NT % 32 == 0, "one upward-pass thread per proxy");
+constexpr int TREE_UP_G = 8;                 // upward pass: point groups per (a, b) proxy column
+constexpr int TREE_UP_NT = (TREE_K * TREE_K * TREE_UP_G + 31) / 32 * 32;  // threads of the upward pass
+static_assert(TREE_UP_NT >= TREE_NPX && TREE_K <= 8, "upward pass shapes");
 constexpr int TREE_TILES_PER_CHUNK = 8;      // source tiles per block
 constexpr double TREE_THETA = 0.6;           // acceptance: r_B + r_C < theta |c_B - c_C|
 
@@ -56,11 +57,13 @@ __global__ void k_tree_permute(int nq, const int* __restrict__ perm, const float
 // proxy k = (a, b, c) at (tx_a, ty_b, tz_c) of the cluster's box receives
 // sum_j L_a(x_j) L_b(y_j) L_c(z_j) (s_j, m_j) over the segment's points, the 1-D values from the
 // barycentric formula l_a(x) = (w_a / (x - t_a)) / sum_m (w_m / (x - t_m)), w_m = (-1)^m (halved at
-// both ends), or the unit vector when x coincides with a node.  The basis values sit point-major
-// (lw[d][j][a]), so the (p+1)^3 proxy threads of a warp read at most p+1 consecutive words per point
-// (no bank conflicts).  The block that completes a cluster's last segment (a per-cluster arrival
-// counter) adds the cluster's segments in index order and writes its proxy source records, then
-// re-arms the counter: the result does not depend on which block arrives last.
+// both ends), or the unit vector when x coincides with a node.  The basis values sit point-major in
+// rows of 8 (lw[d][j][0..7]).  Thread t = 8 (a (p+1) + b) + g takes the column (a, b) -- all p+1
+// proxies c at once, from one product L_a L_b and two 16-byte reads of the row L_c -- over the
+// points j = g mod 8; the 8 groups of a column are adjacent lanes and are added by a xor butterfly
+// (every lane obtains the same sums).  The block that completes a cluster's last segment (a
+// per-cluster arrival counter) adds the cluster's segments in index order and writes its proxy
+// source records, then re-arms the counter: the result does not depend on which block arrives last.
 __device__ __forceinline__ float cheb_node(const float* __restrict__ cbox, int c, int d, int k) {
   const float lo = cbox[6 * c + d], hi = cbox[6 * c + 3 + d];
   return 0.5f * (lo + hi) + 0.5f * (hi - lo) * cospif((float)k / (float)TREE_P);
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ 
                                                         float4* __restrict__ prox_pos,
                                                         float4* __restrict__ prox_dl) {
   __shared__ float node[3][TREE_K];
-  __shared__ float lw[3][TREE_LEAF][TREE_K];
+  __shared__ __align__(16) float lw[3][TREE_LEAF][8];
   __shared__ float4 src[TREE_LEAF];
   __shared__ int last;
   const int g = blockIdx.x;
@@ -105,23 +108,43 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ 
       }
       const float rden = __frcp_rn(den);
 #pragma unroll
-      for (int k = 0; k < TREE_K; ++k) lw[d][j][k] = hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] * rden;
+      for (int k = 0; k < 8; ++k) lw[d][j][k] = k >= TREE_K ? 0.f : (hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] * rden);
     }
   }
   __syncthreads();
-  const int ka = t / (TREE_K * TREE_K), kb = (t / TREE_K) % TREE_K, kc = t % TREE_K;
-  if (t < TREE_NPX) {
-    float fs = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-    for (int jj = 0; jj < cnt; ++jj) {
-      const float w = lw[0][jj][ka] * lw[1][jj][kb] * lw[2][jj][kc];
+  const int col = t / TREE_UP_G, grp = t % TREE_UP_G;
+  const bool colv = col < TREE_K * TREE_K;
+  const int ka = colv ? col / TREE_K : 0, kb = colv ? col % TREE_K : 0;
+  float acc[TREE_K][4];
+#pragma unroll
+  for (int k = 0; k < TREE_K; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
+  if (colv) {
+    for (int jj = grp; jj < cnt; jj += TREE_UP_G) {
+      const float lab = lw[0][jj][ka] * lw[1][jj][kb];
+      const float4 c0 = *reinterpret_cast<const float4*>(&lw[2][jj][0]);
+      const float4 c1 = *reinterpret_cast<const float4*>(&lw[2][jj][4]);
+      const float lc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
       const float4 q = src[jj];
-      fs = fmaf(w, q.x, fs);
-      fx = fmaf(w, q.y, fx);
-      fy = fmaf(w, q.z, fy);
-      fz = fmaf(w, q.w, fz);
+#pragma unroll
+      for (int k = 0; k < TREE_K; ++k) {
+        const float w = lab * lc[k];
+        acc[k][0] = fmaf(w, q.x, acc[k][0]);
+        acc[k][1] = fmaf(w, q.y, acc[k][1]);
+        acc[k][2] = fmaf(w, q.z, acc[k][2]);
+        acc[k][3] = fmaf(w, q.w, acc[k][3]);
+      }
     }
-    part[(size_t)g * TREE_NPX + t] = make_float4(fs, fx, fy, fz);
   }
+#pragma unroll
+  for (int o = 1; o < TREE_UP_G; o <<= 1)
+#pragma unroll
+    for (int k = 0; k < TREE_K; ++k)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[k][v] += __shfl_xor_sync(0xffffffffu, acc[k][v], o);
+  if (colv && grp == 0)
+#pragma unroll
+    for (int k = 0; k < TREE_K; ++k)
+      part[(size_t)g * TREE_NPX + col * TREE_K + k] = make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
   // the last block of the cluster to arrive sums its segments (release: fence before the count)
   __threadfence();
   __syncthreads();
@@ -131,16 +154,26 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ 
   if (!last) return;
   __threadfence();  // acquire: the other segments' partials are visible in L2
   if (t < TREE_NPX) {
+    const int pa = t / (TREE_K * TREE_K), pb = (t / TREE_K) % TREE_K, pc = t % TREE_K;
+    // segment partials in batches of 8 independent loads, added in segment order
     double as = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
-    for (int h = s0; h < s1; ++h) {
-      const float4 v = __ldcg(&part[(size_t)h * TREE_NPX + t]);
-      as += v.x;
-      ax += v.y;
-      ay += v.z;
-      az += v.w;
+    for (int h0 = s0; h0 < s1; h0 += 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = h0 + u < s1 ? __ldcg(&part[(size_t)(h0 + u) * TREE_NPX + t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (h0 + u < s1) {
+          as += v[u].x;
+          ax += v[u].y;
+          ay += v[u].z;
+          az += v[u].w;
+        }
+      }
     }
     const int o = c * TREE_NPX + t;
-    prox_pos[o] = make_float4(node[0][ka], node[1][kb], node[2][kc], (float)as);
+    prox_pos[o] = make_float4(node[0][pa], node[1][pb], node[2][pc], (float)as);
     prox_dl[o] = make_float4((float)ax, (float)ay, (float)az, 0.f);
   }
   if (t == 0) arrivals[c] = 0;
@@ -269,8 +302,17 @@ __global__ void k_tree_sum(int nq, const int* __restrict__ perm, const int* __re
   if (i >= nq) return;
   const int L = pos_leaf[i];
   const int l = i - leaf_beg[L];
+  // chunk partials in batches of 8 independent loads, added in chunk order
   double s = 0.0;
-  for (int c = leaf_chunk[L]; c < leaf_chunk[L + 1]; ++c) s += part[(size_t)c * TREE_LEAF + l];
+  const int c0 = leaf_chunk[L], c1 = leaf_chunk[L + 1];
+  for (int cb = c0; cb < c1; cb += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = cb + u < c1 ? part[(size_t)(cb + u) * TREE_LEAF + l] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (cb + u < c1) s += v[u];
+  }
   val[perm[i]] = s;
 }
 
