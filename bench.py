@@ -351,12 +351,14 @@ def run_pbfb(args):
     if prec == pbfb.MIXED:
         l32, ms32 = prof["nbody_launches"], prof["nbody_ms"]
         if l32:
-            name32 = ("k_tree_eval + k_tree_up (float32 far field of the GMRES operator through the treecode: "
-                      "near pairs and cluster proxies, packed, 2 targets per thread)" if tuned.get("treecode") == 2
+            tree = tuned.get("treecode") in (2, 3)
+            name32 = (f"k_tree_eval + k_tree_up (float32 far field of the GMRES operator through the treecode: "
+                      f"near pairs and cluster proxies, packed, {4 if tuned.get('treecode') == 3 else 2} targets "
+                      f"per thread)" if tree
                       else "k_nbody_f32x2 (float32 far field of the GMRES operator, packed, 2 targets per thread)")
             cands.append(dict(kernel=name32, launches=l32, ms=ms32, pairs=prof["nbody_pairs"],
                               flops=prof["nbody_pairs"] * fpair, peak=peak32,
-                              traffic=None if tuned.get("treecode") == 2 else NBODY_TRAFFIC,
+                              traffic=None if tree else NBODY_TRAFFIC,
                               peak_basis=peak_basis))
         lff, msff = prof["nbodyff_launches"], prof["nbodyff_ms"]
         packed_ff = tuned.get("ff_kernel") == 4

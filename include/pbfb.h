@@ -395,7 +395,8 @@ typedef struct pbfb_tuning {
                                         1: one lane per row over a sliced-ELL copy of the block
                                         (slices of 32 rows, coalesced column-by-column storage) */
   int32_t treecode;                  /* float32 far field (GMRES operator): 1 the direct sum over
-                                        all point pairs, 2 the treecode (a binary tree over the
+                                        all point pairs, 2 the treecode (two targets per thread; 3:
+                                        the same with four targets per thread) (a binary tree over the
                                         quadrature points, leaves of 256; a cluster with
                                         r_leaf + r_cluster < 0.6 times the centre distance is
                                         replaced by 7^3 barycentric Lagrange proxies; the

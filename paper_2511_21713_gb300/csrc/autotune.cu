@@ -39,7 +39,7 @@ bool valid_tuning(const pbfb_tuning* t) {
   if (!in(t->pcg_blocks_per_sm, 1, 32)) return false;
   if (!(t->pcg_lanes == 0 || t->pcg_lanes == 1 || t->pcg_lanes == 2 || t->pcg_lanes == 4 || t->pcg_lanes == 8))
     return false;
-  if (t->treecode < 0 || t->treecode > 2) return false;
+  if (t->treecode < 0 || t->treecode > 3) return false;
   if (t->pcg_precision < 0 || t->pcg_precision > 2) return false;
   return true;
 }
@@ -133,11 +133,11 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
         }
       }
     }
-  // the treecode (surfaces too small for a tree leaf keep the direct sum), against the best direct
-  // shape; its plan is built on the first (untimed) run
-  {
+  // the treecode with two or four targets per thread (surfaces too small for a tree leaf keep the
+  // direct sum), against the best direct shape; its plan is built on the first (untimed) run
+  for (int tc : {2, 3}) {
     pbfb_tuning t = best;
-    t.treecode = 2;
+    t.treecode = tc;
     write_tuning(m, &t);
     double ms;
     int st = time_ms(m, reps, far(PBFB_MIXED), &ms);
@@ -147,7 +147,7 @@ int autotune(Mesh* m, int reps, pbfb_tuning* best_out, double* ms_out) {
     }
     if (ms < t_best[0]) {
       t_best[0] = ms;
-      best.treecode = 2;
+      best.treecode = tc;
     }
   }
   // float-float far field

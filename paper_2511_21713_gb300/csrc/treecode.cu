@@ -31,8 +31,8 @@ namespace pbfb {
 
 namespace {
 
-constexpr int TREE_NT = 128;                 // threads per block; two targets each
-constexpr int TREE_LEAF = 2 * TREE_NT;       // targets per leaf (at most)
+constexpr int TREE_TILE = 128;               // source records per tile
+constexpr int TREE_LEAF = 256;               // targets per leaf (at most)
 constexpr int TREE_P = 6;                    // interpolation degree per dimension
 constexpr int TREE_K = TREE_P + 1;           // Chebyshev points per dimension
 constexpr int TREE_NPX = TREE_K * TREE_K * TREE_K;  // proxies per cluster
@@ -179,89 +179,113 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ 
   if (t == 0) arrivals[c] = 0;
 }
 
-// Evaluation: block = one chunk (a target leaf and a run of its source tiles).  Tiles that overlap
-// the leaf's own points take the scalar path with the coincident-point test; the others the
-// packed one.  Padding entries (past a tile's count) sit far away with zero strength.
-template <bool YUK>
-__global__ void __launch_bounds__(TREE_NT) k_tree_eval(const float4* __restrict__ tgt_t,
-                                                       const int* __restrict__ leaf_beg,
-                                                       const int* __restrict__ leaf_end,
-                                                       const int* __restrict__ chunk_leaf,
-                                                       const int* __restrict__ chunk_tile,
-                                                       const int2* __restrict__ tiles,
-                                                       const float4* __restrict__ spos_t,
-                                                       const float4* __restrict__ sdl_t, float kappa,
-                                                       double* __restrict__ part) {
-  __shared__ ulonglong2 sh[4][TREE_NT];
-  __shared__ float4 shp[TREE_NT], shd[TREE_NT];
+// Evaluation: block = one chunk (a target leaf and a run of its source tiles of TREE_TILE records),
+// TPT targets per thread (2: 128 threads, one f32x2 pack; 4: 64 threads, two packs that share each
+// source's shared-memory reads).  Tiles that overlap the leaf's own points take the scalar path
+// with the coincident-point test; the others the packed one.  Padding entries (past a tile's
+// count) sit far away with zero strength.
+template <bool YUK, int TPT>
+__global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __restrict__ tgt_t,
+                                                               const int* __restrict__ leaf_beg,
+                                                               const int* __restrict__ leaf_end,
+                                                               const int* __restrict__ chunk_leaf,
+                                                               const int* __restrict__ chunk_tile,
+                                                               const int2* __restrict__ tiles,
+                                                               const float4* __restrict__ spos_t,
+                                                               const float4* __restrict__ sdl_t, float kappa,
+                                                               double* __restrict__ part) {
+  constexpr int NT = TREE_LEAF / TPT, NP = TPT / 2;
+  __shared__ ulonglong2 sh[4][TREE_TILE];
+  __shared__ float4 shp[TREE_TILE], shd[TREE_TILE];
   const int c = blockIdx.x;
   const int L = chunk_leaf[c];
   const int lb = leaf_beg[L], le = leaf_end[L];
-  int ti[2];
-  float txs[2], tys[2], tzs[2];
-  double acc64[2] = {0.0, 0.0};
-  for (int k = 0; k < 2; ++k) {
-    ti[k] = lb + k * TREE_NT + threadIdx.x;
+  int ti[TPT];
+  float txs[TPT], tys[TPT], tzs[TPT];
+  double acc64[TPT];
+#pragma unroll
+  for (int k = 0; k < TPT; ++k) {
+    ti[k] = lb + k * NT + threadIdx.x;
     const float4 p = tgt_t[ti[k] < le ? ti[k] : lb];
     txs[k] = p.x;
     tys[k] = p.y;
     tzs[k] = p.z;
+    acc64[k] = 0.0;
   }
-  const f32x2 tx = pk2(txs[0], txs[1]), ty = pk2(tys[0], tys[1]), tz = pk2(tzs[0], tzs[1]);
+  f32x2 tx[NP], ty[NP], tz[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    tx[q] = pk2(txs[2 * q], txs[2 * q + 1]);
+    ty[q] = pk2(tys[2 * q], tys[2 * q + 1]);
+    tz[q] = pk2(tzs[2 * q], tzs[2 * q + 1]);
+  }
   const float nk = -kappa * 1.4426950408889634f;
   const f32x2 nk2 = pk2(nk, nk), kap2 = pk2(kappa, kappa), one2 = pk2(1.f, 1.f);
   for (int tl = chunk_tile[c]; tl < chunk_tile[c + 1]; ++tl) {
     const int2 tile = tiles[tl];
     const int s0 = tile.x, cnt = tile.y;
-    float4 p, d;
-    if ((int)threadIdx.x < cnt) {
-      p = spos_t[s0 + threadIdx.x];
-      d = sdl_t[s0 + threadIdx.x];
-    } else {
-      p = make_float4(1e18f, 1e18f, 1e18f, 0.f);
-      d = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < TREE_TILE; i += NT) {
+      float4 p, d;
+      if (i < cnt) {
+        p = spos_t[s0 + i];
+        d = sdl_t[s0 + i];
+      } else {
+        p = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        d = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      sh[0][i] = make_ulonglong2(pk2(p.x, p.x), pk2(p.y, p.y));
+      sh[1][i] = make_ulonglong2(pk2(p.z, p.z), pk2(p.w, p.w));
+      sh[2][i] = make_ulonglong2(pk2(d.x, d.x), pk2(d.y, d.y));
+      sh[3][i] = make_ulonglong2(pk2(d.z, d.z), 0ull);
+      shp[i] = p;
+      shd[i] = d;
     }
-    sh[0][threadIdx.x] = make_ulonglong2(pk2(p.x, p.x), pk2(p.y, p.y));
-    sh[1][threadIdx.x] = make_ulonglong2(pk2(p.z, p.z), pk2(p.w, p.w));
-    sh[2][threadIdx.x] = make_ulonglong2(pk2(d.x, d.x), pk2(d.y, d.y));
-    sh[3][threadIdx.x] = make_ulonglong2(pk2(d.z, d.z), 0ull);
-    shp[threadIdx.x] = p;
-    shd[threadIdx.x] = d;
     __syncthreads();
     const bool diag = s0 < le && s0 + cnt > lb;
     if (!diag) {
-      f32x2 acc = 0ull;
+      f32x2 acc[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) acc[q] = 0ull;
 #pragma unroll 2
-      for (int jj = 0; jj < TREE_NT; ++jj) {
+      for (int jj = 0; jj < TREE_TILE; ++jj) {
         const ulonglong2 a0 = sh[0][jj], a1 = sh[1][jj], a2 = sh[2][jj], a3 = sh[3][jj];
-        const f32x2 dx = sub2(tx, a0.x), dy = sub2(ty, a0.y), dz = sub2(tz, a1.x);
-        const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-        float ra, rb;
-        upk2(r2, ra, rb);
-        const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
-        const f32x2 nd = fma2(a3.x, dz, fma2(a2.y, dy, mul2(a2.x, dx)));
-        const f32x2 ri2 = mul2(ri, ri);
-        if (YUK) {
-          const f32x2 r = mul2(r2, ri);
-          float xa, xb;
-          upk2(mul2(nk2, r), xa, xb);
-          const f32x2 ex = pk2(ex2_approx(xa), ex2_approx(xb));
-          const f32x2 tt = fma2(mul2(nd, fma2(kap2, r, one2)), ri2, a1.y);
-          acc = fma2(tt, mul2(ex, ri), acc);
-        } else {
-          acc = fma2(fma2(nd, ri2, a1.y), ri, acc);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const f32x2 dx = sub2(tx[q], a0.x), dy = sub2(ty[q], a0.y), dz = sub2(tz[q], a1.x);
+          const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+          float ra, rb;
+          upk2(r2, ra, rb);
+          const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
+          const f32x2 nd = fma2(a3.x, dz, fma2(a2.y, dy, mul2(a2.x, dx)));
+          const f32x2 ri2 = mul2(ri, ri);
+          if (YUK) {
+            const f32x2 r = mul2(r2, ri);
+            float xa, xb;
+            upk2(mul2(nk2, r), xa, xb);
+            const f32x2 ex = pk2(ex2_approx(xa), ex2_approx(xb));
+            const f32x2 tt = fma2(mul2(nd, fma2(kap2, r, one2)), ri2, a1.y);
+            acc[q] = fma2(tt, mul2(ex, ri), acc[q]);
+          } else {
+            acc[q] = fma2(fma2(nd, ri2, a1.y), ri, acc[q]);
+          }
         }
       }
-      float a, b;
-      upk2(acc, a, b);
-      acc64[0] += (double)a;
-      acc64[1] += (double)b;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        float a, b;
+        upk2(acc[q], a, b);
+        acc64[2 * q] += (double)a;
+        acc64[2 * q + 1] += (double)b;
+      }
     } else {
-      float accs[2] = {0.f, 0.f};
-      for (int jj = 0; jj < TREE_NT; ++jj) {
+      float accs[TPT];
+#pragma unroll
+      for (int k = 0; k < TPT; ++k) accs[k] = 0.f;
+      for (int jj = 0; jj < TREE_TILE; ++jj) {
         const float4 q = shp[jj];
         const float4 m = shd[jj];
-        for (int k = 0; k < 2; ++k) {
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
           if (s0 + jj == ti[k]) continue;
           const float dx = txs[k] - q.x, dy = tys[k] - q.y, dz = tzs[k] - q.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -278,13 +302,13 @@ __global__ void __launch_bounds__(TREE_NT) k_tree_eval(const float4* __restrict_
           }
         }
       }
-      acc64[0] += (double)accs[0];
-      acc64[1] += (double)accs[1];
+#pragma unroll
+      for (int k = 0; k < TPT; ++k) acc64[k] += (double)accs[k];
     }
     __syncthreads();
   }
-  part[(size_t)c * TREE_LEAF + threadIdx.x] = acc64[0];
-  part[(size_t)c * TREE_LEAF + TREE_NT + threadIdx.x] = acc64[1];
+#pragma unroll
+  for (int k = 0; k < TPT; ++k) part[(size_t)c * TREE_LEAF + k * NT + threadIdx.x] = acc64[k];
 }
 
 // out[i] = in[perm[i]]
@@ -331,7 +355,7 @@ int build_surface_tree(Mesh* m, Surface* s) {
   for (int j = 0; j < nq; ++j)
     for (int d = 0; d < 3; ++d) xyz[3 * (size_t)j + d] = qx[(size_t)d * nq + j];
   TreeTiles P;
-  if (plan_tree_tiles(xyz.data(), nq, TREE_LEAF, TREE_THETA, TREE_NPX, TREE_NT, TREE_TILES_PER_CHUNK, &P)) {
+  if (plan_tree_tiles(xyz.data(), nq, TREE_LEAF, TREE_THETA, TREE_NPX, TREE_TILE, TREE_TILES_PER_CHUNK, &P)) {
     set_error("treecode: tree plan failed");
     return PBFB_ERR_STATE;
   }
@@ -378,7 +402,7 @@ int build_surface_tree(Mesh* m, Surface* s) {
 
 bool use_tree(const Mesh* m, const Surface* s) {
   if (m->tune_tree == 1) return false;
-  if (m->tune_tree == 2) return s->nq >= TREE_LEAF;
+  if (m->tune_tree >= 2) return s->nq >= TREE_LEAF;
   return s->nq >= TREE_MIN_POINTS;
 }
 
@@ -398,14 +422,13 @@ int launch_tree_far(Mesh* m, Surface* s, double kappa, const float4* spos, const
     PB_LAUNCHED(m);
   }
   const float kf = (float)kappa;
-  if (kappa != 0.0)
-    k_tree_eval<true><<<T.nchunk, TREE_NT, 0, m->stream>>>(T.tgt.p, T.leaf_beg.p, T.leaf_end.p, T.chunk_leaf.p,
-                                                            T.chunk_tile.p, T.tiles.p, T.spos.p, T.sdl.p, kf,
-                                                            T.part.p);
-  else
-    k_tree_eval<false><<<T.nchunk, TREE_NT, 0, m->stream>>>(T.tgt.p, T.leaf_beg.p, T.leaf_end.p, T.chunk_leaf.p,
-                                                             T.chunk_tile.p, T.tiles.p, T.spos.p, T.sdl.p, kf,
-                                                             T.part.p);
+  // four targets per thread with treecode = 3, else two
+  const bool four = m->tune_tree == 3;
+  const void* fn = kappa != 0.0 ? (four ? (const void*)k_tree_eval<true, 4> : (const void*)k_tree_eval<true, 2>)
+                                : (four ? (const void*)k_tree_eval<false, 4> : (const void*)k_tree_eval<false, 2>);
+  void* args[] = {&T.tgt.p, &T.leaf_beg.p, &T.leaf_end.p, &T.chunk_leaf.p, &T.chunk_tile.p, &T.tiles.p,
+                  &T.spos.p, &T.sdl.p, (void*)&kf, &T.part.p};
+  PB_CUDA(cudaLaunchKernel(fn, dim3(T.nchunk), dim3(TREE_LEAF / (four ? 4 : 2)), args, 0, m->stream));
   PB_LAUNCHED(m);
   k_tree_sum<<<blocks(nq, 256), 256, 0, m->stream>>>(nq, T.perm.p, T.pos_leaf.p, T.leaf_beg.p, T.leaf_chunk.p,
                                                       T.part.p, val);

@@ -38,7 +38,7 @@ def test_autotune_shapes_cache_and_results(small_case, tmp_path):
     assert shapes["ff_blocks_per_sm"] in (4, 8, 16, 24) and shapes["ff_kernel"] in (1, 2, 3, 4)
     assert shapes["spmv_lanes"] in (4, 8, 16) and shapes["spmv_block"] in (128, 256, 512)
     assert shapes["pcg_blocks_per_sm"] in (0, 1, 2, 4, 8) and shapes["pcg_lanes"] in (1, 2, 4, 8)
-    assert shapes["treecode"] in (1, 2)
+    assert shapes["treecode"] in (1, 2, 3)
     assert all(v > 0 for v in ms.values())
     stored = json.load(open(cache))
     assert len(stored) == 1 and list(stored.values())[0]["shapes"] == shapes

@@ -134,7 +134,7 @@ def test_boundary_operators(pair, precision):
 @pytest.mark.parametrize("shape", [dict(nbody_targets_per_thread=4, nbody_packed=2, nbody_blocks_per_sm=32),
                                    dict(nbody_targets_per_thread=1, nbody_packed=0, nbody_blocks_per_sm=16),
                                    dict(nbody_targets_per_thread=2, nbody_packed=1, nbody_blocks_per_sm=32),
-                                   dict(treecode=2)])
+                                   dict(treecode=2), dict(treecode=3)])
 def test_float32_far_field_variants(pair, shape):
     """Every float32 far-field variant (mutual pairs, one target per thread, packed f32x2, the
     treecode: leaves of 256 points, ragged here) within 3e-6 of the oracle's operators, ragged
