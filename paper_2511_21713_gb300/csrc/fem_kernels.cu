@@ -17,6 +17,7 @@
 
 #include "pbfb_internal.cuh"
 #include "quad_tables.cuh"
+#include "warp_sum.cuh"
 
 namespace pbfb {
 
@@ -678,12 +679,12 @@ __global__ void __launch_bounds__(RED_T) k_omega_dots(int nv, const int* __restr
 }
 
 // Sum nb partial rows of width w (for each of gridDim.x problems), fixed order.
+// (one warp per problem)
 __global__ void k_sum_partials(const double* __restrict__ part, int nb, int w, double* __restrict__ out) {
-  int o = blockIdx.x;
-  for (int k = threadIdx.x; k < w; k += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[((int64_t)o * nb + b) * w + k];
-    out[o * w + k] = s;
+  const int o = blockIdx.x;
+  for (int k = 0; k < w; ++k) {
+    const double s = warp_strided_sum(part + (int64_t)o * nb * w + k, nb, w);
+    if (threadIdx.x == 0) out[o * w + k] = s;
   }
 }
 

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "pbfb_internal.cuh"
+#include "warp_sum.cuh"
 
 namespace pbfb {
 
@@ -50,12 +51,10 @@ __global__ void k_dot_partial(int n, const double* __restrict__ a, const double*
   }
 }
 
+// one warp: *out = sum of the nb partials (fixed order)
 __global__ void k_sum_to(const double* __restrict__ part, int nb, double* __restrict__ out) {
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[b];
-    *out = s;
-  }
+  const double s = warp_strided_sum(part, nb, 1);
+  if (threadIdx.x == 0) *out = s;
 }
 
 __global__ void k_axpby(int n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
@@ -102,12 +101,12 @@ __global__ void __launch_bounds__(MD_T) k_multidot(int n, int k, const double* _
   }
 }
 
+// one warp per j: h[j] = sum of its nb partials (fixed order)
 __global__ void k_multidot_sum(const double* __restrict__ part, int nb, int k, double* __restrict__ h) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.x;
   if (j >= k) return;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[(int64_t)j * nb + b];
-  h[j] = s;
+  const double s = warp_strided_sum(part + (int64_t)j * nb, nb, 1);
+  if (threadIdx.x == 0) h[j] = s;
 }
 
 // w -= sum_j V[j] h[j]; optional partial sums of ||w||^2 after the update
@@ -1342,7 +1341,7 @@ static int gmres(Mesh* m, const double* b, double* x, double tol, int restart, i
         double* hh = pass == 0 ? h1 : h2;
         k_multidot<<<gd, MD_T, 0, m->stream>>>(n, kk, V, w, m->gpart.p);
         PB_LAUNCHED(m);
-        k_multidot_sum<<<blocks_for(kk, 64), 64, 0, m->stream>>>(m->gpart.p, nbr, kk, hh);
+        k_multidot_sum<<<kk, 32, 0, m->stream>>>(m->gpart.p, nbr, kk, hh);
         PB_LAUNCHED(m);
         k_multiaxpy<<<nbr, MD_T, 0, m->stream>>>(n, kk, V, hh, w, pass == 1 ? m->gpart.p : nullptr);
         PB_LAUNCHED(m);
