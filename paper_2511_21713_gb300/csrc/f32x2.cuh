@@ -2,7 +2,7 @@
 //
 // f32x2: two float32 values in one 64-bit register, operated on by the Blackwell add/sub/mul/fma
 // instructions on pairs (one issue slot for two lanes' worth of float32 work).
-// rsqrt_approx / ex2_approx: the special-function unit's approximations without denormal
+// rsqrt_approx / rcp_approx / ex2_approx: the special-function unit's approximations without denormal
 // fix-ups (inputs here are normal numbers).
 #pragma once
 
@@ -12,6 +12,11 @@ namespace {
 __device__ __forceinline__ float rsqrt_approx(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -32,6 +37,11 @@ __device__ __forceinline__ void upk2(f32x2 v, float& a, float& b) {
 __device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
   f32x2 r;
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
 __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {

@@ -83,12 +83,14 @@ struct SurfaceTree {
   DBuf<int> leaf_beg, leaf_end, leaf_chunk;  // per leaf: targets [beg, end), chunks [chunk[L], chunk[L+1])
   DBuf<int> chunk_leaf, chunk_tile; // per chunk: its leaf; its tiles [tile[c], tile[c+1])
   DBuf<int2> tiles;                 // per tile: first source record, count (<= 128)
-  int nseg = 0;
-  DBuf<int> clus_seg;               // per approximated cluster: its upward-pass segments
+  int npair = 0;
   DBuf<float> clus_box;             // per cluster: lo x, y, z, hi x, y, z (centre-relative)
-  DBuf<int> seg_clus, seg_beg, seg_cnt;  // per segment: cluster, first point (tree order), points
-  DBuf<float4> up_part;             // per segment: partial proxies (charge, dipole) of its cluster
-  DBuf<int> up_arrivals;            // per cluster: segments done in the running upward pass (0 between)
+  DBuf<float> leaf_box;             // per leaf: the same
+  DBuf<float4> leaf_prox;           // per leaf: its (p+1)^3 proxies (charge, dipole) from its points
+  DBuf<int> pair_clus, pair_leaf;   // per (cluster, leaf of the cluster) pair of the upward pass
+  DBuf<int> clus_pair;              // per approximated cluster: its pairs [clus_pair[k], clus_pair[k + 1])
+  DBuf<float4> up_part;             // per pair: the leaf's proxies on the cluster's grid
+  DBuf<int> up_arrivals;            // per cluster: pairs done in the running upward pass (0 between)
   DBuf<float4> tgt;                 // target positions in tree order
   DBuf<float4> spos, sdl;           // nq points in tree order, then nclus x (p+1)^3 proxies
   DBuf<double> part;                // nchunk x 256 partial sums

@@ -53,40 +53,58 @@ __global__ void k_tree_permute(int nq, const int* __restrict__ perm, const float
   sdl_t[i] = sdl[j];
 }
 
-// Upward pass, one kernel.  A block per segment (at most 256 consecutive points of one cluster):
-// proxy k = (a, b, c) at (tx_a, ty_b, tz_c) of the cluster's box receives
-// sum_j L_a(x_j) L_b(y_j) L_c(z_j) (s_j, m_j) over the segment's points, the 1-D values from the
-// barycentric formula l_a(x) = (w_a / (x - t_a)) / sum_m (w_m / (x - t_m)), w_m = (-1)^m (halved at
-// both ends), or the unit vector when x coincides with a node.  The basis values sit point-major in
-// rows of 8 (lw[d][j][0..7]).  Thread t = 8 (a (p+1) + b) + g takes the column (a, b) -- all p+1
-// proxies c at once, from one product L_a L_b and two 16-byte reads of the row L_c -- over the
-// points j = g mod 8; the 8 groups of a column are adjacent lanes and are added by a xor butterfly
-// (every lane obtains the same sums).  The block that completes a cluster's last segment (a
-// per-cluster arrival counter) adds the cluster's segments in index order and writes its proxy
+// Upward pass, in two kernels.
+// k_tree_up_leaf: a block per leaf (at most 256 points): proxy k = (a, b, c) at (tx_a, ty_b, tz_c) of
+// the leaf's box receives sum_j L_a(x_j) L_b(y_j) L_c(z_j) (s_j, m_j) over the leaf's points, the
+// 1-D values from the barycentric formula l_a(x) = (w_a / (x - t_a)) / sum_m (w_m / (x - t_m)),
+// w_m = (-1)^m (halved at both ends), or the unit vector when x coincides with a node.  The basis
+// values sit point-major in rows of 8 (lw[d][j][0..7]).  Thread t = 8 (a (p+1) + b) + g takes the
+// column (a, b) -- all p+1 proxies c at once, from one product L_a L_b and two 16-byte reads of the
+// row L_c -- over the points j = g mod 8; the 8 groups of a column are adjacent lanes and are added
+// by a xor butterfly (every lane obtains the same sums).
+// k_tree_m2c: a block per (cluster, leaf of the cluster) pair: the leaf's proxies moved onto the
+// cluster's Chebyshev grid, Q_C[k] += sum_k' L_k^C(s_k') Q_L[k'] -- exact for the degree-p tensor
+// basis L_k^C, so the cluster's proxies equal the sums over its points up to rounding -- as three
+// passes of a (p+1) x (p+1) matrix, one dimension each.  The block that completes a cluster's last
+// pair (a per-cluster arrival counter) adds the cluster's pairs in index order and writes its proxy
 // source records, then re-arms the counter: the result does not depend on which block arrives last.
+// Each point is touched once per solve-wide leaf instead of once per accepted ancestor.
 __device__ __forceinline__ float cheb_node(const float* __restrict__ cbox, int c, int d, int k) {
   const float lo = cbox[6 * c + d], hi = cbox[6 * c + 3 + d];
   return 0.5f * (lo + hi) + 0.5f * (hi - lo) * cospif((float)k / (float)TREE_P);
 }
 
-__global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ seg_clus,
-                                                        const int* __restrict__ seg_beg,
-                                                        const int* __restrict__ seg_cnt,
-                                                        const int* __restrict__ clus_seg,
-                                                        const float* __restrict__ cbox,
-                                                        const float4* __restrict__ pts_pos,
-                                                        const float4* __restrict__ pts_dl,
-                                                        float4* __restrict__ part, int* __restrict__ arrivals,
-                                                        float4* __restrict__ prox_pos,
-                                                        float4* __restrict__ prox_dl) {
+// the p+1 barycentric Lagrange values at x of the nodes t[0..p] (unit vector on a node)
+__device__ __forceinline__ void bary_row(float x, const float* t, float* l) {
+  float a[TREE_K];
+  float den = 0.f;
+  int hit = -1;
+#pragma unroll
+  for (int k = 0; k < TREE_K; ++k) {
+    const float dx = x - t[k];
+    const float w = ((k & 1) ? -1.f : 1.f) * ((k == 0 || k == TREE_P) ? 0.5f : 1.f);
+    if (dx == 0.f) hit = k;
+    a[k] = dx == 0.f ? 0.f : w * rcp_approx(dx);
+    den += a[k];
+  }
+  const float rden = rcp_approx(den);
+#pragma unroll
+  for (int k = 0; k < TREE_K; ++k) l[k] = hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] * rden;
+}
+
+__global__ void __launch_bounds__(TREE_UP_NT) k_tree_up_leaf(const int* __restrict__ leaf_beg,
+                                                             const int* __restrict__ leaf_end,
+                                                             const float* __restrict__ lbox,
+                                                             const float4* __restrict__ pts_pos,
+                                                             const float4* __restrict__ pts_dl,
+                                                             float4* __restrict__ leaf_prox) {
   __shared__ float node[3][TREE_K];
   __shared__ __align__(16) float lw[3][TREE_LEAF][8];
   __shared__ float4 src[TREE_LEAF];
-  __shared__ int last;
-  const int g = blockIdx.x;
-  const int c = seg_clus[g], b = seg_beg[g], cnt = seg_cnt[g];
+  const int L = blockIdx.x;
+  const int b = leaf_beg[L], cnt = leaf_end[L] - b;
   const int t = threadIdx.x;
-  if (t < 3 * TREE_K) node[t / TREE_K][t % TREE_K] = cheb_node(cbox, c, t / TREE_K, t % TREE_K);
+  if (t < 3 * TREE_K) node[t / TREE_K][t % TREE_K] = cheb_node(lbox, L, t / TREE_K, t % TREE_K);
   __syncthreads();
   for (int j = t; j < cnt; j += TREE_UP_NT) {
     const float4 p = pts_pos[b + j];
@@ -95,20 +113,10 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ 
     const float xs[3] = {p.x, p.y, p.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      float a[TREE_K];
-      float den = 0.f;
-      int hit = -1;
+      float l[TREE_K];
+      bary_row(xs[d], node[d], l);
 #pragma unroll
-      for (int k = 0; k < TREE_K; ++k) {
-        const float dx = xs[d] - node[d][k];
-        const float w = ((k & 1) ? -1.f : 1.f) * ((k == 0 || k == TREE_P) ? 0.5f : 1.f);
-        if (dx == 0.f) hit = k;
-        a[k] = dx == 0.f ? 0.f : w * __frcp_rn(dx);
-        den += a[k];
-      }
-      const float rden = __frcp_rn(den);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) lw[d][j][k] = k >= TREE_K ? 0.f : (hit >= 0 ? (k == hit ? 1.f : 0.f) : a[k] * rden);
+      for (int k = 0; k < 8; ++k) lw[d][j][k] = k < TREE_K ? l[k] : 0.f;
     }
   }
   __syncthreads();
@@ -144,18 +152,94 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ 
   if (colv && grp == 0)
 #pragma unroll
     for (int k = 0; k < TREE_K; ++k)
-      part[(size_t)g * TREE_NPX + col * TREE_K + k] = make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
-  // the last block of the cluster to arrive sums its segments (release: fence before the count)
+      leaf_prox[(size_t)L * TREE_NPX + col * TREE_K + k] = make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+}
+
+constexpr int TREE_M2C_NT = (TREE_NPX + 31) / 32 * 32;
+
+__global__ void __launch_bounds__(TREE_M2C_NT) k_tree_m2c(const int* __restrict__ pair_clus,
+                                                          const int* __restrict__ pair_leaf,
+                                                          const int* __restrict__ clus_pair,
+                                                          const float* __restrict__ cbox,
+                                                          const float* __restrict__ lbox,
+                                                          const float4* __restrict__ leaf_prox,
+                                                          float4* __restrict__ part, int* __restrict__ arrivals,
+                                                          float4* __restrict__ prox_pos,
+                                                          float4* __restrict__ prox_dl) {
+  __shared__ float cn[3][TREE_K];
+  __shared__ float mt[3][TREE_K][TREE_K];  // mt[d][a'][a] = l_a^C (the leaf's node a', dimension d)
+  __shared__ float4 bufa[TREE_NPX], bufb[TREE_NPX];
+  __shared__ int last;
+  const int g = blockIdx.x;
+  const int c = pair_clus[g], L = pair_leaf[g];
+  const int t = threadIdx.x;
+  if (t < 3 * TREE_K) cn[t / TREE_K][t % TREE_K] = cheb_node(cbox, c, t / TREE_K, t % TREE_K);
+  for (int i = t; i < TREE_NPX; i += TREE_M2C_NT) bufa[i] = leaf_prox[(size_t)L * TREE_NPX + i];
+  __syncthreads();
+  if (t < 3 * TREE_K) {
+    const int d = t / TREE_K, ap = t % TREE_K;
+    float l[TREE_K];
+    bary_row(cheb_node(lbox, L, d, ap), cn[d], l);
+#pragma unroll
+    for (int k = 0; k < TREE_K; ++k) mt[d][ap][k] = l[k];
+  }
+  __syncthreads();
+  const int pa = t / (TREE_K * TREE_K), pb = (t / TREE_K) % TREE_K, pc = t % TREE_K;
+  const bool tv = t < TREE_NPX;
+  // x: bufb[a][b'][c'] = sum_a' mt[0][a'][a] bufa[a'][b'][c']
+  if (tv) {
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int ap = 0; ap < TREE_K; ++ap) {
+      const float w = mt[0][ap][pa];
+      const float4 v = bufa[ap * TREE_K * TREE_K + pb * TREE_K + pc];
+      s.x = fmaf(w, v.x, s.x);
+      s.y = fmaf(w, v.y, s.y);
+      s.z = fmaf(w, v.z, s.z);
+      s.w = fmaf(w, v.w, s.w);
+    }
+    bufb[t] = s;
+  }
+  __syncthreads();
+  // y: bufa[a][b][c'] = sum_b' mt[1][b'][b] bufb[a][b'][c']
+  if (tv) {
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int bp = 0; bp < TREE_K; ++bp) {
+      const float w = mt[1][bp][pb];
+      const float4 v = bufb[pa * TREE_K * TREE_K + bp * TREE_K + pc];
+      s.x = fmaf(w, v.x, s.x);
+      s.y = fmaf(w, v.y, s.y);
+      s.z = fmaf(w, v.z, s.z);
+      s.w = fmaf(w, v.w, s.w);
+    }
+    bufa[t] = s;
+  }
+  __syncthreads();
+  // z: the pair's share of the cluster's proxies
+  if (tv) {
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int cp = 0; cp < TREE_K; ++cp) {
+      const float w = mt[2][cp][pc];
+      const float4 v = bufa[pa * TREE_K * TREE_K + pb * TREE_K + cp];
+      s.x = fmaf(w, v.x, s.x);
+      s.y = fmaf(w, v.y, s.y);
+      s.z = fmaf(w, v.z, s.z);
+      s.w = fmaf(w, v.w, s.w);
+    }
+    part[(size_t)g * TREE_NPX + t] = s;
+  }
+  // the last block of the cluster to arrive sums its pairs (release: fence before the count)
   __threadfence();
   __syncthreads();
-  const int s0 = clus_seg[c], s1 = clus_seg[c + 1];
+  const int s0 = clus_pair[c], s1 = clus_pair[c + 1];
   if (t == 0) last = atomicAdd(&arrivals[c], 1) == s1 - s0 - 1;
   __syncthreads();
   if (!last) return;
-  __threadfence();  // acquire: the other segments' partials are visible in L2
-  if (t < TREE_NPX) {
-    const int pa = t / (TREE_K * TREE_K), pb = (t / TREE_K) % TREE_K, pc = t % TREE_K;
-    // segment partials in batches of 8 independent loads, added in segment order
+  __threadfence();  // acquire: the other pairs' partials are visible in L2
+  if (tv) {
+    // pair partials in batches of 8 independent loads, added in pair order
     double as = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
     for (int h0 = s0; h0 < s1; h0 += 8) {
       float4 v[8];
@@ -173,7 +257,7 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up(const int* __restrict__ 
       }
     }
     const int o = c * TREE_NPX + t;
-    prox_pos[o] = make_float4(node[0][pa], node[1][pb], node[2][pc], (float)as);
+    prox_pos[o] = make_float4(cn[0][pa], cn[1][pb], cn[2][pc], (float)as);
     prox_dl[o] = make_float4((float)ax, (float)ay, (float)az, 0.f);
   }
   if (t == 0) arrivals[c] = 0;
@@ -377,14 +461,48 @@ int build_surface_tree(Mesh* m, Surface* s) {
   PB_TRY(T.chunk_leaf.upload(P.chunk_leaf.data(), P.chunk_leaf.size(), m->stream));
   PB_TRY(T.chunk_tile.upload(P.chunk_tile.data(), P.chunk_tile.size(), m->stream));
   PB_TRY(T.tiles.upload(tiles.data(), tiles.size(), m->stream));
-  T.nseg = (int)P.seg_beg.size();
   if (P.nclus > 0) {
-    PB_TRY(T.clus_seg.upload(P.clus_seg.data(), P.clus_seg.size(), m->stream));
+    // leaf boxes (the points' bounding boxes, a flat side widened to 1e-3 of the longest one, as
+    // the clusters'), and per cluster the leaves it is made of: clusters are tree nodes, unions of
+    // consecutive leaves in tree order
+    std::vector<float> lbox(6 * (size_t)P.nleaf);
+    for (int L = 0; L < P.nleaf; ++L) {
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int q = P.leaf_beg[L]; q < P.leaf_end[L]; ++q)
+        for (int d = 0; d < 3; ++d) {
+          const double v = xyz[3 * (size_t)P.perm[q] + d];
+          lo[d] = std::min(lo[d], v);
+          hi[d] = std::max(hi[d], v);
+        }
+      double side = 0.0;
+      for (int d = 0; d < 3; ++d) side = std::max(side, hi[d] - lo[d]);
+      for (int d = 0; d < 3; ++d) {
+        const double pad = std::max(0.0, 1e-3 * side - (hi[d] - lo[d])) * 0.5;
+        lbox[6 * (size_t)L + d] = (float)(lo[d] - pad - s->ctr[d]);
+        lbox[6 * (size_t)L + 3 + d] = (float)(hi[d] + pad - s->ctr[d]);
+      }
+    }
+    std::vector<int> pc, pl, cp(1, 0);
+    for (int k = 0; k < P.nclus; ++k) {
+      const int L0 = P.pos_leaf[P.clus_beg[k]], L1 = P.pos_leaf[P.clus_end[k] - 1];
+      if (P.leaf_beg[L0] != P.clus_beg[k] || P.leaf_end[L1] != P.clus_end[k]) {
+        set_error("treecode: a cluster is not a union of leaves");
+        return PBFB_ERR_STATE;
+      }
+      for (int L = L0; L <= L1; ++L) {
+        pc.push_back(k);
+        pl.push_back(L);
+      }
+      cp.push_back((int)pc.size());
+    }
+    T.npair = (int)pc.size();
     PB_TRY(T.clus_box.upload(cbox.data(), cbox.size(), m->stream));
-    PB_TRY(T.seg_clus.upload(P.seg_clus.data(), T.nseg, m->stream));
-    PB_TRY(T.seg_beg.upload(P.seg_beg.data(), T.nseg, m->stream));
-    PB_TRY(T.seg_cnt.upload(P.seg_cnt.data(), T.nseg, m->stream));
-    PB_TRY(T.up_part.alloc((size_t)T.nseg * TREE_NPX));
+    PB_TRY(T.leaf_box.upload(lbox.data(), lbox.size(), m->stream));
+    PB_TRY(T.pair_clus.upload(pc.data(), pc.size(), m->stream));
+    PB_TRY(T.pair_leaf.upload(pl.data(), pl.size(), m->stream));
+    PB_TRY(T.clus_pair.upload(cp.data(), cp.size(), m->stream));
+    PB_TRY(T.leaf_prox.alloc((size_t)P.nleaf * TREE_NPX));
+    PB_TRY(T.up_part.alloc((size_t)T.npair * TREE_NPX));
     PB_TRY(T.up_arrivals.alloc(P.nclus));
     PB_CUDA(cudaMemsetAsync(T.up_arrivals.p, 0, P.nclus * sizeof(int), m->stream));
   }
@@ -416,9 +534,12 @@ int launch_tree_far(Mesh* m, Surface* s, double kappa, const float4* spos, const
   k_tree_permute<<<blocks(nq, 256), 256, 0, m->stream>>>(nq, T.perm.p, spos, sdl, T.spos.p, T.sdl.p);
   PB_LAUNCHED(m);
   if (T.nclus > 0) {
-    k_tree_up<<<T.nseg, TREE_UP_NT, 0, m->stream>>>(T.seg_clus.p, T.seg_beg.p, T.seg_cnt.p, T.clus_seg.p,
-                                                    T.clus_box.p, T.spos.p, T.sdl.p, T.up_part.p, T.up_arrivals.p,
-                                                    T.spos.p + nq, T.sdl.p + nq);
+    k_tree_up_leaf<<<T.nleaf, TREE_UP_NT, 0, m->stream>>>(T.leaf_beg.p, T.leaf_end.p, T.leaf_box.p, T.spos.p,
+                                                            T.sdl.p, T.leaf_prox.p);
+    PB_LAUNCHED(m);
+    k_tree_m2c<<<T.npair, TREE_M2C_NT, 0, m->stream>>>(T.pair_clus.p, T.pair_leaf.p, T.clus_pair.p, T.clus_box.p,
+                                                        T.leaf_box.p, T.leaf_prox.p, T.up_part.p, T.up_arrivals.p,
+                                                        T.spos.p + nq, T.sdl.p + nq);
     PB_LAUNCHED(m);
   }
   const float kf = (float)kappa;
