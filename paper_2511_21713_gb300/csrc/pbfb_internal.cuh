@@ -83,14 +83,14 @@ struct SurfaceTree {
   DBuf<int> leaf_beg, leaf_end, leaf_chunk;  // per leaf: targets [beg, end), chunks [chunk[L], chunk[L+1])
   DBuf<int> chunk_leaf, chunk_tile; // per chunk: its leaf; its tiles [tile[c], tile[c+1])
   DBuf<int2> tiles;                 // per tile: first source record, count (<= 128)
-  int npair = 0;
+  int npair = 0;                    // runs of leaves in the upward pass
   DBuf<float> clus_box;             // per cluster: lo x, y, z, hi x, y, z (centre-relative)
   DBuf<float> leaf_box;             // per leaf: the same
   DBuf<float4> leaf_prox;           // per leaf: its (p+1)^3 proxies (charge, dipole) from its points
-  DBuf<int> pair_clus, pair_leaf;   // per (cluster, leaf of the cluster) pair of the upward pass
-  DBuf<int> clus_pair;              // per approximated cluster: its pairs [clus_pair[k], clus_pair[k + 1])
-  DBuf<float4> up_part;             // per pair: the leaf's proxies on the cluster's grid
-  DBuf<int> up_arrivals;            // per cluster: pairs done in the running upward pass (0 between)
+  DBuf<int> pair_clus, pair_leaf, pair_nleaf;  // per run of leaves of one cluster: cluster, first leaf, leaves
+  DBuf<int> clus_pair;              // per approximated cluster: its runs [clus_pair[k], clus_pair[k + 1])
+  DBuf<float4> up_part;             // per run: its leaves' proxies on the cluster's grid
+  DBuf<int> up_arrivals;            // per cluster: runs done in the running upward pass (0 between)
   DBuf<float4> tgt;                 // target positions in tree order
   DBuf<float4> spos, sdl;           // nq points in tree order, then nclus x (p+1)^3 proxies
   DBuf<double> part;                // nchunk x 256 partial sums
@@ -116,7 +116,7 @@ struct Surface {
   // test reduction: per vertex list of (tri*3 + a)
   DBuf<int> inc_ptr, inc_idx;
   // special pairs
-  int npair = 0;
+  int npair = 0;                    // runs of leaves in the upward pass
   DBuf<int> pair_t, pair_s, pair_cls, pair_perm;  // perm: 6 ints per pair (pt[3], ps[3])
   // correction CSR over surface vertices (pattern of all special pairs)
   int cnnz = 0;

@@ -62,11 +62,12 @@ __global__ void k_tree_permute(int nq, const int* __restrict__ perm, const float
 // column (a, b) -- all p+1 proxies c at once, from one product L_a L_b and two 16-byte reads of the
 // row L_c -- over the points j = g mod 8; the 8 groups of a column are adjacent lanes and are added
 // by a xor butterfly (every lane obtains the same sums).
-// k_tree_m2c: a block per (cluster, leaf of the cluster) pair: the leaf's proxies moved onto the
-// cluster's Chebyshev grid, Q_C[k] += sum_k' L_k^C(s_k') Q_L[k'] -- exact for the degree-p tensor
-// basis L_k^C, so the cluster's proxies equal the sums over its points up to rounding -- as three
-// passes of a (p+1) x (p+1) matrix, one dimension each.  The block that completes a cluster's last
-// pair (a per-cluster arrival counter) adds the cluster's pairs in index order and writes its proxy
+// k_tree_m2c: a block per run of at most TREE_M2C_LEAVES consecutive leaves of one cluster: each
+// leaf's proxies moved onto the cluster's Chebyshev grid, Q_C[k] += sum_k' L_k^C(s_k') Q_L[k'] --
+// exact for the degree-p tensor basis L_k^C, so the cluster's proxies equal the sums over its points
+// up to rounding -- as three passes of a (p+1) x (p+1) matrix, one dimension each, and added in leaf
+// order.  The block that completes a cluster's last run (a per-cluster arrival counter) adds the
+// cluster's runs in index order and writes its proxy
 // source records, then re-arms the counter: the result does not depend on which block arrives last.
 // Each point is touched once per solve-wide leaf instead of once per accepted ancestor.
 __device__ __forceinline__ float cheb_node(const float* __restrict__ cbox, int c, int d, int k) {
@@ -156,9 +157,11 @@ __global__ void __launch_bounds__(TREE_UP_NT) k_tree_up_leaf(const int* __restri
 }
 
 constexpr int TREE_M2C_NT = (TREE_NPX + 31) / 32 * 32;
+constexpr int TREE_M2C_LEAVES = 4;  // leaves per block of k_tree_m2c
 
 __global__ void __launch_bounds__(TREE_M2C_NT) k_tree_m2c(const int* __restrict__ pair_clus,
                                                           const int* __restrict__ pair_leaf,
+                                                          const int* __restrict__ pair_nleaf,
                                                           const int* __restrict__ clus_pair,
                                                           const float* __restrict__ cbox,
                                                           const float* __restrict__ lbox,
@@ -171,65 +174,67 @@ __global__ void __launch_bounds__(TREE_M2C_NT) k_tree_m2c(const int* __restrict_
   __shared__ float4 bufa[TREE_NPX], bufb[TREE_NPX];
   __shared__ int last;
   const int g = blockIdx.x;
-  const int c = pair_clus[g], L = pair_leaf[g];
+  const int c = pair_clus[g], L0 = pair_leaf[g], nl = pair_nleaf[g];
   const int t = threadIdx.x;
   if (t < 3 * TREE_K) cn[t / TREE_K][t % TREE_K] = cheb_node(cbox, c, t / TREE_K, t % TREE_K);
-  for (int i = t; i < TREE_NPX; i += TREE_M2C_NT) bufa[i] = leaf_prox[(size_t)L * TREE_NPX + i];
-  __syncthreads();
-  if (t < 3 * TREE_K) {
-    const int d = t / TREE_K, ap = t % TREE_K;
-    float l[TREE_K];
-    bary_row(cheb_node(lbox, L, d, ap), cn[d], l);
-#pragma unroll
-    for (int k = 0; k < TREE_K; ++k) mt[d][ap][k] = l[k];
-  }
-  __syncthreads();
   const int pa = t / (TREE_K * TREE_K), pb = (t / TREE_K) % TREE_K, pc = t % TREE_K;
   const bool tv = t < TREE_NPX;
-  // x: bufb[a][b'][c'] = sum_a' mt[0][a'][a] bufa[a'][b'][c']
-  if (tv) {
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int L = L0; L < L0 + nl; ++L) {
+    __syncthreads();  // cn ready; the previous leaf's buffers consumed
+    for (int i = t; i < TREE_NPX; i += TREE_M2C_NT) bufa[i] = leaf_prox[(size_t)L * TREE_NPX + i];
+    if (t < 3 * TREE_K) {
+      const int d = t / TREE_K, ap = t % TREE_K;
+      float l[TREE_K];
+      bary_row(cheb_node(lbox, L, d, ap), cn[d], l);
 #pragma unroll
-    for (int ap = 0; ap < TREE_K; ++ap) {
-      const float w = mt[0][ap][pa];
-      const float4 v = bufa[ap * TREE_K * TREE_K + pb * TREE_K + pc];
-      s.x = fmaf(w, v.x, s.x);
-      s.y = fmaf(w, v.y, s.y);
-      s.z = fmaf(w, v.z, s.z);
-      s.w = fmaf(w, v.w, s.w);
+      for (int k = 0; k < TREE_K; ++k) mt[d][ap][k] = l[k];
     }
-    bufb[t] = s;
-  }
-  __syncthreads();
-  // y: bufa[a][b][c'] = sum_b' mt[1][b'][b] bufb[a][b'][c']
-  if (tv) {
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    // x: bufb[a][b'][c'] = sum_a' mt[0][a'][a] bufa[a'][b'][c']
+    if (tv) {
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int bp = 0; bp < TREE_K; ++bp) {
-      const float w = mt[1][bp][pb];
-      const float4 v = bufb[pa * TREE_K * TREE_K + bp * TREE_K + pc];
-      s.x = fmaf(w, v.x, s.x);
-      s.y = fmaf(w, v.y, s.y);
-      s.z = fmaf(w, v.z, s.z);
-      s.w = fmaf(w, v.w, s.w);
+      for (int ap = 0; ap < TREE_K; ++ap) {
+        const float w = mt[0][ap][pa];
+        const float4 v = bufa[ap * TREE_K * TREE_K + pb * TREE_K + pc];
+        s.x = fmaf(w, v.x, s.x);
+        s.y = fmaf(w, v.y, s.y);
+        s.z = fmaf(w, v.z, s.z);
+        s.w = fmaf(w, v.w, s.w);
+      }
+      bufb[t] = s;
     }
-    bufa[t] = s;
-  }
-  __syncthreads();
-  // z: the pair's share of the cluster's proxies
-  if (tv) {
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    // y: bufa[a][b][c'] = sum_b' mt[1][b'][b] bufb[a][b'][c']
+    if (tv) {
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int cp = 0; cp < TREE_K; ++cp) {
-      const float w = mt[2][cp][pc];
-      const float4 v = bufa[pa * TREE_K * TREE_K + pb * TREE_K + cp];
-      s.x = fmaf(w, v.x, s.x);
-      s.y = fmaf(w, v.y, s.y);
-      s.z = fmaf(w, v.z, s.z);
-      s.w = fmaf(w, v.w, s.w);
+      for (int bp = 0; bp < TREE_K; ++bp) {
+        const float w = mt[1][bp][pb];
+        const float4 v = bufb[pa * TREE_K * TREE_K + bp * TREE_K + pc];
+        s.x = fmaf(w, v.x, s.x);
+        s.y = fmaf(w, v.y, s.y);
+        s.z = fmaf(w, v.z, s.z);
+        s.w = fmaf(w, v.w, s.w);
+      }
+      bufa[t] = s;
     }
-    part[(size_t)g * TREE_NPX + t] = s;
+    __syncthreads();
+    // z: this leaf's share of the cluster's proxies, added to the chunk's
+    if (tv) {
+#pragma unroll
+      for (int cp = 0; cp < TREE_K; ++cp) {
+        const float w = mt[2][cp][pc];
+        const float4 v = bufa[pa * TREE_K * TREE_K + pb * TREE_K + cp];
+        acc.x = fmaf(w, v.x, acc.x);
+        acc.y = fmaf(w, v.y, acc.y);
+        acc.z = fmaf(w, v.z, acc.z);
+        acc.w = fmaf(w, v.w, acc.w);
+      }
+    }
   }
+  if (tv) part[(size_t)g * TREE_NPX + t] = acc;
   // the last block of the cluster to arrive sums its pairs (release: fence before the count)
   __threadfence();
   __syncthreads();
@@ -482,16 +487,17 @@ int build_surface_tree(Mesh* m, Surface* s) {
         lbox[6 * (size_t)L + 3 + d] = (float)(hi[d] + pad - s->ctr[d]);
       }
     }
-    std::vector<int> pc, pl, cp(1, 0);
+    std::vector<int> pc, pl, pn, cp(1, 0);  // runs of leaves: cluster, first leaf, leaves
     for (int k = 0; k < P.nclus; ++k) {
       const int L0 = P.pos_leaf[P.clus_beg[k]], L1 = P.pos_leaf[P.clus_end[k] - 1];
       if (P.leaf_beg[L0] != P.clus_beg[k] || P.leaf_end[L1] != P.clus_end[k]) {
         set_error("treecode: a cluster is not a union of leaves");
         return PBFB_ERR_STATE;
       }
-      for (int L = L0; L <= L1; ++L) {
+      for (int L = L0; L <= L1; L += TREE_M2C_LEAVES) {
         pc.push_back(k);
         pl.push_back(L);
+        pn.push_back(std::min(TREE_M2C_LEAVES, L1 + 1 - L));
       }
       cp.push_back((int)pc.size());
     }
@@ -500,6 +506,7 @@ int build_surface_tree(Mesh* m, Surface* s) {
     PB_TRY(T.leaf_box.upload(lbox.data(), lbox.size(), m->stream));
     PB_TRY(T.pair_clus.upload(pc.data(), pc.size(), m->stream));
     PB_TRY(T.pair_leaf.upload(pl.data(), pl.size(), m->stream));
+    PB_TRY(T.pair_nleaf.upload(pn.data(), pn.size(), m->stream));
     PB_TRY(T.clus_pair.upload(cp.data(), cp.size(), m->stream));
     PB_TRY(T.leaf_prox.alloc((size_t)P.nleaf * TREE_NPX));
     PB_TRY(T.up_part.alloc((size_t)T.npair * TREE_NPX));
@@ -537,9 +544,9 @@ int launch_tree_far(Mesh* m, Surface* s, double kappa, const float4* spos, const
     k_tree_up_leaf<<<T.nleaf, TREE_UP_NT, 0, m->stream>>>(T.leaf_beg.p, T.leaf_end.p, T.leaf_box.p, T.spos.p,
                                                             T.sdl.p, T.leaf_prox.p);
     PB_LAUNCHED(m);
-    k_tree_m2c<<<T.npair, TREE_M2C_NT, 0, m->stream>>>(T.pair_clus.p, T.pair_leaf.p, T.clus_pair.p, T.clus_box.p,
-                                                        T.leaf_box.p, T.leaf_prox.p, T.up_part.p, T.up_arrivals.p,
-                                                        T.spos.p + nq, T.sdl.p + nq);
+    k_tree_m2c<<<T.npair, TREE_M2C_NT, 0, m->stream>>>(T.pair_clus.p, T.pair_leaf.p, T.pair_nleaf.p, T.clus_pair.p,
+                                                        T.clus_box.p, T.leaf_box.p, T.leaf_prox.p, T.up_part.p,
+                                                        T.up_arrivals.p, T.spos.p + nq, T.sdl.p + nq);
     PB_LAUNCHED(m);
   }
   const float kf = (float)kappa;
