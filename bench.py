@@ -352,9 +352,9 @@ def run_pbfb(args):
         l32, ms32 = prof["nbody_launches"], prof["nbody_ms"]
         if l32:
             tree = tuned.get("treecode") in (2, 3)
-            name32 = (f"k_tree_eval + k_tree_up (float32 far field of the GMRES operator through the treecode: "
-                      f"near pairs and cluster proxies, packed, {4 if tuned.get('treecode') == 3 else 2} targets "
-                      f"per thread)" if tree
+            name32 = (f"k_tree_eval + k_tree_up_leaf + k_tree_m2c (float32 far field of the GMRES operator "
+                      f"through the treecode: near pairs and cluster proxies, packed, "
+                      f"{4 if tuned.get('treecode') == 3 else 2} targets per thread)" if tree
                       else "k_nbody_f32x2 (float32 far field of the GMRES operator, packed, 2 targets per thread)")
             cands.append(dict(kernel=name32, launches=l32, ms=ms32, pairs=prof["nbody_pairs"],
                               flops=prof["nbody_pairs"] * fpair, peak=peak32,

@@ -52,8 +52,9 @@ struct TreeTiles {
   std::vector<int> clus_beg, clus_end;   // per cluster: its points [beg, end) in tree order
   std::vector<double> clus_box;          // per cluster: lo x, y, z, hi x, y, z (a flat side widened
                                          // to 1e-3 of the longest one)
-  // the upward pass in segments of at most `leaf` consecutive points of one cluster (one GPU block
-  // each), summed per cluster in segment order
+  // each cluster cut into segments of at most `leaf` consecutive points (the work of an upward pass
+  // that sums every cluster from its points; the device pass interpolates leaf proxies instead,
+  // one (cluster, leaf) pair per segment when the leaves are full)
   std::vector<int> seg_clus, seg_beg, seg_cnt;  // per segment: cluster, first point, points
   std::vector<int> clus_seg;             // per cluster: its segments [clus_seg[k], clus_seg[k + 1])
 };
