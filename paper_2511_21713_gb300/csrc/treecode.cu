@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __r
     tz[q] = pk2(tzs[2 * q], tzs[2 * q + 1]);
   }
   const float nk = -kappa * 1.4426950408889634f;
-  const f32x2 nk2 = pk2(nk, nk), kap2 = pk2(kappa, kappa), one2 = pk2(1.f, 1.f);
+  const f32x2 nk2 = pk2(nk, nk), kap2 = pk2(kappa, kappa);
   for (int tl = chunk_tile[c]; tl < chunk_tile[c + 1]; ++tl) {
     const int2 tile = tiles[tl];
     const int s0 = tile.x, cnt = tile.y;
@@ -346,16 +346,15 @@ __global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __r
           upk2(r2, ra, rb);
           const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
           const f32x2 nd = fma2(a3.x, dz, fma2(a2.y, dy, mul2(a2.x, dx)));
-          const f32x2 ri2 = mul2(ri, ri);
           if (YUK) {
-            const f32x2 r = mul2(r2, ri);
+            // [s + m.d (1 + kappa r) / r^2] e^{-kappa r} / r with (1 + kappa r) / r^2 = (1/r + kappa) / r
             float xa, xb;
-            upk2(mul2(nk2, r), xa, xb);
+            upk2(mul2(mul2(nk2, r2), ri), xa, xb);
             const f32x2 ex = pk2(ex2_approx(xa), ex2_approx(xb));
-            const f32x2 tt = fma2(mul2(nd, fma2(kap2, r, one2)), ri2, a1.y);
+            const f32x2 tt = fma2(mul2(nd, ri), add2(ri, kap2), a1.y);
             acc[q] = fma2(tt, mul2(ex, ri), acc[q]);
           } else {
-            acc[q] = fma2(fma2(nd, ri2, a1.y), ri, acc[q]);
+            acc[q] = fma2(fma2(nd, mul2(ri, ri), a1.y), ri, acc[q]);
           }
         }
       }
