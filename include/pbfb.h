@@ -408,9 +408,12 @@ typedef struct pbfb_tuning {
                                         pbfb_newton_opts.residual_far. */
   int32_t pcg_precision;             /* arithmetic of the cooperative inner PCG (CSR forms):
                                         1 float64, 2 float32 (float32 matrix and vectors, float64
-                                        block and grid sums); 0 built-in: float32 in the
-                                        PBFB_MIXED precision, float64 otherwise.  The sliced-ELL
-                                        form (pcg_lanes 1) is float64 only. */
+                                        block and grid sums; meshes of at most 480 FEM rows per SM
+                                        run the pipelined form with each row and its vectors held
+                                        in registers, one grid barrier per step, whatever
+                                        pcg_lanes); 0 built-in: float32 in the PBFB_MIXED
+                                        precision, float64 otherwise.  The sliced-ELL form
+                                        (pcg_lanes 1) is float64 only. */
 } pbfb_tuning;
 
 /* Current launch shapes of a mesh (zeros where the built-in choice applies). */
