@@ -410,8 +410,8 @@ typedef struct pbfb_tuning {
                                         1 float64, 2 float32 (float32 matrix and vectors, float64
                                         block and grid sums; meshes of at most 480 FEM rows per SM
                                         run the pipelined form with each row and its vectors held
-                                        in registers, one grid barrier per step, whatever
-                                        pcg_lanes); 0 built-in: float32 in the PBFB_MIXED
+                                        in registers, one grid barrier per step, for
+                                        pcg_lanes 2, 4 or 8 alike); 0 built-in: float32 in the PBFB_MIXED
                                         precision, float64 otherwise.  The sliced-ELL form
                                         (pcg_lanes 1) is float64 only. */
 } pbfb_tuning;
