@@ -703,6 +703,13 @@ def run_serving_config(args):
         out["fp64"] = run_serving(pbfb, small, args.concurrency, args.budget_gb << 30, 0.0, precision=pbfb.FP64)
         out["mixed_same_subset"] = run_serving(pbfb, small, args.concurrency, args.budget_gb << 30,
                                                args.residual_update, residual_far=args.residual_far)
+        # every request of the subset checked against the float64 GPU path (itself checked against
+        # the oracle at full size): the metric's bound is 1e-5 relative on the energy
+        e64 = np.array(out["fp64"]["energies_kcal_mol"])
+        emx = np.array(out["mixed_same_subset"]["energies_kcal_mol"])
+        err = np.abs(emx - e64) / np.abs(e64)
+        out["mixed_vs_fp64_energy_rel_err"] = {"max": float(err.max()), "median": float(np.median(err)),
+                                               "requests": int(err.size), "within_1e-5": bool(err.max() <= 1e-5)}
     return out
 
 

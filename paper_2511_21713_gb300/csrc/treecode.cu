@@ -273,65 +273,121 @@ __global__ void __launch_bounds__(TREE_M2C_NT) k_tree_m2c(const int* __restrict_
 // source's shared-memory reads).  Tiles that overlap the leaf's own points take the scalar path
 // with the coincident-point test; the others the packed one.  Padding entries (past a tile's
 // count) sit far away with zero strength.
+// Coordinates of the packed paths: sources and targets relative to the centre c of the target
+// leaf's box and, for the Yukawa kernel, multiplied by beta = kappa log2(e), so that
+// e^{-kappa r} = 2^{-r'} with r' = beta r, d' = beta d and
+//   [s + m.d (1/r + kappa)/r] e^{-kappa r}/r = beta [s + (beta m).d' (1/r' + ln 2)/r'] 2^{-r'}/r'
+// (one multiplication per pair fewer; the factor beta is applied once per target at the end).
+// Proxy tiles (sources at index >= nq) are well separated from the leaf: with r_B + r_C < theta D
+// (D the distance of the box centres), |t'| < theta D, |y'| < (1 + theta) D and r > (1 - theta) D,
+// so r'^2 = |t'|^2 + (|y'|^2 - 2 t'.y') and m'.d' = m'.t' - m'.y' lose at most a few units of
+// float32 rounding to cancellation; they come from per-source records (-2y', |y'|^2, m', -m'.y')
+// in six float32 operations per pair fewer than the differences take.
 template <bool YUK, int TPT>
 __global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __restrict__ tgt_t,
                                                                const int* __restrict__ leaf_beg,
                                                                const int* __restrict__ leaf_end,
+                                                               const float* __restrict__ lbox,
                                                                const int* __restrict__ chunk_leaf,
                                                                const int* __restrict__ chunk_tile,
-                                                               const int2* __restrict__ tiles,
+                                                               const int2* __restrict__ tiles, int nq,
                                                                const float4* __restrict__ spos_t,
                                                                const float4* __restrict__ sdl_t, float kappa,
                                                                double* __restrict__ part) {
   constexpr int NT = TREE_LEAF / TPT, NP = TPT / 2;
   __shared__ ulonglong2 sh[4][TREE_TILE];
+  __shared__ f32x2 shs[TREE_TILE];
   __shared__ float4 shp[TREE_TILE], shd[TREE_TILE];
   const int c = blockIdx.x;
   const int L = chunk_leaf[c];
   const int lb = leaf_beg[L], le = leaf_end[L];
-  int ti[TPT];
-  float txs[TPT], tys[TPT], tzs[TPT];
+  const float cx = 0.5f * (lbox[6 * L] + lbox[6 * L + 3]), cy = 0.5f * (lbox[6 * L + 1] + lbox[6 * L + 4]),
+              cz = 0.5f * (lbox[6 * L + 2] + lbox[6 * L + 5]);
+  const float beta = YUK ? kappa * 1.4426950408889634f : 1.f;
   double acc64[TPT];
 #pragma unroll
-  for (int k = 0; k < TPT; ++k) {
-    ti[k] = lb + k * NT + threadIdx.x;
-    const float4 p = tgt_t[ti[k] < le ? ti[k] : lb];
-    txs[k] = p.x;
-    tys[k] = p.y;
-    tzs[k] = p.z;
-    acc64[k] = 0.0;
-  }
-  f32x2 tx[NP], ty[NP], tz[NP];
+  for (int k = 0; k < TPT; ++k) acc64[k] = 0.0;
+  f32x2 tx[NP], ty[NP], tz[NP], tt2[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
-    tx[q] = pk2(txs[2 * q], txs[2 * q + 1]);
-    ty[q] = pk2(tys[2 * q], tys[2 * q + 1]);
-    tz[q] = pk2(tzs[2 * q], tzs[2 * q + 1]);
+    const int ia = lb + 2 * q * NT + threadIdx.x, ib = ia + NT;
+    const float4 pa = tgt_t[ia < le ? ia : lb], pb = tgt_t[ib < le ? ib : lb];
+    const float xa = (pa.x - cx) * beta, xb = (pb.x - cx) * beta;
+    const float ya = (pa.y - cy) * beta, yb = (pb.y - cy) * beta;
+    const float za = (pa.z - cz) * beta, zb = (pb.z - cz) * beta;
+    tx[q] = pk2(xa, xb);
+    ty[q] = pk2(ya, yb);
+    tz[q] = pk2(za, zb);
+    tt2[q] = pk2(fmaf(za, za, fmaf(ya, ya, xa * xa)), fmaf(zb, zb, fmaf(yb, yb, xb * xb)));
   }
-  const float nk = -kappa * 1.4426950408889634f;
-  const f32x2 nk2 = pk2(nk, nk), kap2 = pk2(kappa, kappa);
+  const f32x2 ln2x2 = pk2(0.6931471805599453f, 0.6931471805599453f);
   for (int tl = chunk_tile[c]; tl < chunk_tile[c + 1]; ++tl) {
     const int2 tile = tiles[tl];
     const int s0 = tile.x, cnt = tile.y;
+    const bool far = s0 >= nq;
     for (int i = threadIdx.x; i < TREE_TILE; i += NT) {
       float4 p, d;
       if (i < cnt) {
         p = spos_t[s0 + i];
         d = sdl_t[s0 + i];
       } else {
-        p = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        p = make_float4(1e15f, 1e15f, 1e15f, 0.f);
         d = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      sh[0][i] = make_ulonglong2(pk2(p.x, p.x), pk2(p.y, p.y));
-      sh[1][i] = make_ulonglong2(pk2(p.z, p.z), pk2(p.w, p.w));
-      sh[2][i] = make_ulonglong2(pk2(d.x, d.x), pk2(d.y, d.y));
-      sh[3][i] = make_ulonglong2(pk2(d.z, d.z), 0ull);
+      const float yx = (p.x - cx) * beta, yy = (p.y - cy) * beta, yz = (p.z - cz) * beta;
+      const float mx = d.x * beta, my = d.y * beta, mz = d.z * beta;
+      if (far) {
+        const float y2 = fmaf(yz, yz, fmaf(yy, yy, yx * yx));
+        const float nmy = -fmaf(mz, yz, fmaf(my, yy, mx * yx));
+        sh[0][i] = make_ulonglong2(pk2(-2.f * yx, -2.f * yx), pk2(-2.f * yy, -2.f * yy));
+        sh[1][i] = make_ulonglong2(pk2(-2.f * yz, -2.f * yz), pk2(y2, y2));
+        sh[3][i] = make_ulonglong2(pk2(mz, mz), pk2(nmy, nmy));
+      } else {
+        sh[0][i] = make_ulonglong2(pk2(yx, yx), pk2(yy, yy));
+        sh[1][i] = make_ulonglong2(pk2(yz, yz), pk2(p.w, p.w));
+        sh[3][i] = make_ulonglong2(pk2(mz, mz), 0ull);
+      }
+      sh[2][i] = make_ulonglong2(pk2(mx, mx), pk2(my, my));
+      shs[i] = pk2(p.w, p.w);
       shp[i] = p;
       shd[i] = d;
     }
     __syncthreads();
     const bool diag = s0 < le && s0 + cnt > lb;
-    if (!diag) {
+    if (far) {
+      f32x2 acc[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) acc[q] = 0ull;
+#pragma unroll 2
+      for (int jj = 0; jj < TREE_TILE; ++jj) {
+        const ulonglong2 a0 = sh[0][jj], a1 = sh[1][jj], a2 = sh[2][jj], a3 = sh[3][jj];
+        const f32x2 sj = shs[jj];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const f32x2 r2 = add2(fma2(a0.x, tx[q], fma2(a0.y, ty[q], fma2(a1.x, tz[q], a1.y))), tt2[q]);
+          float ra, rb;
+          upk2(r2, ra, rb);
+          const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
+          const f32x2 nd = fma2(a2.x, tx[q], fma2(a2.y, ty[q], fma2(a3.x, tz[q], a3.y)));
+          if (YUK) {
+            float xa, xb;
+            upk2(mul2(r2, ri), xa, xb);
+            const f32x2 ex = pk2(ex2_approx(-xa), ex2_approx(-xb));
+            const f32x2 tt = fma2(mul2(nd, ri), add2(ri, ln2x2), sj);
+            acc[q] = fma2(tt, mul2(ex, ri), acc[q]);
+          } else {
+            acc[q] = fma2(fma2(nd, mul2(ri, ri), sj), ri, acc[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        float a, b;
+        upk2(acc[q], a, b);
+        acc64[2 * q] += (double)a;
+        acc64[2 * q + 1] += (double)b;
+      }
+    } else if (!diag) {
       f32x2 acc[NP];
 #pragma unroll
       for (int q = 0; q < NP; ++q) acc[q] = 0ull;
@@ -347,11 +403,10 @@ __global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __r
           const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
           const f32x2 nd = fma2(a3.x, dz, fma2(a2.y, dy, mul2(a2.x, dx)));
           if (YUK) {
-            // [s + m.d (1 + kappa r) / r^2] e^{-kappa r} / r with (1 + kappa r) / r^2 = (1/r + kappa) / r
             float xa, xb;
-            upk2(mul2(mul2(nk2, r2), ri), xa, xb);
-            const f32x2 ex = pk2(ex2_approx(xa), ex2_approx(xb));
-            const f32x2 tt = fma2(mul2(nd, ri), add2(ri, kap2), a1.y);
+            upk2(mul2(r2, ri), xa, xb);
+            const f32x2 ex = pk2(ex2_approx(-xa), ex2_approx(-xb));
+            const f32x2 tt = fma2(mul2(nd, ri), add2(ri, ln2x2), a1.y);
             acc[q] = fma2(tt, mul2(ex, ri), acc[q]);
           } else {
             acc[q] = fma2(fma2(nd, mul2(ri, ri), a1.y), ri, acc[q]);
@@ -366,9 +421,19 @@ __global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __r
         acc64[2 * q + 1] += (double)b;
       }
     } else {
-      float accs[TPT];
+      // the leaf's own points, in the original coordinates and units (scaled by 1 / beta here)
+      const float nk = -kappa * 1.4426950408889634f;
+      int ti[TPT];
+      float txs[TPT], tys[TPT], tzs[TPT], accs[TPT];
 #pragma unroll
-      for (int k = 0; k < TPT; ++k) accs[k] = 0.f;
+      for (int k = 0; k < TPT; ++k) {
+        ti[k] = lb + k * NT + threadIdx.x;
+        const float4 p = tgt_t[ti[k] < le ? ti[k] : lb];
+        txs[k] = p.x;
+        tys[k] = p.y;
+        tzs[k] = p.z;
+        accs[k] = 0.f;
+      }
       for (int jj = 0; jj < TREE_TILE; ++jj) {
         const float4 q = shp[jj];
         const float4 m = shd[jj];
@@ -390,13 +455,15 @@ __global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __r
           }
         }
       }
+      const double ib = YUK ? 1.0 / (double)beta : 1.0;
 #pragma unroll
-      for (int k = 0; k < TPT; ++k) acc64[k] += (double)accs[k];
+      for (int k = 0; k < TPT; ++k) acc64[k] += (double)accs[k] * ib;
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int k = 0; k < TPT; ++k) part[(size_t)c * TREE_LEAF + k * NT + threadIdx.x] = acc64[k];
+  for (int k = 0; k < TPT; ++k)
+    part[(size_t)c * TREE_LEAF + k * NT + threadIdx.x] = YUK ? acc64[k] * (double)beta : acc64[k];
 }
 
 // out[i] = in[perm[i]]
@@ -465,10 +532,9 @@ int build_surface_tree(Mesh* m, Surface* s) {
   PB_TRY(T.chunk_leaf.upload(P.chunk_leaf.data(), P.chunk_leaf.size(), m->stream));
   PB_TRY(T.chunk_tile.upload(P.chunk_tile.data(), P.chunk_tile.size(), m->stream));
   PB_TRY(T.tiles.upload(tiles.data(), tiles.size(), m->stream));
-  if (P.nclus > 0) {
-    // leaf boxes (the points' bounding boxes, a flat side widened to 1e-3 of the longest one, as
-    // the clusters'), and per cluster the leaves it is made of: clusters are tree nodes, unions of
-    // consecutive leaves in tree order
+  // leaf boxes (the points' bounding boxes, a flat side widened to 1e-3 of the longest one, as the
+  // clusters'): the upward pass's interpolation grids and the evaluation's coordinate origins
+  {
     std::vector<float> lbox(6 * (size_t)P.nleaf);
     for (int L = 0; L < P.nleaf; ++L) {
       double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -486,6 +552,11 @@ int build_surface_tree(Mesh* m, Surface* s) {
         lbox[6 * (size_t)L + 3 + d] = (float)(hi[d] + pad - s->ctr[d]);
       }
     }
+    PB_TRY(T.leaf_box.upload(lbox.data(), lbox.size(), m->stream));
+  }
+  if (P.nclus > 0) {
+    // per cluster the leaves it is made of: clusters are tree nodes, unions of consecutive leaves
+    // in tree order
     std::vector<int> pc, pl, pn, cp(1, 0);  // runs of leaves: cluster, first leaf, leaves
     for (int k = 0; k < P.nclus; ++k) {
       const int L0 = P.pos_leaf[P.clus_beg[k]], L1 = P.pos_leaf[P.clus_end[k] - 1];
@@ -502,7 +573,6 @@ int build_surface_tree(Mesh* m, Surface* s) {
     }
     T.npair = (int)pc.size();
     PB_TRY(T.clus_box.upload(cbox.data(), cbox.size(), m->stream));
-    PB_TRY(T.leaf_box.upload(lbox.data(), lbox.size(), m->stream));
     PB_TRY(T.pair_clus.upload(pc.data(), pc.size(), m->stream));
     PB_TRY(T.pair_leaf.upload(pl.data(), pl.size(), m->stream));
     PB_TRY(T.pair_nleaf.upload(pn.data(), pn.size(), m->stream));
@@ -549,12 +619,17 @@ int launch_tree_far(Mesh* m, Surface* s, double kappa, const float4* spos, const
     PB_LAUNCHED(m);
   }
   const float kf = (float)kappa;
-  // four targets per thread with treecode = 3, else two
+  // four targets per thread with treecode = 3, else two.  The Yukawa form works in coordinates
+  // scaled by kappa log2(e); below 1e-12 (no physical ionic strength) the kernel is the Laplace one
+  // to far below float32 rounding (kappa r < 1e-9 here) and runs as such, keeping the scaled
+  // squares clear of underflow.
   const bool four = m->tune_tree == 3;
-  const void* fn = kappa != 0.0 ? (four ? (const void*)k_tree_eval<true, 4> : (const void*)k_tree_eval<true, 2>)
-                                : (four ? (const void*)k_tree_eval<false, 4> : (const void*)k_tree_eval<false, 2>);
-  void* args[] = {&T.tgt.p, &T.leaf_beg.p, &T.leaf_end.p, &T.chunk_leaf.p, &T.chunk_tile.p, &T.tiles.p,
-                  &T.spos.p, &T.sdl.p, (void*)&kf, &T.part.p};
+  const bool yuk = kappa * 1.4426950408889634 >= 1e-12;
+  const void* fn = yuk ? (four ? (const void*)k_tree_eval<true, 4> : (const void*)k_tree_eval<true, 2>)
+                       : (four ? (const void*)k_tree_eval<false, 4> : (const void*)k_tree_eval<false, 2>);
+  int nqa = nq;
+  void* args[] = {&T.tgt.p,   &T.leaf_beg.p, &T.leaf_end.p, &T.leaf_box.p, &T.chunk_leaf.p, &T.chunk_tile.p,
+                  &T.tiles.p, &nqa,          &T.spos.p,     &T.sdl.p,      (void*)&kf,      &T.part.p};
   PB_CUDA(cudaLaunchKernel(fn, dim3(T.nchunk), dim3(TREE_LEAF / (four ? 4 : 2)), args, 0, m->stream));
   PB_LAUNCHED(m);
   k_tree_sum<<<blocks(nq, 256), 256, 0, m->stream>>>(nq, T.perm.p, T.pos_leaf.p, T.leaf_beg.p, T.leaf_chunk.p,
