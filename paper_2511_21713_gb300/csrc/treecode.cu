@@ -40,6 +40,7 @@ constexpr int TREE_UP_G = 8;                 // upward pass: point groups per (a
 constexpr int TREE_UP_NT = (TREE_K * TREE_K * TREE_UP_G + 31) / 32 * 32;  // threads of the upward pass
 static_assert(TREE_UP_NT >= TREE_NPX && TREE_K <= 8, "upward pass shapes");
 constexpr int TREE_TILES_PER_CHUNK = 8;      // source tiles per block
+constexpr int TREE_EVAL_MINB = 8;            // evaluation blocks per SM the registers must allow (measured best)
 constexpr double TREE_THETA = 0.6;           // acceptance: r_B + r_C < theta |c_B - c_C|
 
 // tree order: spos_t[i] = spos[perm[i]] (sources and, for positions, the targets)
@@ -269,10 +270,16 @@ __global__ void __launch_bounds__(TREE_M2C_NT) k_tree_m2c(const int* __restrict_
 }
 
 // Evaluation: block = one chunk (a target leaf and a run of its source tiles of TREE_TILE records),
-// TPT targets per thread (2: 128 threads, one f32x2 pack; 4: 64 threads, two packs that share each
-// source's shared-memory reads).  Tiles that overlap the leaf's own points take the scalar path
-// with the coincident-point test; the others the packed one.  Padding entries (past a tile's
-// count) sit far away with zero strength.
+// TPT targets per thread (2: 128 threads; 4: 64 threads).  Tiles that overlap the leaf's own points
+// take the scalar path with the coincident-point test; the others the packed one.  Padding entries
+// (past a tile's count) sit far away with zero strength.
+// Packed paths: a source tile sits in shared memory as one float array per record field, and a
+// thread takes two consecutive sources at a time -- one 8-byte read per field is the f32x2 pack of
+// both, every lane of the warp reading the same address -- against each of its targets held
+// duplicated in both halves of a pack: per pair of sources and target one f32x2 operation does the
+// work of two pairs.  (Reading one source duplicated into both halves, as the direct-sum kernels
+// do, moves twice the shared-memory bytes per pair, and the shared-memory data path then bounds the
+// kernel.)
 // Coordinates of the packed paths: sources and targets relative to the centre c of the target
 // leaf's box and, for the Yukawa kernel, multiplied by beta = kappa log2(e), so that
 // e^{-kappa r} = 2^{-r'} with r' = beta r, d' = beta d and
@@ -281,10 +288,12 @@ __global__ void __launch_bounds__(TREE_M2C_NT) k_tree_m2c(const int* __restrict_
 // Proxy tiles (sources at index >= nq) are well separated from the leaf: with r_B + r_C < theta D
 // (D the distance of the box centres), |t'| < theta D, |y'| < (1 + theta) D and r > (1 - theta) D,
 // so r'^2 = |t'|^2 + (|y'|^2 - 2 t'.y') and m'.d' = m'.t' - m'.y' lose at most a few units of
-// float32 rounding to cancellation; they come from per-source records (-2y', |y'|^2, m', -m'.y')
+// float32 rounding to cancellation; they come from per-source fields (-2y', |y'|^2, m', -m'.y')
 // in six float32 operations per pair fewer than the differences take.
+enum { F_X, F_Y, F_Z, F_S, F_MX, F_MY, F_MZ, F_Q, F_P, F_N };  // shared-memory fields of a source tile
+
 template <bool YUK, int TPT>
-__global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __restrict__ tgt_t,
+__global__ void __launch_bounds__(TREE_LEAF / TPT, TREE_EVAL_MINB) k_tree_eval(const float4* __restrict__ tgt_t,
                                                                const int* __restrict__ leaf_beg,
                                                                const int* __restrict__ leaf_end,
                                                                const float* __restrict__ lbox,
@@ -294,9 +303,8 @@ __global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __r
                                                                const float4* __restrict__ spos_t,
                                                                const float4* __restrict__ sdl_t, float kappa,
                                                                double* __restrict__ part) {
-  constexpr int NT = TREE_LEAF / TPT, NP = TPT / 2;
-  __shared__ ulonglong2 sh[4][TREE_TILE];
-  __shared__ f32x2 shs[TREE_TILE];
+  constexpr int NT = TREE_LEAF / TPT;
+  __shared__ __align__(16) float fld[F_N][TREE_TILE];
   __shared__ float4 shp[TREE_TILE], shd[TREE_TILE];
   const int c = blockIdx.x;
   const int L = chunk_leaf[c];
@@ -305,20 +313,18 @@ __global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __r
               cz = 0.5f * (lbox[6 * L + 2] + lbox[6 * L + 5]);
   const float beta = YUK ? kappa * 1.4426950408889634f : 1.f;
   double acc64[TPT];
+  f32x2 tx[TPT], ty[TPT], tz[TPT], tt2[TPT];
 #pragma unroll
-  for (int k = 0; k < TPT; ++k) acc64[k] = 0.0;
-  f32x2 tx[NP], ty[NP], tz[NP], tt2[NP];
-#pragma unroll
-  for (int q = 0; q < NP; ++q) {
-    const int ia = lb + 2 * q * NT + threadIdx.x, ib = ia + NT;
-    const float4 pa = tgt_t[ia < le ? ia : lb], pb = tgt_t[ib < le ? ib : lb];
-    const float xa = (pa.x - cx) * beta, xb = (pb.x - cx) * beta;
-    const float ya = (pa.y - cy) * beta, yb = (pb.y - cy) * beta;
-    const float za = (pa.z - cz) * beta, zb = (pb.z - cz) * beta;
-    tx[q] = pk2(xa, xb);
-    ty[q] = pk2(ya, yb);
-    tz[q] = pk2(za, zb);
-    tt2[q] = pk2(fmaf(za, za, fmaf(ya, ya, xa * xa)), fmaf(zb, zb, fmaf(yb, yb, xb * xb)));
+  for (int k = 0; k < TPT; ++k) {
+    acc64[k] = 0.0;
+    const int i = lb + k * NT + threadIdx.x;
+    const float4 p = tgt_t[i < le ? i : lb];
+    const float x = (p.x - cx) * beta, y = (p.y - cy) * beta, z = (p.z - cz) * beta;
+    tx[k] = pk2(x, x);
+    ty[k] = pk2(y, y);
+    tz[k] = pk2(z, z);
+    const float t2 = fmaf(z, z, fmaf(y, y, x * x));
+    tt2[k] = pk2(t2, t2);
   }
   const f32x2 ln2x2 = pk2(0.6931471805599453f, 0.6931471805599453f);
   for (int tl = chunk_tile[c]; tl < chunk_tile[c + 1]; ++tl) {
@@ -337,88 +343,94 @@ __global__ void __launch_bounds__(TREE_LEAF / TPT) k_tree_eval(const float4* __r
       const float yx = (p.x - cx) * beta, yy = (p.y - cy) * beta, yz = (p.z - cz) * beta;
       const float mx = d.x * beta, my = d.y * beta, mz = d.z * beta;
       if (far) {
-        const float y2 = fmaf(yz, yz, fmaf(yy, yy, yx * yx));
-        const float nmy = -fmaf(mz, yz, fmaf(my, yy, mx * yx));
-        sh[0][i] = make_ulonglong2(pk2(-2.f * yx, -2.f * yx), pk2(-2.f * yy, -2.f * yy));
-        sh[1][i] = make_ulonglong2(pk2(-2.f * yz, -2.f * yz), pk2(y2, y2));
-        sh[3][i] = make_ulonglong2(pk2(mz, mz), pk2(nmy, nmy));
+        fld[F_X][i] = -2.f * yx;
+        fld[F_Y][i] = -2.f * yy;
+        fld[F_Z][i] = -2.f * yz;
+        fld[F_Q][i] = fmaf(yz, yz, fmaf(yy, yy, yx * yx));
+        fld[F_P][i] = -fmaf(mz, yz, fmaf(my, yy, mx * yx));
       } else {
-        sh[0][i] = make_ulonglong2(pk2(yx, yx), pk2(yy, yy));
-        sh[1][i] = make_ulonglong2(pk2(yz, yz), pk2(p.w, p.w));
-        sh[3][i] = make_ulonglong2(pk2(mz, mz), 0ull);
+        fld[F_X][i] = yx;
+        fld[F_Y][i] = yy;
+        fld[F_Z][i] = yz;
       }
-      sh[2][i] = make_ulonglong2(pk2(mx, mx), pk2(my, my));
-      shs[i] = pk2(p.w, p.w);
+      fld[F_S][i] = p.w;
+      fld[F_MX][i] = mx;
+      fld[F_MY][i] = my;
+      fld[F_MZ][i] = mz;
       shp[i] = p;
       shd[i] = d;
     }
     __syncthreads();
     const bool diag = s0 < le && s0 + cnt > lb;
-    if (far) {
-      f32x2 acc[NP];
+    if (!diag) {
+      f32x2 acc[TPT];
 #pragma unroll
-      for (int q = 0; q < NP; ++q) acc[q] = 0ull;
+      for (int k = 0; k < TPT; ++k) acc[k] = 0ull;
+      if (far) {
 #pragma unroll 2
-      for (int jj = 0; jj < TREE_TILE; ++jj) {
-        const ulonglong2 a0 = sh[0][jj], a1 = sh[1][jj], a2 = sh[2][jj], a3 = sh[3][jj];
-        const f32x2 sj = shs[jj];
+        for (int jj = 0; jj < TREE_TILE; jj += 2) {
+          const f32x2 X = *reinterpret_cast<const f32x2*>(&fld[F_X][jj]);
+          const f32x2 Y = *reinterpret_cast<const f32x2*>(&fld[F_Y][jj]);
+          const f32x2 Z = *reinterpret_cast<const f32x2*>(&fld[F_Z][jj]);
+          const f32x2 Q = *reinterpret_cast<const f32x2*>(&fld[F_Q][jj]);
+          const f32x2 MX = *reinterpret_cast<const f32x2*>(&fld[F_MX][jj]);
+          const f32x2 MY = *reinterpret_cast<const f32x2*>(&fld[F_MY][jj]);
+          const f32x2 MZ = *reinterpret_cast<const f32x2*>(&fld[F_MZ][jj]);
+          const f32x2 P = *reinterpret_cast<const f32x2*>(&fld[F_P][jj]);
+          const f32x2 S = *reinterpret_cast<const f32x2*>(&fld[F_S][jj]);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          const f32x2 r2 = add2(fma2(a0.x, tx[q], fma2(a0.y, ty[q], fma2(a1.x, tz[q], a1.y))), tt2[q]);
-          float ra, rb;
-          upk2(r2, ra, rb);
-          const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
-          const f32x2 nd = fma2(a2.x, tx[q], fma2(a2.y, ty[q], fma2(a3.x, tz[q], a3.y)));
-          if (YUK) {
-            float xa, xb;
-            upk2(mul2(r2, ri), xa, xb);
-            const f32x2 ex = pk2(ex2_approx(-xa), ex2_approx(-xb));
-            const f32x2 tt = fma2(mul2(nd, ri), add2(ri, ln2x2), sj);
-            acc[q] = fma2(tt, mul2(ex, ri), acc[q]);
-          } else {
-            acc[q] = fma2(fma2(nd, mul2(ri, ri), sj), ri, acc[q]);
+          for (int k = 0; k < TPT; ++k) {
+            const f32x2 r2 = add2(fma2(X, tx[k], fma2(Y, ty[k], fma2(Z, tz[k], Q))), tt2[k]);
+            float ra, rb;
+            upk2(r2, ra, rb);
+            const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
+            const f32x2 nd = fma2(MX, tx[k], fma2(MY, ty[k], fma2(MZ, tz[k], P)));
+            if (YUK) {
+              float xa, xb;
+              upk2(mul2(r2, ri), xa, xb);
+              const f32x2 ex = pk2(ex2_approx(-xa), ex2_approx(-xb));
+              const f32x2 tt = fma2(mul2(nd, ri), add2(ri, ln2x2), S);
+              acc[k] = fma2(tt, mul2(ex, ri), acc[k]);
+            } else {
+              acc[k] = fma2(fma2(nd, mul2(ri, ri), S), ri, acc[k]);
+            }
+          }
+        }
+      } else {
+#pragma unroll 2
+        for (int jj = 0; jj < TREE_TILE; jj += 2) {
+          const f32x2 X = *reinterpret_cast<const f32x2*>(&fld[F_X][jj]);
+          const f32x2 Y = *reinterpret_cast<const f32x2*>(&fld[F_Y][jj]);
+          const f32x2 Z = *reinterpret_cast<const f32x2*>(&fld[F_Z][jj]);
+          const f32x2 MX = *reinterpret_cast<const f32x2*>(&fld[F_MX][jj]);
+          const f32x2 MY = *reinterpret_cast<const f32x2*>(&fld[F_MY][jj]);
+          const f32x2 MZ = *reinterpret_cast<const f32x2*>(&fld[F_MZ][jj]);
+          const f32x2 S = *reinterpret_cast<const f32x2*>(&fld[F_S][jj]);
+#pragma unroll
+          for (int k = 0; k < TPT; ++k) {
+            const f32x2 dx = sub2(tx[k], X), dy = sub2(ty[k], Y), dz = sub2(tz[k], Z);
+            const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+            float ra, rb;
+            upk2(r2, ra, rb);
+            const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
+            const f32x2 nd = fma2(MZ, dz, fma2(MY, dy, mul2(MX, dx)));
+            if (YUK) {
+              float xa, xb;
+              upk2(mul2(r2, ri), xa, xb);
+              const f32x2 ex = pk2(ex2_approx(-xa), ex2_approx(-xb));
+              const f32x2 tt = fma2(mul2(nd, ri), add2(ri, ln2x2), S);
+              acc[k] = fma2(tt, mul2(ex, ri), acc[k]);
+            } else {
+              acc[k] = fma2(fma2(nd, mul2(ri, ri), S), ri, acc[k]);
+            }
           }
         }
       }
 #pragma unroll
-      for (int q = 0; q < NP; ++q) {
+      for (int k = 0; k < TPT; ++k) {
         float a, b;
-        upk2(acc[q], a, b);
-        acc64[2 * q] += (double)a;
-        acc64[2 * q + 1] += (double)b;
-      }
-    } else if (!diag) {
-      f32x2 acc[NP];
-#pragma unroll
-      for (int q = 0; q < NP; ++q) acc[q] = 0ull;
-#pragma unroll 2
-      for (int jj = 0; jj < TREE_TILE; ++jj) {
-        const ulonglong2 a0 = sh[0][jj], a1 = sh[1][jj], a2 = sh[2][jj], a3 = sh[3][jj];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          const f32x2 dx = sub2(tx[q], a0.x), dy = sub2(ty[q], a0.y), dz = sub2(tz[q], a1.x);
-          const f32x2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-          float ra, rb;
-          upk2(r2, ra, rb);
-          const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
-          const f32x2 nd = fma2(a3.x, dz, fma2(a2.y, dy, mul2(a2.x, dx)));
-          if (YUK) {
-            float xa, xb;
-            upk2(mul2(r2, ri), xa, xb);
-            const f32x2 ex = pk2(ex2_approx(-xa), ex2_approx(-xb));
-            const f32x2 tt = fma2(mul2(nd, ri), add2(ri, ln2x2), a1.y);
-            acc[q] = fma2(tt, mul2(ex, ri), acc[q]);
-          } else {
-            acc[q] = fma2(fma2(nd, mul2(ri, ri), a1.y), ri, acc[q]);
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < NP; ++q) {
-        float a, b;
-        upk2(acc[q], a, b);
-        acc64[2 * q] += (double)a;
-        acc64[2 * q + 1] += (double)b;
+        upk2(acc[k], a, b);
+        acc64[k] += (double)a + (double)b;
       }
     } else {
       // the leaf's own points, in the original coordinates and units (scaled by 1 / beta here)
