@@ -13,7 +13,7 @@
 //     proxy sum is the same kernel evaluated at the proxies (barycentric Lagrange treecode of
 //     Wang, Tlupova and Krasny, 2020).
 // Both parts run through one kernel: a block takes one target leaf (up to 256 targets, two per
-// thread on the packed f32x2 instructions) and a chunk of its source tiles (runs of at most 128
+// thread, two sources per packed f32x2 operation) and a chunk of its source tiles (runs of at most 128
 // consecutive source records: leaf points in tree order, or a cluster's proxies), and writes its
 // partial sums; the chunks of a leaf are then added in a fixed order, so the result does not
 // depend on scheduling.  The host plan (tree, acceptance, tiles, chunks) is built once per surface.
