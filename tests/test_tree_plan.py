@@ -320,3 +320,44 @@ def test_tree_tiles_plan_bounds_and_coverage(tiles_driver, nu):
     if nu == 20:
         # the bench-sized surface: proxies replace a good share of the direct pairs
         assert nclus > 0 and p["pairs"] < 0.7 * n * n
+
+
+def test_proxy_tiles_well_separated_from_their_leaf(tiles_driver):
+    """The evaluation kernel forms r^2 on proxy tiles as |t'|^2 + |y'|^2 - 2 t'.y' about the centre
+    of the target leaf's box, which is accurate only while every proxy stays well away from every
+    target of the leaf: with the acceptance rule r_B + r_C < theta D the targets lie within theta D
+    of the leaf centre, the proxies (tensor Chebyshev points of the cluster box, corners included)
+    within (1 + theta) D, and each target-proxy distance exceeds (1 - theta) D, so
+    (|t'| + |y'|) / |t - y| < (1 + 2 theta) / (1 - theta).  Checked point by point on the bench-sized
+    surface at theta = 0.6 (the kernel's), with the leaf boxes widened as the device plan widens them."""
+    theta = 0.6
+    xyz = quadrature_like_points(20)
+    n = len(xyz)
+    p = tiles_plan(tiles_driver, xyz, theta=theta)
+    assert p["status"] == 0 and p["nclus"] > 0
+    perm, lb, le, lc = p["perm"], p["leaf_beg"], p["leaf_end"], p["leaf_chunk"]
+    ct, ts, tc = p["chunk_tile"], p["tile_start"], p["tile_count"]
+    box = p["clus_box"].reshape(-1, 6)
+    cheb = np.cos(np.pi * np.arange(7) / 6)
+    worst = 0.0
+    ntile = 0
+    for L in range(len(lb)):
+        t = xyz[perm[lb[L]:le[L]]]
+        lo, hi = t.min(0), t.max(0)
+        pad = np.maximum(0.0, 1e-3 * (hi - lo).max() - (hi - lo)) * 0.5
+        c = 0.5 * ((lo - pad) + (hi + pad))
+        for ch in range(lc[L], lc[L + 1]):
+            for k in range(ct[ch], ct[ch + 1]):
+                if ts[k] < n:
+                    continue
+                ntile += 1
+                C = (ts[k] - n) // 343
+                bl, bh = box[C, :3], box[C, 3:]
+                g = [0.5 * (bl[d] + bh[d]) + 0.5 * (bh[d] - bl[d]) * cheb for d in range(3)]
+                y = np.stack(np.meshgrid(*g, indexing="ij"), -1).reshape(-1, 3)
+                y = y[(ts[k] - n) % 343:(ts[k] - n) % 343 + tc[k]]
+                r = np.linalg.norm(t[:, None, :] - y[None, :, :], axis=2)
+                ratio = (np.linalg.norm(t - c, axis=1)[:, None] + np.linalg.norm(y - c, axis=1)[None, :]) / r
+                worst = max(worst, ratio.max())
+    assert ntile > 0
+    assert worst < (1 + 2 * theta) / (1 - theta), worst
